@@ -1,0 +1,172 @@
+/*
+ * raftgp.h -- C ABI of the GB300 (sm_103a) RaftGP hot path.
+ *
+ * RaftGP (Gao et al., HPEC 2023) partitions an undirected graph in three stages:
+ *   1. random feature extraction, Y = X Theta (Section III-A, Eq. 5), X one of
+ *        M       = D^-1/2 A D^-1/2                      (NCut operator, Eq. 2)
+ *        Q       = A - d d^T / 2e  (full modularity matrix, Eq. 4), applied as the sparse
+ *                  product A Theta minus the rank-one term d (d^T Theta) / 2e
+ *        Q-tilde = Q kept on the edges of G only       (reduced modularity, Section III-A);
+ *   2. a randomly initialised, untrained GCN (Section III-B, Eq. 6):
+ *        Z^(k) = rownorm(tanh(D-hat^-1/2 (A+I) D-hat^-1/2 Z^(k-1) W^(k))),  Z^(0) = Y;
+ *   3. model selection: k-means for candidate block counts K, each partition scored by
+ *      modularity (Eq. 3, evaluated as Eq. 7 with U = V) or NCut (Eq. 1); the best wins
+ *      (Section III-C; the problem statement, Def. 1, leaves K unknown).
+ *
+ * Conventions for every entry point:
+ *   - Graphs are symmetric CSR without self loops or duplicate entries (Section II:
+ *     undirected, unweighted).  row_ptr has n+1 entries (int32 or int64), col has nnz int32
+ *     entries, nnz = 2|E|.  All graph, feature and label arrays are DEVICE pointers owned by
+ *     the caller; the library never allocates or frees device memory.  Scratch memory is a
+ *     caller-owned device workspace whose size raftgp_workspace_size() returns.
+ *   - Every call is ordered on the given CUDA stream.  Calls with host outputs synchronise
+ *     that stream before returning; the others return as soon as the work is queued.
+ *   - Every call returns a raftgp_status and never aborts.  Invalid arguments (null
+ *     pointers, sizes out of range, a workspace that is too small) return RAFTGP_EINVAL or
+ *     RAFTGP_ENOMEM before any work is queued.  Device-side checks (column index out of
+ *     range, decreasing row_ptr, a self loop) set an error word that is read at the end of
+ *     the call and reported as RAFTGP_EINVAL.  raftgp_last_error() gives a message.
+ *   - Floating point: features are stored in FP32 or BF16 and always accumulated in FP32.
+ *     Block edge counts and volumes are exact int64; modularity is one FP64 division of an
+ *     exact integer numerator by an exact integer denominator; NCut is an FP64 sum in
+ *     ascending block order.  k-means centroid sums are exact 2^-40 fixed point (int64),
+ *     the means are formed in FP64.
+ */
+#ifndef RAFTGP_H
+#define RAFTGP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* raftgp_stream_t; /* a cudaStream_t; NULL is the legacy default stream */
+
+typedef enum {
+    RAFTGP_OK = 0,
+    RAFTGP_EINVAL = 1,      /* bad argument or malformed graph */
+    RAFTGP_ENOMEM = 2,      /* workspace too small */
+    RAFTGP_ECUDA = 3,       /* a CUDA runtime call failed */
+    RAFTGP_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
+    RAFTGP_EUNSUPPORTED = 5 /* a size or mode this build does not support */
+} raftgp_status;
+
+enum { RAFTGP_OP_NCUT = 0, RAFTGP_OP_MOD_FULL = 1, RAFTGP_OP_MOD_REDUCED = 2 };
+enum { RAFTGP_F32 = 0, RAFTGP_BF16 = 1 };
+enum { RAFTGP_CRIT_MOD = 0, RAFTGP_CRIT_NCUT = 1 };
+/* k-means distance engine: plain FP32 FMA, or BF16 tcgen05 tensor cores with an FP32
+ * re-check of near ties in the final assignment. */
+enum { RAFTGP_ASSIGN_FFMA = 0, RAFTGP_ASSIGN_TC = 1 };
+
+#define RAFTGP_MAX_LAYERS 4
+#define RAFTGP_MAX_BATCH_CAND 64 /* candidates evaluated together in one batch */
+
+typedef struct {
+    int64_t n;            /* number of nodes */
+    int64_t nnz;          /* number of stored entries (2|E|) */
+    const void* row_ptr;  /* device, n+1 entries, row_ptr[0] = 0, row_ptr[n] = nnz */
+    int32_t row_ptr_bits; /* 32 or 64 */
+    const int32_t* col;   /* device, nnz entries in [0, n) */
+} raftgp_csr;
+
+/* Embedding options (Section III-A/B). */
+typedef struct {
+    int32_t op;        /* RAFTGP_OP_*: the operator X of Eq. 5 */
+    int32_t n_layers;  /* GCN layers, 0..RAFTGP_MAX_LAYERS; 0 = no GCN (Z = rownorm(Y)) */
+    int32_t dims[RAFTGP_MAX_LAYERS + 1]; /* dims[0] = L, dims[k] = width of layer k;
+                                            each one of 32, 64, 128 */
+    int32_t dtype;     /* RAFTGP_F32 or RAFTGP_BF16: storage of Theta, hidden features, Z */
+    uint64_t seed;     /* Philox4x32-10 key for Theta and W */
+    const float* theta;                 /* optional device N x L FP32 row-major; NULL = draw */
+    const float* W[RAFTGP_MAX_LAYERS];  /* optional device FP32 row-major L_{k-1} x L_k */
+    void* stage_out[RAFTGP_MAX_LAYERS + 1]; /* optional device outputs in `dtype`: stage 0 =
+                                               Y (N x L), stage k = Z^(k) (N x dims[k]) */
+} raftgp_embed_opts;
+
+/* Model-selection options (Section III-C). */
+typedef struct {
+    int32_t kmin, kmax; /* candidate range, 1 <= kmin <= kmax (kmax is clamped to n) */
+    int32_t grid;       /* 0: every K in [kmin, kmax]; G > 0: a coarse grid of G values, then
+                           G refined values between the neighbours of the best coarse K */
+    int32_t iters;      /* maximum Lloyd assignment passes per candidate (>= 1) */
+    int32_t criterion;  /* RAFTGP_CRIT_MOD (default) or RAFTGP_CRIT_NCUT */
+    int32_t assign;     /* RAFTGP_ASSIGN_FFMA or RAFTGP_ASSIGN_TC */
+    int32_t batch;      /* candidates evaluated together (1 = one at a time, the plain form;
+                           0 = as many as fit, at most RAFTGP_MAX_BATCH_CAND) */
+    uint64_t seed;      /* Philox4x32-10 key for k-means++ */
+} raftgp_select_opts;
+
+/* Per-candidate report of raftgp_select / raftgp_partition (host memory). */
+typedef struct {
+    int32_t k_best;        /* out: chosen K */
+    int32_t n_cand;        /* out: candidates evaluated */
+    int32_t cand_cap;      /* in: capacity of the arrays below (they may be NULL if 0) */
+    int32_t* cand_k;       /* out: K of each evaluated candidate, in evaluation order */
+    double* cand_mod;      /* out: modularity (Eq. 3) */
+    double* cand_ncut;     /* out: NCut (Eq. 1) */
+    int32_t* cand_passes;  /* out: Lloyd assignment passes used */
+} raftgp_select_result;
+
+/* Bytes of device workspace the calls below need for this graph and these options.
+ * Pass eopts = NULL for a selection-only call and sopts = NULL for an embedding-only call.
+ * d (the embedding width) is used only when eopts is NULL.  Returns 0 on invalid input. */
+size_t raftgp_workspace_size(const raftgp_csr* g, const raftgp_embed_opts* eopts,
+                             const raftgp_select_opts* sopts, int32_t d);
+
+/* Stages 1-2: Z = the normalised output of the last GCN layer (N x dims[n_layers], stored
+ * in eopts->dtype, row-major) written to the device buffer Z.  Section III-A (Eq. 5) and
+ * III-B (Eq. 6 and the row-wise l2 normalisation).  Asynchronous. */
+raftgp_status raftgp_embed(const raftgp_csr* g, const raftgp_embed_opts* eopts, void* Z, void* ws,
+                           size_t ws_bytes, raftgp_stream_t stream);
+
+/* Stage 3: choose K and the partition for embeddings Z (device, N x d row-major, d one of
+ * 32, 64, 128, stored as z_dtype).  Requires rows of norm <= 1 (the GCN output has unit
+ * rows).  labels: device int32[N], the chosen partition, values in [0, k_best).  res: host
+ * report (may be NULL).  Synchronises the stream. */
+raftgp_status raftgp_select(const raftgp_csr* g, const void* Z, int32_t d, int32_t z_dtype,
+                            const raftgp_select_opts* sopts, int32_t* labels, raftgp_select_result* res,
+                            void* ws, size_t ws_bytes, raftgp_stream_t stream);
+
+/* Stages 1-3 end to end: raftgp_embed followed by raftgp_select.  Synchronises the stream. */
+raftgp_status raftgp_partition(const raftgp_csr* g, const raftgp_embed_opts* eopts,
+                               const raftgp_select_opts* sopts, int32_t* labels, raftgp_select_result* res,
+                               void* ws, size_t ws_bytes, raftgp_stream_t stream);
+
+/* Score a given partition: m[r] = number of undirected edges inside block r, vol[r] = sum of
+ * the degrees in block r (both device int64[K], exact), *mod = Eq. 3 (via Eq. 7 with U = V,
+ * exact integer numerator, one FP64 division) and *ncut = Eq. 1 (host doubles).
+ * labels: device int32[N] with values in [0, K).  Synchronises the stream. */
+raftgp_status raftgp_score(const raftgp_csr* g, const int32_t* labels, int32_t K, int64_t* m, int64_t* vol,
+                           double* mod, double* ncut, void* ws, size_t ws_bytes, raftgp_stream_t stream);
+
+/* k-means++ seeding alone (the seeding step of stage 3): seeds (device int32[K]) receive K
+ * point indices drawn by D^2 sampling from Z (device N x d, z_dtype).  D^2 is the FP32
+ * direct-form squared distance summed over ascending coordinates, quantised to
+ * floor(D^2 * 2^40) (uint64); draw t: r = Philox(seed; t, 0, 0, "Kmpp") words 0-1,
+ * threshold floor(r * sum_q / 2^64), first index whose inclusive prefix exceeds it; if every
+ * q is 0 the lowest-index unchosen point.  Asynchronous. */
+raftgp_status raftgp_kmeanspp(const void* Z, int64_t n, int32_t d, int32_t z_dtype, int32_t K, uint64_t seed,
+                              int32_t* seeds, void* ws, size_t ws_bytes, raftgp_stream_t stream);
+
+/* Lloyd's k-means alone from given FP32 initial centroids mu0 (device K x d): at most
+ * `iters` assignment passes, ties to the lowest centroid, stop when no label changes, an
+ * empty cluster keeps its centroid.  labels: device int32[N]; mu_out: device FP32 K x d
+ * (may be NULL); *passes (host): assignment passes used.  `assign` picks the distance
+ * engine.  Synchronises the stream. */
+raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype, const float* mu0, int32_t K,
+                           int32_t iters, int32_t assign, int32_t* labels, float* mu_out, int32_t* passes,
+                           void* ws, size_t ws_bytes, raftgp_stream_t stream);
+
+/* Message for the last non-OK status returned on the calling thread. */
+const char* raftgp_last_error(void);
+
+/* Library version string. */
+const char* raftgp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RAFTGP_H */

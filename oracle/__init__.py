@@ -187,7 +187,7 @@ def refine_grid(lo, hi, G, done):
     return out[:cnt].tolist()
 
 
-def select(g, Z, kmin, kmax, grid=0, T=50, seed=2, criterion=CRIT_MOD):
+def select(g, Z, kmin, kmax, grid=0, T=50, seed=2, criterion=CRIT_MOD, seed_fp32=False):
     """Model selection; returns dict(labels, k, cands=[(K, mod, ncut, passes), ...])."""
     rp, col = _keep(g)
     Z = _f64(Z)
@@ -201,7 +201,8 @@ def select(g, Z, kmin, kmax, grid=0, T=50, seed=2, criterion=CRIT_MOD):
     cp = np.zeros(cap, dtype=np.int32)
     _check(lib().orc_select(C.c_int64(g.n), _p(rp, C.c_int64), _p(col, C.c_int32), _p(Z, C.c_double),
                             C.c_int(Z.shape[1]), C.c_int(kmin), C.c_int(kmax), C.c_int(grid), C.c_int(T),
-                            C.c_uint64(seed), C.c_int(criterion), C.c_int(cap), _p(labels, C.c_int32), C.byref(kb),
+                            C.c_uint64(seed), C.c_int(criterion), C.c_int(1 if seed_fp32 else 0), C.c_int(cap),
+                            _p(labels, C.c_int32), C.byref(kb),
                             C.byref(nc), _p(ck, C.c_int32), _p(cm, C.c_double), _p(cn, C.c_double),
                             _p(cp, C.c_int32)), "select")
     k = nc.value
@@ -216,3 +217,27 @@ def partition(g, op="ncut", dims=(64, 64, 32), embed_seed=1, kmin=2, kmax=40, gr
     res["Z"] = Z
     res["Y"] = Y
     return res
+
+
+def project_rows(g, op, L, seed, rows):
+    """Rows of Eq. 5's Y for a large graph (Theta rows drawn on demand)."""
+    rp, col = _keep(g)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    Y = np.zeros((rows.shape[0], L), dtype=np.float64)
+    _check(lib().orc_project_rows(C.c_int64(g.n), _p(rp, C.c_int64), _p(col, C.c_int32), C.c_int(OPS.get(op, op)),
+                                  C.c_int(L), C.c_uint64(seed), _p(rows, C.c_int64), C.c_int64(rows.shape[0]),
+                                  _p(Y, C.c_double)), "project_rows")
+    return Y
+
+
+def gcn_rows(g, Zin32, W, rows):
+    """Rows of one Eq. 6 layer (with normalisation) from a single-precision input."""
+    rp, col = _keep(g)
+    Zin32 = np.ascontiguousarray(Zin32, dtype=np.float32)
+    W = _f64(W)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    Z = np.zeros((rows.shape[0], W.shape[1]), dtype=np.float64)
+    _check(lib().orc_gcn_rows(C.c_int64(g.n), _p(rp, C.c_int64), _p(col, C.c_int32), _p(Zin32, C.c_float),
+                              C.c_int(W.shape[0]), _p(W, C.c_double), C.c_int(W.shape[1]), _p(rows, C.c_int64),
+                              C.c_int64(rows.shape[0]), _p(Z, C.c_double)), "gcn_rows")
+    return Z

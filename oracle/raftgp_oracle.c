@@ -235,6 +235,76 @@ int orc_gcn_layer(int64_t n, const int64_t* row_ptr, const int32_t* col, const d
     return ORC_OK;
 }
 
+/* Rows `rows` of Y = X Theta (Eq. 5) for a large graph, drawing the Theta rows of each
+ * listed row's neighbours on demand instead of forming Theta.  For the full modularity matrix
+ * g = d^T Theta is accumulated over every node, one Theta row at a time. */
+int orc_project_rows(int64_t n, const int64_t* row_ptr, const int32_t* col, int op, int L, uint64_t seed,
+                     const int64_t* rows, int64_t n_rows, double* Y) {
+    double two_e = (double)row_ptr[n];
+    double* th = (double*)malloc(sizeof(double) * (size_t)L);
+    double* g = (double*)calloc((size_t)L, sizeof(double));
+    if (!th || !g) { free(th); free(g); return ORC_ENOMEM; }
+    if (op == ORC_OP_MOD_FULL) {
+        for (int64_t j = 0; j < n; ++j) {
+            orc_theta_rows(&j, 1, L, seed, th);
+            for (int r = 0; r < L; ++r) g[r] += (double)degree(row_ptr, j) * th[r];
+        }
+    }
+    for (int64_t t = 0; t < n_rows; ++t) {
+        int64_t i = rows[t];
+        double di = (double)degree(row_ptr, i);
+        double* y = Y + t * L;
+        for (int r = 0; r < L; ++r) y[r] = 0.0;
+        for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+            int64_t j = col[p];
+            double dj = (double)degree(row_ptr, j);
+            double w;
+            if (op == ORC_OP_NCUT) w = (1.0 / sqrt(di)) * (1.0 / sqrt(dj));
+            else if (op == ORC_OP_MOD_FULL) w = 1.0;
+            else w = 1.0 - di * dj / two_e;
+            orc_theta_rows(&j, 1, L, seed, th);
+            for (int r = 0; r < L; ++r) y[r] += w * th[r];
+        }
+        if (op == ORC_OP_MOD_FULL && two_e > 0.0)
+            for (int r = 0; r < L; ++r) y[r] -= di * g[r] / two_e;
+    }
+    free(th);
+    free(g);
+    return (op >= ORC_OP_NCUT && op <= ORC_OP_MOD_REDUCED) ? ORC_OK : ORC_EINVAL;
+}
+
+/* Rows `rows` of one GCN layer (Eq. 6 and the row normalisation) from a given single-precision
+ * input Zin (n x lin), each value widened to FP64. */
+int orc_gcn_rows(int64_t n, const int64_t* row_ptr, const int32_t* col, const float* Zin, int lin, const double* W,
+                 int lout, const int64_t* rows, int64_t n_rows, double* Zout) {
+    (void)n;
+    double* agg = (double*)malloc(sizeof(double) * (size_t)lin);
+    double* h = (double*)malloc(sizeof(double) * (size_t)lout);
+    if (!agg || !h) { free(agg); free(h); return ORC_ENOMEM; }
+    for (int64_t t = 0; t < n_rows; ++t) {
+        int64_t i = rows[t];
+        double rhi = 1.0 / sqrt((double)(degree(row_ptr, i) + 1));
+        for (int a = 0; a < lin; ++a) agg[a] = rhi * rhi * (double)Zin[i * lin + a];
+        for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+            int64_t j = col[p];
+            double rhj = 1.0 / sqrt((double)(degree(row_ptr, j) + 1));
+            for (int a = 0; a < lin; ++a) agg[a] += rhi * rhj * (double)Zin[j * lin + a];
+        }
+        double norm2 = 0.0;
+        for (int b = 0; b < lout; ++b) {
+            double sacc = 0.0;
+            for (int a = 0; a < lin; ++a) sacc += agg[a] * W[(int64_t)a * lout + b];
+            h[b] = tanh(sacc);
+            norm2 += h[b] * h[b];
+        }
+        double inv = norm2 > 0.0 ? 1.0 / sqrt(norm2) : 0.0;
+        for (int b = 0; b < lout; ++b) Zout[t * lout + b] = h[b] * inv;
+    }
+    free(agg);
+    free(h);
+    return ORC_OK;
+}
+
 /* Whole embedding: Y = X Theta, then n_layers GCN layers with widths dims[1..n_layers]
  * (dims[0] = L).  theta_in / W_in may be NULL (then drawn from `seed`); W_in, when given,
  * is the concatenation of the row-major W^(1..n_layers).  Y_out may be NULL. */
@@ -531,20 +601,21 @@ static int eval_candidate(int64_t n, const int64_t* row_ptr, const int32_t* col,
 /* Model selection: candidates K in [kmin, kmax] (flat when grid == 0, else a coarse grid
  * of `grid` values and one refined grid of `grid` values around the best), one k-means++
  * run for K = kmax shared by all candidates (candidate K starts from the first K seeds),
- * Lloyd for each, the best by the criterion (modularity by default).
+ * Lloyd for each, the best by the criterion (modularity by default).  seed_fp32 selects the
+ * single-precision D^2 for the seeding decisions (see orc_kmeanspp).
  * Outputs: labels (n) of the best; cand_k / cand_mod / cand_ncut / cand_passes for every
  * evaluated candidate in evaluation order (arrays of capacity max_cand); returns the
  * number evaluated in *n_cand and the chosen K in *k_best. */
 int orc_select(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* Z, int d, int kmin, int kmax,
-               int grid, int T, uint64_t seed, int criterion, int max_cand, int32_t* labels, int* k_best,
-               int* n_cand, int* cand_k, double* cand_mod, double* cand_ncut, int* cand_passes) {
+               int grid, int T, uint64_t seed, int criterion, int seed_fp32, int max_cand, int32_t* labels,
+               int* k_best, int* n_cand, int* cand_k, double* cand_mod, double* cand_ncut, int* cand_passes) {
     if (kmax > n) kmax = (int)n;
     if (kmin < 1 || kmin > kmax) return ORC_EINVAL;
     int64_t* seeds = (int64_t*)malloc(sizeof(int64_t) * (size_t)kmax);
     int32_t* lab = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
     int* list = (int*)malloc(sizeof(int) * (size_t)(kmax - kmin + 2 + 2 * grid));
     if (!seeds || !lab || !list) { free(seeds); free(lab); free(list); return ORC_ENOMEM; }
-    int rc = orc_kmeanspp(Z, n, d, kmax, seed, 0, seeds);
+    int rc = orc_kmeanspp(Z, n, d, kmax, seed, seed_fp32, seeds);
     int count = 0, best = -1;
     int stages = grid > 0 ? 2 : 1;
     for (int stage = 0; stage < stages && rc == ORC_OK; ++stage) {

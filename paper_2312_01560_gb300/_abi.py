@@ -1,0 +1,93 @@
+"""ctypes mirror of include/raftgp.h and the loader of libraftgp.so.
+
+The library is loaded from this package directory only; if it is missing the import of the
+compute functions raises (there is no CPU fallback)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libraftgp.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
+STATUS_NAMES = {0: "RAFTGP_OK", 1: "RAFTGP_EINVAL", 2: "RAFTGP_ENOMEM", 3: "RAFTGP_ECUDA", 4: "RAFTGP_ETIMEOUT",
+                5: "RAFTGP_EUNSUPPORTED"}
+OP = {"ncut": 0, "mod_full": 1, "mod_reduced": 2}
+DTYPE = {"f32": 0, "bf16": 1}
+CRIT = {"mod": 0, "ncut": 1}
+ASSIGN = {"ffma": 0, "tc": 1}
+MAX_LAYERS = 4
+MAX_BATCH_CAND = 64
+
+# Every entry point declared in include/raftgp.h.
+EXPORTS = ("raftgp_workspace_size", "raftgp_embed", "raftgp_select", "raftgp_partition", "raftgp_score",
+           "raftgp_kmeanspp", "raftgp_lloyd", "raftgp_last_error", "raftgp_version")
+
+
+class Csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p), ("row_ptr_bits", C.c_int32),
+                ("col", C.c_void_p)]
+
+
+class EmbedOpts(C.Structure):
+    _fields_ = [("op", C.c_int32), ("n_layers", C.c_int32), ("dims", C.c_int32 * (MAX_LAYERS + 1)),
+                ("dtype", C.c_int32), ("seed", C.c_uint64), ("theta", C.c_void_p),
+                ("W", C.c_void_p * MAX_LAYERS), ("stage_out", C.c_void_p * (MAX_LAYERS + 1))]
+
+
+class SelectOpts(C.Structure):
+    _fields_ = [("kmin", C.c_int32), ("kmax", C.c_int32), ("grid", C.c_int32), ("iters", C.c_int32),
+                ("criterion", C.c_int32), ("assign", C.c_int32), ("batch", C.c_int32), ("seed", C.c_uint64)]
+
+
+class SelectResult(C.Structure):
+    _fields_ = [("k_best", C.c_int32), ("n_cand", C.c_int32), ("cand_cap", C.c_int32),
+                ("cand_k", C.POINTER(C.c_int32)), ("cand_mod", C.POINTER(C.c_double)),
+                ("cand_ncut", C.POINTER(C.c_double)), ("cand_passes", C.POINTER(C.c_int32))]
+
+
+class RaftgpError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libraftgp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libraftgp.so is not built ({LIB_PATH} missing): run "
+                               "`python -c 'import __graft_entry__ as g; g.build()'` first")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        L.raftgp_workspace_size.restype = C.c_size_t
+        L.raftgp_workspace_size.argtypes = [C.POINTER(Csr), C.POINTER(EmbedOpts), C.POINTER(SelectOpts), C.c_int32]
+        L.raftgp_embed.argtypes = [C.POINTER(Csr), C.POINTER(EmbedOpts), P, P, C.c_size_t, P]
+        L.raftgp_select.argtypes = [C.POINTER(Csr), P, C.c_int32, C.c_int32, C.POINTER(SelectOpts), P,
+                                    C.POINTER(SelectResult), P, C.c_size_t, P]
+        L.raftgp_partition.argtypes = [C.POINTER(Csr), C.POINTER(EmbedOpts), C.POINTER(SelectOpts), P,
+                                       C.POINTER(SelectResult), P, C.c_size_t, P]
+        L.raftgp_score.argtypes = [C.POINTER(Csr), P, C.c_int32, P, P, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                   P, C.c_size_t, P]
+        L.raftgp_kmeanspp.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P, P, C.c_size_t, P]
+        L.raftgp_lloyd.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, P, C.c_int32, C.c_int32, C.c_int32, P, P,
+                                   C.POINTER(C.c_int32), P, C.c_size_t, P]
+        for name in ("raftgp_embed", "raftgp_select", "raftgp_partition", "raftgp_score", "raftgp_kmeanspp",
+                     "raftgp_lloyd"):
+            getattr(L, name).restype = C.c_int
+        L.raftgp_last_error.restype = C.c_char_p
+        L.raftgp_last_error.argtypes = []
+        L.raftgp_version.restype = C.c_char_p
+        L.raftgp_version.argtypes = []
+        _lib = L
+    return _lib
+
+
+def check(status):
+    if status != OK:
+        raise RaftgpError(status, lib().raftgp_last_error().decode())

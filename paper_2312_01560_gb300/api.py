@@ -1,0 +1,224 @@
+"""Python binding of the RaftGP CUDA library: torch tensors in, torch tensors out.
+
+Argument marshalling only -- every step runs in libraftgp.so's kernels.  PyTorch provides
+device memory and the stream; the workspace is a cached device byte tensor.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _abi
+from ._abi import check, lib
+
+
+@dataclass
+class DeviceGraph:
+    """A symmetric CSR graph resident on the GPU."""
+    n: int
+    row_ptr: torch.Tensor   # int32 or int64, n+1
+    col: torch.Tensor       # int32, nnz
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.numel())
+
+    @property
+    def n_edges(self) -> int:
+        return self.nnz // 2
+
+    @classmethod
+    def from_host(cls, g, device="cuda", row_ptr_bits=None):
+        """From any object with n, row_ptr and col numpy arrays (e.g. inputs.dcsbm.Graph)."""
+        import numpy as np
+        rp = np.asarray(g.row_ptr)
+        bits = row_ptr_bits or (32 if rp[-1] < 2 ** 31 - 1 else 64)
+        rp_t = torch.from_numpy(rp.astype(np.int32 if bits == 32 else np.int64)).to(device)
+        col_t = torch.from_numpy(np.asarray(g.col, dtype=np.int32)).to(device)
+        return cls(int(g.n), rp_t, col_t)
+
+    def csr(self) -> _abi.Csr:
+        bits = 32 if self.row_ptr.dtype == torch.int32 else 64
+        return _abi.Csr(self.n, self.nnz, self.row_ptr.data_ptr(), bits, self.col.data_ptr() if self.nnz else None)
+
+
+_ws = {}
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    key = str(device)
+    t = _ws.get(key)
+    if t is None or t.numel() < nbytes:
+        t = torch.empty(max(nbytes, 1 << 20), dtype=torch.uint8, device=device)
+        _ws[key] = t
+    return t
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dtype_code(dtype) -> int:
+    return _abi.DTYPE[dtype] if isinstance(dtype, str) else int(dtype)
+
+
+def _torch_dtype(code: int):
+    return torch.bfloat16 if code == 1 else torch.float32
+
+
+def embed_opts(op="ncut", dims=(64, 64, 32), dtype="f32", seed=1, theta=None, W=None, stages=None):
+    o = _abi.EmbedOpts()
+    o.op = _abi.OP[op] if isinstance(op, str) else int(op)
+    o.n_layers = len(dims) - 1
+    for k, v in enumerate(dims):
+        o.dims[k] = int(v)
+    o.dtype = _dtype_code(dtype)
+    o.seed = int(seed)
+    o.theta = theta.data_ptr() if theta is not None else None
+    if W is not None:
+        for k, w in enumerate(W):
+            o.W[k] = w.data_ptr()
+    if stages is not None:
+        for k, t in enumerate(stages):
+            o.stage_out[k] = t.data_ptr() if t is not None else None
+    return o
+
+
+def select_opts(kmin=2, kmax=40, grid=0, iters=50, criterion="mod", assign="ffma", batch=0, seed=2):
+    o = _abi.SelectOpts()
+    o.kmin, o.kmax, o.grid, o.iters = int(kmin), int(kmax), int(grid), int(iters)
+    o.criterion = _abi.CRIT[criterion] if isinstance(criterion, str) else int(criterion)
+    o.assign = _abi.ASSIGN[assign] if isinstance(assign, str) else int(assign)
+    o.batch = int(batch)
+    o.seed = int(seed)
+    return o
+
+
+def workspace_size(g: DeviceGraph, eopts=None, sopts=None, d=0) -> int:
+    csr = g.csr()
+    return lib().raftgp_workspace_size(C.byref(csr), C.byref(eopts) if eopts is not None else None,
+                                       C.byref(sopts) if sopts is not None else None, int(d))
+
+
+def embed(g: DeviceGraph, op="ncut", dims=(64, 64, 32), dtype="f32", seed=1, theta=None, W=None,
+          return_stages=False, stream=None):
+    """Stages 1-2 (Eq. 5 projection and the Eq. 6 GCN): returns Z (N x dims[-1])."""
+    code = _dtype_code(dtype)
+    dev = g.col.device
+    Z = torch.empty((g.n, dims[-1]), dtype=_torch_dtype(code), device=dev)
+    stages = [torch.empty((g.n, w), dtype=_torch_dtype(code), device=dev) for w in dims] if return_stages else None
+    if theta is not None:
+        theta = theta.to(dev, torch.float32).contiguous()
+    if W is not None:
+        W = [w.to(dev, torch.float32).contiguous() for w in W]
+    o = embed_opts(op, dims, code, seed, theta, W, stages)
+    csr = g.csr()
+    nbytes = lib().raftgp_workspace_size(C.byref(csr), C.byref(o), None, 0)
+    ws = _workspace(nbytes, dev)
+    check(lib().raftgp_embed(C.byref(csr), C.byref(o), C.c_void_p(Z.data_ptr()), C.c_void_p(ws.data_ptr()),
+                             ws.numel(), _stream(stream)))
+    return (Z, stages) if return_stages else Z
+
+
+def _result(cap):
+    r = _abi.SelectResult()
+    keep = ((C.c_int32 * cap)(), (C.c_double * cap)(), (C.c_double * cap)(), (C.c_int32 * cap)())
+    r.cand_cap = cap
+    r.cand_k, r.cand_mod, r.cand_ncut, r.cand_passes = (C.cast(keep[0], C.POINTER(C.c_int32)),
+                                                        C.cast(keep[1], C.POINTER(C.c_double)),
+                                                        C.cast(keep[2], C.POINTER(C.c_double)),
+                                                        C.cast(keep[3], C.POINTER(C.c_int32)))
+    return r, keep
+
+
+def _unpack(r, keep):
+    n = r.n_cand
+    return {"k": r.k_best,
+            "cands": [(keep[0][i], keep[1][i], keep[2][i], keep[3][i]) for i in range(min(n, r.cand_cap))]}
+
+
+def select(g: DeviceGraph, Z: torch.Tensor, kmin=2, kmax=40, grid=0, iters=50, criterion="mod", assign="ffma",
+           batch=0, seed=2, stream=None, labels=None):
+    """Stage 3: returns (labels int32[N] on the device, report dict)."""
+    code = 1 if Z.dtype == torch.bfloat16 else 0
+    o = select_opts(kmin, kmax, grid, iters, criterion, assign, batch, seed)
+    csr = g.csr()
+    d = Z.shape[1]
+    nbytes = lib().raftgp_workspace_size(C.byref(csr), None, C.byref(o), d)
+    ws = _workspace(nbytes, Z.device)
+    if labels is None:
+        labels = torch.empty(g.n, dtype=torch.int32, device=Z.device)
+    r, keep = _result((kmax - kmin + 1) + 2 * grid + 2)
+    Zc = Z.contiguous()
+    check(lib().raftgp_select(C.byref(csr), C.c_void_p(Zc.data_ptr()), d, code, C.byref(o),
+                              C.c_void_p(labels.data_ptr()), C.byref(r), C.c_void_p(ws.data_ptr()), ws.numel(),
+                              _stream(stream)))
+    return labels, _unpack(r, keep)
+
+
+def partition(g: DeviceGraph, op="ncut", dims=(64, 64, 32), dtype="f32", embed_seed=1, kmin=2, kmax=40, grid=0,
+              iters=50, criterion="mod", assign="ffma", batch=0, select_seed=2, stream=None, labels=None):
+    """Stages 1-3 end to end: returns (labels, report)."""
+    eo = embed_opts(op, dims, dtype, embed_seed)
+    so = select_opts(kmin, kmax, grid, iters, criterion, assign, batch, select_seed)
+    csr = g.csr()
+    nbytes = lib().raftgp_workspace_size(C.byref(csr), C.byref(eo), C.byref(so), 0)
+    ws = _workspace(nbytes, g.col.device)
+    if labels is None:
+        labels = torch.empty(g.n, dtype=torch.int32, device=g.col.device)
+    r, keep = _result((kmax - kmin + 1) + 2 * grid + 2)
+    check(lib().raftgp_partition(C.byref(csr), C.byref(eo), C.byref(so), C.c_void_p(labels.data_ptr()), C.byref(r),
+                                 C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return labels, _unpack(r, keep)
+
+
+def score(g: DeviceGraph, labels: torch.Tensor, K: int, stream=None):
+    """Eq. 3 / Eq. 1 of a given partition: returns (m, vol, mod, ncut)."""
+    dev = g.col.device
+    m = torch.empty(K, dtype=torch.int64, device=dev)
+    vol = torch.empty(K, dtype=torch.int64, device=dev)
+    mod = C.c_double(0)
+    ncut = C.c_double(0)
+    ws = _workspace(4096 + 16 * g.n + 4096, dev)
+    csr = g.csr()
+    lab = labels.to(dev, torch.int32).contiguous()
+    check(lib().raftgp_score(C.byref(csr), C.c_void_p(lab.data_ptr()), int(K), C.c_void_p(m.data_ptr()),
+                             C.c_void_p(vol.data_ptr()), C.byref(mod), C.byref(ncut), C.c_void_p(ws.data_ptr()),
+                             ws.numel(), _stream(stream)))
+    return m, vol, mod.value, ncut.value
+
+
+def kmeanspp(Z: torch.Tensor, K: int, seed: int, stream=None):
+    n, d = Z.shape
+    code = 1 if Z.dtype == torch.bfloat16 else 0
+    seeds = torch.empty(K, dtype=torch.int32, device=Z.device)
+    ws = _workspace(8 * n + 16 * n + 8 * (n // 256 + 2) + 4096, Z.device)
+    Zc = Z.contiguous()
+    check(lib().raftgp_kmeanspp(C.c_void_p(Zc.data_ptr()), n, d, code, int(K), int(seed),
+                                C.c_void_p(seeds.data_ptr()), C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return seeds
+
+
+def lloyd(Z: torch.Tensor, mu0: torch.Tensor, iters=50, assign="ffma", stream=None):
+    """Lloyd's iterations from mu0: returns (labels int32[N], mu float32[K, d], passes)."""
+    n, d = Z.shape
+    K = mu0.shape[0]
+    code = 1 if Z.dtype == torch.bfloat16 else 0
+    labels = torch.empty(n, dtype=torch.int32, device=Z.device)
+    mu = torch.empty((K, d), dtype=torch.float32, device=Z.device)
+    m0 = mu0.to(Z.device, torch.float32).contiguous()
+    ws = _workspace(K * d * 16 + 16 * n + 64 * 1024 + K * 16, Z.device)
+    passes = C.c_int32(0)
+    Zc = Z.contiguous()
+    check(lib().raftgp_lloyd(C.c_void_p(Zc.data_ptr()), n, d, code, C.c_void_p(m0.data_ptr()), int(K),
+                             int(iters), _abi.ASSIGN[assign] if isinstance(assign, str) else int(assign),
+                             C.c_void_p(labels.data_ptr()), C.c_void_p(mu.data_ptr()), C.byref(passes),
+                             C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return labels, mu, passes.value
+
+
+def version() -> str:
+    return lib().raftgp_version().decode()

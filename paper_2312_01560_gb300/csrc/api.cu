@@ -1,0 +1,587 @@
+// api.cu -- the C ABI (include/raftgp.h): argument checks, workspace layout and the order of
+// kernel launches for each entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace raftgp {
+
+static thread_local std::string g_last_error;
+
+static raftgp_status fail(raftgp_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+static raftgp_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(RAFTGP_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// Bump allocator over the caller's workspace (base == nullptr measures only).
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base((char*)b) {}
+    template <typename T>
+    T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+static size_t elem_size(int dtype) { return dtype == RAFTGP_BF16 ? 2 : 4; }
+static bool width_ok(int w) { return w == 32 || w == 64 || w == 128; }
+
+static raftgp_status check_csr(const raftgp_csr* g) {
+    if (!g) return fail(RAFTGP_EINVAL, "graph is NULL");
+    if (g->n < 1) return fail(RAFTGP_EINVAL, "graph has n = %lld < 1", (long long)g->n);
+    if (g->n > (int64_t)INT32_MAX - 1) return fail(RAFTGP_EUNSUPPORTED, "n above 2^31-2 is not supported");
+    if (g->nnz < 0) return fail(RAFTGP_EINVAL, "nnz < 0");
+    if (g->row_ptr_bits != 32 && g->row_ptr_bits != 64) return fail(RAFTGP_EINVAL, "row_ptr_bits must be 32 or 64");
+    if (g->row_ptr_bits == 32 && g->nnz > (int64_t)INT32_MAX) return fail(RAFTGP_EINVAL, "nnz exceeds int32 row_ptr");
+    if (!g->row_ptr || (g->nnz > 0 && !g->col)) return fail(RAFTGP_EINVAL, "graph arrays are NULL");
+    if (g->nnz >= ((int64_t)1 << 31)) return fail(RAFTGP_EUNSUPPORTED, "nnz of 2^31 or more is not supported");
+    return RAFTGP_OK;
+}
+
+static raftgp_status check_embed(const raftgp_embed_opts* o) {
+    if (!o) return fail(RAFTGP_EINVAL, "embed options are NULL");
+    if (o->op < RAFTGP_OP_NCUT || o->op > RAFTGP_OP_MOD_REDUCED) return fail(RAFTGP_EINVAL, "unknown operator %d", o->op);
+    if (o->n_layers < 0 || o->n_layers > RAFTGP_MAX_LAYERS) return fail(RAFTGP_EINVAL, "n_layers out of range");
+    for (int k = 0; k <= o->n_layers; ++k)
+        if (!width_ok(o->dims[k])) return fail(RAFTGP_EUNSUPPORTED, "dims[%d] = %d: widths must be 32, 64 or 128", k, o->dims[k]);
+    if (o->dtype != RAFTGP_F32 && o->dtype != RAFTGP_BF16) return fail(RAFTGP_EINVAL, "unknown dtype");
+    return RAFTGP_OK;
+}
+
+static raftgp_status check_select(const raftgp_select_opts* o, int64_t n) {
+    if (!o) return fail(RAFTGP_EINVAL, "select options are NULL");
+    if (o->kmin < 1 || o->kmax < o->kmin) return fail(RAFTGP_EINVAL, "need 1 <= kmin <= kmax");
+    if (std::min<int64_t>(o->kmax, n) < o->kmin) return fail(RAFTGP_EINVAL, "kmin exceeds the number of nodes");
+    if (std::min<int64_t>(o->kmax, n) > 32767) return fail(RAFTGP_EUNSUPPORTED, "K above 32767 is not supported");
+    if (o->grid < 0 || o->grid > RAFTGP_MAX_BATCH_CAND) return fail(RAFTGP_EINVAL, "grid out of range");
+    if (o->iters < 1) return fail(RAFTGP_EINVAL, "iters must be >= 1");
+    if (o->criterion != RAFTGP_CRIT_MOD && o->criterion != RAFTGP_CRIT_NCUT) return fail(RAFTGP_EINVAL, "unknown criterion");
+    if (o->assign != RAFTGP_ASSIGN_FFMA && o->assign != RAFTGP_ASSIGN_TC) return fail(RAFTGP_EINVAL, "unknown assign engine");
+    if (o->batch < 0) return fail(RAFTGP_EINVAL, "batch < 0");
+    if (o->assign == RAFTGP_ASSIGN_TC) return fail(RAFTGP_EUNSUPPORTED, "tensor-core assignment is not built yet");
+    return RAFTGP_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// Workspace layouts
+// ------------------------------------------------------------------------------------
+struct EmbedWs {
+    uint32_t* err;
+    int32_t* deg;
+    float* rs;
+    float* rsh;
+    float* W[RAFTGP_MAX_LAYERS];
+    double* partial;
+    float* gvec;
+    void* bufA;
+    void* bufB;
+};
+
+static int embed_maxw(const raftgp_embed_opts* o) {
+    int w = o->dims[0];
+    for (int k = 1; k <= o->n_layers; ++k) w = std::max(w, o->dims[k]);
+    return w;
+}
+
+static EmbedWs carve_embed(Carver& c, int64_t n, const raftgp_embed_opts* o) {
+    EmbedWs w{};
+    w.err = c.take<uint32_t>(64);
+    w.deg = c.take<int32_t>(n);
+    w.rs = c.take<float>(n);
+    w.rsh = c.take<float>(n);
+    for (int k = 1; k <= o->n_layers; ++k) w.W[k - 1] = c.take<float>((size_t)o->dims[k - 1] * o->dims[k]);
+    const int L = o->dims[0];
+    w.partial = c.take<double>((size_t)theta_blocks(n) * L);
+    w.gvec = c.take<float>(L);
+    const size_t row = (size_t)embed_maxw(o) * elem_size(o->dtype);
+    w.bufA = c.take<char>(row * (size_t)n);
+    w.bufB = c.take<char>(row * (size_t)n);
+    return w;
+}
+
+struct SelectWs {
+    uint32_t* err;
+    int32_t* deg;
+    float* rs;
+    float* rsh;
+    float* D2;
+    uint8_t* chosen;
+    unsigned long long* blocksum;
+    int32_t* seeds;
+    KmState km;
+    ScoreOut so;
+    BestState* best;
+    int cmax;   // candidates per batch
+    int kcap;   // centroids per batch
+};
+
+static int batch_cap(const raftgp_select_opts* o, int kmax) {
+    int span = o->grid > 0 ? o->grid : (kmax - o->kmin + 1);
+    int c = o->batch == 0 ? RAFTGP_MAX_BATCH_CAND : std::min(o->batch, RAFTGP_MAX_BATCH_CAND);
+    return std::max(1, std::min(c, span));
+}
+
+static SelectWs carve_select(Carver& c, int64_t n, int d, const raftgp_select_opts* o, uint32_t* err, int32_t* deg) {
+    SelectWs w{};
+    const int kmax = (int)std::min<int64_t>(o->kmax, n);
+    w.err = err ? err : c.take<uint32_t>(64);
+    if (deg) {
+        w.deg = deg;
+    } else {
+        w.deg = c.take<int32_t>(n);
+        w.rs = c.take<float>(n);
+        w.rsh = c.take<float>(n);
+    }
+    w.D2 = c.take<float>(n);
+    w.chosen = c.take<uint8_t>(n);
+    w.blocksum = c.take<unsigned long long>(seed_nblocks(n));
+    w.seeds = c.take<int32_t>(kmax);
+    w.cmax = batch_cap(o, kmax);
+    w.kcap = w.cmax * kmax;
+    const int cs = (w.cmax + 7) / 8 * 8;
+    w.km.mu = c.take<float>((size_t)w.kcap * d);
+    w.km.norm2 = c.take<float>(w.kcap);
+    w.km.sums = c.take<long long>((size_t)w.kcap * d);
+    w.km.counts = c.take<int32_t>(w.kcap);
+    w.km.labels = c.take<int16_t>((size_t)n * cs);
+    w.km.active = c.take<int32_t>(MAXC);
+    w.km.changed = c.take<int32_t>(2 * MAXC);
+    w.km.passes = c.take<int32_t>(MAXC);
+    w.so.m = c.take<long long>(w.kcap);
+    w.so.vol = c.take<long long>(w.kcap);
+    w.so.mod = c.take<double>(MAXC);
+    w.so.ncut = c.take<double>(MAXC);
+    w.best = c.take<BestState>(1);
+    return w;
+}
+
+static raftgp_status read_error_word(const uint32_t* err, cudaStream_t s);
+
+// ------------------------------------------------------------------------------------
+// Embedding
+// ------------------------------------------------------------------------------------
+static raftgp_status run_embed(const raftgp_csr* g, const raftgp_embed_opts* o, void* Z, const EmbedWs& w,
+                               bool degrees_done, cudaStream_t s) {
+    const int64_t n = g->n;
+    const int L = o->dims[0];
+    if (!degrees_done) {
+        launch_degrees(g, w.deg, w.rs, w.rsh, w.err, s);
+        // no gather runs on a graph that failed the device checks
+        raftgp_status st = read_error_word(w.err, s);
+        if (st != RAFTGP_OK) return st;
+    }
+    for (int k = 1; k <= o->n_layers; ++k) {
+        if (o->W[k - 1]) {
+            cudaMemcpyAsync(w.W[k - 1], o->W[k - 1], sizeof(float) * (size_t)o->dims[k - 1] * o->dims[k],
+                            cudaMemcpyDeviceToDevice, s);
+        } else {
+            launch_weights(k, o->dims[k - 1], o->dims[k], o->seed, w.W[k - 1], s);
+        }
+    }
+    const bool rank1 = o->op == RAFTGP_OP_MOD_FULL;
+    // Theta (prescaled by rs_j for the NCut operator) into bufB
+    launch_theta(n, L, o->dtype, o->seed, o->theta, o->op == RAFTGP_OP_NCUT ? w.rs : nullptr, w.deg, w.bufB,
+                 rank1 ? w.partial : nullptr, w.gvec, s);
+    const int agg0 = o->op == RAFTGP_OP_NCUT ? AGG_NCUT_ : (rank1 ? AGG_MOD_FULL_ : AGG_MOD_REDUCED_);
+    cudaError_t e;
+    if (o->n_layers == 0) {
+        e = launch_layer(agg0, o->dtype, g, w.deg, w.rs, w.gvec, 2, nullptr, L, L, nullptr, w.bufB, Z,
+                         o->stage_out[0], s);
+        if (e != cudaSuccess) return cuda_fail(e, "projection");
+        return RAFTGP_OK;
+    }
+    // layer 0: projection, then x W1, prescaled by rsh for the first GCN gather
+    e = launch_layer(agg0, o->dtype, g, w.deg, w.rs, w.gvec, 0, w.W[0], L, o->dims[1], w.rsh, w.bufB, w.bufA,
+                     o->stage_out[0], s);
+    if (e != cudaSuccess) return cuda_fail(e, "projection");
+    void* cur = w.bufA;
+    void* nxt = w.bufB;
+    for (int k = 1; k <= o->n_layers; ++k) {
+        const bool last = k == o->n_layers;
+        e = launch_layer(AGG_GCN_, o->dtype, g, w.deg, w.rsh, nullptr, 1, last ? nullptr : w.W[k], o->dims[k],
+                         last ? o->dims[k] : o->dims[k + 1], last ? nullptr : w.rsh, cur, last ? Z : nxt,
+                         o->stage_out[k], s);
+        if (e != cudaSuccess) return cuda_fail(e, "gcn layer");
+        std::swap(cur, nxt);
+    }
+    return RAFTGP_OK;
+}
+
+static raftgp_status read_error_word(const uint32_t* err, cudaStream_t s) {
+    uint32_t h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, err, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
+    if (h & (DERR_COL_RANGE | DERR_ROW_PTR | DERR_SELF_LOOP))
+        return fail(RAFTGP_EINVAL, "malformed graph (device check flags 0x%x)", h);
+    if (h & DERR_LABEL_RANGE) return fail(RAFTGP_EINVAL, "a label is outside [0, K)");
+    if (h & DERR_NORM) return fail(RAFTGP_EINVAL, "an embedding row has norm above 1");
+    if (h & DERR_TIMEOUT) return fail(RAFTGP_ETIMEOUT, "a bounded device wait timed out");
+    return RAFTGP_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// Candidate grids (Section III-C model selection over K)
+// ------------------------------------------------------------------------------------
+static std::vector<int> coarse_grid(int kmin, int kmax, int G) {
+    std::vector<int> out;
+    if (G == 1) { out.push_back(kmin); return out; }
+    for (int t = 0; t < G; ++t) {
+        const int64_t num = 2 * (int64_t)(kmax - kmin) * t + (G - 1);
+        const int k = kmin + (int)(num / (2 * (int64_t)(G - 1)));
+        if (out.empty() || out.back() != k) out.push_back(k);
+    }
+    return out;
+}
+
+static std::vector<int> refine_grid(int lo, int hi, int G, const std::vector<int>& done) {
+    std::vector<int> out;
+    for (int t = 1; t <= G; ++t) {
+        const int64_t num = 2 * (int64_t)(hi - lo) * t + (G + 1);
+        const int k = lo + (int)(num / (2 * (int64_t)(G + 1)));
+        if (std::find(done.begin(), done.end(), k) == done.end() && std::find(out.begin(), out.end(), k) == out.end())
+            out.push_back(k);
+    }
+    return out;
+}
+
+struct CandRecord {
+    int k;
+    double mod, ncut;
+    int passes;
+};
+
+static bool host_better(int criterion, const CandRecord& a, const CandRecord& b) {
+    if (criterion == RAFTGP_CRIT_NCUT) {
+        if (a.ncut != b.ncut) return a.ncut < b.ncut;
+    } else {
+        if (a.mod != b.mod) return a.mod > b.mod;
+    }
+    return a.k < b.k;
+}
+
+// Evaluate a list of candidates in batches; appends their records.
+static raftgp_status run_candidates(const raftgp_csr* g, const void* Z, int d, int zdtype,
+                                    const raftgp_select_opts* o, const std::vector<int>& ks, const SelectWs& w,
+                                    int32_t* labels, std::vector<CandRecord>& rec, cudaStream_t s) {
+    const int64_t n = g->n;
+    for (size_t b0 = 0; b0 < ks.size(); b0 += (size_t)w.cmax) {
+        CandBatch b{};
+        b.n = (int)std::min<size_t>((size_t)w.cmax, ks.size() - b0);
+        b.cs = (b.n + 7) / 8 * 8;
+        int off = 0;
+        for (int c = 0; c < b.n; ++c) {
+            b.k[c] = ks[b0 + c];
+            b.off[c] = off;
+            off += b.k[c];
+        }
+        b.total_k = off;
+        launch_batch_init(b, Z, zdtype, n, d, w.seeds, nullptr, w.km, s);
+        for (int pass = 1; pass <= o->iters; ++pass) {
+            cudaError_t e = launch_assign_ffma(b, Z, zdtype, n, d, w.km, pass, s);
+            if (e != cudaSuccess) return cuda_fail(e, "assign");
+            launch_lloyd_update(b, d, w.km, pass, s);
+        }
+        launch_score_batch(b, g, w.deg, w.km.labels, w.so, w.err, s);
+        launch_select_best(b, w.so, o->criterion, w.best, w.km.labels, n, labels, s);
+        double hm[MAXC], hn[MAXC];
+        int32_t hp[MAXC];
+        cudaMemcpyAsync(hm, w.so.mod, sizeof(double) * b.n, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(hn, w.so.ncut, sizeof(double) * b.n, cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(hp, w.km.passes, sizeof(int32_t) * b.n, cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "candidate batch");
+        for (int c = 0; c < b.n; ++c) rec.push_back(CandRecord{b.k[c], hm[c], hn[c], hp[c]});
+    }
+    return RAFTGP_OK;
+}
+
+__global__ void k_check_norms(const void* Z, int zdtype, int64_t n, int d, uint32_t* err) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int k = 0; k < d; ++k) {
+            const float v = zdtype == RAFTGP_BF16 ? __bfloat162float(((const __nv_bfloat16*)Z)[i * d + k])
+                                                  : ((const float*)Z)[i * d + k];
+            s = fmaf(v, v, s);
+        }
+        if (!(s <= 1.0001f)) flag_error(err, DERR_NORM);
+    }
+}
+
+static raftgp_status run_select(const raftgp_csr* g, const void* Z, int d, int zdtype, const raftgp_select_opts* o,
+                                int32_t* labels, raftgp_select_result* res, const SelectWs& w, bool degrees_done,
+                                cudaStream_t s) {
+    const int64_t n = g->n;
+    const int kmax = (int)std::min<int64_t>(o->kmax, n);
+    if (!degrees_done) {
+        cudaMemsetAsync(w.err, 0, sizeof(uint32_t), s);
+        launch_degrees(g, w.deg, w.rs, w.rsh, w.err, s);
+    }
+    {
+        int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8);
+        k_check_norms<<<std::max(blocks, 1), 256, 0, s>>>(Z, zdtype, n, d, w.err);
+    }
+    raftgp_status st = read_error_word(w.err, s);
+    if (st != RAFTGP_OK) return st;
+    // seeding for K_max, shared by every candidate
+    cudaMemsetAsync(w.chosen, 0, (size_t)n, s);
+    launch_seed_first(n, o->seed, w.seeds, w.chosen, s);
+    for (int t = 1; t < kmax; ++t) launch_seed_round(Z, zdtype, n, d, t, o->seed, w.seeds, w.chosen, w.D2, w.blocksum, s);
+    cudaMemsetAsync(w.best, 0, sizeof(BestState), s);
+    std::vector<CandRecord> rec;
+    std::vector<int> ks;
+    if (o->grid == 0) {
+        for (int k = o->kmin; k <= kmax; ++k) ks.push_back(k);
+        st = run_candidates(g, Z, d, zdtype, o, ks, w, labels, rec, s);
+    } else {
+        ks = coarse_grid(o->kmin, kmax, o->grid);
+        st = run_candidates(g, Z, d, zdtype, o, ks, w, labels, rec, s);
+        if (st == RAFTGP_OK) {
+            int jb = 0;
+            for (int j = 1; j < (int)rec.size(); ++j)
+                if (host_better(o->criterion, rec[j], rec[jb])) jb = j;
+            const int nc = (int)rec.size();
+            const int lo = rec[jb > 0 ? jb - 1 : 0].k;
+            const int hi = rec[jb < nc - 1 ? jb + 1 : nc - 1].k;
+            std::vector<int> done;
+            for (auto& r : rec) done.push_back(r.k);
+            std::vector<int> ref = refine_grid(lo, hi, o->grid, done);
+            if (!ref.empty()) st = run_candidates(g, Z, d, zdtype, o, ref, w, labels, rec, s);
+        }
+    }
+    if (st != RAFTGP_OK) return st;
+    st = read_error_word(w.err, s);
+    if (st != RAFTGP_OK) return st;
+    if (res) {
+        int jb = 0;
+        for (int j = 1; j < (int)rec.size(); ++j)
+            if (host_better(o->criterion, rec[j], rec[jb])) jb = j;
+        res->k_best = rec.empty() ? 0 : rec[jb].k;
+        res->n_cand = (int)rec.size();
+        for (int j = 0; j < (int)rec.size() && j < res->cand_cap; ++j) {
+            if (res->cand_k) res->cand_k[j] = rec[j].k;
+            if (res->cand_mod) res->cand_mod[j] = rec[j].mod;
+            if (res->cand_ncut) res->cand_ncut[j] = rec[j].ncut;
+            if (res->cand_passes) res->cand_passes[j] = rec[j].passes;
+        }
+    }
+    return RAFTGP_OK;
+}
+
+}  // namespace raftgp
+
+using namespace raftgp;
+
+extern "C" {
+
+size_t raftgp_workspace_size(const raftgp_csr* g, const raftgp_embed_opts* eopts, const raftgp_select_opts* sopts,
+                             int32_t d) {
+    if (!g || g->n < 1) return 0;
+    Carver c(nullptr);
+    uint32_t* err = nullptr;
+    int32_t* deg = nullptr;
+    if (eopts) {
+        if (check_embed(eopts) != RAFTGP_OK) return 0;
+        EmbedWs w = carve_embed(c, g->n, eopts);
+        (void)w;
+        err = reinterpret_cast<uint32_t*>(1);  // marks "shared with the embedding part"
+        deg = reinterpret_cast<int32_t*>(1);
+        d = eopts->dims[eopts->n_layers];
+        if (sopts) c.take<char>((size_t)g->n * d * elem_size(eopts->dtype));  // Z of raftgp_partition
+    }
+    if (sopts) {
+        if (check_select(sopts, g->n) != RAFTGP_OK || !width_ok(d)) return 0;
+        carve_select(c, g->n, d, sopts, err, deg);
+    }
+    return c.off + 256;
+}
+
+raftgp_status raftgp_embed(const raftgp_csr* g, const raftgp_embed_opts* eopts, void* Z, void* ws, size_t ws_bytes,
+                           raftgp_stream_t stream) {
+    raftgp_status st = check_csr(g);
+    if (st) return st;
+    if ((st = check_embed(eopts))) return st;
+    if (!Z || !ws) return fail(RAFTGP_EINVAL, "Z or workspace is NULL");
+    if (ws_bytes < raftgp_workspace_size(g, eopts, nullptr, 0)) return fail(RAFTGP_ENOMEM, "workspace too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    Carver c(ws);
+    EmbedWs w = carve_embed(c, g->n, eopts);
+    cudaMemsetAsync(w.err, 0, sizeof(uint32_t), s);
+    st = run_embed(g, eopts, Z, w, false, s);
+    if (st) return st;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "raftgp_embed");
+    return RAFTGP_OK;
+}
+
+raftgp_status raftgp_select(const raftgp_csr* g, const void* Z, int32_t d, int32_t z_dtype,
+                            const raftgp_select_opts* sopts, int32_t* labels, raftgp_select_result* res, void* ws,
+                            size_t ws_bytes, raftgp_stream_t stream) {
+    raftgp_status st = check_csr(g);
+    if (st) return st;
+    if ((st = check_select(sopts, g->n))) return st;
+    if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d = %d: must be 32, 64 or 128", d);
+    if (z_dtype != RAFTGP_F32 && z_dtype != RAFTGP_BF16) return fail(RAFTGP_EINVAL, "unknown z_dtype");
+    if (!Z || !labels || !ws) return fail(RAFTGP_EINVAL, "Z, labels or workspace is NULL");
+    if (ws_bytes < raftgp_workspace_size(g, nullptr, sopts, d)) return fail(RAFTGP_ENOMEM, "workspace too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    Carver c(ws);
+    SelectWs w = carve_select(c, g->n, d, sopts, nullptr, nullptr);
+    st = run_select(g, Z, d, z_dtype, sopts, labels, res, w, false, s);
+    if (st) return st;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "raftgp_select");
+    return RAFTGP_OK;
+}
+
+raftgp_status raftgp_partition(const raftgp_csr* g, const raftgp_embed_opts* eopts, const raftgp_select_opts* sopts,
+                               int32_t* labels, raftgp_select_result* res, void* ws, size_t ws_bytes,
+                               raftgp_stream_t stream) {
+    raftgp_status st = check_csr(g);
+    if (st) return st;
+    if ((st = check_embed(eopts))) return st;
+    if ((st = check_select(sopts, g->n))) return st;
+    if (!labels || !ws) return fail(RAFTGP_EINVAL, "labels or workspace is NULL");
+    if (ws_bytes < raftgp_workspace_size(g, eopts, sopts, 0)) return fail(RAFTGP_ENOMEM, "workspace too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int d = eopts->dims[eopts->n_layers];
+    Carver c(ws);
+    EmbedWs ew = carve_embed(c, g->n, eopts);
+    void* Z = c.take<char>((size_t)g->n * d * elem_size(eopts->dtype));
+    SelectWs sw = carve_select(c, g->n, d, sopts, ew.err, ew.deg);
+    cudaMemsetAsync(ew.err, 0, sizeof(uint32_t), s);
+    st = run_embed(g, eopts, Z, ew, false, s);
+    if (st) return st;
+    st = run_select(g, Z, d, eopts->dtype, sopts, labels, res, sw, true, s);
+    if (st) return st;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "raftgp_partition");
+    return RAFTGP_OK;
+}
+
+raftgp_status raftgp_score(const raftgp_csr* g, const int32_t* labels, int32_t K, int64_t* m, int64_t* vol,
+                           double* mod, double* ncut, void* ws, size_t ws_bytes, raftgp_stream_t stream) {
+    raftgp_status st = check_csr(g);
+    if (st) return st;
+    if (K < 1) return fail(RAFTGP_EINVAL, "K must be >= 1");
+    if (!labels || !m || !vol || !mod || !ncut || !ws) return fail(RAFTGP_EINVAL, "NULL argument");
+    Carver c(ws);
+    uint32_t* err = c.take<uint32_t>(64);
+    int32_t* deg = c.take<int32_t>(g->n);
+    float* rs = c.take<float>(g->n);
+    float* rsh = c.take<float>(g->n);
+    double* out2 = c.take<double>(2);
+    if (ws_bytes < c.off) return fail(RAFTGP_ENOMEM, "workspace too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemsetAsync(err, 0, sizeof(uint32_t), s);
+    launch_degrees(g, deg, rs, rsh, err, s);
+    st = read_error_word(err, s);
+    if (st) return st;
+    cudaError_t e = launch_score_labels(g, deg, labels, K, reinterpret_cast<long long*>(m),
+                                        reinterpret_cast<long long*>(vol), out2, err, s);
+    if (e != cudaSuccess) return cuda_fail(e, "score");
+    double h[2];
+    e = cudaMemcpyAsync(h, out2, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "score copy");
+    st = read_error_word(err, s);
+    if (st) return st;
+    *mod = h[0];
+    *ncut = h[1];
+    return RAFTGP_OK;
+}
+
+raftgp_status raftgp_kmeanspp(const void* Z, int64_t n, int32_t d, int32_t z_dtype, int32_t K, uint64_t seed,
+                              int32_t* seeds, void* ws, size_t ws_bytes, raftgp_stream_t stream) {
+    if (!Z || !seeds || !ws || n < 1) return fail(RAFTGP_EINVAL, "NULL argument or n < 1");
+    if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d must be 32, 64 or 128");
+    if (K < 1 || K > n) return fail(RAFTGP_EINVAL, "need 1 <= K <= n");
+    if (z_dtype != RAFTGP_F32 && z_dtype != RAFTGP_BF16) return fail(RAFTGP_EINVAL, "unknown z_dtype");
+    Carver c(ws);
+    float* D2 = c.take<float>(n);
+    uint8_t* chosen = c.take<uint8_t>(n);
+    unsigned long long* bs = c.take<unsigned long long>(seed_nblocks(n));
+    if (ws_bytes < c.off) return fail(RAFTGP_ENOMEM, "workspace too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemsetAsync(chosen, 0, (size_t)n, s);
+    launch_seed_first(n, seed, seeds, chosen, s);
+    for (int t = 1; t < K; ++t) launch_seed_round(Z, z_dtype, n, d, t, seed, seeds, chosen, D2, bs, s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kmeanspp");
+    return RAFTGP_OK;
+}
+
+__global__ void k_labels_out(const int16_t* l16, int cs, int64_t n, int32_t* out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = l16[i * cs];
+}
+
+raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype, const float* mu0, int32_t K,
+                           int32_t iters, int32_t assign, int32_t* labels, float* mu_out, int32_t* passes, void* ws,
+                           size_t ws_bytes, raftgp_stream_t stream) {
+    if (!Z || !mu0 || !labels || !ws || n < 1) return fail(RAFTGP_EINVAL, "NULL argument or n < 1");
+    if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d must be 32, 64 or 128");
+    if (K < 1 || K > 32767) return fail(RAFTGP_EINVAL, "need 1 <= K <= 32767");
+    if (iters < 1) return fail(RAFTGP_EINVAL, "iters must be >= 1");
+    if (assign != RAFTGP_ASSIGN_FFMA && assign != RAFTGP_ASSIGN_TC) return fail(RAFTGP_EINVAL, "unknown assign engine");
+    if (assign == RAFTGP_ASSIGN_TC) return fail(RAFTGP_EUNSUPPORTED, "tensor-core assignment is not built yet");
+    Carver c(ws);
+    KmState km{};
+    km.mu = c.take<float>((size_t)K * d);
+    km.norm2 = c.take<float>(K);
+    km.sums = c.take<long long>((size_t)K * d);
+    km.counts = c.take<int32_t>(K);
+    km.labels = c.take<int16_t>((size_t)n * 8);
+    km.active = c.take<int32_t>(MAXC);
+    km.changed = c.take<int32_t>(2 * MAXC);
+    km.passes = c.take<int32_t>(MAXC);
+    if (ws_bytes < c.off) return fail(RAFTGP_ENOMEM, "workspace too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    CandBatch b{};
+    b.n = 1;
+    b.cs = 8;
+    b.k[0] = K;
+    b.off[0] = 0;
+    b.total_k = K;
+    launch_batch_init(b, Z, z_dtype, n, d, nullptr, mu0, km, s);
+    for (int pass = 1; pass <= iters; ++pass) {
+        cudaError_t e = launch_assign_ffma(b, Z, z_dtype, n, d, km, pass, s);
+        if (e != cudaSuccess) return cuda_fail(e, "assign");
+        launch_lloyd_update(b, d, km, pass, s);
+    }
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8);
+    k_labels_out<<<std::max(blocks, 1), 256, 0, s>>>(km.labels, 8, n, labels);
+    if (mu_out) cudaMemcpyAsync(mu_out, km.mu, sizeof(float) * (size_t)K * d, cudaMemcpyDeviceToDevice, s);
+    int32_t hp = 0;
+    cudaMemcpyAsync(&hp, km.passes, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "lloyd");
+    if (passes) *passes = hp;
+    return RAFTGP_OK;
+}
+
+const char* raftgp_last_error(void) { return g_last_error.c_str(); }
+
+const char* raftgp_version(void) { return "raftgp-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

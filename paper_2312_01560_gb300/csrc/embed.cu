@@ -1,0 +1,417 @@
+// embed.cu -- stages 1 and 2 of RaftGP (Section III-A, Eq. 5; Section III-B, Eq. 6).
+//
+// Data flow for n_layers >= 1 (all feature matrices row-major, storage type T = float or bf16,
+// FP32 accumulation):
+//   degrees:   d_i, rs_i = d_i^-1/2 (0 if isolated), rsh_i = (d_i + 1)^-1/2
+//   Theta':    Theta_j * (rs_j for M, 1 otherwise)                (Philox, N x L)
+//   g:         d^T Theta (FP64, only for the full modularity matrix)
+//   layer 0:   Y_i = sum_j Theta'_j, then the operator's row epilogue (x rs_i, or minus the
+//              rank-one term, or the Q-tilde weights), then P1'_i = rsh_i * (Y_i W1)
+//   layer k:   H_i = rsh_i * (P'_i + sum_j P'_j)  ( = (D-hat^-1/2 (A+I) D-hat^-1/2 Z W)_i ),
+//              Z^(k)_i = rownorm(tanh(H_i)), then P'_{k+1} = rsh_i * (Z^(k)_i W_{k+1})
+// The weight product is applied before the aggregation (Z W, then aggregate): the same
+// matrix product as Eq. 6, cheaper when W narrows the width.  Prescaling the gathered
+// rows by their column weight (rs_j or rsh_j) makes every SpMM an unweighted gather-sum.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace raftgp {
+
+// ------------------------------------------------------------------------------------
+// Degrees, reciprocal square roots and graph checks (warp per row).
+// ------------------------------------------------------------------------------------
+__global__ void k_degrees(int64_t n, int64_t nnz, const int32_t* rp32, const int64_t* rp64, const int32_t* col,
+                          int32_t* deg, float* rs, float* rsh, uint32_t* err) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    if (warp == 0 && lane == 0) {
+        const int64_t first = rp64 ? rp64[0] : rp32[0];
+        const int64_t last = rp64 ? rp64[n] : rp32[n];
+        if (first != 0 || last != nnz) flag_error(err, DERR_ROW_PTR);
+    }
+    for (int64_t i = warp; i < n; i += nwarps) {
+        const int64_t b = rp64 ? rp64[i] : rp32[i];
+        const int64_t e = rp64 ? rp64[i + 1] : rp32[i + 1];
+        if (e < b || b < 0 || e > nnz) {
+            if (lane == 0) flag_error(err, DERR_ROW_PTR);
+            continue;
+        }
+        bool bad_range = false, bad_loop = false;
+        for (int64_t p = b + lane; p < e; p += 32) {
+            const int32_t j = __ldg(col + p);
+            bad_range |= (j < 0 || (int64_t)j >= n);
+            bad_loop |= ((int64_t)j == i);
+        }
+        if (__any_sync(0xffffffffu, bad_range) && lane == 0) flag_error(err, DERR_COL_RANGE);
+        if (__any_sync(0xffffffffu, bad_loop) && lane == 0) flag_error(err, DERR_SELF_LOOP);
+        if (lane == 0) {
+            const int64_t d = e - b;
+            deg[i] = (int32_t)d;
+            rs[i] = d > 0 ? rsqrtf((float)d) : 0.0f;
+            rsh[i] = rsqrtf((float)(d + 1));
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Theta (Eq. 5): Theta_jr ~ N(0, 1/L), four columns per Philox block with counter
+// (q, j_lo, j_hi, "Thet").  Stored prescaled by `colscale_j` (rs_j for M).  For the full
+// modularity matrix the same kernel forms per-block FP32 partials of d_j * Theta_jr
+// (from the stored, rounded values), reduced over blocks in FP64 by k_rank1_finish.
+// ------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_theta(int64_t n, int L, uint64_t seed, const float* user_theta, const float* colscale,
+                        const int32_t* deg, T* theta, double* partial) {
+    const int tpr = L / 4;                       // threads per row
+    const int slots = blockDim.x / tpr;          // rows per block iteration
+    const int q = threadIdx.x % tpr;
+    const int slot = threadIdx.x / tpr;
+    const float sigma = rsqrtf((float)L);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t j = (int64_t)blockIdx.x * slots + slot; j < n; j += (int64_t)gridDim.x * slots) {
+        float g[4];
+        if (user_theta) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s) g[s] = user_theta[j * L + 4 * q + s];
+        } else {
+            const U32x4 x = philox4x32_10((uint32_t)q, (uint32_t)j, (uint32_t)((uint64_t)j >> 32), STREAM_THETA, seed);
+            box_muller(x.x, x.y, g[0], g[1]);
+            box_muller(x.z, x.w, g[2], g[3]);
+#pragma unroll
+            for (int s = 0; s < 4; ++s) g[s] *= sigma;
+        }
+        const float cs = colscale ? colscale[j] : 1.0f;
+        T out[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) out[s] = Vec<T>::from_float(g[s] * cs);
+        if constexpr (sizeof(T) == 4) {
+            *reinterpret_cast<float4*>(theta + j * L + 4 * q) =
+                make_float4(Vec<T>::to_float(out[0]), Vec<T>::to_float(out[1]), Vec<T>::to_float(out[2]),
+                            Vec<T>::to_float(out[3]));
+        } else {
+#pragma unroll
+            for (int s = 0; s < 4; ++s) theta[j * L + 4 * q + s] = out[s];
+        }
+        if (partial) {
+            const float dj = (float)deg[j];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) acc[s] += dj * Vec<T>::to_float(out[s]);
+        }
+    }
+    if (!partial) return;
+    extern __shared__ float sred[];  // [slots][L]
+#pragma unroll
+    for (int s = 0; s < 4; ++s) sred[slot * L + 4 * q + s] = acc[s];
+    __syncthreads();
+    for (int c = threadIdx.x; c < L; c += blockDim.x) {
+        double t = 0.0;
+        for (int r = 0; r < slots; ++r) t += (double)sred[r * L + c];
+        partial[(int64_t)blockIdx.x * L + c] = t;
+    }
+}
+
+__global__ void k_rank1_finish(int nblocks, int L, const double* partial, float* g) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= L) return;
+    double t = 0.0;
+    for (int b = 0; b < nblocks; ++b) t += partial[(int64_t)b * L + c];
+    g[c] = (float)t;
+}
+
+// GCN weights W^(k), Xavier-normal, entry (a, 4q+s) from Philox block (q, a, k, "Wgnn").
+__global__ void k_weights(int layer, int lin, int lout, uint64_t seed, float* W) {
+    const int qn = lout / 4;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= lin * qn) return;
+    const int a = t / qn, q = t % qn;
+    const float s = sqrtf(2.0f / (float)(lin + lout));
+    const U32x4 x = philox4x32_10((uint32_t)q, (uint32_t)a, (uint32_t)layer, STREAM_W, seed);
+    float g[4];
+    box_muller(x.x, x.y, g[0], g[1]);
+    box_muller(x.z, x.w, g[2], g[3]);
+#pragma unroll
+    for (int s2 = 0; s2 < 4; ++s2) W[a * lout + 4 * q + s2] = s * g[s2];
+}
+
+// ------------------------------------------------------------------------------------
+// The SpMM layer: warp per row, lanes split the 16-byte chunks of a gathered row, several
+// neighbour rows in flight per warp, FP32 accumulation, fused row epilogue.
+// ------------------------------------------------------------------------------------
+enum Agg { AGG_NCUT = 0, AGG_MOD_FULL = 1, AGG_MOD_REDUCED = 2, AGG_GCN = 3 };
+
+struct LayerArgs {
+    int64_t n;
+    const int32_t* rp32;
+    const int64_t* rp64;
+    const int32_t* col;
+    const int32_t* deg;
+    const float* rowscale;   // rs (M) or rsh (GCN): multiplies the aggregate
+    const float* g;          // d^T Theta for the full modularity matrix
+    double inv_two_e;        // 1 / 2e
+    int act;                 // 0: none, 1: tanh then row l2-normalisation, 2: normalisation only
+    const float* W;          // LIN x lout FP32, or null
+    int lout;
+    const float* postscale;  // multiplies the W product (rsh for the next GCN gather), or null
+    void* out;               // N x (W ? lout : LIN) in T
+    void* stage;             // optional N x LIN in T: the activated row before W
+};
+
+template <int AGG, typename T, int LIN>
+__global__ void __launch_bounds__(256) k_spmm_layer(LayerArgs a, const T* __restrict__ X) {
+    constexpr int E = Vec<T>::E;             // elements per lane chunk (16 bytes)
+    constexpr int LPR = LIN / E;             // lanes per gathered row
+    constexpr int GPW = 32 / LPR;            // rows gathered concurrently per warp
+    constexpr int U = 4;                     // unrolled gathers per lane
+    static_assert(LPR >= 1 && LPR <= 32 && (32 % LPR) == 0, "bad width");
+    extern __shared__ float smem[];
+    float* Ws = smem;                                       // LIN x lout
+    const int warp_in_block = threadIdx.x >> 5;
+    float* vbuf = smem + (a.W ? LIN * a.lout : 0) + warp_in_block * LIN;
+    if (a.W) {
+        for (int t = threadIdx.x; t < LIN * a.lout; t += blockDim.x) Ws[t] = a.W[t];
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / LPR;
+    const int sub = lane % LPR;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < a.n; i += nwarps) {
+        const int64_t beg = a.rp64 ? a.rp64[i] : a.rp32[i];
+        const int64_t end = a.rp64 ? a.rp64[i + 1] : a.rp32[i + 1];
+        float acc[E];
+        float accd[AGG == AGG_MOD_REDUCED ? E : 1];
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = 0.f;
+        if constexpr (AGG == AGG_MOD_REDUCED) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) accd[e] = 0.f;
+        }
+        if constexpr (AGG == AGG_GCN) {
+            if (grp == 0) Vec<T>::load(X + i * LIN + sub * E, acc);   // the self loop of A + I
+        }
+        for (int64_t base = beg; base < end; base += 32) {
+            const int cnt = (int)((end - base) < 32 ? (end - base) : 32);
+            const int32_t my_col = lane < cnt ? __ldg(a.col + base + lane) : 0;
+            float my_d = 0.f;
+            if constexpr (AGG == AGG_MOD_REDUCED) my_d = lane < cnt ? (float)__ldg(a.deg + my_col) : 0.f;
+            for (int t = 0; t < cnt; t += GPW * U) {
+                float v[U][E];
+                float dj[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int idx = t + u * GPW + grp;
+                    const int src = idx < cnt ? idx : 0;
+                    const int32_t j = __shfl_sync(0xffffffffu, my_col, src);
+                    if constexpr (AGG == AGG_MOD_REDUCED) dj[u] = __shfl_sync(0xffffffffu, my_d, src);
+                    if (idx < cnt) {
+                        Vec<T>::load(X + (int64_t)j * LIN + sub * E, v[u]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < E; ++e) v[u][e] = 0.f;
+                        dj[u] = 0.f;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        acc[e] += v[u][e];
+                        if constexpr (AGG == AGG_MOD_REDUCED) accd[e] += dj[u] * v[u][e];
+                    }
+                }
+            }
+        }
+        // combine the GPW concurrent partial sums: afterwards every group holds the row
+#pragma unroll
+        for (int o = 16; o >= LPR; o >>= 1) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+                if constexpr (AGG == AGG_MOD_REDUCED) accd[e] += __shfl_xor_sync(0xffffffffu, accd[e], o);
+            }
+        }
+        // operator epilogue
+        float y[E];
+        if constexpr (AGG == AGG_NCUT || AGG == AGG_GCN) {
+            const float s = a.rowscale[i];
+#pragma unroll
+            for (int e = 0; e < E; ++e) y[e] = s * acc[e];
+        } else if constexpr (AGG == AGG_MOD_FULL) {
+            const float c = (float)((double)a.deg[i] * a.inv_two_e);
+#pragma unroll
+            for (int e = 0; e < E; ++e) y[e] = acc[e] - c * a.g[sub * E + e];
+        } else {
+            const float c = (float)((double)a.deg[i] * a.inv_two_e);
+#pragma unroll
+            for (int e = 0; e < E; ++e) y[e] = acc[e] - c * accd[e];
+        }
+        if (a.act != 0) {
+            float ss = 0.f;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                if (a.act == 1) y[e] = tanhf(y[e]);
+                ss += y[e] * y[e];
+            }
+#pragma unroll
+            for (int o = LPR / 2; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            const float inv = ss > 0.f ? 1.0f / sqrtf(ss) : 0.f;
+#pragma unroll
+            for (int e = 0; e < E; ++e) y[e] *= inv;
+        }
+        if (a.stage && grp == 0) Vec<T>::store(reinterpret_cast<T*>(a.stage) + i * LIN + sub * E, y);
+        if (!a.W) {
+            if (grp == 0) Vec<T>::store(reinterpret_cast<T*>(a.out) + i * LIN + sub * E, y);
+            continue;
+        }
+        // dense layer: out_i = postscale_i * (y W), lane computes lout/32 adjacent columns
+        if (grp == 0) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) vbuf[sub * E + e] = y[e];
+        }
+        __syncwarp();
+        const float ps = a.postscale ? a.postscale[i] : 1.0f;
+        T* orow = reinterpret_cast<T*>(a.out) + i * a.lout;
+        if (a.lout == 128) {
+            float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+            for (int k = 0; k < LIN; ++k) {
+                const float yk = vbuf[k];
+                const float4 w = *reinterpret_cast<const float4*>(Ws + k * 128 + 4 * lane);
+                o[0] += yk * w.x; o[1] += yk * w.y; o[2] += yk * w.z; o[3] += yk * w.w;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) orow[4 * lane + c] = Vec<T>::from_float(o[c] * ps);
+        } else if (a.lout == 64) {
+            float o[2] = {0.f, 0.f};
+#pragma unroll 8
+            for (int k = 0; k < LIN; ++k) {
+                const float yk = vbuf[k];
+                const float2 w = *reinterpret_cast<const float2*>(Ws + k * 64 + 2 * lane);
+                o[0] += yk * w.x; o[1] += yk * w.y;
+            }
+#pragma unroll
+            for (int c = 0; c < 2; ++c) orow[2 * lane + c] = Vec<T>::from_float(o[c] * ps);
+        } else {
+            float o = 0.f;
+#pragma unroll 8
+            for (int k = 0; k < LIN; ++k) o += vbuf[k] * Ws[k * 32 + lane];
+            orow[lane] = Vec<T>::from_float(o * ps);
+        }
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Host launchers
+// ------------------------------------------------------------------------------------
+static int g_num_sms = 0;
+int num_sms() {
+    if (g_num_sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 148;
+    }
+    return g_num_sms;
+}
+
+void launch_degrees(const raftgp_csr* g, int32_t* deg, float* rs, float* rsh, uint32_t* err, cudaStream_t s) {
+    const int threads = 256;
+    int64_t blocks = (g->n * 32 + threads - 1) / threads;
+    blocks = blocks < 1 ? 1 : (blocks > (int64_t)num_sms() * 16 ? (int64_t)num_sms() * 16 : blocks);
+    k_degrees<<<(unsigned)blocks, threads, 0, s>>>(
+        g->n, g->nnz, g->row_ptr_bits == 32 ? (const int32_t*)g->row_ptr : nullptr,
+        g->row_ptr_bits == 64 ? (const int64_t*)g->row_ptr : nullptr, g->col, deg, rs, rsh, err);
+}
+
+int theta_blocks(int64_t n) {
+    int64_t b = (n + 31) / 32;
+    const int64_t cap = (int64_t)num_sms() * 8;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+void launch_theta(int64_t n, int L, int dtype, uint64_t seed, const float* user_theta, const float* colscale,
+                  const int32_t* deg, void* theta, double* partial, float* gvec, cudaStream_t s) {
+    const int threads = 256;
+    const int blocks = theta_blocks(n);
+    const size_t sm = partial ? (size_t)(threads / (L / 4)) * L * sizeof(float) : 0;
+    if (dtype == RAFTGP_BF16)
+        k_theta<__nv_bfloat16><<<blocks, threads, sm, s>>>(n, L, seed, user_theta, colscale, deg,
+                                                           (__nv_bfloat16*)theta, partial);
+    else
+        k_theta<float><<<blocks, threads, sm, s>>>(n, L, seed, user_theta, colscale, deg, (float*)theta, partial);
+    if (partial) k_rank1_finish<<<(L + 127) / 128, 128, 0, s>>>(blocks, L, partial, gvec);
+}
+
+void launch_weights(int layer, int lin, int lout, uint64_t seed, float* W, cudaStream_t s) {
+    const int total = lin * (lout / 4);
+    k_weights<<<(total + 255) / 256, 256, 0, s>>>(layer, lin, lout, seed, W);
+}
+
+template <int AGG, typename T, int LIN>
+static cudaError_t launch_layer_t(const LayerArgs& a, const void* X, cudaStream_t s) {
+    const int threads = 256;
+    const size_t smem = (size_t)((a.W ? LIN * a.lout : 0) + (threads / 32) * LIN) * sizeof(float);
+    auto kern = k_spmm_layer<AGG, T, LIN>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (a.n + (threads / 32) - 1) / (threads / 32);
+    const int64_t cap = (int64_t)num_sms() * per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, threads, smem, s>>>(a, reinterpret_cast<const T*>(X));
+    return cudaGetLastError();
+}
+
+template <int AGG, typename T>
+static cudaError_t launch_layer_w(const LayerArgs& a, int lin, const void* X, cudaStream_t s) {
+    switch (lin) {
+        case 32: return launch_layer_t<AGG, T, 32>(a, X, s);
+        case 64: return launch_layer_t<AGG, T, 64>(a, X, s);
+        case 128: return launch_layer_t<AGG, T, 128>(a, X, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+static cudaError_t launch_layer_a(int agg, const LayerArgs& a, int lin, const void* X, cudaStream_t s) {
+    switch (agg) {
+        case AGG_NCUT: return launch_layer_w<AGG_NCUT, T>(a, lin, X, s);
+        case AGG_MOD_FULL: return launch_layer_w<AGG_MOD_FULL, T>(a, lin, X, s);
+        case AGG_MOD_REDUCED: return launch_layer_w<AGG_MOD_REDUCED, T>(a, lin, X, s);
+        case AGG_GCN: return launch_layer_w<AGG_GCN, T>(a, lin, X, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_layer(int agg, int dtype, const raftgp_csr* g, const int32_t* deg, const float* rowscale,
+                         const float* gvec, int act, const float* W, int lin, int lout, const float* postscale,
+                         const void* X, void* out, void* stage, cudaStream_t s) {
+    LayerArgs a;
+    a.n = g->n;
+    a.rp32 = g->row_ptr_bits == 32 ? (const int32_t*)g->row_ptr : nullptr;
+    a.rp64 = g->row_ptr_bits == 64 ? (const int64_t*)g->row_ptr : nullptr;
+    a.col = g->col;
+    a.deg = deg;
+    a.rowscale = rowscale;
+    a.g = gvec;
+    a.inv_two_e = g->nnz > 0 ? 1.0 / (double)g->nnz : 0.0;
+    a.act = act;
+    a.W = W;
+    a.lout = lout;
+    a.postscale = postscale;
+    a.out = out;
+    a.stage = stage;
+    if (dtype == RAFTGP_BF16) return launch_layer_a<__nv_bfloat16>(agg, a, lin, X, s);
+    return launch_layer_a<float>(agg, a, lin, X, s);
+}
+
+}  // namespace raftgp

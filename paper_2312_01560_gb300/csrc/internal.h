@@ -1,0 +1,79 @@
+// internal.h -- declarations shared by the library's translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "raftgp.h"
+
+namespace raftgp {
+
+int num_sms();
+
+// ---- embedding (embed.cu) -----------------------------------------------------------
+enum { AGG_NCUT_ = 0, AGG_MOD_FULL_ = 1, AGG_MOD_REDUCED_ = 2, AGG_GCN_ = 3 };
+void launch_degrees(const raftgp_csr* g, int32_t* deg, float* rs, float* rsh, uint32_t* err, cudaStream_t s);
+int theta_blocks(int64_t n);
+void launch_theta(int64_t n, int L, int dtype, uint64_t seed, const float* user_theta, const float* colscale,
+                  const int32_t* deg, void* theta, double* partial, float* gvec, cudaStream_t s);
+void launch_weights(int layer, int lin, int lout, uint64_t seed, float* W, cudaStream_t s);
+cudaError_t launch_layer(int agg, int dtype, const raftgp_csr* g, const int32_t* deg, const float* rowscale,
+                         const float* gvec, int act, const float* W, int lin, int lout, const float* postscale,
+                         const void* X, void* out, void* stage, cudaStream_t s);
+
+// ---- k-means (kmeans.cu) --------------------------------------------------------------
+constexpr int MAXC = RAFTGP_MAX_BATCH_CAND;
+
+// One batch of candidates evaluated together; passed by value to every kernel.
+struct CandBatch {
+    int n;              // candidates in the batch
+    int total_k;        // sum of k[]
+    int cs;             // label row stride (n rounded up to a multiple of 8)
+    int k[MAXC];        // K of each candidate
+    int off[MAXC];      // first centroid of each candidate
+};
+
+struct KmState {                 // device arrays of one batch (workspace)
+    float* mu;                   // total_k x d FP32 centroids
+    float* norm2;                // total_k, ||mu||^2 in FP32
+    long long* sums;             // total_k x d, 2^-40 fixed point
+    int32_t* counts;             // total_k
+    int16_t* labels;             // N x cs
+    int32_t* active;             // MAXC
+    int32_t* changed;            // 2 x MAXC (double-buffered by pass parity)
+    int32_t* passes;             // MAXC
+};
+
+void launch_seed_first(int64_t n, uint64_t seed, int32_t* seeds, uint8_t* chosen, cudaStream_t s);
+void launch_seed_round(const void* Z, int zdtype, int64_t n, int d, int t, uint64_t seed, int32_t* seeds,
+                       uint8_t* chosen, float* D2, unsigned long long* blocksum, cudaStream_t s);
+int seed_nblocks(int64_t n);
+
+void launch_batch_init(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, const int32_t* seeds,
+                       const float* mu0, KmState st, cudaStream_t s);
+cudaError_t launch_assign_ffma(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, KmState st, int pass,
+                               cudaStream_t s);
+void launch_lloyd_update(const CandBatch& b, int d, KmState st, int pass, cudaStream_t s);
+
+// ---- scoring (score.cu) ---------------------------------------------------------------
+struct ScoreOut {                // per batch
+    long long* m;                // total_k, directed intra-block entry counts
+    long long* vol;              // total_k
+    double* mod;                 // MAXC
+    double* ncut;                // MAXC
+};
+struct BestState {               // across batches
+    double mod, ncut;
+    int32_t k;
+    int32_t has;
+    int32_t copy_from;           // batch candidate to copy labels from, or -1
+};
+
+void launch_score_batch(const CandBatch& b, const raftgp_csr* g, const int32_t* deg, const int16_t* labels,
+                        ScoreOut so, uint32_t* err, cudaStream_t s);
+void launch_select_best(const CandBatch& b, ScoreOut so, int criterion, BestState* best, const int16_t* labels,
+                        int64_t n, int32_t* out_labels, cudaStream_t s);
+cudaError_t launch_score_labels(const raftgp_csr* g, const int32_t* deg, const int32_t* labels, int K, long long* m,
+                                long long* vol, double* out2, uint32_t* err, cudaStream_t s);
+
+}  // namespace raftgp

@@ -1,0 +1,443 @@
+// kmeans.cu -- k-means for model selection (Section III-C: "apply KMeans" to the
+// embeddings for each candidate K), FP32 engine.
+//
+//   seeding   k-means++ (D^2 sampling) once for K_max; candidate K starts from the first K
+//             seeds.  D^2 is the FP32 direct-form squared distance (ascending coordinates,
+//             every subtract/multiply/add rounded separately), quantised to
+//             floor(D^2 * 2^40) so the cumulative sums are exact integers.
+//   assign    label_i = argmin_c ||z_i - mu_c||^2 over every candidate of a batch, evaluated
+//             as ||mu_c||^2 - 2 z_i.mu_c (the ||z_i||^2 term is common), ties to the lowest c.
+//   update    centroid sums kept in exact 2^-40 fixed point (int64) and updated incrementally:
+//             a point whose label changes is subtracted from its old cluster and added to its
+//             new one, so the sums equal the from-scratch sums bit for bit in any order.  The
+//             mean is formed in FP64; an empty cluster keeps its centroid.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace raftgp {
+
+template <typename T>
+__device__ __forceinline__ float zval(const T* Z, int64_t i) {
+    return load_elem(Z, i);
+}
+
+// FP32 direct-form squared distance, ascending coordinates, no contraction.
+template <typename T>
+__device__ __forceinline__ float sqdist_direct(const T* __restrict__ zi, const float* __restrict__ c, int d) {
+    float s = 0.0f;
+    for (int k = 0; k < d; ++k) {
+        const float t = __fsub_rn(load_elem(zi, k), c[k]);
+        s = __fadd_rn(s, __fmul_rn(t, t));
+    }
+    return s;
+}
+
+__device__ __forceinline__ uint64_t kmpp_draw(uint64_t seed, int t) {
+    const U32x4 x = philox4x32_10((uint32_t)t, 0u, 0u, STREAM_KMPP, seed);
+    return (uint64_t)x.x | ((uint64_t)x.y << 32);
+}
+
+__device__ __forceinline__ unsigned long long quantise(float d2) {
+    return (unsigned long long)((double)d2 * FIXED_SCALE);
+}
+
+constexpr int SEED_THREADS = 256;  // points per block partial
+
+__global__ void k_seed_first(int64_t n, uint64_t seed, int32_t* seeds, uint8_t* chosen) {
+    const int64_t i = (int64_t)mulhi64(kmpp_draw(seed, 0), (uint64_t)n);
+    seeds[0] = (int32_t)i;
+    chosen[i] = 1;
+}
+
+// D^2_i = min(D^2_i, dist(z_i, z_{seeds[t-1]})), and per-block sums of the quantised D^2.
+template <typename T>
+__global__ void __launch_bounds__(SEED_THREADS) k_seed_update(const T* __restrict__ Z, int64_t n, int d, int t,
+                                                              const int32_t* seeds, float* D2,
+                                                              unsigned long long* blocksum) {
+    __shared__ float c[128];
+    __shared__ unsigned long long wsum[SEED_THREADS / 32];
+    const int64_t ci = seeds[t - 1];
+    for (int k = threadIdx.x; k < d; k += blockDim.x) c[k] = zval(Z, ci * d + k);
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long q = 0;
+    if (i < n) {
+        const float nd = sqdist_direct(Z + i * d, c, d);
+        const float cur = (t == 1) ? nd : fminf(D2[i], nd);
+        D2[i] = cur;
+        q = quantise(cur);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = q;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long s = 0;
+        for (int w = 0; w < SEED_THREADS / 32; ++w) s += wsum[w];
+        blocksum[blockIdx.x] = s;
+    }
+}
+
+// Exclusive scan of 1024 values held one per thread; returns this thread's exclusive prefix
+// and the block total.
+__device__ unsigned long long block_scan_1024(unsigned long long v, unsigned long long* total) {
+    __shared__ unsigned long long ws[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long s = ws[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        ws[lane] = s;  // inclusive over warps
+    }
+    __syncthreads();
+    const unsigned long long before = (w > 0 ? ws[w - 1] : 0ull) + x - v;
+    *total = ws[31];
+    __syncthreads();
+    return before;
+}
+
+// Pick seed t: threshold floor(r_t * sum q / 2^64), first point whose inclusive prefix of q
+// exceeds it.  One block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_seed_pick(int64_t n, int nblocks, const unsigned long long* blocksum,
+                                                    const float* D2, uint64_t seed, int t, int32_t* seeds,
+                                                    uint8_t* chosen) {
+    __shared__ unsigned long long s_thr, s_base;
+    __shared__ int s_block;
+    __shared__ long long s_pick;
+    // total
+    unsigned long long run = 0;  // running prefix of completed chunks
+    unsigned long long tot = 0;
+    for (int b0 = 0; b0 < nblocks; b0 += 1024) {
+        const int b = b0 + threadIdx.x;
+        unsigned long long v = b < nblocks ? blocksum[b] : 0ull, ct;
+        block_scan_1024(v, &ct);
+        tot += ct;
+    }
+    if (threadIdx.x == 0) {
+        s_pick = -1;
+        s_block = -1;
+        s_thr = tot > 0 ? mulhi64(kmpp_draw(seed, t), tot) : 0ull;
+    }
+    __syncthreads();
+    if (tot == 0) {
+        // every remaining point coincides with a seed: lowest-index unchosen point
+        for (int64_t base = 0; base < n; base += 1024) {
+            const int64_t i = base + threadIdx.x;
+            const bool cand = i < n && !chosen[i];
+            const unsigned mask = __ballot_sync(0xffffffffu, cand);
+            __shared__ long long wmin[32];
+            if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = mask ? base + (threadIdx.x & ~31) + __ffs(mask) - 1 : -1;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int w = 0; w < 32; ++w)
+                    if (wmin[w] >= 0) { s_pick = wmin[w]; break; }
+            }
+            __syncthreads();
+            if (s_pick >= 0) break;
+        }
+    } else {
+        const unsigned long long thr = s_thr;
+        for (int b0 = 0; b0 < nblocks; b0 += 1024) {
+            const int b = b0 + threadIdx.x;
+            const unsigned long long v = b < nblocks ? blocksum[b] : 0ull;
+            unsigned long long ct;
+            const unsigned long long ex = block_scan_1024(v, &ct);
+            const unsigned long long incl = run + ex + v;
+            const bool hit = b < nblocks && incl > thr && run + ex <= thr;
+            if (hit) {
+                s_block = b;
+                s_base = run + ex;
+            }
+            __syncthreads();
+            if (s_block >= 0) break;
+            run += ct;
+        }
+        const int b = s_block;
+        // inside the block: points b*SEED_THREADS .. +SEED_THREADS
+        unsigned long long v = 0;
+        const int64_t i = (int64_t)b * SEED_THREADS + threadIdx.x;
+        if (threadIdx.x < SEED_THREADS && i < n) v = quantise(D2[i]);
+        unsigned long long ct;
+        const unsigned long long ex = block_scan_1024(v, &ct);
+        const unsigned long long incl = s_base + ex + v;
+        if (threadIdx.x < SEED_THREADS && i < n && incl > thr && s_base + ex <= thr) s_pick = i;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        long long p = s_pick;
+        if (p < 0) p = 0;  // unreachable for valid input; keeps indices in range
+        seeds[t] = (int32_t)p;
+        chosen[p] = 1;
+    }
+}
+
+int seed_nblocks(int64_t n) { return (int)((n + SEED_THREADS - 1) / SEED_THREADS); }
+
+void launch_seed_first(int64_t n, uint64_t seed, int32_t* seeds, uint8_t* chosen, cudaStream_t s) {
+    k_seed_first<<<1, 1, 0, s>>>(n, seed, seeds, chosen);
+}
+
+void launch_seed_round(const void* Z, int zdtype, int64_t n, int d, int t, uint64_t seed, int32_t* seeds,
+                       uint8_t* chosen, float* D2, unsigned long long* blocksum, cudaStream_t s) {
+    const int nb = seed_nblocks(n);
+    if (zdtype == RAFTGP_BF16)
+        k_seed_update<__nv_bfloat16><<<nb, SEED_THREADS, 0, s>>>((const __nv_bfloat16*)Z, n, d, t, seeds, D2, blocksum);
+    else
+        k_seed_update<float><<<nb, SEED_THREADS, 0, s>>>((const float*)Z, n, d, t, seeds, D2, blocksum);
+    k_seed_pick<<<1, 1024, 0, s>>>(n, nb, blocksum, D2, seed, t, seeds, chosen);
+}
+
+// ------------------------------------------------------------------------------------
+// Batch set-up: centroids from seeds (or given mu0), zero sums/counts, labels = -1.
+// ------------------------------------------------------------------------------------
+template <typename T>
+__global__ void k_batch_init_mu(CandBatch b, const T* Z, int d, const int32_t* seeds, const float* mu0, KmState st) {
+    const int c = blockIdx.y;
+    if (c >= b.n) return;
+    const int K = b.k[c], off = b.off[c];
+    for (int j = blockIdx.x; j < K; j += gridDim.x) {
+        const int64_t src = seeds ? (int64_t)seeds[j] : -1;
+        float part = 0.f;
+        for (int k = threadIdx.x; k < d; k += blockDim.x) {
+            const float v = mu0 ? mu0[(int64_t)j * d + k] : zval(Z, src * d + k);
+            st.mu[(int64_t)(off + j) * d + k] = v;
+            st.sums[(int64_t)(off + j) * d + k] = 0;
+        }
+        (void)part;
+        if (threadIdx.x == 0) st.counts[off + j] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st.active[c] = 1;
+        st.changed[c] = 0;
+        st.changed[MAXC + c] = 0;
+        st.passes[c] = 0;
+    }
+}
+
+// ||mu_c||^2 in FP32, one thread per centroid (ascending coordinates).
+__global__ void k_norms(int total_k, int d, const float* mu, float* norm2) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= total_k) return;
+    float s = 0.f;
+    for (int k = 0; k < d; ++k) s = fmaf(mu[(int64_t)j * d + k], mu[(int64_t)j * d + k], s);
+    norm2[j] = s;
+}
+
+__global__ void k_fill_labels(int16_t* labels, int64_t count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        labels[i] = -1;
+}
+
+void launch_batch_init(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, const int32_t* seeds,
+                       const float* mu0, KmState st, cudaStream_t s) {
+    dim3 grid(64, b.n);
+    if (zdtype == RAFTGP_BF16)
+        k_batch_init_mu<__nv_bfloat16><<<grid, 128, 0, s>>>(b, (const __nv_bfloat16*)Z, d, seeds, mu0, st);
+    else
+        k_batch_init_mu<float><<<grid, 128, 0, s>>>(b, (const float*)Z, d, seeds, mu0, st);
+    k_norms<<<(b.total_k + 127) / 128, 128, 0, s>>>(b.total_k, d, st.mu, st.norm2);
+    const int64_t cnt = n * (int64_t)b.cs;
+    int blocks = (int)((cnt + 255) / 256);
+    if (blocks > num_sms() * 8) blocks = num_sms() * 8;
+    if (blocks < 1) blocks = 1;
+    k_fill_labels<<<blocks, 256, 0, s>>>(st.labels, cnt);
+}
+
+// ------------------------------------------------------------------------------------
+// Plain FP32 assignment: CTA = 128 points x one candidate; centroids in chunks of 64.
+// Thread (pg, cg) owns points 4pg..4pg+3 and chunk centroids 8cg..8cg+7 (register tile).
+// After the scan, the label change is applied to the fixed-point sums and counts.
+// ------------------------------------------------------------------------------------
+constexpr int AS_TP = 128;  // points per CTA
+constexpr int AS_TC = 64;   // centroids per chunk
+
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_assign_ffma(CandBatch b, const T* __restrict__ Z, int64_t n, KmState st,
+                                                     int pass) {
+    const int c = blockIdx.y;
+    if (c >= b.n || !st.active[c]) return;
+    const int K = b.k[c], off = b.off[c];
+    extern __shared__ float sm[];
+    float* zT = sm;                     // D x AS_TP
+    float* mT = sm + D * AS_TP;         // D x AS_TC
+    float* nrm = mT + D * AS_TC;        // AS_TC
+    __shared__ int s_new[AS_TP], s_old[AS_TP];
+    const int64_t p0 = (int64_t)blockIdx.x * AS_TP;
+    for (int t = threadIdx.x; t < D * AS_TP; t += blockDim.x) {
+        const int p = t / D, k = t % D;
+        zT[k * AS_TP + p] = (p0 + p < n) ? zval(Z, (p0 + p) * D + k) : 0.f;
+    }
+    const int pg = threadIdx.x >> 3, cg = threadIdx.x & 7;
+    float bv[4];
+    int bi[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) { bv[r] = INFINITY; bi[r] = 0x7fffffff; }
+    for (int c0 = 0; c0 < K; c0 += AS_TC) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < D * AS_TC; t += blockDim.x) {
+            const int j = t / D, k = t % D;
+            mT[k * AS_TC + j] = (c0 + j < K) ? st.mu[(int64_t)(off + c0 + j) * D + k] : 0.f;
+        }
+        for (int j = threadIdx.x; j < AS_TC; j += blockDim.x) nrm[j] = (c0 + j < K) ? st.norm2[off + c0 + j] : INFINITY;
+        __syncthreads();
+        float acc[4][8];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < D; ++k) {
+            const float4 zv = *reinterpret_cast<const float4*>(zT + k * AS_TP + 4 * pg);
+            const float4 m0 = *reinterpret_cast<const float4*>(mT + k * AS_TC + 8 * cg);
+            const float4 m1 = *reinterpret_cast<const float4*>(mT + k * AS_TC + 8 * cg + 4);
+            const float za[4] = {zv.x, zv.y, zv.z, zv.w};
+            const float ma[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(za[r], ma[q], acc[r][q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float nq = nrm[8 * cg + q];
+            const int idx = c0 + 8 * cg + q;
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const float s = fmaf(-2.0f, acc[r][q], nq);
+                if (s < bv[r]) { bv[r] = s; bi[r] = idx; }
+            }
+        }
+    }
+    // combine the 8 centroid groups (lanes differing in the low 3 bits)
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv[r], o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi[r], o);
+            if (ov < bv[r] || (ov == bv[r] && oi < bi[r])) { bv[r] = ov; bi[r] = oi; }
+        }
+    }
+    if (cg < 4) {
+        const int p = 4 * pg + cg;
+        const int64_t i = p0 + p;
+        int nl = -1, ol = -1;
+        if (i < n) {
+            nl = bi[cg];
+            if (nl < 0 || nl >= K) nl = 0;   // every score NaN (non-finite input): keep indices in range
+            int16_t* lp = st.labels + i * b.cs + c;
+            ol = *lp;
+            *lp = (int16_t)nl;
+        }
+        s_new[p] = nl;
+        s_old[p] = ol;
+    }
+    __syncthreads();
+    // label changes -> counts, fixed-point sums, changed counter
+    int nchanged = 0;
+    for (int p = threadIdx.x; p < AS_TP; p += blockDim.x) {
+        const int nl = s_new[p], ol = s_old[p];
+        if (nl >= 0 && nl != ol) {
+            ++nchanged;
+            atomicAdd(st.counts + off + nl, 1);
+            if (ol >= 0) atomicSub(st.counts + off + ol, 1);
+        }
+    }
+    for (int t = threadIdx.x; t < AS_TP * D; t += blockDim.x) {
+        const int p = t / D, k = t % D;
+        const int nl = s_new[p], ol = s_old[p];
+        if (nl < 0 || nl == ol) continue;
+        const long long v = __float2ll_rn(zT[k * AS_TP + p] * FIXED_SCALE_F);
+        atomicAdd(reinterpret_cast<unsigned long long*>(st.sums + (int64_t)(off + nl) * D + k), (unsigned long long)v);
+        if (ol >= 0)
+            atomicAdd(reinterpret_cast<unsigned long long*>(st.sums + (int64_t)(off + ol) * D + k),
+                      (unsigned long long)(-v));
+    }
+    nchanged = __reduce_add_sync(0xffffffffu, nchanged);
+    if ((threadIdx.x & 31) == 0 && nchanged) atomicAdd(st.changed + (pass & 1) * MAXC + c, nchanged);
+}
+
+template <typename T, int D>
+static cudaError_t launch_assign_t(const CandBatch& b, const T* Z, int64_t n, KmState st, int pass, cudaStream_t s) {
+    const size_t smem = (size_t)(D * AS_TP + D * AS_TC + AS_TC) * sizeof(float);
+    auto kern = k_assign_ffma<T, D>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((unsigned)((n + AS_TP - 1) / AS_TP), b.n);
+    kern<<<grid, 256, smem, s>>>(b, Z, n, st, pass);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assign_ffma(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, KmState st, int pass,
+                               cudaStream_t s) {
+    if (zdtype == RAFTGP_BF16) {
+        const __nv_bfloat16* z = (const __nv_bfloat16*)Z;
+        switch (d) {
+            case 32: return launch_assign_t<__nv_bfloat16, 32>(b, z, n, st, pass, s);
+            case 64: return launch_assign_t<__nv_bfloat16, 64>(b, z, n, st, pass, s);
+            case 128: return launch_assign_t<__nv_bfloat16, 128>(b, z, n, st, pass, s);
+        }
+    } else {
+        const float* z = (const float*)Z;
+        switch (d) {
+            case 32: return launch_assign_t<float, 32>(b, z, n, st, pass, s);
+            case 64: return launch_assign_t<float, 64>(b, z, n, st, pass, s);
+            case 128: return launch_assign_t<float, 128>(b, z, n, st, pass, s);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------------------------
+// After a pass: a candidate with no label change is converged (inactive); otherwise its
+// centroids become the FP64 means of the fixed-point sums (empty clusters keep theirs).
+// ------------------------------------------------------------------------------------
+__global__ void k_lloyd_update(CandBatch b, int d, KmState st, int pass) {
+    const int c = blockIdx.y;
+    if (c >= b.n || !st.active[c]) return;
+    const int changed = st.changed[(pass & 1) * MAXC + c];
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st.passes[c] = pass;
+        st.changed[((pass + 1) & 1) * MAXC + c] = 0;
+    }
+    if (changed == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) st.active[c] = 0;
+        return;
+    }
+    const int K = b.k[c], off = b.off[c];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < K; j += gridDim.x * blockDim.x) {
+        const int cnt = st.counts[off + j];
+        if (cnt <= 0) continue;
+        const double inv = 1.0 / ((double)cnt * FIXED_SCALE);
+        float s = 0.f;
+        for (int k = 0; k < d; ++k) {
+            const float v = (float)((double)st.sums[(int64_t)(off + j) * d + k] * inv);
+            st.mu[(int64_t)(off + j) * d + k] = v;
+            s = fmaf(v, v, s);
+        }
+        st.norm2[off + j] = s;
+    }
+}
+
+void launch_lloyd_update(const CandBatch& b, int d, KmState st, int pass, cudaStream_t s) {
+    dim3 grid(8, b.n);
+    k_lloyd_update<<<grid, 128, 0, s>>>(b, d, st, pass);
+}
+
+}  // namespace raftgp

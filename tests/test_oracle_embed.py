@@ -170,3 +170,16 @@ def test_embed_chains_projection_and_layers():
     Z1 = oracle.gcn_layer(g, Y, oracle.gcn_weight(1, 16, 12, seed=3))
     Z2 = oracle.gcn_layer(g, Z1, oracle.gcn_weight(2, 12, 8, seed=3))
     np.testing.assert_array_equal(Z, Z2)
+
+
+def test_row_sampled_forms_agree_with_whole_graph_forms():
+    g = small.random_graph(80, 0.08, seed=6, isolated=2)
+    rows = np.array([0, 5, 79, 78, 33])
+    for op in ("ncut", "mod_full", "mod_reduced"):
+        full = oracle.project(g, op, oracle.theta(g.n, 16, seed=4))
+        np.testing.assert_allclose(oracle.project_rows(g, op, 16, 4, rows), full[rows], atol=1e-13)
+    rng = np.random.default_rng(6)
+    Zin = rng.normal(size=(80, 8)).astype(np.float32)
+    W = rng.normal(size=(8, 4))
+    np.testing.assert_allclose(oracle.gcn_rows(g, Zin, W, rows), oracle.gcn_layer(g, Zin.astype(np.float64), W)[rows],
+                               atol=1e-14)
