@@ -165,10 +165,10 @@ __global__ void __launch_bounds__(1024) k_seed_pick(int64_t n, int nblocks, cons
             if (s_block >= 0) break;
             run += ct;
         }
-        const int b = s_block;
+        const int b = s_block;   // always found: thr < total
         // inside the block: points b*SEED_THREADS .. +SEED_THREADS
         unsigned long long v = 0;
-        const int64_t i = (int64_t)b * SEED_THREADS + threadIdx.x;
+        const int64_t i = (int64_t)(b < 0 ? 0 : b) * SEED_THREADS + threadIdx.x;
         if (threadIdx.x < SEED_THREADS && i < n) v = quantise(D2[i]);
         unsigned long long ct;
         const unsigned long long ex = block_scan_1024(v, &ct);
