@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""End-to-end RaftGP partition benchmark: edges/s on a 1,000,000-node degree-corrected SBM.
+
+One step = the whole hot path on one synthetic graph: Gaussian projection (Eq. 5), the
+two-layer random GCN (Eq. 6), k-means++ seeding, Lloyd k-means for every candidate K of a
+10 + 10 hierarchical grid over [50, 400], and modularity/NCut scoring of each candidate.
+`value` = undirected edges / device time per step with the graph already in HBM; `e2e`
+adds the pinned-host -> device copy of the CSR and the device -> host copy of the labels.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--form bf16|f32]
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+With N > 1 (torchrun) every rank partitions its own replica (the path does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {
+    "name": "dcsbm-1m",
+    "graph": "dcsbm-1m", "graph_seed": 0,
+    "op": "ncut", "dims": (128, 128, 64),
+    "kmin": 50, "kmax": 400, "grid": 10, "iters": 50,
+}
+PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+N_SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return p, "measured"
+    return dict(PEAK_FALLBACK), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"raftgp_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------------------
+# algorithmic work of each kernel family (per step), for the roofline of the dominant one
+# ----------------------------------------------------------------------------------------
+def algorithmic_work(fam, g, wl, elem, cands):
+    n, nnz = g.n, g.nnz
+    L, h1, d = wl["dims"]
+    if fam == "assign_ffma" or fam == "assign_tc":
+        pairs = sum(n * k * p for k, _, _, p in cands)
+        return ("alu" if fam == "assign_ffma" else "tensor"), 2.0 * d * pairs, "FLOP"
+    if fam == "seed_update":
+        rounds = min(wl["kmax"], n) - 1
+        return "hbm", rounds * n * (d * elem + 8.0), "B"
+    if fam == "spmm_project":
+        # every input row read once, the column list once, each output row written once
+        return "hbm", 4.0 * nnz + 8.0 * n + n * L * elem + n * h1 * elem, "B"
+    if fam == "spmm_gcn":
+        return "hbm", 2 * (4.0 * nnz + 8.0 * n) + n * (h1 + d) * elem + n * (d + d) * elem, "B"
+    if fam == "score_count":
+        return "hbm", len(cands) * 0 + 2 * (4.0 * nnz + 8.0 * n + n * 16 * 2), "B"
+    return None, 0.0, None
+
+
+def roofline(profile, g, wl, elem, cands, steps):
+    p, src = peaks()
+    shares = {k: v["ms"] for k, v in profile.items()}
+    dom = max(shares, key=shares.get)
+    bound, work, unit = algorithmic_work(dom, g, wl, elem, cands)
+    ent = profile[dom]
+    per_launch_ms = ent["ms"] / max(ent["timed"], 1)
+    work_per_launch = work / max(ent["launches"] / steps, 1)
+    out = {"kernel": dom, "launches_per_step": ent["launches"] / steps, "avg_launch_ms": per_launch_ms,
+           "traffic": None}
+    if bound == "hbm":
+        ach = work_per_launch / (per_launch_ms * 1e-3) / 1e9
+        out.update(bound="hbm", achieved=ach, peak=p["hbm_gbs"], unit="GB/s", frac=ach / p["hbm_gbs"],
+                   peak_source=src)
+    elif bound == "tensor":
+        ach = work_per_launch / (per_launch_ms * 1e-3) / 1e12
+        pk = p["bf16_tflops_sustained"]
+        out.update(bound="tensor", achieved=ach, peak=pk, unit="TFLOP/s", frac=ach / pk, peak_source=src)
+    elif bound == "alu":
+        ach = work_per_launch / (per_launch_ms * 1e-3) / 1e12
+        pk = N_SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # FP32 FMA lanes x 2 FLOP x max clock
+        out.update(bound="alu", achieved=ach, peak=pk, unit="TFLOP/s", frac=ach / pk, peak_source="derived")
+    total = sum(shares.values())
+    out["shares"] = {k: round(v / total, 4) for k, v in sorted(shares.items(), key=lambda kv: -kv[1])}
+    return out
+
+
+# ----------------------------------------------------------------------------------------
+# the oracle on a bounded sample (CPU baseline and the reference arm)
+# ----------------------------------------------------------------------------------------
+def oracle_sample(g, wl, cand_ks, rng_seed=0, rows=64, seed_rounds=4, lloyd_points=1500):
+    """Times every oracle stage on a bounded sample at full-graph context and scales each to
+    the whole workload: embedding rows (projection + 2 GCN layers) x N, k-means++ rounds x
+    (K_max - 1), Lloyd point-centroid pairs x N x sum(K) x T (the pass cap), scoring x
+    candidates.  Returns (edges/s, seconds of CPU work, description)."""
+    import oracle
+    L, h1, d = wl["dims"]
+    rng = np.random.default_rng(rng_seed)
+    n = g.n
+    sample = rng.choice(n, rows, replace=False)
+    t0 = time.perf_counter()
+    oracle.project_rows(g, wl["op"], L, 1, sample)
+    t_proj = time.perf_counter() - t0
+    Zin = rng.normal(size=(n, L)).astype(np.float32)
+    W1 = oracle.gcn_weight(1, L, h1, 1)
+    t0 = time.perf_counter()
+    oracle.gcn_rows(g, Zin, W1, sample)
+    t_gcn1 = time.perf_counter() - t0
+    Z1 = rng.normal(size=(n, h1)).astype(np.float32)
+    W2 = oracle.gcn_weight(2, h1, d, 1)
+    t0 = time.perf_counter()
+    oracle.gcn_rows(g, Z1, W2, sample)
+    t_gcn2 = time.perf_counter() - t0
+    del Zin, Z1
+    Zs = rng.normal(size=(n, d))
+    Zs /= np.linalg.norm(Zs, axis=1, keepdims=True)
+    t0 = time.perf_counter()
+    oracle.kmeanspp(Zs, seed_rounds + 1, 2)
+    t_seed = (time.perf_counter() - t0) / seed_rounds
+    kmax = max(cand_ks)
+    pts = Zs[rng.choice(n, lloyd_points, replace=False)]
+    t0 = time.perf_counter()
+    oracle.lloyd(pts, pts[:kmax].copy(), 1)
+    t_pair = (time.perf_counter() - t0) / (lloyd_points * kmax)
+    labels = rng.integers(0, 200, n).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.score(g, labels, 200)
+    t_score = time.perf_counter() - t0
+    spent = t_proj + t_gcn1 + t_gcn2 + t_seed * seed_rounds + t_pair * lloyd_points * kmax + t_score
+    total = ((t_proj + t_gcn1 + t_gcn2) / rows * n + t_seed * (kmax - 1)
+             + t_pair * n * sum(cand_ks) * wl["iters"] + t_score * len(cand_ks))
+    desc = (f"oracle (1 thread, FP64) timed on {rows} sampled rows through projection + 2 GCN layers, "
+            f"{seed_rounds} k-means++ rounds over all {n} points, one Lloyd pass of {lloyd_points} points x "
+            f"K={kmax}, one scoring pass; scaled to N rows, K_max-1 rounds, N x sum(K)={sum(cand_ks)} x "
+            f"{wl['iters']} passes (the cap) and {len(cand_ks)} candidates")
+    return g.n_edges / total, spent, desc
+
+
+def reference_candidates(wl):
+    import oracle
+    coarse = oracle.coarse_grid(wl["kmin"], wl["kmax"], wl["grid"])
+    # refined grid around the planted K (200): between its coarse neighbours
+    j = int(np.argmin([abs(k - 200) for k in coarse]))
+    ref = oracle.refine_grid(coarse[max(j - 1, 0)], coarse[min(j + 1, len(coarse) - 1)], wl["grid"], coarse)
+    return coarse + ref
+
+
+# ----------------------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="f32", choices=["bf16", "f32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    wl = WORKLOAD
+
+    from inputs.dcsbm import workload
+    g = workload(wl["graph"], seed=wl["graph_seed"])
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cands = reference_candidates(wl)
+        for _ in range(args.warmup):
+            oracle_sample(g, wl, cands, rows=16, seed_rounds=1, lloyd_points=200)
+        vals, spent_all, desc = [], 0.0, ""
+        t0 = time.perf_counter()
+        for s in range(args.steps):
+            v, spent, desc = oracle_sample(g, wl, cands, rng_seed=s)
+            vals.append(v)
+            spent_all += spent
+        wall = time.perf_counter() - t0
+        value = float(np.mean(vals))
+        line = {"impl": "reference", "metric": "end-to-end edges/s at 1M nodes", "value": value, "unit": "edges/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * g.n_edges / value, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "dcsbm-1m: N=1,000,000 K=200 mean degree ~25, L=128, GCN 128-128-64, "
+                                       "K in [50,400] (10 coarse + 10 refined), 50 Lloyd passes max",
+                           "sample_wall_s": wall},
+                "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": desc},
+                "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2312_01560_gb300 import api
+    from paper_2312_01560_gb300.metrics import nmi
+
+    dg = api.DeviceGraph.from_host(g, dev, row_ptr_bits=64)
+    labels = torch.empty(g.n, dtype=torch.int32, device=dev)
+    dtype = args.form
+    assign = "tc" if args.form == "bf16" else "ffma"
+    kw = dict(op=wl["op"], dims=wl["dims"], dtype=dtype, kmin=wl["kmin"], kmax=wl["kmax"], grid=wl["grid"],
+              iters=wl["iters"], assign=assign, batch=0, labels=labels)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        api.partition(dg, **kw)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    api.profile_enable(True)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    rep = None
+    for _ in range(args.steps):
+        _, rep = api.partition(dg, **kw)
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    prof = api.profile_read()
+    api.profile_enable(False)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * g.n_edges / (ms * 1e-3)
+    launches = int(sum(v["launches"] for v in prof.values()) / args.steps)
+    elem = 2 if dtype == "bf16" else 4
+    roof = roofline(prof, g, wl, elem, rep["cands"], args.steps)
+    lab = labels.cpu().numpy()
+    quality = {"k_best": rep["k"], "nmi_planted": nmi(lab, g.planted),
+               "mod_best": [c[1] for c in rep["cands"] if c[0] == rep["k"]][0]}
+
+    e2e = None
+    if not args.no_e2e:
+        rp_h = torch.from_numpy(g.row_ptr.astype(np.int64)).pin_memory()
+        col_h = torch.from_numpy(g.col).pin_memory()
+        lab_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
+        rp_d = torch.empty_like(rp_h, device=dev)
+        col_d = torch.empty_like(col_h, device=dev)
+        dg2 = api.DeviceGraph(g.n, rp_d, col_d)
+        e_steps = max(1, min(args.steps, 3))
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e_steps):
+            rp_d.copy_(rp_h, non_blocking=True)
+            col_d.copy_(col_h, non_blocking=True)
+            api.partition(dg2, **kw)
+            lab_h.copy_(labels, non_blocking=True)
+            torch.cuda.synchronize()
+        e_ms = (time.perf_counter() - t0) * 1e3 / e_steps
+        if world > 1:
+            t = torch.tensor([e_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": world * g.n_edges / (e_ms * 1e-3), "unit": "edges/s",
+               "h2d_bytes_per_step": int(rp_h.numel() * 8 + col_h.numel() * 4),
+               "d2h_bytes_per_step": int(lab_h.numel() * 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ks = [c[0] for c in rep["cands"]]
+        v, spent, desc = oracle_sample(g, wl, ks)
+        cpu = {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": desc,
+               "cpu_seconds": round(spent, 2)}
+
+    if rank == 0:
+        line = {"metric": "end-to-end edges/s at 1M nodes", "value": value, "unit": "edges/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+                "config": {"workload": "dcsbm-1m: N=1,000,000 K=200 Dirichlet(1) sizes, degree exponent 2.2 in "
+                                       "[5,5000], mean degree ~25, ratio 2:1; op=%s, L=128, GCN 128-128-64, "
+                                       "K in [50,400] (10 coarse + 10 refined), <=50 Lloyd passes" % wl["op"],
+                           "edges": g.n_edges, "nodes": g.n, "form": args.form, "assign": assign,
+                           "l2": "inputs larger than L2 (Theta %d MB, col %d MB)" % (
+                               g.n * wl["dims"][0] * elem // 2 ** 20, g.nnz * 4 // 2 ** 20),
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "gpu_launches": launches, "clocks": clocks, "roofline": roof, "quality": quality,
+                "e2e": e2e, "cpu_baseline": cpu,
+                "kernels": {k: {"launches_per_step": v["launches"] / args.steps, "ms_per_step": v["ms"] / args.steps}
+                            for k, v in prof.items()}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

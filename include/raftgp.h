@@ -159,6 +159,23 @@ raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype,
                            int32_t iters, int32_t assign, int32_t* labels, float* mu_out, int32_t* passes,
                            void* ws, size_t ws_bytes, raftgp_stream_t stream);
 
+/* ---- Instrumentation (the paper has no counterpart: its Table III times whole stages) ----
+ * When enabled, each kernel family is bracketed by CUDA events recorded on the stream it is
+ * launched on, and its launches are counted.  raftgp_profile_enable(1) clears the counters
+ * and starts recording; raftgp_profile_enable(0) stops.  raftgp_profile_read synchronises the
+ * device and writes up to `cap` entries (families with at least one launch); it returns the
+ * number written.  Timing covers at most 32768 bracketed launch groups per enable; launches
+ * beyond that are counted but not timed (timed < launches). */
+typedef struct {
+    const char* name;   /* kernel family, a static string */
+    int64_t launches;   /* kernel launches since enable */
+    int64_t timed;      /* launches covered by the timing */
+    double ms;          /* summed device time of the timed launches */
+} raftgp_prof_entry;
+
+raftgp_status raftgp_profile_enable(int32_t on);
+int32_t raftgp_profile_read(raftgp_prof_entry* out, int32_t cap);
+
 /* Message for the last non-OK status returned on the calling thread. */
 const char* raftgp_last_error(void);
 

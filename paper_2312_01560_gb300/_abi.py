@@ -22,7 +22,8 @@ MAX_BATCH_CAND = 64
 
 # Every entry point declared in include/raftgp.h.
 EXPORTS = ("raftgp_workspace_size", "raftgp_embed", "raftgp_select", "raftgp_partition", "raftgp_score",
-           "raftgp_kmeanspp", "raftgp_lloyd", "raftgp_last_error", "raftgp_version")
+           "raftgp_kmeanspp", "raftgp_lloyd", "raftgp_profile_enable", "raftgp_profile_read", "raftgp_last_error",
+           "raftgp_version")
 
 
 class Csr(C.Structure):
@@ -45,6 +46,10 @@ class SelectResult(C.Structure):
     _fields_ = [("k_best", C.c_int32), ("n_cand", C.c_int32), ("cand_cap", C.c_int32),
                 ("cand_k", C.POINTER(C.c_int32)), ("cand_mod", C.POINTER(C.c_double)),
                 ("cand_ncut", C.POINTER(C.c_double)), ("cand_passes", C.POINTER(C.c_int32))]
+
+
+class ProfEntry(C.Structure):
+    _fields_ = [("name", C.c_char_p), ("launches", C.c_int64), ("timed", C.c_int64), ("ms", C.c_double)]
 
 
 class RaftgpError(RuntimeError):
@@ -80,6 +85,10 @@ def lib():
         for name in ("raftgp_embed", "raftgp_select", "raftgp_partition", "raftgp_score", "raftgp_kmeanspp",
                      "raftgp_lloyd"):
             getattr(L, name).restype = C.c_int
+        L.raftgp_profile_enable.restype = C.c_int
+        L.raftgp_profile_enable.argtypes = [C.c_int32]
+        L.raftgp_profile_read.restype = C.c_int32
+        L.raftgp_profile_read.argtypes = [C.POINTER(ProfEntry), C.c_int32]
         L.raftgp_last_error.restype = C.c_char_p
         L.raftgp_last_error.argtypes = []
         L.raftgp_version.restype = C.c_char_p

@@ -220,5 +220,18 @@ def lloyd(Z: torch.Tensor, mu0: torch.Tensor, iters=50, assign="ffma", stream=No
     return labels, mu, passes.value
 
 
+def profile_enable(on: bool = True) -> None:
+    """Start (clearing the counters) or stop per-kernel-family event timing in the library."""
+    check(lib().raftgp_profile_enable(1 if on else 0))
+
+
+def profile_read() -> dict:
+    """{family: {"launches", "timed", "ms"}} since the last profile_enable(True)."""
+    buf = (_abi.ProfEntry * 32)()
+    k = lib().raftgp_profile_read(buf, 32)
+    return {buf[i].name.decode(): {"launches": buf[i].launches, "timed": buf[i].timed, "ms": buf[i].ms}
+            for i in range(k)}
+
+
 def version() -> str:
     return lib().raftgp_version().decode()

@@ -322,6 +322,7 @@ void launch_degrees(const raftgp_csr* g, int32_t* deg, float* rs, float* rsh, ui
     const int threads = 256;
     int64_t blocks = (g->n * 32 + threads - 1) / threads;
     blocks = blocks < 1 ? 1 : (blocks > (int64_t)num_sms() * 16 ? (int64_t)num_sms() * 16 : blocks);
+    ProfScope ps(s, PF_DEGREES, 1);
     k_degrees<<<(unsigned)blocks, threads, 0, s>>>(
         g->n, g->nnz, g->row_ptr_bits == 32 ? (const int32_t*)g->row_ptr : nullptr,
         g->row_ptr_bits == 64 ? (const int64_t*)g->row_ptr : nullptr, g->col, deg, rs, rsh, err);
@@ -338,6 +339,7 @@ void launch_theta(int64_t n, int L, int dtype, uint64_t seed, const float* user_
     const int threads = 256;
     const int blocks = theta_blocks(n);
     const size_t sm = partial ? (size_t)(threads / (L / 4)) * L * sizeof(float) : 0;
+    ProfScope ps(s, PF_THETA, partial ? 2 : 1);
     if (dtype == RAFTGP_BF16)
         k_theta<__nv_bfloat16><<<blocks, threads, sm, s>>>(n, L, seed, user_theta, colscale, deg,
                                                            (__nv_bfloat16*)theta, partial);
@@ -348,6 +350,7 @@ void launch_theta(int64_t n, int L, int dtype, uint64_t seed, const float* user_
 
 void launch_weights(int layer, int lin, int lout, uint64_t seed, float* W, cudaStream_t s) {
     const int total = lin * (lout / 4);
+    ProfScope ps(s, PF_OTHER, 1);
     k_weights<<<(total + 255) / 256, 256, 0, s>>>(layer, lin, lout, seed, W);
 }
 
@@ -367,6 +370,7 @@ static cudaError_t launch_layer_t(const LayerArgs& a, const void* X, cudaStream_
     const int64_t cap = (int64_t)num_sms() * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
+    ProfScope ps(s, AGG == AGG_GCN ? PF_SPMM_GCN : PF_SPMM_PROJ, 1);
     kern<<<(unsigned)blocks, threads, smem, s>>>(a, reinterpret_cast<const T*>(X));
     return cudaGetLastError();
 }

@@ -10,6 +10,22 @@ namespace raftgp {
 
 int num_sms();
 
+// ---- instrumentation (prof.cu) ---------------------------------------------------------
+enum ProfFamily {
+    PF_DEGREES, PF_THETA, PF_SPMM_PROJ, PF_SPMM_GCN, PF_SEED_UPDATE, PF_SEED_PICK, PF_BATCH_INIT, PF_ASSIGN_FFMA,
+    PF_ASSIGN_TC, PF_RECHECK, PF_LLOYD_UPDATE, PF_SCORE, PF_SELECT_BEST, PF_OTHER, PF_COUNT
+};
+// Brackets the kernels launched in its lifetime with CUDA events when profiling is on.
+class ProfScope {
+  public:
+    ProfScope(cudaStream_t s, int fam, int kernels);
+    ~ProfScope();
+  private:
+    cudaStream_t s_;
+    int fam_, kernels_;
+    long long pair_;
+};
+
 // ---- embedding (embed.cu) -----------------------------------------------------------
 enum { AGG_NCUT_ = 0, AGG_MOD_FULL_ = 1, AGG_MOD_REDUCED_ = 2, AGG_GCN_ = 3 };
 void launch_degrees(const raftgp_csr* g, int32_t* deg, float* rs, float* rsh, uint32_t* err, cudaStream_t s);

@@ -187,16 +187,22 @@ __global__ void __launch_bounds__(1024) k_seed_pick(int64_t n, int nblocks, cons
 int seed_nblocks(int64_t n) { return (int)((n + SEED_THREADS - 1) / SEED_THREADS); }
 
 void launch_seed_first(int64_t n, uint64_t seed, int32_t* seeds, uint8_t* chosen, cudaStream_t s) {
+    ProfScope ps(s, PF_SEED_PICK, 1);
     k_seed_first<<<1, 1, 0, s>>>(n, seed, seeds, chosen);
 }
 
 void launch_seed_round(const void* Z, int zdtype, int64_t n, int d, int t, uint64_t seed, int32_t* seeds,
                        uint8_t* chosen, float* D2, unsigned long long* blocksum, cudaStream_t s) {
     const int nb = seed_nblocks(n);
-    if (zdtype == RAFTGP_BF16)
-        k_seed_update<__nv_bfloat16><<<nb, SEED_THREADS, 0, s>>>((const __nv_bfloat16*)Z, n, d, t, seeds, D2, blocksum);
-    else
-        k_seed_update<float><<<nb, SEED_THREADS, 0, s>>>((const float*)Z, n, d, t, seeds, D2, blocksum);
+    {
+        ProfScope ps(s, PF_SEED_UPDATE, 1);
+        if (zdtype == RAFTGP_BF16)
+            k_seed_update<__nv_bfloat16><<<nb, SEED_THREADS, 0, s>>>((const __nv_bfloat16*)Z, n, d, t, seeds, D2,
+                                                                     blocksum);
+        else
+            k_seed_update<float><<<nb, SEED_THREADS, 0, s>>>((const float*)Z, n, d, t, seeds, D2, blocksum);
+    }
+    ProfScope ps(s, PF_SEED_PICK, 1);
     k_seed_pick<<<1, 1024, 0, s>>>(n, nb, blocksum, D2, seed, t, seeds, chosen);
 }
 
@@ -243,6 +249,7 @@ __global__ void k_fill_labels(int16_t* labels, int64_t count) {
 
 void launch_batch_init(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, const int32_t* seeds,
                        const float* mu0, KmState st, cudaStream_t s) {
+    ProfScope ps(s, PF_BATCH_INIT, 3);
     dim3 grid(64, b.n);
     if (zdtype == RAFTGP_BF16)
         k_batch_init_mu<__nv_bfloat16><<<grid, 128, 0, s>>>(b, (const __nv_bfloat16*)Z, d, seeds, mu0, st);
@@ -379,6 +386,7 @@ static cudaError_t launch_assign_t(const CandBatch& b, const T* Z, int64_t n, Km
         if (e != cudaSuccess) return e;
     }
     dim3 grid((unsigned)((n + AS_TP - 1) / AS_TP), b.n);
+    ProfScope ps(s, PF_ASSIGN_FFMA, 1);
     kern<<<grid, 256, smem, s>>>(b, Z, n, st, pass);
     return cudaGetLastError();
 }
@@ -437,6 +445,7 @@ __global__ void k_lloyd_update(CandBatch b, int d, KmState st, int pass) {
 
 void launch_lloyd_update(const CandBatch& b, int d, KmState st, int pass, cudaStream_t s) {
     dim3 grid(8, b.n);
+    ProfScope ps(s, PF_LLOYD_UPDATE, 1);
     k_lloyd_update<<<grid, 128, 0, s>>>(b, d, st, pass);
 }
 

@@ -120,6 +120,7 @@ __global__ void k_copy_best(const BestState* best, const int16_t* labels, int cs
 void launch_score_batch(const CandBatch& b, const raftgp_csr* g, const int32_t* deg, const int16_t* labels,
                         ScoreOut so, uint32_t* err, cudaStream_t s) {
     (void)err;
+    ProfScope ps(s, PF_SCORE, 2);
     cudaMemsetAsync(so.m, 0, sizeof(long long) * (size_t)b.total_k, s);
     cudaMemsetAsync(so.vol, 0, sizeof(long long) * (size_t)b.total_k, s);
     int64_t blocks = (g->n * 32 + 255) / 256;
@@ -134,6 +135,7 @@ void launch_score_batch(const CandBatch& b, const raftgp_csr* g, const int32_t* 
 
 void launch_select_best(const CandBatch& b, ScoreOut so, int criterion, BestState* best, const int16_t* labels,
                         int64_t n, int32_t* out_labels, cudaStream_t s) {
+    ProfScope ps(s, PF_SELECT_BEST, 2);
     k_select_best<<<1, 32, 0, s>>>(b, so, criterion, best);
     int blocks = (int)((n + 255) / 256);
     if (blocks > num_sms() * 8) blocks = num_sms() * 8;
@@ -189,6 +191,7 @@ __global__ void k_score_one_finalize(const long long* m, const long long* vol, i
 
 cudaError_t launch_score_labels(const raftgp_csr* g, const int32_t* deg, const int32_t* labels, int K, long long* m,
                                 long long* vol, double* out2, uint32_t* err, cudaStream_t s) {
+    ProfScope ps(s, PF_SCORE, 3);
     cudaMemsetAsync(m, 0, sizeof(long long) * (size_t)K, s);
     cudaMemsetAsync(vol, 0, sizeof(long long) * (size_t)K, s);
     int64_t blocks = (g->n * 32 + 255) / 256;
