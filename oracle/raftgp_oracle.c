@@ -430,7 +430,8 @@ int orc_kmeanspp(const double* Z, int64_t n, int d, int K, uint64_t seed, int fp
 /* Lloyd's iterations from the given centroids mu (K x d, updated in place).  Each pass
  * assigns every point to its nearest centroid (ties to the lowest index); the pass stops
  * the loop if no label changed, otherwise every non-empty cluster's centroid becomes the
- * mean of its points (an empty cluster keeps its centroid).  At most T passes.
+ * mean of its points (an empty cluster keeps its centroid).  At most T passes; after the T-th
+ * the centroids are left as they were, so mu holds the centroids of the final assignment.
  * Returns the number of assignment passes in *passes; labels get the last assignment.
  * If `objective` is not NULL, objective[p] = sum_i ||z_i - mu_{label_i}||^2 of pass p. */
 int orc_lloyd(const double* Z, int64_t n, int d, int K, double* mu, int T, int32_t* labels, int* passes,
@@ -457,6 +458,7 @@ int orc_lloyd(const double* Z, int64_t n, int d, int K, double* mu, int T, int32
         if (objective) objective[p - 1] = obj;
         if (changed == 0) break;
         for (int64_t i = 0; i < n; ++i) labels[i] = nl[i];
+        if (p == T) break;   /* the returned centroids are those the final labels were assigned against */
         for (int c = 0; c < K; ++c) {
             int64_t cnt = 0;
             for (int k = 0; k < d; ++k) sum[k] = 0.0;

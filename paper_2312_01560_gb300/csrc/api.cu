@@ -79,7 +79,6 @@ static raftgp_status check_select(const raftgp_select_opts* o, int64_t n) {
     if (o->criterion != RAFTGP_CRIT_MOD && o->criterion != RAFTGP_CRIT_NCUT) return fail(RAFTGP_EINVAL, "unknown criterion");
     if (o->assign != RAFTGP_ASSIGN_FFMA && o->assign != RAFTGP_ASSIGN_TC) return fail(RAFTGP_EINVAL, "unknown assign engine");
     if (o->batch < 0) return fail(RAFTGP_EINVAL, "batch < 0");
-    if (o->assign == RAFTGP_ASSIGN_TC) return fail(RAFTGP_EUNSUPPORTED, "tensor-core assignment is not built yet");
     return RAFTGP_OK;
 }
 
@@ -132,9 +131,28 @@ struct SelectWs {
     KmState km;
     ScoreOut so;
     BestState* best;
+    int2* recheck;
+    int* recheck_count;
     int cmax;   // candidates per batch
     int kcap;   // centroids per batch
 };
+
+static int64_t kpad_of(int64_t k) { return (k + 255) / 256 * 256; }
+
+static void carve_km(Carver& c, KmState& km, int64_t kcap, int d, int64_t n, int cs) {
+    const int64_t kp = kpad_of(kcap);
+    km.mu = c.take<float>((size_t)kp * d);
+    km.norm2 = c.take<float>(kp + 64);
+    km.sums = c.take<long long>((size_t)kcap * d);
+    km.counts = c.take<int32_t>(kcap);
+    km.labels = c.take<int16_t>((size_t)n * cs);
+    km.active = c.take<int32_t>(MAXC);
+    km.changed = c.take<int32_t>(2 * MAXC);
+    km.passes = c.take<int32_t>(MAXC);
+    km.bhi = c.take<__nv_bfloat16>((size_t)kp * d);
+    km.blo = c.take<__nv_bfloat16>((size_t)kp * d);
+    km.bhi_rows = kp;
+}
 
 static int batch_cap(const raftgp_select_opts* o, int kmax) {
     int span = o->grid > 0 ? o->grid : (kmax - o->kmin + 1);
@@ -160,14 +178,9 @@ static SelectWs carve_select(Carver& c, int64_t n, int d, const raftgp_select_op
     w.cmax = batch_cap(o, kmax);
     w.kcap = w.cmax * kmax;
     const int cs = (w.cmax + 7) / 8 * 8;
-    w.km.mu = c.take<float>((size_t)w.kcap * d);
-    w.km.norm2 = c.take<float>(w.kcap);
-    w.km.sums = c.take<long long>((size_t)w.kcap * d);
-    w.km.counts = c.take<int32_t>(w.kcap);
-    w.km.labels = c.take<int16_t>((size_t)n * cs);
-    w.km.active = c.take<int32_t>(MAXC);
-    w.km.changed = c.take<int32_t>(2 * MAXC);
-    w.km.passes = c.take<int32_t>(MAXC);
+    carve_km(c, w.km, w.kcap, d, n, cs);
+    w.recheck = c.take<int2>((size_t)n * w.cmax);
+    w.recheck_count = c.take<int>(64);
     w.so.m = c.take<long long>(w.kcap);
     w.so.vol = c.take<long long>(w.kcap);
     w.so.mod = c.take<double>(MAXC);
@@ -281,6 +294,26 @@ static bool host_better(int criterion, const CandRecord& a, const CandRecord& b)
     return a.k < b.k;
 }
 
+// Lloyd passes for one batch.  Tensor-core engine: FAST passes, then one FINAL assignment
+// with the FP32 re-check of near ties (the reported labels).
+static raftgp_status run_lloyd(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, int iters, int engine,
+                               KmState km, int2* recheck, int* recheck_count, uint32_t* err, cudaStream_t s) {
+    for (int pass = 1; pass <= iters; ++pass) {
+        cudaError_t e = engine == RAFTGP_ASSIGN_TC
+                            ? launch_assign_tc(b, Z, n, d, km, pass, 0, nullptr, nullptr, err, s)
+                            : launch_assign_ffma(b, Z, zdtype, n, d, km, pass, s);
+        if (e != cudaSuccess) return cuda_fail(e, "assign");
+        launch_lloyd_update(b, d, km, pass, iters, s);
+    }
+    if (engine == RAFTGP_ASSIGN_TC) {
+        cudaMemsetAsync(recheck_count, 0, sizeof(int), s);
+        cudaError_t e = launch_assign_tc(b, Z, n, d, km, iters + 1, 1, recheck, recheck_count, err, s);
+        if (e != cudaSuccess) return cuda_fail(e, "final assign");
+        launch_recheck(b, Z, d, km, recheck, recheck_count, s);
+    }
+    return RAFTGP_OK;
+}
+
 // Evaluate a list of candidates in batches; appends their records.
 static raftgp_status run_candidates(const raftgp_csr* g, const void* Z, int d, int zdtype,
                                     const raftgp_select_opts* o, const std::vector<int>& ks, const SelectWs& w,
@@ -298,11 +331,8 @@ static raftgp_status run_candidates(const raftgp_csr* g, const void* Z, int d, i
         }
         b.total_k = off;
         launch_batch_init(b, Z, zdtype, n, d, w.seeds, nullptr, w.km, s);
-        for (int pass = 1; pass <= o->iters; ++pass) {
-            cudaError_t e = launch_assign_ffma(b, Z, zdtype, n, d, w.km, pass, s);
-            if (e != cudaSuccess) return cuda_fail(e, "assign");
-            launch_lloyd_update(b, d, w.km, pass, s);
-        }
+        raftgp_status st = run_lloyd(b, Z, zdtype, n, d, o->iters, o->assign, w.km, w.recheck, w.recheck_count, w.err, s);
+        if (st != RAFTGP_OK) return st;
         launch_score_batch(b, g, w.deg, w.km.labels, w.so, w.err, s);
         launch_select_best(b, w.so, o->criterion, w.best, w.km.labels, n, labels, s);
         double hm[MAXC], hn[MAXC];
@@ -446,6 +476,8 @@ raftgp_status raftgp_select(const raftgp_csr* g, const void* Z, int32_t d, int32
     if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d = %d: must be 32, 64 or 128", d);
     if (z_dtype != RAFTGP_F32 && z_dtype != RAFTGP_BF16) return fail(RAFTGP_EINVAL, "unknown z_dtype");
     if (!Z || !labels || !ws) return fail(RAFTGP_EINVAL, "Z, labels or workspace is NULL");
+    if (sopts->assign == RAFTGP_ASSIGN_TC && z_dtype != RAFTGP_BF16)
+        return fail(RAFTGP_EINVAL, "tensor-core assignment needs BF16 embeddings");
     if (ws_bytes < raftgp_workspace_size(g, nullptr, sopts, d)) return fail(RAFTGP_ENOMEM, "workspace too small");
     cudaStream_t s = (cudaStream_t)stream;
     Carver c(ws);
@@ -465,6 +497,8 @@ raftgp_status raftgp_partition(const raftgp_csr* g, const raftgp_embed_opts* eop
     if ((st = check_embed(eopts))) return st;
     if ((st = check_select(sopts, g->n))) return st;
     if (!labels || !ws) return fail(RAFTGP_EINVAL, "labels or workspace is NULL");
+    if (sopts->assign == RAFTGP_ASSIGN_TC && eopts->dtype != RAFTGP_BF16)
+        return fail(RAFTGP_EINVAL, "tensor-core assignment needs BF16 embeddings");
     if (ws_bytes < raftgp_workspace_size(g, eopts, sopts, 0)) return fail(RAFTGP_ENOMEM, "workspace too small");
     cudaStream_t s = (cudaStream_t)stream;
     const int d = eopts->dims[eopts->n_layers];
@@ -546,17 +580,14 @@ raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype,
     if (K < 1 || K > 32767) return fail(RAFTGP_EINVAL, "need 1 <= K <= 32767");
     if (iters < 1) return fail(RAFTGP_EINVAL, "iters must be >= 1");
     if (assign != RAFTGP_ASSIGN_FFMA && assign != RAFTGP_ASSIGN_TC) return fail(RAFTGP_EINVAL, "unknown assign engine");
-    if (assign == RAFTGP_ASSIGN_TC) return fail(RAFTGP_EUNSUPPORTED, "tensor-core assignment is not built yet");
+    if (assign == RAFTGP_ASSIGN_TC && z_dtype != RAFTGP_BF16)
+        return fail(RAFTGP_EINVAL, "tensor-core assignment needs BF16 embeddings");
     Carver c(ws);
     KmState km{};
-    km.mu = c.take<float>((size_t)K * d);
-    km.norm2 = c.take<float>(K);
-    km.sums = c.take<long long>((size_t)K * d);
-    km.counts = c.take<int32_t>(K);
-    km.labels = c.take<int16_t>((size_t)n * 8);
-    km.active = c.take<int32_t>(MAXC);
-    km.changed = c.take<int32_t>(2 * MAXC);
-    km.passes = c.take<int32_t>(MAXC);
+    carve_km(c, km, K, d, n, 8);
+    uint32_t* err = c.take<uint32_t>(64);
+    int2* recheck = c.take<int2>((size_t)n);
+    int* recheck_count = c.take<int>(64);
     if (ws_bytes < c.off) return fail(RAFTGP_ENOMEM, "workspace too small");
     cudaStream_t s = (cudaStream_t)stream;
     CandBatch b{};
@@ -565,12 +596,10 @@ raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype,
     b.k[0] = K;
     b.off[0] = 0;
     b.total_k = K;
+    cudaMemsetAsync(err, 0, sizeof(uint32_t), s);
     launch_batch_init(b, Z, z_dtype, n, d, nullptr, mu0, km, s);
-    for (int pass = 1; pass <= iters; ++pass) {
-        cudaError_t e = launch_assign_ffma(b, Z, z_dtype, n, d, km, pass, s);
-        if (e != cudaSuccess) return cuda_fail(e, "assign");
-        launch_lloyd_update(b, d, km, pass, s);
-    }
+    raftgp_status st = run_lloyd(b, Z, z_dtype, n, d, iters, assign, km, recheck, recheck_count, err, s);
+    if (st != RAFTGP_OK) return st;
     int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8);
     ProfScope ps(s, PF_OTHER, 1);
     k_labels_out<<<std::max(blocks, 1), 256, 0, s>>>(km.labels, 8, n, labels);
@@ -579,6 +608,8 @@ raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype,
     cudaMemcpyAsync(&hp, km.passes, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "lloyd");
+    st = read_error_word(err, s);
+    if (st != RAFTGP_OK) return st;
     if (passes) *passes = hp;
     return RAFTGP_OK;
 }

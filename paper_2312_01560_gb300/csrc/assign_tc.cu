@@ -1,0 +1,542 @@
+// assign_tc.cu -- k-means assignment on the 5th-generation tensor cores (sm_103a).
+//
+// For a tile of 128 points and a chunk of NCH centroids the distance GEMM
+//     D[p][c] = z_p . mu_c
+// runs as tcgen05.mma (kind::f16, BF16 operands, FP32 accumulator in tensor memory).  The
+// centroids are split into two BF16 halves, mu = hi + lo (lo = the rounded residual), and
+// both halves are multiplied into the same accumulator, so the dot product carries about 16
+// significant bits of mu instead of 8.  The epilogue reads the accumulator with tcgen05.ld
+// (thread t owns TMEM lane t = point t) and keeps, per candidate K, the argmin of
+//     ||mu_c||^2 - 2 D[p][c]        (= ||z_p - mu_c||^2 - ||z_p||^2, ties to the lowest c).
+//
+// Warp roles in a persistent CTA (one per SM): warp 0 issues TMA loads (the point tile once
+// per tile, centroid chunks through a STAGES-deep ring), warp 1 allocates tensor memory and
+// issues the MMAs into two accumulator buffers, warps 2-5 are the epilogue.  Every mbarrier
+// wait is bounded: on timeout the CTA raises an abort flag, records DERR_TIMEOUT, drains its
+// in-flight copies and MMAs (again bounded), frees its tensor memory and returns.
+//
+// Modes: FAST (Lloyd passes) writes labels, counts changes and applies each change to the
+// 2^-40 fixed-point centroid sums; FINAL (the assignment whose labels are reported) also
+// tracks the second-best score and lists every (point, candidate) whose best two scores lie
+// within the error band of the BF16 product, for an exact FP32 re-check.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace raftgp {
+
+template <int D>
+struct TcCfg {
+    static constexpr int ATOM = D < 64 ? D : 64;          // K elements per swizzle-atom row
+    static constexpr int ATOM_BYTES = ATOM * 2;           // 64 or 128
+    static constexpr int NATOM = D / ATOM;
+    static constexpr int NCH = D == 128 ? 128 : 256;      // centroids per chunk = MMA N
+    static constexpr int STAGES = D == 128 ? 2 : (D == 64 ? 3 : 4);
+    static constexpr int A_ATOM_BYTES = 128 * ATOM_BYTES;
+    static constexpr int A_BYTES = NATOM * A_ATOM_BYTES;
+    static constexpr int B_ATOM_BYTES = NCH * ATOM_BYTES;
+    static constexpr int B_BYTES = NATOM * B_ATOM_BYTES;  // one half (hi or lo) of a chunk
+    static constexpr int STAGE_BYTES = 2 * B_BYTES;
+    static constexpr int LAYOUT = ATOM_BYTES == 128 ? 2 : 4;  // descriptor swizzle: 128B or 64B
+    static constexpr int SBO = 8 * ATOM_BYTES;                 // stride between 8-row groups
+    static constexpr int SMEM = 1024 + A_BYTES + STAGES * STAGE_BYTES;
+};
+
+constexpr int TC_MAX_CHUNKS = 512;
+constexpr int TC_THREADS = 192;
+
+struct TcCtl {
+    uint64_t a_full, a_empty;
+    uint64_t b_full[4], b_empty[4];
+    uint64_t acc_full[2], acc_empty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+    int nchunks;
+    int chunk_col[TC_MAX_CHUNKS];
+};
+
+// ---------------------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait: false when the CTA aborted (another wait timed out) or this one timed out.
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;  // 2 s
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, TcCtl* ctl, uint32_t* err) {
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if (*(volatile int*)&ctl->abort) return false;
+        if ((it & 255) == 255 && global_ns() - t0 > TC_WAIT_NS) {
+            *(volatile int*)&ctl->abort = 1;
+            atomicOr(err, DERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+// Drain wait used on the exit path: bounded, ignores the abort flag.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity) {
+    const uint64_t t0 = global_ns();
+    while (!mbar_test(bar, parity) && global_ns() - t0 < TC_WAIT_NS) {
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_addr(dst)),
+        "l"(map), "r"(smem_addr(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, int layout, int sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;                                   // leading byte offset (unused, swizzled K-major)
+    d |= (uint64_t)((uint32_t)(sbo >> 4) & 0x3FFFu) << 32;   // stride byte offset
+    d |= (uint64_t)1 << 46;                                   // descriptor version
+    d |= (uint64_t)layout << 61;                              // swizzle mode
+    return d;
+}
+
+// kind::f16 instruction descriptor: D=F32, A=B=BF16, both K-major, M=128, N=n.
+__device__ __forceinline__ uint32_t instr_desc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------------------
+// The kernel
+// ---------------------------------------------------------------------------------------
+struct TcArgs {
+    CandBatch b;
+    int64_t n;
+    const __nv_bfloat16* Z;   // N x D
+    KmState st;
+    int pass;                 // FAST: pass number (parity selects the change counter)
+    int final_mode;           // 1 = FINAL
+    float tie_band;           // FINAL: second-best within this band -> re-check
+    int2* recheck;            // FINAL: list of (point, candidate)
+    int* recheck_count;
+    uint32_t* err;
+};
+
+template <int D>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_assign_tc(const __grid_constant__ TcArgs a, const __grid_constant__ CUtensorMap tmA,
+                const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo) {
+    using C = TcCfg<D>;
+    extern __shared__ uint8_t dyn_smem[];
+    __shared__ TcCtl ctl;
+    uint8_t* base = (uint8_t*)(((uintptr_t)dyn_smem + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = base;
+    uint8_t* sB = base + C::A_BYTES;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const CandBatch& b = a.b;
+
+    if (threadIdx.x == 0) {
+        ctl.abort = 0;
+        mbar_init(&ctl.a_full, 1);
+        mbar_init(&ctl.a_empty, 1);
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(&ctl.b_full[s], 1);
+            mbar_init(&ctl.b_empty[s], 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&ctl.acc_full[q], 1);
+            mbar_init(&ctl.acc_empty[q], 128);
+        }
+        mbar_init(&ctl.drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // chunks of the concatenated centroid list that hold at least one column of an
+        // active candidate (FINAL: every candidate)
+        int nch = 0;
+        const int total_chunks = (b.total_k + C::NCH - 1) / C::NCH;
+        for (int q = 0; q < total_chunks && nch < TC_MAX_CHUNKS; ++q) {
+            const int lo = q * C::NCH, hi = lo + C::NCH;
+            bool need = false;
+            for (int c = 0; c < b.n && !need; ++c)
+                need = (a.final_mode || a.st.active[c]) && b.off[c] < hi && b.off[c] + b.k[c] > lo;
+            if (need) ctl.chunk_col[nch++] = lo;
+        }
+        ctl.nchunks = nch;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_addr(&ctl.tmem_base)));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = ctl.tmem_base;
+    const int nchunks = ctl.nchunks;
+    const int64_t ntiles = (a.n + 127) / 128;
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0 && nchunks > 0) {
+            int it = 0, tl = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tl) {
+                if (!(ok = mbar_wait(&ctl.a_empty, (tl & 1) ^ 1, &ctl, a.err))) break;
+                mbar_expect_tx(&ctl.a_full, C::A_BYTES);
+                for (int t = 0; t < C::NATOM; ++t)
+                    tma_load_2d(sA + t * C::A_ATOM_BYTES, &tmA, &ctl.a_full, t * C::ATOM, (int)(tile * 128));
+                for (int q = 0; q < nchunks; ++q, ++it) {
+                    const int s = it % C::STAGES;
+                    if (!(ok = mbar_wait(&ctl.b_empty[s], ((it / C::STAGES) & 1) ^ 1, &ctl, a.err))) break;
+                    uint8_t* dst = sB + s * C::STAGE_BYTES;
+                    mbar_expect_tx(&ctl.b_full[s], C::STAGE_BYTES);
+                    for (int t = 0; t < C::NATOM; ++t) {
+                        tma_load_2d(dst + t * C::B_ATOM_BYTES, &tmBhi, &ctl.b_full[s], t * C::ATOM, ctl.chunk_col[q]);
+                        tma_load_2d(dst + C::B_BYTES + t * C::B_ATOM_BYTES, &tmBlo, &ctl.b_full[s], t * C::ATOM,
+                                    ctl.chunk_col[q]);
+                    }
+                }
+            }
+            if (!ok) {
+                // let the copies already issued land before the CTA can exit
+                const int last = it;
+                for (int k = (last > C::STAGES ? last - C::STAGES : 0); k < last; ++k)
+                    mbar_drain(&ctl.b_full[k % C::STAGES], (k / C::STAGES) & 1);
+                mbar_drain(&ctl.a_full, (tl & 1));
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0 && nchunks > 0) {
+            const uint32_t idesc = instr_desc(C::NCH);
+            int it = 0, tl = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tl) {
+                if (!(ok = mbar_wait(&ctl.a_full, tl & 1, &ctl, a.err))) break;
+                tc_fence_after();
+                for (int q = 0; q < nchunks; ++q, ++it) {
+                    const int s = it % C::STAGES;
+                    const int buf = it & 1;
+                    if (!(ok = mbar_wait(&ctl.b_full[s], (it / C::STAGES) & 1, &ctl, a.err))) break;
+                    if (!(ok = mbar_wait(&ctl.acc_empty[buf], ((it >> 1) & 1) ^ 1, &ctl, a.err))) break;
+                    tc_fence_after();
+                    const uint32_t dcol = tmem + (uint32_t)(buf * C::NCH);
+                    const uint32_t bhi = smem_addr(sB + s * C::STAGE_BYTES);
+                    const uint32_t blo = bhi + C::B_BYTES;
+                    const uint32_t a0 = smem_addr(sA);
+                    int first = 1;
+                    for (int half = 0; half < 2; ++half) {
+                        const uint32_t bb = half ? blo : bhi;
+                        for (int t = 0; t < C::NATOM; ++t)
+                            for (int k = 0; k < C::ATOM / 16; ++k) {
+                                const uint64_t ad = smem_desc(a0 + t * C::A_ATOM_BYTES + k * 32, C::LAYOUT, C::SBO);
+                                const uint64_t bd = smem_desc(bb + t * C::B_ATOM_BYTES + k * 32, C::LAYOUT, C::SBO);
+                                mma_bf16(dcol, ad, bd, idesc, first ? 0 : 1);
+                                first = 0;
+                            }
+                    }
+                    mma_commit(&ctl.b_empty[s]);        // the stage is free once these MMAs retire
+                    mma_commit(&ctl.acc_full[buf]);     // the accumulator is ready for the epilogue
+                }
+                if (ok) mma_commit(&ctl.a_empty);       // the point tile is free after its last chunk
+            }
+            // wait for every MMA issued by this thread before tensor memory is released
+            mma_commit(&ctl.drain);
+            mbar_drain(&ctl.drain, 0);
+        }
+    } else {
+        // ---------------- epilogue (warps 2..5) ----------------
+        const int quarter = warp & 3;                 // TMEM lanes this warp may access
+        const int row = quarter * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+        int it = 0;
+        bool ok = nchunks > 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const int64_t i = tile * 128 + row;
+            const bool valid = i < a.n;
+            int seg = 0;                              // candidate whose columns come next
+            float bv = INFINITY, b2 = INFINITY;
+            int bi = -1;
+            for (int q = 0; q < nchunks; ++q, ++it) {
+                const int buf = it & 1;
+                if (!(ok = mbar_wait(&ctl.acc_full[buf], (it >> 1) & 1, &ctl, a.err))) break;
+                tc_fence_after();
+                const int chunk0 = ctl.chunk_col[q];
+                for (int sl = 0; sl < C::NCH / 32; ++sl) {
+                    const int col0 = chunk0 + sl * 32;
+                    if (col0 >= b.total_k) break;
+                    uint32_t r[32];
+                    tmem_ld32(lane_base + (uint32_t)(buf * C::NCH + sl * 32), r);
+                    float nrm[32];
+#pragma unroll
+                    for (int v = 0; v < 8; ++v) {
+                        const float4 t4 = __ldg(reinterpret_cast<const float4*>(a.st.norm2 + col0) + v);
+                        nrm[4 * v] = t4.x; nrm[4 * v + 1] = t4.y; nrm[4 * v + 2] = t4.z; nrm[4 * v + 3] = t4.w;
+                    }
+                    int c_lo = col0;
+                    const int c_hi = min(col0 + 32, b.total_k);
+                    while (c_lo < c_hi) {
+                        const int seg_end = b.off[seg] + b.k[seg];
+                        if (c_lo >= seg_end) {
+                            // candidate `seg` complete for this tile
+                            ++seg;
+                            continue;
+                        }
+                        const int run_end = min(c_hi, seg_end);
+                        const bool act = a.final_mode || a.st.active[seg];
+                        if (act) {
+                            const int r_lo = c_lo - col0, r_hi = run_end - col0;
+                            if (r_lo == 0 && r_hi == 32) {
+#pragma unroll
+                                for (int k = 0; k < 32; ++k) {
+                                    const float s = fmaf(-2.0f, __uint_as_float(r[k]), nrm[k]);
+                                    if (a.final_mode) {
+                                        if (s < bv) { b2 = bv; bv = s; bi = col0 + k; } else { b2 = fminf(b2, s); }
+                                    } else if (s < bv) { bv = s; bi = col0 + k; }
+                                }
+                            } else {
+#pragma unroll
+                                for (int k = 0; k < 32; ++k) {
+                                    if (k < r_lo || k >= r_hi) continue;
+                                    const float s = fmaf(-2.0f, __uint_as_float(r[k]), nrm[k]);
+                                    if (a.final_mode) {
+                                        if (s < bv) { b2 = bv; bv = s; bi = col0 + k; } else { b2 = fminf(b2, s); }
+                                    } else if (s < bv) { bv = s; bi = col0 + k; }
+                                }
+                            }
+                        }
+                        if (run_end == seg_end && act) {
+                            // ---- candidate `seg` finished for this tile: label, change, sums ----
+                            const int K = b.k[seg], off = b.off[seg];
+                            int nl = bi - off;
+                            if (nl < 0 || nl >= K) nl = 0;   // non-finite scores: keep indices in range
+                            int ol = -1;
+                            if (valid) {
+                                int16_t* lp = a.st.labels + i * b.cs + seg;
+                                ol = *lp;
+                                *lp = (int16_t)nl;
+                            }
+                            if (a.final_mode) {
+                                if (valid && !(b2 - bv > a.tie_band)) {
+                                    const int slot = atomicAdd(a.recheck_count, 1);
+                                    a.recheck[slot] = make_int2((int)i, seg);
+                                }
+                            } else {
+                                const bool ch = valid && nl != ol;
+                                unsigned mask = __ballot_sync(0xffffffffu, ch);
+                                if (lane == 0 && mask) atomicAdd(a.st.changed + (a.pass & 1) * MAXC + seg, __popc(mask));
+                                if (ch) {
+                                    atomicAdd(a.st.counts + off + nl, 1);
+                                    if (ol >= 0) atomicSub(a.st.counts + off + ol, 1);
+                                }
+                                while (mask) {
+                                    const int src = __ffs(mask) - 1;
+                                    mask &= mask - 1;
+                                    const int64_t pi = __shfl_sync(0xffffffffu, i, src);
+                                    const int pn = __shfl_sync(0xffffffffu, nl, src);
+                                    const int po = __shfl_sync(0xffffffffu, ol, src);
+                                    for (int k = lane; k < D; k += 32) {
+                                        const long long v =
+                                            __float2ll_rn(__bfloat162float(a.Z[pi * D + k]) * FIXED_SCALE_F);
+                                        atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + pn) * D + k),
+                                                  (unsigned long long)v);
+                                        if (po >= 0)
+                                            atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + po) * D + k),
+                                                      (unsigned long long)(-v));
+                                    }
+                                }
+                            }
+                            bv = INFINITY;
+                            b2 = INFINITY;
+                            bi = -1;
+                        }
+                        c_lo = run_end;
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&ctl.acc_empty[buf]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+}
+
+// FP32 direct-form re-check of the listed (point, candidate) pairs: one warp per pair, lanes
+// split the candidate's centroids, ascending coordinates per distance, ties to the lowest index.
+template <int D>
+__global__ void __launch_bounds__(256) k_recheck(CandBatch b, const __nv_bfloat16* __restrict__ Z, KmState st,
+                                                 const int2* list, const int* count) {
+    const int lane = threadIdx.x & 31;
+    const int total = *count;
+    for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < total; e += (gridDim.x * blockDim.x) >> 5) {
+        const int2 pc = list[e];
+        const int64_t i = pc.x;
+        const int c = pc.y;
+        float z[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) z[k] = __bfloat162float(Z[i * D + k]);
+        const int K = b.k[c], off = b.off[c];
+        float bv = INFINITY;
+        int bi = 0x7fffffff;
+        for (int j = lane; j < K; j += 32) {
+            const float* mu = st.mu + (int64_t)(off + j) * D;
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const float t = __fsub_rn(z[k], mu[k]);
+                s = __fadd_rn(s, __fmul_rn(t, t));
+            }
+            if (s < bv) { bv = s; bi = j; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov < bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+        }
+        if (lane == 0 && bi >= 0 && bi < K) st.labels[i * b.cs + c] = (int16_t)bi;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static cudaError_t get_encoder() {
+    if (g_encode) return cudaSuccess;
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    return cudaSuccess;
+}
+
+// 2-D BF16 tensor map over a row-major rows x D matrix, box = (atom, box_rows), swizzled.
+template <int D>
+static cudaError_t make_map(CUtensorMap* m, const void* base, int64_t rows, int box_rows) {
+    using C = TcCfg<D>;
+    const cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)D * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)C::ATOM, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          C::ATOM_BYTES == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int D>
+static cudaError_t launch_tc_t(const CandBatch& b, const __nv_bfloat16* Z, int64_t n, KmState st, int pass,
+                               int final_mode, int2* recheck, int* recheck_count, uint32_t* err, cudaStream_t s) {
+    using C = TcCfg<D>;
+    cudaError_t e = get_encoder();
+    if (e != cudaSuccess) return e;
+    CUtensorMap ta, th, tl;
+    if ((e = make_map<D>(&ta, Z, n, 128)) != cudaSuccess) return e;
+    if ((e = make_map<D>(&th, st.bhi, st.bhi_rows, C::NCH)) != cudaSuccess) return e;
+    if ((e = make_map<D>(&tl, st.blo, st.bhi_rows, C::NCH)) != cudaSuccess) return e;
+    TcArgs a;
+    a.b = b;
+    a.n = n;
+    a.Z = Z;
+    a.st = st;
+    a.pass = pass;
+    a.final_mode = final_mode;
+    a.tie_band = 1.5e-4f * (float)D / 64.0f + 2.0e-5f;
+    a.recheck = recheck;
+    a.recheck_count = recheck_count;
+    a.err = err;
+    const int smem = C::SMEM;
+    auto kern = k_assign_tc<D>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    const int64_t ntiles = (n + 127) / 128;
+    const int grid = (int)(ntiles < num_sms() ? ntiles : num_sms());
+    {
+        ProfScope ps(s, PF_ASSIGN_TC, 1);
+        kern<<<grid, TC_THREADS, smem, s>>>(a, ta, th, tl);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assign_tc(const CandBatch& b, const void* Z, int64_t n, int d, KmState st, int pass, int final_mode,
+                             int2* recheck, int* recheck_count, uint32_t* err, cudaStream_t s) {
+    if (b.total_k > TC_MAX_CHUNKS * 128) return cudaErrorInvalidValue;
+    const __nv_bfloat16* z = (const __nv_bfloat16*)Z;
+    switch (d) {
+        case 32: return launch_tc_t<32>(b, z, n, st, pass, final_mode, recheck, recheck_count, err, s);
+        case 64: return launch_tc_t<64>(b, z, n, st, pass, final_mode, recheck, recheck_count, err, s);
+        case 128: return launch_tc_t<128>(b, z, n, st, pass, final_mode, recheck, recheck_count, err, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+void launch_recheck(const CandBatch& b, const void* Z, int d, KmState st, const int2* list, const int* count,
+                    cudaStream_t s) {
+    const int blocks = num_sms() * 4;
+    ProfScope ps(s, PF_RECHECK, 1);
+    const __nv_bfloat16* z = (const __nv_bfloat16*)Z;
+    switch (d) {
+        case 32: k_recheck<32><<<blocks, 256, 0, s>>>(b, z, st, list, count); break;
+        case 64: k_recheck<64><<<blocks, 256, 0, s>>>(b, z, st, list, count); break;
+        case 128: k_recheck<128><<<blocks, 256, 0, s>>>(b, z, st, list, count); break;
+    }
+}
+
+}  // namespace raftgp

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cuda_bf16.h>
+
 #include "raftgp.h"
 
 namespace raftgp {
@@ -58,6 +60,9 @@ struct KmState {                 // device arrays of one batch (workspace)
     int32_t* active;             // MAXC
     int32_t* changed;            // 2 x MAXC (double-buffered by pass parity)
     int32_t* passes;             // MAXC
+    __nv_bfloat16* bhi;          // kpad x d: BF16 rounding of mu (tensor-core operand)
+    __nv_bfloat16* blo;          // kpad x d: BF16 rounding of mu - hi
+    int64_t bhi_rows;            // kpad (total_k rounded up, so chunk loads stay in bounds)
 };
 
 void launch_seed_first(int64_t n, uint64_t seed, int32_t* seeds, uint8_t* chosen, cudaStream_t s);
@@ -69,7 +74,11 @@ void launch_batch_init(const CandBatch& b, const void* Z, int zdtype, int64_t n,
                        const float* mu0, KmState st, cudaStream_t s);
 cudaError_t launch_assign_ffma(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, KmState st, int pass,
                                cudaStream_t s);
-void launch_lloyd_update(const CandBatch& b, int d, KmState st, int pass, cudaStream_t s);
+void launch_lloyd_update(const CandBatch& b, int d, KmState st, int pass, int last_pass, cudaStream_t s);
+cudaError_t launch_assign_tc(const CandBatch& b, const void* Z, int64_t n, int d, KmState st, int pass, int final_mode,
+                             int2* recheck, int* recheck_count, uint32_t* err, cudaStream_t s);
+void launch_recheck(const CandBatch& b, const void* Z, int d, KmState st, const int2* list, const int* count,
+                    cudaStream_t s);
 
 // ---- scoring (score.cu) ---------------------------------------------------------------
 struct ScoreOut {                // per batch

@@ -209,6 +209,13 @@ void launch_seed_round(const void* Z, int zdtype, int64_t n, int d, int t, uint6
 // ------------------------------------------------------------------------------------
 // Batch set-up: centroids from seeds (or given mu0), zero sums/counts, labels = -1.
 // ------------------------------------------------------------------------------------
+// mu = hi + lo with hi = bf16(mu), lo = bf16(mu - hi): two BF16 operands that carry ~16 bits.
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    *hi = h;
+    *lo = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
 template <typename T>
 __global__ void k_batch_init_mu(CandBatch b, const T* Z, int d, const int32_t* seeds, const float* mu0, KmState st) {
     const int c = blockIdx.y;
@@ -221,9 +228,18 @@ __global__ void k_batch_init_mu(CandBatch b, const T* Z, int d, const int32_t* s
             const float v = mu0 ? mu0[(int64_t)j * d + k] : zval(Z, src * d + k);
             st.mu[(int64_t)(off + j) * d + k] = v;
             st.sums[(int64_t)(off + j) * d + k] = 0;
+            split_bf16(v, st.bhi + (int64_t)(off + j) * d + k, st.blo + (int64_t)(off + j) * d + k);
         }
         (void)part;
         if (threadIdx.x == 0) st.counts[off + j] = 0;
+    }
+    if (c == b.n - 1) {
+        // zero the padding rows after the last centroid (read by full-size chunk loads)
+        const int64_t first = (int64_t)b.total_k * d, last = st.bhi_rows * d;
+        for (int64_t t = first + blockIdx.x * blockDim.x + threadIdx.x; t < last; t += gridDim.x * blockDim.x) {
+            st.bhi[t] = __float2bfloat16_rn(0.f);
+            st.blo[t] = __float2bfloat16_rn(0.f);
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st.active[c] = 1;
@@ -415,7 +431,7 @@ cudaError_t launch_assign_ffma(const CandBatch& b, const void* Z, int zdtype, in
 // After a pass: a candidate with no label change is converged (inactive); otherwise its
 // centroids become the FP64 means of the fixed-point sums (empty clusters keep theirs).
 // ------------------------------------------------------------------------------------
-__global__ void k_lloyd_update(CandBatch b, int d, KmState st, int pass) {
+__global__ void k_lloyd_update(CandBatch b, int d, KmState st, int pass, int last_pass) {
     const int c = blockIdx.y;
     if (c >= b.n || !st.active[c]) return;
     const int changed = st.changed[(pass & 1) * MAXC + c];
@@ -428,6 +444,8 @@ __global__ void k_lloyd_update(CandBatch b, int d, KmState st, int pass) {
         if (blockIdx.x == 0 && threadIdx.x == 0) st.active[c] = 0;
         return;
     }
+    // after the last allowed pass the centroids stay those the final labels were assigned against
+    if (pass >= last_pass) return;
     const int K = b.k[c], off = b.off[c];
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < K; j += gridDim.x * blockDim.x) {
         const int cnt = st.counts[off + j];
@@ -437,16 +455,17 @@ __global__ void k_lloyd_update(CandBatch b, int d, KmState st, int pass) {
         for (int k = 0; k < d; ++k) {
             const float v = (float)((double)st.sums[(int64_t)(off + j) * d + k] * inv);
             st.mu[(int64_t)(off + j) * d + k] = v;
+            split_bf16(v, st.bhi + (int64_t)(off + j) * d + k, st.blo + (int64_t)(off + j) * d + k);
             s = fmaf(v, v, s);
         }
         st.norm2[off + j] = s;
     }
 }
 
-void launch_lloyd_update(const CandBatch& b, int d, KmState st, int pass, cudaStream_t s) {
+void launch_lloyd_update(const CandBatch& b, int d, KmState st, int pass, int last_pass, cudaStream_t s) {
     dim3 grid(8, b.n);
     ProfScope ps(s, PF_LLOYD_UPDATE, 1);
-    k_lloyd_update<<<grid, 128, 0, s>>>(b, d, st, pass);
+    k_lloyd_update<<<grid, 128, 0, s>>>(b, d, st, pass, last_pass);
 }
 
 }  // namespace raftgp
