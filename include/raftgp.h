@@ -159,6 +159,26 @@ raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype,
                            int32_t iters, int32_t assign, int32_t* labels, float* mu_out, int32_t* passes,
                            void* ws, size_t ws_bytes, raftgp_stream_t stream);
 
+/* k-means++ seeding exactly as raftgp_kmeanspp, for callers that cannot allocate device
+ * memory: for example a plugin running inside another program's CUDA context, whose device
+ * memory that program's own allocator owns and budgets, or a process that reserves all the
+ * device memory it may use before it starts partitioning.  The paper has no counterpart;
+ * this is a deployment variant of the seeding step.
+ * Its scratch (the D^2 array, the chosen-point flags and the block sums, about 5 bytes per
+ * point) is a file-scope device array of RAFTGP_NOALLOC_SCRATCH_BYTES that every GPU which
+ * loads this library holds until the process exits.  n above RAFTGP_NOALLOC_MAX_N is
+ * rejected with RAFTGP_EUNSUPPORTED before any work is queued.  The call allocates nothing:
+ * no cudaMalloc, cudaFree or allocating library routine.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call uses the same array, which keeps the previous
+ * call's contents (the call clears what must start at zero): calls whose work overlaps on the
+ * GPU (other streams, other host threads) race on it and must not be issued.  Same arguments,
+ * results and status codes as raftgp_kmeanspp otherwise; asynchronous. */
+#define RAFTGP_NOALLOC_SCRATCH_BYTES (32u << 20) /* 32 MiB */
+#define RAFTGP_NOALLOC_MAX_N 6000000
+raftgp_status raftgp_kmeanspp_noalloc(const void* Z, int64_t n, int32_t d, int32_t z_dtype, int32_t K, uint64_t seed,
+                                      int32_t* seeds, raftgp_stream_t stream);
+
 /* ---- Instrumentation (the paper has no counterpart: its Table III times whole stages) ----
  * When enabled, each kernel family is bracketed by CUDA events recorded on the stream it is
  * launched on, and its launches are counted.  raftgp_profile_enable(1) clears the counters

@@ -22,7 +22,7 @@ MAX_BATCH_CAND = 64
 
 # Every entry point declared in include/raftgp.h.
 EXPORTS = ("raftgp_workspace_size", "raftgp_embed", "raftgp_select", "raftgp_partition", "raftgp_score",
-           "raftgp_kmeanspp", "raftgp_lloyd", "raftgp_profile_enable", "raftgp_profile_read", "raftgp_last_error",
+           "raftgp_kmeanspp", "raftgp_kmeanspp_noalloc", "raftgp_lloyd", "raftgp_profile_enable", "raftgp_profile_read", "raftgp_last_error",
            "raftgp_version")
 
 
@@ -80,6 +80,8 @@ def lib():
         L.raftgp_score.argtypes = [C.POINTER(Csr), P, C.c_int32, P, P, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                    P, C.c_size_t, P]
         L.raftgp_kmeanspp.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P, P, C.c_size_t, P]
+        L.raftgp_kmeanspp_noalloc.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P, P]
+        L.raftgp_kmeanspp_noalloc.restype = C.c_int
         L.raftgp_lloyd.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, P, C.c_int32, C.c_int32, C.c_int32, P, P,
                                    C.POINTER(C.c_int32), P, C.c_size_t, P]
         for name in ("raftgp_embed", "raftgp_select", "raftgp_partition", "raftgp_score", "raftgp_kmeanspp",

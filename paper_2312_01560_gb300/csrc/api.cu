@@ -26,6 +26,16 @@ static raftgp_status fail(raftgp_status st, const char* fmt, ...) {
     return st;
 }
 
+raftgp_status set_error(raftgp_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
 static raftgp_status cuda_fail(cudaError_t e, const char* where) {
     return fail(RAFTGP_ECUDA, "%s: %s", where, cudaGetErrorString(e));
 }

@@ -11,6 +11,8 @@
 namespace raftgp {
 
 int num_sms();
+// Records the message returned by raftgp_last_error() and returns st.
+raftgp_status set_error(raftgp_status st, const char* fmt, ...);
 
 // ---- instrumentation (prof.cu) ---------------------------------------------------------
 enum ProfFamily {
