@@ -164,10 +164,10 @@ raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype,
  * memory that program's own allocator owns and budgets, or a process that reserves all the
  * device memory it may use before it starts partitioning.  The paper has no counterpart;
  * this is a deployment variant of the seeding step.
- * Its scratch (the D^2 array, the chosen-point flags and the block sums, about 5 bytes per
- * point) is a file-scope device array of RAFTGP_NOALLOC_SCRATCH_BYTES that every GPU which
- * loads this library holds until the process exits.  n above RAFTGP_NOALLOC_MAX_N is
- * rejected with RAFTGP_EUNSUPPORTED before any work is queued.  The call allocates nothing:
+ * Its scratch (the D^2 array, nearest-seed indices, chosen-point flags and block sums, about
+ * 7 bytes per point) is a file-scope device array of RAFTGP_NOALLOC_SCRATCH_BYTES that every GPU which
+ * loads this library holds until the process exits.  n above RAFTGP_NOALLOC_MAX_N (or K above
+ * 32767) is rejected with RAFTGP_EUNSUPPORTED before any work is queued.  The call allocates nothing:
  * no cudaMalloc, cudaFree or allocating library routine.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) with that device current; make that first
  * call before any stream capture.  Every call uses the same array, which keeps the previous
@@ -175,7 +175,7 @@ raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype,
  * GPU (other streams, other host threads) race on it and must not be issued.  Same arguments,
  * results and status codes as raftgp_kmeanspp otherwise; asynchronous. */
 #define RAFTGP_NOALLOC_SCRATCH_BYTES (32u << 20) /* 32 MiB */
-#define RAFTGP_NOALLOC_MAX_N 6000000
+#define RAFTGP_NOALLOC_MAX_N 4500000
 raftgp_status raftgp_kmeanspp_noalloc(const void* Z, int64_t n, int32_t d, int32_t z_dtype, int32_t K, uint64_t seed,
                                       int32_t* seeds, raftgp_stream_t stream);
 

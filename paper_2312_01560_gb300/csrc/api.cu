@@ -134,9 +134,7 @@ struct SelectWs {
     int32_t* deg;
     float* rs;
     float* rsh;
-    float* D2;
-    uint8_t* chosen;
-    unsigned long long* blocksum;
+    SeedState seed;
     int32_t* seeds;
     KmState km;
     ScoreOut so;
@@ -153,6 +151,7 @@ static void carve_km(Carver& c, KmState& km, int64_t kcap, int d, int64_t n, int
     const int64_t kp = kpad_of(kcap);
     km.mu = c.take<float>((size_t)kp * d);
     km.norm2 = c.take<float>(kp + 64);
+    km.norm2p = c.take<float>(kp + 64);
     km.sums = c.take<long long>((size_t)kcap * d);
     km.counts = c.take<int32_t>(kcap);
     km.labels = c.take<int16_t>((size_t)n * cs);
@@ -181,10 +180,8 @@ static SelectWs carve_select(Carver& c, int64_t n, int d, const raftgp_select_op
         w.rs = c.take<float>(n);
         w.rsh = c.take<float>(n);
     }
-    w.D2 = c.take<float>(n);
-    w.chosen = c.take<uint8_t>(n);
-    w.blocksum = c.take<unsigned long long>(seed_nblocks(n));
     w.seeds = c.take<int32_t>(kmax);
+    w.seed = carve_seed(c.take<char>(seed_scratch_bytes(n, kmax)), n, kmax, w.seeds);
     w.cmax = batch_cap(o, kmax);
     w.kcap = w.cmax * kmax;
     const int cs = (w.cmax + 7) / 8 * 8;
@@ -324,6 +321,22 @@ static raftgp_status run_lloyd(const CandBatch& b, const void* Z, int zdtype, in
     return RAFTGP_OK;
 }
 
+// Splits the candidates of a batch between the two tensor-core epilogue groups, largest K
+// first onto the lighter group.
+static void assign_owners(CandBatch& b) {
+    long long load[2] = {0, 0};
+    bool done[MAXC] = {};
+    for (int r = 0; r < b.n; ++r) {
+        int pick = -1;
+        for (int c = 0; c < b.n; ++c)
+            if (!done[c] && (pick < 0 || b.k[c] > b.k[pick])) pick = c;
+        done[pick] = true;
+        const int g = load[0] <= load[1] ? 0 : 1;
+        b.owner[pick] = g;
+        load[g] += b.k[pick];
+    }
+}
+
 // Evaluate a list of candidates in batches; appends their records.
 static raftgp_status run_candidates(const raftgp_csr* g, const void* Z, int d, int zdtype,
                                     const raftgp_select_opts* o, const std::vector<int>& ks, const SelectWs& w,
@@ -340,6 +353,7 @@ static raftgp_status run_candidates(const raftgp_csr* g, const void* Z, int d, i
             off += b.k[c];
         }
         b.total_k = off;
+        assign_owners(b);
         launch_batch_init(b, Z, zdtype, n, d, w.seeds, nullptr, w.km, s);
         raftgp_status st = run_lloyd(b, Z, zdtype, n, d, o->iters, o->assign, w.km, w.recheck, w.recheck_count, w.err, s);
         if (st != RAFTGP_OK) return st;
@@ -387,9 +401,10 @@ static raftgp_status run_select(const raftgp_csr* g, const void* Z, int d, int z
     raftgp_status st = read_error_word(w.err, s);
     if (st != RAFTGP_OK) return st;
     // seeding for K_max, shared by every candidate
-    cudaMemsetAsync(w.chosen, 0, (size_t)n, s);
-    launch_seed_first(n, o->seed, w.seeds, w.chosen, s);
-    for (int t = 1; t < kmax; ++t) launch_seed_round(Z, zdtype, n, d, t, o->seed, w.seeds, w.chosen, w.D2, w.blocksum, s);
+    {
+        cudaError_t e = launch_seeding(Z, zdtype, n, d, kmax, o->seed, w.seed, s);
+        if (e != cudaSuccess) return cuda_fail(e, "seeding");
+    }
     cudaMemsetAsync(w.best, 0, sizeof(BestState), s);
     std::vector<CandRecord> rec;
     std::vector<int> ks;
@@ -562,17 +577,14 @@ raftgp_status raftgp_kmeanspp(const void* Z, int64_t n, int32_t d, int32_t z_dty
     if (!Z || !seeds || !ws || n < 1) return fail(RAFTGP_EINVAL, "NULL argument or n < 1");
     if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d must be 32, 64 or 128");
     if (K < 1 || K > n) return fail(RAFTGP_EINVAL, "need 1 <= K <= n");
+    if (K > 32767) return fail(RAFTGP_EUNSUPPORTED, "K above 32767 is not supported");
     if (z_dtype != RAFTGP_F32 && z_dtype != RAFTGP_BF16) return fail(RAFTGP_EINVAL, "unknown z_dtype");
     Carver c(ws);
-    float* D2 = c.take<float>(n);
-    uint8_t* chosen = c.take<uint8_t>(n);
-    unsigned long long* bs = c.take<unsigned long long>(seed_nblocks(n));
+    char* region = c.take<char>(seed_scratch_bytes(n, K));
     if (ws_bytes < c.off) return fail(RAFTGP_ENOMEM, "workspace too small");
     cudaStream_t s = (cudaStream_t)stream;
-    cudaMemsetAsync(chosen, 0, (size_t)n, s);
-    launch_seed_first(n, seed, seeds, chosen, s);
-    for (int t = 1; t < K; ++t) launch_seed_round(Z, z_dtype, n, d, t, seed, seeds, chosen, D2, bs, s);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_seeding(Z, z_dtype, n, d, K, seed, carve_seed(region, n, K, seeds), s);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kmeanspp");
     return RAFTGP_OK;
 }

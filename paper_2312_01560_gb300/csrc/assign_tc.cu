@@ -46,7 +46,7 @@ struct TcCfg {
 };
 
 constexpr int TC_MAX_CHUNKS = 512;
-constexpr int TC_THREADS = 192;
+constexpr int TC_THREADS = 320;   // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue (two groups of 4)
 
 struct TcCtl {
     uint64_t a_full, a_empty;
@@ -159,6 +159,29 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,"
+        "%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]),
+          "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]),
+          "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
+          "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
+          "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // ---------------------------------------------------------------------------------------
 // The kernel
 // ---------------------------------------------------------------------------------------
@@ -198,7 +221,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         for (int q = 0; q < 2; ++q) {
             mbar_init(&ctl.acc_full[q], 1);
-            mbar_init(&ctl.acc_empty[q], 128);
+            mbar_init(&ctl.acc_empty[q], 256);
         }
         mbar_init(&ctl.drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -296,7 +319,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_drain(&ctl.drain, 0);
         }
     } else {
-        // ---------------- epilogue (warps 2..5) ----------------
+        // ---------------- epilogue (warps 2..9: two groups, each owning whole candidates) -----
+        const int wg = (warp - 2) >> 2;               // epilogue group
         const int quarter = warp & 3;                 // TMEM lanes this warp may access
         const int row = quarter * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
@@ -305,7 +329,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             const int64_t i = tile * 128 + row;
             const bool valid = i < a.n;
-            int seg = 0;                              // candidate whose columns come next
+            int seg = 0;                              // first candidate that may still have columns ahead
             float bv = INFINITY, b2 = INFINITY;
             int bi = -1;
             for (int q = 0; q < nchunks; ++q, ++it) {
@@ -313,95 +337,107 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (!(ok = mbar_wait(&ctl.acc_full[buf], (it >> 1) & 1, &ctl, a.err))) break;
                 tc_fence_after();
                 const int chunk0 = ctl.chunk_col[q];
-                for (int sl = 0; sl < C::NCH / 32; ++sl) {
-                    const int col0 = chunk0 + sl * 32;
+                for (int sl = 0; sl < C::NCH / 64; ++sl) {
+                    const int col0 = chunk0 + sl * 64;
                     if (col0 >= b.total_k) break;
-                    uint32_t r[32];
-                    tmem_ld32(lane_base + (uint32_t)(buf * C::NCH + sl * 32), r);
-                    float nrm[32];
+                    const int c_hi = min(col0 + 64, b.total_k);
+                    // skip candidates that end before this slice
+                    while (b.off[seg] + b.k[seg] <= col0) ++seg;
+                    // does this group own an active candidate with columns in the slice?
+                    bool need = false;
+                    for (int s2 = seg; s2 < b.n && b.off[s2] < c_hi; ++s2)
+                        need |= b.owner[s2] == wg && (a.final_mode || a.st.active[s2]);
+                    if (!need) continue;
+                    uint32_t r[64];
+                    tmem_ld64(lane_base + (uint32_t)(buf * C::NCH + sl * 64), r);
+                    float np4[64];                    // ||mu||^2 + 4 (keeps every score positive)
 #pragma unroll
-                    for (int v = 0; v < 8; ++v) {
-                        const float4 t4 = __ldg(reinterpret_cast<const float4*>(a.st.norm2 + col0) + v);
-                        nrm[4 * v] = t4.x; nrm[4 * v + 1] = t4.y; nrm[4 * v + 2] = t4.z; nrm[4 * v + 3] = t4.w;
+                    for (int v = 0; v < 16; ++v) {
+                        const float4 t4 = __ldg(reinterpret_cast<const float4*>(a.st.norm2p + col0) + v);
+                        np4[4 * v] = t4.x; np4[4 * v + 1] = t4.y; np4[4 * v + 2] = t4.z; np4[4 * v + 3] = t4.w;
                     }
-                    int c_lo = col0;
-                    const int c_hi = min(col0 + 32, b.total_k);
-                    while (c_lo < c_hi) {
-                        const int seg_end = b.off[seg] + b.k[seg];
-                        if (c_lo >= seg_end) {
-                            // candidate `seg` complete for this tile
-                            ++seg;
-                            continue;
-                        }
-                        const int run_end = min(c_hi, seg_end);
-                        const bool act = a.final_mode || a.st.active[seg];
-                        if (act) {
-                            const int r_lo = c_lo - col0, r_hi = run_end - col0;
-                            if (r_lo == 0 && r_hi == 32) {
+                    for (int s2 = seg; s2 < b.n && b.off[s2] < c_hi; ++s2) {
+                        const int seg_end = b.off[s2] + b.k[s2];
+                        const bool mine = b.owner[s2] == wg && (a.final_mode || a.st.active[s2]);
+                        if (!mine) continue;
+                        const int r_lo = max(b.off[s2], col0) - col0, r_hi = min(seg_end, c_hi) - col0;
+                        if (a.final_mode) {
+                            // exact best and second best (FP32 compare), for the near-tie test
 #pragma unroll
-                                for (int k = 0; k < 32; ++k) {
-                                    const float s = fmaf(-2.0f, __uint_as_float(r[k]), nrm[k]);
-                                    if (a.final_mode) {
-                                        if (s < bv) { b2 = bv; bv = s; bi = col0 + k; } else { b2 = fminf(b2, s); }
-                                    } else if (s < bv) { bv = s; bi = col0 + k; }
+                            for (int k = 0; k < 64; ++k) {
+                                if (k < r_lo || k >= r_hi) continue;
+                                const float sc = fmaf(-2.0f, __uint_as_float(r[k]), np4[k]);
+                                if (sc < bv) { b2 = bv; bv = sc; bi = col0 + k; } else { b2 = fminf(b2, sc); }
+                            }
+                        } else {
+                            // packed keys: score bits with the low 6 bits replaced by the column in
+                            // the slice; a float minimum then yields value and column at once
+                            float kmin = INFINITY;
+                            if (r_lo == 0 && r_hi == 64) {
+#pragma unroll
+                                for (int k = 0; k < 64; k += 2) {
+                                    const float s0 = fmaf(-2.0f, __uint_as_float(r[k]), np4[k]);
+                                    const float s1 = fmaf(-2.0f, __uint_as_float(r[k + 1]), np4[k + 1]);
+                                    const float k0 = __uint_as_float((__float_as_uint(s0) & 0xFFFFFFC0u) | (uint32_t)k);
+                                    const float k1 = __uint_as_float((__float_as_uint(s1) & 0xFFFFFFC0u) | (uint32_t)(k + 1));
+                                    kmin = min3f(kmin, k0, k1);
                                 }
                             } else {
 #pragma unroll
-                                for (int k = 0; k < 32; ++k) {
-                                    if (k < r_lo || k >= r_hi) continue;
-                                    const float s = fmaf(-2.0f, __uint_as_float(r[k]), nrm[k]);
-                                    if (a.final_mode) {
-                                        if (s < bv) { b2 = bv; bv = s; bi = col0 + k; } else { b2 = fminf(b2, s); }
-                                    } else if (s < bv) { bv = s; bi = col0 + k; }
+                                for (int k = 0; k < 64; ++k) {
+                                    const float s0 = fmaf(-2.0f, __uint_as_float(r[k]), np4[k]);
+                                    const float k0 = __uint_as_float((__float_as_uint(s0) & 0xFFFFFFC0u) | (uint32_t)k);
+                                    kmin = (k >= r_lo && k < r_hi) ? fminf(kmin, k0) : kmin;
+                                }
+                            }
+                            const uint32_t kb = __float_as_uint(kmin);
+                            const float v = __uint_as_float(kb & 0xFFFFFFC0u);
+                            if (v < bv) { bv = v; bi = col0 + (int)(kb & 63u); }
+                        }
+                        if (seg_end > c_hi) continue;   // the candidate continues in a later slice
+                        // ---- candidate s2 finished for this tile: label, change, sums ----
+                        const int K = b.k[s2], off = b.off[s2];
+                        int nl = bi - off;
+                        if (nl < 0 || nl >= K) nl = 0;   // non-finite scores: keep indices in range
+                        int ol = -1;
+                        if (valid) {
+                            int16_t* lp = a.st.labels + i * b.cs + s2;
+                            ol = *lp;
+                            *lp = (int16_t)nl;
+                        }
+                        if (a.final_mode) {
+                            if (valid && !(b2 - bv > a.tie_band)) {
+                                const int slot = atomicAdd(a.recheck_count, 1);
+                                a.recheck[slot] = make_int2((int)i, s2);
+                            }
+                        } else {
+                            const bool ch = valid && nl != ol;
+                            unsigned mask = __ballot_sync(0xffffffffu, ch);
+                            if (lane == 0 && mask) atomicAdd(a.st.changed + (a.pass & 1) * MAXC + s2, __popc(mask));
+                            if (ch) {
+                                atomicAdd(a.st.counts + off + nl, 1);
+                                if (ol >= 0) atomicSub(a.st.counts + off + ol, 1);
+                            }
+                            while (mask) {
+                                const int src = __ffs(mask) - 1;
+                                mask &= mask - 1;
+                                const int64_t pi = __shfl_sync(0xffffffffu, i, src);
+                                const int pn = __shfl_sync(0xffffffffu, nl, src);
+                                const int po = __shfl_sync(0xffffffffu, ol, src);
+                                for (int k = lane; k < D; k += 32) {
+                                    const long long v =
+                                        __float2ll_rn(__bfloat162float(a.Z[pi * D + k]) * FIXED_SCALE_F);
+                                    atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + pn) * D + k),
+                                              (unsigned long long)v);
+                                    if (po >= 0)
+                                        atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + po) * D + k),
+                                                  (unsigned long long)(-v));
                                 }
                             }
                         }
-                        if (run_end == seg_end && act) {
-                            // ---- candidate `seg` finished for this tile: label, change, sums ----
-                            const int K = b.k[seg], off = b.off[seg];
-                            int nl = bi - off;
-                            if (nl < 0 || nl >= K) nl = 0;   // non-finite scores: keep indices in range
-                            int ol = -1;
-                            if (valid) {
-                                int16_t* lp = a.st.labels + i * b.cs + seg;
-                                ol = *lp;
-                                *lp = (int16_t)nl;
-                            }
-                            if (a.final_mode) {
-                                if (valid && !(b2 - bv > a.tie_band)) {
-                                    const int slot = atomicAdd(a.recheck_count, 1);
-                                    a.recheck[slot] = make_int2((int)i, seg);
-                                }
-                            } else {
-                                const bool ch = valid && nl != ol;
-                                unsigned mask = __ballot_sync(0xffffffffu, ch);
-                                if (lane == 0 && mask) atomicAdd(a.st.changed + (a.pass & 1) * MAXC + seg, __popc(mask));
-                                if (ch) {
-                                    atomicAdd(a.st.counts + off + nl, 1);
-                                    if (ol >= 0) atomicSub(a.st.counts + off + ol, 1);
-                                }
-                                while (mask) {
-                                    const int src = __ffs(mask) - 1;
-                                    mask &= mask - 1;
-                                    const int64_t pi = __shfl_sync(0xffffffffu, i, src);
-                                    const int pn = __shfl_sync(0xffffffffu, nl, src);
-                                    const int po = __shfl_sync(0xffffffffu, ol, src);
-                                    for (int k = lane; k < D; k += 32) {
-                                        const long long v =
-                                            __float2ll_rn(__bfloat162float(a.Z[pi * D + k]) * FIXED_SCALE_F);
-                                        atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + pn) * D + k),
-                                                  (unsigned long long)v);
-                                        if (po >= 0)
-                                            atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + po) * D + k),
-                                                      (unsigned long long)(-v));
-                                    }
-                                }
-                            }
-                            bv = INFINITY;
-                            b2 = INFINITY;
-                            bi = -1;
-                        }
-                        c_lo = run_end;
+                        bv = INFINITY;
+                        b2 = INFINITY;
+                        bi = -1;
                     }
                 }
                 tc_fence_before();
@@ -509,7 +545,7 @@ static cudaError_t launch_tc_t(const CandBatch& b, const __nv_bfloat16* Z, int64
     const int64_t ntiles = (n + 127) / 128;
     const int grid = (int)(ntiles < num_sms() ? ntiles : num_sms());
     {
-        ProfScope ps(s, PF_ASSIGN_TC, 1);
+        ProfScope ps(s, final_mode ? PF_ASSIGN_TC_FINAL : (pass == 1 ? PF_ASSIGN_TC_FIRST : PF_ASSIGN_TC), 1);
         kern<<<grid, TC_THREADS, smem, s>>>(a, ta, th, tl);
     }
     return cudaGetLastError();

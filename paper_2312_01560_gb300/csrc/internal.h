@@ -17,7 +17,8 @@ raftgp_status set_error(raftgp_status st, const char* fmt, ...);
 // ---- instrumentation (prof.cu) ---------------------------------------------------------
 enum ProfFamily {
     PF_DEGREES, PF_THETA, PF_SPMM_PROJ, PF_SPMM_GCN, PF_SEED_UPDATE, PF_SEED_PICK, PF_BATCH_INIT, PF_ASSIGN_FFMA,
-    PF_ASSIGN_TC, PF_RECHECK, PF_LLOYD_UPDATE, PF_SCORE, PF_SELECT_BEST, PF_OTHER, PF_COUNT
+    PF_ASSIGN_TC, PF_ASSIGN_TC_FIRST, PF_ASSIGN_TC_FINAL, PF_RECHECK, PF_LLOYD_UPDATE, PF_SCORE, PF_SELECT_BEST,
+    PF_OTHER, PF_COUNT
 };
 // Brackets the kernels launched in its lifetime with CUDA events when profiling is on.
 class ProfScope {
@@ -51,11 +52,13 @@ struct CandBatch {
     int cs;             // label row stride (n rounded up to a multiple of 8)
     int k[MAXC];        // K of each candidate
     int off[MAXC];      // first centroid of each candidate
+    int owner[MAXC];    // tensor-core epilogue group that evaluates the candidate (0 or 1)
 };
 
 struct KmState {                 // device arrays of one batch (workspace)
     float* mu;                   // total_k x d FP32 centroids
     float* norm2;                // total_k, ||mu||^2 in FP32
+    float* norm2p;               // kpad, ||mu||^2 + 4 (tensor-core epilogue: positive scores)
     long long* sums;             // total_k x d, 2^-40 fixed point
     int32_t* counts;             // total_k
     int16_t* labels;             // N x cs
@@ -67,10 +70,20 @@ struct KmState {                 // device arrays of one batch (workspace)
     int64_t bhi_rows;            // kpad (total_k rounded up, so chunk loads stay in bounds)
 };
 
-void launch_seed_first(int64_t n, uint64_t seed, int32_t* seeds, uint8_t* chosen, cudaStream_t s);
-void launch_seed_round(const void* Z, int zdtype, int64_t n, int d, int t, uint64_t seed, int32_t* seeds,
-                       uint8_t* chosen, float* D2, unsigned long long* blocksum, cudaStream_t s);
+// k-means++ seeding scratch (carved from one region by carve_seed)
+struct SeedState {
+    float* D2;                     // n: squared distance to the nearest seed so far
+    int16_t* nearest;              // n: index (into seeds) of that seed
+    uint8_t* chosen;               // n: already a seed
+    unsigned long long* blocksum;  // seed_nblocks(n): block sums of the quantised D^2
+    float* cc2;                    // K: squared distance from each seed to the newest one
+    int32_t* seeds;                // K (caller's output)
+};
 int seed_nblocks(int64_t n);
+size_t seed_scratch_bytes(int64_t n, int K);
+SeedState carve_seed(void* base, int64_t n, int K, int32_t* seeds);
+cudaError_t launch_seeding(const void* Z, int zdtype, int64_t n, int d, int K, uint64_t seed, SeedState ss,
+                           cudaStream_t s);
 
 void launch_batch_init(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, const int32_t* seeds,
                        const float* mu0, KmState st, cudaStream_t s);

@@ -23,60 +23,89 @@ __device__ __forceinline__ float zval(const T* Z, int64_t i) {
     return load_elem(Z, i);
 }
 
-// FP32 direct-form squared distance, ascending coordinates, no contraction.
-template <typename T>
-__device__ __forceinline__ float sqdist_direct(const T* __restrict__ zi, const float* __restrict__ c, int d) {
-    float s = 0.0f;
-    for (int k = 0; k < d; ++k) {
-        const float t = __fsub_rn(load_elem(zi, k), c[k]);
-        s = __fadd_rn(s, __fmul_rn(t, t));
-    }
-    return s;
-}
-
 __device__ __forceinline__ uint64_t kmpp_draw(uint64_t seed, int t) {
     const U32x4 x = philox4x32_10((uint32_t)t, 0u, 0u, STREAM_KMPP, seed);
     return (uint64_t)x.x | ((uint64_t)x.y << 32);
 }
 
-__device__ __forceinline__ unsigned long long quantise(float d2) {
-    return (unsigned long long)((double)d2 * FIXED_SCALE);
+// floor(D^2 * 2^40): the FP32 product by a power of two is exact, the conversion truncates.
+__device__ __forceinline__ unsigned long long quantise(float d2) { return __float2ull_rz(d2 * FIXED_SCALE_F); }
+
+constexpr int SEED_THREADS = 256;
+constexpr int SEED_PPT = 8;                               // points per thread
+constexpr int SEED_PPB = SEED_THREADS * SEED_PPT;         // points per block partial
+
+// FP32 direct-form squared distance of one row against the centre in shared memory:
+// ascending coordinates, 16-byte vector loads, every subtract/multiply/add rounded separately.
+template <typename T, int D>
+__device__ __forceinline__ float row_sqdist(const T* __restrict__ zi, const float* __restrict__ c) {
+    constexpr int E = Vec<T>::E;
+    float s = 0.0f;
+#pragma unroll
+    for (int v = 0; v < D / E; ++v) {
+        float x[E];
+        Vec<T>::load(zi + v * E, x);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const float t = __fsub_rn(x[e], c[v * E + e]);
+            s = __fadd_rn(s, __fmul_rn(t, t));
+        }
+    }
+    return s;
 }
 
-constexpr int SEED_THREADS = 256;  // points per block partial
-
-__global__ void k_seed_first(int64_t n, uint64_t seed, int32_t* seeds, uint8_t* chosen) {
+__global__ void k_seed_first(int64_t n, uint64_t seed, SeedState ss) {
     const int64_t i = (int64_t)mulhi64(kmpp_draw(seed, 0), (uint64_t)n);
-    seeds[0] = (int32_t)i;
-    chosen[i] = 1;
+    ss.seeds[0] = (int32_t)i;
+    ss.chosen[i] = 1;
 }
 
-// D^2_i = min(D^2_i, dist(z_i, z_{seeds[t-1]})), and per-block sums of the quantised D^2.
-template <typename T>
-__global__ void __launch_bounds__(SEED_THREADS) k_seed_update(const T* __restrict__ Z, int64_t n, int d, int t,
-                                                              const int32_t* seeds, float* D2,
-                                                              unsigned long long* blocksum) {
-    __shared__ float c[128];
+// Round t: D^2_i = min(D^2_i, dist(z_i, c)) for the newest seed c = seeds[t-1], and per-block
+// sums of the quantised D^2.  A point whose nearest seed c_j satisfies
+// |c_j - c|^2 >= 4 D^2_i (1 + 1e-4) cannot get closer (triangle inequality, with a margin that
+// covers the FP32 rounding of both sides), so its row is not read: the result is identical to
+// evaluating every distance.
+template <typename T, int D>
+__global__ void __launch_bounds__(SEED_THREADS) k_seed_update(const T* __restrict__ Z, int64_t n, int t,
+                                                              SeedState ss) {
+    __shared__ float c[D];
     __shared__ unsigned long long wsum[SEED_THREADS / 32];
-    const int64_t ci = seeds[t - 1];
-    for (int k = threadIdx.x; k < d; k += blockDim.x) c[k] = zval(Z, ci * d + k);
+    const int64_t ci = ss.seeds[t - 1];
+    for (int k = threadIdx.x; k < D; k += blockDim.x) c[k] = load_elem(Z, ci * D + k);
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long q = 0;
-    if (i < n) {
-        const float nd = sqdist_direct(Z + i * d, c, d);
-        const float cur = (t == 1) ? nd : fminf(D2[i], nd);
-        D2[i] = cur;
-        q = quantise(cur);
+    const int64_t base = (int64_t)blockIdx.x * SEED_PPB + threadIdx.x;
+#pragma unroll 2
+    for (int r = 0; r < SEED_PPT; ++r) {
+        const int64_t i = base + (int64_t)r * SEED_THREADS;
+        if (i >= n) break;
+        float cur;
+        if (t == 1) {
+            cur = row_sqdist<T, D>(Z + i * D, c);
+            ss.D2[i] = cur;
+            ss.nearest[i] = 0;
+        } else {
+            cur = ss.D2[i];
+            const float bound = __ldg(ss.cc2 + ss.nearest[i]);
+            if (!(bound >= 4.0f * cur * 1.0001f)) {
+                const float nd = row_sqdist<T, D>(Z + i * D, c);
+                if (nd < cur) {
+                    cur = nd;
+                    ss.D2[i] = nd;
+                    ss.nearest[i] = (int16_t)(t - 1);
+                }
+            }
+        }
+        q += quantise(cur);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
     if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = q;
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long s = 0;
-        for (int w = 0; w < SEED_THREADS / 32; ++w) s += wsum[w];
-        blocksum[blockIdx.x] = s;
+        unsigned long long sum = 0;
+        for (int w = 0; w < SEED_THREADS / 32; ++w) sum += wsum[w];
+        ss.blocksum[blockIdx.x] = sum;
     }
 }
 
@@ -110,19 +139,20 @@ __device__ unsigned long long block_scan_1024(unsigned long long v, unsigned lon
 }
 
 // Pick seed t: threshold floor(r_t * sum q / 2^64), first point whose inclusive prefix of q
-// exceeds it.  One block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_seed_pick(int64_t n, int nblocks, const unsigned long long* blocksum,
-                                                    const float* D2, uint64_t seed, int t, int32_t* seeds,
-                                                    uint8_t* chosen) {
+// exceeds it (the lowest-index unchosen point if every q is 0).  Then the squared distances
+// from every earlier seed to the new one, for the next round's skip test.  One block of 1024.
+template <typename T, int D>
+__global__ void __launch_bounds__(1024) k_seed_pick(const T* __restrict__ Z, int64_t n, int nblocks, uint64_t seed,
+                                                    int t, SeedState ss) {
     __shared__ unsigned long long s_thr, s_base;
     __shared__ int s_block;
     __shared__ long long s_pick;
-    // total
+    __shared__ long long wmin[32];
     unsigned long long run = 0;  // running prefix of completed chunks
     unsigned long long tot = 0;
     for (int b0 = 0; b0 < nblocks; b0 += 1024) {
         const int b = b0 + threadIdx.x;
-        unsigned long long v = b < nblocks ? blocksum[b] : 0ull, ct;
+        unsigned long long v = b < nblocks ? ss.blocksum[b] : 0ull, ct;
         block_scan_1024(v, &ct);
         tot += ct;
     }
@@ -136,9 +166,8 @@ __global__ void __launch_bounds__(1024) k_seed_pick(int64_t n, int nblocks, cons
         // every remaining point coincides with a seed: lowest-index unchosen point
         for (int64_t base = 0; base < n; base += 1024) {
             const int64_t i = base + threadIdx.x;
-            const bool cand = i < n && !chosen[i];
+            const bool cand = i < n && !ss.chosen[i];
             const unsigned mask = __ballot_sync(0xffffffffu, cand);
-            __shared__ long long wmin[32];
             if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = mask ? base + (threadIdx.x & ~31) + __ffs(mask) - 1 : -1;
             __syncthreads();
             if (threadIdx.x == 0) {
@@ -152,12 +181,10 @@ __global__ void __launch_bounds__(1024) k_seed_pick(int64_t n, int nblocks, cons
         const unsigned long long thr = s_thr;
         for (int b0 = 0; b0 < nblocks; b0 += 1024) {
             const int b = b0 + threadIdx.x;
-            const unsigned long long v = b < nblocks ? blocksum[b] : 0ull;
+            const unsigned long long v = b < nblocks ? ss.blocksum[b] : 0ull;
             unsigned long long ct;
             const unsigned long long ex = block_scan_1024(v, &ct);
-            const unsigned long long incl = run + ex + v;
-            const bool hit = b < nblocks && incl > thr && run + ex <= thr;
-            if (hit) {
+            if (b < nblocks && run + ex + v > thr && run + ex <= thr) {
                 s_block = b;
                 s_base = run + ex;
             }
@@ -165,45 +192,100 @@ __global__ void __launch_bounds__(1024) k_seed_pick(int64_t n, int nblocks, cons
             if (s_block >= 0) break;
             run += ct;
         }
-        const int b = s_block;   // always found: thr < total
-        // inside the block: points b*SEED_THREADS .. +SEED_THREADS
-        unsigned long long v = 0;
-        const int64_t i = (int64_t)(b < 0 ? 0 : b) * SEED_THREADS + threadIdx.x;
-        if (threadIdx.x < SEED_THREADS && i < n) v = quantise(D2[i]);
-        unsigned long long ct;
-        const unsigned long long ex = block_scan_1024(v, &ct);
-        const unsigned long long incl = s_base + ex + v;
-        if (threadIdx.x < SEED_THREADS && i < n && incl > thr && s_base + ex <= thr) s_pick = i;
-        __syncthreads();
+        const int b = s_block < 0 ? 0 : s_block;   // always found: thr < total
+        // inside the block: SEED_PPB points, 2 per thread in index order
+        unsigned long long base = s_base;
+        for (int h = 0; h < SEED_PPB / 1024; ++h) {
+            const int64_t i = (int64_t)b * SEED_PPB + h * 1024 + threadIdx.x;
+            const unsigned long long v = i < n ? quantise(ss.D2[i]) : 0ull;
+            unsigned long long ct;
+            const unsigned long long ex = block_scan_1024(v, &ct);
+            if (i < n && base + ex + v > thr && base + ex <= thr) s_pick = i;
+            __syncthreads();
+            if (s_pick >= 0) break;
+            base += ct;
+        }
     }
+    __syncthreads();
+    const long long p = s_pick < 0 ? 0 : s_pick;     // unreachable fallback keeps indices in range
     if (threadIdx.x == 0) {
-        long long p = s_pick;
-        if (p < 0) p = 0;  // unreachable for valid input; keeps indices in range
-        seeds[t] = (int32_t)p;
-        chosen[p] = 1;
+        ss.seeds[t] = (int32_t)p;
+        ss.chosen[p] = 1;
+    }
+    // |c_j - c_t|^2 for j < t (FP32; used only as a conservative bound)
+    for (int j = threadIdx.x; j < t; j += blockDim.x) {
+        const int64_t sj = ss.seeds[j];
+        float acc = 0.f;
+        for (int k = 0; k < D; ++k) {
+            const float dlt = load_elem(Z, sj * D + k) - load_elem(Z, p * D + k);
+            acc = fmaf(dlt, dlt, acc);
+        }
+        ss.cc2[j] = acc;
     }
 }
 
-int seed_nblocks(int64_t n) { return (int)((n + SEED_THREADS - 1) / SEED_THREADS); }
+int seed_nblocks(int64_t n) { return (int)((n + SEED_PPB - 1) / SEED_PPB); }
 
-void launch_seed_first(int64_t n, uint64_t seed, int32_t* seeds, uint8_t* chosen, cudaStream_t s) {
-    ProfScope ps(s, PF_SEED_PICK, 1);
-    k_seed_first<<<1, 1, 0, s>>>(n, seed, seeds, chosen);
+size_t seed_scratch_bytes(int64_t n, int K) {
+    auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    return a((size_t)n * 4) + a((size_t)n * 2) + a((size_t)n) + a((size_t)seed_nblocks(n) * 8) + a((size_t)K * 4);
 }
 
-void launch_seed_round(const void* Z, int zdtype, int64_t n, int d, int t, uint64_t seed, int32_t* seeds,
-                       uint8_t* chosen, float* D2, unsigned long long* blocksum, cudaStream_t s) {
+SeedState carve_seed(void* base, int64_t n, int K, int32_t* seeds) {
+    auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    char* p = (char*)base;
+    SeedState ss;
+    ss.D2 = (float*)p;
+    p += a((size_t)n * 4);
+    ss.nearest = (int16_t*)p;
+    p += a((size_t)n * 2);
+    ss.chosen = (uint8_t*)p;
+    p += a((size_t)n);
+    ss.blocksum = (unsigned long long*)p;
+    p += a((size_t)seed_nblocks(n) * 8);
+    ss.cc2 = (float*)p;
+    ss.seeds = seeds;
+    return ss;
+}
+
+template <typename T, int D>
+static void seed_run_t(const T* Z, int64_t n, int K, uint64_t seed, SeedState ss, cudaStream_t s) {
     const int nb = seed_nblocks(n);
+    cudaMemsetAsync(ss.chosen, 0, (size_t)n, s);
     {
-        ProfScope ps(s, PF_SEED_UPDATE, 1);
-        if (zdtype == RAFTGP_BF16)
-            k_seed_update<__nv_bfloat16><<<nb, SEED_THREADS, 0, s>>>((const __nv_bfloat16*)Z, n, d, t, seeds, D2,
-                                                                     blocksum);
-        else
-            k_seed_update<float><<<nb, SEED_THREADS, 0, s>>>((const float*)Z, n, d, t, seeds, D2, blocksum);
+        ProfScope ps(s, PF_SEED_PICK, 1);
+        k_seed_first<<<1, 1, 0, s>>>(n, seed, ss);
     }
-    ProfScope ps(s, PF_SEED_PICK, 1);
-    k_seed_pick<<<1, 1024, 0, s>>>(n, nb, blocksum, D2, seed, t, seeds, chosen);
+    for (int t = 1; t < K; ++t) {
+        {
+            ProfScope ps(s, PF_SEED_UPDATE, 1);
+            k_seed_update<T, D><<<nb, SEED_THREADS, 0, s>>>(Z, n, t, ss);
+        }
+        ProfScope ps(s, PF_SEED_PICK, 1);
+        k_seed_pick<T, D><<<1, 1024, 0, s>>>(Z, n, nb, seed, t, ss);
+    }
+}
+
+cudaError_t launch_seeding(const void* Z, int zdtype, int64_t n, int d, int K, uint64_t seed, SeedState ss,
+                           cudaStream_t s) {
+    if (zdtype == RAFTGP_BF16) {
+        const __nv_bfloat16* z = (const __nv_bfloat16*)Z;
+        switch (d) {
+            case 32: seed_run_t<__nv_bfloat16, 32>(z, n, K, seed, ss, s); break;
+            case 64: seed_run_t<__nv_bfloat16, 64>(z, n, K, seed, ss, s); break;
+            case 128: seed_run_t<__nv_bfloat16, 128>(z, n, K, seed, ss, s); break;
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        const float* z = (const float*)Z;
+        switch (d) {
+            case 32: seed_run_t<float, 32>(z, n, K, seed, ss, s); break;
+            case 64: seed_run_t<float, 64>(z, n, K, seed, ss, s); break;
+            case 128: seed_run_t<float, 128>(z, n, K, seed, ss, s); break;
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------------
@@ -249,13 +331,14 @@ __global__ void k_batch_init_mu(CandBatch b, const T* Z, int d, const int32_t* s
     }
 }
 
-// ||mu_c||^2 in FP32, one thread per centroid (ascending coordinates).
-__global__ void k_norms(int total_k, int d, const float* mu, float* norm2) {
+// ||mu_c||^2 in FP32, one thread per centroid (ascending coordinates), and the +4 copy.
+__global__ void k_norms(int total_k, int d, const float* mu, float* norm2, float* norm2p) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= total_k) return;
     float s = 0.f;
     for (int k = 0; k < d; ++k) s = fmaf(mu[(int64_t)j * d + k], mu[(int64_t)j * d + k], s);
     norm2[j] = s;
+    norm2p[j] = s + 4.0f;
 }
 
 __global__ void k_fill_labels(int16_t* labels, int64_t count) {
@@ -271,7 +354,7 @@ void launch_batch_init(const CandBatch& b, const void* Z, int zdtype, int64_t n,
         k_batch_init_mu<__nv_bfloat16><<<grid, 128, 0, s>>>(b, (const __nv_bfloat16*)Z, d, seeds, mu0, st);
     else
         k_batch_init_mu<float><<<grid, 128, 0, s>>>(b, (const float*)Z, d, seeds, mu0, st);
-    k_norms<<<(b.total_k + 127) / 128, 128, 0, s>>>(b.total_k, d, st.mu, st.norm2);
+    k_norms<<<(b.total_k + 127) / 128, 128, 0, s>>>(b.total_k, d, st.mu, st.norm2, st.norm2p);
     const int64_t cnt = n * (int64_t)b.cs;
     int blocks = (int)((cnt + 255) / 256);
     if (blocks > num_sms() * 8) blocks = num_sms() * 8;
@@ -459,6 +542,7 @@ __global__ void k_lloyd_update(CandBatch b, int d, KmState st, int pass, int las
             s = fmaf(v, v, s);
         }
         st.norm2[off + j] = s;
+        st.norm2p[off + j] = s + 4.0f;
     }
 }
 

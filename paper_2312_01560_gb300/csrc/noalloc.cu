@@ -1,7 +1,8 @@
 // noalloc.cu -- k-means++ seeding without a caller-provided workspace.
 //
-// raftgp_kmeanspp needs scratch memory (the D^2 array, the chosen-point flags and the block
-// sums of the sampling scan) and takes it from a workspace the caller allocates.  Some
+// raftgp_kmeanspp needs scratch memory (the D^2 array, the nearest-seed indices, the
+// chosen-point flags and the block sums of the sampling scan) and takes it from a workspace the
+// caller allocates.  Some
 // callers cannot allocate device memory at all: for example a plugin running inside another
 // program's CUDA context, whose device memory is owned and budgeted by that program's own
 // allocator, or a host process that has reserved all the device memory it may use before it
@@ -17,11 +18,9 @@ namespace raftgp {
 // The scratch of raftgp_kmeanspp_noalloc: RAFTGP_NOALLOC_SCRATCH_BYTES bytes of device memory.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[RAFTGP_NOALLOC_SCRATCH_BYTES];
 
-// Layout inside the scratch for n points: D^2 (n floats), chosen flags (n bytes), block sums
-// (one uint64 per 256 points), each part 256-byte aligned.
-static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-// RAFTGP_NOALLOC_MAX_N points need 4 + 1 + 8/256 bytes each plus alignment: 30.2 MB < 32 MiB.
-static_assert((size_t)RAFTGP_NOALLOC_MAX_N * 4 + RAFTGP_NOALLOC_MAX_N + (RAFTGP_NOALLOC_MAX_N / 256 + 1) * 8 + 768 <=
+// Layout inside the scratch: the seeding state of carve_seed (D^2 floats, nearest-seed int16,
+// chosen flags, block sums, seed-to-seed distances), about 7 bytes per point plus 4 per seed.
+static_assert((size_t)RAFTGP_NOALLOC_MAX_N * 7 + (RAFTGP_NOALLOC_MAX_N / 2048 + 1) * 8 + 32767 * 4 + 5 * 256 <=
                   (size_t)RAFTGP_NOALLOC_SCRATCH_BYTES,
               "static scratch too small for RAFTGP_NOALLOC_MAX_N");
 
@@ -54,6 +53,7 @@ extern "C" raftgp_status raftgp_kmeanspp_noalloc(const void* Z, int64_t n, int32
     if (!Z || !seeds || n < 1) return set_error(RAFTGP_EINVAL, "NULL argument or n < 1");
     if (d != 32 && d != 64 && d != 128) return set_error(RAFTGP_EUNSUPPORTED, "d must be 32, 64 or 128");
     if (K < 1 || K > n) return set_error(RAFTGP_EINVAL, "need 1 <= K <= n");
+    if (K > 32767) return set_error(RAFTGP_EUNSUPPORTED, "K above 32767 is not supported");
     if (z_dtype != RAFTGP_F32 && z_dtype != RAFTGP_BF16) return set_error(RAFTGP_EINVAL, "unknown z_dtype");
     if (n > RAFTGP_NOALLOC_MAX_N)
         return set_error(RAFTGP_EUNSUPPORTED,
@@ -64,17 +64,12 @@ extern "C" raftgp_status raftgp_kmeanspp_noalloc(const void* Z, int64_t n, int32
     const cudaError_t ae = scratch_address(&base);
     if (ae != cudaSuccess)
         return set_error(RAFTGP_ECUDA, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(ae));
-    char* p = (char*)base;
-    float* D2 = (float*)p;
-    uint8_t* chosen = (uint8_t*)(p + align256((size_t)n * sizeof(float)));
-    unsigned long long* bs = (unsigned long long*)(p + align256((size_t)n * sizeof(float)) + align256((size_t)n));
-    cudaStream_t s = (cudaStream_t)stream;
-    // the array keeps the previous call's contents: the chosen flags must start at zero
-    // (D^2 and the block sums are written before they are read)
-    cudaError_t e = cudaMemsetAsync(chosen, 0, (size_t)n, s);
-    if (e != cudaSuccess) return set_error(RAFTGP_ECUDA, "clearing the static scratch: %s", cudaGetErrorString(e));
-    launch_seed_first(n, seed, seeds, chosen, s);
-    for (int t = 1; t < K; ++t) launch_seed_round(Z, z_dtype, n, d, t, seed, seeds, chosen, D2, bs, s);
+    if (seed_scratch_bytes(n, K) > (size_t)RAFTGP_NOALLOC_SCRATCH_BYTES)
+        return set_error(RAFTGP_EUNSUPPORTED, "n = %lld, K = %d do not fit the static scratch", (long long)n, K);
+    // every part of the state is written before it is read except the chosen flags, which
+    // carry the previous call's contents and are cleared by the seeding launch itself
+    cudaError_t e = launch_seeding(Z, z_dtype, n, d, K, seed, carve_seed(base, n, K, seeds), (cudaStream_t)stream);
+    if (e != cudaSuccess) return set_error(RAFTGP_ECUDA, "raftgp_kmeanspp_noalloc: %s", cudaGetErrorString(e));
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(RAFTGP_ECUDA, "raftgp_kmeanspp_noalloc: %s", cudaGetErrorString(e));
     return RAFTGP_OK;

@@ -51,7 +51,7 @@ def test_noalloc_matches_workspace_entry_point_twice(cuda, dtype):
 def test_noalloc_rejects_more_points_than_its_scratch_holds(cuda):
     Z = _unit_rows(64, 64, 3, torch.float32)
     seeds = torch.empty(4, dtype=torch.int32, device="cuda")
-    n_too_big = 6_000_001      # RAFTGP_NOALLOC_MAX_N + 1: rejected on the host before any work
+    n_too_big = 4_500_001      # RAFTGP_NOALLOC_MAX_N + 1: rejected on the host before any work
     st = _abi.lib().raftgp_kmeanspp_noalloc(C.c_void_p(Z.data_ptr()), n_too_big, 64, 0, 4, 1,
                                             C.c_void_p(seeds.data_ptr()), None)
     assert st == _abi.EUNSUPPORTED
