@@ -146,20 +146,24 @@ struct SelectWs {
 };
 
 static int64_t kpad_of(int64_t k) { return (k + 255) / 256 * 256; }
+static int pad64h(int k) { return (k + 63) / 64 * 64; }
+// Most centroid columns one batch may hold (every candidate padded to a multiple of 64).
+constexpr int kMaxBatchCols = 65536;
 
 static void carve_km(Carver& c, KmState& km, int64_t kcap, int d, int64_t n, int cs) {
     const int64_t kp = kpad_of(kcap);
     km.mu = c.take<float>((size_t)kp * d);
     km.norm2 = c.take<float>(kp + 64);
     km.norm2p = c.take<float>(kp + 64);
-    km.sums = c.take<long long>((size_t)kcap * d);
-    km.counts = c.take<int32_t>(kcap);
+    km.sums = c.take<long long>((size_t)kp * d);
+    km.counts = c.take<int32_t>(kp);
     km.labels = c.take<int16_t>((size_t)n * cs);
     km.active = c.take<int32_t>(MAXC);
     km.changed = c.take<int32_t>(2 * MAXC);
     km.passes = c.take<int32_t>(MAXC);
     km.bhi = c.take<__nv_bfloat16>((size_t)kp * d);
     km.blo = c.take<__nv_bfloat16>((size_t)kp * d);
+    km.baug = c.take<__nv_bfloat16>((size_t)kp * 16);
     km.bhi_rows = kp;
 }
 
@@ -183,7 +187,7 @@ static SelectWs carve_select(Carver& c, int64_t n, int d, const raftgp_select_op
     w.seeds = c.take<int32_t>(kmax);
     w.seed = carve_seed(c.take<char>(seed_scratch_bytes(n, kmax)), n, kmax, w.seeds);
     w.cmax = batch_cap(o, kmax);
-    w.kcap = w.cmax * kmax;
+    w.kcap = (int)std::min<int64_t>((int64_t)w.cmax * pad64h(kmax), kMaxBatchCols > pad64h(kmax) ? kMaxBatchCols : pad64h(kmax));
     const int cs = (w.cmax + 7) / 8 * 8;
     carve_km(c, w.km, w.kcap, d, n, cs);
     w.recheck = c.take<int2>((size_t)n * w.cmax);
@@ -342,16 +346,18 @@ static raftgp_status run_candidates(const raftgp_csr* g, const void* Z, int d, i
                                     const raftgp_select_opts* o, const std::vector<int>& ks, const SelectWs& w,
                                     int32_t* labels, std::vector<CandRecord>& rec, cudaStream_t s) {
     const int64_t n = g->n;
-    for (size_t b0 = 0; b0 < ks.size(); b0 += (size_t)w.cmax) {
+    for (size_t b0 = 0; b0 < ks.size();) {
+        // a batch: up to cmax candidates whose padded centroid ranges fit the workspace
         CandBatch b{};
-        b.n = (int)std::min<size_t>((size_t)w.cmax, ks.size() - b0);
-        b.cs = (b.n + 7) / 8 * 8;
         int off = 0;
-        for (int c = 0; c < b.n; ++c) {
-            b.k[c] = ks[b0 + c];
-            b.off[c] = off;
-            off += b.k[c];
+        while (b.n < w.cmax && b0 + b.n < ks.size() && (b.n == 0 || off + pad64h(ks[b0 + b.n]) <= w.kcap)) {
+            b.k[b.n] = ks[b0 + b.n];
+            b.off[b.n] = off;
+            off += pad64h(b.k[b.n]);
+            ++b.n;
         }
+        b0 += b.n;
+        b.cs = (b.n + 7) / 8 * 8;
         b.total_k = off;
         assign_owners(b);
         launch_batch_init(b, Z, zdtype, n, d, w.seeds, nullptr, w.km, s);
@@ -606,7 +612,7 @@ raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype,
         return fail(RAFTGP_EINVAL, "tensor-core assignment needs BF16 embeddings");
     Carver c(ws);
     KmState km{};
-    carve_km(c, km, K, d, n, 8);
+    carve_km(c, km, pad64h(K), d, n, 8);
     uint32_t* err = c.take<uint32_t>(64);
     int2* recheck = c.take<int2>((size_t)n);
     int* recheck_count = c.take<int>(64);
@@ -617,7 +623,7 @@ raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype,
     b.cs = 8;
     b.k[0] = K;
     b.off[0] = 0;
-    b.total_k = K;
+    b.total_k = pad64h(K);
     cudaMemsetAsync(err, 0, sizeof(uint32_t), s);
     launch_batch_init(b, Z, z_dtype, n, d, nullptr, mu0, km, s);
     raftgp_status st = run_lloyd(b, Z, z_dtype, n, d, iters, assign, km, recheck, recheck_count, err, s);

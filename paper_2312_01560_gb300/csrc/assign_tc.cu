@@ -33,19 +33,24 @@ struct TcCfg {
     static constexpr int ATOM = D < 64 ? D : 64;          // K elements per swizzle-atom row
     static constexpr int ATOM_BYTES = ATOM * 2;           // 64 or 128
     static constexpr int NATOM = D / ATOM;
-    static constexpr int NCH = D == 128 ? 128 : 256;      // centroids per chunk = MMA N
+    static constexpr int NCH = D == 128 ? 128 : (D == 64 ? 192 : 256);  // centroids per chunk = MMA N
     static constexpr int STAGES = D == 128 ? 2 : (D == 64 ? 3 : 4);
     static constexpr int A_ATOM_BYTES = 128 * ATOM_BYTES;
     static constexpr int A_BYTES = NATOM * A_ATOM_BYTES;
+    static constexpr int AUG_A_BYTES = 128 * 32;          // the constant K=16 slice of the point tile
     static constexpr int B_ATOM_BYTES = NCH * ATOM_BYTES;
     static constexpr int B_BYTES = NATOM * B_ATOM_BYTES;  // one half (hi or lo) of a chunk
-    static constexpr int STAGE_BYTES = 2 * B_BYTES;
+    static constexpr int AUG_B_BYTES = NCH * 32;          // the K=16 norm slice of a chunk
+    static constexpr int STAGE_BYTES = 2 * B_BYTES + AUG_B_BYTES;
     static constexpr int LAYOUT = ATOM_BYTES == 128 ? 2 : 4;  // descriptor swizzle: 128B or 64B
     static constexpr int SBO = 8 * ATOM_BYTES;                 // stride between 8-row groups
-    static constexpr int SMEM = 1024 + A_BYTES + STAGES * STAGE_BYTES;
+    static constexpr int SMEM = 1024 + A_BYTES + AUG_A_BYTES + STAGES * STAGE_BYTES;
+    static_assert(SMEM <= 227 * 1024, "shared memory budget");
+    static_assert(NCH % 64 == 0 && 2 * NCH <= 512, "chunk must be whole slices and fit two TMEM buffers");
 };
 
 constexpr int TC_MAX_CHUNKS = 512;
+constexpr int TC_MAX_SLICES = 2048;
 constexpr int TC_THREADS = 320;   // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue (two groups of 4)
 
 struct TcCtl {
@@ -57,6 +62,9 @@ struct TcCtl {
     int abort;
     int nchunks;
     int chunk_col[TC_MAX_CHUNKS];
+    // per 64-column slice of the chunk list: candidate index + 128 if the candidate's padded
+    // range ends with this slice, or -1 (no active candidate / beyond the batch)
+    int16_t slice[TC_MAX_SLICES];
 };
 
 // ---------------------------------------------------------------------------------------
@@ -201,15 +209,18 @@ struct TcArgs {
 template <int D>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_assign_tc(const __grid_constant__ TcArgs a, const __grid_constant__ CUtensorMap tmA,
-                const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo) {
+                const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
+                const __grid_constant__ CUtensorMap tmAug) {
     using C = TcCfg<D>;
     extern __shared__ uint8_t dyn_smem[];
     __shared__ TcCtl ctl;
     uint8_t* base = (uint8_t*)(((uintptr_t)dyn_smem + 1023) & ~(uintptr_t)1023);
     uint8_t* sA = base;
-    uint8_t* sB = base + C::A_BYTES;
+    uint8_t* sAug = base + C::A_BYTES;                 // 128 rows x 32 B, constant
+    uint8_t* sB = sAug + C::AUG_A_BYTES;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const CandBatch& b = a.b;
+    const int nslice_chunk = C::NCH / 64;
 
     if (threadIdx.x == 0) {
         ctl.abort = 0;
@@ -225,19 +236,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         mbar_init(&ctl.drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        // chunks of the concatenated centroid list that hold at least one column of an
-        // active candidate (FINAL: every candidate)
-        int nch = 0;
+        // chunks holding at least one column of an active candidate (FINAL: every candidate),
+        // by walking candidates and chunks together
+        int nch = 0, c = 0;
         const int total_chunks = (b.total_k + C::NCH - 1) / C::NCH;
         for (int q = 0; q < total_chunks && nch < TC_MAX_CHUNKS; ++q) {
             const int lo = q * C::NCH, hi = lo + C::NCH;
+            while (c < b.n && b.off[c] + b.k[c] <= lo) ++c;
             bool need = false;
-            for (int c = 0; c < b.n && !need; ++c)
-                need = (a.final_mode || a.st.active[c]) && b.off[c] < hi && b.off[c] + b.k[c] > lo;
+            for (int c2 = c; c2 < b.n && b.off[c2] < hi && !need; ++c2)
+                need = a.final_mode || a.st.active[c2];
             if (need) ctl.chunk_col[nch++] = lo;
         }
         ctl.nchunks = nch;
     }
+    // constant K=16 slice of the point tile: every row reads 1, 1 at K = 0, 1 (and again at 8, 9,
+    // so the row is the same under the 32-byte swizzle, which may exchange its two halves)
+    for (int t = threadIdx.x; t < C::AUG_A_BYTES / 16; t += blockDim.x)
+        reinterpret_cast<uint4*>(sAug)[t] = make_uint4(0x3F803F80u, 0u, 0u, 0u);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_addr(&ctl.tmem_base)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -247,6 +264,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = ctl.tmem_base;
     const int nchunks = ctl.nchunks;
+    // slice table (all threads): candidate of each 64-column slice and whether it ends there
+    for (int e = threadIdx.x; e < nchunks * nslice_chunk && e < TC_MAX_SLICES; e += blockDim.x) {
+        const int col0 = ctl.chunk_col[e / nslice_chunk] + (e % nslice_chunk) * 64;
+        int v = -1;
+        if (col0 < b.total_k) {
+            int c = 0;
+            while (c + 1 < b.n && b.off[c + 1] <= col0) ++c;
+            const int pad_end = c + 1 < b.n ? b.off[c + 1] : b.total_k;
+            if (col0 < b.off[c] + b.k[c] && (a.final_mode || a.st.active[c])) v = c + (col0 + 64 >= pad_end ? 128 : 0);
+        }
+        ctl.slice[e] = (int16_t)v;
+    }
+    __syncthreads();
     const int64_t ntiles = (a.n + 127) / 128;
 
     if (warp == 0) {
@@ -269,6 +299,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         tma_load_2d(dst + C::B_BYTES + t * C::B_ATOM_BYTES, &tmBlo, &ctl.b_full[s], t * C::ATOM,
                                     ctl.chunk_col[q]);
                     }
+                    tma_load_2d(dst + 2 * C::B_BYTES, &tmAug, &ctl.b_full[s], 0, ctl.chunk_col[q]);
                 }
             }
             if (!ok) {
@@ -285,6 +316,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint32_t idesc = instr_desc(C::NCH);
             int it = 0, tl = 0;
             bool ok = true;
+            const uint64_t aug_a = smem_desc(smem_addr(sAug), 6, 256);
             for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tl) {
                 if (!(ok = mbar_wait(&ctl.a_full, tl & 1, &ctl, a.err))) break;
                 tc_fence_after();
@@ -299,6 +331,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const uint32_t blo = bhi + C::B_BYTES;
                     const uint32_t a0 = smem_addr(sA);
                     int first = 1;
+                    // -z.mu from the BF16 hi and lo halves of -mu
                     for (int half = 0; half < 2; ++half) {
                         const uint32_t bb = half ? blo : bhi;
                         for (int t = 0; t < C::NATOM; ++t)
@@ -309,6 +342,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 first = 0;
                             }
                     }
+                    // FAST: + (||mu||^2 + 4)/2 from the constant slice, so the accumulator is the
+                    // positive score (||z - mu||^2 - ||z||^2 + 4)/2 itself
+                    if (!a.final_mode) mma_bf16(dcol, aug_a, smem_desc(bhi + 2 * C::B_BYTES, 6, 256), idesc, 1);
                     mma_commit(&ctl.b_empty[s]);        // the stage is free once these MMAs retire
                     mma_commit(&ctl.acc_full[buf]);     // the accumulator is ready for the epilogue
                 }
@@ -329,116 +365,92 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             const int64_t i = tile * 128 + row;
             const bool valid = i < a.n;
-            int seg = 0;                              // first candidate that may still have columns ahead
             float bv = INFINITY, b2 = INFINITY;
             int bi = -1;
             for (int q = 0; q < nchunks; ++q, ++it) {
                 const int buf = it & 1;
                 if (!(ok = mbar_wait(&ctl.acc_full[buf], (it >> 1) & 1, &ctl, a.err))) break;
                 tc_fence_after();
-                const int chunk0 = ctl.chunk_col[q];
-                for (int sl = 0; sl < C::NCH / 64; ++sl) {
-                    const int col0 = chunk0 + sl * 64;
-                    if (col0 >= b.total_k) break;
-                    const int c_hi = min(col0 + 64, b.total_k);
-                    // skip candidates that end before this slice
-                    while (b.off[seg] + b.k[seg] <= col0) ++seg;
-                    // does this group own an active candidate with columns in the slice?
-                    bool need = false;
-                    for (int s2 = seg; s2 < b.n && b.off[s2] < c_hi; ++s2)
-                        need |= b.owner[s2] == wg && (a.final_mode || a.st.active[s2]);
-                    if (!need) continue;
+                for (int sl = 0; sl < nslice_chunk; ++sl) {
+                    const int info = ctl.slice[q * nslice_chunk + sl];
+                    if (info < 0) continue;
+                    const int cand = info & 127;
+                    if (b.owner[cand] != wg) continue;
+                    const int col0 = ctl.chunk_col[q] + sl * 64;
                     uint32_t r[64];
                     tmem_ld64(lane_base + (uint32_t)(buf * C::NCH + sl * 64), r);
-                    float np4[64];                    // ||mu||^2 + 4 (keeps every score positive)
+                    if (a.final_mode) {
+                        // exact best and second best of ||mu||^2 + 4 - 2 z.mu (FP32 norms; padding
+                        // columns carry an infinite norm and never win)
+                        float np4[64];
 #pragma unroll
-                    for (int v = 0; v < 16; ++v) {
-                        const float4 t4 = __ldg(reinterpret_cast<const float4*>(a.st.norm2p + col0) + v);
-                        np4[4 * v] = t4.x; np4[4 * v + 1] = t4.y; np4[4 * v + 2] = t4.z; np4[4 * v + 3] = t4.w;
+                        for (int v = 0; v < 16; ++v) {
+                            const float4 t4 = __ldg(reinterpret_cast<const float4*>(a.st.norm2p + col0) + v);
+                            np4[4 * v] = t4.x; np4[4 * v + 1] = t4.y; np4[4 * v + 2] = t4.z; np4[4 * v + 3] = t4.w;
+                        }
+#pragma unroll
+                        for (int k = 0; k < 64; ++k) {
+                            const float sc = fmaf(2.0f, __uint_as_float(r[k]), np4[k]);
+                            if (sc < bv) { b2 = bv; bv = sc; bi = col0 + k; } else { b2 = fminf(b2, sc); }
+                        }
+                    } else {
+                        // packed keys: the positive score with its low 6 bits replaced by the column
+                        // within the slice; one float minimum gives value and column together
+                        float kmin = INFINITY;
+#pragma unroll
+                        for (int k = 0; k < 64; k += 2) {
+                            const float k0 = __uint_as_float((r[k] & 0xFFFFFFC0u) | (uint32_t)k);
+                            const float k1 = __uint_as_float((r[k + 1] & 0xFFFFFFC0u) | (uint32_t)(k + 1));
+                            kmin = min3f(kmin, k0, k1);
+                        }
+                        const uint32_t kb = __float_as_uint(kmin);
+                        const float v = __uint_as_float(kb & 0xFFFFFFC0u);
+                        if (v < bv) { bv = v; bi = col0 + (int)(kb & 63u); }
                     }
-                    for (int s2 = seg; s2 < b.n && b.off[s2] < c_hi; ++s2) {
-                        const int seg_end = b.off[s2] + b.k[s2];
-                        const bool mine = b.owner[s2] == wg && (a.final_mode || a.st.active[s2]);
-                        if (!mine) continue;
-                        const int r_lo = max(b.off[s2], col0) - col0, r_hi = min(seg_end, c_hi) - col0;
-                        if (a.final_mode) {
-                            // exact best and second best (FP32 compare), for the near-tie test
-#pragma unroll
-                            for (int k = 0; k < 64; ++k) {
-                                if (k < r_lo || k >= r_hi) continue;
-                                const float sc = fmaf(-2.0f, __uint_as_float(r[k]), np4[k]);
-                                if (sc < bv) { b2 = bv; bv = sc; bi = col0 + k; } else { b2 = fminf(b2, sc); }
-                            }
-                        } else {
-                            // packed keys: score bits with the low 6 bits replaced by the column in
-                            // the slice; a float minimum then yields value and column at once
-                            float kmin = INFINITY;
-                            if (r_lo == 0 && r_hi == 64) {
-#pragma unroll
-                                for (int k = 0; k < 64; k += 2) {
-                                    const float s0 = fmaf(-2.0f, __uint_as_float(r[k]), np4[k]);
-                                    const float s1 = fmaf(-2.0f, __uint_as_float(r[k + 1]), np4[k + 1]);
-                                    const float k0 = __uint_as_float((__float_as_uint(s0) & 0xFFFFFFC0u) | (uint32_t)k);
-                                    const float k1 = __uint_as_float((__float_as_uint(s1) & 0xFFFFFFC0u) | (uint32_t)(k + 1));
-                                    kmin = min3f(kmin, k0, k1);
-                                }
-                            } else {
-#pragma unroll
-                                for (int k = 0; k < 64; ++k) {
-                                    const float s0 = fmaf(-2.0f, __uint_as_float(r[k]), np4[k]);
-                                    const float k0 = __uint_as_float((__float_as_uint(s0) & 0xFFFFFFC0u) | (uint32_t)k);
-                                    kmin = (k >= r_lo && k < r_hi) ? fminf(kmin, k0) : kmin;
-                                }
-                            }
-                            const uint32_t kb = __float_as_uint(kmin);
-                            const float v = __uint_as_float(kb & 0xFFFFFFC0u);
-                            if (v < bv) { bv = v; bi = col0 + (int)(kb & 63u); }
-                        }
-                        if (seg_end > c_hi) continue;   // the candidate continues in a later slice
-                        // ---- candidate s2 finished for this tile: label, change, sums ----
-                        const int K = b.k[s2], off = b.off[s2];
-                        int nl = bi - off;
-                        if (nl < 0 || nl >= K) nl = 0;   // non-finite scores: keep indices in range
-                        int ol = -1;
-                        if (valid) {
-                            int16_t* lp = a.st.labels + i * b.cs + s2;
-                            ol = *lp;
-                            *lp = (int16_t)nl;
-                        }
-                        if (a.final_mode) {
-                            if (valid && !(b2 - bv > a.tie_band)) {
-                                const int slot = atomicAdd(a.recheck_count, 1);
-                                a.recheck[slot] = make_int2((int)i, s2);
-                            }
-                        } else {
-                            const bool ch = valid && nl != ol;
-                            unsigned mask = __ballot_sync(0xffffffffu, ch);
-                            if (lane == 0 && mask) atomicAdd(a.st.changed + (a.pass & 1) * MAXC + s2, __popc(mask));
-                            if (ch) {
-                                atomicAdd(a.st.counts + off + nl, 1);
-                                if (ol >= 0) atomicSub(a.st.counts + off + ol, 1);
-                            }
-                            while (mask) {
-                                const int src = __ffs(mask) - 1;
-                                mask &= mask - 1;
-                                const int64_t pi = __shfl_sync(0xffffffffu, i, src);
-                                const int pn = __shfl_sync(0xffffffffu, nl, src);
-                                const int po = __shfl_sync(0xffffffffu, ol, src);
-                                for (int k = lane; k < D; k += 32) {
-                                    const long long v =
-                                        __float2ll_rn(__bfloat162float(a.Z[pi * D + k]) * FIXED_SCALE_F);
-                                    atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + pn) * D + k),
-                                              (unsigned long long)v);
-                                    if (po >= 0)
-                                        atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + po) * D + k),
-                                                  (unsigned long long)(-v));
-                                }
-                            }
-                        }
-                        bv = INFINITY;
-                        b2 = INFINITY;
-                        bi = -1;
+                    if (info < 128) continue;          // the candidate continues in a later slice
+                    // ---- candidate finished for this tile: label, change, sums ----
+                    const int K = b.k[cand], off = b.off[cand];
+                    int nl = bi - off;
+                    if (nl < 0 || nl >= K) nl = 0;   // non-finite scores: keep indices in range
+                    int ol = -1;
+                    if (valid) {
+                        int16_t* lp = a.st.labels + i * b.cs + cand;
+                        ol = *lp;
+                        *lp = (int16_t)nl;
                     }
+                    if (a.final_mode) {
+                        if (valid && !(b2 - bv > a.tie_band)) {
+                            const int slot = atomicAdd(a.recheck_count, 1);
+                            a.recheck[slot] = make_int2((int)i, cand);
+                        }
+                    } else {
+                        const bool ch = valid && nl != ol;
+                        unsigned mask = __ballot_sync(0xffffffffu, ch);
+                        if (lane == 0 && mask) atomicAdd(a.st.changed + (a.pass & 1) * MAXC + cand, __popc(mask));
+                        if (ch) {
+                            atomicAdd(a.st.counts + off + nl, 1);
+                            if (ol >= 0) atomicSub(a.st.counts + off + ol, 1);
+                        }
+                        while (mask) {
+                            const int src = __ffs(mask) - 1;
+                            mask &= mask - 1;
+                            const int64_t pi = __shfl_sync(0xffffffffu, i, src);
+                            const int pn = __shfl_sync(0xffffffffu, nl, src);
+                            const int po = __shfl_sync(0xffffffffu, ol, src);
+                            for (int k = lane; k < D; k += 32) {
+                                const long long v =
+                                    __float2ll_rn(__bfloat162float(a.Z[pi * D + k]) * FIXED_SCALE_F);
+                                atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + pn) * D + k),
+                                          (unsigned long long)v);
+                                if (po >= 0)
+                                    atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + po) * D + k),
+                                              (unsigned long long)(-v));
+                            }
+                        }
+                    }
+                    bv = INFINITY;
+                    b2 = INFINITY;
+                    bi = -1;
                 }
                 tc_fence_before();
                 mbar_arrive(&ctl.acc_empty[buf]);
@@ -504,18 +516,24 @@ static cudaError_t get_encoder() {
 }
 
 // 2-D BF16 tensor map over a row-major rows x D matrix, box = (atom, box_rows), swizzled.
+// 2-D BF16 tensor map over a row-major rows x width matrix, box = (box_width, box_rows).
+static cudaError_t make_map_w(CUtensorMap* m, const void* base, int width, int64_t rows, int box_width, int box_rows,
+                              CUtensorMapSwizzle swz) {
+    const cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)width * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)box_width, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int D>
 static cudaError_t make_map(CUtensorMap* m, const void* base, int64_t rows, int box_rows) {
     using C = TcCfg<D>;
-    const cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)D * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)C::ATOM, (cuuint32_t)box_rows};
-    const cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          C::ATOM_BYTES == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+    return make_map_w(m, base, D, rows, C::ATOM, box_rows,
+                      C::ATOM_BYTES == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B);
 }
 
 template <int D>
@@ -524,10 +542,11 @@ static cudaError_t launch_tc_t(const CandBatch& b, const __nv_bfloat16* Z, int64
     using C = TcCfg<D>;
     cudaError_t e = get_encoder();
     if (e != cudaSuccess) return e;
-    CUtensorMap ta, th, tl;
+    CUtensorMap ta, th, tl, tg;
     if ((e = make_map<D>(&ta, Z, n, 128)) != cudaSuccess) return e;
     if ((e = make_map<D>(&th, st.bhi, st.bhi_rows, C::NCH)) != cudaSuccess) return e;
     if ((e = make_map<D>(&tl, st.blo, st.bhi_rows, C::NCH)) != cudaSuccess) return e;
+    if ((e = make_map_w(&tg, st.baug, 16, st.bhi_rows, 16, C::NCH, CU_TENSOR_MAP_SWIZZLE_32B)) != cudaSuccess) return e;
     TcArgs a;
     a.b = b;
     a.n = n;
@@ -546,14 +565,15 @@ static cudaError_t launch_tc_t(const CandBatch& b, const __nv_bfloat16* Z, int64
     const int grid = (int)(ntiles < num_sms() ? ntiles : num_sms());
     {
         ProfScope ps(s, final_mode ? PF_ASSIGN_TC_FINAL : (pass == 1 ? PF_ASSIGN_TC_FIRST : PF_ASSIGN_TC), 1);
-        kern<<<grid, TC_THREADS, smem, s>>>(a, ta, th, tl);
+        kern<<<grid, TC_THREADS, smem, s>>>(a, ta, th, tl, tg);
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_assign_tc(const CandBatch& b, const void* Z, int64_t n, int d, KmState st, int pass, int final_mode,
                              int2* recheck, int* recheck_count, uint32_t* err, cudaStream_t s) {
-    if (b.total_k > TC_MAX_CHUNKS * 128) return cudaErrorInvalidValue;
+    // the chunk and slice tables hold every column of the batch
+    if (b.total_k > TC_MAX_SLICES * 64 || b.total_k > TC_MAX_CHUNKS * 128) return cudaErrorInvalidValue;
     const __nv_bfloat16* z = (const __nv_bfloat16*)Z;
     switch (d) {
         case 32: return launch_tc_t<32>(b, z, n, st, pass, final_mode, recheck, recheck_count, err, s);

@@ -51,7 +51,7 @@ struct CandBatch {
     int total_k;        // sum of k[]
     int cs;             // label row stride (n rounded up to a multiple of 8)
     int k[MAXC];        // K of each candidate
-    int off[MAXC];      // first centroid of each candidate
+    int off[MAXC];      // first centroid of each candidate (multiples of 64: candidates padded)
     int owner[MAXC];    // tensor-core epilogue group that evaluates the candidate (0 or 1)
 };
 
@@ -65,8 +65,9 @@ struct KmState {                 // device arrays of one batch (workspace)
     int32_t* active;             // MAXC
     int32_t* changed;            // 2 x MAXC (double-buffered by pass parity)
     int32_t* passes;             // MAXC
-    __nv_bfloat16* bhi;          // kpad x d: BF16 rounding of mu (tensor-core operand)
-    __nv_bfloat16* blo;          // kpad x d: BF16 rounding of mu - hi
+    __nv_bfloat16* bhi;          // kpad x d: BF16 rounding of -mu (tensor-core operand)
+    __nv_bfloat16* blo;          // kpad x d: BF16 rounding of -mu - hi
+    __nv_bfloat16* baug;         // kpad x 16: the norm slice [(||mu||^2+4)/2 hi, lo, 0...]
     int64_t bhi_rows;            // kpad (total_k rounded up, so chunk loads stay in bounds)
 };
 

@@ -291,11 +291,44 @@ cudaError_t launch_seeding(const void* Z, int zdtype, int64_t n, int d, int K, u
 // ------------------------------------------------------------------------------------
 // Batch set-up: centroids from seeds (or given mu0), zero sums/counts, labels = -1.
 // ------------------------------------------------------------------------------------
-// mu = hi + lo with hi = bf16(mu), lo = bf16(mu - hi): two BF16 operands that carry ~16 bits.
+// v = hi + lo with hi = bf16(v), lo = bf16(v - hi): two BF16 operands that carry ~16 bits.
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16* hi, __nv_bfloat16* lo) {
     const __nv_bfloat16 h = __float2bfloat16_rn(v);
     *hi = h;
     *lo = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+__host__ __device__ __forceinline__ int pad64(int k) { return (k + 63) / 64 * 64; }
+
+// Everything derived from one FP32 centroid row: ||mu||^2 (ascending coordinates), the
+// +4-shifted copy, the tensor-core operands -mu = hi + lo, and the norm slice
+// [(||mu||^2 + 4)/2 as hi, lo, then zeros].  A padding row (no centroid) gets an infinite
+// norm and a huge norm slice so it never wins an argmin.
+__device__ void write_row_operands(KmState st, int64_t row, int d, bool padding) {
+    float* mu = st.mu + row * d;
+    __nv_bfloat16* aug = st.baug + row * 16;
+    if (padding) {
+        for (int k = 0; k < d; ++k) {
+            mu[k] = 0.f;
+            st.bhi[row * d + k] = __float2bfloat16_rn(0.f);
+            st.blo[row * d + k] = __float2bfloat16_rn(0.f);
+        }
+        st.norm2[row] = INFINITY;
+        st.norm2p[row] = INFINITY;
+        aug[0] = __float2bfloat16_rn(1.0e30f);
+        for (int k = 1; k < 16; ++k) aug[k] = __float2bfloat16_rn(0.f);
+        return;
+    }
+    float s = 0.f;
+    for (int k = 0; k < d; ++k) {
+        const float v = mu[k];
+        s = fmaf(v, v, s);
+        split_bf16(-v, st.bhi + row * d + k, st.blo + row * d + k);
+    }
+    st.norm2[row] = s;
+    st.norm2p[row] = s + 4.0f;
+    split_bf16(0.5f * (s + 4.0f), aug, aug + 1);
+    for (int k = 2; k < 16; ++k) aug[k] = __float2bfloat16_rn(0.f);
 }
 
 template <typename T>
@@ -303,25 +336,25 @@ __global__ void k_batch_init_mu(CandBatch b, const T* Z, int d, const int32_t* s
     const int c = blockIdx.y;
     if (c >= b.n) return;
     const int K = b.k[c], off = b.off[c];
-    for (int j = blockIdx.x; j < K; j += gridDim.x) {
-        const int64_t src = seeds ? (int64_t)seeds[j] : -1;
-        float part = 0.f;
+    for (int j = blockIdx.x; j < pad64(K); j += gridDim.x) {
+        const int64_t src = (seeds && j < K) ? (int64_t)seeds[j] : -1;
         for (int k = threadIdx.x; k < d; k += blockDim.x) {
-            const float v = mu0 ? mu0[(int64_t)j * d + k] : zval(Z, src * d + k);
+            float v = 0.f;
+            if (j < K) v = mu0 ? mu0[(int64_t)j * d + k] : zval(Z, src * d + k);
             st.mu[(int64_t)(off + j) * d + k] = v;
             st.sums[(int64_t)(off + j) * d + k] = 0;
-            split_bf16(v, st.bhi + (int64_t)(off + j) * d + k, st.blo + (int64_t)(off + j) * d + k);
         }
-        (void)part;
         if (threadIdx.x == 0) st.counts[off + j] = 0;
     }
     if (c == b.n - 1) {
-        // zero the padding rows after the last centroid (read by full-size chunk loads)
-        const int64_t first = (int64_t)b.total_k * d, last = st.bhi_rows * d;
-        for (int64_t t = first + blockIdx.x * blockDim.x + threadIdx.x; t < last; t += gridDim.x * blockDim.x) {
+        // zero the rows after the batch (read by full-size chunk loads)
+        const int64_t first = (int64_t)b.total_k, last = st.bhi_rows;
+        for (int64_t t = first * d + blockIdx.x * blockDim.x + threadIdx.x; t < last * d; t += gridDim.x * blockDim.x) {
             st.bhi[t] = __float2bfloat16_rn(0.f);
             st.blo[t] = __float2bfloat16_rn(0.f);
         }
+        for (int64_t t = first * 16 + blockIdx.x * blockDim.x + threadIdx.x; t < last * 16; t += gridDim.x * blockDim.x)
+            st.baug[t] = __float2bfloat16_rn(0.f);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st.active[c] = 1;
@@ -331,14 +364,13 @@ __global__ void k_batch_init_mu(CandBatch b, const T* Z, int d, const int32_t* s
     }
 }
 
-// ||mu_c||^2 in FP32, one thread per centroid (ascending coordinates), and the +4 copy.
-__global__ void k_norms(int total_k, int d, const float* mu, float* norm2, float* norm2p) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= total_k) return;
-    float s = 0.f;
-    for (int k = 0; k < d; ++k) s = fmaf(mu[(int64_t)j * d + k], mu[(int64_t)j * d + k], s);
-    norm2[j] = s;
-    norm2p[j] = s + 4.0f;
+// Operands of every row of the batch, one thread per row.
+__global__ void k_operands(CandBatch b, int d, KmState st) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= b.total_k) return;
+    int c = 0;
+    while (c + 1 < b.n && b.off[c + 1] <= row) ++c;
+    write_row_operands(st, row, d, row - b.off[c] >= b.k[c]);
 }
 
 __global__ void k_fill_labels(int16_t* labels, int64_t count) {
@@ -354,7 +386,7 @@ void launch_batch_init(const CandBatch& b, const void* Z, int zdtype, int64_t n,
         k_batch_init_mu<__nv_bfloat16><<<grid, 128, 0, s>>>(b, (const __nv_bfloat16*)Z, d, seeds, mu0, st);
     else
         k_batch_init_mu<float><<<grid, 128, 0, s>>>(b, (const float*)Z, d, seeds, mu0, st);
-    k_norms<<<(b.total_k + 127) / 128, 128, 0, s>>>(b.total_k, d, st.mu, st.norm2, st.norm2p);
+    k_operands<<<(b.total_k + 127) / 128, 128, 0, s>>>(b, d, st);
     const int64_t cnt = n * (int64_t)b.cs;
     int blocks = (int)((cnt + 255) / 256);
     if (blocks > num_sms() * 8) blocks = num_sms() * 8;
@@ -534,15 +566,9 @@ __global__ void k_lloyd_update(CandBatch b, int d, KmState st, int pass, int las
         const int cnt = st.counts[off + j];
         if (cnt <= 0) continue;
         const double inv = 1.0 / ((double)cnt * FIXED_SCALE);
-        float s = 0.f;
-        for (int k = 0; k < d; ++k) {
-            const float v = (float)((double)st.sums[(int64_t)(off + j) * d + k] * inv);
-            st.mu[(int64_t)(off + j) * d + k] = v;
-            split_bf16(v, st.bhi + (int64_t)(off + j) * d + k, st.blo + (int64_t)(off + j) * d + k);
-            s = fmaf(v, v, s);
-        }
-        st.norm2[off + j] = s;
-        st.norm2p[off + j] = s + 4.0f;
+        for (int k = 0; k < d; ++k)
+            st.mu[(int64_t)(off + j) * d + k] = (float)((double)st.sums[(int64_t)(off + j) * d + k] * inv);
+        write_row_operands(st, off + j, d, false);
     }
 }
 
