@@ -325,17 +325,20 @@ static raftgp_status run_lloyd(const CandBatch& b, const void* Z, int zdtype, in
     return RAFTGP_OK;
 }
 
-// Splits the candidates of a batch between the two tensor-core epilogue groups, largest K
-// first onto the lighter group.
+// Splits the candidates of a batch between the tensor-core epilogue groups, largest K first
+// onto the lightest group.
 static void assign_owners(CandBatch& b) {
-    long long load[2] = {0, 0};
+    constexpr int G = 4;
+    long long load[G] = {0, 0, 0, 0};
     bool done[MAXC] = {};
     for (int r = 0; r < b.n; ++r) {
         int pick = -1;
         for (int c = 0; c < b.n; ++c)
             if (!done[c] && (pick < 0 || b.k[c] > b.k[pick])) pick = c;
         done[pick] = true;
-        const int g = load[0] <= load[1] ? 0 : 1;
+        int g = 0;
+        for (int h = 1; h < G; ++h)
+            if (load[h] < load[g]) g = h;
         b.owner[pick] = g;
         load[g] += b.k[pick];
     }

@@ -51,7 +51,8 @@ struct TcCfg {
 
 constexpr int TC_MAX_CHUNKS = 512;
 constexpr int TC_MAX_SLICES = 2048;
-constexpr int TC_THREADS = 320;   // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue (two groups of 4)
+constexpr int TC_GROUPS = 4;                          // epilogue warpgroups
+constexpr int TC_THREADS = 64 + TC_GROUPS * 128;      // warp 0 TMA, warp 1 MMA, then the epilogue groups
 
 struct TcCtl {
     uint64_t a_full, a_empty;
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         for (int q = 0; q < 2; ++q) {
             mbar_init(&ctl.acc_full[q], 1);
-            mbar_init(&ctl.acc_empty[q], 256);
+            mbar_init(&ctl.acc_empty[q], TC_GROUPS * 128);
         }
         mbar_init(&ctl.drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -355,7 +356,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_drain(&ctl.drain, 0);
         }
     } else {
-        // ---------------- epilogue (warps 2..9: two groups, each owning whole candidates) -----
+        // ---------------- epilogue (warps 2.., groups of 4 warps, each owning whole candidates) --
         const int wg = (warp - 2) >> 2;               // epilogue group
         const int quarter = warp & 3;                 // TMEM lanes this warp may access
         const int row = quarter * 32 + lane;
@@ -382,27 +383,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     if (a.final_mode) {
                         // exact best and second best of ||mu||^2 + 4 - 2 z.mu (FP32 norms; padding
                         // columns carry an infinite norm and never win)
-                        float np4[64];
 #pragma unroll
-                        for (int v = 0; v < 16; ++v) {
-                            const float4 t4 = __ldg(reinterpret_cast<const float4*>(a.st.norm2p + col0) + v);
-                            np4[4 * v] = t4.x; np4[4 * v + 1] = t4.y; np4[4 * v + 2] = t4.z; np4[4 * v + 3] = t4.w;
-                        }
+                        for (int v = 0; v < 4; ++v) {
+                            float np4[16];
 #pragma unroll
-                        for (int k = 0; k < 64; ++k) {
-                            const float sc = fmaf(2.0f, __uint_as_float(r[k]), np4[k]);
-                            if (sc < bv) { b2 = bv; bv = sc; bi = col0 + k; } else { b2 = fminf(b2, sc); }
+                            for (int u = 0; u < 4; ++u) {
+                                const float4 t4 = __ldg(reinterpret_cast<const float4*>(a.st.norm2p + col0) + 4 * v + u);
+                                np4[4 * u] = t4.x; np4[4 * u + 1] = t4.y; np4[4 * u + 2] = t4.z; np4[4 * u + 3] = t4.w;
+                            }
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) {
+                                const float sc = fmaf(2.0f, __uint_as_float(r[16 * v + k]), np4[k]);
+                                if (sc < bv) { b2 = bv; bv = sc; bi = col0 + 16 * v + k; } else { b2 = fminf(b2, sc); }
+                            }
                         }
                     } else {
                         // packed keys: the positive score with its low 6 bits replaced by the column
-                        // within the slice; one float minimum gives value and column together
-                        float kmin = INFINITY;
+                        // within the slice; a float minimum gives value and column together (four
+                        // independent chains, merged at the end)
+                        float m0 = INFINITY, m1 = INFINITY, m2 = INFINITY, m3 = INFINITY;
 #pragma unroll
-                        for (int k = 0; k < 64; k += 2) {
-                            const float k0 = __uint_as_float((r[k] & 0xFFFFFFC0u) | (uint32_t)k);
-                            const float k1 = __uint_as_float((r[k + 1] & 0xFFFFFFC0u) | (uint32_t)(k + 1));
-                            kmin = min3f(kmin, k0, k1);
+                        for (int k = 0; k < 64; k += 8) {
+                            m0 = min3f(m0, __uint_as_float((r[k] & 0xFFFFFFC0u) | (uint32_t)k),
+                                       __uint_as_float((r[k + 1] & 0xFFFFFFC0u) | (uint32_t)(k + 1)));
+                            m1 = min3f(m1, __uint_as_float((r[k + 2] & 0xFFFFFFC0u) | (uint32_t)(k + 2)),
+                                       __uint_as_float((r[k + 3] & 0xFFFFFFC0u) | (uint32_t)(k + 3)));
+                            m2 = min3f(m2, __uint_as_float((r[k + 4] & 0xFFFFFFC0u) | (uint32_t)(k + 4)),
+                                       __uint_as_float((r[k + 5] & 0xFFFFFFC0u) | (uint32_t)(k + 5)));
+                            m3 = min3f(m3, __uint_as_float((r[k + 6] & 0xFFFFFFC0u) | (uint32_t)(k + 6)),
+                                       __uint_as_float((r[k + 7] & 0xFFFFFFC0u) | (uint32_t)(k + 7)));
                         }
+                        const float kmin = fminf(min3f(m0, m1, m2), m3);
                         const uint32_t kb = __float_as_uint(kmin);
                         const float v = __uint_as_float(kb & 0xFFFFFFC0u);
                         if (v < bv) { bv = v; bi = col0 + (int)(kb & 63u); }
