@@ -33,39 +33,40 @@ struct TcCfg {
     static constexpr int ATOM = D < 64 ? D : 64;          // K elements per swizzle-atom row
     static constexpr int ATOM_BYTES = ATOM * 2;           // 64 or 128
     static constexpr int NATOM = D / ATOM;
-    static constexpr int NCH = D == 128 ? 128 : (D == 64 ? 192 : 256);  // centroids per chunk = MMA N
-    static constexpr int STAGES = D == 128 ? 2 : (D == 64 ? 3 : 4);
+    static constexpr int NCH = 64;                        // centroids per chunk = MMA N = one slice
+    static constexpr int GROUPS = 4;                      // point tiles per CTA step, one per epilogue group
+    static constexpr int A_BUFS = D == 128 ? 1 : 2;       // point-tile groups in flight
+    static constexpr int STAGES = D == 128 ? 2 : (D == 64 ? 4 : 6);
     static constexpr int A_ATOM_BYTES = 128 * ATOM_BYTES;
-    static constexpr int A_BYTES = NATOM * A_ATOM_BYTES;
-    static constexpr int AUG_A_BYTES = 128 * 32;          // the constant K=16 slice of the point tile
+    static constexpr int A_TILE_BYTES = NATOM * A_ATOM_BYTES;     // one 128-point tile
+    static constexpr int A_BYTES = GROUPS * A_TILE_BYTES;         // one group of tiles
+    static constexpr int AUG_A_BYTES = 128 * 32;          // the constant K=16 slice of a point tile
     static constexpr int B_ATOM_BYTES = NCH * ATOM_BYTES;
     static constexpr int B_BYTES = NATOM * B_ATOM_BYTES;  // one half (hi or lo) of a chunk
     static constexpr int AUG_B_BYTES = NCH * 32;          // the K=16 norm slice of a chunk
     static constexpr int STAGE_BYTES = 2 * B_BYTES + AUG_B_BYTES;
     static constexpr int LAYOUT = ATOM_BYTES == 128 ? 2 : 4;  // descriptor swizzle: 128B or 64B
     static constexpr int SBO = 8 * ATOM_BYTES;                 // stride between 8-row groups
-    static constexpr int SMEM = 1024 + A_BYTES + AUG_A_BYTES + STAGES * STAGE_BYTES;
+    static constexpr int SMEM = 1024 + A_BUFS * A_BYTES + AUG_A_BYTES + STAGES * STAGE_BYTES;
     static_assert(SMEM <= 227 * 1024, "shared memory budget");
-    static_assert(NCH % 64 == 0 && 2 * NCH <= 512, "chunk must be whole slices and fit two TMEM buffers");
+    static_assert(GROUPS * 2 * NCH <= 512, "two accumulator buffers per group must fit tensor memory");
 };
 
-constexpr int TC_MAX_CHUNKS = 512;
-constexpr int TC_MAX_SLICES = 2048;
+constexpr int TC_MAX_CHUNKS = 2048;
 constexpr int TC_GROUPS = 4;                          // epilogue warpgroups
 constexpr int TC_THREADS = 64 + TC_GROUPS * 128;      // warp 0 TMA, warp 1 MMA, then the epilogue groups
 
 struct TcCtl {
-    uint64_t a_full, a_empty;
-    uint64_t b_full[4], b_empty[4];
-    uint64_t acc_full[2], acc_empty[2];
+    uint64_t a_full[2], a_empty[2];
+    uint64_t b_full[8], b_empty[8];
+    uint64_t acc_full[TC_GROUPS][2], acc_empty[TC_GROUPS][2];
     uint64_t drain;
     uint32_t tmem_base;
     int abort;
     int nchunks;
     int chunk_col[TC_MAX_CHUNKS];
-    // per 64-column slice of the chunk list: candidate index + 128 if the candidate's padded
-    // range ends with this slice, or -1 (no active candidate / beyond the batch)
-    int16_t slice[TC_MAX_SLICES];
+    // candidate of each chunk + 128 if the candidate's padded range ends with the chunk
+    int16_t chunk_info[TC_MAX_CHUNKS];
 };
 
 // ---------------------------------------------------------------------------------------
@@ -216,42 +217,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     extern __shared__ uint8_t dyn_smem[];
     __shared__ TcCtl ctl;
     uint8_t* base = (uint8_t*)(((uintptr_t)dyn_smem + 1023) & ~(uintptr_t)1023);
-    uint8_t* sA = base;
-    uint8_t* sAug = base + C::A_BYTES;                 // 128 rows x 32 B, constant
+    uint8_t* sA = base;                                   // A_BUFS groups of GROUPS point tiles
+    uint8_t* sAug = base + C::A_BUFS * C::A_BYTES;        // 128 rows x 32 B, constant
     uint8_t* sB = sAug + C::AUG_A_BYTES;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const CandBatch& b = a.b;
-    const int nslice_chunk = C::NCH / 64;
 
     if (threadIdx.x == 0) {
         ctl.abort = 0;
-        mbar_init(&ctl.a_full, 1);
-        mbar_init(&ctl.a_empty, 1);
+        for (int q = 0; q < C::A_BUFS; ++q) {
+            mbar_init(&ctl.a_full[q], 1);
+            mbar_init(&ctl.a_empty[q], 1);
+        }
         for (int s = 0; s < C::STAGES; ++s) {
             mbar_init(&ctl.b_full[s], 1);
             mbar_init(&ctl.b_empty[s], 1);
         }
-        for (int q = 0; q < 2; ++q) {
-            mbar_init(&ctl.acc_full[q], 1);
-            mbar_init(&ctl.acc_empty[q], TC_GROUPS * 128);
-        }
+        for (int g = 0; g < TC_GROUPS; ++g)
+            for (int q = 0; q < 2; ++q) {
+                mbar_init(&ctl.acc_full[g][q], 1);
+                mbar_init(&ctl.acc_empty[g][q], 128);
+            }
         mbar_init(&ctl.drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        // chunks holding at least one column of an active candidate (FINAL: every candidate),
-        // by walking candidates and chunks together
-        int nch = 0, c = 0;
-        const int total_chunks = (b.total_k + C::NCH - 1) / C::NCH;
-        for (int q = 0; q < total_chunks && nch < TC_MAX_CHUNKS; ++q) {
-            const int lo = q * C::NCH, hi = lo + C::NCH;
-            while (c < b.n && b.off[c] + b.k[c] <= lo) ++c;
-            bool need = false;
-            for (int c2 = c; c2 < b.n && b.off[c2] < hi && !need; ++c2)
-                need = a.final_mode || a.st.active[c2];
-            if (need) ctl.chunk_col[nch++] = lo;
+        // 64-column chunks holding columns of an active candidate (FINAL: every candidate);
+        // candidates are padded to whole chunks, so each chunk belongs to one candidate
+        int nch = 0;
+        for (int c = 0; c < b.n; ++c) {
+            if (!(a.final_mode || a.st.active[c])) continue;
+            const int pad_end = c + 1 < b.n ? b.off[c + 1] : b.total_k;
+            for (int col = b.off[c]; col < b.off[c] + b.k[c] && nch < TC_MAX_CHUNKS; col += C::NCH) {
+                ctl.chunk_col[nch] = col;
+                ctl.chunk_info[nch] = (int16_t)(c + (col + C::NCH >= pad_end ? 128 : 0));
+                ++nch;
+            }
         }
         ctl.nchunks = nch;
     }
-    // constant K=16 slice of the point tile: every row reads 1, 1 at K = 0, 1 (and again at 8, 9,
+    // constant K=16 slice of a point tile: every row reads 1, 1 at K = 0, 1 (and again at 8, 9,
     // so the row is the same under the 32-byte swizzle, which may exchange its two halves)
     for (int t = threadIdx.x; t < C::AUG_A_BYTES / 16; t += blockDim.x)
         reinterpret_cast<uint4*>(sAug)[t] = make_uint4(0x3F803F80u, 0u, 0u, 0u);
@@ -265,31 +268,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = ctl.tmem_base;
     const int nchunks = ctl.nchunks;
-    // slice table (all threads): candidate of each 64-column slice and whether it ends there
-    for (int e = threadIdx.x; e < nchunks * nslice_chunk && e < TC_MAX_SLICES; e += blockDim.x) {
-        const int col0 = ctl.chunk_col[e / nslice_chunk] + (e % nslice_chunk) * 64;
-        int v = -1;
-        if (col0 < b.total_k) {
-            int c = 0;
-            while (c + 1 < b.n && b.off[c + 1] <= col0) ++c;
-            const int pad_end = c + 1 < b.n ? b.off[c + 1] : b.total_k;
-            if (col0 < b.off[c] + b.k[c] && (a.final_mode || a.st.active[c])) v = c + (col0 + 64 >= pad_end ? 128 : 0);
-        }
-        ctl.slice[e] = (int16_t)v;
-    }
-    __syncthreads();
-    const int64_t ntiles = (a.n + 127) / 128;
+    const int64_t nsteps = (a.n + 128 * C::GROUPS - 1) / (128 * C::GROUPS);   // groups of 4 tiles
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
         if (lane == 0 && nchunks > 0) {
             int it = 0, tl = 0;
             bool ok = true;
-            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tl) {
-                if (!(ok = mbar_wait(&ctl.a_empty, (tl & 1) ^ 1, &ctl, a.err))) break;
-                mbar_expect_tx(&ctl.a_full, C::A_BYTES);
-                for (int t = 0; t < C::NATOM; ++t)
-                    tma_load_2d(sA + t * C::A_ATOM_BYTES, &tmA, &ctl.a_full, t * C::ATOM, (int)(tile * 128));
+            for (int64_t step = blockIdx.x; step < nsteps && ok; step += gridDim.x, ++tl) {
+                const int ab = tl % C::A_BUFS;
+                if (!(ok = mbar_wait(&ctl.a_empty[ab], ((tl / C::A_BUFS) & 1) ^ 1, &ctl, a.err))) break;
+                mbar_expect_tx(&ctl.a_full[ab], C::A_BYTES);
+                for (int g = 0; g < C::GROUPS; ++g)
+                    for (int t = 0; t < C::NATOM; ++t)
+                        tma_load_2d(sA + ab * C::A_BYTES + g * C::A_TILE_BYTES + t * C::A_ATOM_BYTES, &tmA,
+                                    &ctl.a_full[ab], t * C::ATOM, (int)((step * C::GROUPS + g) * 128));
                 for (int q = 0; q < nchunks; ++q, ++it) {
                     const int s = it % C::STAGES;
                     if (!(ok = mbar_wait(&ctl.b_empty[s], ((it / C::STAGES) & 1) ^ 1, &ctl, a.err))) break;
@@ -305,166 +298,165 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             if (!ok) {
                 // let the copies already issued land before the CTA can exit
-                const int last = it;
-                for (int k = (last > C::STAGES ? last - C::STAGES : 0); k < last; ++k)
+                for (int k = (it > C::STAGES ? it - C::STAGES : 0); k < it; ++k)
                     mbar_drain(&ctl.b_full[k % C::STAGES], (k / C::STAGES) & 1);
-                mbar_drain(&ctl.a_full, (tl & 1));
+                for (int k = (tl > C::A_BUFS ? tl - C::A_BUFS : 0); k <= tl; ++k)
+                    mbar_drain(&ctl.a_full[k % C::A_BUFS], (k / C::A_BUFS) & 1);
             }
         }
     } else if (warp == 1) {
         // ---------------- MMA issuer ----------------
         if (lane == 0 && nchunks > 0) {
             const uint32_t idesc = instr_desc(C::NCH);
+            const uint64_t aug_a = smem_desc(smem_addr(sAug), 6, 256);
             int it = 0, tl = 0;
             bool ok = true;
-            const uint64_t aug_a = smem_desc(smem_addr(sAug), 6, 256);
-            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tl) {
-                if (!(ok = mbar_wait(&ctl.a_full, tl & 1, &ctl, a.err))) break;
+            for (int64_t step = blockIdx.x; step < nsteps && ok; step += gridDim.x, ++tl) {
+                const int ab = tl % C::A_BUFS;
+                if (!(ok = mbar_wait(&ctl.a_full[ab], (tl / C::A_BUFS) & 1, &ctl, a.err))) break;
                 tc_fence_after();
-                for (int q = 0; q < nchunks; ++q, ++it) {
+                const uint32_t a_grp = smem_addr(sA + ab * C::A_BYTES);
+                for (int q = 0; q < nchunks && ok; ++q, ++it) {
                     const int s = it % C::STAGES;
                     const int buf = it & 1;
                     if (!(ok = mbar_wait(&ctl.b_full[s], (it / C::STAGES) & 1, &ctl, a.err))) break;
-                    if (!(ok = mbar_wait(&ctl.acc_empty[buf], ((it >> 1) & 1) ^ 1, &ctl, a.err))) break;
-                    tc_fence_after();
-                    const uint32_t dcol = tmem + (uint32_t)(buf * C::NCH);
                     const uint32_t bhi = smem_addr(sB + s * C::STAGE_BYTES);
                     const uint32_t blo = bhi + C::B_BYTES;
-                    const uint32_t a0 = smem_addr(sA);
-                    int first = 1;
-                    // -z.mu from the BF16 hi and lo halves of -mu
-                    for (int half = 0; half < 2; ++half) {
-                        const uint32_t bb = half ? blo : bhi;
-                        for (int t = 0; t < C::NATOM; ++t)
-                            for (int k = 0; k < C::ATOM / 16; ++k) {
-                                const uint64_t ad = smem_desc(a0 + t * C::A_ATOM_BYTES + k * 32, C::LAYOUT, C::SBO);
-                                const uint64_t bd = smem_desc(bb + t * C::B_ATOM_BYTES + k * 32, C::LAYOUT, C::SBO);
-                                mma_bf16(dcol, ad, bd, idesc, first ? 0 : 1);
-                                first = 0;
-                            }
+                    for (int g = 0; g < C::GROUPS && ok; ++g) {
+                        if (!(ok = mbar_wait(&ctl.acc_empty[g][buf], ((it >> 1) & 1) ^ 1, &ctl, a.err))) break;
+                        tc_fence_after();
+                        const uint32_t dcol = tmem + (uint32_t)(g * 2 * C::NCH + buf * C::NCH);
+                        const uint32_t a0 = a_grp + g * C::A_TILE_BYTES;
+                        int first = 1;
+                        // -z.mu from the BF16 hi and lo halves of -mu
+                        for (int half = 0; half < 2; ++half) {
+                            const uint32_t bb = half ? blo : bhi;
+                            for (int t = 0; t < C::NATOM; ++t)
+                                for (int k = 0; k < C::ATOM / 16; ++k) {
+                                    const uint64_t ad = smem_desc(a0 + t * C::A_ATOM_BYTES + k * 32, C::LAYOUT, C::SBO);
+                                    const uint64_t bd = smem_desc(bb + t * C::B_ATOM_BYTES + k * 32, C::LAYOUT, C::SBO);
+                                    mma_bf16(dcol, ad, bd, idesc, first ? 0 : 1);
+                                    first = 0;
+                                }
+                        }
+                        // FAST: + (||mu||^2 + 4)/2 from the constant slice, so the accumulator is
+                        // the positive score (||z - mu||^2 - ||z||^2 + 4)/2 itself
+                        if (!a.final_mode) mma_bf16(dcol, aug_a, smem_desc(bhi + 2 * C::B_BYTES, 6, 256), idesc, 1);
+                        mma_commit(&ctl.acc_full[g][buf]);  // this group's accumulator is ready
                     }
-                    // FAST: + (||mu||^2 + 4)/2 from the constant slice, so the accumulator is the
-                    // positive score (||z - mu||^2 - ||z||^2 + 4)/2 itself
-                    if (!a.final_mode) mma_bf16(dcol, aug_a, smem_desc(bhi + 2 * C::B_BYTES, 6, 256), idesc, 1);
-                    mma_commit(&ctl.b_empty[s]);        // the stage is free once these MMAs retire
-                    mma_commit(&ctl.acc_full[buf]);     // the accumulator is ready for the epilogue
+                    if (ok) mma_commit(&ctl.b_empty[s]);  // the stage is free once these MMAs retire
                 }
-                if (ok) mma_commit(&ctl.a_empty);       // the point tile is free after its last chunk
+                if (ok) mma_commit(&ctl.a_empty[ab]);     // the point tiles are free after the last chunk
             }
             // wait for every MMA issued by this thread before tensor memory is released
             mma_commit(&ctl.drain);
             mbar_drain(&ctl.drain, 0);
         }
     } else {
-        // ---------------- epilogue (warps 2.., groups of 4 warps, each owning whole candidates) --
+        // ---------------- epilogue: group wg owns point tile wg of each step ----------------
         const int wg = (warp - 2) >> 2;               // epilogue group
         const int quarter = warp & 3;                 // TMEM lanes this warp may access
         const int row = quarter * 32 + lane;
-        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(wg * 2 * C::NCH);
         int it = 0;
         bool ok = nchunks > 0;
-        for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-            const int64_t i = tile * 128 + row;
+        for (int64_t step = blockIdx.x; step < nsteps && ok; step += gridDim.x) {
+            const int64_t i = (step * C::GROUPS + wg) * 128 + row;
             const bool valid = i < a.n;
             float bv = INFINITY, b2 = INFINITY;
             int bi = -1;
             for (int q = 0; q < nchunks; ++q, ++it) {
                 const int buf = it & 1;
-                if (!(ok = mbar_wait(&ctl.acc_full[buf], (it >> 1) & 1, &ctl, a.err))) break;
+                if (!(ok = mbar_wait(&ctl.acc_full[wg][buf], (it >> 1) & 1, &ctl, a.err))) break;
                 tc_fence_after();
-                for (int sl = 0; sl < nslice_chunk; ++sl) {
-                    const int info = ctl.slice[q * nslice_chunk + sl];
-                    if (info < 0) continue;
-                    const int cand = info & 127;
-                    if (b.owner[cand] != wg) continue;
-                    const int col0 = ctl.chunk_col[q] + sl * 64;
-                    uint32_t r[64];
-                    tmem_ld64(lane_base + (uint32_t)(buf * C::NCH + sl * 64), r);
-                    if (a.final_mode) {
-                        // exact best and second best of ||mu||^2 + 4 - 2 z.mu (FP32 norms; padding
-                        // columns carry an infinite norm and never win)
-#pragma unroll
-                        for (int v = 0; v < 4; ++v) {
-                            float np4[16];
-#pragma unroll
-                            for (int u = 0; u < 4; ++u) {
-                                const float4 t4 = __ldg(reinterpret_cast<const float4*>(a.st.norm2p + col0) + 4 * v + u);
-                                np4[4 * u] = t4.x; np4[4 * u + 1] = t4.y; np4[4 * u + 2] = t4.z; np4[4 * u + 3] = t4.w;
-                            }
-#pragma unroll
-                            for (int k = 0; k < 16; ++k) {
-                                const float sc = fmaf(2.0f, __uint_as_float(r[16 * v + k]), np4[k]);
-                                if (sc < bv) { b2 = bv; bv = sc; bi = col0 + 16 * v + k; } else { b2 = fminf(b2, sc); }
-                            }
-                        }
-                    } else {
-                        // packed keys: the positive score with its low 6 bits replaced by the column
-                        // within the slice; a float minimum gives value and column together (four
-                        // independent chains, merged at the end)
-                        float m0 = INFINITY, m1 = INFINITY, m2 = INFINITY, m3 = INFINITY;
-#pragma unroll
-                        for (int k = 0; k < 64; k += 8) {
-                            m0 = min3f(m0, __uint_as_float((r[k] & 0xFFFFFFC0u) | (uint32_t)k),
-                                       __uint_as_float((r[k + 1] & 0xFFFFFFC0u) | (uint32_t)(k + 1)));
-                            m1 = min3f(m1, __uint_as_float((r[k + 2] & 0xFFFFFFC0u) | (uint32_t)(k + 2)),
-                                       __uint_as_float((r[k + 3] & 0xFFFFFFC0u) | (uint32_t)(k + 3)));
-                            m2 = min3f(m2, __uint_as_float((r[k + 4] & 0xFFFFFFC0u) | (uint32_t)(k + 4)),
-                                       __uint_as_float((r[k + 5] & 0xFFFFFFC0u) | (uint32_t)(k + 5)));
-                            m3 = min3f(m3, __uint_as_float((r[k + 6] & 0xFFFFFFC0u) | (uint32_t)(k + 6)),
-                                       __uint_as_float((r[k + 7] & 0xFFFFFFC0u) | (uint32_t)(k + 7)));
-                        }
-                        const float kmin = fminf(min3f(m0, m1, m2), m3);
-                        const uint32_t kb = __float_as_uint(kmin);
-                        const float v = __uint_as_float(kb & 0xFFFFFFC0u);
-                        if (v < bv) { bv = v; bi = col0 + (int)(kb & 63u); }
-                    }
-                    if (info < 128) continue;          // the candidate continues in a later slice
-                    // ---- candidate finished for this tile: label, change, sums ----
-                    const int K = b.k[cand], off = b.off[cand];
-                    int nl = bi - off;
-                    if (nl < 0 || nl >= K) nl = 0;   // non-finite scores: keep indices in range
-                    int ol = -1;
-                    if (valid) {
-                        int16_t* lp = a.st.labels + i * b.cs + cand;
-                        ol = *lp;
-                        *lp = (int16_t)nl;
-                    }
-                    if (a.final_mode) {
-                        if (valid && !(b2 - bv > a.tie_band)) {
-                            const int slot = atomicAdd(a.recheck_count, 1);
-                            a.recheck[slot] = make_int2((int)i, cand);
-                        }
-                    } else {
-                        const bool ch = valid && nl != ol;
-                        unsigned mask = __ballot_sync(0xffffffffu, ch);
-                        if (lane == 0 && mask) atomicAdd(a.st.changed + (a.pass & 1) * MAXC + cand, __popc(mask));
-                        if (ch) {
-                            atomicAdd(a.st.counts + off + nl, 1);
-                            if (ol >= 0) atomicSub(a.st.counts + off + ol, 1);
-                        }
-                        while (mask) {
-                            const int src = __ffs(mask) - 1;
-                            mask &= mask - 1;
-                            const int64_t pi = __shfl_sync(0xffffffffu, i, src);
-                            const int pn = __shfl_sync(0xffffffffu, nl, src);
-                            const int po = __shfl_sync(0xffffffffu, ol, src);
-                            for (int k = lane; k < D; k += 32) {
-                                const long long v =
-                                    __float2ll_rn(__bfloat162float(a.Z[pi * D + k]) * FIXED_SCALE_F);
-                                atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + pn) * D + k),
-                                          (unsigned long long)v);
-                                if (po >= 0)
-                                    atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + po) * D + k),
-                                              (unsigned long long)(-v));
-                            }
-                        }
-                    }
-                    bv = INFINITY;
-                    b2 = INFINITY;
-                    bi = -1;
-                }
+                const int info = ctl.chunk_info[q];
+                const int cand = info & 127;
+                const int col0 = ctl.chunk_col[q];
+                uint32_t r[64];
+                tmem_ld64(lane_base + (uint32_t)(buf * C::NCH), r);
                 tc_fence_before();
-                mbar_arrive(&ctl.acc_empty[buf]);
+                mbar_arrive(&ctl.acc_empty[wg][buf]);   // registers hold the chunk: the buffer is free
+                if (a.final_mode) {
+                    // exact best and second best of ||mu||^2 + 4 - 2 z.mu (FP32 norms; padding
+                    // columns carry an infinite norm and never win)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        float np4[16];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float4 t4 = __ldg(reinterpret_cast<const float4*>(a.st.norm2p + col0) + 4 * v + u);
+                            np4[4 * u] = t4.x; np4[4 * u + 1] = t4.y; np4[4 * u + 2] = t4.z; np4[4 * u + 3] = t4.w;
+                        }
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) {
+                            const float sc = fmaf(2.0f, __uint_as_float(r[16 * v + k]), np4[k]);
+                            if (sc < bv) { b2 = bv; bv = sc; bi = col0 + 16 * v + k; } else { b2 = fminf(b2, sc); }
+                        }
+                    }
+                } else {
+                    // packed keys: the positive score with its low 6 bits replaced by the column
+                    // within the chunk; a float minimum gives value and column together (four
+                    // independent chains, merged at the end)
+                    float m0 = INFINITY, m1 = INFINITY, m2 = INFINITY, m3 = INFINITY;
+#pragma unroll
+                    for (int k = 0; k < 64; k += 8) {
+                        m0 = min3f(m0, __uint_as_float((r[k] & 0xFFFFFFC0u) | (uint32_t)k),
+                                   __uint_as_float((r[k + 1] & 0xFFFFFFC0u) | (uint32_t)(k + 1)));
+                        m1 = min3f(m1, __uint_as_float((r[k + 2] & 0xFFFFFFC0u) | (uint32_t)(k + 2)),
+                                   __uint_as_float((r[k + 3] & 0xFFFFFFC0u) | (uint32_t)(k + 3)));
+                        m2 = min3f(m2, __uint_as_float((r[k + 4] & 0xFFFFFFC0u) | (uint32_t)(k + 4)),
+                                   __uint_as_float((r[k + 5] & 0xFFFFFFC0u) | (uint32_t)(k + 5)));
+                        m3 = min3f(m3, __uint_as_float((r[k + 6] & 0xFFFFFFC0u) | (uint32_t)(k + 6)),
+                                   __uint_as_float((r[k + 7] & 0xFFFFFFC0u) | (uint32_t)(k + 7)));
+                    }
+                    const float kmin = fminf(min3f(m0, m1, m2), m3);
+                    const uint32_t kb = __float_as_uint(kmin);
+                    const float v = __uint_as_float(kb & 0xFFFFFFC0u);
+                    if (v < bv) { bv = v; bi = col0 + (int)(kb & 63u); }
+                }
+                if (info < 128) continue;              // the candidate continues in a later chunk
+                // ---- candidate finished for this tile: label, change, sums ----
+                const int K = b.k[cand], off = b.off[cand];
+                int nl = bi - off;
+                if (nl < 0 || nl >= K) nl = 0;       // non-finite scores: keep indices in range
+                int ol = -1;
+                if (valid) {
+                    int16_t* lp = a.st.labels + i * b.cs + cand;
+                    ol = *lp;
+                    *lp = (int16_t)nl;
+                }
+                if (a.final_mode) {
+                    if (valid && !(b2 - bv > a.tie_band)) {
+                        const int slot = atomicAdd(a.recheck_count, 1);
+                        a.recheck[slot] = make_int2((int)i, cand);
+                    }
+                } else {
+                    const bool ch = valid && nl != ol;
+                    unsigned mask = __ballot_sync(0xffffffffu, ch);
+                    if (lane == 0 && mask) atomicAdd(a.st.changed + (a.pass & 1) * MAXC + cand, __popc(mask));
+                    if (ch) {
+                        atomicAdd(a.st.counts + off + nl, 1);
+                        if (ol >= 0) atomicSub(a.st.counts + off + ol, 1);
+                    }
+                    while (mask) {
+                        const int src = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        const int64_t pi = __shfl_sync(0xffffffffu, i, src);
+                        const int pn = __shfl_sync(0xffffffffu, nl, src);
+                        const int po = __shfl_sync(0xffffffffu, ol, src);
+                        for (int k = lane; k < D; k += 32) {
+                            const long long v = __float2ll_rn(__bfloat162float(a.Z[pi * D + k]) * FIXED_SCALE_F);
+                            atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + pn) * D + k),
+                                      (unsigned long long)v);
+                            if (po >= 0)
+                                atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + po) * D + k),
+                                          (unsigned long long)(-v));
+                        }
+                    }
+                }
+                bv = INFINITY;
+                b2 = INFINITY;
+                bi = -1;
             }
         }
     }
@@ -572,8 +564,8 @@ static cudaError_t launch_tc_t(const CandBatch& b, const __nv_bfloat16* Z, int64
     const int smem = C::SMEM;
     auto kern = k_assign_tc<D>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
-    const int64_t ntiles = (n + 127) / 128;
-    const int grid = (int)(ntiles < num_sms() ? ntiles : num_sms());
+    const int64_t nsteps = (n + 128 * C::GROUPS - 1) / (128 * C::GROUPS);
+    const int grid = (int)(nsteps < num_sms() ? nsteps : num_sms());
     {
         ProfScope ps(s, final_mode ? PF_ASSIGN_TC_FINAL : (pass == 1 ? PF_ASSIGN_TC_FIRST : PF_ASSIGN_TC), 1);
         kern<<<grid, TC_THREADS, smem, s>>>(a, ta, th, tl, tg);
@@ -583,8 +575,8 @@ static cudaError_t launch_tc_t(const CandBatch& b, const __nv_bfloat16* Z, int64
 
 cudaError_t launch_assign_tc(const CandBatch& b, const void* Z, int64_t n, int d, KmState st, int pass, int final_mode,
                              int2* recheck, int* recheck_count, uint32_t* err, cudaStream_t s) {
-    // the chunk and slice tables hold every column of the batch
-    if (b.total_k > TC_MAX_SLICES * 64 || b.total_k > TC_MAX_CHUNKS * 128) return cudaErrorInvalidValue;
+    // the chunk table holds every 64-column chunk of the batch
+    if (b.total_k > TC_MAX_CHUNKS * 64) return cudaErrorInvalidValue;
     const __nv_bfloat16* z = (const __nv_bfloat16*)Z;
     switch (d) {
         case 32: return launch_tc_t<32>(b, z, n, st, pass, final_mode, recheck, recheck_count, err, s);
