@@ -308,40 +308,46 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ---------------- MMA issuer ----------------
         if (lane == 0 && nchunks > 0) {
             const uint32_t idesc = instr_desc(C::NCH);
-            const uint64_t aug_a = smem_desc(smem_addr(sAug), 6, 256);
+            // descriptors of the region bases; each operand adds its byte offset / 16 to the start
+            // address field (every address stays below 256 KB, so the field never overflows)
+            const uint64_t dA = smem_desc(smem_addr(sA), C::LAYOUT, C::SBO);
+            const uint64_t dB = smem_desc(smem_addr(sB), C::LAYOUT, C::SBO);
+            const uint64_t dAugA = smem_desc(smem_addr(sAug), 6, 256);
+            const uint64_t dAugB = smem_desc(smem_addr(sB + 2 * C::B_BYTES), 6, 256);
             int it = 0, tl = 0;
             bool ok = true;
             for (int64_t step = blockIdx.x; step < nsteps && ok; step += gridDim.x, ++tl) {
                 const int ab = tl % C::A_BUFS;
                 if (!(ok = mbar_wait(&ctl.a_full[ab], (tl / C::A_BUFS) & 1, &ctl, a.err))) break;
                 tc_fence_after();
-                const uint32_t a_grp = smem_addr(sA + ab * C::A_BYTES);
+                const uint64_t dAgrp = dA + (uint64_t)((ab * C::A_BYTES) >> 4);
                 for (int q = 0; q < nchunks && ok; ++q, ++it) {
                     const int s = it % C::STAGES;
                     const int buf = it & 1;
                     if (!(ok = mbar_wait(&ctl.b_full[s], (it / C::STAGES) & 1, &ctl, a.err))) break;
-                    const uint32_t bhi = smem_addr(sB + s * C::STAGE_BYTES);
-                    const uint32_t blo = bhi + C::B_BYTES;
-                    for (int g = 0; g < C::GROUPS && ok; ++g) {
+                    const uint64_t dBst = dB + (uint64_t)((s * C::STAGE_BYTES) >> 4);
+                    const uint64_t dAugBst = dAugB + (uint64_t)((s * C::STAGE_BYTES) >> 4);
+#pragma unroll
+                    for (int g = 0; g < C::GROUPS; ++g) {
                         if (!(ok = mbar_wait(&ctl.acc_empty[g][buf], ((it >> 1) & 1) ^ 1, &ctl, a.err))) break;
                         tc_fence_after();
                         const uint32_t dcol = tmem + (uint32_t)(g * 2 * C::NCH + buf * C::NCH);
-                        const uint32_t a0 = a_grp + g * C::A_TILE_BYTES;
-                        int first = 1;
+                        const uint64_t dAg = dAgrp + (uint64_t)((g * C::A_TILE_BYTES) >> 4);
                         // -z.mu from the BF16 hi and lo halves of -mu
-                        for (int half = 0; half < 2; ++half) {
-                            const uint32_t bb = half ? blo : bhi;
+#pragma unroll
+                        for (int half = 0; half < 2; ++half)
+#pragma unroll
                             for (int t = 0; t < C::NATOM; ++t)
+#pragma unroll
                                 for (int k = 0; k < C::ATOM / 16; ++k) {
-                                    const uint64_t ad = smem_desc(a0 + t * C::A_ATOM_BYTES + k * 32, C::LAYOUT, C::SBO);
-                                    const uint64_t bd = smem_desc(bb + t * C::B_ATOM_BYTES + k * 32, C::LAYOUT, C::SBO);
-                                    mma_bf16(dcol, ad, bd, idesc, first ? 0 : 1);
-                                    first = 0;
+                                    const uint64_t ad = dAg + (uint64_t)((t * C::A_ATOM_BYTES + k * 32) >> 4);
+                                    const uint64_t bd =
+                                        dBst + (uint64_t)((half * C::B_BYTES + t * C::B_ATOM_BYTES + k * 32) >> 4);
+                                    mma_bf16(dcol, ad, bd, idesc, (half | t | k) ? 1 : 0);
                                 }
-                        }
                         // FAST: + (||mu||^2 + 4)/2 from the constant slice, so the accumulator is
                         // the positive score (||z - mu||^2 - ||z||^2 + 4)/2 itself
-                        if (!a.final_mode) mma_bf16(dcol, aug_a, smem_desc(bhi + 2 * C::B_BYTES, 6, 256), idesc, 1);
+                        if (!a.final_mode) mma_bf16(dcol, dAugA, dAugBst, idesc, 1);
                         mma_commit(&ctl.acc_full[g][buf]);  // this group's accumulator is ready
                     }
                     if (ok) mma_commit(&ctl.b_empty[s]);  // the stage is free once these MMAs retire
