@@ -33,8 +33,8 @@ struct TcCfg {
     static constexpr int ATOM = D < 64 ? D : 64;          // K elements per swizzle-atom row
     static constexpr int ATOM_BYTES = ATOM * 2;           // 64 or 128
     static constexpr int NATOM = D / ATOM;
-    static constexpr int NCH = 64;                        // centroids per chunk = MMA N = one slice
-    static constexpr int GROUPS = 4;                      // point tiles per CTA step, one per epilogue group
+    static constexpr int NCH = 128;                       // centroids per chunk = MMA N = two slices
+    static constexpr int GROUPS = 2;                      // point tiles per CTA step, one per epilogue group
     static constexpr int A_BUFS = D == 128 ? 1 : 2;       // point-tile groups in flight
     static constexpr int STAGES = D == 128 ? 2 : (D == 64 ? 4 : 6);
     static constexpr int A_ATOM_BYTES = 128 * ATOM_BYTES;
@@ -52,8 +52,8 @@ struct TcCfg {
     static_assert(GROUPS * 2 * NCH <= 512, "two accumulator buffers per group must fit tensor memory");
 };
 
-constexpr int TC_MAX_CHUNKS = 2048;
-constexpr int TC_GROUPS = 4;                          // epilogue warpgroups
+constexpr int TC_MAX_CHUNKS = 1024;
+constexpr int TC_GROUPS = 2;                          // epilogue warpgroups
 constexpr int TC_THREADS = 64 + TC_GROUPS * 128;      // warp 0 TMA, warp 1 MMA, then the epilogue groups
 
 struct TcCtl {
@@ -65,8 +65,9 @@ struct TcCtl {
     int abort;
     int nchunks;
     int chunk_col[TC_MAX_CHUNKS];
-    // candidate of each chunk + 128 if the candidate's padded range ends with the chunk
-    int16_t chunk_info[TC_MAX_CHUNKS];
+    // per 64-column slice (two per chunk): candidate + 128 if the candidate's padded range ends
+    // with the slice, or -1 (inactive candidate / beyond the batch)
+    int16_t slice_info[2 * TC_MAX_CHUNKS];
 };
 
 // ---------------------------------------------------------------------------------------
@@ -240,15 +241,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
         mbar_init(&ctl.drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        // 64-column chunks holding columns of an active candidate (FINAL: every candidate);
-        // candidates are padded to whole chunks, so each chunk belongs to one candidate
-        int nch = 0;
-        for (int c = 0; c < b.n; ++c) {
-            if (!(a.final_mode || a.st.active[c])) continue;
-            const int pad_end = c + 1 < b.n ? b.off[c + 1] : b.total_k;
-            for (int col = b.off[c]; col < b.off[c] + b.k[c] && nch < TC_MAX_CHUNKS; col += C::NCH) {
-                ctl.chunk_col[nch] = col;
-                ctl.chunk_info[nch] = (int16_t)(c + (col + C::NCH >= pad_end ? 128 : 0));
+        // 128-column chunks holding columns of an active candidate (FINAL: every candidate), with
+        // the candidate of each 64-column half; candidates are padded to whole slices
+        int nch = 0, c = 0;
+        const int total_chunks = (b.total_k + C::NCH - 1) / C::NCH;
+        for (int q = 0; q < total_chunks && nch < TC_MAX_CHUNKS; ++q) {
+            const int lo = q * C::NCH;
+            int info[2] = {-1, -1};
+            bool need = false;
+            for (int h = 0; h < 2; ++h) {
+                const int col0 = lo + 64 * h;
+                if (col0 >= b.total_k) break;
+                while (c + 1 < b.n && b.off[c + 1] <= col0) ++c;
+                const int pad_end = c + 1 < b.n ? b.off[c + 1] : b.total_k;
+                if (col0 < b.off[c] + b.k[c] && (a.final_mode || a.st.active[c])) {
+                    info[h] = c + (col0 + 64 >= pad_end ? 128 : 0);
+                    need = true;
+                }
+            }
+            if (need) {
+                ctl.chunk_col[nch] = lo;
+                ctl.slice_info[2 * nch] = (int16_t)info[0];
+                ctl.slice_info[2 * nch + 1] = (int16_t)info[1];
                 ++nch;
             }
         }
@@ -375,94 +389,100 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int buf = it & 1;
                 if (!(ok = mbar_wait(&ctl.acc_full[wg][buf], (it >> 1) & 1, &ctl, a.err))) break;
                 tc_fence_after();
-                const int info = ctl.chunk_info[q];
-                const int cand = info & 127;
-                const int col0 = ctl.chunk_col[q];
-                uint32_t r[64];
-                tmem_ld64(lane_base + (uint32_t)(buf * C::NCH), r);
+                const int info0 = ctl.slice_info[2 * q], info1 = ctl.slice_info[2 * q + 1];
+                uint32_t r[2][64];
+                if (info0 >= 0) tmem_ld64(lane_base + (uint32_t)(buf * C::NCH), r[0]);
+                if (info1 >= 0) tmem_ld64(lane_base + (uint32_t)(buf * C::NCH + 64), r[1]);
                 tc_fence_before();
                 mbar_arrive(&ctl.acc_empty[wg][buf]);   // registers hold the chunk: the buffer is free
-                if (a.final_mode) {
-                    // exact best and second best of ||mu||^2 + 4 - 2 z.mu (FP32 norms; padding
-                    // columns carry an infinite norm and never win)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        float np4[16];
+                for (int h = 0; h < 2; ++h) {
+                    const int info = h ? info1 : info0;
+                    if (info < 0) continue;
+                    const int cand = info & 127;
+                    const int col0 = ctl.chunk_col[q] + 64 * h;
+                    if (a.final_mode) {
+                        // exact best and second best of ||mu||^2 + 4 - 2 z.mu (FP32 norms; padding
+                        // columns carry an infinite norm and never win)
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const float4 t4 = __ldg(reinterpret_cast<const float4*>(a.st.norm2p + col0) + 4 * v + u);
-                            np4[4 * u] = t4.x; np4[4 * u + 1] = t4.y; np4[4 * u + 2] = t4.z; np4[4 * u + 3] = t4.w;
+                        for (int v = 0; v < 4; ++v) {
+                            float np4[16];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const float4 t4 = __ldg(reinterpret_cast<const float4*>(a.st.norm2p + col0) + 4 * v + u);
+                                np4[4 * u] = t4.x; np4[4 * u + 1] = t4.y; np4[4 * u + 2] = t4.z; np4[4 * u + 3] = t4.w;
+                            }
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) {
+                                const float sc = fmaf(2.0f, __uint_as_float(r[h][16 * v + k]), np4[k]);
+                                if (sc < bv) { b2 = bv; bv = sc; bi = col0 + 16 * v + k; } else { b2 = fminf(b2, sc); }
+                            }
                         }
+                    } else {
+                        // packed keys: the positive score with its low 6 bits replaced by the column
+                        // within the slice; a float minimum gives value and column together (four
+                        // independent chains, merged at the end)
+                        float m0 = INFINITY, m1 = INFINITY, m2 = INFINITY, m3 = INFINITY;
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) {
-                            const float sc = fmaf(2.0f, __uint_as_float(r[16 * v + k]), np4[k]);
-                            if (sc < bv) { b2 = bv; bv = sc; bi = col0 + 16 * v + k; } else { b2 = fminf(b2, sc); }
+                        for (int k = 0; k < 64; k += 8) {
+                            m0 = min3f(m0, __uint_as_float((r[h][k] & 0xFFFFFFC0u) | (uint32_t)k),
+                                       __uint_as_float((r[h][k + 1] & 0xFFFFFFC0u) | (uint32_t)(k + 1)));
+                            m1 = min3f(m1, __uint_as_float((r[h][k + 2] & 0xFFFFFFC0u) | (uint32_t)(k + 2)),
+                                       __uint_as_float((r[h][k + 3] & 0xFFFFFFC0u) | (uint32_t)(k + 3)));
+                            m2 = min3f(m2, __uint_as_float((r[h][k + 4] & 0xFFFFFFC0u) | (uint32_t)(k + 4)),
+                                       __uint_as_float((r[h][k + 5] & 0xFFFFFFC0u) | (uint32_t)(k + 5)));
+                            m3 = min3f(m3, __uint_as_float((r[h][k + 6] & 0xFFFFFFC0u) | (uint32_t)(k + 6)),
+                                       __uint_as_float((r[h][k + 7] & 0xFFFFFFC0u) | (uint32_t)(k + 7)));
+                        }
+                        const float kmin = fminf(min3f(m0, m1, m2), m3);
+                        const uint32_t kb = __float_as_uint(kmin);
+                        const float v = __uint_as_float(kb & 0xFFFFFFC0u);
+                        if (v < bv) { bv = v; bi = col0 + (int)(kb & 63u); }
+                    }
+                    if (info < 128) continue;              // the candidate continues in a later slice
+                    // ---- candidate finished for this tile: label, change, sums ----
+                    const int K = b.k[cand], off = b.off[cand];
+                    int nl = bi - off;
+                    if (nl < 0 || nl >= K) nl = 0;       // non-finite scores: keep indices in range
+                    int ol = -1;
+                    if (valid) {
+                        int16_t* lp = a.st.labels + i * b.cs + cand;
+                        ol = *lp;
+                        *lp = (int16_t)nl;
+                    }
+                    if (a.final_mode) {
+                        if (valid && !(b2 - bv > a.tie_band)) {
+                            const int slot = atomicAdd(a.recheck_count, 1);
+                            a.recheck[slot] = make_int2((int)i, cand);
+                        }
+                    } else {
+                        const bool ch = valid && nl != ol;
+                        unsigned mask = __ballot_sync(0xffffffffu, ch);
+                        if (lane == 0 && mask) atomicAdd(a.st.changed + (a.pass & 1) * MAXC + cand, __popc(mask));
+                        if (ch) {
+                            atomicAdd(a.st.counts + off + nl, 1);
+                            if (ol >= 0) atomicSub(a.st.counts + off + ol, 1);
+                        }
+                        while (mask) {
+                            const int src = __ffs(mask) - 1;
+                            mask &= mask - 1;
+                            const int64_t pi = __shfl_sync(0xffffffffu, i, src);
+                            const int pn = __shfl_sync(0xffffffffu, nl, src);
+                            const int po = __shfl_sync(0xffffffffu, ol, src);
+                            for (int k = lane; k < D; k += 32) {
+                                const long long v = __float2ll_rn(__bfloat162float(a.Z[pi * D + k]) * FIXED_SCALE_F);
+                                atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + pn) * D + k),
+                                          (unsigned long long)v);
+                                if (po >= 0)
+                                    atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + po) * D + k),
+                                              (unsigned long long)(-v));
+                            }
                         }
                     }
-                } else {
-                    // packed keys: the positive score with its low 6 bits replaced by the column
-                    // within the chunk; a float minimum gives value and column together (four
-                    // independent chains, merged at the end)
-                    float m0 = INFINITY, m1 = INFINITY, m2 = INFINITY, m3 = INFINITY;
-#pragma unroll
-                    for (int k = 0; k < 64; k += 8) {
-                        m0 = min3f(m0, __uint_as_float((r[k] & 0xFFFFFFC0u) | (uint32_t)k),
-                                   __uint_as_float((r[k + 1] & 0xFFFFFFC0u) | (uint32_t)(k + 1)));
-                        m1 = min3f(m1, __uint_as_float((r[k + 2] & 0xFFFFFFC0u) | (uint32_t)(k + 2)),
-                                   __uint_as_float((r[k + 3] & 0xFFFFFFC0u) | (uint32_t)(k + 3)));
-                        m2 = min3f(m2, __uint_as_float((r[k + 4] & 0xFFFFFFC0u) | (uint32_t)(k + 4)),
-                                   __uint_as_float((r[k + 5] & 0xFFFFFFC0u) | (uint32_t)(k + 5)));
-                        m3 = min3f(m3, __uint_as_float((r[k + 6] & 0xFFFFFFC0u) | (uint32_t)(k + 6)),
-                                   __uint_as_float((r[k + 7] & 0xFFFFFFC0u) | (uint32_t)(k + 7)));
-                    }
-                    const float kmin = fminf(min3f(m0, m1, m2), m3);
-                    const uint32_t kb = __float_as_uint(kmin);
-                    const float v = __uint_as_float(kb & 0xFFFFFFC0u);
-                    if (v < bv) { bv = v; bi = col0 + (int)(kb & 63u); }
+                    bv = INFINITY;
+                    b2 = INFINITY;
+                    bi = -1;
                 }
-                if (info < 128) continue;              // the candidate continues in a later chunk
-                // ---- candidate finished for this tile: label, change, sums ----
-                const int K = b.k[cand], off = b.off[cand];
-                int nl = bi - off;
-                if (nl < 0 || nl >= K) nl = 0;       // non-finite scores: keep indices in range
-                int ol = -1;
-                if (valid) {
-                    int16_t* lp = a.st.labels + i * b.cs + cand;
-                    ol = *lp;
-                    *lp = (int16_t)nl;
-                }
-                if (a.final_mode) {
-                    if (valid && !(b2 - bv > a.tie_band)) {
-                        const int slot = atomicAdd(a.recheck_count, 1);
-                        a.recheck[slot] = make_int2((int)i, cand);
-                    }
-                } else {
-                    const bool ch = valid && nl != ol;
-                    unsigned mask = __ballot_sync(0xffffffffu, ch);
-                    if (lane == 0 && mask) atomicAdd(a.st.changed + (a.pass & 1) * MAXC + cand, __popc(mask));
-                    if (ch) {
-                        atomicAdd(a.st.counts + off + nl, 1);
-                        if (ol >= 0) atomicSub(a.st.counts + off + ol, 1);
-                    }
-                    while (mask) {
-                        const int src = __ffs(mask) - 1;
-                        mask &= mask - 1;
-                        const int64_t pi = __shfl_sync(0xffffffffu, i, src);
-                        const int pn = __shfl_sync(0xffffffffu, nl, src);
-                        const int po = __shfl_sync(0xffffffffu, ol, src);
-                        for (int k = lane; k < D; k += 32) {
-                            const long long v = __float2ll_rn(__bfloat162float(a.Z[pi * D + k]) * FIXED_SCALE_F);
-                            atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + pn) * D + k),
-                                      (unsigned long long)v);
-                            if (po >= 0)
-                                atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + po) * D + k),
-                                          (unsigned long long)(-v));
-                        }
-                    }
-                }
-                bv = INFINITY;
-                b2 = INFINITY;
-                bi = -1;
             }
         }
     }
@@ -581,8 +601,8 @@ static cudaError_t launch_tc_t(const CandBatch& b, const __nv_bfloat16* Z, int64
 
 cudaError_t launch_assign_tc(const CandBatch& b, const void* Z, int64_t n, int d, KmState st, int pass, int final_mode,
                              int2* recheck, int* recheck_count, uint32_t* err, cudaStream_t s) {
-    // the chunk table holds every 64-column chunk of the batch
-    if (b.total_k > TC_MAX_CHUNKS * 64) return cudaErrorInvalidValue;
+    // the chunk table holds every 128-column chunk of the batch
+    if (b.total_k > TC_MAX_CHUNKS * 128) return cudaErrorInvalidValue;
     const __nv_bfloat16* z = (const __nv_bfloat16*)Z;
     switch (d) {
         case 32: return launch_tc_t<32>(b, z, n, st, pass, final_mode, recheck, recheck_count, err, s);
