@@ -34,9 +34,10 @@ struct TcCfg {
     static constexpr int ATOM_BYTES = ATOM * 2;           // 64 or 128
     static constexpr int NATOM = D / ATOM;
     static constexpr int NCH = 128;                       // centroids per chunk = MMA N = two slices
-    static constexpr int GROUPS = 2;                      // point tiles per CTA step, one per epilogue group
+    static constexpr int GROUPS = 4;                      // point tiles per CTA step, one per epilogue group
+    static constexpr int ACC_BUFS = 1;                    // accumulator buffers per group
     static constexpr int A_BUFS = D == 128 ? 1 : 2;       // point-tile groups in flight
-    static constexpr int STAGES = D == 128 ? 2 : (D == 64 ? 4 : 6);
+    static constexpr int STAGES = D == 128 ? 1 : (D == 64 ? 2 : 4);
     static constexpr int A_ATOM_BYTES = 128 * ATOM_BYTES;
     static constexpr int A_TILE_BYTES = NATOM * A_ATOM_BYTES;     // one 128-point tile
     static constexpr int A_BYTES = GROUPS * A_TILE_BYTES;         // one group of tiles
@@ -49,11 +50,11 @@ struct TcCfg {
     static constexpr int SBO = 8 * ATOM_BYTES;                 // stride between 8-row groups
     static constexpr int SMEM = 1024 + A_BUFS * A_BYTES + AUG_A_BYTES + STAGES * STAGE_BYTES;
     static_assert(SMEM <= 227 * 1024, "shared memory budget");
-    static_assert(GROUPS * 2 * NCH <= 512, "two accumulator buffers per group must fit tensor memory");
+    static_assert(GROUPS * ACC_BUFS * NCH <= 512, "the accumulator buffers must fit tensor memory");
 };
 
 constexpr int TC_MAX_CHUNKS = 1024;
-constexpr int TC_GROUPS = 2;                          // epilogue warpgroups
+constexpr int TC_GROUPS = 4;                          // epilogue warpgroups
 constexpr int TC_THREADS = 64 + TC_GROUPS * 128;      // warp 0 TMA, warp 1 MMA, then the epilogue groups
 
 struct TcCtl {
@@ -337,15 +338,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const uint64_t dAgrp = dA + (uint64_t)((ab * C::A_BYTES) >> 4);
                 for (int q = 0; q < nchunks && ok; ++q, ++it) {
                     const int s = it % C::STAGES;
-                    const int buf = it & 1;
+                    const int buf = it % C::ACC_BUFS;
+                    const uint32_t acc_par = (uint32_t)((it / C::ACC_BUFS) & 1);
                     if (!(ok = mbar_wait(&ctl.b_full[s], (it / C::STAGES) & 1, &ctl, a.err))) break;
                     const uint64_t dBst = dB + (uint64_t)((s * C::STAGE_BYTES) >> 4);
                     const uint64_t dAugBst = dAugB + (uint64_t)((s * C::STAGE_BYTES) >> 4);
 #pragma unroll
                     for (int g = 0; g < C::GROUPS; ++g) {
-                        if (!(ok = mbar_wait(&ctl.acc_empty[g][buf], ((it >> 1) & 1) ^ 1, &ctl, a.err))) break;
+                        if (!(ok = mbar_wait(&ctl.acc_empty[g][buf], acc_par ^ 1, &ctl, a.err))) break;
                         tc_fence_after();
-                        const uint32_t dcol = tmem + (uint32_t)(g * 2 * C::NCH + buf * C::NCH);
+                        const uint32_t dcol = tmem + (uint32_t)((g * C::ACC_BUFS + buf) * C::NCH);
                         const uint64_t dAg = dAgrp + (uint64_t)((g * C::A_TILE_BYTES) >> 4);
                         // -z.mu from the BF16 hi and lo halves of -mu
 #pragma unroll
@@ -377,7 +379,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int wg = (warp - 2) >> 2;               // epilogue group
         const int quarter = warp & 3;                 // TMEM lanes this warp may access
         const int row = quarter * 32 + lane;
-        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(wg * 2 * C::NCH);
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(wg * C::ACC_BUFS * C::NCH);
         int it = 0;
         bool ok = nchunks > 0;
         for (int64_t step = blockIdx.x; step < nsteps && ok; step += gridDim.x) {
@@ -386,18 +388,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             float bv = INFINITY, b2 = INFINITY;
             int bi = -1;
             for (int q = 0; q < nchunks; ++q, ++it) {
-                const int buf = it & 1;
-                if (!(ok = mbar_wait(&ctl.acc_full[wg][buf], (it >> 1) & 1, &ctl, a.err))) break;
+                const int buf = it % C::ACC_BUFS;
+                if (!(ok = mbar_wait(&ctl.acc_full[wg][buf], (it / C::ACC_BUFS) & 1, &ctl, a.err))) break;
                 tc_fence_after();
-                const int info0 = ctl.slice_info[2 * q], info1 = ctl.slice_info[2 * q + 1];
-                uint32_t r[2][64];
-                if (info0 >= 0) tmem_ld64(lane_base + (uint32_t)(buf * C::NCH), r[0]);
-                if (info1 >= 0) tmem_ld64(lane_base + (uint32_t)(buf * C::NCH + 64), r[1]);
-                tc_fence_before();
-                mbar_arrive(&ctl.acc_empty[wg][buf]);   // registers hold the chunk: the buffer is free
-#pragma unroll
+#pragma unroll 1
                 for (int h = 0; h < 2; ++h) {
-                    const int info = h ? info1 : info0;
+                    const int info = ctl.slice_info[2 * q + h];
+                    uint32_t r[1][64];
+                    if (info >= 0) tmem_ld64(lane_base + (uint32_t)(buf * C::NCH + 64 * h), r[0]);
+                    if (h == 1) {
+                        tc_fence_before();
+                        mbar_arrive(&ctl.acc_empty[wg][buf]);   // both halves read: the buffer is free
+                    }
                     if (info < 0) continue;
                     const int cand = info & 127;
                     const int col0 = ctl.chunk_col[q] + 64 * h;
@@ -414,7 +416,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             }
 #pragma unroll
                             for (int k = 0; k < 16; ++k) {
-                                const float sc = fmaf(2.0f, __uint_as_float(r[h][16 * v + k]), np4[k]);
+                                const float sc = fmaf(2.0f, __uint_as_float(r[0][16 * v + k]), np4[k]);
                                 if (sc < bv) { b2 = bv; bv = sc; bi = col0 + 16 * v + k; } else { b2 = fminf(b2, sc); }
                             }
                         }
@@ -425,14 +427,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         float m0 = INFINITY, m1 = INFINITY, m2 = INFINITY, m3 = INFINITY;
 #pragma unroll
                         for (int k = 0; k < 64; k += 8) {
-                            m0 = min3f(m0, __uint_as_float((r[h][k] & 0xFFFFFFC0u) | (uint32_t)k),
-                                       __uint_as_float((r[h][k + 1] & 0xFFFFFFC0u) | (uint32_t)(k + 1)));
-                            m1 = min3f(m1, __uint_as_float((r[h][k + 2] & 0xFFFFFFC0u) | (uint32_t)(k + 2)),
-                                       __uint_as_float((r[h][k + 3] & 0xFFFFFFC0u) | (uint32_t)(k + 3)));
-                            m2 = min3f(m2, __uint_as_float((r[h][k + 4] & 0xFFFFFFC0u) | (uint32_t)(k + 4)),
-                                       __uint_as_float((r[h][k + 5] & 0xFFFFFFC0u) | (uint32_t)(k + 5)));
-                            m3 = min3f(m3, __uint_as_float((r[h][k + 6] & 0xFFFFFFC0u) | (uint32_t)(k + 6)),
-                                       __uint_as_float((r[h][k + 7] & 0xFFFFFFC0u) | (uint32_t)(k + 7)));
+                            m0 = min3f(m0, __uint_as_float((r[0][k] & 0xFFFFFFC0u) | (uint32_t)k),
+                                       __uint_as_float((r[0][k + 1] & 0xFFFFFFC0u) | (uint32_t)(k + 1)));
+                            m1 = min3f(m1, __uint_as_float((r[0][k + 2] & 0xFFFFFFC0u) | (uint32_t)(k + 2)),
+                                       __uint_as_float((r[0][k + 3] & 0xFFFFFFC0u) | (uint32_t)(k + 3)));
+                            m2 = min3f(m2, __uint_as_float((r[0][k + 4] & 0xFFFFFFC0u) | (uint32_t)(k + 4)),
+                                       __uint_as_float((r[0][k + 5] & 0xFFFFFFC0u) | (uint32_t)(k + 5)));
+                            m3 = min3f(m3, __uint_as_float((r[0][k + 6] & 0xFFFFFFC0u) | (uint32_t)(k + 6)),
+                                       __uint_as_float((r[0][k + 7] & 0xFFFFFFC0u) | (uint32_t)(k + 7)));
                         }
                         const float kmin = fminf(min3f(m0, m1, m2), m3);
                         const uint32_t kb = __float_as_uint(kmin);
