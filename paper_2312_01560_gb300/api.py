@@ -213,7 +213,7 @@ def lloyd(Z: torch.Tensor, mu0: torch.Tensor, iters=50, assign="ffma", stream=No
     kp = (K + 255) // 256 * 256
     # mu (4 B), sums (8 B), hi and lo (2 + 2 B) per centroid coordinate, norms and the norm
     # slice per centroid, labels and re-check list per point, alignment slack
-    ws = _workspace(kp * d * 16 + kp * 128 + 32 * n + 256 * 1024, Z.device)
+    ws = _workspace(kp * d * 16 + kp * 128 + 64 * n + 256 * 1024, Z.device)
     passes = C.c_int32(0)
     Zc = Z.contiguous()
     check(lib().raftgp_lloyd(C.c_void_p(Zc.data_ptr()), n, d, code, C.c_void_p(m0.data_ptr()), int(K),

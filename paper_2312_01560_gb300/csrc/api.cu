@@ -158,6 +158,7 @@ static void carve_km(Carver& c, KmState& km, int64_t kcap, int d, int64_t n, int
     km.sums = c.take<long long>((size_t)kp * d);
     km.counts = c.take<int32_t>(kp);
     km.labels = c.take<int16_t>((size_t)n * cs);
+    km.labels_new = c.take<int16_t>((size_t)n * cs);
     km.active = c.take<int32_t>(MAXC);
     km.changed = c.take<int32_t>(2 * MAXC);
     km.passes = c.take<int32_t>(MAXC);
@@ -314,6 +315,7 @@ static raftgp_status run_lloyd(const CandBatch& b, const void* Z, int zdtype, in
                             ? launch_assign_tc(b, Z, n, d, km, pass, 0, nullptr, nullptr, err, s)
                             : launch_assign_ffma(b, Z, zdtype, n, d, km, pass, s);
         if (e != cudaSuccess) return cuda_fail(e, "assign");
+        if (engine == RAFTGP_ASSIGN_TC) launch_apply_changes(b, Z, zdtype, n, d, km, pass, s);
         launch_lloyd_update(b, d, km, pass, iters, s);
     }
     if (engine == RAFTGP_ASSIGN_TC) {

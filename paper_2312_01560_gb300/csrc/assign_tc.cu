@@ -15,10 +15,10 @@
 // wait is bounded: on timeout the CTA raises an abort flag, records DERR_TIMEOUT, drains its
 // in-flight copies and MMAs (again bounded), frees its tensor memory and returns.
 //
-// Modes: FAST (Lloyd passes) writes labels, counts changes and applies each change to the
-// 2^-40 fixed-point centroid sums; FINAL (the assignment whose labels are reported) also
-// tracks the second-best score and lists every (point, candidate) whose best two scores lie
-// within the error band of the BF16 product, for an exact FP32 re-check.
+// Modes: FAST (Lloyd passes) writes the new labels (k_apply_changes then counts the changes
+// and applies them to the 2^-40 fixed-point centroid sums); FINAL (the assignment whose labels
+// are reported) also tracks the second-best score and lists every (point, candidate) whose best
+// two scores lie within the error band of the BF16 product, for an exact FP32 re-check.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -442,44 +442,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         if (v < bv) { bv = v; bi = col0 + (int)(kb & 63u); }
                     }
                     if (info < 128) continue;              // the candidate continues in a later slice
-                    // ---- candidate finished for this tile: label, change, sums ----
+                    // ---- candidate finished for this tile: write the label ----
                     const int K = b.k[cand], off = b.off[cand];
                     int nl = bi - off;
                     if (nl < 0 || nl >= K) nl = 0;       // non-finite scores: keep indices in range
-                    int ol = -1;
-                    if (valid) {
-                        int16_t* lp = a.st.labels + i * b.cs + cand;
-                        ol = *lp;
-                        *lp = (int16_t)nl;
-                    }
                     if (a.final_mode) {
-                        if (valid && !(b2 - bv > a.tie_band)) {
-                            const int slot = atomicAdd(a.recheck_count, 1);
-                            a.recheck[slot] = make_int2((int)i, cand);
-                        }
-                    } else {
-                        const bool ch = valid && nl != ol;
-                        unsigned mask = __ballot_sync(0xffffffffu, ch);
-                        if (lane == 0 && mask) atomicAdd(a.st.changed + (a.pass & 1) * MAXC + cand, __popc(mask));
-                        if (ch) {
-                            atomicAdd(a.st.counts + off + nl, 1);
-                            if (ol >= 0) atomicSub(a.st.counts + off + ol, 1);
-                        }
-                        while (mask) {
-                            const int src = __ffs(mask) - 1;
-                            mask &= mask - 1;
-                            const int64_t pi = __shfl_sync(0xffffffffu, i, src);
-                            const int pn = __shfl_sync(0xffffffffu, nl, src);
-                            const int po = __shfl_sync(0xffffffffu, ol, src);
-                            for (int k = lane; k < D; k += 32) {
-                                const long long v = __float2ll_rn(__bfloat162float(a.Z[pi * D + k]) * FIXED_SCALE_F);
-                                atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + pn) * D + k),
-                                          (unsigned long long)v);
-                                if (po >= 0)
-                                    atomicAdd(reinterpret_cast<unsigned long long*>(a.st.sums + (int64_t)(off + po) * D + k),
-                                              (unsigned long long)(-v));
+                        if (valid) {
+                            a.st.labels[i * b.cs + cand] = (int16_t)nl;
+                            if (!(b2 - bv > a.tie_band)) {
+                                const int slot = atomicAdd(a.recheck_count, 1);
+                                a.recheck[slot] = make_int2((int)i, cand);
                             }
                         }
+                    } else if (valid) {
+                        // the change against the previous pass is applied by k_apply_changes, so
+                        // this epilogue never waits on a load
+                        a.st.labels_new[i * b.cs + cand] = (int16_t)nl;
                     }
                     bv = INFINITY;
                     b2 = INFINITY;

@@ -17,8 +17,8 @@ raftgp_status set_error(raftgp_status st, const char* fmt, ...);
 // ---- instrumentation (prof.cu) ---------------------------------------------------------
 enum ProfFamily {
     PF_DEGREES, PF_THETA, PF_SPMM_PROJ, PF_SPMM_GCN, PF_SEED_UPDATE, PF_SEED_PICK, PF_BATCH_INIT, PF_ASSIGN_FFMA,
-    PF_ASSIGN_TC, PF_ASSIGN_TC_FIRST, PF_ASSIGN_TC_FINAL, PF_RECHECK, PF_LLOYD_UPDATE, PF_SCORE, PF_SELECT_BEST,
-    PF_OTHER, PF_COUNT
+    PF_ASSIGN_TC, PF_ASSIGN_TC_FIRST, PF_ASSIGN_TC_FINAL, PF_RECHECK, PF_APPLY, PF_LLOYD_UPDATE, PF_SCORE,
+    PF_SELECT_BEST, PF_OTHER, PF_COUNT
 };
 // Brackets the kernels launched in its lifetime with CUDA events when profiling is on.
 class ProfScope {
@@ -62,6 +62,7 @@ struct KmState {                 // device arrays of one batch (workspace)
     long long* sums;             // total_k x d, 2^-40 fixed point
     int32_t* counts;             // total_k
     int16_t* labels;             // N x cs
+    int16_t* labels_new;         // N x cs: tensor-core pass output before the changes are applied
     int32_t* active;             // MAXC
     int32_t* changed;            // 2 x MAXC (double-buffered by pass parity)
     int32_t* passes;             // MAXC
@@ -91,6 +92,8 @@ void launch_batch_init(const CandBatch& b, const void* Z, int zdtype, int64_t n,
 cudaError_t launch_assign_ffma(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, KmState st, int pass,
                                cudaStream_t s);
 void launch_lloyd_update(const CandBatch& b, int d, KmState st, int pass, int last_pass, cudaStream_t s);
+void launch_apply_changes(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, KmState st, int pass,
+                          cudaStream_t s);
 cudaError_t launch_assign_tc(const CandBatch& b, const void* Z, int64_t n, int d, KmState st, int pass, int final_mode,
                              int2* recheck, int* recheck_count, uint32_t* err, cudaStream_t s);
 void launch_recheck(const CandBatch& b, const void* Z, int d, KmState st, const int2* list, const int* count,

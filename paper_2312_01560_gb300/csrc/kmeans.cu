@@ -543,6 +543,69 @@ cudaError_t launch_assign_ffma(const CandBatch& b, const void* Z, int zdtype, in
 }
 
 // ------------------------------------------------------------------------------------
+// After a tensor-core pass: compare the new labels with the previous ones (coalesced: a warp
+// reads 32 consecutive (point, candidate) pairs), count the changes, move each changed point
+// between the fixed-point sums of its old and new cluster (lanes over coordinates), and keep
+// the new labels.  Inactive candidates were not reassigned and are skipped.
+// ------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_apply_changes(CandBatch b, const T* __restrict__ Z, int64_t n, int d,
+                                                       KmState st, int pass) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = n * b.cs;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total; base += stride) {
+        const int64_t e = base + threadIdx.x;
+        const int64_t i = e / b.cs;
+        const int c = (int)(e - i * b.cs);
+        int nl = -1, ol = -1;
+        bool ch = false;
+        if (e < total && c < b.n && st.active[c]) {
+            nl = st.labels_new[e];
+            ol = st.labels[e];
+            ch = nl != ol;
+            if (ch) {
+                st.labels[e] = (int16_t)nl;
+                atomicAdd(st.counts + b.off[c] + nl, 1);
+                if (ol >= 0) atomicSub(st.counts + b.off[c] + ol, 1);
+                atomicAdd(st.changed + (pass & 1) * MAXC + c, 1);
+            }
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, ch);
+        while (mask) {
+            const int src = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int64_t pi = __shfl_sync(0xffffffffu, i, src);
+            const int pc = __shfl_sync(0xffffffffu, c, src);
+            const int pn = __shfl_sync(0xffffffffu, nl, src);
+            const int po = __shfl_sync(0xffffffffu, ol, src);
+            const int off = b.off[pc];
+            for (int k = lane; k < d; k += 32) {
+                const long long v = __float2ll_rn(zval(Z, pi * d + k) * FIXED_SCALE_F);
+                atomicAdd(reinterpret_cast<unsigned long long*>(st.sums + (int64_t)(off + pn) * d + k),
+                          (unsigned long long)v);
+                if (po >= 0)
+                    atomicAdd(reinterpret_cast<unsigned long long*>(st.sums + (int64_t)(off + po) * d + k),
+                              (unsigned long long)(-v));
+            }
+        }
+    }
+}
+
+void launch_apply_changes(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, KmState st, int pass,
+                          cudaStream_t s) {
+    const int64_t total = n * b.cs;
+    int64_t blocks = (total + 255) / 256;
+    const int64_t cap = (int64_t)num_sms() * 16;
+    if (blocks > cap) blocks = cap;
+    ProfScope ps(s, PF_APPLY, 1);
+    if (zdtype == RAFTGP_BF16)
+        k_apply_changes<__nv_bfloat16><<<(unsigned)blocks, 256, 0, s>>>(b, (const __nv_bfloat16*)Z, n, d, st, pass);
+    else
+        k_apply_changes<float><<<(unsigned)blocks, 256, 0, s>>>(b, (const float*)Z, n, d, st, pass);
+}
+
+// ------------------------------------------------------------------------------------
 // After a pass: a candidate with no label change is converged (inactive); otherwise its
 // centroids become the FP64 means of the fixed-point sums (empty clusters keep theirs).
 // ------------------------------------------------------------------------------------

@@ -12,8 +12,8 @@ namespace raftgp {
 
 static const char* kFamilyNames[PF_COUNT] = {
     "degrees", "theta", "spmm_project", "spmm_gcn", "seed_update", "seed_pick", "batch_init", "assign_ffma",
-    "assign_tc", "assign_tc_first", "assign_tc_final", "assign_recheck", "lloyd_update", "score_count",
-    "select_best", "other"};
+    "assign_tc", "assign_tc_first", "assign_tc_final", "assign_recheck", "apply_changes", "lloyd_update",
+    "score_count", "select_best", "other"};
 
 struct Profiler {
     std::mutex mu;
