@@ -32,7 +32,7 @@ __device__ __forceinline__ uint64_t kmpp_draw(uint64_t seed, int t) {
 __device__ __forceinline__ unsigned long long quantise(float d2) { return __float2ull_rz(d2 * FIXED_SCALE_F); }
 
 constexpr int SEED_THREADS = 256;
-constexpr int SEED_PPT = 8;                               // points per thread
+constexpr int SEED_PPT = 4;                               // points per thread
 constexpr int SEED_PPB = SEED_THREADS * SEED_PPT;         // points per block partial
 
 // FP32 direct-form squared distance of one row against the centre in shared memory:
@@ -75,28 +75,37 @@ __global__ void __launch_bounds__(SEED_THREADS) k_seed_update(const T* __restric
     __syncthreads();
     unsigned long long q = 0;
     const int64_t base = (int64_t)blockIdx.x * SEED_PPB + threadIdx.x;
-#pragma unroll 2
-    for (int r = 0; r < SEED_PPT; ++r) {
-        const int64_t i = base + (int64_t)r * SEED_THREADS;
-        if (i >= n) break;
-        float cur;
-        if (t == 1) {
-            cur = row_sqdist<T, D>(Z + i * D, c);
+    if (t == 1) {
+        for (int r = 0; r < SEED_PPT; ++r) {
+            const int64_t i = base + (int64_t)r * SEED_THREADS;
+            if (i >= n) break;
+            const float cur = row_sqdist<T, D>(Z + i * D, c);
             ss.D2[i] = cur;
             ss.nearest[i] = 0;
-        } else {
-            cur = ss.D2[i];
-            const float bound = __ldg(ss.cc2 + ss.nearest[i]);
-            if (!(bound >= 4.0f * cur * 1.0001f)) {
+            q += quantise(cur);
+        }
+    } else {
+        // independent loads first: current D^2, nearest seed, and that seed's distance to c
+        float cur[SEED_PPT], bound[SEED_PPT];
+#pragma unroll
+        for (int r = 0; r < SEED_PPT; ++r) {
+            const int64_t i = base + (int64_t)r * SEED_THREADS;
+            cur[r] = i < n ? ss.D2[i] : 0.f;
+            bound[r] = i < n ? __ldg(ss.cc2 + ss.nearest[i]) : 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < SEED_PPT; ++r) {
+            const int64_t i = base + (int64_t)r * SEED_THREADS;
+            if (i < n && !(bound[r] >= 4.0f * cur[r] * 1.0001f)) {
                 const float nd = row_sqdist<T, D>(Z + i * D, c);
-                if (nd < cur) {
-                    cur = nd;
+                if (nd < cur[r]) {
+                    cur[r] = nd;
                     ss.D2[i] = nd;
                     ss.nearest[i] = (int16_t)(t - 1);
                 }
             }
+            if (i < n) q += quantise(cur[r]);
         }
-        q += quantise(cur);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
@@ -212,15 +221,18 @@ __global__ void __launch_bounds__(1024) k_seed_pick(const T* __restrict__ Z, int
         ss.seeds[t] = (int32_t)p;
         ss.chosen[p] = 1;
     }
-    // |c_j - c_t|^2 for j < t (FP32; used only as a conservative bound)
-    for (int j = threadIdx.x; j < t; j += blockDim.x) {
+    // |c_j - c_t|^2 for j < t (FP32; used only as a conservative bound): a warp per seed,
+    // lanes over coordinates
+    const int lane = threadIdx.x & 31;
+    for (int j = threadIdx.x >> 5; j < t; j += blockDim.x >> 5) {
         const int64_t sj = ss.seeds[j];
         float acc = 0.f;
-        for (int k = 0; k < D; ++k) {
+        for (int k = lane; k < D; k += 32) {
             const float dlt = load_elem(Z, sj * D + k) - load_elem(Z, p * D + k);
             acc = fmaf(dlt, dlt, acc);
         }
-        ss.cc2[j] = acc;
+        acc = warp_sum(acc);
+        if (lane == 0) ss.cc2[j] = acc;
     }
 }
 
@@ -329,6 +341,30 @@ __device__ void write_row_operands(KmState st, int64_t row, int d, bool padding)
     st.norm2p[row] = s + 4.0f;
     split_bf16(0.5f * (s + 4.0f), aug, aug + 1);
     for (int k = 2; k < 16; ++k) aug[k] = __float2bfloat16_rn(0.f);
+}
+
+// The same for one real centroid row by a whole warp (lanes over coordinates; the norm is a
+// fixed-order warp reduction).
+__device__ void warp_row_operands(KmState st, int64_t row, int d) {
+    const int lane = threadIdx.x & 31;
+    float s = 0.f;
+    for (int k = lane; k < d; k += 32) {
+        const float v = st.mu[row * d + k];
+        s = fmaf(v, v, s);
+        split_bf16(-v, st.bhi + row * d + k, st.blo + row * d + k);
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+        st.norm2[row] = s;
+        st.norm2p[row] = s + 4.0f;
+    }
+    if (lane < 16) {
+        __nv_bfloat16* aug = st.baug + row * 16;
+        const __nv_bfloat16 h = __float2bfloat16_rn(0.5f * (s + 4.0f));
+        aug[lane] = lane == 0 ? h
+                  : lane == 1 ? __float2bfloat16_rn(0.5f * (s + 4.0f) - __bfloat162float(h))
+                              : __float2bfloat16_rn(0.f);
+    }
 }
 
 template <typename T>
@@ -598,7 +634,7 @@ void launch_apply_changes(const CandBatch& b, const void* Z, int zdtype, int64_t
     int64_t blocks = (total + 255) / 256;
     const int64_t cap = (int64_t)num_sms() * 16;
     if (blocks > cap) blocks = cap;
-    ProfScope ps(s, PF_APPLY, 1);
+    ProfScope ps(s, pass == 1 ? PF_APPLY_FIRST : PF_APPLY, 1);
     if (zdtype == RAFTGP_BF16)
         k_apply_changes<__nv_bfloat16><<<(unsigned)blocks, 256, 0, s>>>(b, (const __nv_bfloat16*)Z, n, d, st, pass);
     else
@@ -625,20 +661,23 @@ __global__ void k_lloyd_update(CandBatch b, int d, KmState st, int pass, int las
     // after the last allowed pass the centroids stay those the final labels were assigned against
     if (pass >= last_pass) return;
     const int K = b.k[c], off = b.off[c];
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < K; j += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    for (int j = blockIdx.x * wpb + (threadIdx.x >> 5); j < K; j += gridDim.x * wpb) {
         const int cnt = st.counts[off + j];
         if (cnt <= 0) continue;
         const double inv = 1.0 / ((double)cnt * FIXED_SCALE);
-        for (int k = 0; k < d; ++k)
+        for (int k = lane; k < d; k += 32)
             st.mu[(int64_t)(off + j) * d + k] = (float)((double)st.sums[(int64_t)(off + j) * d + k] * inv);
-        write_row_operands(st, off + j, d, false);
+        __syncwarp();
+        warp_row_operands(st, off + j, d);
     }
 }
 
 void launch_lloyd_update(const CandBatch& b, int d, KmState st, int pass, int last_pass, cudaStream_t s) {
-    dim3 grid(8, b.n);
+    dim3 grid(16, b.n);
     ProfScope ps(s, PF_LLOYD_UPDATE, 1);
-    k_lloyd_update<<<grid, 128, 0, s>>>(b, d, st, pass, last_pass);
+    k_lloyd_update<<<grid, 256, 0, s>>>(b, d, st, pass, last_pass);
 }
 
 }  // namespace raftgp
