@@ -304,7 +304,8 @@ def main():
     roof = roofline(prof, g, wl, elem, rep["cands"], args.steps)
     lab = labels.cpu().numpy()
     quality = {"k_best": rep["k"], "nmi_planted": nmi(lab, g.planted),
-               "mod_best": [c[1] for c in rep["cands"] if c[0] == rep["k"]][0]}
+               "mod_best": [c[1] for c in rep["cands"] if c[0] == rep["k"]][0],
+               "candidates": [[c[0], round(c[1], 6), c[3]] for c in rep["cands"]]}
 
     e2e = None
     if not args.no_e2e:

@@ -101,6 +101,8 @@ struct EmbedWs {
     float* rs;
     float* rsh;
     float* W[RAFTGP_MAX_LAYERS];
+    __nv_bfloat16* Whi[RAFTGP_MAX_LAYERS];  // BF16 form: W^T split into hi and lo for the tensor cores
+    __nv_bfloat16* Wlo[RAFTGP_MAX_LAYERS];
     double* partial;
     float* gvec;
     void* bufA;
@@ -119,7 +121,11 @@ static EmbedWs carve_embed(Carver& c, int64_t n, const raftgp_embed_opts* o) {
     w.deg = c.take<int32_t>(n);
     w.rs = c.take<float>(n);
     w.rsh = c.take<float>(n);
-    for (int k = 1; k <= o->n_layers; ++k) w.W[k - 1] = c.take<float>((size_t)o->dims[k - 1] * o->dims[k]);
+    for (int k = 1; k <= o->n_layers; ++k) {
+        w.W[k - 1] = c.take<float>((size_t)o->dims[k - 1] * o->dims[k]);
+        w.Whi[k - 1] = c.take<__nv_bfloat16>((size_t)o->dims[k - 1] * o->dims[k]);
+        w.Wlo[k - 1] = c.take<__nv_bfloat16>((size_t)o->dims[k - 1] * o->dims[k]);
+    }
     const int L = o->dims[0];
     w.partial = c.take<double>((size_t)theta_blocks(n) * L);
     w.gvec = c.take<float>(L);
@@ -236,7 +242,29 @@ static raftgp_status run_embed(const raftgp_csr* g, const raftgp_embed_opts* o, 
         if (e != cudaSuccess) return cuda_fail(e, "projection");
         return RAFTGP_OK;
     }
-    // layer 0: projection, then x W1, prescaled by rsh for the first GCN gather
+    if (o->dtype == RAFTGP_BF16) {
+        // BF16: every SpMM is a pure gather with its row epilogue; the weight products run as
+        // tensor-core GEMMs (bufA / bufB alternate: the gather reads one, writes the other)
+        for (int k = 1; k <= o->n_layers; ++k) launch_w_split(w.W[k - 1], o->dims[k - 1], o->dims[k], w.Whi[k - 1],
+                                                              w.Wlo[k - 1], s);
+        e = launch_layer(agg0, o->dtype, g, w.deg, w.rs, w.gvec, 0, nullptr, L, L, nullptr, w.bufB, w.bufA,
+                         o->stage_out[0], s);
+        if (e != cudaSuccess) return cuda_fail(e, "projection");
+        e = launch_dense_tc(L, o->dims[1], n, w.bufA, w.Whi[0], w.Wlo[0], w.rsh, w.bufB, w.err, s);
+        if (e != cudaSuccess) return cuda_fail(e, "dense layer");
+        for (int k = 1; k <= o->n_layers; ++k) {
+            const bool last = k == o->n_layers;
+            e = launch_layer(AGG_GCN_, o->dtype, g, w.deg, w.rsh, nullptr, 1, nullptr, o->dims[k], o->dims[k], nullptr,
+                             w.bufB, last ? Z : w.bufA, o->stage_out[k], s);
+            if (e != cudaSuccess) return cuda_fail(e, "gcn layer");
+            if (!last) {
+                e = launch_dense_tc(o->dims[k], o->dims[k + 1], n, w.bufA, w.Whi[k], w.Wlo[k], w.rsh, w.bufB, w.err, s);
+                if (e != cudaSuccess) return cuda_fail(e, "dense layer");
+            }
+        }
+        return RAFTGP_OK;
+    }
+    // FP32: layer 0 is the projection then x W1, prescaled by rsh for the first GCN gather
     e = launch_layer(agg0, o->dtype, g, w.deg, w.rs, w.gvec, 0, w.W[0], L, o->dims[1], w.rsh, w.bufB, w.bufA,
                      o->stage_out[0], s);
     if (e != cudaSuccess) return cuda_fail(e, "projection");

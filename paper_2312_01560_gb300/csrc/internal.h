@@ -16,7 +16,7 @@ raftgp_status set_error(raftgp_status st, const char* fmt, ...);
 
 // ---- instrumentation (prof.cu) ---------------------------------------------------------
 enum ProfFamily {
-    PF_DEGREES, PF_THETA, PF_SPMM_PROJ, PF_SPMM_GCN, PF_SEED_UPDATE, PF_SEED_PICK, PF_BATCH_INIT, PF_ASSIGN_FFMA,
+    PF_DEGREES, PF_THETA, PF_SPMM_PROJ, PF_SPMM_GCN, PF_DENSE_TC, PF_SEED_UPDATE, PF_SEED_PICK, PF_BATCH_INIT, PF_ASSIGN_FFMA,
     PF_ASSIGN_TC, PF_ASSIGN_TC_FIRST, PF_ASSIGN_TC_FINAL, PF_RECHECK, PF_APPLY, PF_APPLY_FIRST, PF_LLOYD_UPDATE, PF_SCORE,
     PF_SELECT_BEST, PF_OTHER, PF_COUNT
 };
@@ -41,6 +41,11 @@ void launch_weights(int layer, int lin, int lout, uint64_t seed, float* W, cudaS
 cudaError_t launch_layer(int agg, int dtype, const raftgp_csr* g, const int32_t* deg, const float* rowscale,
                          const float* gvec, int act, const float* W, int lin, int lout, const float* postscale,
                          const void* X, void* out, void* stage, cudaStream_t s);
+
+// ---- dense layer on tensor cores (dense_tc.cu) -----------------------------------------
+void launch_w_split(const float* W, int lin, int lout, __nv_bfloat16* whi, __nv_bfloat16* wlo, cudaStream_t s);
+cudaError_t launch_dense_tc(int lin, int lout, int64_t n, const void* X, const __nv_bfloat16* whi,
+                            const __nv_bfloat16* wlo, const float* scale, void* out, uint32_t* err, cudaStream_t s);
 
 // ---- k-means (kmeans.cu) --------------------------------------------------------------
 constexpr int MAXC = RAFTGP_MAX_BATCH_CAND;

@@ -588,41 +588,47 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_apply_changes(CandBatch b, const T* __restrict__ Z, int64_t n, int d,
                                                        KmState st, int pass) {
     const int lane = threadIdx.x & 31;
-    const int64_t total = n * b.cs;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < total; base += stride) {
-        const int64_t e = base + threadIdx.x;
-        const int64_t i = e / b.cs;
-        const int c = (int)(e - i * b.cs);
-        int nl = -1, ol = -1;
-        bool ch = false;
-        if (e < total && c < b.n && st.active[c]) {
-            nl = st.labels_new[e];
-            ol = st.labels[e];
-            ch = nl != ol;
-            if (ch) {
-                st.labels[e] = (int16_t)nl;
-                atomicAdd(st.counts + b.off[c] + nl, 1);
-                if (ol >= 0) atomicSub(st.counts + b.off[c] + ol, 1);
-                atomicAdd(st.changed + (pass & 1) * MAXC + c, 1);
+    // thread per point; its label row (cs int16 = whole 16-byte vectors) is read once
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t i = base + threadIdx.x;
+        const bool valid = i < n;
+        for (int g0 = 0; g0 < b.n; g0 += 8) {
+            uint4 nv = make_uint4(0, 0, 0, 0), ov = make_uint4(0, 0, 0, 0);
+            if (valid) {
+                nv = *reinterpret_cast<const uint4*>(st.labels_new + i * b.cs + g0);
+                ov = *reinterpret_cast<const uint4*>(st.labels + i * b.cs + g0);
             }
-        }
-        unsigned mask = __ballot_sync(0xffffffffu, ch);
-        while (mask) {
-            const int src = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const int64_t pi = __shfl_sync(0xffffffffu, i, src);
-            const int pc = __shfl_sync(0xffffffffu, c, src);
-            const int pn = __shfl_sync(0xffffffffu, nl, src);
-            const int po = __shfl_sync(0xffffffffu, ol, src);
-            const int off = b.off[pc];
-            for (int k = lane; k < d; k += 32) {
-                const long long v = __float2ll_rn(zval(Z, pi * d + k) * FIXED_SCALE_F);
-                atomicAdd(reinterpret_cast<unsigned long long*>(st.sums + (int64_t)(off + pn) * d + k),
-                          (unsigned long long)v);
-                if (po >= 0)
-                    atomicAdd(reinterpret_cast<unsigned long long*>(st.sums + (int64_t)(off + po) * d + k),
-                              (unsigned long long)(-v));
+            const uint32_t nw[4] = {nv.x, nv.y, nv.z, nv.w}, ow[4] = {ov.x, ov.y, ov.z, ov.w};
+#pragma unroll
+            for (int h = 0; h < 8; ++h) {
+                const int c = g0 + h;
+                const int nl = (int16_t)(nw[h >> 1] >> (16 * (h & 1)));
+                const int ol = (int16_t)(ow[h >> 1] >> (16 * (h & 1)));
+                const bool ch = valid && c < b.n && st.active[c] && nl != ol;
+                if (ch) {
+                    st.labels[i * b.cs + c] = (int16_t)nl;
+                    atomicAdd(st.counts + b.off[c] + nl, 1);
+                    if (ol >= 0) atomicSub(st.counts + b.off[c] + ol, 1);
+                }
+                unsigned mask = __ballot_sync(0xffffffffu, ch);
+                if (lane == 0 && mask) atomicAdd(st.changed + (pass & 1) * MAXC + c, __popc(mask));
+                while (mask) {
+                    const int src = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const int64_t pi = __shfl_sync(0xffffffffu, i, src);
+                    const int pn = __shfl_sync(0xffffffffu, nl, src);
+                    const int po = __shfl_sync(0xffffffffu, ol, src);
+                    const int off = b.off[c];
+                    for (int k = lane; k < d; k += 32) {
+                        const long long v = __float2ll_rn(zval(Z, pi * d + k) * FIXED_SCALE_F);
+                        atomicAdd(reinterpret_cast<unsigned long long*>(st.sums + (int64_t)(off + pn) * d + k),
+                                  (unsigned long long)v);
+                        if (po >= 0)
+                            atomicAdd(reinterpret_cast<unsigned long long*>(st.sums + (int64_t)(off + po) * d + k),
+                                      (unsigned long long)(-v));
+                    }
+                }
             }
         }
     }
@@ -630,8 +636,7 @@ __global__ void __launch_bounds__(256) k_apply_changes(CandBatch b, const T* __r
 
 void launch_apply_changes(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, KmState st, int pass,
                           cudaStream_t s) {
-    const int64_t total = n * b.cs;
-    int64_t blocks = (total + 255) / 256;
+    int64_t blocks = (n + 255) / 256;
     const int64_t cap = (int64_t)num_sms() * 16;
     if (blocks > cap) blocks = cap;
     ProfScope ps(s, pass == 1 ? PF_APPLY_FIRST : PF_APPLY, 1);
