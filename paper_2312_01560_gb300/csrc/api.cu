@@ -100,6 +100,8 @@ struct EmbedWs {
     int32_t* deg;
     float* rs;
     float* rsh;
+    int32_t* heavy;        // rows of degree above 256 (gathered by a whole CTA)
+    int* heavy_count;
     float* W[RAFTGP_MAX_LAYERS];
     __nv_bfloat16* Whi[RAFTGP_MAX_LAYERS];  // BF16 form: W^T split into hi and lo for the tensor cores
     __nv_bfloat16* Wlo[RAFTGP_MAX_LAYERS];
@@ -121,6 +123,8 @@ static EmbedWs carve_embed(Carver& c, int64_t n, const raftgp_embed_opts* o) {
     w.deg = c.take<int32_t>(n);
     w.rs = c.take<float>(n);
     w.rsh = c.take<float>(n);
+    w.heavy = c.take<int32_t>(n);
+    w.heavy_count = c.take<int>(64);
     for (int k = 1; k <= o->n_layers; ++k) {
         w.W[k - 1] = c.take<float>((size_t)o->dims[k - 1] * o->dims[k]);
         w.Whi[k - 1] = c.take<__nv_bfloat16>((size_t)o->dims[k - 1] * o->dims[k]);
@@ -217,7 +221,7 @@ static raftgp_status run_embed(const raftgp_csr* g, const raftgp_embed_opts* o, 
     const int64_t n = g->n;
     const int L = o->dims[0];
     if (!degrees_done) {
-        launch_degrees(g, w.deg, w.rs, w.rsh, w.err, s);
+        launch_degrees(g, w.deg, w.rs, w.rsh, w.err, w.heavy, w.heavy_count, s);
         // no gather runs on a graph that failed the device checks
         raftgp_status st = read_error_word(w.err, s);
         if (st != RAFTGP_OK) return st;
@@ -238,7 +242,7 @@ static raftgp_status run_embed(const raftgp_csr* g, const raftgp_embed_opts* o, 
     cudaError_t e;
     if (o->n_layers == 0) {
         e = launch_layer(agg0, o->dtype, g, w.deg, w.rs, w.gvec, 2, nullptr, L, L, nullptr, w.bufB, Z,
-                         o->stage_out[0], s);
+                         o->stage_out[0], w.heavy, w.heavy_count, s);
         if (e != cudaSuccess) return cuda_fail(e, "projection");
         return RAFTGP_OK;
     }
@@ -248,14 +252,14 @@ static raftgp_status run_embed(const raftgp_csr* g, const raftgp_embed_opts* o, 
         for (int k = 1; k <= o->n_layers; ++k) launch_w_split(w.W[k - 1], o->dims[k - 1], o->dims[k], w.Whi[k - 1],
                                                               w.Wlo[k - 1], s);
         e = launch_layer(agg0, o->dtype, g, w.deg, w.rs, w.gvec, 0, nullptr, L, L, nullptr, w.bufB, w.bufA,
-                         o->stage_out[0], s);
+                         o->stage_out[0], w.heavy, w.heavy_count, s);
         if (e != cudaSuccess) return cuda_fail(e, "projection");
         e = launch_dense_tc(L, o->dims[1], n, w.bufA, w.Whi[0], w.Wlo[0], w.rsh, w.bufB, w.err, s);
         if (e != cudaSuccess) return cuda_fail(e, "dense layer");
         for (int k = 1; k <= o->n_layers; ++k) {
             const bool last = k == o->n_layers;
             e = launch_layer(AGG_GCN_, o->dtype, g, w.deg, w.rsh, nullptr, 1, nullptr, o->dims[k], o->dims[k], nullptr,
-                             w.bufB, last ? Z : w.bufA, o->stage_out[k], s);
+                             w.bufB, last ? Z : w.bufA, o->stage_out[k], w.heavy, w.heavy_count, s);
             if (e != cudaSuccess) return cuda_fail(e, "gcn layer");
             if (!last) {
                 e = launch_dense_tc(o->dims[k], o->dims[k + 1], n, w.bufA, w.Whi[k], w.Wlo[k], w.rsh, w.bufB, w.err, s);
@@ -266,7 +270,7 @@ static raftgp_status run_embed(const raftgp_csr* g, const raftgp_embed_opts* o, 
     }
     // FP32: layer 0 is the projection then x W1, prescaled by rsh for the first GCN gather
     e = launch_layer(agg0, o->dtype, g, w.deg, w.rs, w.gvec, 0, w.W[0], L, o->dims[1], w.rsh, w.bufB, w.bufA,
-                     o->stage_out[0], s);
+                     o->stage_out[0], w.heavy, w.heavy_count, s);
     if (e != cudaSuccess) return cuda_fail(e, "projection");
     void* cur = w.bufA;
     void* nxt = w.bufB;
@@ -274,7 +278,7 @@ static raftgp_status run_embed(const raftgp_csr* g, const raftgp_embed_opts* o, 
         const bool last = k == o->n_layers;
         e = launch_layer(AGG_GCN_, o->dtype, g, w.deg, w.rsh, nullptr, 1, last ? nullptr : w.W[k], o->dims[k],
                          last ? o->dims[k] : o->dims[k + 1], last ? nullptr : w.rsh, cur, last ? Z : nxt,
-                         o->stage_out[k], s);
+                         o->stage_out[k], w.heavy, w.heavy_count, s);
         if (e != cudaSuccess) return cuda_fail(e, "gcn layer");
         std::swap(cur, nxt);
     }
@@ -430,7 +434,7 @@ static raftgp_status run_select(const raftgp_csr* g, const void* Z, int d, int z
     const int kmax = (int)std::min<int64_t>(o->kmax, n);
     if (!degrees_done) {
         cudaMemsetAsync(w.err, 0, sizeof(uint32_t), s);
-        launch_degrees(g, w.deg, w.rs, w.rsh, w.err, s);
+        launch_degrees(g, w.deg, w.rs, w.rsh, w.err, nullptr, nullptr, s);
     }
     {
         int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8);
@@ -595,7 +599,7 @@ raftgp_status raftgp_score(const raftgp_csr* g, const int32_t* labels, int32_t K
     if (ws_bytes < c.off) return fail(RAFTGP_ENOMEM, "workspace too small");
     cudaStream_t s = (cudaStream_t)stream;
     cudaMemsetAsync(err, 0, sizeof(uint32_t), s);
-    launch_degrees(g, deg, rs, rsh, err, s);
+    launch_degrees(g, deg, rs, rsh, err, nullptr, nullptr, s);
     st = read_error_word(err, s);
     if (st) return st;
     cudaError_t e = launch_score_labels(g, deg, labels, K, reinterpret_cast<long long*>(m),

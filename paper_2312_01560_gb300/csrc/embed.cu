@@ -23,7 +23,7 @@ namespace raftgp {
 // Degrees, reciprocal square roots and graph checks (warp per row).
 // ------------------------------------------------------------------------------------
 __global__ void k_degrees(int64_t n, int64_t nnz, const int32_t* rp32, const int64_t* rp64, const int32_t* col,
-                          int32_t* deg, float* rs, float* rsh, uint32_t* err) {
+                          int32_t* deg, float* rs, float* rsh, uint32_t* err, int32_t* heavy, int* heavy_count) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -52,6 +52,7 @@ __global__ void k_degrees(int64_t n, int64_t nnz, const int32_t* rp32, const int
             deg[i] = (int32_t)d;
             rs[i] = d > 0 ? rsqrtf((float)d) : 0.0f;
             rsh[i] = rsqrtf((float)(d + 1));
+            if (heavy && d > 256) heavy[atomicAdd(heavy_count, 1)] = (int32_t)i;   // HEAVY_DEG
         }
     }
 }
@@ -157,30 +158,176 @@ struct LayerArgs {
     const float* postscale;  // multiplies the W product (rsh for the next GCN gather), or null
     void* out;               // N x (W ? lout : LIN) in T
     void* stage;             // optional N x LIN in T: the activated row before W
+    const int32_t* heavy;    // rows gathered by k_spmm_heavy (null: every row by k_spmm_layer)
+    const int* heavy_count;
 };
 
+// Rows with more neighbours than this are gathered by a whole CTA (k_spmm_heavy) instead of
+// one warp: on power-law graphs they carry a large share of the entries.
+constexpr int HEAVY_DEG = 256;
+
+template <typename T, int LIN>
+struct Lanes {
+    static constexpr int E = Vec<T>::E;   // elements per lane chunk (16 bytes)
+    static constexpr int LPR = LIN / E;   // lanes per gathered row
+    static constexpr int GPW = 32 / LPR;  // rows gathered concurrently per warp
+    static constexpr int U = 4;           // unrolled gathers per lane
+    static_assert(LPR >= 1 && LPR <= 32 && (32 % LPR) == 0, "bad width");
+};
+
+// Adds X[col[p]] for p in [beg, end) to this lane's chunk of the row sum (and, for the
+// reduced modularity operator, the d_j-weighted sum).  Lane groups take different neighbours;
+// the caller combines the groups.
+template <int AGG, typename T, int LIN>
+__device__ __forceinline__ void gather_range(const LayerArgs& a, const T* __restrict__ X, int64_t beg, int64_t end,
+                                             int lane, float* acc, float* accd) {
+    using Ln = Lanes<T, LIN>;
+    constexpr int E = Ln::E, GPW = Ln::GPW, U = Ln::U;
+    const int grp = lane / Ln::LPR, sub = lane % Ln::LPR;
+    for (int64_t base = beg; base < end; base += 32) {
+        const int cnt = (int)((end - base) < 32 ? (end - base) : 32);
+        const int32_t my_col = lane < cnt ? __ldg(a.col + base + lane) : 0;
+        float my_d = 0.f;
+        if constexpr (AGG == AGG_MOD_REDUCED) my_d = lane < cnt ? (float)__ldg(a.deg + my_col) : 0.f;
+        for (int t = 0; t < cnt; t += GPW * U) {
+            float v[U][E];
+            float dj[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int idx = t + u * GPW + grp;
+                const int src = idx < cnt ? idx : 0;
+                const int32_t j = __shfl_sync(0xffffffffu, my_col, src);
+                if constexpr (AGG == AGG_MOD_REDUCED) dj[u] = __shfl_sync(0xffffffffu, my_d, src);
+                if (idx < cnt) {
+                    Vec<T>::load(X + (int64_t)j * LIN + sub * E, v[u]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) v[u][e] = 0.f;
+                    dj[u] = 0.f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    acc[e] += v[u][e];
+                    if constexpr (AGG == AGG_MOD_REDUCED) accd[e] += dj[u] * v[u][e];
+                }
+            }
+        }
+    }
+}
+
+// Combines the lane groups of a warp: afterwards every group holds the warp's row sum.
+template <int AGG, typename T, int LIN>
+__device__ __forceinline__ void combine_groups(float* acc, float* accd) {
+    using Ln = Lanes<T, LIN>;
+#pragma unroll
+    for (int o = 16; o >= Ln::LPR; o >>= 1) {
+#pragma unroll
+        for (int e = 0; e < Ln::E; ++e) {
+            acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+            if constexpr (AGG == AGG_MOD_REDUCED) accd[e] += __shfl_xor_sync(0xffffffffu, accd[e], o);
+        }
+    }
+}
+
+// Row epilogue of row i from its full neighbour sum (held by every lane group): the operator's
+// row term, the activation, the optional stage output, then either the plain output row or
+// the dense layer out_i = postscale_i * (y W).  Executed by one full warp.
+template <int AGG, typename T, int LIN>
+__device__ __forceinline__ void row_epilogue(const LayerArgs& a, int64_t i, const float* acc, const float* accd,
+                                             int lane, float* vbuf, const float* Ws) {
+    using Ln = Lanes<T, LIN>;
+    constexpr int E = Ln::E, LPR = Ln::LPR;
+    const int grp = lane / LPR, sub = lane % LPR;
+    float y[E];
+    if constexpr (AGG == AGG_NCUT || AGG == AGG_GCN) {
+        const float s = a.rowscale[i];
+#pragma unroll
+        for (int e = 0; e < E; ++e) y[e] = s * acc[e];
+    } else if constexpr (AGG == AGG_MOD_FULL) {
+        const float c = (float)((double)a.deg[i] * a.inv_two_e);
+#pragma unroll
+        for (int e = 0; e < E; ++e) y[e] = acc[e] - c * a.g[sub * E + e];
+    } else {
+        const float c = (float)((double)a.deg[i] * a.inv_two_e);
+#pragma unroll
+        for (int e = 0; e < E; ++e) y[e] = acc[e] - c * accd[e];
+    }
+    if (a.act != 0) {
+        float ss = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            if (a.act == 1) y[e] = tanhf(y[e]);
+            ss += y[e] * y[e];
+        }
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        const float inv = ss > 0.f ? 1.0f / sqrtf(ss) : 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e) y[e] *= inv;
+    }
+    if (a.stage && grp == 0) Vec<T>::store(reinterpret_cast<T*>(a.stage) + i * LIN + sub * E, y);
+    if (!a.W) {
+        if (grp == 0) Vec<T>::store(reinterpret_cast<T*>(a.out) + i * LIN + sub * E, y);
+        return;
+    }
+    // dense layer: lane computes lout/32 adjacent columns from W in shared memory
+    if (grp == 0) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) vbuf[sub * E + e] = y[e];
+    }
+    __syncwarp();
+    const float ps = a.postscale ? a.postscale[i] : 1.0f;
+    T* orow = reinterpret_cast<T*>(a.out) + i * a.lout;
+    if (a.lout == 128) {
+        float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+        for (int k = 0; k < LIN; ++k) {
+            const float yk = vbuf[k];
+            const float4 w = *reinterpret_cast<const float4*>(Ws + k * 128 + 4 * lane);
+            o[0] += yk * w.x; o[1] += yk * w.y; o[2] += yk * w.z; o[3] += yk * w.w;
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) orow[4 * lane + c] = Vec<T>::from_float(o[c] * ps);
+    } else if (a.lout == 64) {
+        float o[2] = {0.f, 0.f};
+#pragma unroll 8
+        for (int k = 0; k < LIN; ++k) {
+            const float yk = vbuf[k];
+            const float2 w = *reinterpret_cast<const float2*>(Ws + k * 64 + 2 * lane);
+            o[0] += yk * w.x; o[1] += yk * w.y;
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c) orow[2 * lane + c] = Vec<T>::from_float(o[c] * ps);
+    } else {
+        float o = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < LIN; ++k) o += vbuf[k] * Ws[k * 32 + lane];
+        orow[lane] = Vec<T>::from_float(o * ps);
+    }
+    __syncwarp();
+}
+
+// Light rows: one warp per row (grid-stride), FP32 accumulation, fused row epilogue.
 template <int AGG, typename T, int LIN>
 __global__ void __launch_bounds__(256) k_spmm_layer(LayerArgs a, const T* __restrict__ X) {
-    constexpr int E = Vec<T>::E;             // elements per lane chunk (16 bytes)
-    constexpr int LPR = LIN / E;             // lanes per gathered row
-    constexpr int GPW = 32 / LPR;            // rows gathered concurrently per warp
-    constexpr int U = 4;                     // unrolled gathers per lane
-    static_assert(LPR >= 1 && LPR <= 32 && (32 % LPR) == 0, "bad width");
+    constexpr int E = Lanes<T, LIN>::E;
     extern __shared__ float smem[];
     float* Ws = smem;                                       // LIN x lout
-    const int warp_in_block = threadIdx.x >> 5;
-    float* vbuf = smem + (a.W ? LIN * a.lout : 0) + warp_in_block * LIN;
+    float* vbuf = smem + (a.W ? LIN * a.lout : 0) + (threadIdx.x >> 5) * LIN;
     if (a.W) {
         for (int t = threadIdx.x; t < LIN * a.lout; t += blockDim.x) Ws[t] = a.W[t];
         __syncthreads();
     }
     const int lane = threadIdx.x & 31;
-    const int grp = lane / LPR;
-    const int sub = lane % LPR;
+    const int grp = lane / Lanes<T, LIN>::LPR, sub = lane % Lanes<T, LIN>::LPR;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < a.n; i += nwarps) {
         const int64_t beg = a.rp64 ? a.rp64[i] : a.rp32[i];
         const int64_t end = a.rp64 ? a.rp64[i + 1] : a.rp32[i + 1];
+        if (a.heavy && end - beg > HEAVY_DEG) continue;     // gathered by k_spmm_heavy
         float acc[E];
         float accd[AGG == AGG_MOD_REDUCED ? E : 1];
 #pragma unroll
@@ -192,115 +339,70 @@ __global__ void __launch_bounds__(256) k_spmm_layer(LayerArgs a, const T* __rest
         if constexpr (AGG == AGG_GCN) {
             if (grp == 0) Vec<T>::load(X + i * LIN + sub * E, acc);   // the self loop of A + I
         }
-        for (int64_t base = beg; base < end; base += 32) {
-            const int cnt = (int)((end - base) < 32 ? (end - base) : 32);
-            const int32_t my_col = lane < cnt ? __ldg(a.col + base + lane) : 0;
-            float my_d = 0.f;
-            if constexpr (AGG == AGG_MOD_REDUCED) my_d = lane < cnt ? (float)__ldg(a.deg + my_col) : 0.f;
-            for (int t = 0; t < cnt; t += GPW * U) {
-                float v[U][E];
-                float dj[U];
+        gather_range<AGG, T, LIN>(a, X, beg, end, lane, acc, accd);
+        combine_groups<AGG, T, LIN>(acc, accd);
+        row_epilogue<AGG, T, LIN>(a, i, acc, accd, lane, vbuf, a.W ? Ws : nullptr);
+    }
+}
+
+// Heavy rows: one CTA of 8 warps per row; each warp gathers a fixed slice of the neighbour
+// list, the slices are added in warp order (deterministic), then warp 0 runs the epilogue.
+template <int AGG, typename T, int LIN>
+__global__ void __launch_bounds__(256) k_spmm_heavy(LayerArgs a, const T* __restrict__ X) {
+    constexpr int E = Lanes<T, LIN>::E, LPR = Lanes<T, LIN>::LPR;
+    constexpr int NW = 8;
+    extern __shared__ float smem[];
+    float* Ws = smem;                                       // LIN x lout
+    float* vbuf = smem + (a.W ? LIN * a.lout : 0);          // LIN
+    float* part = vbuf + LIN;                               // NW x LIN (and NW x LIN for accd)
+    if (a.W) {
+        for (int t = threadIdx.x; t < LIN * a.lout; t += blockDim.x) Ws[t] = a.W[t];
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int grp = lane / LPR, sub = lane % LPR;
+    const int nheavy = *a.heavy_count;
+    for (int h = blockIdx.x; h < nheavy; h += gridDim.x) {
+        const int64_t i = a.heavy[h];
+        const int64_t beg = a.rp64 ? a.rp64[i] : a.rp32[i];
+        const int64_t end = a.rp64 ? a.rp64[i + 1] : a.rp32[i + 1];
+        const int64_t chunk = ((end - beg + NW - 1) / NW + 31) / 32 * 32;
+        const int64_t b0 = beg + w * chunk;
+        const int64_t b1 = b0 + chunk < end ? b0 + chunk : end;
+        float acc[E];
+        float accd[AGG == AGG_MOD_REDUCED ? E : 1];
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int idx = t + u * GPW + grp;
-                    const int src = idx < cnt ? idx : 0;
-                    const int32_t j = __shfl_sync(0xffffffffu, my_col, src);
-                    if constexpr (AGG == AGG_MOD_REDUCED) dj[u] = __shfl_sync(0xffffffffu, my_d, src);
-                    if (idx < cnt) {
-                        Vec<T>::load(X + (int64_t)j * LIN + sub * E, v[u]);
-                    } else {
+        for (int e = 0; e < E; ++e) acc[e] = 0.f;
+        if constexpr (AGG == AGG_MOD_REDUCED) {
 #pragma unroll
-                        for (int e = 0; e < E; ++e) v[u][e] = 0.f;
-                        dj[u] = 0.f;
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-#pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        acc[e] += v[u][e];
-                        if constexpr (AGG == AGG_MOD_REDUCED) accd[e] += dj[u] * v[u][e];
-                    }
-                }
-            }
+            for (int e = 0; e < E; ++e) accd[e] = 0.f;
         }
-        // combine the GPW concurrent partial sums: afterwards every group holds the row
-#pragma unroll
-        for (int o = 16; o >= LPR; o >>= 1) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
-                if constexpr (AGG == AGG_MOD_REDUCED) accd[e] += __shfl_xor_sync(0xffffffffu, accd[e], o);
-            }
+        if constexpr (AGG == AGG_GCN) {
+            if (w == 0 && grp == 0) Vec<T>::load(X + i * LIN + sub * E, acc);   // the self loop of A + I
         }
-        // operator epilogue
-        float y[E];
-        if constexpr (AGG == AGG_NCUT || AGG == AGG_GCN) {
-            const float s = a.rowscale[i];
-#pragma unroll
-            for (int e = 0; e < E; ++e) y[e] = s * acc[e];
-        } else if constexpr (AGG == AGG_MOD_FULL) {
-            const float c = (float)((double)a.deg[i] * a.inv_two_e);
-#pragma unroll
-            for (int e = 0; e < E; ++e) y[e] = acc[e] - c * a.g[sub * E + e];
-        } else {
-            const float c = (float)((double)a.deg[i] * a.inv_two_e);
-#pragma unroll
-            for (int e = 0; e < E; ++e) y[e] = acc[e] - c * accd[e];
-        }
-        if (a.act != 0) {
-            float ss = 0.f;
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                if (a.act == 1) y[e] = tanhf(y[e]);
-                ss += y[e] * y[e];
-            }
-#pragma unroll
-            for (int o = LPR / 2; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-            const float inv = ss > 0.f ? 1.0f / sqrtf(ss) : 0.f;
-#pragma unroll
-            for (int e = 0; e < E; ++e) y[e] *= inv;
-        }
-        if (a.stage && grp == 0) Vec<T>::store(reinterpret_cast<T*>(a.stage) + i * LIN + sub * E, y);
-        if (!a.W) {
-            if (grp == 0) Vec<T>::store(reinterpret_cast<T*>(a.out) + i * LIN + sub * E, y);
-            continue;
-        }
-        // dense layer: out_i = postscale_i * (y W), lane computes lout/32 adjacent columns
+        if (b0 < b1) gather_range<AGG, T, LIN>(a, X, b0, b1, lane, acc, accd);
+        combine_groups<AGG, T, LIN>(acc, accd);
+        __syncthreads();   // previous row's epilogue is done with part[]
         if (grp == 0) {
 #pragma unroll
-            for (int e = 0; e < E; ++e) vbuf[sub * E + e] = y[e];
-        }
-        __syncwarp();
-        const float ps = a.postscale ? a.postscale[i] : 1.0f;
-        T* orow = reinterpret_cast<T*>(a.out) + i * a.lout;
-        if (a.lout == 128) {
-            float o[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 8
-            for (int k = 0; k < LIN; ++k) {
-                const float yk = vbuf[k];
-                const float4 w = *reinterpret_cast<const float4*>(Ws + k * 128 + 4 * lane);
-                o[0] += yk * w.x; o[1] += yk * w.y; o[2] += yk * w.z; o[3] += yk * w.w;
+            for (int e = 0; e < E; ++e) {
+                part[w * LIN + sub * E + e] = acc[e];
+                if constexpr (AGG == AGG_MOD_REDUCED) part[(NW + w) * LIN + sub * E + e] = accd[e];
             }
-#pragma unroll
-            for (int c = 0; c < 4; ++c) orow[4 * lane + c] = Vec<T>::from_float(o[c] * ps);
-        } else if (a.lout == 64) {
-            float o[2] = {0.f, 0.f};
-#pragma unroll 8
-            for (int k = 0; k < LIN; ++k) {
-                const float yk = vbuf[k];
-                const float2 w = *reinterpret_cast<const float2*>(Ws + k * 64 + 2 * lane);
-                o[0] += yk * w.x; o[1] += yk * w.y;
-            }
-#pragma unroll
-            for (int c = 0; c < 2; ++c) orow[2 * lane + c] = Vec<T>::from_float(o[c] * ps);
-        } else {
-            float o = 0.f;
-#pragma unroll 8
-            for (int k = 0; k < LIN; ++k) o += vbuf[k] * Ws[k * 32 + lane];
-            orow[lane] = Vec<T>::from_float(o * ps);
         }
-        __syncwarp();
+        __syncthreads();
+        if (w == 0) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                float s = 0.f, sd = 0.f;
+                for (int q = 0; q < NW; ++q) {
+                    s += part[q * LIN + sub * E + e];
+                    if constexpr (AGG == AGG_MOD_REDUCED) sd += part[(NW + q) * LIN + sub * E + e];
+                }
+                acc[e] = s;
+                if constexpr (AGG == AGG_MOD_REDUCED) accd[e] = sd;
+            }
+            row_epilogue<AGG, T, LIN>(a, i, acc, accd, lane, vbuf, a.W ? Ws : nullptr);
+        }
     }
 }
 
@@ -318,14 +420,16 @@ int num_sms() {
     return g_num_sms;
 }
 
-void launch_degrees(const raftgp_csr* g, int32_t* deg, float* rs, float* rsh, uint32_t* err, cudaStream_t s) {
+void launch_degrees(const raftgp_csr* g, int32_t* deg, float* rs, float* rsh, uint32_t* err, int32_t* heavy,
+                    int* heavy_count, cudaStream_t s) {
+    if (heavy) cudaMemsetAsync(heavy_count, 0, sizeof(int), s);
     const int threads = 256;
     int64_t blocks = (g->n * 32 + threads - 1) / threads;
     blocks = blocks < 1 ? 1 : (blocks > (int64_t)num_sms() * 16 ? (int64_t)num_sms() * 16 : blocks);
     ProfScope ps(s, PF_DEGREES, 1);
     k_degrees<<<(unsigned)blocks, threads, 0, s>>>(
         g->n, g->nnz, g->row_ptr_bits == 32 ? (const int32_t*)g->row_ptr : nullptr,
-        g->row_ptr_bits == 64 ? (const int64_t*)g->row_ptr : nullptr, g->col, deg, rs, rsh, err);
+        g->row_ptr_bits == 64 ? (const int64_t*)g->row_ptr : nullptr, g->col, deg, rs, rsh, err, heavy, heavy_count);
 }
 
 int theta_blocks(int64_t n) {
@@ -370,8 +474,17 @@ static cudaError_t launch_layer_t(const LayerArgs& a, const void* X, cudaStream_
     const int64_t cap = (int64_t)num_sms() * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    ProfScope ps(s, AGG == AGG_GCN ? PF_SPMM_GCN : PF_SPMM_PROJ, 1);
+    ProfScope ps(s, AGG == AGG_GCN ? PF_SPMM_GCN : PF_SPMM_PROJ, a.heavy ? 2 : 1);
     kern<<<(unsigned)blocks, threads, smem, s>>>(a, reinterpret_cast<const T*>(X));
+    if (a.heavy) {
+        const size_t hsmem = (size_t)((a.W ? LIN * a.lout : 0) + LIN + 2 * 8 * LIN) * sizeof(float);
+        auto hk = k_spmm_heavy<AGG, T, LIN>;
+        if (hsmem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(hk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem);
+            if (e != cudaSuccess) return e;
+        }
+        hk<<<(unsigned)(num_sms() * 4), 256, hsmem, s>>>(a, reinterpret_cast<const T*>(X));
+    }
     return cudaGetLastError();
 }
 
@@ -398,8 +511,11 @@ static cudaError_t launch_layer_a(int agg, const LayerArgs& a, int lin, const vo
 
 cudaError_t launch_layer(int agg, int dtype, const raftgp_csr* g, const int32_t* deg, const float* rowscale,
                          const float* gvec, int act, const float* W, int lin, int lout, const float* postscale,
-                         const void* X, void* out, void* stage, cudaStream_t s) {
+                         const void* X, void* out, void* stage, const int32_t* heavy, const int* heavy_count,
+                         cudaStream_t s) {
     LayerArgs a;
+    a.heavy = heavy;
+    a.heavy_count = heavy_count;
     a.n = g->n;
     a.rp32 = g->row_ptr_bits == 32 ? (const int32_t*)g->row_ptr : nullptr;
     a.rp64 = g->row_ptr_bits == 64 ? (const int64_t*)g->row_ptr : nullptr;

@@ -33,14 +33,18 @@ class ProfScope {
 
 // ---- embedding (embed.cu) -----------------------------------------------------------
 enum { AGG_NCUT_ = 0, AGG_MOD_FULL_ = 1, AGG_MOD_REDUCED_ = 2, AGG_GCN_ = 3 };
-void launch_degrees(const raftgp_csr* g, int32_t* deg, float* rs, float* rsh, uint32_t* err, cudaStream_t s);
+// Degrees, scales and graph checks; if `heavy` is given, the rows gathered by a whole CTA
+// (degree above 256) are listed there and counted in *heavy_count.
+void launch_degrees(const raftgp_csr* g, int32_t* deg, float* rs, float* rsh, uint32_t* err, int32_t* heavy,
+                    int* heavy_count, cudaStream_t s);
 int theta_blocks(int64_t n);
 void launch_theta(int64_t n, int L, int dtype, uint64_t seed, const float* user_theta, const float* colscale,
                   const int32_t* deg, void* theta, double* partial, float* gvec, cudaStream_t s);
 void launch_weights(int layer, int lin, int lout, uint64_t seed, float* W, cudaStream_t s);
 cudaError_t launch_layer(int agg, int dtype, const raftgp_csr* g, const int32_t* deg, const float* rowscale,
                          const float* gvec, int act, const float* W, int lin, int lout, const float* postscale,
-                         const void* X, void* out, void* stage, cudaStream_t s);
+                         const void* X, void* out, void* stage, const int32_t* heavy, const int* heavy_count,
+                         cudaStream_t s);
 
 // ---- dense layer on tensor cores (dense_tc.cu) -----------------------------------------
 void launch_w_split(const float* W, int lin, int lout, __nv_bfloat16* whi, __nv_bfloat16* wlo, cudaStream_t s);

@@ -589,6 +589,9 @@ __global__ void __launch_bounds__(256) k_apply_changes(CandBatch b, const T* __r
                                                        KmState st, int pass) {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    unsigned long long act = 0;   // candidates reassigned in this pass
+    for (int c = 0; c < b.n; ++c)
+        if (st.active[c]) act |= 1ull << c;
     // thread per point; its label row (cs int16 = whole 16-byte vectors) is read once
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
         const int64_t i = base + threadIdx.x;
@@ -605,7 +608,7 @@ __global__ void __launch_bounds__(256) k_apply_changes(CandBatch b, const T* __r
                 const int c = g0 + h;
                 const int nl = (int16_t)(nw[h >> 1] >> (16 * (h & 1)));
                 const int ol = (int16_t)(ow[h >> 1] >> (16 * (h & 1)));
-                const bool ch = valid && c < b.n && st.active[c] && nl != ol;
+                const bool ch = valid && c < b.n && ((act >> c) & 1ull) && nl != ol;
                 if (ch) {
                     st.labels[i * b.cs + c] = (int16_t)nl;
                     atomicAdd(st.counts + b.off[c] + nl, 1);
