@@ -214,6 +214,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="bf16", choices=["bf16", "f32"])
+    ap.add_argument("--assign", default=None, choices=["tc", "tc8", "ffma"],
+                    help="k-means engine (default: tc8 for bf16, ffma for f32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -265,7 +267,7 @@ def main():
     dg = api.DeviceGraph.from_host(g, dev, row_ptr_bits=64)
     labels = torch.empty(g.n, dtype=torch.int32, device=dev)
     dtype = args.form
-    assign = "tc" if args.form == "bf16" else "ffma"
+    assign = args.assign or ("tc8" if args.form == "bf16" else "ffma")
     kw = dict(op=wl["op"], dims=wl["dims"], dtype=dtype, kmin=wl["kmin"], kmax=wl["kmax"], grid=wl["grid"],
               iters=wl["iters"], assign=assign, batch=0, labels=labels)
 
@@ -341,6 +343,8 @@ def main():
         cpu = {"value": v, "unit": "edges/s", "cores": 1, "kind": "oracle", "sample": desc,
                "cpu_seconds": round(spent, 2)}
 
+    free_b, total_b = torch.cuda.mem_get_info(dev)
+    print("device memory in use at exit: %.2f GB" % ((total_b - free_b) / 1e9), file=sys.stderr, flush=True)
     if rank == 0:
         line = {"metric": "end-to-end edges/s at 1M nodes", "value": value, "unit": "edges/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,

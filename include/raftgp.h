@@ -56,9 +56,12 @@ typedef enum {
 enum { RAFTGP_OP_NCUT = 0, RAFTGP_OP_MOD_FULL = 1, RAFTGP_OP_MOD_REDUCED = 2 };
 enum { RAFTGP_F32 = 0, RAFTGP_BF16 = 1 };
 enum { RAFTGP_CRIT_MOD = 0, RAFTGP_CRIT_NCUT = 1 };
-/* k-means distance engine: plain FP32 FMA, or BF16 tcgen05 tensor cores with an FP32
- * re-check of near ties in the final assignment. */
-enum { RAFTGP_ASSIGN_FFMA = 0, RAFTGP_ASSIGN_TC = 1 };
+/* k-means distance engine: plain FP32 FMA; or BF16 tcgen05 tensor cores with the centroids
+ * split into BF16 hi + lo halves (~16-bit products) and an FP32 re-check of near ties in the
+ * final assignment (RAFTGP_ASSIGN_TC); or the same with the hi half only in the Lloyd passes
+ * (8-bit centroid products; the final assignment is still hi + lo with the FP32 re-check)
+ * (RAFTGP_ASSIGN_TC8). */
+enum { RAFTGP_ASSIGN_FFMA = 0, RAFTGP_ASSIGN_TC = 1, RAFTGP_ASSIGN_TC8 = 2 };
 
 #define RAFTGP_MAX_LAYERS 4
 #define RAFTGP_MAX_BATCH_CAND 64 /* candidates evaluated together in one batch */
@@ -92,7 +95,7 @@ typedef struct {
                            G refined values between the neighbours of the best coarse K */
     int32_t iters;      /* maximum Lloyd assignment passes per candidate (>= 1) */
     int32_t criterion;  /* RAFTGP_CRIT_MOD (default) or RAFTGP_CRIT_NCUT */
-    int32_t assign;     /* RAFTGP_ASSIGN_FFMA or RAFTGP_ASSIGN_TC */
+    int32_t assign;     /* RAFTGP_ASSIGN_FFMA, RAFTGP_ASSIGN_TC or RAFTGP_ASSIGN_TC8 */
     int32_t batch;      /* candidates evaluated together (1 = one at a time, the plain form;
                            0 = as many as fit, at most RAFTGP_MAX_BATCH_CAND) */
     uint64_t seed;      /* Philox4x32-10 key for k-means++ */

@@ -16,7 +16,7 @@ STATUS_NAMES = {0: "RAFTGP_OK", 1: "RAFTGP_EINVAL", 2: "RAFTGP_ENOMEM", 3: "RAFT
 OP = {"ncut": 0, "mod_full": 1, "mod_reduced": 2}
 DTYPE = {"f32": 0, "bf16": 1}
 CRIT = {"mod": 0, "ncut": 1}
-ASSIGN = {"ffma": 0, "tc": 1}
+ASSIGN = {"ffma": 0, "tc": 1, "tc8": 2}
 MAX_LAYERS = 4
 MAX_BATCH_CAND = 64
 

@@ -87,7 +87,7 @@ static raftgp_status check_select(const raftgp_select_opts* o, int64_t n) {
     if (o->grid < 0 || o->grid > RAFTGP_MAX_BATCH_CAND) return fail(RAFTGP_EINVAL, "grid out of range");
     if (o->iters < 1) return fail(RAFTGP_EINVAL, "iters must be >= 1");
     if (o->criterion != RAFTGP_CRIT_MOD && o->criterion != RAFTGP_CRIT_NCUT) return fail(RAFTGP_EINVAL, "unknown criterion");
-    if (o->assign != RAFTGP_ASSIGN_FFMA && o->assign != RAFTGP_ASSIGN_TC) return fail(RAFTGP_EINVAL, "unknown assign engine");
+    if (o->assign < RAFTGP_ASSIGN_FFMA || o->assign > RAFTGP_ASSIGN_TC8) return fail(RAFTGP_EINVAL, "unknown assign engine");
     if (o->batch < 0) return fail(RAFTGP_EINVAL, "batch < 0");
     return RAFTGP_OK;
 }
@@ -343,16 +343,17 @@ static bool host_better(int criterion, const CandRecord& a, const CandRecord& b)
 static raftgp_status run_lloyd(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, int iters, int engine,
                                KmState km, int2* recheck, int* recheck_count, uint32_t* err, cudaStream_t s) {
     for (int pass = 1; pass <= iters; ++pass) {
-        cudaError_t e = engine == RAFTGP_ASSIGN_TC
-                            ? launch_assign_tc(b, Z, n, d, km, pass, 0, nullptr, nullptr, err, s)
-                            : launch_assign_ffma(b, Z, zdtype, n, d, km, pass, s);
+        const bool tc = engine != RAFTGP_ASSIGN_FFMA;
+        cudaError_t e = tc ? launch_assign_tc(b, Z, n, d, km, pass, 0, engine == RAFTGP_ASSIGN_TC ? 1 : 0, nullptr,
+                                              nullptr, err, s)
+                           : launch_assign_ffma(b, Z, zdtype, n, d, km, pass, s);
         if (e != cudaSuccess) return cuda_fail(e, "assign");
-        if (engine == RAFTGP_ASSIGN_TC) launch_apply_changes(b, Z, zdtype, n, d, km, pass, s);
+        if (tc) launch_apply_changes(b, Z, zdtype, n, d, km, pass, s);
         launch_lloyd_update(b, d, km, pass, iters, s);
     }
-    if (engine == RAFTGP_ASSIGN_TC) {
+    if (engine != RAFTGP_ASSIGN_FFMA) {
         cudaMemsetAsync(recheck_count, 0, sizeof(int), s);
-        cudaError_t e = launch_assign_tc(b, Z, n, d, km, iters + 1, 1, recheck, recheck_count, err, s);
+        cudaError_t e = launch_assign_tc(b, Z, n, d, km, iters + 1, 1, 1, recheck, recheck_count, err, s);
         if (e != cudaSuccess) return cuda_fail(e, "final assign");
         launch_recheck(b, Z, d, km, recheck, recheck_count, s);
     }
@@ -544,7 +545,7 @@ raftgp_status raftgp_select(const raftgp_csr* g, const void* Z, int32_t d, int32
     if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d = %d: must be 32, 64 or 128", d);
     if (z_dtype != RAFTGP_F32 && z_dtype != RAFTGP_BF16) return fail(RAFTGP_EINVAL, "unknown z_dtype");
     if (!Z || !labels || !ws) return fail(RAFTGP_EINVAL, "Z, labels or workspace is NULL");
-    if (sopts->assign == RAFTGP_ASSIGN_TC && z_dtype != RAFTGP_BF16)
+    if (sopts->assign != RAFTGP_ASSIGN_FFMA && z_dtype != RAFTGP_BF16)
         return fail(RAFTGP_EINVAL, "tensor-core assignment needs BF16 embeddings");
     if (ws_bytes < raftgp_workspace_size(g, nullptr, sopts, d)) return fail(RAFTGP_ENOMEM, "workspace too small");
     cudaStream_t s = (cudaStream_t)stream;
@@ -565,7 +566,7 @@ raftgp_status raftgp_partition(const raftgp_csr* g, const raftgp_embed_opts* eop
     if ((st = check_embed(eopts))) return st;
     if ((st = check_select(sopts, g->n))) return st;
     if (!labels || !ws) return fail(RAFTGP_EINVAL, "labels or workspace is NULL");
-    if (sopts->assign == RAFTGP_ASSIGN_TC && eopts->dtype != RAFTGP_BF16)
+    if (sopts->assign != RAFTGP_ASSIGN_FFMA && eopts->dtype != RAFTGP_BF16)
         return fail(RAFTGP_EINVAL, "tensor-core assignment needs BF16 embeddings");
     if (ws_bytes < raftgp_workspace_size(g, eopts, sopts, 0)) return fail(RAFTGP_ENOMEM, "workspace too small");
     cudaStream_t s = (cudaStream_t)stream;
@@ -644,8 +645,8 @@ raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype,
     if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d must be 32, 64 or 128");
     if (K < 1 || K > 32767) return fail(RAFTGP_EINVAL, "need 1 <= K <= 32767");
     if (iters < 1) return fail(RAFTGP_EINVAL, "iters must be >= 1");
-    if (assign != RAFTGP_ASSIGN_FFMA && assign != RAFTGP_ASSIGN_TC) return fail(RAFTGP_EINVAL, "unknown assign engine");
-    if (assign == RAFTGP_ASSIGN_TC && z_dtype != RAFTGP_BF16)
+    if (assign < RAFTGP_ASSIGN_FFMA || assign > RAFTGP_ASSIGN_TC8) return fail(RAFTGP_EINVAL, "unknown assign engine");
+    if (assign != RAFTGP_ASSIGN_FFMA && z_dtype != RAFTGP_BF16)
         return fail(RAFTGP_EINVAL, "tensor-core assignment needs BF16 embeddings");
     Carver c(ws);
     KmState km{};

@@ -8,6 +8,11 @@
 // significant bits of mu instead of 8.  The epilogue reads the accumulator with tcgen05.ld
 // (thread t owns TMEM lane t = point t) and keeps, per candidate K, the argmin of
 //     ||mu_c||^2 - 2 D[p][c]        (= ||z_p - mu_c||^2 - ||z_p||^2, ties to the lowest c).
+// In the Lloyd passes a constant K=16 slice adds (||mu_c||^2 + 4)/2 + 128 to the product, so
+// the accumulator is 128 + (||z_p - mu_c||^2 - ||z_p||^2 + 4)/2, inside [128, 256) for unit
+// rows: there its FP32 bit pattern is 0x43000000 + m with m the score on a 2^-16 grid, and one
+// integer multiply-add turns it into the key 64 m + column, whose minimum gives score and
+// column at once.
 //
 // Warp roles in a persistent CTA (one per SM): warp 0 issues TMA loads (the point tile once
 // per tile, centroid chunks through a STAGES-deep ring), warp 1 allocates tensor memory and
@@ -15,7 +20,7 @@
 // wait is bounded: on timeout the CTA raises an abort flag, records DERR_TIMEOUT, drains its
 // in-flight copies and MMAs (again bounded), frees its tensor memory and returns.
 //
-// Modes: FAST (Lloyd passes) writes the new labels (k_apply_changes then counts the changes
+// Modes: FAST (Lloyd passes; the lo half is optional there) writes the new labels (k_apply_changes then counts the changes
 // and applies them to the 2^-40 fixed-point centroid sums); FINAL (the assignment whose labels
 // are reported) also tracks the second-best score and lists every (point, candidate) whose best
 // two scores lie within the error band of the BF16 product, for an exact FP32 re-check.
@@ -29,7 +34,9 @@
 
 namespace raftgp {
 
-template <int D>
+// LO: the centroid chunks carry the lo half too (FINAL always; FAST optionally).  Without it a
+// ring stage is smaller, so the ring gets deeper.
+template <int D, bool LO = true>
 struct TcCfg {
     static constexpr int ATOM = D < 64 ? D : 64;          // K elements per swizzle-atom row
     static constexpr int ATOM_BYTES = ATOM * 2;           // 64 or 128
@@ -38,7 +45,7 @@ struct TcCfg {
     static constexpr int GROUPS = 4;                      // point tiles per CTA step, one per epilogue group
     static constexpr int ACC_BUFS = 1;                    // accumulator buffers per group
     static constexpr int A_BUFS = D == 128 ? 1 : 2;       // point-tile groups in flight
-    static constexpr int STAGES = D == 128 ? 1 : (D == 64 ? 2 : 4);
+    static constexpr int STAGES = LO ? (D == 128 ? 1 : (D == 64 ? 2 : 4)) : (D == 128 ? 2 : (D == 64 ? 4 : 8));
     static constexpr int A_ATOM_BYTES = 128 * ATOM_BYTES;
     static constexpr int A_TILE_BYTES = NATOM * A_ATOM_BYTES;     // one 128-point tile
     static constexpr int A_BYTES = GROUPS * A_TILE_BYTES;         // one group of tiles
@@ -46,7 +53,8 @@ struct TcCfg {
     static constexpr int B_ATOM_BYTES = NCH * ATOM_BYTES;
     static constexpr int B_BYTES = NATOM * B_ATOM_BYTES;  // one half (hi or lo) of a chunk
     static constexpr int AUG_B_BYTES = NCH * 32;          // the K=16 norm slice of a chunk
-    static constexpr int STAGE_BYTES = 2 * B_BYTES + AUG_B_BYTES;
+    static constexpr int NHALF = LO ? 2 : 1;              // hi (and lo) halves per ring stage
+    static constexpr int STAGE_BYTES = NHALF * B_BYTES + AUG_B_BYTES;
     static constexpr int LAYOUT = ATOM_BYTES == 128 ? 2 : 4;  // descriptor swizzle: 128B or 64B
     static constexpr int SBO = 8 * ATOM_BYTES;                 // stride between 8-row groups
     static constexpr int SMEM = 1024 + A_BUFS * A_BYTES + AUG_A_BYTES + STAGES * STAGE_BYTES;
@@ -82,18 +90,19 @@ struct TcArgs {
     KmState st;
     int pass;                 // FAST: pass number (parity selects the change counter)
     int final_mode;           // 1 = FINAL
+    uint32_t key_mul;         // 64 (a run-time operand, so the key is one integer multiply-add)
     float tie_band;           // FINAL: second-best within this band -> re-check
     int2* recheck;            // FINAL: list of (point, candidate)
     int* recheck_count;
     uint32_t* err;
 };
 
-template <int D>
+template <int D, bool LO>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_assign_tc(const __grid_constant__ TcArgs a, const __grid_constant__ CUtensorMap tmA,
                 const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
                 const __grid_constant__ CUtensorMap tmAug) {
-    using C = TcCfg<D>;
+    using C = TcCfg<D, LO>;
     extern __shared__ uint8_t dyn_smem[];
     __shared__ TcCtl ctl;
     uint8_t* base = (uint8_t*)(((uintptr_t)dyn_smem + 1023) & ~(uintptr_t)1023);
@@ -102,6 +111,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint8_t* sB = sAug + C::AUG_A_BYTES;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const CandBatch& b = a.b;
+    constexpr bool use_lo = LO;
 
     if (threadIdx.x == 0) {
         ctl.abort = 0;
@@ -147,10 +157,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         ctl.nchunks = nch;
     }
-    // constant K=16 slice of a point tile: every row reads 1, 1 at K = 0, 1 (and again at 8, 9,
-    // so the row is the same under the 32-byte swizzle, which may exchange its two halves)
+    // constant K=16 slice of a point tile: every row reads 1, 1, 1 at K = 0, 1, 2 (and again at
+    // 8, 9, 10, so the row is the same under the 32-byte swizzle, which may exchange its halves)
     for (int t = threadIdx.x; t < C::AUG_A_BYTES / 16; t += blockDim.x)
-        reinterpret_cast<uint4*>(sAug)[t] = make_uint4(0x3F803F80u, 0u, 0u, 0u);
+        reinterpret_cast<uint4*>(sAug)[t] = make_uint4(0x3F803F80u, 0x00003F80u, 0u, 0u);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_addr(&ctl.tmem_base)));
@@ -183,10 +193,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     mbar_expect_tx(&ctl.b_full[s], C::STAGE_BYTES);
                     for (int t = 0; t < C::NATOM; ++t) {
                         tma_load_2d(dst + t * C::B_ATOM_BYTES, &tmBhi, &ctl.b_full[s], t * C::ATOM, ctl.chunk_col[q]);
-                        tma_load_2d(dst + C::B_BYTES + t * C::B_ATOM_BYTES, &tmBlo, &ctl.b_full[s], t * C::ATOM,
-                                    ctl.chunk_col[q]);
+                        if (use_lo)
+                            tma_load_2d(dst + C::B_BYTES + t * C::B_ATOM_BYTES, &tmBlo, &ctl.b_full[s], t * C::ATOM,
+                                        ctl.chunk_col[q]);
                     }
-                    tma_load_2d(dst + 2 * C::B_BYTES, &tmAug, &ctl.b_full[s], 0, ctl.chunk_col[q]);
+                    tma_load_2d(dst + C::NHALF * C::B_BYTES, &tmAug, &ctl.b_full[s], 0, ctl.chunk_col[q]);
                 }
             }
             if (!ok) {
@@ -206,7 +217,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint64_t dA = smem_desc(smem_addr(sA), C::LAYOUT, C::SBO);
             const uint64_t dB = smem_desc(smem_addr(sB), C::LAYOUT, C::SBO);
             const uint64_t dAugA = smem_desc(smem_addr(sAug), 6, 256);
-            const uint64_t dAugB = smem_desc(smem_addr(sB + 2 * C::B_BYTES), 6, 256);
+            const uint64_t dAugB = smem_desc(smem_addr(sB + C::NHALF * C::B_BYTES), 6, 256);
             int it = 0, tl = 0;
             bool ok = true;
             for (int64_t step = blockIdx.x; step < nsteps && ok; step += gridDim.x, ++tl) {
@@ -227,9 +238,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         tc_fence_after();
                         const uint32_t dcol = tmem + (uint32_t)((g * C::ACC_BUFS + buf) * C::NCH);
                         const uint64_t dAg = dAgrp + (uint64_t)((g * C::A_TILE_BYTES) >> 4);
-                        // -z.mu from the BF16 hi and lo halves of -mu
+                        // -z.mu from the BF16 hi (and lo) halves of -mu
 #pragma unroll
                         for (int half = 0; half < 2; ++half)
+                            if (half < C::NHALF)
 #pragma unroll
                             for (int t = 0; t < C::NATOM; ++t)
 #pragma unroll
@@ -239,8 +251,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                         dBst + (uint64_t)((half * C::B_BYTES + t * C::B_ATOM_BYTES + k * 32) >> 4);
                                     mma_bf16(dcol, ad, bd, idesc, (half | t | k) ? 1 : 0);
                                 }
-                        // FAST: + (||mu||^2 + 4)/2 from the constant slice, so the accumulator is
-                        // the positive score (||z - mu||^2 - ||z||^2 + 4)/2 itself
+                        // FAST: + (||mu||^2 + 4)/2 + 128 from the constant slice, so the accumulator
+                        // is 128 + (||z - mu||^2 - ||z||^2 + 4)/2
                         if (!a.final_mode) mma_bf16(dcol, dAugA, dAugBst, idesc, 1);
                         mma_commit(&ctl.acc_full[g][buf]);  // this group's accumulator is ready
                     }
@@ -299,21 +311,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             }
                         }
                     } else {
-                        // packed keys: the positive score with its low 6 bits replaced by the column
-                        // within the slice; a float minimum gives value and column together (four
-                        // independent chains, merged at the end)
+                        // keys: accumulator bits x 64 + (0x48000000 + column) wraps to
+                        // 0x08000000 + 64 m + column, a positive normal float, so a float minimum
+                        // gives the (score, column) minimum (four independent chains, merged at
+                        // the end).  An accumulator outside [128, 256) (a non-finite row) gives
+                        // a meaningless key; the label stays in range below.
+                        const uint32_t mul = a.key_mul;
+#define RAFTGP_KEY(j) __uint_as_float(r[0][j] * mul + (0x48000000u + (uint32_t)(j)))
                         float m0 = INFINITY, m1 = INFINITY, m2 = INFINITY, m3 = INFINITY;
 #pragma unroll
                         for (int k = 0; k < 64; k += 8) {
-                            m0 = min3f(m0, __uint_as_float((r[0][k] & 0xFFFFFFC0u) | (uint32_t)k),
-                                       __uint_as_float((r[0][k + 1] & 0xFFFFFFC0u) | (uint32_t)(k + 1)));
-                            m1 = min3f(m1, __uint_as_float((r[0][k + 2] & 0xFFFFFFC0u) | (uint32_t)(k + 2)),
-                                       __uint_as_float((r[0][k + 3] & 0xFFFFFFC0u) | (uint32_t)(k + 3)));
-                            m2 = min3f(m2, __uint_as_float((r[0][k + 4] & 0xFFFFFFC0u) | (uint32_t)(k + 4)),
-                                       __uint_as_float((r[0][k + 5] & 0xFFFFFFC0u) | (uint32_t)(k + 5)));
-                            m3 = min3f(m3, __uint_as_float((r[0][k + 6] & 0xFFFFFFC0u) | (uint32_t)(k + 6)),
-                                       __uint_as_float((r[0][k + 7] & 0xFFFFFFC0u) | (uint32_t)(k + 7)));
+                            m0 = min3f(m0, RAFTGP_KEY(k), RAFTGP_KEY(k + 1));
+                            m1 = min3f(m1, RAFTGP_KEY(k + 2), RAFTGP_KEY(k + 3));
+                            m2 = min3f(m2, RAFTGP_KEY(k + 4), RAFTGP_KEY(k + 5));
+                            m3 = min3f(m3, RAFTGP_KEY(k + 6), RAFTGP_KEY(k + 7));
                         }
+#undef RAFTGP_KEY
                         const float kmin = fminf(min3f(m0, m1, m2), m3);
                         const uint32_t kb = __float_as_uint(kmin);
                         const float v = __uint_as_float(kb & 0xFFFFFFC0u);
@@ -428,10 +441,11 @@ static cudaError_t make_map(CUtensorMap* m, const void* base, int64_t rows, int 
                       C::ATOM_BYTES == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B);
 }
 
-template <int D>
+template <int D, bool LO>
 static cudaError_t launch_tc_t(const CandBatch& b, const __nv_bfloat16* Z, int64_t n, KmState st, int pass,
                                int final_mode, int2* recheck, int* recheck_count, uint32_t* err, cudaStream_t s) {
-    using C = TcCfg<D>;
+    using C = TcCfg<D, LO>;
+    static_assert(C::SMEM + sizeof(TcCtl) <= 227 * 1024, "dynamic + static shared memory budget");
     cudaError_t e = get_encoder();
     if (e != cudaSuccess) return e;
     CUtensorMap ta, th, tl, tg;
@@ -446,12 +460,13 @@ static cudaError_t launch_tc_t(const CandBatch& b, const __nv_bfloat16* Z, int64
     a.st = st;
     a.pass = pass;
     a.final_mode = final_mode;
+    a.key_mul = 64u;
     a.tie_band = 1.5e-4f * (float)D / 64.0f + 2.0e-5f;
     a.recheck = recheck;
     a.recheck_count = recheck_count;
     a.err = err;
     const int smem = C::SMEM;
-    auto kern = k_assign_tc<D>;
+    auto kern = k_assign_tc<D, LO>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
     const int64_t nsteps = (n + 128 * C::GROUPS - 1) / (128 * C::GROUPS);
     const int grid = (int)(nsteps < num_sms() ? nsteps : num_sms());
@@ -463,15 +478,21 @@ static cudaError_t launch_tc_t(const CandBatch& b, const __nv_bfloat16* Z, int64
 }
 
 cudaError_t launch_assign_tc(const CandBatch& b, const void* Z, int64_t n, int d, KmState st, int pass, int final_mode,
-                             int2* recheck, int* recheck_count, uint32_t* err, cudaStream_t s) {
+                             int fast_lo, int2* recheck, int* recheck_count, uint32_t* err, cudaStream_t s) {
     // the chunk table holds every 128-column chunk of the batch
     if (b.total_k > TC_MAX_CHUNKS * 128) return cudaErrorInvalidValue;
     const __nv_bfloat16* z = (const __nv_bfloat16*)Z;
+    const bool lo = final_mode || fast_lo;     // FINAL always multiplies both halves
+#define RAFTGP_TC_CASE(DD)                                                                         \
+    case DD:                                                                                     \
+        return lo ? launch_tc_t<DD, true>(b, z, n, st, pass, final_mode, recheck, recheck_count, err, s) \
+                  : launch_tc_t<DD, false>(b, z, n, st, pass, final_mode, recheck, recheck_count, err, s);
     switch (d) {
-        case 32: return launch_tc_t<32>(b, z, n, st, pass, final_mode, recheck, recheck_count, err, s);
-        case 64: return launch_tc_t<64>(b, z, n, st, pass, final_mode, recheck, recheck_count, err, s);
-        case 128: return launch_tc_t<128>(b, z, n, st, pass, final_mode, recheck, recheck_count, err, s);
+        RAFTGP_TC_CASE(32)
+        RAFTGP_TC_CASE(64)
+        RAFTGP_TC_CASE(128)
     }
+#undef RAFTGP_TC_CASE
     return cudaErrorInvalidValue;
 }
 

@@ -104,7 +104,7 @@ void launch_lloyd_update(const CandBatch& b, int d, KmState st, int pass, int la
 void launch_apply_changes(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, KmState st, int pass,
                           cudaStream_t s);
 cudaError_t launch_assign_tc(const CandBatch& b, const void* Z, int64_t n, int d, KmState st, int pass, int final_mode,
-                             int2* recheck, int* recheck_count, uint32_t* err, cudaStream_t s);
+                             int fast_lo, int2* recheck, int* recheck_count, uint32_t* err, cudaStream_t s);
 void launch_recheck(const CandBatch& b, const void* Z, int d, KmState st, const int2* list, const int* count,
                     cudaStream_t s);
 

@@ -314,8 +314,10 @@ __host__ __device__ __forceinline__ int pad64(int k) { return (k + 63) / 64 * 64
 
 // Everything derived from one FP32 centroid row: ||mu||^2 (ascending coordinates), the
 // +4-shifted copy, the tensor-core operands -mu = hi + lo, and the norm slice
-// [(||mu||^2 + 4)/2 as hi, lo, then zeros].  A padding row (no centroid) gets an infinite
-// norm and a huge norm slice so it never wins an argmin.
+// [(||mu||^2 + 4)/2 as hi, lo, then 128, then zeros] (the 128 puts every score of the
+// tensor-core Lloyd pass in [128, 256)).  A padding row (no centroid) gets an infinite norm
+// and the norm slice [127, 0, 128]: its score is 255, above every real one (below 132), so
+// it never wins an argmin.
 __device__ void write_row_operands(KmState st, int64_t row, int d, bool padding) {
     float* mu = st.mu + row * d;
     __nv_bfloat16* aug = st.baug + row * 16;
@@ -327,8 +329,10 @@ __device__ void write_row_operands(KmState st, int64_t row, int d, bool padding)
         }
         st.norm2[row] = INFINITY;
         st.norm2p[row] = INFINITY;
-        aug[0] = __float2bfloat16_rn(1.0e30f);
-        for (int k = 1; k < 16; ++k) aug[k] = __float2bfloat16_rn(0.f);
+        aug[0] = __float2bfloat16_rn(127.0f);
+        aug[1] = __float2bfloat16_rn(0.f);
+        aug[2] = __float2bfloat16_rn(128.0f);
+        for (int k = 3; k < 16; ++k) aug[k] = __float2bfloat16_rn(0.f);
         return;
     }
     float s = 0.f;
@@ -340,7 +344,8 @@ __device__ void write_row_operands(KmState st, int64_t row, int d, bool padding)
     st.norm2[row] = s;
     st.norm2p[row] = s + 4.0f;
     split_bf16(0.5f * (s + 4.0f), aug, aug + 1);
-    for (int k = 2; k < 16; ++k) aug[k] = __float2bfloat16_rn(0.f);
+    aug[2] = __float2bfloat16_rn(128.0f);
+    for (int k = 3; k < 16; ++k) aug[k] = __float2bfloat16_rn(0.f);
 }
 
 // The same for one real centroid row by a whole warp (lanes over coordinates; the norm is a
@@ -363,6 +368,7 @@ __device__ void warp_row_operands(KmState st, int64_t row, int d) {
         const __nv_bfloat16 h = __float2bfloat16_rn(0.5f * (s + 4.0f));
         aug[lane] = lane == 0 ? h
                   : lane == 1 ? __float2bfloat16_rn(0.5f * (s + 4.0f) - __bfloat162float(h))
+                  : lane == 2 ? __float2bfloat16_rn(128.0f)
                               : __float2bfloat16_rn(0.f);
     }
 }
