@@ -149,7 +149,10 @@ raftgp_status raftgp_score(const raftgp_csr* g, const int32_t* labels, int32_t K
  * direct-form squared distance summed over ascending coordinates, quantised to
  * floor(D^2 * 2^40) (uint64); draw t: r = Philox(seed; t, 0, 0, "Kmpp") words 0-1,
  * threshold floor(r * sum_q / 2^64), first index whose inclusive prefix exceeds it; if every
- * q is 0 the lowest-index unchosen point.  Asynchronous. */
+ * q is 0 the lowest-index unchosen point.  ws: at least 7 N + 8 max(ceil(N / 1024), 2048)
+ * + 4 K + 2048 bytes.  All rounds usually run in one cooperative launch whose blocks meet at
+ * bounded grid barriers; if a barrier gives up (2 s) the seeds not yet drawn are written as
+ * -1.  Asynchronous. */
 raftgp_status raftgp_kmeanspp(const void* Z, int64_t n, int32_t d, int32_t z_dtype, int32_t K, uint64_t seed,
                               int32_t* seeds, void* ws, size_t ws_bytes, raftgp_stream_t stream);
 
@@ -167,8 +170,8 @@ raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype,
  * memory that program's own allocator owns and budgets, or a process that reserves all the
  * device memory it may use before it starts partitioning.  The paper has no counterpart;
  * this is a deployment variant of the seeding step.
- * Its scratch (the D^2 array, nearest-seed indices, chosen-point flags and block sums, about
- * 7 bytes per point) is a file-scope device array of RAFTGP_NOALLOC_SCRATCH_BYTES that every GPU which
+ * Its scratch (the D^2 array, nearest-seed indices, chosen-point flags, block sums and grid
+ * barrier words, about 7 bytes per point) is a file-scope device array of RAFTGP_NOALLOC_SCRATCH_BYTES that every GPU which
  * loads this library holds until the process exits.  n above RAFTGP_NOALLOC_MAX_N (or K above
  * 32767) is rejected with RAFTGP_EUNSUPPORTED before any work is queued.  The call allocates nothing:
  * no cudaMalloc, cudaFree or allocating library routine.  The first call on a device looks up

@@ -195,7 +195,7 @@ def kmeanspp(Z: torch.Tensor, K: int, seed: int, stream=None):
     n, d = Z.shape
     code = 1 if Z.dtype == torch.bfloat16 else 0
     seeds = torch.empty(K, dtype=torch.int32, device=Z.device)
-    ws = _workspace(8 * n + 16 * n + 8 * (n // 256 + 2) + 4096, Z.device)
+    ws = _workspace(7 * n + 8 * max(n // 1024 + 1, 2048) + 4 * K + 4096, Z.device)
     Zc = Z.contiguous()
     check(lib().raftgp_kmeanspp(C.c_void_p(Zc.data_ptr()), n, d, code, int(K), int(seed),
                                 C.c_void_p(seeds.data_ptr()), C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))

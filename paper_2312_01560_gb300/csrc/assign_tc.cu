@@ -14,11 +14,14 @@
 // integer multiply-add turns it into the key 64 m + column, whose minimum gives score and
 // column at once.
 //
-// Warp roles in a persistent CTA (one per SM): warp 0 issues TMA loads (the point tile once
-// per tile, centroid chunks through a STAGES-deep ring), warp 1 allocates tensor memory and
-// issues the MMAs into two accumulator buffers, warps 2-5 are the epilogue.  Every mbarrier
-// wait is bounded: on timeout the CTA raises an abort flag, records DERR_TIMEOUT, drains its
-// in-flight copies and MMAs (again bounded), frees its tensor memory and returns.
+// Warp roles in a persistent CTA (one per SM): warp 0 issues TMA loads (four point tiles per
+// step, centroid chunks of NCH = 128 columns through a ring of up to 8 stages), warp 1
+// allocates tensor memory and issues the MMAs, warps 2-17 are four epilogue groups of 4
+// warps, each owning one point tile of the step and one 128-column accumulator (4 x 128
+// columns fill tensor memory; 64-column chunks with two buffers per group measured slower).
+// Every mbarrier wait is bounded: on timeout the CTA raises an abort flag, records
+// DERR_TIMEOUT, drains its in-flight copies and MMAs (again bounded), frees its tensor memory
+// and returns.
 //
 // Modes: FAST (Lloyd passes; the lo half is optional there) writes the new labels (k_apply_changes then counts the changes
 // and applies them to the 2^-40 fixed-point centroid sums); FINAL (the assignment whose labels
@@ -42,10 +45,10 @@ struct TcCfg {
     static constexpr int ATOM_BYTES = ATOM * 2;           // 64 or 128
     static constexpr int NATOM = D / ATOM;
     static constexpr int NCH = 128;                       // centroids per chunk = MMA N = two slices
+    static constexpr int SLICES = NCH / 64;               // 64-column slices per chunk
     static constexpr int GROUPS = 4;                      // point tiles per CTA step, one per epilogue group
-    static constexpr int ACC_BUFS = 1;                    // accumulator buffers per group
+    static constexpr int ACC_BUFS = 512 / (GROUPS * NCH); // accumulator buffers per group
     static constexpr int A_BUFS = D == 128 ? 1 : 2;       // point-tile groups in flight
-    static constexpr int STAGES = LO ? (D == 128 ? 1 : (D == 64 ? 2 : 4)) : (D == 128 ? 2 : (D == 64 ? 4 : 8));
     static constexpr int A_ATOM_BYTES = 128 * ATOM_BYTES;
     static constexpr int A_TILE_BYTES = NATOM * A_ATOM_BYTES;     // one 128-point tile
     static constexpr int A_BYTES = GROUPS * A_TILE_BYTES;         // one group of tiles
@@ -57,7 +60,12 @@ struct TcCfg {
     static constexpr int STAGE_BYTES = NHALF * B_BYTES + AUG_B_BYTES;
     static constexpr int LAYOUT = ATOM_BYTES == 128 ? 2 : 4;  // descriptor swizzle: 128B or 64B
     static constexpr int SBO = 8 * ATOM_BYTES;                 // stride between 8-row groups
-    static constexpr int SMEM = 1024 + A_BUFS * A_BYTES + AUG_A_BYTES + STAGES * STAGE_BYTES;
+    static constexpr int FIXED = 1024 + A_BUFS * A_BYTES + AUG_A_BYTES;
+    // ring depth: what the budget (227 KB less the static control block) leaves, at most 8
+    static constexpr int STAGES_FIT = (218 * 1024 - FIXED) / STAGE_BYTES;
+    static constexpr int STAGES = STAGES_FIT < 8 ? STAGES_FIT : 8;
+    static_assert(STAGES >= 1, "the centroid ring needs a stage");
+    static constexpr int SMEM = FIXED + STAGES * STAGE_BYTES;
     static_assert(SMEM <= 227 * 1024, "shared memory budget");
     static_assert(GROUPS * ACC_BUFS * NCH <= 512, "the accumulator buffers must fit tensor memory");
 };
@@ -77,7 +85,7 @@ struct TcCtl {
     int chunk_col[TC_MAX_CHUNKS];
     // per 64-column slice (two per chunk): candidate + 128 if the candidate's padded range ends
     // with the slice, or -1 (inactive candidate / beyond the batch)
-    int16_t slice_info[2 * TC_MAX_CHUNKS];
+    int16_t slice_info[2 * TC_MAX_CHUNKS];   // SLICES per chunk (at most 2)
 };
 
 // ---------------------------------------------------------------------------------------
@@ -130,15 +138,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
         mbar_init(&ctl.drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        // 128-column chunks holding columns of an active candidate (FINAL: every candidate), with
-        // the candidate of each 64-column half; candidates are padded to whole slices
+        // NCH-column chunks holding columns of an active candidate (FINAL: every candidate), with
+        // the candidate of each 64-column slice; candidates are padded to whole slices
         int nch = 0, c = 0;
         const int total_chunks = (b.total_k + C::NCH - 1) / C::NCH;
         for (int q = 0; q < total_chunks && nch < TC_MAX_CHUNKS; ++q) {
             const int lo = q * C::NCH;
             int info[2] = {-1, -1};
             bool need = false;
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < C::SLICES; ++h) {
                 const int col0 = lo + 64 * h;
                 if (col0 >= b.total_k) break;
                 while (c + 1 < b.n && b.off[c + 1] <= col0) ++c;
@@ -150,8 +158,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             if (need) {
                 ctl.chunk_col[nch] = lo;
-                ctl.slice_info[2 * nch] = (int16_t)info[0];
-                ctl.slice_info[2 * nch + 1] = (int16_t)info[1];
+                for (int h = 0; h < C::SLICES; ++h) ctl.slice_info[C::SLICES * nch + h] = (int16_t)info[h];
                 ++nch;
             }
         }
@@ -282,13 +289,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (!(ok = mbar_wait(&ctl.acc_full[wg][buf], (it / C::ACC_BUFS) & 1, &ctl, a.err))) break;
                 tc_fence_after();
 #pragma unroll 1
-                for (int h = 0; h < 2; ++h) {
-                    const int info = ctl.slice_info[2 * q + h];
+                for (int h = 0; h < C::SLICES; ++h) {
+                    const int info = ctl.slice_info[C::SLICES * q + h];
                     uint32_t r[1][64];
                     if (info >= 0) tmem_ld64(lane_base + (uint32_t)(buf * C::NCH + 64 * h), r[0]);
-                    if (h == 1) {
+                    if (h == C::SLICES - 1) {
                         tc_fence_before();
-                        mbar_arrive(&ctl.acc_empty[wg][buf]);   // both halves read: the buffer is free
+                        mbar_arrive(&ctl.acc_empty[wg][buf]);   // every slice read: the buffer is free
                     }
                     if (info < 0) continue;
                     const int cand = info & 127;
@@ -479,8 +486,8 @@ static cudaError_t launch_tc_t(const CandBatch& b, const __nv_bfloat16* Z, int64
 
 cudaError_t launch_assign_tc(const CandBatch& b, const void* Z, int64_t n, int d, KmState st, int pass, int final_mode,
                              int fast_lo, int2* recheck, int* recheck_count, uint32_t* err, cudaStream_t s) {
-    // the chunk table holds every 128-column chunk of the batch
-    if (b.total_k > TC_MAX_CHUNKS * 128) return cudaErrorInvalidValue;
+    // the chunk table holds every chunk of the batch
+    if (b.total_k > TC_MAX_CHUNKS * TcCfg<64>::NCH) return cudaErrorInvalidValue;
     const __nv_bfloat16* z = (const __nv_bfloat16*)Z;
     const bool lo = final_mode || fast_lo;     // FINAL always multiplies both halves
 #define RAFTGP_TC_CASE(DD)                                                                         \

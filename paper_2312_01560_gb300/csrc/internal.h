@@ -88,6 +88,8 @@ struct SeedState {
     uint8_t* chosen;               // n: already a seed
     unsigned long long* blocksum;  // seed_nblocks(n): block sums of the quantised D^2
     float* cc2;                    // K: squared distance from each seed to the newest one
+    unsigned* bar;                 // 4 words: grid barrier count, generation, abort; spare error word
+    uint32_t* err;                 // device error word (DERR_TIMEOUT); bar + 3 unless the caller has one
     int32_t* seeds;                // K (caller's output)
 };
 int seed_nblocks(int64_t n);

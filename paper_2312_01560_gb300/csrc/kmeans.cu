@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tc_util.cuh"
 
 namespace raftgp {
 
@@ -238,9 +239,345 @@ __global__ void __launch_bounds__(1024) k_seed_pick(const T* __restrict__ Z, int
 
 int seed_nblocks(int64_t n) { return (int)((n + SEED_PPB - 1) / SEED_PPB); }
 
+// ------------------------------------------------------------------------------------
+// Persistent seeding: every round in one cooperative launch (all blocks resident), one block
+// per SM.  A block owns a contiguous range of points whose D^2 and nearest seed stay in
+// shared memory for all K rounds, together with a copy of every seed row (for the skip
+// bound).  Per round:
+//   1. each block loads the newest seed, computes its squared distance to every earlier
+//      seed, and updates its points.  A row is read one 32-byte sector at a time in ascending
+//      coordinates; the FP32 partial sums never decrease (every term is >= 0 and rounding is
+//      monotone), so once a partial sum reaches the current D^2 the row cannot lower it and
+//      the rest of the row is not read.  The rows that do lower D^2 are summed in full, so
+//      every D^2 is the same as the plain evaluation.  Thread j walks rows j, j + 1024, ...;
+//      a thread that finishes a row starts its next one at once.
+//   2. block partial sums of the quantised D^2 are published; grid barrier.
+//   3. every block finds the owner of the threshold from the partial sums (the same integer
+//      arithmetic in every block); the owner scans its points in index order, writes the
+//      seed; grid barrier.
+// The barriers spin with a 2 s limit; on a timeout the kernel records DERR_TIMEOUT, raises
+// an abort word that releases the other blocks, marks the unfinished seeds -1 and returns.
+// ------------------------------------------------------------------------------------
+constexpr int SP_THREADS = 1024;
+constexpr int SP_MAX_SMEM = 200 * 1024;
+
+__device__ __forceinline__ unsigned ld_volatile(const unsigned* p) { return *(volatile const unsigned*)p; }
+
+// bar[0] arrivals, bar[1] generation, bar[2] abort.  Returns false in every thread of the
+// block if the wait gave up or another block aborted.
+__device__ bool grid_barrier(unsigned* bar, uint32_t* err, int* s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned gen = ld_volatile(bar + 1);
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const uint64_t t0 = global_ns();
+            unsigned it = 0;
+            while (ld_volatile(bar + 1) == gen) {
+                if (ld_volatile(bar + 2)) { ok = 0; break; }
+                if ((++it & 63) == 0 && global_ns() - t0 > TC_WAIT_NS) {
+                    atomicOr(err, (uint32_t)DERR_TIMEOUT);
+                    atomicExch(bar + 2, 1u);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// 16-byte row loads that ask L2 to keep the lines (evict_last): the rows are read again
+// every round, and Z is about the size of L2.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint4 ld_keep16(const void* p, uint64_t pol) {
+    uint4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void load_keep(const float* p, float* out, uint64_t pol) {
+    const uint4 v = ld_keep16(p, pol);
+    out[0] = __uint_as_float(v.x); out[1] = __uint_as_float(v.y);
+    out[2] = __uint_as_float(v.z); out[3] = __uint_as_float(v.w);
+}
+__device__ __forceinline__ void load_keep(const __nv_bfloat16* p, float* out, uint64_t pol) {
+    const uint4 v = ld_keep16(p, pol);
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        out[2 * i] = __uint_as_float(w[i] << 16);
+        out[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+    }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(SP_THREADS, 1)
+    k_seed_persistent(const T* __restrict__ Z, int64_t n, int K, uint64_t seed, SeedState ss, int per_block,
+                      int off_near, int off_rows, int off_cc2) {
+    extern __shared__ __align__(16) uint8_t sp_smem[];
+    float* sD2 = reinterpret_cast<float*>(sp_smem);
+    int16_t* sNear = reinterpret_cast<int16_t*>(sp_smem + off_near);
+    T* srow = reinterpret_cast<T*>(sp_smem + off_rows);
+    float* scc2 = reinterpret_cast<float*>(sp_smem + off_cc2);
+    __shared__ float c[D];
+    __shared__ unsigned long long wsum[SP_THREADS / 32];
+    __shared__ unsigned long long s_thr, s_base;
+    __shared__ long long s_pick;
+    __shared__ int s_owner, s_ok;
+    __shared__ unsigned long long s_part[1024];
+    constexpr int E = Vec<T>::E;                    // elements per 16-byte load
+    constexpr int SEC = 32 / (int)sizeof(T);        // elements per 32-byte sector
+    constexpr int NSEC = D / SEC;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t lo = (int64_t)blockIdx.x * per_block;
+    const int cnt = (int)(n - lo < per_block ? (n - lo > 0 ? n - lo : 0) : per_block);
+    const int G = gridDim.x;
+    const uint64_t pol = l2_keep_policy();
+
+    long long p = (long long)mulhi64(kmpp_draw(seed, 0), (uint64_t)n);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ss.seeds[0] = (int32_t)p;
+        ss.chosen[p] = 1;
+    }
+    int t = 1;
+    for (; t < K; ++t) {
+        // ---- 1. the newest seed, its distance to the earlier ones, the update ----
+        for (int k = threadIdx.x; k < D; k += SP_THREADS) {
+            const T v = Z[p * D + k];
+            c[k] = Vec<T>::to_float(v);
+            srow[(int64_t)(t - 1) * D + k] = v;
+        }
+        __syncthreads();
+        for (int j = warp; j < t - 1; j += SP_THREADS / 32) {
+            float acc = 0.f;
+            for (int k = lane; k < D; k += 32) {
+                const float dl = Vec<T>::to_float(srow[(int64_t)j * D + k]) - c[k];
+                acc = fmaf(dl, dl, acc);
+            }
+            acc = warp_sum(acc);
+            if (lane == 0) scc2[j] = acc;
+        }
+        __syncthreads();
+        unsigned long long q = 0;
+        int r = threadIdx.x;
+        float cur = 0.f, acc = 0.f;
+        int sec = 0;
+        // next row that needs its distance (rows passing the skip test only add their q)
+        auto next_row = [&]() -> bool {
+            for (; r < cnt; r += SP_THREADS) {
+                if (t == 1) {
+                    cur = INFINITY;
+                    break;
+                }
+                cur = sD2[r];
+                if (!(scc2[sNear[r]] >= 4.0f * cur * 1.0001f)) break;
+                q += quantise(cur);
+            }
+            acc = 0.f;
+            sec = 0;
+            return r < cnt;
+        };
+        bool active = next_row();
+        while (active) {
+            const T* zs = Z + (lo + r) * D + sec * SEC;
+#pragma unroll
+            for (int v = 0; v < SEC / E; ++v) {
+                float x[E];
+                load_keep(zs + v * E, x, pol);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const float dl = __fsub_rn(x[e], c[sec * SEC + v * E + e]);
+                    acc = __fadd_rn(acc, __fmul_rn(dl, dl));
+                }
+            }
+            ++sec;
+            const bool full = sec == NSEC;
+            // round 1 reads every row in full and always stores it, so the shared state is
+            // initialised whatever the data (a non-finite sum included)
+            if (full || (t > 1 && acc >= cur)) {
+                if (full && (t == 1 || acc < cur)) {
+                    cur = acc;
+                    sD2[r] = acc;
+                    sNear[r] = (int16_t)(t - 1);
+                }
+                q += quantise(cur);
+                r += SP_THREADS;
+                active = next_row();
+            }
+        }
+        // ---- 2. block partial sum; barrier ----
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+        if (lane == 0) wsum[warp] = q;
+        __syncthreads();
+        unsigned long long* part = ss.blocksum + (size_t)(t & 1) * G;
+        if (threadIdx.x == 0) {
+            unsigned long long sum = 0;
+            for (int w = 0; w < SP_THREADS / 32; ++w) sum += wsum[w];
+            part[blockIdx.x] = sum;
+        }
+        if (!grid_barrier(ss.bar, ss.err, &s_ok)) break;
+        // ---- 3. the owner of the threshold picks the seed; barrier ----
+        for (int b = threadIdx.x; b < G; b += SP_THREADS) s_part[b] = __ldcg(part + b);
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long tot = 0;
+            for (int b = lane; b < G; b += 32) tot += s_part[b];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+            const unsigned long long thr = tot > 0 ? mulhi64(kmpp_draw(seed, t), tot) : 0ull;
+            int owner = -1;
+            unsigned long long run = 0, base = 0;
+            for (int b0 = 0; b0 < G && owner < 0 && tot > 0; b0 += 32) {
+                const unsigned long long v = b0 + lane < G ? s_part[b0 + lane] : 0ull;
+                unsigned long long x = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += y;
+                }
+                const unsigned hit = __ballot_sync(0xffffffffu, b0 + lane < G && run + x > thr && run + x - v <= thr);
+                if (hit) {
+                    const int l = __ffs(hit) - 1;
+                    owner = b0 + l;
+                    base = run + __shfl_sync(0xffffffffu, x - v, l);
+                }
+                run += __shfl_sync(0xffffffffu, x, 31);
+            }
+            if (lane == 0) {
+                s_owner = tot > 0 ? owner : -2;
+                s_thr = thr;
+                s_base = base;
+                s_pick = -1;
+            }
+        }
+        __syncthreads();
+        if (s_owner == -2 && blockIdx.x == 0) {
+            // every remaining point coincides with a seed: the lowest-index unchosen point
+            for (int64_t b0 = 0; b0 < n; b0 += SP_THREADS) {
+                const int64_t i = b0 + threadIdx.x;
+                const bool cand = i < n && !__ldcg(ss.chosen + i);
+                const unsigned m = __ballot_sync(0xffffffffu, cand);
+                if (lane == 0) wsum[warp] = m ? (unsigned long long)(b0 + warp * 32 + __ffs(m) - 1) : ~0ull;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    for (int w = 0; w < SP_THREADS / 32; ++w)
+                        if (wsum[w] != ~0ull) { s_pick = (long long)wsum[w]; break; }
+                }
+                __syncthreads();
+                if (s_pick >= 0) break;
+            }
+        } else if (s_owner == (int)blockIdx.x) {
+            // contiguous segments in index order, one per thread
+            const unsigned long long thr = s_thr - s_base;
+            const int L = (cnt + SP_THREADS - 1) / SP_THREADS;
+            const int r0 = threadIdx.x * L;
+            const int r1 = r0 + L < cnt ? r0 + L : cnt;
+            unsigned long long v = 0;
+            for (int rr = r0; rr < r1; ++rr) v += quantise(sD2[rr]);
+            unsigned long long ct;
+            const unsigned long long ex = block_scan_1024(v, &ct);
+            if (r0 < r1 && ex + v > thr && ex <= thr) {
+                unsigned long long run = ex;
+                for (int rr = r0; rr < r1; ++rr) {
+                    run += quantise(sD2[rr]);
+                    if (run > thr) {
+                        s_pick = lo + rr;
+                        break;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if ((s_owner == -2 && blockIdx.x == 0) || s_owner == (int)blockIdx.x) {
+            if (threadIdx.x == 0) {
+                const long long pk = s_pick < 0 ? 0 : s_pick;   // unreachable fallback keeps indices in range
+                ss.seeds[t] = (int32_t)pk;
+                ss.chosen[pk] = 1;
+            }
+        }
+        if (!grid_barrier(ss.bar, ss.err, &s_ok)) break;
+        p = (long long)__ldcg(ss.seeds + t);
+    }
+    if (t < K && threadIdx.x == 0) {
+        for (int j = t; j < K; ++j) ss.seeds[j] = -1;   // aborted: the unfinished seeds are invalid
+    }
+}
+
+// Shared-memory layout of the persistent kernel; false if it does not fit.
+template <typename T, int D>
+static bool persistent_layout(int per_block, int K, int* off_near, int* off_rows, int* off_cc2, int* bytes) {
+    auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    const size_t near = a16((size_t)per_block * 4);
+    const size_t rows = near + a16((size_t)per_block * 2);
+    const size_t cc2 = rows + a16((size_t)K * D * sizeof(T));
+    const size_t total = cc2 + a16((size_t)K * 4);
+    if (total > (size_t)SP_MAX_SMEM) return false;
+    *off_near = (int)near;
+    *off_rows = (int)rows;
+    *off_cc2 = (int)cc2;
+    *bytes = (int)total;
+    return true;
+}
+
+// Launches the persistent kernel; returns false (nothing launched) if the state does not fit
+// shared memory or the device cannot hold one resident block per SM.
+template <typename T, int D>
+static bool seed_persistent_t(const T* Z, int64_t n, int K, uint64_t seed, SeedState ss, cudaStream_t s) {
+    int G = num_sms();
+    if (G > 1024) G = 1024;
+    if ((int64_t)G > n) G = (int)n;
+    const int per_block = (int)((n + G - 1) / G);
+    int off_near, off_rows, off_cc2, bytes;
+    if (!persistent_layout<T, D>(per_block, K, &off_near, &off_rows, &off_cc2, &bytes)) return false;
+    auto kern = k_seed_persistent<T, D>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SP_THREADS, bytes) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaMemsetAsync(ss.chosen, 0, (size_t)n, s);
+    cudaMemsetAsync(ss.bar, 0, 3 * sizeof(unsigned), s);
+    void* args[] = {(void*)&Z, (void*)&n, (void*)&K, (void*)&seed, (void*)&ss, (void*)&per_block,
+                    (void*)&off_near, (void*)&off_rows, (void*)&off_cc2};
+    ProfScope ps(s, PF_SEED_UPDATE, 1);
+    if (cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(SP_THREADS), args, (size_t)bytes, s) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+
+// the partial sums hold seed_nblocks(n) entries for the per-round kernels, or two rounds of
+// one per SM for the persistent kernel (at most 2 x 1024 blocks)
+static size_t seed_partials(int64_t n) {
+    const size_t nb = (size_t)seed_nblocks(n);
+    return nb > 2048 ? nb : 2048;
+}
+
 size_t seed_scratch_bytes(int64_t n, int K) {
     auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
-    return a((size_t)n * 4) + a((size_t)n * 2) + a((size_t)n) + a((size_t)seed_nblocks(n) * 8) + a((size_t)K * 4);
+    return a((size_t)n * 4) + a((size_t)n * 2) + a((size_t)n) + a(seed_partials(n) * 8) + a((size_t)K * 4) + a(16);
 }
 
 SeedState carve_seed(void* base, int64_t n, int K, int32_t* seeds) {
@@ -254,14 +591,19 @@ SeedState carve_seed(void* base, int64_t n, int K, int32_t* seeds) {
     ss.chosen = (uint8_t*)p;
     p += a((size_t)n);
     ss.blocksum = (unsigned long long*)p;
-    p += a((size_t)seed_nblocks(n) * 8);
+    p += a(seed_partials(n) * 8);
     ss.cc2 = (float*)p;
+    p += a((size_t)K * 4);
+    ss.bar = (unsigned*)p;
+    ss.err = ss.bar + 3;
     ss.seeds = seeds;
     return ss;
 }
 
 template <typename T, int D>
 static void seed_run_t(const T* Z, int64_t n, int K, uint64_t seed, SeedState ss, cudaStream_t s) {
+    if (seed_persistent_t<T, D>(Z, n, K, seed, ss, s)) return;
+    // one launch per round for the update and one for the pick
     const int nb = seed_nblocks(n);
     cudaMemsetAsync(ss.chosen, 0, (size_t)n, s);
     {

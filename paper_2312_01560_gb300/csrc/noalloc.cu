@@ -19,8 +19,9 @@ namespace raftgp {
 static __device__ __align__(256) unsigned char g_noalloc_scratch[RAFTGP_NOALLOC_SCRATCH_BYTES];
 
 // Layout inside the scratch: the seeding state of carve_seed (D^2 floats, nearest-seed int16,
-// chosen flags, block sums, seed-to-seed distances), about 7 bytes per point plus 4 per seed.
-static_assert((size_t)RAFTGP_NOALLOC_MAX_N * 7 + (RAFTGP_NOALLOC_MAX_N / 2048 + 1) * 8 + 32767 * 4 + 5 * 256 <=
+// chosen flags, block sums, seed-to-seed distances, grid barrier words), about 7 bytes per
+// point plus 4 per seed.
+static_assert((size_t)RAFTGP_NOALLOC_MAX_N * 7 + (RAFTGP_NOALLOC_MAX_N / 1024 + 2048) * 8 + 32767 * 4 + 6 * 256 <=
                   (size_t)RAFTGP_NOALLOC_SCRATCH_BYTES,
               "static scratch too small for RAFTGP_NOALLOC_MAX_N");
 

@@ -41,6 +41,33 @@ def test_kmeanspp_bit_exact_bf16_and_widths(cuda, d):
     assert np.array_equal(seeds, ref)
 
 
+def _clustered_rows(rng, n, d, k, spread):
+    centres = _unit_rows(rng, k, d)
+    z = centres[rng.integers(0, k, n)] + spread * rng.normal(size=(n, d)) / np.sqrt(d)
+    return z / np.linalg.norm(z, axis=1, keepdims=True)
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float32])
+def test_kmeanspp_bit_exact_many_blocks(cuda, dtype):
+    # clustered rows, so the skip bound and the partial-row cut both fire; the point count
+    # spreads ragged ranges over every SM's block
+    rng = np.random.default_rng(11)
+    Z = torch.tensor(_clustered_rows(rng, 150_001, 64, 300, 0.6), dtype=dtype, device=cuda)
+    seeds = api.kmeanspp(Z, 200, seed=5).cpu().numpy()
+    ref = oracle.kmeanspp(Z.float().cpu().numpy().astype(np.float64), 200, 5, fp32_decision=True)
+    assert np.array_equal(seeds, ref)
+
+
+def test_kmeanspp_bit_exact_per_round_kernels(cuda):
+    # 450 seed rows of 128 FP32 coordinates do not fit the persistent kernel's shared memory,
+    # so the seeding runs as one update and one pick launch per round
+    rng = np.random.default_rng(12)
+    Z = torch.tensor(_clustered_rows(rng, 4000, 128, 50, 0.5), dtype=torch.float32, device=cuda)
+    seeds = api.kmeanspp(Z, 450, seed=2).cpu().numpy()
+    ref = oracle.kmeanspp(Z.cpu().numpy().astype(np.float64), 450, 2, fp32_decision=True)
+    assert np.array_equal(seeds, ref)
+
+
 def test_kmeanspp_duplicates(cuda):
     Z = torch.zeros((50, 32), device=cuda)
     Z[:, 0] = 1.0
