@@ -200,6 +200,10 @@ typedef struct {
 } raftgp_prof_entry;
 
 raftgp_status raftgp_profile_enable(int32_t on);
+/* As raftgp_profile_enable(1), but only the named family (a name raftgp_profile_read reports,
+ * e.g. "assign_tc") records events; the other families' launches are not counted.  NULL: every
+ * family.  RAFTGP_EINVAL for an unknown name (profiling state unchanged). */
+raftgp_status raftgp_profile_enable_family(const char* family);
 int32_t raftgp_profile_read(raftgp_prof_entry* out, int32_t cap);
 
 /* Message for the last non-OK status returned on the calling thread. */

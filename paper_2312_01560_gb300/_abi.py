@@ -22,7 +22,7 @@ MAX_BATCH_CAND = 64
 
 # Every entry point declared in include/raftgp.h.
 EXPORTS = ("raftgp_workspace_size", "raftgp_embed", "raftgp_select", "raftgp_partition", "raftgp_score",
-           "raftgp_kmeanspp", "raftgp_kmeanspp_noalloc", "raftgp_lloyd", "raftgp_profile_enable", "raftgp_profile_read", "raftgp_last_error",
+           "raftgp_kmeanspp", "raftgp_kmeanspp_noalloc", "raftgp_lloyd", "raftgp_profile_enable", "raftgp_profile_enable_family", "raftgp_profile_read", "raftgp_last_error",
            "raftgp_version")
 
 
@@ -89,6 +89,8 @@ def lib():
             getattr(L, name).restype = C.c_int
         L.raftgp_profile_enable.restype = C.c_int
         L.raftgp_profile_enable.argtypes = [C.c_int32]
+        L.raftgp_profile_enable_family.restype = C.c_int
+        L.raftgp_profile_enable_family.argtypes = [C.c_char_p]
         L.raftgp_profile_read.restype = C.c_int32
         L.raftgp_profile_read.argtypes = [C.POINTER(ProfEntry), C.c_int32]
         L.raftgp_last_error.restype = C.c_char_p

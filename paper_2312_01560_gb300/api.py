@@ -223,9 +223,13 @@ def lloyd(Z: torch.Tensor, mu0: torch.Tensor, iters=50, assign="ffma", stream=No
     return labels, mu, passes.value
 
 
-def profile_enable(on: bool = True) -> None:
-    """Start (clearing the counters) or stop per-kernel-family event timing in the library."""
-    check(lib().raftgp_profile_enable(1 if on else 0))
+def profile_enable(on: bool = True, family: str | None = None) -> None:
+    """Start (clearing the counters) or stop per-kernel-family event timing in the library;
+    with `family`, only that family records events."""
+    if on and family is not None:
+        check(lib().raftgp_profile_enable_family(family.encode()))
+    else:
+        check(lib().raftgp_profile_enable(1 if on else 0))
 
 
 def profile_read() -> dict:

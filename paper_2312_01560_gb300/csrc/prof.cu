@@ -3,6 +3,7 @@
 // profile synchronises the device and sums the elapsed times per family.
 #include <cuda_runtime.h>
 
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -18,6 +19,7 @@ static const char* kFamilyNames[PF_COUNT] = {
 struct Profiler {
     std::mutex mu;
     bool on = false;
+    uint64_t mask = ~0ull;              // families that record events
     std::vector<cudaEvent_t> pool;      // 2 events per record
     size_t used = 0;                    // pairs used
     struct Rec { int fam; int kernels; };
@@ -35,7 +37,7 @@ static constexpr size_t kPairs = 1 << 15;
 
 ProfScope::ProfScope(cudaStream_t s, int fam, int kernels) : s_(s), fam_(fam), kernels_(kernels), pair_(-1) {
     Profiler& p = prof();
-    if (!p.on) return;
+    if (!p.on || !((p.mask >> fam) & 1ull)) return;
     std::lock_guard<std::mutex> g(p.mu);
     p.launches[fam] += kernels;
     if (p.used >= kPairs) {
@@ -58,9 +60,10 @@ using namespace raftgp;
 
 extern "C" {
 
-raftgp_status raftgp_profile_enable(int32_t on) {
+static raftgp_status profile_start(int32_t on, uint64_t mask) {
     Profiler& p = prof();
     std::lock_guard<std::mutex> g(p.mu);
+    p.mask = mask;
     if (on && p.pool.empty()) {
         p.pool.resize(2 * kPairs);
         for (auto& e : p.pool)
@@ -71,6 +74,15 @@ raftgp_status raftgp_profile_enable(int32_t on) {
     p.recs.clear();
     for (int f = 0; f < PF_COUNT; ++f) p.launches[f] = p.untimed[f] = 0;
     return RAFTGP_OK;
+}
+
+raftgp_status raftgp_profile_enable(int32_t on) { return profile_start(on, ~0ull); }
+
+raftgp_status raftgp_profile_enable_family(const char* family) {
+    if (!family) return profile_start(1, ~0ull);
+    for (int f = 0; f < PF_COUNT; ++f)
+        if (std::strcmp(family, kFamilyNames[f]) == 0) return profile_start(1, 1ull << f);
+    return RAFTGP_EINVAL;
 }
 
 int32_t raftgp_profile_read(raftgp_prof_entry* out, int32_t cap) {
