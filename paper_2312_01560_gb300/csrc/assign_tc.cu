@@ -37,6 +37,8 @@
 
 namespace raftgp {
 
+constexpr int TC_GROUPS = 4;                          // epilogue warpgroups = point tiles per step
+
 // LO: the centroid chunks carry the lo half too (FINAL always; FAST optionally).  Without it a
 // ring stage is smaller, so the ring gets deeper.
 template <int D, bool LO = true>
@@ -46,7 +48,7 @@ struct TcCfg {
     static constexpr int NATOM = D / ATOM;
     static constexpr int NCH = 128;                       // centroids per chunk = MMA N = two slices
     static constexpr int SLICES = NCH / 64;               // 64-column slices per chunk
-    static constexpr int GROUPS = 4;                      // point tiles per CTA step, one per epilogue group
+    static constexpr int GROUPS = TC_GROUPS;              // point tiles per CTA step, one per epilogue group
     static constexpr int ACC_BUFS = 512 / (GROUPS * NCH); // accumulator buffers per group
     static constexpr int A_BUFS = D == 128 ? 1 : 2;       // point-tile groups in flight
     static constexpr int A_ATOM_BYTES = 128 * ATOM_BYTES;
@@ -71,7 +73,6 @@ struct TcCfg {
 };
 
 constexpr int TC_MAX_CHUNKS = 1024;
-constexpr int TC_GROUPS = 4;                          // epilogue warpgroups
 constexpr int TC_THREADS = 64 + TC_GROUPS * 128;      // warp 0 TMA, warp 1 MMA, then the epilogue groups
 
 struct TcCtl {
@@ -97,7 +98,6 @@ struct TcArgs {
     const __nv_bfloat16* Z;   // N x D
     KmState st;
     int pass;                 // FAST: pass number (parity selects the change counter)
-    int final_mode;           // 1 = FINAL
     uint32_t key_mul;         // 64 (a run-time operand, so the key is one integer multiply-add)
     float tie_band;           // FINAL: second-best within this band -> re-check
     int2* recheck;            // FINAL: list of (point, candidate)
@@ -105,12 +105,15 @@ struct TcArgs {
     uint32_t* err;
 };
 
-template <int D, bool LO>
+// FINAL: the reported assignment (hi + lo, exact top two, near-tie list); otherwise a Lloyd
+// pass.  One CTA of 576 threads per SM (at most 96 registers per thread).
+template <int D, bool LO, bool FINAL>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_assign_tc(const __grid_constant__ TcArgs a, const __grid_constant__ CUtensorMap tmA,
                 const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo,
                 const __grid_constant__ CUtensorMap tmAug) {
     using C = TcCfg<D, LO>;
+    static_assert(LO || !FINAL, "the final assignment multiplies both halves");
     extern __shared__ uint8_t dyn_smem[];
     __shared__ TcCtl ctl;
     uint8_t* base = (uint8_t*)(((uintptr_t)dyn_smem + 1023) & ~(uintptr_t)1023);
@@ -151,7 +154,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (col0 >= b.total_k) break;
                 while (c + 1 < b.n && b.off[c + 1] <= col0) ++c;
                 const int pad_end = c + 1 < b.n ? b.off[c + 1] : b.total_k;
-                if (col0 < b.off[c] + b.k[c] && (a.final_mode || a.st.active[c])) {
+                if (col0 < b.off[c] + b.k[c] && (FINAL || a.st.active[c])) {
                     info[h] = c + (col0 + 64 >= pad_end ? 128 : 0);
                     need = true;
                 }
@@ -260,7 +263,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 }
                         // FAST: + (||mu||^2 + 4)/2 + 128 from the constant slice, so the accumulator
                         // is 128 + (||z - mu||^2 - ||z||^2 + 4)/2
-                        if (!a.final_mode) mma_bf16(dcol, dAugA, dAugBst, idesc, 1);
+                        if (!FINAL) mma_bf16(dcol, dAugA, dAugBst, idesc, 1);
                         mma_commit(&ctl.acc_full[g][buf]);  // this group's accumulator is ready
                     }
                     if (ok) mma_commit(&ctl.b_empty[s]);  // the stage is free once these MMAs retire
@@ -288,19 +291,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int buf = it % C::ACC_BUFS;
                 if (!(ok = mbar_wait(&ctl.acc_full[wg][buf], (it / C::ACC_BUFS) & 1, &ctl, a.err))) break;
                 tc_fence_after();
-#pragma unroll 1
-                for (int h = 0; h < C::SLICES; ++h) {
-                    const int info = ctl.slice_info[C::SLICES * q + h];
-                    uint32_t r[1][64];
-                    if (info >= 0) tmem_ld64(lane_base + (uint32_t)(buf * C::NCH + 64 * h), r[0]);
-                    if (h == C::SLICES - 1) {
-                        tc_fence_before();
-                        mbar_arrive(&ctl.acc_empty[wg][buf]);   // every slice read: the buffer is free
-                    }
-                    if (info < 0) continue;
+                const int col_q = ctl.chunk_col[q];
+                // the candidate of slice h ends here: write its label for this point
+                auto finish = [&](int info) {
                     const int cand = info & 127;
-                    const int col0 = ctl.chunk_col[q] + 64 * h;
-                    if (a.final_mode) {
+                    const int K = b.k[cand], off = b.off[cand];
+                    int nl = bi - off;
+                    if (nl < 0 || nl >= K) nl = 0;       // non-finite scores: keep indices in range
+                    if (FINAL) {
+                        if (valid) {
+                            a.st.labels[i * b.cs + cand] = (int16_t)nl;
+                            if (!(b2 - bv > a.tie_band)) {
+                                const int slot = atomicAdd(a.recheck_count, 1);
+                                a.recheck[slot] = make_int2((int)i, cand);
+                            }
+                        }
+                    } else if (valid) {
+                        // the change against the previous pass is applied by k_apply_changes, so
+                        // this epilogue never waits on a load
+                        a.st.labels_new[i * b.cs + cand] = (int16_t)nl;
+                    }
+                    bv = INFINITY;
+                    b2 = INFINITY;
+                    bi = -1;
+                };
+                if (FINAL) {
+#pragma unroll 1
+                    for (int h = 0; h < C::SLICES; ++h) {
+                        const int info = ctl.slice_info[C::SLICES * q + h];
+                        uint32_t r[1][64];
+                        if (info >= 0) tmem_ld64(lane_base + (uint32_t)(buf * C::NCH + 64 * h), r[0]);
+                        if (h == C::SLICES - 1) {
+                            tc_fence_before();
+                            mbar_arrive(&ctl.acc_empty[wg][buf]);   // every slice read: the buffer is free
+                        }
+                        if (info < 0) continue;
+                        const int col0 = col_q + 64 * h;
                         // exact best and second best of ||mu||^2 + 4 - 2 z.mu (FP32 norms; padding
                         // columns carry an infinite norm and never win)
 #pragma unroll
@@ -317,49 +343,55 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 if (sc < bv) { b2 = bv; bv = sc; bi = col0 + 16 * v + k; } else { b2 = fminf(b2, sc); }
                             }
                         }
-                    } else {
-                        // keys: accumulator bits x 64 + (0x48000000 + column) wraps to
-                        // 0x08000000 + 64 m + column, a positive normal float, so a float minimum
-                        // gives the (score, column) minimum (four independent chains, merged at
-                        // the end).  An accumulator outside [128, 256) (a non-finite row) gives
-                        // a meaningless key; the label stays in range below.
-                        const uint32_t mul = a.key_mul;
-#define RAFTGP_KEY(j) __uint_as_float(r[0][j] * mul + (0x48000000u + (uint32_t)(j)))
-                        float m0 = INFINITY, m1 = INFINITY, m2 = INFINITY, m3 = INFINITY;
+                        if (info >= 128) finish(info);
+                    }
+                } else {
+                    // Lloyd pass: the chunk in 32-column pieces, the next piece's load in flight
+                    // while the current one is reduced; the buffer is released once the last
+                    // piece has landed.  Keys: accumulator bits x 64 + (0x48000000 + column)
+                    // wraps to 0x08000000 + 64 m + column, a positive normal float, so a float
+                    // minimum gives the (score, column) minimum (four independent chains).  An
+                    // accumulator outside [128, 256) (a non-finite row) gives a meaningless
+                    // key; the label stays in range in finish().
+                    constexpr int PIECES = C::NCH / 32;
+                    const uint32_t mul = a.key_mul;
+                    const uint32_t cbase = lane_base + (uint32_t)(buf * C::NCH);
+                    uint32_t r[2][32];
+                    float m0 = INFINITY, m1 = INFINITY, m2 = INFINITY, m3 = INFINITY;
+                    tmem_ld32_issue(cbase, r[0]);
+                    tmem_wait_ld(r[0]);
 #pragma unroll
-                        for (int k = 0; k < 64; k += 8) {
-                            m0 = min3f(m0, RAFTGP_KEY(k), RAFTGP_KEY(k + 1));
-                            m1 = min3f(m1, RAFTGP_KEY(k + 2), RAFTGP_KEY(k + 3));
-                            m2 = min3f(m2, RAFTGP_KEY(k + 4), RAFTGP_KEY(k + 5));
-                            m3 = min3f(m3, RAFTGP_KEY(k + 6), RAFTGP_KEY(k + 7));
+                    for (int pc = 0; pc < PIECES; ++pc) {
+                        if (pc + 1 < PIECES) {
+                            tmem_ld32_issue(cbase + 32u * (pc + 1), r[(pc + 1) & 1]);
+                        } else {
+                            tc_fence_before();
+                            mbar_arrive(&ctl.acc_empty[wg][buf]);   // every piece read: the buffer is free
                         }
-#undef RAFTGP_KEY
-                        const float kmin = fminf(min3f(m0, m1, m2), m3);
-                        const uint32_t kb = __float_as_uint(kmin);
-                        const float v = __uint_as_float(kb & 0xFFFFFFC0u);
-                        if (v < bv) { bv = v; bi = col0 + (int)(kb & 63u); }
-                    }
-                    if (info < 128) continue;              // the candidate continues in a later slice
-                    // ---- candidate finished for this tile: write the label ----
-                    const int K = b.k[cand], off = b.off[cand];
-                    int nl = bi - off;
-                    if (nl < 0 || nl >= K) nl = 0;       // non-finite scores: keep indices in range
-                    if (a.final_mode) {
-                        if (valid) {
-                            a.st.labels[i * b.cs + cand] = (int16_t)nl;
-                            if (!(b2 - bv > a.tie_band)) {
-                                const int slot = atomicAdd(a.recheck_count, 1);
-                                a.recheck[slot] = make_int2((int)i, cand);
+                        const uint32_t* x = r[pc & 1];
+                        const uint32_t c0 = 0x48000000u + 32u * (pc & 1);
+#pragma unroll
+                        for (int k = 0; k < 32; k += 8) {
+                            m0 = min3f(m0, __uint_as_float(x[k] * mul + (c0 + k)), __uint_as_float(x[k + 1] * mul + (c0 + k + 1)));
+                            m1 = min3f(m1, __uint_as_float(x[k + 2] * mul + (c0 + k + 2)), __uint_as_float(x[k + 3] * mul + (c0 + k + 3)));
+                            m2 = min3f(m2, __uint_as_float(x[k + 4] * mul + (c0 + k + 4)), __uint_as_float(x[k + 5] * mul + (c0 + k + 5)));
+                            m3 = min3f(m3, __uint_as_float(x[k + 6] * mul + (c0 + k + 6)), __uint_as_float(x[k + 7] * mul + (c0 + k + 7)));
+                        }
+                        if (pc & 1) {
+                            // end of 64-column slice h
+                            const int h = pc >> 1;
+                            const int info = ctl.slice_info[C::SLICES * q + h];
+                            if (info >= 0) {
+                                const float kmin = fminf(min3f(m0, m1, m2), m3);
+                                const uint32_t kb = __float_as_uint(kmin);
+                                const float v = __uint_as_float(kb & 0xFFFFFFC0u);
+                                if (v < bv) { bv = v; bi = col_q + 64 * h + (int)(kb & 63u); }
+                                if (info >= 128) finish(info);
                             }
+                            m0 = m1 = m2 = m3 = INFINITY;
                         }
-                    } else if (valid) {
-                        // the change against the previous pass is applied by k_apply_changes, so
-                        // this epilogue never waits on a load
-                        a.st.labels_new[i * b.cs + cand] = (int16_t)nl;
+                        if (pc + 1 < PIECES) tmem_wait_ld(r[(pc + 1) & 1]);
                     }
-                    bv = INFINITY;
-                    b2 = INFINITY;
-                    bi = -1;
                 }
             }
         }
@@ -448,9 +480,9 @@ static cudaError_t make_map(CUtensorMap* m, const void* base, int64_t rows, int 
                       C::ATOM_BYTES == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B);
 }
 
-template <int D, bool LO>
+template <int D, bool LO, bool FINAL>
 static cudaError_t launch_tc_t(const CandBatch& b, const __nv_bfloat16* Z, int64_t n, KmState st, int pass,
-                               int final_mode, int2* recheck, int* recheck_count, uint32_t* err, cudaStream_t s) {
+                               int2* recheck, int* recheck_count, uint32_t* err, cudaStream_t s) {
     using C = TcCfg<D, LO>;
     static_assert(C::SMEM + sizeof(TcCtl) <= 227 * 1024, "dynamic + static shared memory budget");
     cudaError_t e = get_encoder();
@@ -466,19 +498,18 @@ static cudaError_t launch_tc_t(const CandBatch& b, const __nv_bfloat16* Z, int64
     a.Z = Z;
     a.st = st;
     a.pass = pass;
-    a.final_mode = final_mode;
     a.key_mul = 64u;
     a.tie_band = 1.5e-4f * (float)D / 64.0f + 2.0e-5f;
     a.recheck = recheck;
     a.recheck_count = recheck_count;
     a.err = err;
     const int smem = C::SMEM;
-    auto kern = k_assign_tc<D, LO>;
+    auto kern = k_assign_tc<D, LO, FINAL>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
     const int64_t nsteps = (n + 128 * C::GROUPS - 1) / (128 * C::GROUPS);
     const int grid = (int)(nsteps < num_sms() ? nsteps : num_sms());
     {
-        ProfScope ps(s, final_mode ? PF_ASSIGN_TC_FINAL : (pass == 1 ? PF_ASSIGN_TC_FIRST : PF_ASSIGN_TC), 1);
+        ProfScope ps(s, FINAL ? PF_ASSIGN_TC_FINAL : (pass == 1 ? PF_ASSIGN_TC_FIRST : PF_ASSIGN_TC), 1);
         kern<<<grid, TC_THREADS, smem, s>>>(a, ta, th, tl, tg);
     }
     return cudaGetLastError();
@@ -492,8 +523,9 @@ cudaError_t launch_assign_tc(const CandBatch& b, const void* Z, int64_t n, int d
     const bool lo = final_mode || fast_lo;     // FINAL always multiplies both halves
 #define RAFTGP_TC_CASE(DD)                                                                         \
     case DD:                                                                                     \
-        return lo ? launch_tc_t<DD, true>(b, z, n, st, pass, final_mode, recheck, recheck_count, err, s) \
-                  : launch_tc_t<DD, false>(b, z, n, st, pass, final_mode, recheck, recheck_count, err, s);
+        return final_mode ? launch_tc_t<DD, true, true>(b, z, n, st, pass, recheck, recheck_count, err, s)   \
+               : lo       ? launch_tc_t<DD, true, false>(b, z, n, st, pass, recheck, recheck_count, err, s)  \
+                          : launch_tc_t<DD, false, false>(b, z, n, st, pass, recheck, recheck_count, err, s);
     switch (d) {
         RAFTGP_TC_CASE(32)
         RAFTGP_TC_CASE(64)

@@ -867,6 +867,8 @@ __global__ void __launch_bounds__(256) k_assign_ffma(CandBatch b, const T* __res
         s_new[p] = nl;
         s_old[p] = ol;
     }
+    __shared__ int s_nch;
+    if (threadIdx.x == 0) s_nch = 0;
     __syncthreads();
     // label changes -> counts, fixed-point sums, changed counter
     int nchanged = 0;
@@ -888,8 +890,11 @@ __global__ void __launch_bounds__(256) k_assign_ffma(CandBatch b, const T* __res
             atomicAdd(reinterpret_cast<unsigned long long*>(st.sums + (int64_t)(off + ol) * D + k),
                       (unsigned long long)(-v));
     }
+    // one global atomic per CTA on the candidate's change counter
     nchanged = __reduce_add_sync(0xffffffffu, nchanged);
-    if ((threadIdx.x & 31) == 0 && nchanged) atomicAdd(st.changed + (pass & 1) * MAXC + c, nchanged);
+    if ((threadIdx.x & 31) == 0 && nchanged) atomicAdd(&s_nch, nchanged);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_nch) atomicAdd(st.changed + (pass & 1) * MAXC + c, s_nch);
 }
 
 template <typename T, int D>
@@ -940,6 +945,11 @@ __global__ void __launch_bounds__(256) k_apply_changes(CandBatch b, const T* __r
     unsigned long long act = 0;   // candidates reassigned in this pass
     for (int c = 0; c < b.n; ++c)
         if (st.active[c]) act |= 1ull << c;
+    // changes per candidate, counted in shared memory and added to the global counter once per
+    // block (one global atomic per warp would serialise every warp on the same few words)
+    __shared__ int s_changed[MAXC];
+    for (int c = threadIdx.x; c < MAXC; c += blockDim.x) s_changed[c] = 0;
+    __syncthreads();
     // thread per point; its label row (cs int16 = whole 16-byte vectors) is read once
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
         const int64_t i = base + threadIdx.x;
@@ -963,7 +973,7 @@ __global__ void __launch_bounds__(256) k_apply_changes(CandBatch b, const T* __r
                     if (ol >= 0) atomicSub(st.counts + b.off[c] + ol, 1);
                 }
                 unsigned mask = __ballot_sync(0xffffffffu, ch);
-                if (lane == 0 && mask) atomicAdd(st.changed + (pass & 1) * MAXC + c, __popc(mask));
+                if (lane == 0 && mask) atomicAdd(&s_changed[c], __popc(mask));
                 while (mask) {
                     const int src = __ffs(mask) - 1;
                     mask &= mask - 1;
@@ -983,6 +993,9 @@ __global__ void __launch_bounds__(256) k_apply_changes(CandBatch b, const T* __r
             }
         }
     }
+    __syncthreads();
+    for (int c = threadIdx.x; c < b.n; c += blockDim.x)
+        if (s_changed[c]) atomicAdd(st.changed + (pass & 1) * MAXC + c, s_changed[c]);
 }
 
 void launch_apply_changes(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, KmState st, int pass,
