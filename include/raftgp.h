@@ -212,6 +212,52 @@ const char* raftgp_last_error(void);
 /* Library version string. */
 const char* raftgp_version(void);
 
+/* ---- Differentiation form (the paper trains nothing: its GNN stays random, Section III-B;
+ * these calls let the Eq. 6 weights be tuned against a relaxed modularity) ----
+ * All arrays are device FP32, row-major; widths (lin, lout, d) are 32, 64 or 128; K <= 128.
+ * Each call validates the graph on the device first (malformed graph: RAFTGP_EINVAL, nothing
+ * else runs) and synchronises the stream once for that check.  `ws` is a device workspace
+ * of at least raftgp_diff_workspace_size(n, width, K) bytes, width = the largest layer
+ * width used, K = the largest centroid count; the caller owns every buffer. */
+size_t raftgp_diff_workspace_size(int64_t n, int32_t width, int32_t K);
+
+/* One Eq. 6 layer: H_out = rownorm(tanh(Ahat (H_in W))), Ahat = Dhat^-1/2 (A + I) Dhat^-1/2,
+ * dhat = d + 1; H_in n x lin, W lin x lout, H_out n x lout; a zero row stays zero. */
+raftgp_status raftgp_gcn_layer_forward(const raftgp_csr* g, const float* H_in, int32_t lin, const float* W,
+                                       int32_t lout, float* H_out, void* ws, size_t ws_bytes, raftgp_stream_t stream);
+
+/* Gradients of that layer given dH_out = dL/dH_out (n x lout): dW (lin x lout) and, unless
+ * dH_in is NULL, dH_in (n x lin).  Nothing from the forward is kept: P = H_in W and the
+ * pre-activation are computed again here.  dW is summed over the points in FP64 in a fixed
+ * order (deterministic). */
+raftgp_status raftgp_gcn_layer_backward(const raftgp_csr* g, const float* H_in, int32_t lin, const float* W,
+                                        int32_t lout, const float* dH_out, float* dH_in, float* dW, void* ws,
+                                        size_t ws_bytes, raftgp_stream_t stream);
+
+/* Relaxed modularity of the soft assignment S_i = softmax_c(-||z_i - mu_c||^2 / tau) against
+ * fixed centroids mu (K x d): *loss (host) = -(tr(S^T A S) - ||d^T S||^2 / 2e) / 2e, which is
+ * -Mod (Eq. 3) when S is one-hot.  Unless dZ is NULL, dZ = dL/dZ (n x d).  Synchronises. */
+raftgp_status raftgp_softmod_loss(const raftgp_csr* g, const float* Z, int32_t d, const float* mu, int32_t K,
+                                  float tau, double* loss, float* dZ, void* ws, size_t ws_bytes,
+                                  raftgp_stream_t stream);
+
+/* Centroids of a labelling: mu (K x d) = the mean of the rows of each label (exact 2^-40
+ * fixed-point sums, FP64 mean); an empty label gets a zero row.  labels: int32 in [0, K)
+ * (RAFTGP_EINVAL otherwise).  Synchronises. */
+raftgp_status raftgp_centroids(const float* Z, int64_t n, int32_t d, const int32_t* labels, int32_t K, float* mu,
+                               void* ws, size_t ws_bytes, raftgp_stream_t stream);
+
+/* The Eq. 6 weights the embedding draws for layer `layer` (1-based) from `seed`: W (device,
+ * lin x lout) = Xavier-normal, std sqrt(2 / (lin + lout)), from Philox counters (q, a, layer,
+ * "Wgnn").  The starting point of a tuning run.  Asynchronous. */
+raftgp_status raftgp_gcn_weights(int32_t layer, int32_t lin, int32_t lout, uint64_t seed, float* W,
+                                 raftgp_stream_t stream);
+
+/* One Adam step (Kingma and Ba, 2015) in place on count FP32 parameters: m, v are the moment
+ * buffers (zero before step 1), step counts from 1.  Asynchronous. */
+raftgp_status raftgp_adam_step(float* param, const float* grad, float* m, float* v, int64_t count, float lr,
+                               float beta1, float beta2, float eps, int32_t step, raftgp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

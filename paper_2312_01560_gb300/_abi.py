@@ -23,7 +23,8 @@ MAX_BATCH_CAND = 64
 # Every entry point declared in include/raftgp.h.
 EXPORTS = ("raftgp_workspace_size", "raftgp_embed", "raftgp_select", "raftgp_partition", "raftgp_score",
            "raftgp_kmeanspp", "raftgp_kmeanspp_noalloc", "raftgp_lloyd", "raftgp_profile_enable", "raftgp_profile_enable_family", "raftgp_profile_read", "raftgp_last_error",
-           "raftgp_version")
+           "raftgp_version", "raftgp_diff_workspace_size", "raftgp_gcn_layer_forward", "raftgp_gcn_layer_backward",
+           "raftgp_softmod_loss", "raftgp_centroids", "raftgp_gcn_weights", "raftgp_adam_step")
 
 
 class Csr(C.Structure):
@@ -93,6 +94,19 @@ def lib():
         L.raftgp_profile_enable_family.argtypes = [C.c_char_p]
         L.raftgp_profile_read.restype = C.c_int32
         L.raftgp_profile_read.argtypes = [C.POINTER(ProfEntry), C.c_int32]
+        L.raftgp_diff_workspace_size.restype = C.c_size_t
+        L.raftgp_diff_workspace_size.argtypes = [C.c_int64, C.c_int32, C.c_int32]
+        L.raftgp_gcn_layer_forward.argtypes = [C.POINTER(Csr), P, C.c_int32, P, C.c_int32, P, P, C.c_size_t, P]
+        L.raftgp_gcn_layer_backward.argtypes = [C.POINTER(Csr), P, C.c_int32, P, C.c_int32, P, P, P, P, C.c_size_t, P]
+        L.raftgp_softmod_loss.argtypes = [C.POINTER(Csr), P, C.c_int32, P, C.c_int32, C.c_float,
+                                          C.POINTER(C.c_double), P, P, C.c_size_t, P]
+        L.raftgp_centroids.argtypes = [P, C.c_int64, C.c_int32, P, C.c_int32, P, P, C.c_size_t, P]
+        L.raftgp_adam_step.argtypes = [P, P, P, P, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int32,
+                                       P]
+        L.raftgp_gcn_weights.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P, P]
+        for name in ("raftgp_gcn_layer_forward", "raftgp_gcn_layer_backward", "raftgp_softmod_loss",
+                     "raftgp_centroids", "raftgp_gcn_weights", "raftgp_adam_step"):
+            getattr(L, name).restype = C.c_int
         L.raftgp_last_error.restype = C.c_char_p
         L.raftgp_last_error.argtypes = []
         L.raftgp_version.restype = C.c_char_p

@@ -160,9 +160,11 @@ def select(g: DeviceGraph, Z: torch.Tensor, kmin=2, kmax=40, grid=0, iters=50, c
 
 
 def partition(g: DeviceGraph, op="ncut", dims=(64, 64, 32), dtype="f32", embed_seed=1, kmin=2, kmax=40, grid=0,
-              iters=50, criterion="mod", assign="ffma", batch=0, select_seed=2, stream=None, labels=None):
-    """Stages 1-3 end to end: returns (labels, report)."""
-    eo = embed_opts(op, dims, dtype, embed_seed)
+              iters=50, criterion="mod", assign="ffma", batch=0, select_seed=2, stream=None, labels=None, W=None):
+    """Stages 1-3 end to end: returns (labels, report).  W: optional GNN weights (FP32)."""
+    if W is not None:
+        W = [w.to(g.col.device, torch.float32).contiguous() for w in W]
+    eo = embed_opts(op, dims, dtype, embed_seed, None, W)
     so = select_opts(kmin, kmax, grid, iters, criterion, assign, batch, select_seed)
     csr = g.csr()
     nbytes = lib().raftgp_workspace_size(C.byref(csr), C.byref(eo), C.byref(so), 0)
@@ -242,3 +244,86 @@ def profile_read() -> dict:
 
 def version() -> str:
     return lib().raftgp_version().decode()
+
+
+# ---- differentiation form (argument marshalling only; every step runs in the library) ----
+def _diff_ws(n, width, K, device):
+    return _workspace(int(lib().raftgp_diff_workspace_size(int(n), int(width), int(K))), device)
+
+
+def _f32(t: torch.Tensor) -> torch.Tensor:
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float32 tensor")
+    return t
+
+
+def gcn_layer_forward(g: DeviceGraph, H: torch.Tensor, W: torch.Tensor, stream=None) -> torch.Tensor:
+    """One Eq. 6 layer: rownorm(tanh(Ahat (H W)))."""
+    H, W = _f32(H), _f32(W)
+    lin, lout = W.shape
+    out = torch.empty((g.n, lout), dtype=torch.float32, device=H.device)
+    ws = _diff_ws(g.n, max(lin, lout), 0, H.device)
+    csr = g.csr()
+    check(lib().raftgp_gcn_layer_forward(C.byref(csr), C.c_void_p(H.data_ptr()), lin, C.c_void_p(W.data_ptr()), lout,
+                                         C.c_void_p(out.data_ptr()), C.c_void_p(ws.data_ptr()), ws.numel(),
+                                         _stream(stream)))
+    return out
+
+
+def gcn_layer_backward(g: DeviceGraph, H: torch.Tensor, W: torch.Tensor, dH_out: torch.Tensor, need_dH=True,
+                       stream=None):
+    """(dH_in or None, dW) of one layer, the forward recomputed from H."""
+    H, W, dH_out = _f32(H), _f32(W), _f32(dH_out)
+    lin, lout = W.shape
+    dW = torch.empty((lin, lout), dtype=torch.float32, device=H.device)
+    dH = torch.empty((g.n, lin), dtype=torch.float32, device=H.device) if need_dH else None
+    ws = _diff_ws(g.n, max(lin, lout), 0, H.device)
+    csr = g.csr()
+    check(lib().raftgp_gcn_layer_backward(C.byref(csr), C.c_void_p(H.data_ptr()), lin, C.c_void_p(W.data_ptr()), lout,
+                                          C.c_void_p(dH_out.data_ptr()), C.c_void_p(dH.data_ptr() if need_dH else None),
+                                          C.c_void_p(dW.data_ptr()), C.c_void_p(ws.data_ptr()), ws.numel(),
+                                          _stream(stream)))
+    return dH, dW
+
+
+def softmod_loss(g: DeviceGraph, Z: torch.Tensor, mu: torch.Tensor, tau: float, need_grad=True, stream=None):
+    """(loss as a Python float, dL/dZ or None) of the relaxed soft-assignment modularity."""
+    Z, mu = _f32(Z), _f32(mu)
+    d = Z.shape[1]
+    K = mu.shape[0]
+    dZ = torch.empty_like(Z) if need_grad else None
+    ws = _diff_ws(g.n, d, K, Z.device)
+    loss = C.c_double(0.0)
+    csr = g.csr()
+    check(lib().raftgp_softmod_loss(C.byref(csr), C.c_void_p(Z.data_ptr()), d, C.c_void_p(mu.data_ptr()), K,
+                                    float(tau), C.byref(loss), C.c_void_p(dZ.data_ptr() if need_grad else None),
+                                    C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return loss.value, dZ
+
+
+def centroids(Z: torch.Tensor, labels: torch.Tensor, K: int, stream=None) -> torch.Tensor:
+    Z = _f32(Z)
+    n, d = Z.shape
+    lab = labels.to(torch.int32).contiguous()
+    mu = torch.empty((K, d), dtype=torch.float32, device=Z.device)
+    ws = _diff_ws(n, d, K, Z.device)
+    check(lib().raftgp_centroids(C.c_void_p(Z.data_ptr()), n, d, C.c_void_p(lab.data_ptr()), int(K),
+                                 C.c_void_p(mu.data_ptr()), C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return mu
+
+
+def adam_step(param: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor, step: int, lr=1e-3,
+              beta1=0.9, beta2=0.999, eps=1e-8, stream=None) -> None:
+    for t in (param, grad, m, v):
+        _f32(t)
+    check(lib().raftgp_adam_step(C.c_void_p(param.data_ptr()), C.c_void_p(grad.data_ptr()), C.c_void_p(m.data_ptr()),
+                                 C.c_void_p(v.data_ptr()), param.numel(), float(lr), float(beta1), float(beta2),
+                                 float(eps), int(step), _stream(stream)))
+
+
+def gcn_weights(layer: int, lin: int, lout: int, seed: int, device, stream=None) -> torch.Tensor:
+    """The Eq. 6 weights the embedding draws for `layer` (1-based) from `seed`."""
+    W = torch.empty((lin, lout), dtype=torch.float32, device=device)
+    check(lib().raftgp_gcn_weights(int(layer), int(lin), int(lout), int(seed), C.c_void_p(W.data_ptr()),
+                                   _stream(stream)))
+    return W

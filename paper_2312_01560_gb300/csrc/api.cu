@@ -686,3 +686,163 @@ const char* raftgp_last_error(void) { return g_last_error.c_str(); }
 const char* raftgp_version(void) { return "raftgp-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------
+// Differentiation form: one workspace layout for every call
+// ------------------------------------------------------------------------------------
+namespace {
+struct DiffWs {
+    int32_t* deg;
+    float *rs, *rsh;
+    uint32_t* err;
+    float *P, *dA, *dP;     // n x width each
+    float* wpart;           // wgrad partials
+    float *S, *AS;          // n x 128 each
+    double *spart, *red;    // loss partials, reduced sums
+    long long* csums;       // K x width
+    int* ccounts;           // K
+};
+
+DiffWs carve_diff(Carver& c, int64_t n, int width, int K) {
+    DiffWs w{};
+    w.deg = c.take<int32_t>(n);
+    w.rs = c.take<float>(n);
+    w.rsh = c.take<float>(n);
+    w.err = c.take<uint32_t>(64);
+    w.P = c.take<float>((size_t)n * width);
+    w.dA = c.take<float>((size_t)n * width);
+    w.dP = c.take<float>((size_t)n * width);
+    w.wpart = c.take<float>((size_t)wgrad_blocks(n) * width * width);
+    w.S = c.take<float>((size_t)n * 128);
+    w.AS = c.take<float>((size_t)n * 128);
+    w.spart = c.take<double>((size_t)softmod_blocks(n) * 129);
+    w.red = c.take<double>(129 + 64);
+    w.csums = c.take<long long>((size_t)(K > 0 ? K : 1) * width);
+    w.ccounts = c.take<int>(K > 0 ? K : 1);
+    return w;
+}
+
+// degrees, the normalisation and the device graph check (read back before any gather)
+raftgp_status diff_prepare(const raftgp_csr* g, const DiffWs& w, cudaStream_t s) {
+    cudaMemsetAsync(w.err, 0, sizeof(uint32_t), s);
+    launch_degrees(g, w.deg, w.rs, w.rsh, w.err, nullptr, nullptr, s);
+    return read_error_word(w.err, s);
+}
+}  // namespace
+
+extern "C" {
+
+size_t raftgp_diff_workspace_size(int64_t n, int32_t width, int32_t K) {
+    Carver c(nullptr);
+    carve_diff(c, n, width, K);
+    return c.off + 256;
+}
+
+raftgp_status raftgp_gcn_layer_forward(const raftgp_csr* g, const float* H_in, int32_t lin, const float* W,
+                                       int32_t lout, float* H_out, void* ws, size_t ws_bytes, raftgp_stream_t stream) {
+    raftgp_status st = check_csr(g);
+    if (st) return st;
+    if (!H_in || !W || !H_out || !ws) return fail(RAFTGP_EINVAL, "NULL argument");
+    if (!width_ok(lin) || !width_ok(lout)) return fail(RAFTGP_EUNSUPPORTED, "widths must be 32, 64 or 128");
+    const int width = std::max(lin, lout);
+    if (ws_bytes < raftgp_diff_workspace_size(g->n, width, 0)) return fail(RAFTGP_ENOMEM, "workspace too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    Carver c(ws);
+    DiffWs w = carve_diff(c, g->n, width, 0);
+    if ((st = diff_prepare(g, w, s))) return st;
+    cudaError_t e = launch_rowmm(g->n, H_in, lin, W, lout, false, w.P, s);
+    if (e == cudaSuccess) e = launch_spmm32(g, lout, w.rsh, w.P, nullptr, H_out, 0, s);
+    if (e != cudaSuccess) return cuda_fail(e, "gcn layer forward");
+    return RAFTGP_OK;
+}
+
+raftgp_status raftgp_gcn_layer_backward(const raftgp_csr* g, const float* H_in, int32_t lin, const float* W,
+                                        int32_t lout, const float* dH_out, float* dH_in, float* dW, void* ws,
+                                        size_t ws_bytes, raftgp_stream_t stream) {
+    raftgp_status st = check_csr(g);
+    if (st) return st;
+    if (!H_in || !W || !dH_out || !dW || !ws) return fail(RAFTGP_EINVAL, "NULL argument");
+    if (!width_ok(lin) || !width_ok(lout)) return fail(RAFTGP_EUNSUPPORTED, "widths must be 32, 64 or 128");
+    const int width = std::max(lin, lout);
+    if (ws_bytes < raftgp_diff_workspace_size(g->n, width, 0)) return fail(RAFTGP_ENOMEM, "workspace too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    Carver c(ws);
+    DiffWs w = carve_diff(c, g->n, width, 0);
+    if ((st = diff_prepare(g, w, s))) return st;
+    // recompute P = H_in W; dA from the recomputed pre-activation and dH_out; dP = Ahat dA
+    cudaError_t e = launch_rowmm(g->n, H_in, lin, W, lout, false, w.P, s);
+    if (e == cudaSuccess) e = launch_spmm32(g, lout, w.rsh, w.P, dH_out, w.dA, 1, s);
+    if (e == cudaSuccess) e = launch_spmm32(g, lout, w.rsh, w.dA, nullptr, w.dP, 2, s);
+    if (e == cudaSuccess) e = launch_wgrad(g->n, H_in, lin, w.dP, lout, w.wpart, dW, s);
+    if (e == cudaSuccess && dH_in) e = launch_rowmm(g->n, w.dP, lout, W, lin, true, dH_in, s);
+    if (e != cudaSuccess) return cuda_fail(e, "gcn layer backward");
+    return RAFTGP_OK;
+}
+
+raftgp_status raftgp_softmod_loss(const raftgp_csr* g, const float* Z, int32_t d, const float* mu, int32_t K,
+                                  float tau, double* loss, float* dZ, void* ws, size_t ws_bytes,
+                                  raftgp_stream_t stream) {
+    raftgp_status st = check_csr(g);
+    if (st) return st;
+    if (!Z || !mu || !loss || !ws) return fail(RAFTGP_EINVAL, "NULL argument");
+    if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d must be 32, 64 or 128");
+    if (K < 1 || K > 128) return fail(RAFTGP_EUNSUPPORTED, "K must be in [1, 128]");
+    if (!(tau > 0.f)) return fail(RAFTGP_EINVAL, "tau must be positive");
+    if (ws_bytes < raftgp_diff_workspace_size(g->n, d, K)) return fail(RAFTGP_ENOMEM, "workspace too small");
+    if (g->nnz == 0) return fail(RAFTGP_EINVAL, "the loss needs at least one edge");
+    cudaStream_t s = (cudaStream_t)stream;
+    Carver c(ws);
+    DiffWs w = carve_diff(c, g->n, d, K);
+    if ((st = diff_prepare(g, w, s))) return st;
+    const double two_e = (double)g->nnz;
+    cudaError_t e = launch_soft_assign(g->n, d, Z, mu, K, tau, w.S, s);
+    if (e == cudaSuccess) e = launch_spmm32(g, 128, w.rsh, w.S, nullptr, w.AS, 3, s);
+    if (e == cudaSuccess) e = launch_softmod_reduce(g->n, w.deg, w.S, w.AS, w.spart, w.red, s);
+    if (e == cudaSuccess && dZ) e = launch_softmod_grad(g->n, d, Z, mu, K, tau, w.deg, w.S, w.AS, w.red, two_e, dZ, s);
+    if (e != cudaSuccess) return cuda_fail(e, "softmod loss");
+    double h[129];
+    e = cudaMemcpyAsync(h, w.red, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "softmod loss readback");
+    double dd = 0.0;
+    for (int k = 0; k < K; ++k) dd += h[k] * h[k];
+    *loss = -(h[128] - dd / two_e) / two_e;
+    return RAFTGP_OK;
+}
+
+raftgp_status raftgp_centroids(const float* Z, int64_t n, int32_t d, const int32_t* labels, int32_t K, float* mu,
+                               void* ws, size_t ws_bytes, raftgp_stream_t stream) {
+    if (!Z || !labels || !mu || !ws || n < 1) return fail(RAFTGP_EINVAL, "NULL argument or n < 1");
+    if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d must be 32, 64 or 128");
+    if (K < 1) return fail(RAFTGP_EINVAL, "K < 1");
+    if (ws_bytes < raftgp_diff_workspace_size(n, d, K)) return fail(RAFTGP_ENOMEM, "workspace too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    Carver c(ws);
+    DiffWs w = carve_diff(c, n, d, K);
+    cudaMemsetAsync(w.err, 0, sizeof(uint32_t), s);
+    cudaError_t e = launch_centroids(n, d, Z, labels, K, w.csums, w.ccounts, mu, w.err, s);
+    if (e != cudaSuccess) return cuda_fail(e, "centroids");
+    return read_error_word(w.err, s);
+}
+
+raftgp_status raftgp_gcn_weights(int32_t layer, int32_t lin, int32_t lout, uint64_t seed, float* W,
+                                 raftgp_stream_t stream) {
+    if (!W) return fail(RAFTGP_EINVAL, "W is NULL");
+    if (layer < 1 || layer > RAFTGP_MAX_LAYERS) return fail(RAFTGP_EINVAL, "layer must be in [1, %d]", RAFTGP_MAX_LAYERS);
+    if (!width_ok(lin) || !width_ok(lout)) return fail(RAFTGP_EUNSUPPORTED, "widths must be 32, 64 or 128");
+    launch_weights(layer, lin, lout, seed, W, (cudaStream_t)stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "gcn weights");
+    return RAFTGP_OK;
+}
+
+raftgp_status raftgp_adam_step(float* param, const float* grad, float* m, float* v, int64_t count, float lr,
+                               float beta1, float beta2, float eps, int32_t step, raftgp_stream_t stream) {
+    if (!param || !grad || !m || !v || count < 1) return fail(RAFTGP_EINVAL, "NULL argument or count < 1");
+    if (step < 1) return fail(RAFTGP_EINVAL, "step counts from 1");
+    cudaError_t e = launch_adam(param, grad, m, v, count, lr, beta1, beta2, eps, step, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "adam");
+    return RAFTGP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,576 @@
+// diff.cu -- the differentiation form: forward and backward of one Eq. 6 GCN layer, a relaxed
+// soft-assignment modularity loss with its gradient, an Adam step, and centroids from labels.
+//
+// Layer (FP32 storage, FP32 arithmetic, FP64 for the reductions over points):
+//     P = H W,  A = Ahat P,  T = tanh(A),  H' = T / ||T||_row          (a zero row stays 0)
+//     Ahat = Dhat^-1/2 (A + I) Dhat^-1/2, dhat = d + 1
+// Backward with recomputation (only the layer input is kept): P and A are computed again,
+//     dT = (dH' - H' (H' . dH')) / ||T||,  dA = dT (1 - T^2),  dP = Ahat dA  (Ahat symmetric),
+//     dW = H^T dP,  dH = dP W^T.
+// Loss against fixed centroids mu (K <= 128), temperature tau:
+//     S_i = softmax_c(-||z_i - mu_c||^2 / tau),  L = -(tr(S^T A S) - ||d^T S||^2 / 2e) / 2e,
+//     dL/dS = -(A S - d (d^T S) / 2e) / e,  dL/dD = -S (dL/dS - rowsum(S dL/dS)) / tau,
+//     dL/dz_i = 2 (sum_c G_ic) z_i - 2 sum_c G_ic mu_c.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace raftgp {
+
+// ------------------------------------------------------------------------------------
+// Y = X W (TRANS: X W^T), X: n x LIN, W: LIN x LOUT (TRANS: LOUT x LIN, row-major).
+// Block of 256 threads, 64 rows per tile; thread (ty, tx) owns rows 4ty..4ty+3 and columns
+// tx*CW..tx*CW+CW-1 (CW = LOUT/16); the k loop runs in ascending order.
+// ------------------------------------------------------------------------------------
+template <int LIN, int LOUT, bool TRANS>
+__global__ void __launch_bounds__(256) k_rowmm(int64_t n, const float* __restrict__ X, const float* __restrict__ W,
+                                               float* __restrict__ Y) {
+    constexpr int CW = LOUT / 16;
+    extern __shared__ float sm[];
+    float* sW = sm;                    // LIN x LOUT
+    float* sX = sm + LIN * LOUT;       // 64 x (LIN + 1)
+    for (int t = threadIdx.x; t < LIN * LOUT; t += 256) {
+        const int k = t / LOUT, c = t % LOUT;
+        sW[t] = TRANS ? W[(int64_t)c * LIN + k] : W[t];
+    }
+    const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+    for (int64_t r0 = (int64_t)blockIdx.x * 64; r0 < n; r0 += (int64_t)gridDim.x * 64) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < 64 * LIN; t += 256) {
+            const int r = t / LIN, k = t % LIN;
+            sX[r * (LIN + 1) + k] = r0 + r < n ? X[(r0 + r) * LIN + k] : 0.f;
+        }
+        __syncthreads();
+        float acc[4][CW];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < CW; ++j) acc[i][j] = 0.f;
+        for (int k = 0; k < LIN; ++k) {
+            float a[4], b[CW];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = sX[(4 * ty + i) * (LIN + 1) + k];
+#pragma unroll
+            for (int j = 0; j < CW; ++j) b[j] = sW[k * LOUT + tx * CW + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < CW; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t r = r0 + 4 * ty + i;
+            if (r < n)
+#pragma unroll
+                for (int j = 0; j < CW; ++j) Y[r * LOUT + tx * CW + j] = acc[i][j];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Warp-per-row SpMM over FP32 rows of width L (a multiple of 32; each lane VW = L/32
+// consecutive columns), four neighbour rows in flight per lane.  Modes:
+//   SP_GCN_FWD  out = rownorm(tanh(rsh_i (rsh_i x_i + sum_j rsh_j x_j)))
+//   SP_GCN_BWD  the same T, r, H' recomputed, then with g = dH'_i:
+//               out = (g - H' (H'.g)) / r * (1 - T^2)            (dA of the layer)
+//   SP_LINEAR   out = rsh_i (rsh_i x_i + sum_j rsh_j x_j)       (Ahat x)
+//   SP_ADJ      out = sum_j x_j                                  (A x)
+// ------------------------------------------------------------------------------------
+enum SpMode { SP_GCN_FWD = 0, SP_GCN_BWD = 1, SP_LINEAR = 2, SP_ADJ = 3 };
+
+template <typename OffT, int VW, int MODE>
+__global__ void __launch_bounds__(256) k_spmm32(Csr<OffT> g, const float* __restrict__ rsh, const float* __restrict__ X,
+                                                const float* __restrict__ G, float* __restrict__ out) {
+    constexpr int L = 32 * VW;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < g.n; i += warps) {
+        float acc[VW];
+        const float wi = MODE == SP_ADJ ? 0.f : __ldg(rsh + i);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) acc[v] = MODE == SP_ADJ ? 0.f : wi * __ldg(X + i * L + lane * VW + v);
+        const int64_t b = g.begin(i), e = g.end(i);
+        int64_t p = b;
+        for (; p + 4 <= e; p += 4) {
+            int j[4];
+            float w[4], x[4][VW];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) j[u] = __ldg(g.col + p + u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                w[u] = MODE == SP_ADJ ? 1.f : __ldg(rsh + j[u]);
+#pragma unroll
+                for (int v = 0; v < VW; ++v) x[u][v] = __ldg(X + (int64_t)j[u] * L + lane * VW + v);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < VW; ++v) acc[v] = fmaf(w[u], x[u][v], acc[v]);
+        }
+        for (; p < e; ++p) {
+            const int j = __ldg(g.col + p);
+            const float w = MODE == SP_ADJ ? 1.f : __ldg(rsh + j);
+#pragma unroll
+            for (int v = 0; v < VW; ++v) acc[v] = fmaf(w, __ldg(X + (int64_t)j * L + lane * VW + v), acc[v]);
+        }
+        float* o = out + i * L + lane * VW;
+        if constexpr (MODE == SP_ADJ) {
+#pragma unroll
+            for (int v = 0; v < VW; ++v) o[v] = acc[v];
+            continue;
+        } else {
+#pragma unroll
+            for (int v = 0; v < VW; ++v) acc[v] *= wi;
+        }
+        if constexpr (MODE == SP_LINEAR) {
+#pragma unroll
+            for (int v = 0; v < VW; ++v) o[v] = acc[v];
+            continue;
+        }
+        float T[VW], ss = 0.f;
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+            T[v] = tanhf(acc[v]);
+            ss = fmaf(T[v], T[v], ss);
+        }
+        ss = warp_sum(ss);
+        const float r = sqrtf(ss);
+        if (MODE == SP_GCN_FWD) {
+            const float inv = r > 0.f ? 1.0f / r : 0.f;
+#pragma unroll
+            for (int v = 0; v < VW; ++v) o[v] = T[v] * inv;
+        } else {
+            float H[VW], gv[VW], dot = 0.f;
+            const float inv = r > 0.f ? 1.0f / r : 0.f;
+#pragma unroll
+            for (int v = 0; v < VW; ++v) {
+                H[v] = T[v] * inv;
+                gv[v] = __ldg(G + i * L + lane * VW + v);
+                dot = fmaf(H[v], gv[v], dot);
+            }
+            dot = warp_sum(dot);
+#pragma unroll
+            for (int v = 0; v < VW; ++v) o[v] = (gv[v] - H[v] * dot) * inv * (1.0f - T[v] * T[v]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// dW = H^T dP over all rows: each block sums a contiguous row range into a LIN x LOUT FP32
+// partial (thread owns an 8 x 8 (or smaller) tile), then one kernel adds the partials in
+// block order in FP64.
+// ------------------------------------------------------------------------------------
+template <int LIN, int LOUT>
+__global__ void __launch_bounds__(256) k_wgrad(int64_t n, int64_t rows_per_block, const float* __restrict__ H,
+                                               const float* __restrict__ dP, float* __restrict__ partial) {
+    constexpr int TA = LIN / 16, TB = LOUT / 16;
+    __shared__ float sH[32][LIN + 1];
+    __shared__ float sP[32][LOUT + 1];
+    const int ta = threadIdx.x / 16, tb = threadIdx.x % 16;
+    float acc[TA][TB];
+#pragma unroll
+    for (int a = 0; a < TA; ++a)
+#pragma unroll
+        for (int c = 0; c < TB; ++c) acc[a][c] = 0.f;
+    const int64_t lo = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t hi = lo + rows_per_block < n ? lo + rows_per_block : n;
+    for (int64_t r0 = lo; r0 < hi; r0 += 32) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < 32 * LIN; t += 256) {
+            const int r = t / LIN, k = t % LIN;
+            sH[r][k] = r0 + r < hi ? H[(r0 + r) * LIN + k] : 0.f;
+        }
+        for (int t = threadIdx.x; t < 32 * LOUT; t += 256) {
+            const int r = t / LOUT, k = t % LOUT;
+            sP[r][k] = r0 + r < hi ? dP[(r0 + r) * LOUT + k] : 0.f;
+        }
+        __syncthreads();
+        for (int r = 0; r < 32; ++r) {
+            float a[TA], b[TB];
+#pragma unroll
+            for (int x = 0; x < TA; ++x) a[x] = sH[r][ta * TA + x];
+#pragma unroll
+            for (int y = 0; y < TB; ++y) b[y] = sP[r][tb * TB + y];
+#pragma unroll
+            for (int x = 0; x < TA; ++x)
+#pragma unroll
+                for (int y = 0; y < TB; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+        }
+    }
+    float* out = partial + (int64_t)blockIdx.x * LIN * LOUT;
+#pragma unroll
+    for (int x = 0; x < TA; ++x)
+#pragma unroll
+        for (int y = 0; y < TB; ++y) out[(ta * TA + x) * LOUT + tb * TB + y] = acc[x][y];
+}
+
+__global__ void k_sum_partials(const float* __restrict__ partial, int blocks, int count, float* __restrict__ out) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < blocks; ++b) s += (double)partial[(int64_t)b * count + t];
+        out[t] = (float)s;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Soft assignment: warp per point, lane owns centroids lane + 32u (u < 4); distances in
+// ascending coordinates; S written as n x 128 (zeros past K).
+// ------------------------------------------------------------------------------------
+constexpr int SK = 128;   // padded soft-assignment width
+
+template <int D>
+__global__ void __launch_bounds__(256) k_soft_assign(int64_t n, const float* __restrict__ Z, const float* __restrict__ mu,
+                                                     int K, float tau, float* __restrict__ S) {
+    extern __shared__ float smu[];   // K x D
+    for (int t = threadIdx.x; t < K * D; t += blockDim.x) smu[t] = mu[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        float z[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) z[k] = __ldg(Z + i * D + k);
+        float lg[4], mx = -INFINITY;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = lane + 32 * u;
+            lg[u] = -INFINITY;
+            if (c < K) {
+                float s = 0.f;
+#pragma unroll 8
+                for (int k = 0; k < D; ++k) {
+                    const float t = z[k] - smu[c * D + k];
+                    s = fmaf(t, t, s);
+                }
+                lg[u] = -s / tau;
+                mx = fmaxf(mx, lg[u]);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        float e[4], sum = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            e[u] = lane + 32 * u < K ? expf(lg[u] - mx) : 0.f;
+            sum += e[u];
+        }
+        sum = warp_sum(sum);
+        const float inv = 1.0f / sum;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) S[i * SK + lane + 32 * u] = e[u] * inv;
+    }
+}
+
+// Per-block FP64 partials of d^T S (SK columns) and of sum_i S_i . (AS)_i (column SK).
+__global__ void __launch_bounds__(256) k_softmod_partials(int64_t n, const int32_t* __restrict__ deg,
+                                                          const float* __restrict__ S, const float* __restrict__ AS,
+                                                          int64_t rows_per_block, double* __restrict__ partial) {
+    __shared__ double sdts[8][SK];
+    __shared__ double sq[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    double dts[4] = {0, 0, 0, 0}, q = 0.0;
+    const int64_t lo = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t hi = lo + rows_per_block < n ? lo + rows_per_block : n;
+    for (int64_t i = lo + w; i < hi; i += 8) {
+        const double di = (double)__ldg(deg + i);
+        double qi = 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float s = __ldg(S + i * SK + lane + 32 * u);
+            dts[u] += di * (double)s;
+            qi += (double)s * (double)__ldg(AS + i * SK + lane + 32 * u);
+        }
+        q += qi;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) sdts[w][lane + 32 * u] = dts[u];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if (lane == 0) sq[w] = q;
+    __syncthreads();
+    double* out = partial + (int64_t)blockIdx.x * (SK + 1);
+    for (int c = threadIdx.x; c < SK; c += blockDim.x) {
+        double s = 0.0;
+        for (int ww = 0; ww < 8; ++ww) s += sdts[ww][c];
+        out[c] = s;
+    }
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int ww = 0; ww < 8; ++ww) s += sq[ww];
+        out[SK] = s;
+    }
+}
+
+// Adds the block partials in block order: red[0..SK) = d^T S, red[SK] = sum S . AS.
+__global__ void k_softmod_finish(const double* __restrict__ partial, int blocks, double* __restrict__ red) {
+    for (int c = threadIdx.x; c <= SK; c += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < blocks; ++b) s += partial[(int64_t)b * (SK + 1) + c];
+        red[c] = s;
+    }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_softmod_grad(int64_t n, const float* __restrict__ Z, const float* __restrict__ mu,
+                                                      int K, float tau, const int32_t* __restrict__ deg,
+                                                      const float* __restrict__ S, const float* __restrict__ AS,
+                                                      const double* __restrict__ red, double two_e,
+                                                      float* __restrict__ dZ) {
+    extern __shared__ float smu[];   // K x D, then SK values of d^T S / 2e
+    float* sdts = smu + K * D;
+    for (int t = threadIdx.x; t < K * D; t += blockDim.x) smu[t] = mu[t];
+    for (int c = threadIdx.x; c < SK; c += blockDim.x) sdts[c] = (float)(red[c] / two_e);
+    __syncthreads();
+    const float inv_e = (float)(2.0 / two_e);
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        const float di = (float)__ldg(deg + i);
+        float s[4], gs[4], sdot = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = lane + 32 * u;
+            s[u] = __ldg(S + i * SK + c);
+            gs[u] = c < K ? -(__ldg(AS + i * SK + c) - di * sdts[c]) * inv_e : 0.f;
+            sdot = fmaf(s[u], gs[u], sdot);
+        }
+        sdot = warp_sum(sdot);
+        float G[4], gsum = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            G[u] = -s[u] * (gs[u] - sdot) / tau;
+            gsum += G[u];
+        }
+        gsum = warp_sum(gsum);
+        // dZ_i[k] = 2 gsum z_ik - 2 sum_c G_c mu_ck, lanes over coordinates
+        float m[D / 32];
+#pragma unroll
+        for (int q = 0; q < D / 32; ++q) m[q] = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int cend = K - 32 * u < 32 ? K - 32 * u : 32;
+            for (int l = 0; l < cend; ++l) {
+                const float Gc = __shfl_sync(0xffffffffu, G[u], l);
+                const int c = 32 * u + l;
+#pragma unroll
+                for (int q = 0; q < D / 32; ++q) m[q] = fmaf(Gc, smu[c * D + lane + 32 * q], m[q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < D / 32; ++q)
+            dZ[i * D + lane + 32 * q] = 2.0f * (gsum * __ldg(Z + i * D + lane + 32 * q) - m[q]);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Adam (Kingma and Ba, 2015), FP32 state.
+// ------------------------------------------------------------------------------------
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       int64_t count, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < count; t += (int64_t)gridDim.x * blockDim.x) {
+        const float gt = g[t];
+        const float mt = b1 * m[t] + (1.0f - b1) * gt;
+        const float vt = b2 * v[t] + (1.0f - b2) * gt * gt;
+        m[t] = mt;
+        v[t] = vt;
+        p[t] -= lr * (mt / c1) / (sqrtf(vt / c2) + eps);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Centroids of a labelling: exact 2^-40 fixed-point sums (int64 atomics, order-free), FP64
+// means; an empty cluster gets a zero row.
+// ------------------------------------------------------------------------------------
+__global__ void k_centroid_sums(int64_t n, int d, const float* __restrict__ Z, const int32_t* __restrict__ labels,
+                                int K, long long* __restrict__ sums, int* __restrict__ counts, uint32_t* err) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * d; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / d;
+        const int k = (int)(t % d);
+        const int l = labels[i];
+        if (l < 0 || l >= K) {
+            if (k == 0) flag_error(err, DERR_LABEL_RANGE);
+            continue;
+        }
+        atomicAdd(reinterpret_cast<unsigned long long*>(sums + (int64_t)l * d + k),
+                  (unsigned long long)__float2ll_rn(Z[t] * FIXED_SCALE_F));
+        if (k == 0) atomicAdd(counts + l, 1);
+    }
+}
+
+__global__ void k_centroid_means(int K, int d, const long long* __restrict__ sums, const int* __restrict__ counts,
+                                 float* __restrict__ mu) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < K * d; t += gridDim.x * blockDim.x) {
+        const int c = t / d;
+        mu[t] = counts[c] > 0 ? (float)((double)sums[t] / ((double)counts[c] * FIXED_SCALE)) : 0.f;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Host launchers
+// ------------------------------------------------------------------------------------
+static int grid_for(int64_t warps_needed) {
+    const int64_t cap = (int64_t)num_sms() * 16;
+    int64_t b = (warps_needed * 32 + 255) / 256;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+template <int LIN, int LOUT, bool TRANS>
+static cudaError_t rowmm_t(int64_t n, const float* X, const float* W, float* Y, cudaStream_t s) {
+    const size_t smem = (size_t)(LIN * LOUT + 64 * (LIN + 1)) * sizeof(float);
+    auto kern = k_rowmm<LIN, LOUT, TRANS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (n + 63) / 64;
+    const int64_t cap = (int64_t)num_sms() * 2;
+    if (blocks > cap) blocks = cap;
+    kern<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, smem, s>>>(n, X, W, Y);
+    return cudaGetLastError();
+}
+
+#define RAFTGP_WIDTHS(M)                                                                            \
+    M(32, 32) M(32, 64) M(32, 128) M(64, 32) M(64, 64) M(64, 128) M(128, 32) M(128, 64) M(128, 128)
+
+cudaError_t launch_rowmm(int64_t n, const float* X, int lin, const float* W, int lout, bool trans, float* Y,
+                         cudaStream_t s) {
+#define RAFTGP_RM(A, B)                                                                             \
+    if (lin == A && lout == B) return trans ? rowmm_t<A, B, true>(n, X, W, Y, s) : rowmm_t<A, B, false>(n, X, W, Y, s);
+    RAFTGP_WIDTHS(RAFTGP_RM)
+#undef RAFTGP_RM
+    return cudaErrorInvalidValue;
+}
+
+template <typename OffT, int VW>
+static cudaError_t spmm32_t(const Csr<OffT>& g, const float* rsh, const float* X, const float* G, float* out, int mode,
+                            cudaStream_t s) {
+    const int blocks = grid_for(g.n);
+    switch (mode) {
+        case SP_GCN_FWD: k_spmm32<OffT, VW, SP_GCN_FWD><<<blocks, 256, 0, s>>>(g, rsh, X, G, out); break;
+        case SP_GCN_BWD: k_spmm32<OffT, VW, SP_GCN_BWD><<<blocks, 256, 0, s>>>(g, rsh, X, G, out); break;
+        case SP_LINEAR: k_spmm32<OffT, VW, SP_LINEAR><<<blocks, 256, 0, s>>>(g, rsh, X, G, out); break;
+        default: k_spmm32<OffT, VW, SP_ADJ><<<blocks, 256, 0, s>>>(g, rsh, X, G, out); break;
+    }
+    return cudaGetLastError();
+}
+
+template <typename OffT>
+static cudaError_t spmm32_w(const Csr<OffT>& g, int L, const float* rsh, const float* X, const float* G, float* out,
+                            int mode, cudaStream_t s) {
+    switch (L) {
+        case 32: return spmm32_t<OffT, 1>(g, rsh, X, G, out, mode, s);
+        case 64: return spmm32_t<OffT, 2>(g, rsh, X, G, out, mode, s);
+        case 128: return spmm32_t<OffT, 4>(g, rsh, X, G, out, mode, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_spmm32(const raftgp_csr* g, int L, const float* rsh, const float* X, const float* G, float* out,
+                          int mode, cudaStream_t s) {
+    ProfScope ps(s, PF_DIFF, 1);
+    if (g->row_ptr_bits == 64) {
+        Csr<int64_t> c{g->n, g->nnz, (const int64_t*)g->row_ptr, g->col};
+        return spmm32_w(c, L, rsh, X, G, out, mode, s);
+    }
+    Csr<int32_t> c{g->n, g->nnz, (const int32_t*)g->row_ptr, g->col};
+    return spmm32_w(c, L, rsh, X, G, out, mode, s);
+}
+
+int wgrad_blocks(int64_t n) {
+    int64_t b = (n + 1023) / 1024;
+    const int64_t cap = (int64_t)num_sms() * 2;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+cudaError_t launch_wgrad(int64_t n, const float* H, int lin, const float* dP, int lout, float* partial, float* dW,
+                         cudaStream_t s) {
+    ProfScope ps(s, PF_DIFF, 2);
+    const int blocks = wgrad_blocks(n);
+    const int64_t rpb = (n + blocks - 1) / blocks;
+    bool done = false;
+#define RAFTGP_WG(A, B)                                                                             \
+    if (lin == A && lout == B) {                                                                    \
+        k_wgrad<A, B><<<blocks, 256, 0, s>>>(n, rpb, H, dP, partial);                              \
+        done = true;                                                                                \
+    }
+    RAFTGP_WIDTHS(RAFTGP_WG)
+#undef RAFTGP_WG
+    if (!done) return cudaErrorInvalidValue;
+    const int count = lin * lout;
+    k_sum_partials<<<(count + 255) / 256, 256, 0, s>>>(partial, blocks, count, dW);
+    return cudaGetLastError();
+}
+
+int softmod_blocks(int64_t n) {
+    int64_t b = (n + 2047) / 2048;
+    const int64_t cap = (int64_t)num_sms() * 2;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+cudaError_t launch_soft_assign(int64_t n, int d, const float* Z, const float* mu, int K, float tau, float* S,
+                               cudaStream_t s) {
+    ProfScope ps(s, PF_DIFF, 1);
+    const size_t smem = (size_t)K * d * sizeof(float);
+    const int blocks = grid_for(n);
+    switch (d) {
+        case 32: k_soft_assign<32><<<blocks, 256, smem, s>>>(n, Z, mu, K, tau, S); break;
+        case 64: k_soft_assign<64><<<blocks, 256, smem, s>>>(n, Z, mu, K, tau, S); break;
+        case 128:
+            cudaFuncSetAttribute(k_soft_assign<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_soft_assign<128><<<blocks, 256, smem, s>>>(n, Z, mu, K, tau, S);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_softmod_reduce(int64_t n, const int32_t* deg, const float* S, const float* AS, double* partial,
+                                  double* red, cudaStream_t s) {
+    ProfScope ps(s, PF_DIFF, 2);
+    const int blocks = softmod_blocks(n);
+    const int64_t rpb = (n + blocks - 1) / blocks;
+    k_softmod_partials<<<blocks, 256, 0, s>>>(n, deg, S, AS, rpb, partial);
+    k_softmod_finish<<<1, 256, 0, s>>>(partial, blocks, red);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_softmod_grad(int64_t n, int d, const float* Z, const float* mu, int K, float tau, const int32_t* deg,
+                                const float* S, const float* AS, const double* red, double two_e, float* dZ,
+                                cudaStream_t s) {
+    ProfScope ps(s, PF_DIFF, 1);
+    const size_t smem = (size_t)(K * d + SK) * sizeof(float);
+    const int blocks = grid_for(n);
+    switch (d) {
+        case 32: k_softmod_grad<32><<<blocks, 256, smem, s>>>(n, Z, mu, K, tau, deg, S, AS, red, two_e, dZ); break;
+        case 64: k_softmod_grad<64><<<blocks, 256, smem, s>>>(n, Z, mu, K, tau, deg, S, AS, red, two_e, dZ); break;
+        case 128:
+            cudaFuncSetAttribute(k_softmod_grad<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_softmod_grad<128><<<blocks, 256, smem, s>>>(n, Z, mu, K, tau, deg, S, AS, red, two_e, dZ);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t count, float lr, float b1, float b2,
+                        float eps, int step, cudaStream_t s) {
+    ProfScope ps(s, PF_DIFF, 1);
+    const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
+    int64_t blocks = (count + 255) / 256;
+    if (blocks > (int64_t)num_sms() * 8) blocks = (int64_t)num_sms() * 8;
+    k_adam<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(p, g, m, v, count, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_centroids(int64_t n, int d, const float* Z, const int32_t* labels, int K, long long* sums,
+                             int* counts, float* mu, uint32_t* err, cudaStream_t s) {
+    ProfScope ps(s, PF_DIFF, 2);
+    cudaMemsetAsync(sums, 0, (size_t)K * d * sizeof(long long), s);
+    cudaMemsetAsync(counts, 0, (size_t)K * sizeof(int), s);
+    int64_t blocks = (n * d + 255) / 256;
+    if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
+    k_centroid_sums<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, s>>>(n, d, Z, labels, K, sums, counts, err);
+    k_centroid_means<<<(K * d + 255) / 256, 256, 0, s>>>(K, d, sums, counts, mu);
+    return cudaGetLastError();
+}
+
+}  // namespace raftgp

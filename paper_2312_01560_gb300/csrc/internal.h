@@ -18,7 +18,7 @@ raftgp_status set_error(raftgp_status st, const char* fmt, ...);
 enum ProfFamily {
     PF_DEGREES, PF_THETA, PF_SPMM_PROJ, PF_SPMM_GCN, PF_DENSE_TC, PF_SEED_UPDATE, PF_SEED_PICK, PF_BATCH_INIT, PF_ASSIGN_FFMA,
     PF_ASSIGN_TC, PF_ASSIGN_TC_FIRST, PF_ASSIGN_TC_FINAL, PF_RECHECK, PF_APPLY, PF_APPLY_FIRST, PF_LLOYD_UPDATE, PF_SCORE,
-    PF_SELECT_BEST, PF_OTHER, PF_COUNT
+    PF_SELECT_BEST, PF_DIFF, PF_OTHER, PF_COUNT
 };
 // Brackets the kernels launched in its lifetime with CUDA events when profiling is on.
 class ProfScope {
@@ -130,5 +130,27 @@ void launch_select_best(const CandBatch& b, ScoreOut so, int criterion, BestStat
                         int64_t n, int32_t* out_labels, cudaStream_t s);
 cudaError_t launch_score_labels(const raftgp_csr* g, const int32_t* deg, const int32_t* labels, int K, long long* m,
                                 long long* vol, double* out2, uint32_t* err, cudaStream_t s);
+
+// ---- differentiation form (diff.cu) ----
+cudaError_t launch_rowmm(int64_t n, const float* X, int lin, const float* W, int lout, bool trans, float* Y,
+                         cudaStream_t s);
+// mode: 0 GCN forward, 1 GCN backward (dA), 2 Ahat x, 3 A x
+cudaError_t launch_spmm32(const raftgp_csr* g, int L, const float* rsh, const float* X, const float* G, float* out,
+                          int mode, cudaStream_t s);
+int wgrad_blocks(int64_t n);
+cudaError_t launch_wgrad(int64_t n, const float* H, int lin, const float* dP, int lout, float* partial, float* dW,
+                         cudaStream_t s);
+int softmod_blocks(int64_t n);
+cudaError_t launch_soft_assign(int64_t n, int d, const float* Z, const float* mu, int K, float tau, float* S,
+                               cudaStream_t s);
+cudaError_t launch_softmod_reduce(int64_t n, const int32_t* deg, const float* S, const float* AS, double* partial,
+                                  double* red, cudaStream_t s);
+cudaError_t launch_softmod_grad(int64_t n, int d, const float* Z, const float* mu, int K, float tau, const int32_t* deg,
+                                const float* S, const float* AS, const double* red, double two_e, float* dZ,
+                                cudaStream_t s);
+cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t count, float lr, float b1, float b2,
+                        float eps, int step, cudaStream_t s);
+cudaError_t launch_centroids(int64_t n, int d, const float* Z, const int32_t* labels, int K, long long* sums,
+                             int* counts, float* mu, uint32_t* err, cudaStream_t s);
 
 }  // namespace raftgp
