@@ -38,6 +38,9 @@ WORKLOAD = {
     "op": "mod_full", "dims": (128, 128, 128, 128, 64),
     "kmin": 50, "kmax": 400, "grid": 10, "iters": 50,
 }
+# the differentiation form: GNN weights tuned by Adam against the relaxed modularity
+DIFF_WORKLOAD = {"graph": "dcsbm-200k", "graph_seed": 0, "op": "mod_full", "dims": (128, 128, 64), "kmin": 2,
+                 "kmax": 128, "grid": 10, "tau": 0.1, "lr": 1e-3}
 PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 N_SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
@@ -221,13 +224,68 @@ def reference_candidates(wl):
 
 
 # ----------------------------------------------------------------------------------------
+def bench_diff(args):
+    """Times the Adam steps of the differentiation form (each step: the GNN layers forward,
+    the relaxed modularity with its gradient, the layers backward with recomputation, Adam),
+    and reports the loss and the partition quality before and after tuning."""
+    import torch
+    from inputs.dcsbm import workload
+    from paper_2312_01560_gb300 import api, diff
+    from paper_2312_01560_gb300.metrics import nmi
+    wl = DIFF_WORKLOAD
+    steps = args.steps if args.steps != 5 else 200
+    g = workload(wl["graph"], seed=wl["graph_seed"])
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    dg = api.DeviceGraph.from_host(g, dev)
+    dims = wl["dims"]
+    kw = dict(op=wl["op"], dims=dims, dtype="f32", kmin=wl["kmin"], kmax=wl["kmax"], grid=wl["grid"])
+    lab0, rep0 = api.partition(dg, **kw)
+    Z0, st = api.embed(dg, op=wl["op"], dims=dims, dtype="f32", seed=1, return_stages=True)
+    mu = api.centroids(Z0, lab0, rep0["k"])
+    Y = st[0]
+    Ws = [api.gcn_weights(k, dims[k - 1], dims[k], 1, dev) for k in range(1, len(dims))]
+    diff.tune(dg, Y, Ws, mu, tau=wl["tau"], steps=max(args.warmup, 1), lr=wl["lr"])   # warm-up
+    api.profile_enable(True)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    Wt, losses = diff.tune(dg, Y, Ws, mu, tau=wl["tau"], steps=steps, lr=wl["lr"])
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    prof = api.profile_read()
+    api.profile_enable(False)
+    ms = e0.elapsed_time(e1) / steps
+    lab1, rep1 = api.partition(dg, W=Wt, **kw)
+    l0, l1 = lab0.cpu().numpy(), lab1.cpu().numpy()
+    line = {"metric": "Adam tuning steps/s at 200k nodes (differentiation form)", "value": 1e3 / ms,
+            "unit": "steps/s", "n_gpus": 1, "steps": steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "dcsbm-200k: N=200,000, K=80, Dirichlet(2), exponent 2.5 in [5,500], mean degree "
+                                   "20, 2:1; op=%s, GNN 128-128-64, tau=%g, lr=%g, layers recomputed in the backward"
+                                   % (wl["op"], wl["tau"], wl["lr"]),
+                       "edges": g.n_edges, "nodes": g.n},
+            "loss": {"first": losses[0], "last": losses[-1]},
+            "quality": {"untrained": {"k_best": rep0["k"], "nmi_planted": nmi(l0, g.planted)},
+                        "tuned": {"k_best": rep1["k"], "nmi_planted": nmi(l1, g.planted)}},
+            "clocks": clocks, "gpu_launches": int(sum(v["launches"] for v in prof.values()) / steps),
+            "kernels": {k: {"launches_per_step": v["launches"] / steps, "ms_per_step": v["ms"] / steps}
+                        for k, v in prof.items()}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="bf16", choices=["bf16", "f32"])
+    ap.add_argument("--form", default="bf16", choices=["bf16", "f32", "diff"],
+                    help="bf16/f32: the partition benchmark; diff: Adam tuning steps of the GNN weights "
+                         "(N=200,000, GNN 128-128-64, --steps Adam steps, default 200)")
     ap.add_argument("--assign", default=None, choices=["tc", "tc8", "ffma"],
                     help="k-means engine (default: tc8 for bf16, ffma for f32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -235,6 +293,8 @@ def main():
     ap.add_argument("--no-fp32-check", action="store_true",
                     help="skip the untimed plain-FP32 run that checks the BF16 result's NMI")
     args = ap.parse_args()
+    if args.form == "diff":
+        return bench_diff(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

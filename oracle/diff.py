@@ -65,7 +65,10 @@ def layer_backward(Ah, H, W, T, r, Hout, dHout):
 
 
 def soft_assignment(Z, mu, tau):
-    D = ((Z[:, None, :] - mu[None, :, :]) ** 2).sum(axis=2)
+    # direct-form squared distances, computed in row blocks to bound the temporary
+    D = np.empty((Z.shape[0], mu.shape[0]))
+    for r0 in range(0, Z.shape[0], 2048):
+        D[r0:r0 + 2048] = ((Z[r0:r0 + 2048, None, :] - mu[None, :, :]) ** 2).sum(axis=2)
     logit = -D / tau
     logit -= logit.max(axis=1, keepdims=True)
     E = np.exp(logit)

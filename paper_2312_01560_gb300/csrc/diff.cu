@@ -417,6 +417,7 @@ static int grid_for(int64_t warps_needed) {
 
 template <int LIN, int LOUT, bool TRANS>
 static cudaError_t rowmm_t(int64_t n, const float* X, const float* W, float* Y, cudaStream_t s) {
+    ProfScope ps(s, PF_DIFF_DENSE, 1);
     const size_t smem = (size_t)(LIN * LOUT + 64 * (LIN + 1)) * sizeof(float);
     auto kern = k_rowmm<LIN, LOUT, TRANS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -466,7 +467,7 @@ static cudaError_t spmm32_w(const Csr<OffT>& g, int L, const float* rsh, const f
 
 cudaError_t launch_spmm32(const raftgp_csr* g, int L, const float* rsh, const float* X, const float* G, float* out,
                           int mode, cudaStream_t s) {
-    ProfScope ps(s, PF_DIFF, 1);
+    ProfScope ps(s, mode == 3 ? PF_DIFF_LOSS : PF_DIFF_SPMM, 1);
     if (g->row_ptr_bits == 64) {
         Csr<int64_t> c{g->n, g->nnz, (const int64_t*)g->row_ptr, g->col};
         return spmm32_w(c, L, rsh, X, G, out, mode, s);
@@ -483,7 +484,7 @@ int wgrad_blocks(int64_t n) {
 
 cudaError_t launch_wgrad(int64_t n, const float* H, int lin, const float* dP, int lout, float* partial, float* dW,
                          cudaStream_t s) {
-    ProfScope ps(s, PF_DIFF, 2);
+    ProfScope ps(s, PF_DIFF_DENSE, 2);
     const int blocks = wgrad_blocks(n);
     const int64_t rpb = (n + blocks - 1) / blocks;
     bool done = false;
@@ -508,7 +509,7 @@ int softmod_blocks(int64_t n) {
 
 cudaError_t launch_soft_assign(int64_t n, int d, const float* Z, const float* mu, int K, float tau, float* S,
                                cudaStream_t s) {
-    ProfScope ps(s, PF_DIFF, 1);
+    ProfScope ps(s, PF_DIFF_LOSS, 1);
     const size_t smem = (size_t)K * d * sizeof(float);
     const int blocks = grid_for(n);
     switch (d) {
@@ -525,7 +526,7 @@ cudaError_t launch_soft_assign(int64_t n, int d, const float* Z, const float* mu
 
 cudaError_t launch_softmod_reduce(int64_t n, const int32_t* deg, const float* S, const float* AS, double* partial,
                                   double* red, cudaStream_t s) {
-    ProfScope ps(s, PF_DIFF, 2);
+    ProfScope ps(s, PF_DIFF_LOSS, 2);
     const int blocks = softmod_blocks(n);
     const int64_t rpb = (n + blocks - 1) / blocks;
     k_softmod_partials<<<blocks, 256, 0, s>>>(n, deg, S, AS, rpb, partial);
@@ -536,7 +537,7 @@ cudaError_t launch_softmod_reduce(int64_t n, const int32_t* deg, const float* S,
 cudaError_t launch_softmod_grad(int64_t n, int d, const float* Z, const float* mu, int K, float tau, const int32_t* deg,
                                 const float* S, const float* AS, const double* red, double two_e, float* dZ,
                                 cudaStream_t s) {
-    ProfScope ps(s, PF_DIFF, 1);
+    ProfScope ps(s, PF_DIFF_LOSS, 1);
     const size_t smem = (size_t)(K * d + SK) * sizeof(float);
     const int blocks = grid_for(n);
     switch (d) {

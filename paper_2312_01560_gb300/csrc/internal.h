@@ -18,7 +18,7 @@ raftgp_status set_error(raftgp_status st, const char* fmt, ...);
 enum ProfFamily {
     PF_DEGREES, PF_THETA, PF_SPMM_PROJ, PF_SPMM_GCN, PF_DENSE_TC, PF_SEED_UPDATE, PF_SEED_PICK, PF_BATCH_INIT, PF_ASSIGN_FFMA,
     PF_ASSIGN_TC, PF_ASSIGN_TC_FIRST, PF_ASSIGN_TC_FINAL, PF_RECHECK, PF_APPLY, PF_APPLY_FIRST, PF_LLOYD_UPDATE, PF_SCORE,
-    PF_SELECT_BEST, PF_DIFF, PF_OTHER, PF_COUNT
+    PF_SELECT_BEST, PF_DIFF_SPMM, PF_DIFF_DENSE, PF_DIFF_LOSS, PF_DIFF, PF_OTHER, PF_COUNT
 };
 // Brackets the kernels launched in its lifetime with CUDA events when profiling is on.
 class ProfScope {

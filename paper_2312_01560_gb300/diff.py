@@ -66,7 +66,7 @@ def tune(g, Y, Ws, mu, tau=0.1, steps=200, lr=1e-3, betas=(0.9, 0.999), eps=1e-8
         with torch.no_grad():
             for k, p in enumerate(params):
                 api.adam_step(p.data, p.grad.contiguous(), m[k], v[k], t, lr, betas[0], betas[1], eps)
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
     return [p.detach() for p in params], losses
 
 

@@ -138,3 +138,24 @@ def test_tuned_weights_partition_and_score(cuda):
     k0, k1 = out["untrained"][1]["k"], out["tuned"][1]["k"]
     assert 2 <= k0 <= 16 and 2 <= k1 <= 16
     assert out["losses"][-1] < out["losses"][0]
+
+
+def test_chain_gradient_at_full_size(cuda):
+    # the differentiation form's configuration: N = 200,000, GNN 128-128-64, the untrained
+    # partition's centroids; every weight gradient against the FP64 oracle
+    g = workload("dcsbm-200k")
+    dg = api.DeviceGraph.from_host(g, cuda)
+    dims = (128, 128, 64)
+    Z0, st = api.embed(dg, op="mod_full", dims=dims, dtype="f32", seed=1, return_stages=True)
+    lab, rep = api.partition(dg, op="mod_full", dims=dims, dtype="f32", kmin=2, kmax=128, grid=10)
+    mu = api.centroids(Z0, lab, rep["k"])
+    Ws = [api.gcn_weights(k, dims[k - 1], dims[k], 1, cuda) for k in range(1, len(dims))]
+    params = [W.clone().requires_grad_(True) for W in Ws]
+    loss = diff.SoftModLossFn.apply(diff.chain(dg, st[0], params), mu, dg, 0.1)
+    loss.backward()
+    lo, dWo = odiff.chain_grad(g, _np(st[0]), [_np(W) for W in Ws], _np(mu), 0.1)
+    print(f"N=200k: K*={rep['k']} loss {float(loss.detach()):.6f} (oracle {lo:.6f}); gradient rel. errors "
+          + ", ".join(f"{rel_fro(_np(p.grad), r):.2e}" for p, r in zip(params, dWo)))
+    assert abs(float(loss.detach()) - lo) <= 1e-5 * abs(lo)
+    for p, ref in zip(params, dWo):
+        assert rel_fro(_np(p.grad), ref) <= 1e-4
