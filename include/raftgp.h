@@ -212,6 +212,59 @@ const char* raftgp_last_error(void);
 /* Library version string. */
 const char* raftgp_version(void);
 
+/* ---- Many graphs at once ----
+ * The graphs arrive as one block-diagonal CSR: graph g owns the nodes graph_off[g] ..
+ * graph_off[g+1]-1 (host int64[n_graphs + 1], graph_off[0] = 0, graph_off[n_graphs] = n) and
+ * every column of its rows lies in that range (checked on the device).  Each graph is
+ * partitioned as raftgp_partition would partition it alone with the NCut operator and the
+ * FP32 k-means engine: its own Eq. 5 projection (Philox rows by the node's index inside the
+ * graph), the Eq. 6 layers, k-means++ and Lloyd for the candidates of its own coarse + refined
+ * grid over [kmin, K_max(g)], K_max(g) = min(ceil(kmax_factor * N_g^0.35), 128, N_g), scored
+ * by Eq. 3 / Eq. 1.  The embedding is one pass over the concatenation; the model selection
+ * runs in persistent kernels over per-graph and per-candidate work queues; the whole
+ * pipeline is captured once into a CUDA graph and replayed.  Embedding widths: final d of 32
+ * or 64. */
+typedef struct {
+    int32_t kmin;          /* smallest K (>= 2) */
+    float kmax_factor;     /* K_max(g) = min(ceil(kmax_factor * N_g^0.35), 128, N_g), e.g. 2 */
+    int32_t grid;          /* coarse and refined grid size, 1..10 */
+    int32_t iters;         /* Lloyd pass cap T */
+    int32_t criterion;     /* RAFTGP_CRIT_MOD or RAFTGP_CRIT_NCUT */
+    uint64_t seed;         /* k-means++ seed (the same for every graph) */
+} raftgp_batch_opts;
+
+typedef struct raftgp_batch_plan raftgp_batch_plan;   /* opaque */
+
+size_t raftgp_batch_workspace_size(const raftgp_csr* g, const int64_t* graph_off, int32_t n_graphs,
+                                   const raftgp_embed_opts* eo, const raftgp_batch_opts* bo);
+
+/* Validates the batch (synchronises), runs the autotuner (the Lloyd kernel's threads per CTA
+ * and points per thread, timed on this batch; none of them changes a result) and captures the
+ * whole partition into a CUDA graph.  labels (device int32[n]: each node's block inside its
+ * graph), k_out (device int32[n_graphs]: K*), ws (device workspace) and any caller arrays the
+ * options point at (eo->theta, eo->W) must stay valid for the plan's life.  *plan receives the
+ * plan (NULL on failure). */
+raftgp_status raftgp_batch_plan_create(const raftgp_csr* g, const int64_t* graph_off, int32_t n_graphs,
+                                       const raftgp_embed_opts* eo, const raftgp_batch_opts* bo, int32_t* labels,
+                                       int32_t* k_out, void* ws, size_t ws_bytes, raftgp_stream_t stream,
+                                       raftgp_batch_plan** plan);
+/* Replays the captured partition on `stream` (asynchronous). */
+raftgp_status raftgp_batch_plan_run(raftgp_batch_plan* plan, raftgp_stream_t stream);
+/* Host copies of every graph's candidates (n_graphs x 20 each; slots 0..9 coarse, 10..19
+ * refined; unused slots have k = 0) after a run.  Synchronises. */
+raftgp_status raftgp_batch_plan_candidates(raftgp_batch_plan* plan, int32_t* k, double* mod, double* ncut,
+                                           int32_t* passes);
+/* The autotuner's choice and its measured times (ms of the coarse Lloyd phase) for the six
+ * variants {128, 256, 512 threads} x {1, 2 points per thread}, in that order. */
+raftgp_status raftgp_batch_plan_tuning(const raftgp_batch_plan* plan, int32_t* threads, int32_t* points_per_thread,
+                                       float* ms);
+void raftgp_batch_plan_destroy(raftgp_batch_plan* plan);
+
+/* One-shot: plan, run, synchronise, destroy. */
+raftgp_status raftgp_partition_batched(const raftgp_csr* g, const int64_t* graph_off, int32_t n_graphs,
+                                       const raftgp_embed_opts* eo, const raftgp_batch_opts* bo, int32_t* labels,
+                                       int32_t* k_out, void* ws, size_t ws_bytes, raftgp_stream_t stream);
+
 /* ---- Differentiation form (the paper trains nothing: its GNN stays random, Section III-B;
  * these calls let the Eq. 6 weights be tuned against a relaxed modularity) ----
  * All arrays are device FP32, row-major; widths (lin, lout, d) are 32, 64 or 128; K <= 128.

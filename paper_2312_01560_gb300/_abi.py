@@ -24,7 +24,11 @@ MAX_BATCH_CAND = 64
 EXPORTS = ("raftgp_workspace_size", "raftgp_embed", "raftgp_select", "raftgp_partition", "raftgp_score",
            "raftgp_kmeanspp", "raftgp_kmeanspp_noalloc", "raftgp_lloyd", "raftgp_profile_enable", "raftgp_profile_enable_family", "raftgp_profile_read", "raftgp_last_error",
            "raftgp_version", "raftgp_diff_workspace_size", "raftgp_gcn_layer_forward", "raftgp_gcn_layer_backward",
-           "raftgp_softmod_loss", "raftgp_centroids", "raftgp_gcn_weights", "raftgp_adam_step")
+           "raftgp_softmod_loss", "raftgp_centroids", "raftgp_gcn_weights", "raftgp_adam_step",
+           "raftgp_batch_workspace_size", "raftgp_batch_plan_create", "raftgp_batch_plan_run",
+           "raftgp_batch_plan_candidates", "raftgp_batch_plan_tuning", "raftgp_batch_plan_destroy",
+           "raftgp_partition_batched")
+BATCH_SLOTS = 20
 
 
 class Csr(C.Structure):
@@ -36,6 +40,11 @@ class EmbedOpts(C.Structure):
     _fields_ = [("op", C.c_int32), ("n_layers", C.c_int32), ("dims", C.c_int32 * (MAX_LAYERS + 1)),
                 ("dtype", C.c_int32), ("seed", C.c_uint64), ("theta", C.c_void_p),
                 ("W", C.c_void_p * MAX_LAYERS), ("stage_out", C.c_void_p * (MAX_LAYERS + 1))]
+
+
+class BatchOpts(C.Structure):
+    _fields_ = [("kmin", C.c_int32), ("kmax_factor", C.c_float), ("grid", C.c_int32), ("iters", C.c_int32),
+                ("criterion", C.c_int32), ("seed", C.c_uint64)]
 
 
 class SelectOpts(C.Structure):
@@ -106,6 +115,23 @@ def lib():
         L.raftgp_gcn_weights.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P, P]
         for name in ("raftgp_gcn_layer_forward", "raftgp_gcn_layer_backward", "raftgp_softmod_loss",
                      "raftgp_centroids", "raftgp_gcn_weights", "raftgp_adam_step"):
+            getattr(L, name).restype = C.c_int
+        I64P = C.POINTER(C.c_int64)
+        L.raftgp_batch_workspace_size.restype = C.c_size_t
+        L.raftgp_batch_workspace_size.argtypes = [C.POINTER(Csr), I64P, C.c_int32, C.POINTER(EmbedOpts),
+                                                  C.POINTER(BatchOpts)]
+        L.raftgp_batch_plan_create.argtypes = [C.POINTER(Csr), I64P, C.c_int32, C.POINTER(EmbedOpts),
+                                               C.POINTER(BatchOpts), P, P, P, C.c_size_t, P, C.POINTER(C.c_void_p)]
+        L.raftgp_batch_plan_run.argtypes = [C.c_void_p, P]
+        L.raftgp_batch_plan_candidates.argtypes = [C.c_void_p, P, P, P, P]
+        L.raftgp_batch_plan_tuning.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                               C.POINTER(C.c_float)]
+        L.raftgp_batch_plan_destroy.argtypes = [C.c_void_p]
+        L.raftgp_batch_plan_destroy.restype = None
+        L.raftgp_partition_batched.argtypes = [C.POINTER(Csr), I64P, C.c_int32, C.POINTER(EmbedOpts),
+                                               C.POINTER(BatchOpts), P, P, P, C.c_size_t, P]
+        for name in ("raftgp_batch_plan_create", "raftgp_batch_plan_run", "raftgp_batch_plan_candidates",
+                     "raftgp_batch_plan_tuning", "raftgp_partition_batched"):
             getattr(L, name).restype = C.c_int
         L.raftgp_last_error.restype = C.c_char_p
         L.raftgp_last_error.argtypes = []

@@ -327,3 +327,97 @@ def gcn_weights(layer: int, lin: int, lout: int, seed: int, device, stream=None)
     check(lib().raftgp_gcn_weights(int(layer), int(lin), int(lout), int(seed), C.c_void_p(W.data_ptr()),
                                    _stream(stream)))
     return W
+
+
+# ---- many graphs at once ----
+def concat_graphs(graphs, device, row_ptr_bits=64):
+    """One block-diagonal DeviceGraph of host graphs (row_ptr, col) and the node offsets."""
+    import numpy as np
+    offs = [0]
+    rps, cols = [], []
+    e0 = 0
+    for g in graphs:
+        rp = np.asarray(g.row_ptr, dtype=np.int64)
+        rps.append(rp[:-1] + e0)
+        cols.append(np.asarray(g.col, dtype=np.int64) + offs[-1])
+        e0 += int(rp[-1])
+        offs.append(offs[-1] + g.n)
+    rp = np.concatenate(rps + [np.array([e0], dtype=np.int64)])
+    col = np.concatenate(cols).astype(np.int32)
+    rdt = torch.int64 if row_ptr_bits == 64 else torch.int32
+    dg = DeviceGraph(offs[-1], torch.tensor(rp, dtype=rdt, device=device), torch.tensor(col, device=device))
+    return dg, np.asarray(offs, dtype=np.int64)
+
+
+def batch_opts(kmin=2, kmax_factor=2.0, grid=10, iters=50, criterion="mod", seed=2):
+    o = _abi.BatchOpts()
+    o.kmin, o.kmax_factor, o.grid, o.iters = int(kmin), float(kmax_factor), int(grid), int(iters)
+    o.criterion = _abi.CRIT[criterion] if isinstance(criterion, str) else int(criterion)
+    o.seed = int(seed)
+    return o
+
+
+class BatchPlan:
+    """A captured partition of many graphs (one block-diagonal CSR): run() replays it."""
+
+    def __init__(self, g: DeviceGraph, graph_off, dims=(64, 64, 32), dtype="f32", embed_seed=1, theta=None, W=None,
+                 stream=None, **kw):
+        import numpy as np
+        self.g = g
+        self.off = np.ascontiguousarray(graph_off, dtype=np.int64)
+        self.ng = len(self.off) - 1
+        dev = g.col.device
+        if theta is not None:
+            theta = theta.to(dev, torch.float32).contiguous()
+        if W is not None:
+            W = [w.to(dev, torch.float32).contiguous() for w in W]
+        self._keep = (theta, W)
+        self.eo = embed_opts("ncut", dims, _dtype_code(dtype), embed_seed, theta, W)
+        self.bo = batch_opts(**kw)
+        self.csr = g.csr()
+        offp = self.off.ctypes.data_as(C.POINTER(C.c_int64))
+        nbytes = lib().raftgp_batch_workspace_size(C.byref(self.csr), offp, self.ng, C.byref(self.eo), C.byref(self.bo))
+        if nbytes == 0:
+            raise _abi.RaftgpError(_abi.EINVAL, "invalid batch")
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.labels = torch.empty(g.n, dtype=torch.int32, device=dev)
+        self.k = torch.empty(self.ng, dtype=torch.int32, device=dev)
+        h = C.c_void_p()
+        check(lib().raftgp_batch_plan_create(C.byref(self.csr), offp, self.ng, C.byref(self.eo), C.byref(self.bo),
+                                             C.c_void_p(self.labels.data_ptr()), C.c_void_p(self.k.data_ptr()),
+                                             C.c_void_p(self.ws.data_ptr()), self.ws.numel(), _stream(stream),
+                                             C.byref(h)))
+        self._h = h
+
+    def run(self, stream=None):
+        check(lib().raftgp_batch_plan_run(self._h, _stream(stream)))
+        return self.labels, self.k
+
+    def candidates(self):
+        import numpy as np
+        n = self.ng * _abi.BATCH_SLOTS
+        k = np.zeros(n, dtype=np.int32)
+        mod = np.zeros(n)
+        ncut = np.zeros(n)
+        passes = np.zeros(n, dtype=np.int32)
+        check(lib().raftgp_batch_plan_candidates(self._h, C.c_void_p(k.ctypes.data), C.c_void_p(mod.ctypes.data),
+                                                 C.c_void_p(ncut.ctypes.data), C.c_void_p(passes.ctypes.data)))
+        shp = (self.ng, _abi.BATCH_SLOTS)
+        return k.reshape(shp), mod.reshape(shp), ncut.reshape(shp), passes.reshape(shp)
+
+    def tuning(self):
+        th, pp = C.c_int32(), C.c_int32()
+        ms = (C.c_float * 6)()
+        check(lib().raftgp_batch_plan_tuning(self._h, C.byref(th), C.byref(pp), ms))
+        return {"threads": th.value, "points_per_thread": pp.value, "ms": list(ms)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().raftgp_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

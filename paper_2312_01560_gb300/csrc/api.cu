@@ -3,9 +3,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -109,6 +111,7 @@ struct EmbedWs {
     float* gvec;
     void* bufA;
     void* bufB;
+    const int32_t* local_row;   // many graphs in one CSR: each node's index inside its graph
 };
 
 static int embed_maxw(const raftgp_embed_opts* o) {
@@ -237,7 +240,7 @@ static raftgp_status run_embed(const raftgp_csr* g, const raftgp_embed_opts* o, 
     }
     const bool rank1 = o->op == RAFTGP_OP_MOD_FULL;
     // Theta (prescaled by rs_j for the NCut operator) into bufB
-    launch_theta(n, L, o->dtype, o->seed, o->theta, o->op == RAFTGP_OP_NCUT ? w.rs : nullptr, w.deg, w.bufB,
+    launch_theta(n, L, o->dtype, o->seed, o->theta, o->op == RAFTGP_OP_NCUT ? w.rs : nullptr, w.local_row, w.deg, w.bufB,
                  rank1 ? w.partial : nullptr, w.gvec, s);
     const int agg0 = o->op == RAFTGP_OP_NCUT ? AGG_NCUT_ : (rank1 ? AGG_MOD_FULL_ : AGG_MOD_REDUCED_);
     cudaError_t e;
@@ -842,6 +845,274 @@ raftgp_status raftgp_adam_step(float* param, const float* grad, float* m, float*
     if (step < 1) return fail(RAFTGP_EINVAL, "step counts from 1");
     cudaError_t e = launch_adam(param, grad, m, v, count, lr, beta1, beta2, eps, step, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "adam");
+    return RAFTGP_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------
+// Many graphs at once: plan (validation, autotuning, CUDA-graph capture) and replay
+// ------------------------------------------------------------------------------------
+struct raftgp_batch_plan {
+    raftgp_csr g;
+    raftgp_embed_opts eo;
+    raftgp_batch_opts bo;
+    int ng = 0, d = 0;
+    int64_t total_n = 0;
+    std::vector<int64_t> h_off;
+    std::vector<int32_t> h_kmax, h_seed_off, h_order;
+    EmbedWs ew{};
+    void* Z = nullptr;
+    BatchDev bd{};
+    uint32_t* err = nullptr;
+    int32_t* labels = nullptr;
+    int32_t* k_out = nullptr;
+    int threads = 256, ppt = 1;
+    float tune_ms[6] = {};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;   // the plan's own stream, on which the graph is captured
+};
+
+namespace {
+const int kTuneThreads[3] = {128, 256, 512};
+
+raftgp_status batch_layout(const raftgp_csr* g, const int64_t* off, int ng, const raftgp_embed_opts* eo,
+                           const raftgp_batch_opts* bo, raftgp_batch_plan& p) {
+    raftgp_status st = check_csr(g);
+    if (st) return st;
+    if ((st = check_embed(eo))) return st;
+    if (!off || ng < 1 || !bo) return fail(RAFTGP_EINVAL, "NULL argument or n_graphs < 1");
+    if (eo->op != RAFTGP_OP_NCUT) return fail(RAFTGP_EUNSUPPORTED, "the batched form supports the NCut operator");
+    const int d = eo->dims[eo->n_layers];
+    if (d != 32 && d != 64) return fail(RAFTGP_EUNSUPPORTED, "the batched form needs a final width of 32 or 64");
+    if (bo->kmin < 2) return fail(RAFTGP_EINVAL, "kmin must be >= 2");
+    if (bo->grid < 1 || bo->grid > BATCH_COARSE) return fail(RAFTGP_EINVAL, "grid must be in [1, %d]", BATCH_COARSE);
+    if (bo->iters < 1) return fail(RAFTGP_EINVAL, "iters must be >= 1");
+    if (!(bo->kmax_factor > 0.f)) return fail(RAFTGP_EINVAL, "kmax_factor must be positive");
+    if (off[0] != 0 || off[ng] != g->n) return fail(RAFTGP_EINVAL, "graph_off must run from 0 to n");
+    p.g = *g;
+    p.eo = *eo;
+    p.bo = *bo;
+    p.ng = ng;
+    p.d = d;
+    p.total_n = g->n;
+    p.h_off.assign(off, off + ng + 1);
+    p.h_kmax.resize(ng);
+    p.h_seed_off.resize(ng + 1);
+    p.h_seed_off[0] = 0;
+    for (int i = 0; i < ng; ++i) {
+        const int64_t n = off[i + 1] - off[i];
+        if (n < 2) return fail(RAFTGP_EINVAL, "graph %d has fewer than 2 nodes", i);
+        int64_t km = (int64_t)std::ceil((double)bo->kmax_factor * std::pow((double)n, 0.35));
+        km = std::min<int64_t>(std::min<int64_t>(km, BATCH_KMAX), n);
+        if (km < bo->kmin) return fail(RAFTGP_EINVAL, "graph %d: K_max %lld is below kmin", i, (long long)km);
+        p.h_kmax[i] = (int32_t)km;
+        p.h_seed_off[i + 1] = p.h_seed_off[i] + (int32_t)km;
+    }
+    p.h_order.resize(ng);
+    for (int i = 0; i < ng; ++i) p.h_order[i] = i;
+    std::stable_sort(p.h_order.begin(), p.h_order.end(),
+                     [&](int a, int b) { return off[a + 1] - off[a] > off[b + 1] - off[b]; });
+    return RAFTGP_OK;
+}
+
+void carve_batch(Carver& c, raftgp_batch_plan& p) {
+    const int64_t n = p.total_n;
+    p.ew = carve_embed(c, n, &p.eo);
+    p.Z = c.take<char>((size_t)n * p.d * elem_size(p.eo.dtype));
+    p.err = c.take<uint32_t>(64);
+    BatchDev& b = p.bd;
+    b.ng = p.ng;
+    b.total_n = n;
+    b.node_off = c.take<int64_t>(p.ng + 1);
+    b.kmax = c.take<int32_t>(p.ng);
+    b.seed_off = c.take<int32_t>(p.ng + 1);
+    b.order = c.take<int32_t>(p.ng);
+    b.local_row = c.take<int32_t>(n);
+    b.seeds = c.take<int32_t>(p.h_seed_off.empty() ? 1 : p.h_seed_off.back());
+    b.cand_k = c.take<int32_t>((size_t)p.ng * BATCH_SLOTS);
+    b.n_coarse = c.take<int32_t>(p.ng);
+    b.n_refine = c.take<int32_t>(p.ng);
+    b.cand_mod = c.take<double>((size_t)p.ng * BATCH_SLOTS);
+    b.cand_ncut = c.take<double>((size_t)p.ng * BATCH_SLOTS);
+    b.cand_passes = c.take<int32_t>((size_t)p.ng * BATCH_SLOTS);
+    b.labels = c.take<int16_t>((size_t)BATCH_SLOTS * n);
+    b.D2 = c.take<float>(n);
+    b.chosen = c.take<uint8_t>(n);
+    b.queue = c.take<int>(64);
+    p.ew.local_row = b.local_row;
+}
+
+// everything after validation: embedding, grids, seeding, both Lloyd phases, selection
+raftgp_status batch_enqueue(raftgp_batch_plan& p, cudaStream_t s) {
+    const int zdtype = p.eo.dtype;
+    cudaMemsetAsync(p.bd.cand_k, 0, sizeof(int32_t) * (size_t)p.ng * BATCH_SLOTS, s);
+    launch_batch_prologue(p.bd, p.bo.kmin, p.bo.grid, s);   // work counters, local rows, coarse grids
+    raftgp_status st = run_embed(&p.g, &p.eo, p.Z, p.ew, true, s);
+    if (st) return st;
+    cudaError_t e = launch_batch_seed(p.bd, p.Z, zdtype, p.d, p.bo.seed, s);
+    if (e == cudaSuccess) e = launch_batch_lloyd(p.bd, p.Z, zdtype, p.d, 0, p.bo.iters, &p.g, p.threads, p.ppt, s);
+    if (e != cudaSuccess) return cuda_fail(e, "batched selection");
+    if (p.bo.grid > 1) {
+        launch_batch_refine(p.bd, p.bo.grid, p.bo.criterion, s);
+        e = launch_batch_lloyd(p.bd, p.Z, zdtype, p.d, 1, p.bo.iters, &p.g, p.threads, p.ppt, s);
+        if (e != cudaSuccess) return cuda_fail(e, "batched selection");
+    }
+    launch_batch_select(p.bd, p.bo.criterion, p.labels, p.k_out, s);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "batched selection");
+    return RAFTGP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+size_t raftgp_batch_workspace_size(const raftgp_csr* g, const int64_t* graph_off, int32_t n_graphs,
+                                   const raftgp_embed_opts* eo, const raftgp_batch_opts* bo) {
+    raftgp_batch_plan p;
+    if (batch_layout(g, graph_off, n_graphs, eo, bo, p) != RAFTGP_OK) return 0;
+    Carver c(nullptr);
+    carve_batch(c, p);
+    return c.off + 256;
+}
+
+raftgp_status raftgp_batch_plan_create(const raftgp_csr* g, const int64_t* graph_off, int32_t n_graphs,
+                                       const raftgp_embed_opts* eo, const raftgp_batch_opts* bo, int32_t* labels,
+                                       int32_t* k_out, void* ws, size_t ws_bytes, raftgp_stream_t stream,
+                                       raftgp_batch_plan** plan) {
+    if (!plan) return fail(RAFTGP_EINVAL, "plan is NULL");
+    *plan = nullptr;
+    if (!labels || !k_out || !ws) return fail(RAFTGP_EINVAL, "labels, k_out or workspace is NULL");
+    std::unique_ptr<raftgp_batch_plan> p(new raftgp_batch_plan());
+    raftgp_status st = batch_layout(g, graph_off, n_graphs, eo, bo, *p);
+    if (st) return st;
+    if (ws_bytes < raftgp_batch_workspace_size(g, graph_off, n_graphs, eo, bo))
+        return fail(RAFTGP_ENOMEM, "workspace too small");
+    Carver c(ws);
+    carve_batch(c, *p);
+    p->labels = labels;
+    p->k_out = k_out;
+    cudaStream_t s = (cudaStream_t)stream;
+    BatchDev& b = p->bd;
+    cudaMemcpyAsync((void*)b.node_off, p->h_off.data(), sizeof(int64_t) * (p->ng + 1), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync((void*)b.kmax, p->h_kmax.data(), sizeof(int32_t) * p->ng, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync((void*)b.seed_off, p->h_seed_off.data(), sizeof(int32_t) * (p->ng + 1), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync((void*)b.order, p->h_order.data(), sizeof(int32_t) * p->ng, cudaMemcpyHostToDevice, s);
+    // the graph checks (CSR, block-diagonal), degrees and the heavy-row list, once
+    cudaMemsetAsync(p->ew.err, 0, sizeof(uint32_t), s);
+    launch_degrees(&p->g, p->ew.deg, p->ew.rs, p->ew.rsh, p->ew.err, p->ew.heavy, p->ew.heavy_count, s);
+    launch_batch_check(&p->g, p->ng, b.node_off, p->ew.err, s);
+    if ((st = read_error_word(p->ew.err, s))) return st;
+    // autotuning: the coarse Lloyd phase timed for every variant on this batch (results are
+    // the same for all of them)
+    p->threads = 256;
+    p->ppt = 1;
+    if ((st = batch_enqueue(*p, s))) return st;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = INFINITY;
+    for (int v = 0; v < 6; ++v) {
+        const int th = kTuneThreads[v / 2], pp = 1 + v % 2;
+        cudaMemsetAsync(b.queue + 1, 0, sizeof(int), s);
+        cudaEventRecord(e0, s);
+        cudaError_t e = launch_batch_lloyd(b, p->Z, p->eo.dtype, p->d, 0, p->bo.iters, &p->g, th, pp, s);
+        cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = INFINITY;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        else cudaGetLastError();
+        p->tune_ms[v] = ms;
+        if (ms < best) {
+            best = ms;
+            p->threads = th;
+            p->ppt = pp;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!(best < INFINITY)) return fail(RAFTGP_ECUDA, "no Lloyd variant could run");
+    // capture the whole partition on the plan's own stream (the caller's stream may be the
+    // legacy default stream, which cannot be captured); the graph is launched on any stream
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "plan stream");
+    e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(p->cap);
+        return cuda_fail(e, "begin capture");
+    }
+    st = batch_enqueue(*p, p->cap);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(p->cap, &graph);
+    if (st || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(p->cap);
+        return st ? st : cuda_fail(e, "end capture");
+    }
+    p->graph = graph;
+    e = cudaGraphInstantiate(&p->exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        cudaStreamDestroy(p->cap);
+        return cuda_fail(e, "graph instantiate");
+    }
+    *plan = p.release();
+    return RAFTGP_OK;
+}
+
+raftgp_status raftgp_batch_plan_run(raftgp_batch_plan* plan, raftgp_stream_t stream) {
+    if (!plan || !plan->exec) return fail(RAFTGP_EINVAL, "plan is NULL");
+    cudaError_t e = cudaGraphLaunch(plan->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    return RAFTGP_OK;
+}
+
+raftgp_status raftgp_batch_plan_candidates(raftgp_batch_plan* plan, int32_t* k, double* mod, double* ncut,
+                                           int32_t* passes) {
+    if (!plan) return fail(RAFTGP_EINVAL, "plan is NULL");
+    const size_t cnt = (size_t)plan->ng * BATCH_SLOTS;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && k) e = cudaMemcpy(k, plan->bd.cand_k, cnt * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && mod) e = cudaMemcpy(mod, plan->bd.cand_mod, cnt * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && ncut) e = cudaMemcpy(ncut, plan->bd.cand_ncut, cnt * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && passes)
+        e = cudaMemcpy(passes, plan->bd.cand_passes, cnt * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "candidates");
+    return RAFTGP_OK;
+}
+
+raftgp_status raftgp_batch_plan_tuning(const raftgp_batch_plan* plan, int32_t* threads, int32_t* points_per_thread,
+                                       float* ms) {
+    if (!plan) return fail(RAFTGP_EINVAL, "plan is NULL");
+    if (threads) *threads = plan->threads;
+    if (points_per_thread) *points_per_thread = plan->ppt;
+    if (ms)
+        for (int v = 0; v < 6; ++v) ms[v] = plan->tune_ms[v];
+    return RAFTGP_OK;
+}
+
+void raftgp_batch_plan_destroy(raftgp_batch_plan* plan) {
+    if (!plan) return;
+    if (plan->exec) cudaGraphExecDestroy(plan->exec);
+    if (plan->graph) cudaGraphDestroy(plan->graph);
+    if (plan->cap) cudaStreamDestroy(plan->cap);
+    delete plan;
+}
+
+raftgp_status raftgp_partition_batched(const raftgp_csr* g, const int64_t* graph_off, int32_t n_graphs,
+                                       const raftgp_embed_opts* eo, const raftgp_batch_opts* bo, int32_t* labels,
+                                       int32_t* k_out, void* ws, size_t ws_bytes, raftgp_stream_t stream) {
+    raftgp_batch_plan* plan = nullptr;
+    raftgp_status st = raftgp_batch_plan_create(g, graph_off, n_graphs, eo, bo, labels, k_out, ws, ws_bytes, stream,
+                                                &plan);
+    if (st) return st;
+    st = raftgp_batch_plan_run(plan, stream);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    raftgp_batch_plan_destroy(plan);
+    if (st) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "batched partition");
     return RAFTGP_OK;
 }
 

@@ -65,7 +65,7 @@ __global__ void k_degrees(int64_t n, int64_t nnz, const int32_t* rp32, const int
 // ------------------------------------------------------------------------------------
 template <typename T>
 __global__ void k_theta(int64_t n, int L, uint64_t seed, const float* user_theta, const float* colscale,
-                        const int32_t* deg, T* theta, double* partial) {
+                        const int32_t* deg, T* theta, double* partial, const int32_t* local_row) {
     const int tpr = L / 4;                       // threads per row
     const int slots = blockDim.x / tpr;          // rows per block iteration
     const int q = threadIdx.x % tpr;
@@ -78,7 +78,10 @@ __global__ void k_theta(int64_t n, int L, uint64_t seed, const float* user_theta
 #pragma unroll
             for (int s = 0; s < 4; ++s) g[s] = user_theta[j * L + 4 * q + s];
         } else {
-            const U32x4 x = philox4x32_10((uint32_t)q, (uint32_t)j, (uint32_t)((uint64_t)j >> 32), STREAM_THETA, seed);
+            // the row counter is the node's index inside its own graph when several graphs share
+            // one concatenated CSR
+            const int64_t jr = local_row ? (int64_t)local_row[j] : j;
+            const U32x4 x = philox4x32_10((uint32_t)q, (uint32_t)jr, (uint32_t)((uint64_t)jr >> 32), STREAM_THETA, seed);
             box_muller(x.x, x.y, g[0], g[1]);
             box_muller(x.z, x.w, g[2], g[3]);
 #pragma unroll
@@ -438,7 +441,7 @@ int theta_blocks(int64_t n) {
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
-void launch_theta(int64_t n, int L, int dtype, uint64_t seed, const float* user_theta, const float* colscale,
+void launch_theta(int64_t n, int L, int dtype, uint64_t seed, const float* user_theta, const float* colscale, const int32_t* local_row,
                   const int32_t* deg, void* theta, double* partial, float* gvec, cudaStream_t s) {
     const int threads = 256;
     const int blocks = theta_blocks(n);
@@ -446,9 +449,10 @@ void launch_theta(int64_t n, int L, int dtype, uint64_t seed, const float* user_
     ProfScope ps(s, PF_THETA, partial ? 2 : 1);
     if (dtype == RAFTGP_BF16)
         k_theta<__nv_bfloat16><<<blocks, threads, sm, s>>>(n, L, seed, user_theta, colscale, deg,
-                                                           (__nv_bfloat16*)theta, partial);
+                                                           (__nv_bfloat16*)theta, partial, local_row);
     else
-        k_theta<float><<<blocks, threads, sm, s>>>(n, L, seed, user_theta, colscale, deg, (float*)theta, partial);
+        k_theta<float><<<blocks, threads, sm, s>>>(n, L, seed, user_theta, colscale, deg, (float*)theta, partial,
+                                                   local_row);
     if (partial) k_rank1_finish<<<(L + 127) / 128, 128, 0, s>>>(blocks, L, partial, gvec);
 }
 

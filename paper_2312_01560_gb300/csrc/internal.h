@@ -38,7 +38,7 @@ enum { AGG_NCUT_ = 0, AGG_MOD_FULL_ = 1, AGG_MOD_REDUCED_ = 2, AGG_GCN_ = 3 };
 void launch_degrees(const raftgp_csr* g, int32_t* deg, float* rs, float* rsh, uint32_t* err, int32_t* heavy,
                     int* heavy_count, cudaStream_t s);
 int theta_blocks(int64_t n);
-void launch_theta(int64_t n, int L, int dtype, uint64_t seed, const float* user_theta, const float* colscale,
+void launch_theta(int64_t n, int L, int dtype, uint64_t seed, const float* user_theta, const float* colscale, const int32_t* local_row,
                   const int32_t* deg, void* theta, double* partial, float* gvec, cudaStream_t s);
 void launch_weights(int layer, int lin, int lout, uint64_t seed, float* W, cudaStream_t s);
 cudaError_t launch_layer(int agg, int dtype, const raftgp_csr* g, const int32_t* deg, const float* rowscale,
@@ -152,5 +152,38 @@ cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t co
                         float eps, int step, cudaStream_t s);
 cudaError_t launch_centroids(int64_t n, int d, const float* Z, const int32_t* labels, int K, long long* sums,
                              int* counts, float* mu, uint32_t* err, cudaStream_t s);
+
+// ---- many graphs at once (batched.cu) ----
+constexpr int BATCH_COARSE = 10;   // candidate slots 0..9: the coarse grid
+constexpr int BATCH_SLOTS = 20;    // slots 10..19: the refined grid
+constexpr int BATCH_KMAX = 128;    // largest K of a graph in the batch
+struct BatchDev {
+    int ng;                        // graphs
+    int64_t total_n;               // nodes of all graphs
+    const int64_t* node_off;       // ng + 1
+    const int32_t* kmax;           // ng
+    const int32_t* seed_off;       // ng + 1: each graph's seeds in `seeds`
+    const int32_t* order;          // ng: graphs by decreasing size (work order)
+    int32_t* local_row;            // total_n: index of the node inside its graph
+    int32_t* seeds;                // sum of kmax
+    int32_t* cand_k;               // ng x BATCH_SLOTS
+    int32_t* n_coarse;             // ng
+    int32_t* n_refine;             // ng
+    double* cand_mod;              // ng x BATCH_SLOTS
+    double* cand_ncut;             // ng x BATCH_SLOTS
+    int32_t* cand_passes;          // ng x BATCH_SLOTS
+    int16_t* labels;               // BATCH_SLOTS x total_n
+    float* D2;                     // total_n (seeding)
+    uint8_t* chosen;               // total_n (seeding)
+    int* queue;                    // 4 work counters
+};
+size_t batch_lloyd_smem(int d);
+void launch_batch_prologue(BatchDev b, int kmin, int G, cudaStream_t s);
+cudaError_t launch_batch_seed(BatchDev b, const void* Z, int zdtype, int d, uint64_t seed, cudaStream_t s);
+cudaError_t launch_batch_lloyd(BatchDev b, const void* Z, int zdtype, int d, int phase, int iters, const raftgp_csr* g,
+                               int threads, int ppt, cudaStream_t s);
+void launch_batch_refine(BatchDev b, int G, int criterion, cudaStream_t s);
+void launch_batch_select(BatchDev b, int criterion, int32_t* labels_out, int32_t* k_out, cudaStream_t s);
+void launch_batch_check(const raftgp_csr* g, int ng, const int64_t* node_off, uint32_t* err, cudaStream_t s);
 
 }  // namespace raftgp

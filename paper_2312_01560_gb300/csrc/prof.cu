@@ -38,6 +38,9 @@ static constexpr size_t kPairs = 1 << 15;
 ProfScope::ProfScope(cudaStream_t s, int fam, int kernels) : s_(s), fam_(fam), kernels_(kernels), pair_(-1) {
     Profiler& p = prof();
     if (!p.on || !((p.mask >> fam) & 1ull)) return;
+    // no events inside a stream capture (a captured graph is replayed without the profiler)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     std::lock_guard<std::mutex> g(p.mu);
     p.launches[fam] += kernels;
     if (p.used >= kPairs) {

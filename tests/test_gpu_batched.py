@@ -1,0 +1,109 @@
+"""Many graphs at once: a batch of uneven graphs partitioned by one captured plan gives every
+graph exactly the result of partitioning it alone (NCut operator, FP32 engine, same seeds and
+grid), and agrees with the FP64 oracle's partition; replays are deterministic; malformed
+batches are rejected before any work."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from inputs.dcsbm import batch_workload, dcsbm
+from paper_2312_01560_gb300 import api
+from paper_2312_01560_gb300.metrics import nmi
+
+pytestmark = pytest.mark.gpu
+
+DIMS = (64, 64, 32)
+
+
+def _kmax(n, factor=2.0):
+    return min(int(math.ceil(factor * n ** 0.35)), 128, n)
+
+
+@pytest.fixture(scope="module")
+def batch():
+    return batch_workload(n_graphs=12, seed=17, n_lo=1000, n_hi=6000)
+
+
+def test_batched_equals_single_graph_partitions(cuda, batch):
+    dg, off = api.concat_graphs(batch, cuda)
+    plan = api.BatchPlan(dg, off, dims=DIMS, dtype="f32", kmin=2, grid=10, iters=50, seed=2)
+    labels, ks = plan.run()
+    torch.cuda.synchronize()
+    labels, ks = labels.cpu().numpy(), ks.cpu().numpy()
+    ck, cmod, cncut, cpass = plan.candidates()
+    for gi, g in enumerate(batch):
+        one = api.DeviceGraph.from_host(g, cuda)
+        lab1, rep1 = api.partition(one, op="ncut", dims=DIMS, dtype="f32", kmin=2, kmax=_kmax(g.n), grid=10,
+                                   iters=50, assign="ffma", select_seed=2)
+        assert ks[gi] == rep1["k"], gi
+        assert np.array_equal(labels[off[gi]:off[gi + 1]], lab1.cpu().numpy()), gi
+        mine = sorted((int(k), m, c, int(p)) for k, m, c, p in zip(ck[gi], cmod[gi], cncut[gi], cpass[gi]) if k > 0)
+        theirs = sorted((int(c[0]), c[1], c[2], int(c[3])) for c in rep1["cands"])
+        assert mine == theirs, gi
+    plan.close()
+
+
+def test_batched_agrees_with_oracle(cuda):
+    # strongly planted graphs of uneven size, where the FP64 oracle's partition is a stable
+    # target (on weakly planted graphs FP32 and FP64 Lloyd runs settle in different optima; the
+    # batched result there equals the single-graph FP32 result, checked above)
+    sub = [dcsbm(n, k, alpha=5.0, gamma=2.5, dmin=8, dmax=60, mean_degree=24, ratio=12.0, seed=30 + i)
+           for i, (n, k) in enumerate([(1500, 6), (3000, 9), (2200, 7)])]
+    dg, off = api.concat_graphs(sub, cuda)
+    plan = api.BatchPlan(dg, off, dims=DIMS, dtype="f32", kmin=2, grid=10, iters=50, seed=2)
+    labels, ks = plan.run()
+    torch.cuda.synchronize()
+    labels, ks = labels.cpu().numpy(), ks.cpu().numpy()
+    for gi, g in enumerate(sub):
+        ref = oracle.partition(g, "ncut", DIMS, kmin=2, kmax=_kmax(g.n), grid=10)
+        lab = labels[off[gi]:off[gi + 1]]
+        a = nmi(lab, ref["labels"])
+        print(f"graph {gi} (N={g.n}): K* {ks[gi]} (oracle {ref['k']}), NMI vs oracle {a:.4f}, "
+              f"vs planted {nmi(lab, g.planted):.4f}")
+        assert ks[gi] == ref["k"]
+        assert a >= 0.99
+    plan.close()
+
+
+def test_replay_is_deterministic_and_tuned(cuda, batch):
+    dg, off = api.concat_graphs(batch[:6], cuda)
+    plan = api.BatchPlan(dg, off, dims=DIMS, dtype="f32", kmin=2, grid=10, iters=50, seed=2)
+    a = [t.clone() for t in plan.run()]
+    b = [t.clone() for t in plan.run()]
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    t = plan.tuning()
+    assert t["threads"] in (128, 256, 512) and t["points_per_thread"] in (1, 2)
+    assert all(m > 0 for m in t["ms"])
+    plan.close()
+
+
+def test_bf16_batch_runs(cuda, batch):
+    dg, off = api.concat_graphs(batch[:4], cuda)
+    plan = api.BatchPlan(dg, off, dims=DIMS, dtype="bf16", kmin=2, grid=10, iters=50, seed=2)
+    labels, ks = plan.run()
+    torch.cuda.synchronize()
+    ks = ks.cpu().numpy()
+    for gi, g in enumerate(batch[:4]):
+        assert 2 <= ks[gi] <= _kmax(g.n)
+        lab = labels[off[gi]:off[gi + 1]].cpu().numpy()
+        assert lab.min() >= 0 and lab.max() < ks[gi]
+    plan.close()
+
+
+def test_cross_graph_edge_is_rejected(cuda, batch):
+    dg, off = api.concat_graphs(batch[:2], cuda)
+    col = dg.col.clone()
+    col[0] = int(off[1])           # a column of graph 0's first row pointing into graph 1
+    bad = api.DeviceGraph(dg.n, dg.row_ptr, col)
+    with pytest.raises(api._abi.RaftgpError, match="malformed"):
+        api.BatchPlan(bad, off, dims=DIMS, dtype="f32")
+
+
+def test_bad_offsets_are_rejected(cuda, batch):
+    dg, off = api.concat_graphs(batch[:2], cuda)
+    with pytest.raises(api._abi.RaftgpError):
+        api.BatchPlan(dg, off[:-1], dims=DIMS, dtype="f32")
