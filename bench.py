@@ -41,6 +41,9 @@ WORKLOAD = {
 # the differentiation form: GNN weights tuned by Adam against the relaxed modularity
 DIFF_WORKLOAD = {"graph": "dcsbm-200k", "graph_seed": 0, "op": "mod_full", "dims": (128, 128, 64), "kmin": 2,
                  "kmax": 128, "grid": 10, "tau": 0.1, "lr": 1e-3}
+# the batched form: 512 independent graphs of uneven size in one captured plan
+BATCH_WORKLOAD = {"n_graphs": 512, "seed": 4000, "n_lo": 1000, "n_hi": 50000, "dims": (128, 128, 64), "dtype": "f32",
+                  "kmin": 2, "kmax_factor": 2.0, "grid": 10, "iters": 50}
 PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 N_SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
@@ -224,6 +227,76 @@ def reference_candidates(wl):
 
 
 # ----------------------------------------------------------------------------------------
+def _one_graph(args):
+    from inputs.dcsbm import dcsbm
+    return dcsbm(*args[0], **args[1])
+
+
+def bench_batched(args):
+    """Times replays of one captured plan that partitions 512 DC-SBM graphs of uneven size
+    (N log-uniform in [1,000, 50,000], K = round(N^0.35), exponent 2.5, mean degree uniform in
+    [10, 30], ratio uniform in [2, 6]); each graph runs its own coarse + refined model
+    selection over [2, ceil(2 N^0.35)].  Plan creation (validation, autotuning, capture) is
+    not timed."""
+    import multiprocessing as mp
+    wl = BATCH_WORKLOAD
+    # the generator's recipe, drawn in worker processes started before any GPU call
+    rng = np.random.Generator(np.random.PCG64(wl["seed"]))
+    jobs = []
+    for gi in range(wl["n_graphs"]):
+        n = int(round(np.exp(rng.uniform(np.log(wl["n_lo"]), np.log(wl["n_hi"])))))
+        k = max(2, int(round(n ** 0.35)))
+        md = float(rng.uniform(10, 30))
+        ratio = float(rng.uniform(2, 6))
+        jobs.append(((n, k), dict(alpha=2.0, gamma=2.5, dmin=5, dmax=min(500.0, n / 4), mean_degree=md, ratio=ratio,
+                                  seed=wl["seed"] * 1000 + gi)))
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        graphs = pool.map(_one_graph, jobs)
+    import torch
+    from paper_2312_01560_gb300 import api
+    from paper_2312_01560_gb300.metrics import nmi
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    dg, off = api.concat_graphs(graphs, dev)
+    edges = sum(g.n_edges for g in graphs)
+    t0 = time.perf_counter()
+    plan = api.BatchPlan(dg, off, dims=wl["dims"], dtype=wl["dtype"], kmin=wl["kmin"], kmax_factor=wl["kmax_factor"],
+                         grid=wl["grid"], iters=wl["iters"], seed=2)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    for _ in range(max(args.warmup, 1)):
+        plan.run()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        labels, ks = plan.run()
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    lab = labels.cpu().numpy()
+    ks = ks.cpu().numpy()
+    nmis = [nmi(lab[off[i]:off[i + 1]], g.planted) for i, g in enumerate(graphs)]
+    kdiff = [int(ks[i]) - g.k_planted for i, g in enumerate(graphs)]
+    line = {"metric": "batched partition of 512 uneven DC-SBM graphs: edges/s", "value": edges / (ms * 1e-3),
+            "unit": "edges/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": wl["dtype"], "data": "synthetic",
+            "config": {"workload": "512 DC-SBM graphs, N log-uniform in [1000, 50000], K = round(N^0.35), exponent "
+                                   "2.5, mean degree U[10, 30], ratio U[2, 6]; NCut operator, GNN 128-128-64, "
+                                   "K in [2, ceil(2 N^0.35)] (10 coarse + 10 refined), <=50 Lloyd passes; "
+                                   "one captured plan",
+                       "graphs": len(graphs), "nodes": int(off[-1]), "edges": edges},
+            "graphs_per_s": len(graphs) / (ms * 1e-3), "plan_create_s": plan_s, "tuning": plan.tuning(),
+            "quality": {"nmi_planted_mean": float(np.mean(nmis)), "nmi_planted_min": float(np.min(nmis)),
+                        "k_minus_planted_mean": float(np.mean(kdiff))},
+            "clocks": clocks}
+    plan.close()
+    print(json.dumps(line), flush=True)
+
+
 def bench_diff(args):
     """Times the Adam steps of the differentiation form (each step: the GNN layers forward,
     the relaxed modularity with its gradient, the layers backward with recomputation, Adam),
@@ -283,9 +356,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="bf16", choices=["bf16", "f32", "diff"],
+    ap.add_argument("--form", default="bf16", choices=["bf16", "f32", "diff", "batched"],
                     help="bf16/f32: the partition benchmark; diff: Adam tuning steps of the GNN weights "
-                         "(N=200,000, GNN 128-128-64, --steps Adam steps, default 200)")
+                         "(N=200,000, GNN 128-128-64, --steps Adam steps, default 200); batched: 512 uneven graphs "
+                         "partitioned by one captured plan (--steps replays)")
     ap.add_argument("--assign", default=None, choices=["tc", "tc8", "ffma"],
                     help="k-means engine (default: tc8 for bf16, ffma for f32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -295,6 +369,8 @@ def main():
     args = ap.parse_args()
     if args.form == "diff":
         return bench_diff(args)
+    if args.form == "batched":
+        return bench_batched(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
