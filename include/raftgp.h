@@ -212,6 +212,28 @@ const char* raftgp_last_error(void);
 /* Library version string. */
 const char* raftgp_version(void);
 
+/* ---- Algorithm 1: recursive bisection by local modularity ----
+ * Partition(U): LMod(U; G) with U as one block (Definition 5, Eq. 7); K=2 k-means on U's
+ * embeddings; LMod(U1, U2; G); U is a block if |U1| <= eps or |U2| <= eps or LMod(U) >
+ * LMod(U1, U2) (compared exactly), otherwise U1 and U2 are partitioned.  `reading` chooses
+ * e in Eq. 7: 0 = the G-degree sum of U over 2 (Definition 5 as printed), 1 = |E| of the
+ * whole graph (a split is taken exactly when it raises the graph's modularity).  k-means++
+ * draws Philox(seed; t, id_lo, id_hi, "Kmpp") with id the set's node in the recursion tree
+ * (root 1, children 2 id, 2 id + 1); Lloyd as the FP32 engine, at most `iters` passes.  All
+ * sets of one depth run together; the host reads the set count once per depth.  labels
+ * (device int32[n]): blocks numbered by increasing smallest node; *k_out (host): the block
+ * count.  Z: device N x d (32, 64 or 128), z_dtype F32 or BF16. */
+typedef struct {
+    int32_t eps;        /* size threshold, 5 in the paper */
+    int32_t iters;      /* Lloyd pass cap */
+    int32_t reading;    /* 0 literal, 1 global (see above) */
+    uint64_t seed;
+} raftgp_bisect_opts;
+size_t raftgp_bisect_workspace_size(int64_t n, int32_t d, int32_t eps);
+raftgp_status raftgp_select_bisect(const raftgp_csr* g, const void* Z, int32_t d, int32_t z_dtype,
+                                   const raftgp_bisect_opts* o, int32_t* labels, int32_t* k_out, void* ws,
+                                   size_t ws_bytes, raftgp_stream_t stream);
+
 /* ---- Many graphs at once ----
  * The graphs arrive as one block-diagonal CSR: graph g owns the nodes graph_off[g] ..
  * graph_off[g+1]-1 (host int64[n_graphs + 1], graph_off[0] = 0, graph_off[n_graphs] = n) and

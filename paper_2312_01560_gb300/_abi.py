@@ -27,7 +27,7 @@ EXPORTS = ("raftgp_workspace_size", "raftgp_embed", "raftgp_select", "raftgp_par
            "raftgp_softmod_loss", "raftgp_centroids", "raftgp_gcn_weights", "raftgp_adam_step",
            "raftgp_batch_workspace_size", "raftgp_batch_plan_create", "raftgp_batch_plan_run",
            "raftgp_batch_plan_candidates", "raftgp_batch_plan_tuning", "raftgp_batch_plan_destroy",
-           "raftgp_partition_batched")
+           "raftgp_partition_batched", "raftgp_bisect_workspace_size", "raftgp_select_bisect")
 BATCH_SLOTS = 20
 
 
@@ -40,6 +40,10 @@ class EmbedOpts(C.Structure):
     _fields_ = [("op", C.c_int32), ("n_layers", C.c_int32), ("dims", C.c_int32 * (MAX_LAYERS + 1)),
                 ("dtype", C.c_int32), ("seed", C.c_uint64), ("theta", C.c_void_p),
                 ("W", C.c_void_p * MAX_LAYERS), ("stage_out", C.c_void_p * (MAX_LAYERS + 1))]
+
+
+class BisectOpts(C.Structure):
+    _fields_ = [("eps", C.c_int32), ("iters", C.c_int32), ("reading", C.c_int32), ("seed", C.c_uint64)]
 
 
 class BatchOpts(C.Structure):
@@ -133,6 +137,11 @@ def lib():
         for name in ("raftgp_batch_plan_create", "raftgp_batch_plan_run", "raftgp_batch_plan_candidates",
                      "raftgp_batch_plan_tuning", "raftgp_partition_batched"):
             getattr(L, name).restype = C.c_int
+        L.raftgp_bisect_workspace_size.restype = C.c_size_t
+        L.raftgp_bisect_workspace_size.argtypes = [C.c_int64, C.c_int32, C.c_int32]
+        L.raftgp_select_bisect.restype = C.c_int
+        L.raftgp_select_bisect.argtypes = [C.POINTER(Csr), P, C.c_int32, C.c_int32, C.POINTER(BisectOpts), P,
+                                           C.POINTER(C.c_int32), P, C.c_size_t, P]
         L.raftgp_last_error.restype = C.c_char_p
         L.raftgp_last_error.argtypes = []
         L.raftgp_version.restype = C.c_char_p

@@ -421,3 +421,25 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+# ---- Algorithm 1 ----
+READING = {"literal": 0, "global": 1}
+
+
+def select_bisect(g: DeviceGraph, Z: torch.Tensor, eps=5, iters=50, reading="literal", seed=2, stream=None):
+    """Algorithm 1 (recursive bisection by local modularity): returns (labels int32[N], K)."""
+    n, d = Z.shape
+    code = 1 if Z.dtype == torch.bfloat16 else 0
+    o = _abi.BisectOpts()
+    o.eps, o.iters, o.seed = int(eps), int(iters), int(seed)
+    o.reading = READING[reading] if isinstance(reading, str) else int(reading)
+    Zc = Z.contiguous()
+    labels = torch.empty(n, dtype=torch.int32, device=Z.device)
+    ws = _workspace(int(lib().raftgp_bisect_workspace_size(n, d, int(eps))), Z.device)
+    k = C.c_int32(0)
+    csr = g.csr()
+    check(lib().raftgp_select_bisect(C.byref(csr), C.c_void_p(Zc.data_ptr()), d, code, C.byref(o),
+                                     C.c_void_p(labels.data_ptr()), C.byref(k), C.c_void_p(ws.data_ptr()),
+                                     ws.numel(), _stream(stream)))
+    return labels, k.value

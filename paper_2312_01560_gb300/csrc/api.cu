@@ -1117,3 +1117,96 @@ raftgp_status raftgp_partition_batched(const raftgp_csr* g, const int64_t* graph
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------
+// Algorithm 1
+// ------------------------------------------------------------------------------------
+namespace {
+BisectDev carve_bisect(Carver& c, int64_t n, int d, int eps) {
+    BisectDev b{};
+    b.eps = eps;
+    const int64_t cap = n / (eps + 1) + 2;
+    b.cap_sets = (int)cap;
+    b.perm = c.take<int32_t>(n);
+    b.perm_next = c.take<int32_t>(n);
+    b.pos_set = c.take<int32_t>(n);
+    b.lab = c.take<int8_t>(n);
+    b.q = c.take<unsigned long long>(n);
+    b.P = c.take<unsigned long long>(n);
+    b.F = c.take<unsigned long long>(n);
+    b.tiles = c.take<unsigned long long>(n / 4096 + 64);
+    b.node_set = c.take<int32_t>(n);
+    b.node_lab = c.take<int32_t>(n);
+    b.block_of = c.take<int32_t>(n);
+    b.set_off = c.take<int64_t>(cap);
+    b.set_n = c.take<int64_t>(cap);
+    b.nset_off = c.take<int64_t>(cap);
+    b.nset_n = c.take<int64_t>(cap);
+    b.set_id = c.take<uint64_t>(cap);
+    b.nset_id = c.take<uint64_t>(cap);
+    b.s0 = c.take<int64_t>(cap);
+    b.child_pos = c.take<int64_t>(cap);
+    b.active = c.take<int32_t>(cap);
+    b.changed = c.take<int32_t>(2 * cap);
+    b.counts = c.take<int32_t>(2 * cap);
+    b.split = c.take<int32_t>(cap);
+    b.block_id = c.take<int32_t>(cap);
+    b.mu = c.take<float>((size_t)cap * 2 * d);
+    b.norm2 = c.take<float>(2 * cap);
+    b.sums = c.take<long long>((size_t)cap * 2 * d);
+    b.acc = c.take<unsigned long long>(5 * cap);
+    b.scan_in = c.take<unsigned long long>(3 * cap);
+    b.scan_out = c.take<unsigned long long>(3 * cap);
+    b.bmin = c.take<int32_t>(n);
+    b.counters = c.take<int>(64);
+    b.counters_ll = c.take<long long>(8);
+    return b;
+}
+
+__global__ void k_iota(int32_t* p, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = (int32_t)i;
+}
+}  // namespace
+
+extern "C" {
+
+size_t raftgp_bisect_workspace_size(int64_t n, int32_t d, int32_t eps) {
+    Carver c(nullptr);
+    c.take<uint32_t>(64);
+    c.take<int32_t>(n);
+    c.take<float>(n);
+    c.take<float>(n);
+    carve_bisect(c, n, d, eps < 1 ? 1 : eps);
+    return c.off + 256;
+}
+
+raftgp_status raftgp_select_bisect(const raftgp_csr* g, const void* Z, int32_t d, int32_t z_dtype,
+                                   const raftgp_bisect_opts* o, int32_t* labels, int32_t* k_out, void* ws,
+                                   size_t ws_bytes, raftgp_stream_t stream) {
+    raftgp_status st = check_csr(g);
+    if (st) return st;
+    if (!Z || !o || !labels || !k_out || !ws) return fail(RAFTGP_EINVAL, "NULL argument");
+    if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d must be 32, 64 or 128");
+    if (z_dtype != RAFTGP_F32 && z_dtype != RAFTGP_BF16) return fail(RAFTGP_EINVAL, "unknown z_dtype");
+    if (o->eps < 1) return fail(RAFTGP_EINVAL, "eps must be >= 1");
+    if (o->iters < 1) return fail(RAFTGP_EINVAL, "iters must be >= 1");
+    if (o->reading != 0 && o->reading != 1) return fail(RAFTGP_EINVAL, "reading must be 0 or 1");
+    if (ws_bytes < raftgp_bisect_workspace_size(g->n, d, o->eps)) return fail(RAFTGP_ENOMEM, "workspace too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    Carver c(ws);
+    uint32_t* err = c.take<uint32_t>(64);
+    int32_t* deg = c.take<int32_t>(g->n);
+    float* rs = c.take<float>(g->n);
+    float* rsh = c.take<float>(g->n);
+    BisectDev b = carve_bisect(c, g->n, d, o->eps);
+    cudaMemsetAsync(err, 0, sizeof(uint32_t), s);
+    launch_degrees(g, deg, rs, rsh, err, nullptr, nullptr, s);
+    if ((st = read_error_word(err, s))) return st;
+    k_iota<<<(unsigned)std::min<int64_t>((g->n + 255) / 256, 4096), 256, 0, s>>>(b.perm, g->n);
+    cudaError_t e = launch_bisect(g, Z, z_dtype, d, b, o->iters, o->seed, o->reading, labels, k_out, s);
+    if (e != cudaSuccess) return cuda_fail(e, "bisect");
+    return RAFTGP_OK;
+}
+
+}  // extern "C"

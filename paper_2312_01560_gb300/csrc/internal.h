@@ -186,4 +186,28 @@ void launch_batch_refine(BatchDev b, int G, int criterion, cudaStream_t s);
 void launch_batch_select(BatchDev b, int criterion, int32_t* labels_out, int32_t* k_out, cudaStream_t s);
 void launch_batch_check(const raftgp_csr* g, int ng, const int64_t* node_off, uint32_t* err, cudaStream_t s);
 
+// ---- Algorithm 1, recursive bisection (bisect.cu) ----
+struct BisectDev {
+    int eps, depth, cap_sets;
+    // per position (current level)
+    int32_t *perm, *perm_next, *pos_set;
+    int8_t* lab;
+    unsigned long long *q, *P, *F, *tiles;
+    // per node
+    int32_t *node_set, *node_lab, *block_of;
+    // per set (current / next level)
+    int64_t *set_off, *set_n, *nset_off, *nset_n;
+    uint64_t *set_id, *nset_id;
+    int64_t *s0, *child_pos;
+    int32_t *active, *changed, *counts, *split, *block_id;
+    float *mu, *norm2;
+    long long* sums;
+    unsigned long long *acc, *scan_in, *scan_out;
+    int32_t* bmin;
+    int* counters;
+    long long* counters_ll;
+};
+cudaError_t launch_bisect(const raftgp_csr* g, const void* Z, int zdtype, int d, BisectDev b, int iters, uint64_t seed,
+                          int reading, int32_t* labels, int32_t* k_out, cudaStream_t s);
+
 }  // namespace raftgp
