@@ -232,6 +232,46 @@ def _one_graph(args):
     return dcsbm(*args[0], **args[1])
 
 
+def bench_bisect(args):
+    """The 1M-node partition with Algorithm 1 as the model selection (global reading of e):
+    one step = the BF16 embedding + the level-synchronous recursive bisection."""
+    import torch
+    from inputs.dcsbm import workload
+    from paper_2312_01560_gb300 import api
+    from paper_2312_01560_gb300.metrics import nmi
+    wl = WORKLOAD
+    g = workload(wl["graph"], seed=wl["graph_seed"])
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    dg = api.DeviceGraph.from_host(g, dev, row_ptr_bits=64)
+
+    def step():
+        Z = api.embed(dg, op=wl["op"], dims=wl["dims"], dtype="bf16", seed=1)
+        return api.select_bisect(dg, Z, reading="global", seed=2)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        lab, K = step()
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    clocks = sampler.stop()
+    line = {"metric": "end-to-end edges/s at 1M nodes, Algorithm 1 model selection", "value": g.n_edges / (ms * 1e-3),
+            "unit": "edges/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "dcsbm-1m (as the default benchmark); BF16 embedding; recursive bisection with "
+                                   "eps = 5, <= 50 Lloyd passes per split, global reading of e",
+                       "timing": "host clock around synchronised steps (the bisection reads the set count once "
+                                 "per depth)"},
+            "quality": {"k": K, "k_planted": g.k_planted, "nmi_planted": nmi(lab.cpu().numpy(), g.planted)},
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def bench_batched(args):
     """Times replays of one captured plan that partitions 512 DC-SBM graphs of uneven size
     (N log-uniform in [1,000, 50,000], K = round(N^0.35), exponent 2.5, mean degree uniform in
@@ -356,10 +396,11 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="bf16", choices=["bf16", "f32", "diff", "batched"],
+    ap.add_argument("--form", default="bf16", choices=["bf16", "f32", "diff", "batched", "bisect"],
                     help="bf16/f32: the partition benchmark; diff: Adam tuning steps of the GNN weights "
                          "(N=200,000, GNN 128-128-64, --steps Adam steps, default 200); batched: 512 uneven graphs "
-                         "partitioned by one captured plan (--steps replays)")
+                         "partitioned by one captured plan (--steps replays); bisect: the 1M-node partition "
+                         "with Algorithm 1 (recursive bisection by local modularity) as the model selection")
     ap.add_argument("--assign", default=None, choices=["tc", "tc8", "ffma"],
                     help="k-means engine (default: tc8 for bf16, ffma for f32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -371,6 +412,8 @@ def main():
         return bench_diff(args)
     if args.form == "batched":
         return bench_batched(args)
+    if args.form == "bisect":
+        return bench_bisect(args)
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
