@@ -99,6 +99,12 @@ struct Vec<float> {
     }
     __device__ __forceinline__ static float to_float(float v) { return v; }
     __device__ __forceinline__ static float from_float(float v) { return v; }
+    // 16 raw bytes, kept packed until they are added (4 registers per gather in flight)
+    __device__ __forceinline__ static uint4 load_raw(const float* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
+    __device__ __forceinline__ static void unpack(const uint4& v, float* out) {
+        out[0] = __uint_as_float(v.x); out[1] = __uint_as_float(v.y);
+        out[2] = __uint_as_float(v.z); out[3] = __uint_as_float(v.w);
+    }
 };
 template <>
 struct Vec<__nv_bfloat16> {
@@ -123,6 +129,17 @@ struct Vec<__nv_bfloat16> {
     }
     __device__ __forceinline__ static float to_float(__nv_bfloat16 v) { return __bfloat162float(v); }
     __device__ __forceinline__ static __nv_bfloat16 from_float(float v) { return __float2bfloat16_rn(v); }
+    __device__ __forceinline__ static uint4 load_raw(const __nv_bfloat16* p) {
+        return __ldg(reinterpret_cast<const uint4*>(p));
+    }
+    __device__ __forceinline__ static void unpack(const uint4& v, float* out) {
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            out[2 * i] = __uint_as_float(w[i] << 16);
+            out[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+        }
+    }
 };
 
 __device__ __forceinline__ float load_elem(const float* p, int64_t i) { return __ldg(p + i); }

@@ -174,9 +174,60 @@ struct Lanes {
     static constexpr int E = Vec<T>::E;   // elements per lane chunk (16 bytes)
     static constexpr int LPR = LIN / E;   // lanes per gathered row
     static constexpr int GPW = 32 / LPR;  // rows gathered concurrently per warp
-    static constexpr int U = 4;           // unrolled gathers per lane
+    static constexpr int U = 8;           // unrolled gathers per lane
     static_assert(LPR >= 1 && LPR <= 32 && (32 % LPR) == 0, "bad width");
 };
+
+// Issues this lane's U gathers of chunk positions t + u GPW + grp (column indices held one per
+// lane in my_col, cnt of them valid); rows are kept as raw 16-byte words until added.
+template <int AGG, typename T, int LIN>
+__device__ __forceinline__ void gather_issue(const T* __restrict__ X, int32_t my_col, float my_d, int cnt, int t,
+                                             int grp, int sub, uint4 (&r)[Lanes<T, LIN>::U],
+                                             float (&dj)[Lanes<T, LIN>::U]) {
+    using Ln = Lanes<T, LIN>;
+#pragma unroll
+    for (int u = 0; u < Ln::U; ++u) {
+        const int idx = t + u * Ln::GPW + grp;
+        const int src = idx < cnt ? idx : 0;
+        const int32_t j = __shfl_sync(0xffffffffu, my_col, src);
+        if constexpr (AGG == AGG_MOD_REDUCED) dj[u] = __shfl_sync(0xffffffffu, my_d, src);
+        if (idx < cnt) {
+            r[u] = Vec<T>::load_raw(X + (int64_t)j * LIN + sub * Ln::E);
+        } else {
+            r[u] = make_uint4(0u, 0u, 0u, 0u);
+            dj[u] = 0.f;
+        }
+    }
+}
+
+template <int AGG, typename T, int LIN>
+__device__ __forceinline__ void gather_add(const uint4 (&r)[Lanes<T, LIN>::U], const float (&dj)[Lanes<T, LIN>::U],
+                                           float* acc, float* accd) {
+    using Ln = Lanes<T, LIN>;
+#pragma unroll
+    for (int u = 0; u < Ln::U; ++u) {
+        float v[Ln::E];
+        Vec<T>::unpack(r[u], v);
+#pragma unroll
+        for (int e = 0; e < Ln::E; ++e) {
+            acc[e] += v[e];
+            if constexpr (AGG == AGG_MOD_REDUCED) accd[e] += dj[u] * v[e];
+        }
+    }
+}
+
+// Gathers chunk positions [t0, cnt) of one chunk of at most 32 neighbours.
+template <int AGG, typename T, int LIN>
+__device__ __forceinline__ void gather_chunk(const T* __restrict__ X, int32_t my_col, float my_d, int cnt, int t0,
+                                             int grp, int sub, float* acc, float* accd) {
+    using Ln = Lanes<T, LIN>;
+    for (int t = t0; t < cnt; t += Ln::GPW * Ln::U) {
+        uint4 r[Ln::U];
+        float dj[Ln::U];
+        gather_issue<AGG, T, LIN>(X, my_col, my_d, cnt, t, grp, sub, r, dj);
+        gather_add<AGG, T, LIN>(r, dj, acc, accd);
+    }
+}
 
 // Adds X[col[p]] for p in [beg, end) to this lane's chunk of the row sum (and, for the
 // reduced modularity operator, the d_j-weighted sum).  Lane groups take different neighbours;
@@ -185,39 +236,13 @@ template <int AGG, typename T, int LIN>
 __device__ __forceinline__ void gather_range(const LayerArgs& a, const T* __restrict__ X, int64_t beg, int64_t end,
                                              int lane, float* acc, float* accd) {
     using Ln = Lanes<T, LIN>;
-    constexpr int E = Ln::E, GPW = Ln::GPW, U = Ln::U;
     const int grp = lane / Ln::LPR, sub = lane % Ln::LPR;
     for (int64_t base = beg; base < end; base += 32) {
         const int cnt = (int)((end - base) < 32 ? (end - base) : 32);
         const int32_t my_col = lane < cnt ? __ldg(a.col + base + lane) : 0;
         float my_d = 0.f;
         if constexpr (AGG == AGG_MOD_REDUCED) my_d = lane < cnt ? (float)__ldg(a.deg + my_col) : 0.f;
-        for (int t = 0; t < cnt; t += GPW * U) {
-            float v[U][E];
-            float dj[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int idx = t + u * GPW + grp;
-                const int src = idx < cnt ? idx : 0;
-                const int32_t j = __shfl_sync(0xffffffffu, my_col, src);
-                if constexpr (AGG == AGG_MOD_REDUCED) dj[u] = __shfl_sync(0xffffffffu, my_d, src);
-                if (idx < cnt) {
-                    Vec<T>::load(X + (int64_t)j * LIN + sub * E, v[u]);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < E; ++e) v[u][e] = 0.f;
-                    dj[u] = 0.f;
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    acc[e] += v[u][e];
-                    if constexpr (AGG == AGG_MOD_REDUCED) accd[e] += dj[u] * v[u][e];
-                }
-            }
-        }
+        gather_chunk<AGG, T, LIN>(X, my_col, my_d, cnt, 0, grp, sub, acc, accd);
     }
 }
 
@@ -315,7 +340,7 @@ __device__ __forceinline__ void row_epilogue(const LayerArgs& a, int64_t i, cons
 
 // Light rows: one warp per row (grid-stride), FP32 accumulation, fused row epilogue.
 template <int AGG, typename T, int LIN>
-__global__ void __launch_bounds__(256) k_spmm_layer(LayerArgs a, const T* __restrict__ X) {
+__global__ void __launch_bounds__(256, 4) k_spmm_layer(LayerArgs a, const T* __restrict__ X) {
     constexpr int E = Lanes<T, LIN>::E;
     extern __shared__ float smem[];
     float* Ws = smem;                                       // LIN x lout
@@ -327,10 +352,28 @@ __global__ void __launch_bounds__(256) k_spmm_layer(LayerArgs a, const T* __rest
     const int lane = threadIdx.x & 31;
     const int grp = lane / Lanes<T, LIN>::LPR, sub = lane % Lanes<T, LIN>::LPR;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < a.n; i += nwarps) {
-        const int64_t beg = a.rp64 ? a.rp64[i] : a.rp32[i];
-        const int64_t end = a.rp64 ? a.rp64[i + 1] : a.rp32[i + 1];
-        if (a.heavy && end - beg > HEAVY_DEG) continue;     // gathered by k_spmm_heavy
+    // Software pipeline over the warp's rows: the next row's bounds and first 32 column indices
+    // are loaded while this row's first gathers are in flight.
+    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t beg = 0, end = 0;
+    int32_t my_col = 0;
+    if (i < a.n) {
+        beg = a.rp64 ? a.rp64[i] : a.rp32[i];
+        end = a.rp64 ? a.rp64[i + 1] : a.rp32[i + 1];
+        const int c0 = (a.heavy && end - beg > HEAVY_DEG) ? 0 : (int)(end - beg < 32 ? end - beg : 32);
+        my_col = lane < c0 ? __ldg(a.col + beg + lane) : 0;
+    }
+    for (; i < a.n; i += nwarps) {
+        const int64_t inext = i + nwarps;
+        int64_t nbeg = 0, nend = 0;
+        if (inext < a.n) {
+            nbeg = a.rp64 ? a.rp64[inext] : a.rp32[inext];
+            nend = a.rp64 ? a.rp64[inext + 1] : a.rp32[inext + 1];
+        }
+        const bool heavy_row = a.heavy && end - beg > HEAVY_DEG;   // gathered by k_spmm_heavy
+        const int cnt = heavy_row ? 0 : (int)(end - beg < 32 ? end - beg : 32);
+        float my_d = 0.f;
+        if constexpr (AGG == AGG_MOD_REDUCED) my_d = lane < cnt ? (float)__ldg(a.deg + my_col) : 0.f;
         float acc[E];
         float accd[AGG == AGG_MOD_REDUCED ? E : 1];
 #pragma unroll
@@ -339,12 +382,25 @@ __global__ void __launch_bounds__(256) k_spmm_layer(LayerArgs a, const T* __rest
 #pragma unroll
             for (int e = 0; e < E; ++e) accd[e] = 0.f;
         }
+        uint4 r[Lanes<T, LIN>::U];
+        float dj[Lanes<T, LIN>::U];
+        gather_issue<AGG, T, LIN>(X, my_col, my_d, cnt, 0, grp, sub, r, dj);
         if constexpr (AGG == AGG_GCN) {
-            if (grp == 0) Vec<T>::load(X + i * LIN + sub * E, acc);   // the self loop of A + I
+            if (grp == 0 && !heavy_row) Vec<T>::load(X + i * LIN + sub * E, acc);   // the self loop of A + I
         }
-        gather_range<AGG, T, LIN>(a, X, beg, end, lane, acc, accd);
-        combine_groups<AGG, T, LIN>(acc, accd);
-        row_epilogue<AGG, T, LIN>(a, i, acc, accd, lane, vbuf, a.W ? Ws : nullptr);
+        const int ncnt = (a.heavy && nend - nbeg > HEAVY_DEG) ? 0 : (int)(nend - nbeg < 32 ? nend - nbeg : 32);
+        const int32_t ncol = lane < ncnt ? __ldg(a.col + nbeg + lane) : 0;
+        if (!heavy_row) {
+            gather_add<AGG, T, LIN>(r, dj, acc, accd);
+            gather_chunk<AGG, T, LIN>(X, my_col, my_d, cnt, Lanes<T, LIN>::GPW * Lanes<T, LIN>::U, grp, sub, acc,
+                                      accd);
+            if (end - beg > 32) gather_range<AGG, T, LIN>(a, X, beg + 32, end, lane, acc, accd);
+            combine_groups<AGG, T, LIN>(acc, accd);
+            row_epilogue<AGG, T, LIN>(a, i, acc, accd, lane, vbuf, a.W ? Ws : nullptr);
+        }
+        beg = nbeg;
+        end = nend;
+        my_col = ncol;
     }
 }
 
