@@ -104,6 +104,9 @@ struct EmbedWs {
     float* rsh;
     int32_t* heavy;        // rows of degree above 256 (gathered by a whole CTA)
     int* heavy_count;
+    int* work;             // chunk counters of the BF16 flat-stream gathers, one per layer
+    int64_t* rp_self;      // BF16 GCN gathers: CSR of A + I (null otherwise)
+    int32_t* col_self;
     float* W[RAFTGP_MAX_LAYERS];
     __nv_bfloat16* Whi[RAFTGP_MAX_LAYERS];  // BF16 form: W^T split into hi and lo for the tensor cores
     __nv_bfloat16* Wlo[RAFTGP_MAX_LAYERS];
@@ -120,7 +123,7 @@ static int embed_maxw(const raftgp_embed_opts* o) {
     return w;
 }
 
-static EmbedWs carve_embed(Carver& c, int64_t n, const raftgp_embed_opts* o) {
+static EmbedWs carve_embed(Carver& c, int64_t n, int64_t nnz, const raftgp_embed_opts* o) {
     EmbedWs w{};
     w.err = c.take<uint32_t>(64);
     w.deg = c.take<int32_t>(n);
@@ -128,6 +131,11 @@ static EmbedWs carve_embed(Carver& c, int64_t n, const raftgp_embed_opts* o) {
     w.rsh = c.take<float>(n);
     w.heavy = c.take<int32_t>(n);
     w.heavy_count = c.take<int>(64);
+    w.work = c.take<int>(64);
+    if (o->dtype == RAFTGP_BF16 && o->n_layers >= 1) {
+        w.rp_self = c.take<int64_t>(n + 1);
+        w.col_self = c.take<int32_t>(nnz + n);
+    }
     for (int k = 1; k <= o->n_layers; ++k) {
         w.W[k - 1] = c.take<float>((size_t)o->dims[k - 1] * o->dims[k]);
         w.Whi[k - 1] = c.take<__nv_bfloat16>((size_t)o->dims[k - 1] * o->dims[k]);
@@ -244,26 +252,42 @@ static raftgp_status run_embed(const raftgp_csr* g, const raftgp_embed_opts* o, 
                  rank1 ? w.partial : nullptr, w.gvec, s);
     const int agg0 = o->op == RAFTGP_OP_NCUT ? AGG_NCUT_ : (rank1 ? AGG_MOD_FULL_ : AGG_MOD_REDUCED_);
     cudaError_t e;
+    // BF16 gathers without a fused weight product run as flat entry streams (spmm_flat.cu)
+    const bool flat0 = spmm_flat_supported(agg0, o->dtype, L);
     if (o->n_layers == 0) {
-        e = launch_layer(agg0, o->dtype, g, w.deg, w.rs, w.gvec, 2, nullptr, L, L, nullptr, w.bufB, Z,
-                         o->stage_out[0], w.heavy, w.heavy_count, s);
+        if (flat0)
+            e = launch_spmm_flat(agg0, n, g->row_ptr_bits, g->row_ptr, g->col, g->nnz, w.deg, w.rs, w.gvec, 2, L,
+                                 w.bufB, Z, o->stage_out[0], w.work, s);
+        else
+            e = launch_layer(agg0, o->dtype, g, w.deg, w.rs, w.gvec, 2, nullptr, L, L, nullptr, w.bufB, Z,
+                             o->stage_out[0], w.heavy, w.heavy_count, s);
         if (e != cudaSuccess) return cuda_fail(e, "projection");
         return RAFTGP_OK;
     }
     if (o->dtype == RAFTGP_BF16) {
         // BF16: every SpMM is a pure gather with its row epilogue; the weight products run as
-        // tensor-core GEMMs (bufA / bufB alternate: the gather reads one, writes the other)
+        // tensor-core GEMMs (bufA / bufB alternate: the gather reads one, writes the other).
+        // The GCN gathers walk the CSR of A + I, so the self loop is one more stored entry.
         for (int k = 1; k <= o->n_layers; ++k) launch_w_split(w.W[k - 1], o->dims[k - 1], o->dims[k], w.Whi[k - 1],
                                                               w.Wlo[k - 1], s);
-        e = launch_layer(agg0, o->dtype, g, w.deg, w.rs, w.gvec, 0, nullptr, L, L, nullptr, w.bufB, w.bufA,
-                         o->stage_out[0], w.heavy, w.heavy_count, s);
+        launch_self_csr(g, w.rp_self, w.col_self, s);
+        if (flat0)
+            e = launch_spmm_flat(agg0, n, g->row_ptr_bits, g->row_ptr, g->col, g->nnz, w.deg, w.rs, w.gvec, 0, L,
+                                 w.bufB, w.bufA, o->stage_out[0], w.work, s);
+        else
+            e = launch_layer(agg0, o->dtype, g, w.deg, w.rs, w.gvec, 0, nullptr, L, L, nullptr, w.bufB, w.bufA,
+                             o->stage_out[0], w.heavy, w.heavy_count, s);
         if (e != cudaSuccess) return cuda_fail(e, "projection");
         e = launch_dense_tc(L, o->dims[1], n, w.bufA, w.Whi[0], w.Wlo[0], w.rsh, w.bufB, w.err, s);
         if (e != cudaSuccess) return cuda_fail(e, "dense layer");
         for (int k = 1; k <= o->n_layers; ++k) {
             const bool last = k == o->n_layers;
-            e = launch_layer(AGG_GCN_, o->dtype, g, w.deg, w.rsh, nullptr, 1, nullptr, o->dims[k], o->dims[k], nullptr,
-                             w.bufB, last ? Z : w.bufA, o->stage_out[k], w.heavy, w.heavy_count, s);
+            if (spmm_flat_supported(AGG_GCN_, o->dtype, o->dims[k]))
+                e = launch_spmm_flat(AGG_GCN_, n, 64, w.rp_self, w.col_self, g->nnz, w.deg, w.rsh, nullptr, 1,
+                                     o->dims[k], w.bufB, last ? Z : w.bufA, o->stage_out[k], w.work + k, s);
+            else
+                e = launch_layer(AGG_GCN_, o->dtype, g, w.deg, w.rsh, nullptr, 1, nullptr, o->dims[k], o->dims[k],
+                                 nullptr, w.bufB, last ? Z : w.bufA, o->stage_out[k], w.heavy, w.heavy_count, s);
             if (e != cudaSuccess) return cuda_fail(e, "gcn layer");
             if (!last) {
                 e = launch_dense_tc(o->dims[k], o->dims[k + 1], n, w.bufA, w.Whi[k], w.Wlo[k], w.rsh, w.bufB, w.err, s);
@@ -508,7 +532,7 @@ size_t raftgp_workspace_size(const raftgp_csr* g, const raftgp_embed_opts* eopts
     int32_t* deg = nullptr;
     if (eopts) {
         if (check_embed(eopts) != RAFTGP_OK) return 0;
-        EmbedWs w = carve_embed(c, g->n, eopts);
+        EmbedWs w = carve_embed(c, g->n, g->nnz, eopts);
         (void)w;
         err = reinterpret_cast<uint32_t*>(1);  // marks "shared with the embedding part"
         deg = reinterpret_cast<int32_t*>(1);
@@ -531,7 +555,7 @@ raftgp_status raftgp_embed(const raftgp_csr* g, const raftgp_embed_opts* eopts, 
     if (ws_bytes < raftgp_workspace_size(g, eopts, nullptr, 0)) return fail(RAFTGP_ENOMEM, "workspace too small");
     cudaStream_t s = (cudaStream_t)stream;
     Carver c(ws);
-    EmbedWs w = carve_embed(c, g->n, eopts);
+    EmbedWs w = carve_embed(c, g->n, g->nnz, eopts);
     cudaMemsetAsync(w.err, 0, sizeof(uint32_t), s);
     st = run_embed(g, eopts, Z, w, false, s);
     if (st) return st;
@@ -576,7 +600,7 @@ raftgp_status raftgp_partition(const raftgp_csr* g, const raftgp_embed_opts* eop
     cudaStream_t s = (cudaStream_t)stream;
     const int d = eopts->dims[eopts->n_layers];
     Carver c(ws);
-    EmbedWs ew = carve_embed(c, g->n, eopts);
+    EmbedWs ew = carve_embed(c, g->n, g->nnz, eopts);
     void* Z = c.take<char>((size_t)g->n * d * elem_size(eopts->dtype));
     SelectWs sw = carve_select(c, g->n, d, sopts, ew.err, ew.deg);
     cudaMemsetAsync(ew.err, 0, sizeof(uint32_t), s);
@@ -919,7 +943,7 @@ raftgp_status batch_layout(const raftgp_csr* g, const int64_t* off, int ng, cons
 
 void carve_batch(Carver& c, raftgp_batch_plan& p) {
     const int64_t n = p.total_n;
-    p.ew = carve_embed(c, n, &p.eo);
+    p.ew = carve_embed(c, n, p.g.nnz, &p.eo);
     p.Z = c.take<char>((size_t)n * p.d * elem_size(p.eo.dtype));
     p.err = c.take<uint32_t>(64);
     BatchDev& b = p.bd;

@@ -45,6 +45,15 @@ cudaError_t launch_layer(int agg, int dtype, const raftgp_csr* g, const int32_t*
                          const float* gvec, int act, const float* W, int lin, int lout, const float* postscale,
                          const void* X, void* out, void* stage, const int32_t* heavy, const int* heavy_count,
                          cudaStream_t s);
+// BF16 gather-only layers (no fused W, not the reduced operator) as a flat stream of stored
+// entries staged by cp.async (spmm_flat.cu).  `work` is a chunk counter the launch zeroes;
+// nnz_g is the graph's stored-entry count (2e) for the modularity term.
+bool spmm_flat_supported(int agg, int dtype, int lin);
+cudaError_t launch_spmm_flat(int agg, int64_t n, int rp_bits, const void* row_ptr, const int32_t* col, int64_t nnz_g,
+                             const int32_t* deg, const float* rowscale, const float* gvec, int act, int lin,
+                             const void* X, void* out, void* stage, int* work, cudaStream_t s);
+// CSR of A + I (row i: i, then its neighbours): rp_self has n + 1 entries, col_self nnz + n.
+void launch_self_csr(const raftgp_csr* g, int64_t* rp_self, int32_t* col_self, cudaStream_t s);
 
 // ---- dense layer on tensor cores (dense_tc.cu) -----------------------------------------
 void launch_w_split(const float* W, int lin, int lout, __nv_bfloat16* whi, __nv_bfloat16* wlo, cudaStream_t s);

@@ -136,3 +136,60 @@ def test_workspace_too_small(cuda):
     st = api.lib().raftgp_embed(C.byref(csr), C.byref(o), C.c_void_p(Z.data_ptr()), C.c_void_p(ws.data_ptr()), 1024,
                                 None)
     assert st == api._abi.ENOMEM
+
+
+def _bf16(a):
+    """Round to BF16 (nearest even) as the kernels store it."""
+    return torch.as_tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("graph", ["ragged", "dcsbm-50k"])
+@pytest.mark.parametrize("op,dims", [("mod_full", (128, 128, 64)), ("ncut", (64, 64, 32))])
+def test_embed_bf16_gathers_match_oracle(cuda, graph, op, dims):
+    """The BF16 gathers (projection and each GCN layer) against the oracle fed the same BF16
+    inputs the kernels read: Theta as stored (rounded after the NCut column scale), and for
+    each GCN layer the previous stage's BF16 output through W (rounded as the dense layer
+    stores it).  Bound: the projection element by element within 2^-8 relative (one BF16
+    rounding of the output) plus 1e-4 of the RMS (FP32 accumulation) plus two BF16 ulps of
+    the row's largest stored term (the kernel scales Theta by a single-precision reciprocal
+    square root before rounding, so a stored term can sit one ulp from the one rebuilt here;
+    a missing or extra neighbour is a whole term, far above this); each GCN row within
+    6e-3 of the unit-norm oracle row."""
+    g = ragged_graph(3) if graph == "ragged" else workload(graph)
+    dg = api.DeviceGraph.from_host(g, cuda)
+    L = dims[0]
+    th = oracle.theta(g.n, L, 3)
+    Z, st = api.embed(dg, op, dims, "bf16", seed=3, theta=torch.as_tensor(th, dtype=torch.float32),
+                      return_stages=True)
+    torch.cuda.synchronize()
+    deg = np.diff(np.asarray(g.row_ptr, dtype=np.int64)).astype(np.float64)
+    if op == "ncut":
+        rs32 = np.where(deg > 0, 1.0 / np.sqrt(deg.astype(np.float32)), 0).astype(np.float32)
+        stored = _bf16(th.astype(np.float32) * rs32[:, None])
+        th_eff = np.where(deg[:, None] > 0, stored * np.sqrt(np.maximum(deg, 1))[:, None], 0.0)
+    else:
+        th_eff = _bf16(th)
+    Y_ref = oracle.project(g, op, th_eff)
+    Y = _np(st[0]).astype(np.float64)
+    rms = np.sqrt(np.mean(Y_ref ** 2))
+    tol = 2.0 ** -8 * np.abs(Y_ref) + 1e-4 * rms
+    if op == "ncut":
+        rp = np.asarray(g.row_ptr, dtype=np.int64)
+        col = np.asarray(g.col, dtype=np.int64)
+        big = np.zeros_like(Y_ref)
+        nz = np.flatnonzero(deg > 0)
+        big[nz] = np.maximum.reduceat(np.abs(stored)[col], rp[:-1][nz], axis=0)
+        tol += 2 * 2.0 ** -8 * (rs32[:, None] * big)
+    bad = np.abs(Y - Y_ref) > tol
+    print(f"{graph} {op} projection: max |error| / bound {np.max(np.abs(Y - Y_ref) / tol):.3f}")
+    assert not bad.any(), (int(bad.sum()), np.argwhere(bad)[:5])
+    rsh = 1.0 / np.sqrt(deg + 1.0)
+    for k in range(1, len(dims)):
+        W = oracle.gcn_weight(k, dims[k - 1], dims[k], 3)
+        prev = _np(st[k - 1]).astype(np.float64)
+        P = _bf16(rsh[:, None] * (prev @ W))        # what the gather reads: rsh_j (Z W)_j
+        ref = oracle.gcn_layer(g, P / rsh[:, None], np.eye(dims[k]))
+        got = _np(st[k]).astype(np.float64)
+        row_err = np.linalg.norm(got - ref, axis=1)
+        print(f"{graph} {op} layer {k}: max row error {row_err.max():.2e}, mean {row_err.mean():.2e}")
+        assert row_err.max() <= 6e-3, (k, int(np.argmax(row_err)), row_err.max())
