@@ -272,6 +272,58 @@ def bench_bisect(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_sbm(args):
+    """Algorithm 2 on the GPU at the 1M-node model (the dcsbm-1m parameters: K = 200,
+    Dirichlet(1) block sizes, theta a power law with exponent 2.2 in [5, 5000], expected mean
+    degree 25, 2:1 within/between): one step = count pass + emit pass (the edge list) + the
+    symmetric sorted CSR build, parameters resident in HBM.  The CPU oracle draws the
+    dcsbm-50k model for the baseline line."""
+    import torch
+    from inputs.dcsbm import WORKLOADS, dcsbm_params
+    from paper_2312_01560_gb300 import api
+    block, theta, om = dcsbm_params(seed=0, **WORKLOADS["dcsbm-1m"])
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    bt, tt, ot = (torch.as_tensor(x, device=dev) for x in (block, theta, om))
+    n = len(block)
+
+    def step(seed):
+        s, d = api.sbm_sample(bt, tt, ot, seed=seed)
+        g = api.coo_to_csr(n, s, d)
+        return s.numel(), g
+
+    for w in range(max(args.warmup, 1)):
+        step(1000 + w)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    edges = 0
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        m, g = step(k)
+        edges += m
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    clocks = sampler.stop()
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        b2, t2, o2 = dcsbm_params(seed=0, **WORKLOADS["dcsbm-50k"])
+        c0 = time.perf_counter()
+        s2, _, _ = oracle.sbm_sample(b2, t2, o2, 1)
+        cs = time.perf_counter() - c0
+        cpu = {"value": len(s2) / cs, "unit": "edges/s", "cores": 1, "kind": "oracle",
+               "sample": "the FP64 C oracle of Algorithm 2 on the dcsbm-50k model (edge list only, one thread)"}
+    line = {"metric": "graph generation edges/s, Algorithm 2 at 1M nodes", "value": edges / args.steps / (ms * 1e-3),
+            "unit": "edges/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "dcsbm-1m model: N = 1,000,000, K = 200; count + emit + CSR build per step",
+                       "edges_per_step": edges / args.steps,
+                       "timing": "host clock around synchronised steps (the count pass returns the edge count)"},
+            "cpu_baseline": cpu, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def bench_batched(args):
     """Times replays of one captured plan that partitions 512 DC-SBM graphs of uneven size
     (N log-uniform in [1,000, 50,000], K = round(N^0.35), exponent 2.5, mean degree uniform in
@@ -396,7 +448,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="bf16", choices=["bf16", "f32", "diff", "batched", "bisect"],
+    ap.add_argument("--form", default="bf16", choices=["bf16", "f32", "diff", "batched", "bisect", "sbm"],
                     help="bf16/f32: the partition benchmark; diff: Adam tuning steps of the GNN weights "
                          "(N=200,000, GNN 128-128-64, --steps Adam steps, default 200); batched: 512 uneven graphs "
                          "partitioned by one captured plan (--steps replays); bisect: the 1M-node partition "
@@ -412,6 +464,8 @@ def main():
         return bench_diff(args)
     if args.form == "batched":
         return bench_batched(args)
+    if args.form == "sbm":
+        return bench_sbm(args)
     if args.form == "bisect":
         return bench_bisect(args)
 

@@ -333,6 +333,43 @@ raftgp_status raftgp_gcn_weights(int32_t layer, int32_t lin, int32_t lout, uint6
 raftgp_status raftgp_adam_step(float* param, const float* grad, float* m, float* v, int64_t count, float lr,
                                float beta1, float beta2, float eps, int32_t step, raftgp_stream_t stream);
 
+/* ---- Algorithm 2 (Section IV): graphs drawn from the SBM of Definition 1 ----
+ * A_ij ~ Pois(lambda_ij), lambda_ij = theta_i theta_j Omega_{c_i c_j}, for i < j (undirected,
+ * no self loops); the drawn graph is the support of A (one edge per nonzero entry; its value
+ * A_ij >= 1 is returned as a weight).  Each block pair r <= s has a virtual table of its
+ * node pairs (row-major over the blocks' nodes in ascending order; the entries above the
+ * diagonal when r = s), cut into segments of 2^16 consecutive entries; every segment runs the
+ * paper's loop on its own (draw p, skip to the first entry t with RangeSum(m, t) > -ln p by
+ * binary search over prefix sums of theta, draw the value Pois(lambda | >= 1), go on at t + 1).
+ * Draw j of global segment g is Philox4x32-10(seed; g_lo, g_hi, j, "Sbm2").  All arrays are
+ * device pointers; the caller owns them.
+ *
+ * raftgp_sbm_count checks the parameters (RAFTGP_EINVAL for a block outside [0, k), a
+ * negative or non-finite theta or Omega), draws the graph's size and returns it in *m
+ * (host); it synchronises.  raftgp_sbm_emit, called next with the same parameters and
+ * workspace, writes the m edges (src[e], dst[e]: node ids; weight[e] may be NULL) in the order
+ * (block pair, segment, draw); RAFTGP_EINVAL if m differs from the count's.  The workspace
+ * grows as n^2 / 2^14 bytes (about 120 MB at n = 1M).
+ *
+ * raftgp_coo_to_csr builds the symmetric CSR of m undirected edges (both directions, every
+ * row sorted): row_ptr int64[n + 1], col int32[2 m].  RAFTGP_EINVAL for an endpoint outside
+ * [0, n) or a self loop, RAFTGP_EUNSUPPORTED for a row longer than 16384.  Synchronises. */
+typedef struct {
+    int64_t n;              /* nodes, 1 .. 2^31 - 2 */
+    int32_t k;              /* blocks, >= 1 */
+    const int32_t* block;   /* [n]: block c_i of node i, in [0, k) */
+    const double* theta;    /* [n]: degree correction theta_i >= 0 */
+    const double* omega;    /* [k * k], row-major: Omega_rs >= 0; entries with r <= s are read */
+    uint64_t seed;
+} raftgp_sbm;
+size_t raftgp_sbm_workspace_size(int64_t n, int32_t k);
+raftgp_status raftgp_sbm_count(const raftgp_sbm* p, int64_t* m, void* ws, size_t ws_bytes, raftgp_stream_t stream);
+raftgp_status raftgp_sbm_emit(const raftgp_sbm* p, int32_t* src, int32_t* dst, int32_t* weight, int64_t m, void* ws,
+                              size_t ws_bytes, raftgp_stream_t stream);
+size_t raftgp_coo_to_csr_workspace_size(int64_t n);
+raftgp_status raftgp_coo_to_csr(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, int64_t* row_ptr,
+                                int32_t* col, void* ws, size_t ws_bytes, raftgp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -126,6 +126,34 @@ def dcsbm(n: int, k: int, *, alpha: float = 5.0, gamma: float = 2.5, dmin: float
     return _csr_from_unique_pairs(n, perm[u_], perm[v_], planted, k)
 
 
+def dcsbm_params(n: int, k: int, *, alpha: float = 5.0, gamma: float = 2.5, dmin: float = 5.0,
+                 dmax: float = 100.0, mean_degree: float = 16.0, ratio: float = 5.0, seed: int = 0):
+    """The model of steps 1-3 of the recipe as the parameters of Definition 1 (for a sampler
+    that draws the graph itself): block[i] (int32, node ids randomly permuted), theta[i]
+    (float64) and Omega (K x K float64; Omega_rr = a / kappa_r, Omega_rs = b)."""
+    if n < 1 or k < 1 or k > n:
+        raise ValueError("need 1 <= k <= n")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sizes = _block_sizes(rng, n, k, alpha)
+    block_of_sorted = np.repeat(np.arange(k, dtype=np.int64), sizes)
+    theta = _power_law(rng, n, gamma, dmin, dmax)
+    start = np.concatenate([[0], np.cumsum(sizes)])
+    kappa = np.add.reduceat(theta, start[:-1])
+    S = kappa.sum()
+    total = n * mean_degree / 2.0
+    a = 2.0 * (total * ratio / (1.0 + ratio)) / S
+    denom = S * S - np.sum(kappa * kappa)
+    b = 2.0 * (total / (1.0 + ratio)) / denom if denom > 0 else 0.0
+    omega = np.full((k, k), b)
+    np.fill_diagonal(omega, a / kappa)
+    perm = rng.permutation(n).astype(np.int64)          # sorted position -> public node id
+    block = np.empty(n, dtype=np.int32)
+    block[perm] = block_of_sorted.astype(np.int32)
+    th = np.empty(n, dtype=np.float64)
+    th[perm] = theta
+    return block, th, omega
+
+
 def _csr_from_unique_pairs(n, u, v, planted, k_planted):
     """Symmetric CSR from distinct undirected pairs u != v (each listed once)."""
     src = np.concatenate([u, v])

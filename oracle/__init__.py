@@ -241,3 +241,25 @@ def gcn_rows(g, Zin32, W, rows):
                               C.c_int(W.shape[0]), _p(W, C.c_double), C.c_int(W.shape[1]), _p(rows, C.c_int64),
                               C.c_int64(rows.shape[0]), _p(Z, C.c_double)), "gcn_rows")
     return Z
+
+
+def sbm_sample(block, theta, omega, seed, seg=65536):
+    """Algorithm 2 (Section IV): one draw of the support of A ~ Pois(theta_i theta_j
+    Omega_{c_i c_j}) over i < j (Definition 1), each block pair's table cut into segments of
+    `seg` entries (2^16 in the library).  Returns (src, dst, weight) in the order (block
+    pair, segment, draw); weight is A_ij >= 1."""
+    block = np.ascontiguousarray(block, dtype=np.int32)
+    theta = _f64(theta)
+    omega = _f64(omega)
+    n, K = block.shape[0], omega.shape[0]
+    m = C.c_int64(0)
+    args = (C.c_int64(n), C.c_int(K), _p(block, C.c_int32), _p(theta, C.c_double), _p(omega, C.c_double),
+            C.c_uint64(seed), C.c_int64(seg))
+    _check(lib().orc_sbm_sample(*args, C.c_int64(0), None, None, None, C.byref(m)), "sbm_sample")
+    cnt = m.value
+    src = np.zeros(cnt, np.int32)
+    dst = np.zeros(cnt, np.int32)
+    w = np.zeros(cnt, np.int32)
+    _check(lib().orc_sbm_sample(*args, C.c_int64(cnt), _p(src, C.c_int32), _p(dst, C.c_int32), _p(w, C.c_int32),
+                                C.byref(m)), "sbm_sample")
+    return src, dst, w

@@ -653,3 +653,202 @@ int orc_select(int64_t n, const int64_t* row_ptr, const int32_t* col, const doub
     free(seeds); free(lab); free(list);
     return rc;
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* Algorithm 2 (Section IV): graphs from the degree-corrected SBM of Definition 1,       */
+/* A_ij ~ Pois(lambda_ij), lambda_ij = theta_i theta_j Omega_{c_i c_j}.                  */
+/*                                                                                       */
+/* Readings (the paper is silent on these):                                              */
+/*   - Undirected, no self loops: block pairs r <= s; for r = s only the entries i < j   */
+/*     (the upper triangle without the diagonal).                                        */
+/*   - C_r lists the nodes of block r in ascending index order; the virtual table of     */
+/*     (r, s) is row-major over (position in C_r, position in C_s), upper triangle rows  */
+/*     for r = s (row a holds b = a+1 .. n_r-1).                                         */
+/*   - Each table is cut into segments of `seg` consecutive entries (2^16 in the        */
+/*     library) and the loop of Algorithm 2 runs on each segment on its own.  The        */
+/*     entries are independent, so                                                        */
+/*     the cut leaves the distribution unchanged; it fixes which draws each segment      */
+/*     uses: draw j of global segment g comes from Philox counter (g_lo, g_hi, j,        */
+/*     "Sbm2"), words 0-1 the skip uniform, words 2-3 the weight uniform.               */
+/*   - The skip: p = (x >> 11 + 1) 2^-53 in (0, 1] from the 64-bit word x = w0 | w1 << 32,*/
+/*     E = -ln p; with F(t) the sum of lambda over the entries before linear index t,    */
+/*     the next nonzero entry is the smallest t >= m with F(t+1) > F(m) + E (i.e.        */
+/*     p > exp(-RangeSum(m, t))), found by binary search on [m, segment end); none if    */
+/*     F(segment end) <= F(m) + E.                                                        */
+/*   - F from per-block prefix sums of theta, summed left to right:                      */
+/*       r < s:  F(a, b) = om (Pre_r[a] Tot_s) + om (theta_a Pre_s[b])                  */
+/*       r = s:  F(a, b) = om Tri_r[a] + om (theta_a (Pre_r[b] - Pre_r[a+1])),            */
+/*               Tri_r[a] = sum_{a' < a} theta_a' (Tot_r - Pre_r[a'+1])                   */
+/*     (a, b) being the table entry at linear index t, or the start of the next row.     */
+/*   - The weight: A_ij ~ Pois(lambda) given A_ij >= 1 by inversion from k = 1 with the  */
+/*     uniform u = (y >> 11) 2^-53 of words 2-3: P(1 | >= 1) = lambda / expm1(lambda),   */
+/*     each next term times lambda / k (exact for lambda <= 700; at most 2^20 steps).    */
+/*   The output graph is the support of A (each nonzero entry one edge, weight kept     */
+/*   separately), so multi-edges collapse to one edge.                                   */
+/* ------------------------------------------------------------------------------------ */
+#define ORC_STREAM_SBM 0x53626d32u      /* "Sbm2" */
+
+typedef struct {
+    int r, s;
+    int64_t nr, ns;
+    const int32_t* nodes_r;
+    const int32_t* nodes_s;
+    const double* th_r;   /* theta in C_r order */
+    const double* th_s;
+    const double* pre_r;
+    const double* pre_s;
+    const double* tri_r;
+    double tot_s, om;
+} SbmPair;
+
+static int64_t sbm_tri_row_start(int64_t n, int64_t a) { return a * n - a * (a + 1) / 2; }
+
+/* The table entry (a, b) at linear index t (t may equal the table size: the end). */
+static void sbm_entry(const SbmPair* P, int64_t t, int64_t* a, int64_t* b) {
+    if (P->r != P->s) {
+        *a = t / P->ns;
+        *b = t % P->ns;
+        return;
+    }
+    int64_t n = P->nr;
+    int64_t size = n * (n - 1) / 2;
+    if (t >= size) { *a = n - 1; *b = n; return; }   /* the end: after the last row */
+    double q = (double)(2 * n - 1);
+    int64_t r = (int64_t)((q - sqrt(q * q - 8.0 * (double)t)) / 2.0);
+    if (r < 0) r = 0;
+    if (r > n - 2) r = n - 2;
+    while (r > 0 && sbm_tri_row_start(n, r) > t) --r;
+    while (r + 1 <= n - 2 && sbm_tri_row_start(n, r + 1) <= t) ++r;
+    *a = r;
+    *b = r + 1 + (t - sbm_tri_row_start(n, r));
+}
+
+static double sbm_F(const SbmPair* P, int64_t t) {
+    int64_t a, b;
+    sbm_entry(P, t, &a, &b);
+    if (P->r != P->s) {
+        if (a >= P->nr) return P->om * (P->pre_r[P->nr] * P->tot_s);
+        double rowpart = P->om * (P->pre_r[a] * P->tot_s);
+        double colpart = P->om * (P->th_r[a] * P->pre_s[b]);
+        return rowpart + colpart;
+    }
+    double rowpart = P->om * P->tri_r[a];
+    double colpart = P->om * (P->th_r[a] * (P->pre_r[b] - P->pre_r[a + 1]));
+    return rowpart + colpart;
+}
+
+static int sbm_weight(double lam, uint64_t y) {
+    double u = (double)(y >> 11) * (1.0 / 9007199254740992.0);
+    double term = lam / expm1(lam);
+    double c = term;
+    int k = 1;
+    while (u >= c && k < (1 << 20)) {
+        ++k;
+        term = term * (lam / (double)k);
+        c = c + term;
+    }
+    return k;
+}
+
+/* n nodes in K blocks (block[i] in [0, K)), theta[n] > 0, omega[K*K] row-major (entries
+ * with r <= s read), segments of `seg` table entries.  Writes at most max_edges edges (src, dst, weight; any may be NULL
+ * to only count) in the order (pair, segment, draw) and the count in *m_out. */
+int orc_sbm_sample(int64_t n, int K, const int32_t* block, const double* theta, const double* omega, uint64_t seed,
+                   int64_t seg, int64_t max_edges, int32_t* src, int32_t* dst, int32_t* weight, int64_t* m_out) {
+    if (n < 0 || K < 1 || seg < 1) return ORC_EINVAL;
+    for (int64_t i = 0; i < n; ++i)
+        if (block[i] < 0 || block[i] >= K || !(theta[i] >= 0.0)) return ORC_EINVAL;
+    int64_t* boff = (int64_t*)calloc((size_t)K + 1, sizeof(int64_t));
+    int32_t* nodes = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    double* th = (double*)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    double* pre = (double*)malloc(sizeof(double) * (size_t)(n + K));
+    double* tri = (double*)malloc(sizeof(double) * (size_t)(n + K));
+    if (!boff || !nodes || !th || !pre || !tri) {
+        free(boff); free(nodes); free(th); free(pre); free(tri);
+        return ORC_ENOMEM;
+    }
+    for (int64_t i = 0; i < n; ++i) boff[block[i] + 1]++;
+    for (int r = 0; r < K; ++r) boff[r + 1] += boff[r];
+    {
+        int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)K);
+        if (!fill) { free(boff); free(nodes); free(th); free(pre); free(tri); return ORC_ENOMEM; }
+        for (int r = 0; r < K; ++r) fill[r] = boff[r];
+        for (int64_t i = 0; i < n; ++i) {   /* ascending node order inside each block */
+            int64_t q = fill[block[i]]++;
+            nodes[q] = (int32_t)i;
+            th[q] = theta[i];
+        }
+        free(fill);
+    }
+    /* per block: Pre (n_r + 1 entries) and Tri (n_r + 1 entries) at offset boff[r] + r */
+    for (int r = 0; r < K; ++r) {
+        int64_t o = boff[r], nr = boff[r + 1] - boff[r];
+        double* P = pre + o + r;
+        double* T = tri + o + r;
+        P[0] = 0.0;
+        for (int64_t k = 0; k < nr; ++k) P[k + 1] = P[k] + th[o + k];
+        double tot = P[nr];
+        T[0] = 0.0;
+        for (int64_t a = 0; a < nr; ++a) T[a + 1] = T[a] + th[o + a] * (tot - P[a + 1]);
+    }
+    int64_t m = 0, g = 0;
+    int rc = ORC_OK;
+    for (int r = 0; r < K && rc == ORC_OK; ++r) {
+        for (int s = r; s < K && rc == ORC_OK; ++s) {
+            SbmPair Pp;
+            Pp.r = r; Pp.s = s;
+            Pp.nr = boff[r + 1] - boff[r];
+            Pp.ns = boff[s + 1] - boff[s];
+            Pp.nodes_r = nodes + boff[r];
+            Pp.nodes_s = nodes + boff[s];
+            Pp.th_r = th + boff[r];
+            Pp.th_s = th + boff[s];
+            Pp.pre_r = pre + boff[r] + r;
+            Pp.pre_s = pre + boff[s] + s;
+            Pp.tri_r = tri + boff[r] + r;
+            Pp.tot_s = Pp.pre_s[Pp.ns];
+            Pp.om = omega[(int64_t)r * K + s];
+            int64_t size = r != s ? Pp.nr * Pp.ns : Pp.nr * (Pp.nr - 1) / 2;
+            int64_t nseg = (size + seg - 1) / seg;
+            for (int64_t sg = 0; sg < nseg; ++sg, ++g) {
+                int64_t t0 = sg * seg;
+                int64_t t1 = t0 + seg < size ? t0 + seg : size;
+                int64_t mm = t0;
+                uint32_t j = 0;
+                double Fend = sbm_F(&Pp, t1);
+                while (mm < t1) {
+                    uint32_t x[4];
+                    philox_stream(seed, (uint32_t)g, (uint32_t)((uint64_t)g >> 32), j, ORC_STREAM_SBM, x);
+                    ++j;
+                    uint64_t w01 = (uint64_t)x[0] | ((uint64_t)x[1] << 32);
+                    uint64_t w23 = (uint64_t)x[2] | ((uint64_t)x[3] << 32);
+                    double p = (double)((w01 >> 11) + 1) * (1.0 / 9007199254740992.0);
+                    double V = sbm_F(&Pp, mm) + (-log(p));
+                    if (!(Fend > V)) break;
+                    int64_t lo = mm, hi = t1 - 1;
+                    while (lo < hi) {
+                        int64_t mid = lo + (hi - lo) / 2;
+                        if (sbm_F(&Pp, mid + 1) > V) hi = mid;
+                        else lo = mid + 1;
+                    }
+                    int64_t a, b;
+                    sbm_entry(&Pp, lo, &a, &b);
+                    if (m < max_edges) {
+                        double lam = Pp.om * (Pp.th_r[a] * Pp.th_s[b]);
+                        if (src) src[m] = Pp.nodes_r[a];
+                        if (dst) dst[m] = Pp.nodes_s[b];
+                        if (weight) weight[m] = sbm_weight(lam, w23);
+                    } else if (src || dst || weight) {
+                        rc = ORC_ENOMEM;
+                        break;
+                    }
+                    ++m;
+                    mm = lo + 1;
+                }
+            }
+        }
+    }
+    *m_out = m;
+    free(boff); free(nodes); free(th); free(pre); free(tri);
+    return rc;
+}

@@ -27,7 +27,9 @@ EXPORTS = ("raftgp_workspace_size", "raftgp_embed", "raftgp_select", "raftgp_par
            "raftgp_softmod_loss", "raftgp_centroids", "raftgp_gcn_weights", "raftgp_adam_step",
            "raftgp_batch_workspace_size", "raftgp_batch_plan_create", "raftgp_batch_plan_run",
            "raftgp_batch_plan_candidates", "raftgp_batch_plan_tuning", "raftgp_batch_plan_destroy",
-           "raftgp_partition_batched", "raftgp_bisect_workspace_size", "raftgp_select_bisect")
+           "raftgp_partition_batched", "raftgp_bisect_workspace_size", "raftgp_select_bisect",
+           "raftgp_sbm_workspace_size", "raftgp_sbm_count", "raftgp_sbm_emit", "raftgp_coo_to_csr_workspace_size",
+           "raftgp_coo_to_csr")
 BATCH_SLOTS = 20
 
 
@@ -44,6 +46,11 @@ class EmbedOpts(C.Structure):
 
 class BisectOpts(C.Structure):
     _fields_ = [("eps", C.c_int32), ("iters", C.c_int32), ("reading", C.c_int32), ("seed", C.c_uint64)]
+
+
+class Sbm(C.Structure):
+    _fields_ = [("n", C.c_int64), ("k", C.c_int32), ("block", C.c_void_p), ("theta", C.c_void_p),
+                ("omega", C.c_void_p), ("seed", C.c_uint64)]
 
 
 class BatchOpts(C.Structure):
@@ -142,6 +149,16 @@ def lib():
         L.raftgp_select_bisect.restype = C.c_int
         L.raftgp_select_bisect.argtypes = [C.POINTER(Csr), P, C.c_int32, C.c_int32, C.POINTER(BisectOpts), P,
                                            C.POINTER(C.c_int32), P, C.c_size_t, P]
+        L.raftgp_sbm_workspace_size.restype = C.c_size_t
+        L.raftgp_sbm_workspace_size.argtypes = [C.c_int64, C.c_int32]
+        L.raftgp_sbm_count.restype = C.c_int
+        L.raftgp_sbm_count.argtypes = [C.POINTER(Sbm), C.POINTER(C.c_int64), P, C.c_size_t, P]
+        L.raftgp_sbm_emit.restype = C.c_int
+        L.raftgp_sbm_emit.argtypes = [C.POINTER(Sbm), P, P, P, C.c_int64, P, C.c_size_t, P]
+        L.raftgp_coo_to_csr_workspace_size.restype = C.c_size_t
+        L.raftgp_coo_to_csr_workspace_size.argtypes = [C.c_int64]
+        L.raftgp_coo_to_csr.restype = C.c_int
+        L.raftgp_coo_to_csr.argtypes = [C.c_int64, C.c_int64, P, P, P, P, P, C.c_size_t, P]
         L.raftgp_last_error.restype = C.c_char_p
         L.raftgp_last_error.argtypes = []
         L.raftgp_version.restype = C.c_char_p

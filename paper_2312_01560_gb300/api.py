@@ -443,3 +443,43 @@ def select_bisect(g: DeviceGraph, Z: torch.Tensor, eps=5, iters=50, reading="lit
                                      C.c_void_p(labels.data_ptr()), C.byref(k), C.c_void_p(ws.data_ptr()),
                                      ws.numel(), _stream(stream)))
     return labels, k.value
+
+
+# ---- Algorithm 2: graphs from the SBM of Definition 1 (argument marshalling only) ----
+def sbm_sample(block: torch.Tensor, theta: torch.Tensor, omega: torch.Tensor, seed=0, weights=False, stream=None):
+    """One draw of an undirected graph from the degree-corrected SBM (A_ij ~ Pois(theta_i
+    theta_j Omega_{c_i c_j}), i < j) by Algorithm 2 on the device: returns (src, dst) int32
+    edge lists (and the values A_ij >= 1 with weights=True) in the order (block pair,
+    segment, draw)."""
+    dev = block.device
+    blk = block.to(torch.int32).contiguous()
+    th = theta.to(torch.float64).contiguous()
+    om = omega.to(torch.float64).contiguous()
+    p = _abi.Sbm()
+    p.n, p.k, p.seed = int(blk.numel()), int(om.shape[0]), int(seed)
+    p.block, p.theta, p.omega = blk.data_ptr(), th.data_ptr(), om.data_ptr()
+    ws = _workspace(int(lib().raftgp_sbm_workspace_size(p.n, p.k)), dev)
+    m = C.c_int64(0)
+    check(lib().raftgp_sbm_count(C.byref(p), C.byref(m), C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    src = torch.empty(max(m.value, 1), dtype=torch.int32, device=dev)
+    dst = torch.empty(max(m.value, 1), dtype=torch.int32, device=dev)
+    w = torch.empty(max(m.value, 1), dtype=torch.int32, device=dev) if weights else None
+    check(lib().raftgp_sbm_emit(C.byref(p), C.c_void_p(src.data_ptr()), C.c_void_p(dst.data_ptr()),
+                                C.c_void_p(w.data_ptr()) if weights else None, m.value, C.c_void_p(ws.data_ptr()),
+                                ws.numel(), _stream(stream)))
+    src, dst = src[:m.value], dst[:m.value]
+    return (src, dst, w[:m.value]) if weights else (src, dst)
+
+
+def coo_to_csr(n: int, src: torch.Tensor, dst: torch.Tensor, stream=None) -> DeviceGraph:
+    """The symmetric CSR (int64 row_ptr, every row sorted) of undirected edges (src, dst)."""
+    dev = src.device
+    m = int(src.numel())
+    row_ptr = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    col = torch.empty(max(2 * m, 1), dtype=torch.int32, device=dev)
+    ws = _workspace(int(lib().raftgp_coo_to_csr_workspace_size(n)), dev)
+    s32, d32 = src.to(torch.int32).contiguous(), dst.to(torch.int32).contiguous()
+    check(lib().raftgp_coo_to_csr(int(n), m, C.c_void_p(s32.data_ptr()), C.c_void_p(d32.data_ptr()),
+                                  C.c_void_p(row_ptr.data_ptr()), C.c_void_p(col.data_ptr()),
+                                  C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return DeviceGraph(int(n), row_ptr, col[:2 * m])

@@ -43,19 +43,6 @@ static raftgp_status cuda_fail(cudaError_t e, const char* where) {
 }
 
 // Bump allocator over the caller's workspace (base == nullptr measures only).
-struct Carver {
-    char* base;
-    size_t off = 0;
-    explicit Carver(void* b) : base((char*)b) {}
-    template <typename T>
-    T* take(size_t count) {
-        off = (off + 255) & ~(size_t)255;
-        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
-        off += count * sizeof(T);
-        return p;
-    }
-};
-
 static size_t elem_size(int dtype) { return dtype == RAFTGP_BF16 ? 2 : 4; }
 static bool width_ok(int w) { return w == 32 || w == 64 || w == 128; }
 
@@ -1230,6 +1217,85 @@ raftgp_status raftgp_select_bisect(const raftgp_csr* g, const void* Z, int32_t d
     k_iota<<<(unsigned)std::min<int64_t>((g->n + 255) / 256, 4096), 256, 0, s>>>(b.perm, g->n);
     cudaError_t e = launch_bisect(g, Z, z_dtype, d, b, o->iters, o->seed, o->reading, labels, k_out, s);
     if (e != cudaSuccess) return cuda_fail(e, "bisect");
+    return RAFTGP_OK;
+}
+
+// ---- Algorithm 2 sampler and the CSR build ----
+static raftgp_status check_sbm(const raftgp_sbm* p) {
+    if (!p) return fail(RAFTGP_EINVAL, "sbm parameters are NULL");
+    if (p->n < 1) return fail(RAFTGP_EINVAL, "sbm n must be >= 1");
+    if (p->n > (int64_t)INT32_MAX - 1) return fail(RAFTGP_EUNSUPPORTED, "n above 2^31-2 is not supported");
+    if (p->k < 1 || p->k > 65535) return fail(RAFTGP_EINVAL, "sbm k must be in 1..65535");
+    if (!p->block || !p->theta || !p->omega) return fail(RAFTGP_EINVAL, "sbm arrays are NULL");
+    return RAFTGP_OK;
+}
+
+size_t raftgp_sbm_workspace_size(int64_t n, int32_t k) {
+    Carver c(nullptr);
+    carve_sbm(c, n < 1 ? 1 : n, k < 1 ? 1 : k);
+    return c.off + 256;
+}
+
+raftgp_status raftgp_sbm_count(const raftgp_sbm* p, int64_t* m, void* ws, size_t ws_bytes, raftgp_stream_t stream) {
+    raftgp_status st = check_sbm(p);
+    if (st) return st;
+    if (!m || !ws) return fail(RAFTGP_EINVAL, "NULL argument");
+    if (ws_bytes < raftgp_sbm_workspace_size(p->n, p->k)) return fail(RAFTGP_ENOMEM, "workspace too small");
+    Carver c(ws);
+    SbmWs w = carve_sbm(c, p->n, p->k);
+    int64_t G = 0;
+    cudaError_t e = sbm_count(p, w, &G, m, (cudaStream_t)stream);
+    if (e == cudaErrorInvalidValue) return fail(RAFTGP_EINVAL, "sbm: a block outside [0, k) or a negative theta/Omega");
+    if (e != cudaSuccess) return cuda_fail(e, "sbm count");
+    return RAFTGP_OK;
+}
+
+raftgp_status raftgp_sbm_emit(const raftgp_sbm* p, int32_t* src, int32_t* dst, int32_t* weight, int64_t m, void* ws,
+                              size_t ws_bytes, raftgp_stream_t stream) {
+    raftgp_status st = check_sbm(p);
+    if (st) return st;
+    if ((m > 0 && (!src || !dst)) || !ws) return fail(RAFTGP_EINVAL, "NULL argument");
+    if (ws_bytes < raftgp_sbm_workspace_size(p->n, p->k)) return fail(RAFTGP_ENOMEM, "workspace too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    Carver c(ws);
+    SbmWs w = carve_sbm(c, p->n, p->k);
+    // the segment and edge counts the count pass left in the workspace
+    const int64_t npairs = (int64_t)p->k * (p->k + 1) / 2;
+    unsigned long long G = 0, mm = 0;
+    cudaMemcpyAsync(&G, w.pincl + (npairs - 1), sizeof(G), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "sbm emit");
+    if ((int64_t)G > sbm_max_segments(p->n, p->k)) return fail(RAFTGP_EINVAL, "sbm emit without a count pass");
+    if (G > 0) {
+        cudaMemcpyAsync(&mm, w.seg_incl + (G - 1), sizeof(mm), cudaMemcpyDeviceToHost, s);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "sbm emit");
+    }
+    if ((int64_t)mm != m) return fail(RAFTGP_EINVAL, "m = %lld differs from the count pass (%lld)", (long long)m,
+                                      (long long)mm);
+    e = sbm_emit(p, w, (int64_t)G, src, dst, weight, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sbm emit");
+    return RAFTGP_OK;
+}
+
+size_t raftgp_coo_to_csr_workspace_size(int64_t n) {
+    Carver c(nullptr);
+    carve_csr_build(c, n < 1 ? 1 : n);
+    return c.off + 256;
+}
+
+raftgp_status raftgp_coo_to_csr(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, int64_t* row_ptr,
+                                int32_t* col, void* ws, size_t ws_bytes, raftgp_stream_t stream) {
+    if (n < 1 || n > (int64_t)INT32_MAX - 1) return fail(RAFTGP_EINVAL, "n must be in 1..2^31-2");
+    if (m < 0 || 2 * m >= ((int64_t)1 << 31)) return fail(RAFTGP_EUNSUPPORTED, "2 m must be below 2^31");
+    if (!row_ptr || !ws || (m > 0 && (!src || !dst || !col))) return fail(RAFTGP_EINVAL, "NULL argument");
+    if (ws_bytes < raftgp_coo_to_csr_workspace_size(n)) return fail(RAFTGP_ENOMEM, "workspace too small");
+    Carver c(ws);
+    CsrBuildWs w = carve_csr_build(c, n);
+    uint32_t herr = 0;
+    cudaError_t e = coo_to_csr(n, m, src, dst, row_ptr, col, w, &herr, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "coo to csr");
+    if (herr & (DERR_COL_RANGE | DERR_SELF_LOOP)) return fail(RAFTGP_EINVAL, "an endpoint outside [0, n) or a self loop");
+    if (herr & DERR_ROW_PTR) return fail(RAFTGP_EUNSUPPORTED, "a row longer than 16384");
     return RAFTGP_OK;
 }
 

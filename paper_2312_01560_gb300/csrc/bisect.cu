@@ -36,6 +36,7 @@ __device__ __forceinline__ uint64_t bs_draw(uint64_t seed, int t, uint64_t id) {
 // Device-wide inclusive scan of unsigned 64-bit values (three launches).
 // ------------------------------------------------------------------------------------
 constexpr int SC_T = 1024, SC_ITEMS = 4, SC_TILE = SC_T * SC_ITEMS;
+static_assert(SC_TILE == SCAN_TILE, "the tile count callers reserve");
 
 __device__ unsigned long long sc_block_incl(unsigned long long v, unsigned long long* ws, unsigned long long* total) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -105,8 +106,8 @@ __global__ void k_scan_add(unsigned long long* out, int64_t n, const unsigned lo
         out[i] += tile_off[i / SC_TILE];
 }
 
-static void scan_incl(const unsigned long long* in, int64_t n, unsigned long long* out, unsigned long long* tiles,
-                      cudaStream_t s) {
+void scan_incl(const unsigned long long* in, int64_t n, unsigned long long* out, unsigned long long* tiles,
+               cudaStream_t s) {
     if (n <= 0) return;
     const int64_t nt = (n + SC_TILE - 1) / SC_TILE;
     k_scan_tiles<<<(unsigned)nt, SC_T, 0, s>>>(in, n, out, tiles);

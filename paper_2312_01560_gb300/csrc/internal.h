@@ -11,6 +11,21 @@
 namespace raftgp {
 
 int num_sms();
+
+// Carves typed, 256-byte aligned arrays out of a caller-owned workspace; with a null base
+// it only adds up the size.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base((char*)b) {}
+    template <typename T>
+    T* take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+};
 // Records the message returned by raftgp_last_error() and returns st.
 raftgp_status set_error(raftgp_status st, const char* fmt, ...);
 
@@ -54,6 +69,37 @@ cudaError_t launch_spmm_flat(int agg, int64_t n, int rp_bits, const void* row_pt
                              const void* X, void* out, void* stage, int* work, cudaStream_t s);
 // CSR of A + I (row i: i, then its neighbours): rp_self has n + 1 entries, col_self nnz + n.
 void launch_self_csr(const raftgp_csr* g, int64_t* rp_self, int32_t* col_self, cudaStream_t s);
+
+// ---- device-wide inclusive scan of unsigned 64-bit values (bisect.cu) -------------------
+// `tiles` holds ceil(n / SCAN_TILE) values; in and out may not overlap.
+constexpr int64_t SCAN_TILE = 4096;
+void scan_incl(const unsigned long long* in, int64_t n, unsigned long long* out, unsigned long long* tiles,
+               cudaStream_t s);
+
+// ---- Algorithm 2 SBM sampler and the CSR build of its output (sbm.cu) -------------------
+struct SbmWs {
+    uint32_t* err;
+    unsigned long long *bcnt, *bincl;   // block sizes, inclusive scan
+    int32_t* nodes;                     // nodes grouped by block (ascending in a block)
+    double *th, *pre, *tri;             // theta in that order; per-block prefix sums
+    unsigned long long *pseg, *pincl;   // segments per block pair, inclusive scan
+    unsigned long long *seg_cnt, *seg_incl;   // edges per segment, inclusive scan
+    unsigned long long* tiles;
+};
+int64_t sbm_max_segments(int64_t n, int K);
+SbmWs carve_sbm(Carver& c, int64_t n, int K);
+cudaError_t sbm_count(const raftgp_sbm* p, const SbmWs& w, int64_t* G_out, int64_t* m_out, cudaStream_t s);
+cudaError_t sbm_emit(const raftgp_sbm* p, const SbmWs& w, int64_t G, int32_t* src, int32_t* dst, int32_t* weight,
+                     cudaStream_t s);
+struct CsrBuildWs {
+    uint32_t* err;
+    unsigned long long *deg, *incl, *fill, *tiles;
+    int* long_rows;
+    int* n_long;
+};
+CsrBuildWs carve_csr_build(Carver& c, int64_t n);
+cudaError_t coo_to_csr(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, int64_t* row_ptr, int32_t* col,
+                       const CsrBuildWs& w, uint32_t* herr, cudaStream_t s);
 
 // ---- dense layer on tensor cores (dense_tc.cu) -----------------------------------------
 void launch_w_split(const float* W, int lin, int lout, __nv_bfloat16* whi, __nv_bfloat16* wlo, cudaStream_t s);
