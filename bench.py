@@ -324,6 +324,93 @@ def bench_sbm(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_stream(args):
+    """Streaming updates (Section III-D) on the 1M-node graph: the FP32 NCut embedding with
+    a two-layer GCN (64-64-32) kept on the device; one step = one batch of new random edges
+    (1,000) merged into the graph and the affected rows re-embedded.  Reported beside it: the
+    rows recomputed per stage and the time of a full embedding of the same graph."""
+    import torch
+    from inputs.dcsbm import workload
+    from paper_2312_01560_gb300 import api
+    wl = WORKLOAD
+    g = workload(wl["graph"], seed=wl["graph_seed"])
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    dims = (64, 64, 32)
+    batch = 1000
+    total = args.steps + max(args.warmup, 1)
+    dg = api.DeviceGraph.from_host(g, dev, row_ptr_bits=64)
+    st = api.Stream(dg, dims=dims, seed=1, nnz_cap=g.nnz + 2 * batch * (total + 1) + 64)
+    rp = np.asarray(g.row_ptr, dtype=np.int64)
+    present = set()
+    rng = np.random.default_rng(5)
+    batches = []
+    for _ in range(total):
+        out = set()
+        while len(out) < batch:
+            u, v = (int(x) for x in rng.integers(0, g.n, 2))
+            a, b = min(u, v), max(u, v)
+            if a == b or (a, b) in out or (a, b) in present:
+                continue
+            row = g.col[rp[a]:rp[a + 1]]
+            k = np.searchsorted(row, b)
+            if k < len(row) and row[k] == b:
+                continue
+            out.add((a, b))
+        present |= out
+        e = np.array(sorted(out), dtype=np.int32)
+        batches.append((torch.as_tensor(e[:, 0], device=dev), torch.as_tensor(e[:, 1], device=dev)))
+    for w in range(max(args.warmup, 1)):
+        st.add_edges(*batches[w])
+    torch.cuda.synchronize()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    sampler.start()
+    t0 = time.perf_counter()
+    aff = None
+    for k in range(args.steps):
+        aff = st.add_edges(*batches[max(args.warmup, 1) + k])
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    clocks = sampler.stop()
+    # small batches: how many rows one or ten new edges reach, and the update time
+    small = {}
+    extra = set()
+    for b in (1, 10):
+        out = []
+        while len(out) < b:
+            u, v = (int(x) for x in rng.integers(0, g.n, 2))
+            a, c = min(u, v), max(u, v)
+            if a == c or (a, c) in present or (a, c) in extra:
+                continue
+            row = g.col[rp[a]:rp[a + 1]]
+            k = np.searchsorted(row, c)
+            if k < len(row) and row[k] == c:
+                continue
+            extra.add((a, c))
+            out.append((a, c))
+        e = np.array(out, dtype=np.int32)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        aff_b = st.add_edges(torch.as_tensor(e[:, 0], device=dev), torch.as_tensor(e[:, 1], device=dev))
+        torch.cuda.synchronize()
+        small[str(b)] = {"ms": (time.perf_counter() - t2) * 1e3, "recomputed_rows_per_stage": aff_b}
+    full_g = st.graph()
+    api.embed(full_g, "ncut", dims, "f32", seed=1)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for _ in range(3):
+        api.embed(full_g, "ncut", dims, "f32", seed=1)
+    torch.cuda.synchronize()
+    full_ms = (time.perf_counter() - t1) * 1e3 / 3
+    line = {"metric": "streaming insert edges/s at 1M nodes (embedding kept current)", "value": batch / (ms * 1e-3),
+            "unit": "edges/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "dcsbm-1m, NCut operator, FP32, GCN 64-64-32; batches of 1,000 random new edges",
+                       "timing": "host clock around synchronised updates"},
+            "recomputed_rows_per_stage": aff, "full_embedding_ms": full_ms, "small_batches": small, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def bench_batched(args):
     """Times replays of one captured plan that partitions 512 DC-SBM graphs of uneven size
     (N log-uniform in [1,000, 50,000], K = round(N^0.35), exponent 2.5, mean degree uniform in
@@ -448,7 +535,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="bf16", choices=["bf16", "f32", "diff", "batched", "bisect", "sbm"],
+    ap.add_argument("--form", default="bf16", choices=["bf16", "f32", "diff", "batched", "bisect", "sbm", "stream"],
                     help="bf16/f32: the partition benchmark; diff: Adam tuning steps of the GNN weights "
                          "(N=200,000, GNN 128-128-64, --steps Adam steps, default 200); batched: 512 uneven graphs "
                          "partitioned by one captured plan (--steps replays); bisect: the 1M-node partition "
@@ -466,6 +553,8 @@ def main():
         return bench_batched(args)
     if args.form == "sbm":
         return bench_sbm(args)
+    if args.form == "stream":
+        return bench_stream(args)
     if args.form == "bisect":
         return bench_bisect(args)
 

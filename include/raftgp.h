@@ -370,6 +370,34 @@ size_t raftgp_coo_to_csr_workspace_size(int64_t n);
 raftgp_status raftgp_coo_to_csr(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, int64_t* row_ptr,
                                 int32_t* col, void* ws, size_t ws_bytes, raftgp_stream_t stream);
 
+/* ---- Streaming updates (Section III-D) ----
+ * A stream owns a graph and the FP32 embedding of it with the NCut operator M (Eq. 5, Eq. 6):
+ * Theta' = Theta_j d_j^-1/2, every GCN gather's input and Z, all inside the caller's workspace
+ * (raftgp_stream_workspace_size; the CSR is double-buffered with room for nnz_cap stored
+ * entries).  raftgp_stream_create embeds the graph in full (rows of g sorted, as everywhere).
+ * raftgp_stream_add_edges adds m new undirected edges (src[e], dst[e], device int32): it
+ * rejects (RAFTGP_EINVAL, stream unchanged) an endpoint outside [0, n), a self loop, an edge
+ * already present or listed twice; RAFTGP_ENOMEM past nnz_cap.  It recomputes only the rows
+ * whose values change -- S_0 = V' u N(V') for the projection (V' the endpoints of the new
+ * edges), S_k = S_{k-1} u N(S_{k-1}) for GCN layer k -- with the same per-row kernels as a full
+ * embedding, so Z equals raftgp_embed on the new graph bit for bit.  Synchronises.
+ * raftgp_stream_info returns n, the stored-entry count and, per stage 0..n_layers, the rows
+ * the last update recomputed (host; any pointer may be NULL).  raftgp_stream_copy copies the
+ * current graph (row_ptr int64[n + 1], col int32[nnz]) and Z (FP32 n x d) into caller
+ * buffers (device; any may be NULL), asynchronously on `stream`.  The modularity
+ * operators and BF16 storage are not streamed (RAFTGP_EUNSUPPORTED): 2e and d^T Theta reach
+ * every row. */
+typedef struct raftgp_stream raftgp_stream;   /* opaque */
+size_t raftgp_stream_workspace_size(int64_t n, int64_t nnz_cap, const raftgp_embed_opts* o);
+raftgp_status raftgp_stream_create(const raftgp_csr* g, const raftgp_embed_opts* o, int64_t nnz_cap, void* ws,
+                                   size_t ws_bytes, raftgp_stream** out, raftgp_stream_t stream);
+raftgp_status raftgp_stream_add_edges(raftgp_stream* s, const int32_t* src, const int32_t* dst, int64_t m,
+                                      raftgp_stream_t stream);
+raftgp_status raftgp_stream_info(const raftgp_stream* s, int64_t* n, int64_t* nnz, int64_t* affected);
+raftgp_status raftgp_stream_copy(const raftgp_stream* s, int64_t* row_ptr, int32_t* col, float* Z,
+                                 raftgp_stream_t stream);
+void raftgp_stream_destroy(raftgp_stream* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,7 +29,8 @@ EXPORTS = ("raftgp_workspace_size", "raftgp_embed", "raftgp_select", "raftgp_par
            "raftgp_batch_plan_candidates", "raftgp_batch_plan_tuning", "raftgp_batch_plan_destroy",
            "raftgp_partition_batched", "raftgp_bisect_workspace_size", "raftgp_select_bisect",
            "raftgp_sbm_workspace_size", "raftgp_sbm_count", "raftgp_sbm_emit", "raftgp_coo_to_csr_workspace_size",
-           "raftgp_coo_to_csr")
+           "raftgp_coo_to_csr", "raftgp_stream_workspace_size", "raftgp_stream_create", "raftgp_stream_add_edges",
+           "raftgp_stream_info", "raftgp_stream_copy", "raftgp_stream_destroy")
 BATCH_SLOTS = 20
 
 
@@ -159,6 +160,19 @@ def lib():
         L.raftgp_coo_to_csr_workspace_size.argtypes = [C.c_int64]
         L.raftgp_coo_to_csr.restype = C.c_int
         L.raftgp_coo_to_csr.argtypes = [C.c_int64, C.c_int64, P, P, P, P, P, C.c_size_t, P]
+        L.raftgp_stream_workspace_size.restype = C.c_size_t
+        L.raftgp_stream_workspace_size.argtypes = [C.c_int64, C.c_int64, C.POINTER(EmbedOpts)]
+        L.raftgp_stream_create.restype = C.c_int
+        L.raftgp_stream_create.argtypes = [C.POINTER(Csr), C.POINTER(EmbedOpts), C.c_int64, P, C.c_size_t,
+                                           C.POINTER(P), P]
+        L.raftgp_stream_add_edges.restype = C.c_int
+        L.raftgp_stream_add_edges.argtypes = [P, P, P, C.c_int64, P]
+        L.raftgp_stream_info.restype = C.c_int
+        L.raftgp_stream_info.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.raftgp_stream_copy.restype = C.c_int
+        L.raftgp_stream_copy.argtypes = [P, P, P, P, P]
+        L.raftgp_stream_destroy.restype = None
+        L.raftgp_stream_destroy.argtypes = [P]
         L.raftgp_last_error.restype = C.c_char_p
         L.raftgp_last_error.argtypes = []
         L.raftgp_version.restype = C.c_char_p

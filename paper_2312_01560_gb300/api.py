@@ -483,3 +483,69 @@ def coo_to_csr(n: int, src: torch.Tensor, dst: torch.Tensor, stream=None) -> Dev
                                   C.c_void_p(row_ptr.data_ptr()), C.c_void_p(col.data_ptr()),
                                   C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
     return DeviceGraph(int(n), row_ptr, col[:2 * m])
+
+
+# ---- streaming updates (Section III-D; argument marshalling only) ----
+class Stream:
+    """A graph and its FP32 NCut embedding kept on the device; add_edges() recomputes only the
+    rows whose values change (the result equals a full embedding of the new graph)."""
+
+    def __init__(self, g: DeviceGraph, dims=(64, 64, 32), seed=1, nnz_cap=None, W=None, stream=None, op="ncut",
+                 dtype="f32"):
+        self.device = g.col.device
+        self.dims = tuple(dims)
+        self.n = g.n
+        self._h = C.c_void_p()
+        if W is not None:
+            W = [w.to(self.device, torch.float32).contiguous() for w in W]
+        self._W = W
+        self._o = embed_opts(op, dims, dtype, seed, None, W, None)
+        cap = int(nnz_cap if nnz_cap is not None else 2 * g.nnz + 1024)
+        nbytes = int(lib().raftgp_stream_workspace_size(g.n, cap, C.byref(self._o)))
+        self._ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=self.device)   # owned by this stream
+        csr = g.csr()
+        check(lib().raftgp_stream_create(C.byref(csr), C.byref(self._o), cap, C.c_void_p(self._ws.data_ptr()),
+                                         self._ws.numel(), C.byref(self._h), _stream(stream)))
+
+    def add_edges(self, src: torch.Tensor, dst: torch.Tensor, stream=None):
+        s = src.to(self.device, torch.int32).contiguous()
+        d = dst.to(self.device, torch.int32).contiguous()
+        check(lib().raftgp_stream_add_edges(self._h, C.c_void_p(s.data_ptr()), C.c_void_p(d.data_ptr()),
+                                            int(s.numel()), _stream(stream)))
+        return self.affected()
+
+    def _info(self):
+        n, nnz = C.c_int64(0), C.c_int64(0)
+        aff = (C.c_int64 * (_abi.MAX_LAYERS + 1))()
+        check(lib().raftgp_stream_info(self._h, C.byref(n), C.byref(nnz), aff))
+        return n.value, nnz.value, [aff[k] for k in range(len(self.dims))]
+
+    def affected(self):
+        """Rows recomputed by the last update, per stage (projection, then each GCN layer)."""
+        return self._info()[2]
+
+    def graph(self, stream=None) -> DeviceGraph:
+        """A copy of the current graph (int64 row pointers, sorted rows)."""
+        n, nnz, _ = self._info()
+        rp = torch.empty(n + 1, dtype=torch.int64, device=self.device)
+        col = torch.empty(max(nnz, 1), dtype=torch.int32, device=self.device)
+        check(lib().raftgp_stream_copy(self._h, C.c_void_p(rp.data_ptr()), C.c_void_p(col.data_ptr()), None,
+                                       _stream(stream)))
+        return DeviceGraph(n, rp, col[:nnz])
+
+    def embedding(self, stream=None) -> torch.Tensor:
+        """A copy of the current Z (n x dims[-1], FP32)."""
+        Z = torch.empty((self.n, self.dims[-1]), dtype=torch.float32, device=self.device)
+        check(lib().raftgp_stream_copy(self._h, None, None, C.c_void_p(Z.data_ptr()), _stream(stream)))
+        return Z
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().raftgp_stream_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -65,14 +65,16 @@ __global__ void k_degrees(int64_t n, int64_t nnz, const int32_t* rp32, const int
 // ------------------------------------------------------------------------------------
 template <typename T>
 __global__ void k_theta(int64_t n, int L, uint64_t seed, const float* user_theta, const float* colscale,
-                        const int32_t* deg, T* theta, double* partial, const int32_t* local_row) {
+                        const int32_t* deg, T* theta, double* partial, const int32_t* local_row,
+                        const int32_t* rows) {
     const int tpr = L / 4;                       // threads per row
     const int slots = blockDim.x / tpr;          // rows per block iteration
     const int q = threadIdx.x % tpr;
     const int slot = threadIdx.x / tpr;
     const float sigma = rsqrtf((float)L);
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int64_t j = (int64_t)blockIdx.x * slots + slot; j < n; j += (int64_t)gridDim.x * slots) {
+    for (int64_t jq = (int64_t)blockIdx.x * slots + slot; jq < n; jq += (int64_t)gridDim.x * slots) {
+        const int64_t j = rows ? (int64_t)rows[jq] : jq;   // with a row list, n counts its entries
         float g[4];
         if (user_theta) {
 #pragma unroll
@@ -163,6 +165,8 @@ struct LayerArgs {
     void* stage;             // optional N x LIN in T: the activated row before W
     const int32_t* heavy;    // rows gathered by k_spmm_heavy (null: every row by k_spmm_layer)
     const int* heavy_count;
+    const int32_t* rows;     // the rows k_spmm_layer gathers (null: 0 .. n-1)
+    int64_t nrows;
 };
 
 // Rows with more neighbours than this are gathered by a whole CTA (k_spmm_heavy) instead of
@@ -354,19 +358,24 @@ __global__ void __launch_bounds__(256, 4) k_spmm_layer(LayerArgs a, const T* __r
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     // Software pipeline over the warp's rows: the next row's bounds and first 32 column indices
     // are loaded while this row's first gathers are in flight.
-    int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    // rows are visited by index q (row a.rows[q] with a list, else q)
+    const int64_t count = a.rows ? a.nrows : a.n;
+    int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int64_t beg = 0, end = 0;
     int32_t my_col = 0;
-    if (i < a.n) {
-        beg = a.rp64 ? a.rp64[i] : a.rp32[i];
-        end = a.rp64 ? a.rp64[i + 1] : a.rp32[i + 1];
+    if (q < count) {
+        const int64_t r0 = a.rows ? (int64_t)a.rows[q] : q;
+        beg = a.rp64 ? a.rp64[r0] : a.rp32[r0];
+        end = a.rp64 ? a.rp64[r0 + 1] : a.rp32[r0 + 1];
         const int c0 = (a.heavy && end - beg > HEAVY_DEG) ? 0 : (int)(end - beg < 32 ? end - beg : 32);
         my_col = lane < c0 ? __ldg(a.col + beg + lane) : 0;
     }
-    for (; i < a.n; i += nwarps) {
-        const int64_t inext = i + nwarps;
+    for (; q < count; q += nwarps) {
+        const int64_t i = a.rows ? (int64_t)a.rows[q] : q;
+        const int64_t qnext = q + nwarps;
         int64_t nbeg = 0, nend = 0;
-        if (inext < a.n) {
+        if (qnext < count) {
+            const int64_t inext = a.rows ? (int64_t)a.rows[qnext] : qnext;
             nbeg = a.rp64 ? a.rp64[inext] : a.rp32[inext];
             nend = a.rp64 ? a.rp64[inext + 1] : a.rp32[inext + 1];
         }
@@ -498,17 +507,23 @@ int theta_blocks(int64_t n) {
 }
 
 void launch_theta(int64_t n, int L, int dtype, uint64_t seed, const float* user_theta, const float* colscale, const int32_t* local_row,
-                  const int32_t* deg, void* theta, double* partial, float* gvec, cudaStream_t s) {
+                  const int32_t* deg, void* theta, double* partial, float* gvec, cudaStream_t s, const int32_t* rows,
+                  int64_t nrows) {
     const int threads = 256;
+    if (rows) {
+        n = nrows;          // the listed rows only (no rank-one partials)
+        partial = nullptr;
+        if (n == 0) return;
+    }
     const int blocks = theta_blocks(n);
     const size_t sm = partial ? (size_t)(threads / (L / 4)) * L * sizeof(float) : 0;
     ProfScope ps(s, PF_THETA, partial ? 2 : 1);
     if (dtype == RAFTGP_BF16)
         k_theta<__nv_bfloat16><<<blocks, threads, sm, s>>>(n, L, seed, user_theta, colscale, deg,
-                                                           (__nv_bfloat16*)theta, partial, local_row);
+                                                           (__nv_bfloat16*)theta, partial, local_row, rows);
     else
         k_theta<float><<<blocks, threads, sm, s>>>(n, L, seed, user_theta, colscale, deg, (float*)theta, partial,
-                                                   local_row);
+                                                   local_row, rows);
     if (partial) k_rank1_finish<<<(L + 127) / 128, 128, 0, s>>>(blocks, L, partial, gvec);
 }
 
@@ -530,12 +545,13 @@ static cudaError_t launch_layer_t(const LayerArgs& a, const void* X, cudaStream_
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (per_sm < 1) per_sm = 1;
-    int64_t blocks = (a.n + (threads / 32) - 1) / (threads / 32);
+    const int64_t count = a.rows ? a.nrows : a.n;
+    int64_t blocks = (count + (threads / 32) - 1) / (threads / 32);
     const int64_t cap = (int64_t)num_sms() * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     ProfScope ps(s, AGG == AGG_GCN ? PF_SPMM_GCN : PF_SPMM_PROJ, a.heavy ? 2 : 1);
-    kern<<<(unsigned)blocks, threads, smem, s>>>(a, reinterpret_cast<const T*>(X));
+    if (count > 0) kern<<<(unsigned)blocks, threads, smem, s>>>(a, reinterpret_cast<const T*>(X));
     if (a.heavy) {
         const size_t hsmem = (size_t)((a.W ? LIN * a.lout : 0) + LIN + 2 * 8 * LIN) * sizeof(float);
         auto hk = k_spmm_heavy<AGG, T, LIN>;
@@ -572,10 +588,12 @@ static cudaError_t launch_layer_a(int agg, const LayerArgs& a, int lin, const vo
 cudaError_t launch_layer(int agg, int dtype, const raftgp_csr* g, const int32_t* deg, const float* rowscale,
                          const float* gvec, int act, const float* W, int lin, int lout, const float* postscale,
                          const void* X, void* out, void* stage, const int32_t* heavy, const int* heavy_count,
-                         cudaStream_t s) {
+                         cudaStream_t s, const int32_t* rows, int64_t nrows) {
     LayerArgs a;
     a.heavy = heavy;
     a.heavy_count = heavy_count;
+    a.rows = rows;
+    a.nrows = nrows;
     a.n = g->n;
     a.rp32 = g->row_ptr_bits == 32 ? (const int32_t*)g->row_ptr : nullptr;
     a.rp64 = g->row_ptr_bits == 64 ? (const int64_t*)g->row_ptr : nullptr;

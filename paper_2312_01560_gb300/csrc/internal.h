@@ -53,13 +53,15 @@ enum { AGG_NCUT_ = 0, AGG_MOD_FULL_ = 1, AGG_MOD_REDUCED_ = 2, AGG_GCN_ = 3 };
 void launch_degrees(const raftgp_csr* g, int32_t* deg, float* rs, float* rsh, uint32_t* err, int32_t* heavy,
                     int* heavy_count, cudaStream_t s);
 int theta_blocks(int64_t n);
+// With `rows`, only the listed rows of Theta are written (nrows of them; no rank-one partials).
 void launch_theta(int64_t n, int L, int dtype, uint64_t seed, const float* user_theta, const float* colscale, const int32_t* local_row,
-                  const int32_t* deg, void* theta, double* partial, float* gvec, cudaStream_t s);
+                  const int32_t* deg, void* theta, double* partial, float* gvec, cudaStream_t s,
+                  const int32_t* rows = nullptr, int64_t nrows = 0);
 void launch_weights(int layer, int lin, int lout, uint64_t seed, float* W, cudaStream_t s);
 cudaError_t launch_layer(int agg, int dtype, const raftgp_csr* g, const int32_t* deg, const float* rowscale,
                          const float* gvec, int act, const float* W, int lin, int lout, const float* postscale,
                          const void* X, void* out, void* stage, const int32_t* heavy, const int* heavy_count,
-                         cudaStream_t s);
+                         cudaStream_t s, const int32_t* rows = nullptr, int64_t nrows = 0);
 // BF16 gather-only layers (no fused W, not the reduced operator) as a flat stream of stored
 // entries staged by cp.async (spmm_flat.cu).  `work` is a chunk counter the launch zeroes;
 // nnz_g is the graph's stored-entry count (2e) for the modularity term.
@@ -98,6 +100,12 @@ struct CsrBuildWs {
     int* n_long;
 };
 CsrBuildWs carve_csr_build(Carver& c, int64_t n);
+// Sorts every CSR row (or those with only[i] != 0) in place; long_rows holds n entries; a
+// row longer than 16384 sets DERR_ROW_PTR in *err and stays unsorted.
+cudaError_t sort_csr_rows(const int64_t* row_ptr, int64_t n, int32_t* col, const uint8_t* only, int* long_rows,
+                          int* n_long, uint32_t* err, cudaStream_t s);
+// Blocks for a grid-stride loop over `items` (at most 16 per SM).
+int grid_for(int64_t items, int threads);
 cudaError_t coo_to_csr(int64_t n, int64_t m, const int32_t* src, const int32_t* dst, int64_t* row_ptr, int32_t* col,
                        const CsrBuildWs& w, uint32_t* herr, cudaStream_t s);
 

@@ -155,16 +155,25 @@ __global__ void k_sbm_fill(const int32_t* block, const double* theta, int64_t n,
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < K; r += warps) {
         int64_t pos = r == 0 ? 0 : (int64_t)bincl[r - 1];
-        for (int64_t base = 0; base < n; base += 32) {
-            const int64_t i = base + lane;
-            const bool mine = i < n && block[i] == r;
-            const unsigned m = __ballot_sync(0xffffffffu, mine);
-            if (mine) {
-                const int64_t q = pos + __popc(m & ((1u << lane) - 1u));
-                nodes[q] = (int32_t)i;
-                th[q] = theta[i];
+        for (int64_t base = 0; base < n; base += 256) {
+            int32_t c[8];   // eight independent loads in flight, then the ballots in order
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int64_t i = base + 32 * k + lane;
+                c[k] = i < n ? block[i] : -1;
             }
-            pos += __popc(m);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int64_t i = base + 32 * k + lane;
+                const bool mine = c[k] == r;
+                const unsigned m = __ballot_sync(0xffffffffu, mine);
+                if (mine) {
+                    const int64_t q = pos + __popc(m & ((1u << lane) - 1u));
+                    nodes[q] = (int32_t)i;
+                    th[q] = theta[i];
+                }
+                pos += __popc(m);
+            }
         }
     }
 }
@@ -329,12 +338,14 @@ __device__ __forceinline__ void bitonic_row(int32_t* sm, int P, int tid, int thr
 constexpr int CSR_WARP_MAX = 256;     // rows up to this length: one warp each
 constexpr int CSR_BLOCK_MAX = 16384;  // longer rows: one block each, up to this length
 
-__global__ void __launch_bounds__(256) k_csr_sort_short(const int64_t* row_ptr, int64_t n, int32_t* col, int* long_rows,
-                                                        int* n_long, uint32_t* err) {
+__global__ void __launch_bounds__(256) k_csr_sort_short(const int64_t* row_ptr, int64_t n, int32_t* col,
+                                                        const uint8_t* only, int* long_rows, int* n_long,
+                                                        uint32_t* err) {
     __shared__ int32_t sm[8][CSR_WARP_MAX];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        if (only && !only[i]) continue;
         const int64_t b = row_ptr[i], e = row_ptr[i + 1], len = e - b;
         if (len <= 1) continue;
         if (len > CSR_WARP_MAX) {
@@ -370,13 +381,13 @@ __global__ void __launch_bounds__(1024) k_csr_sort_long(const int64_t* row_ptr, 
     }
 }
 
+}  // namespace
+
 int grid_for(int64_t items, int threads) {
     int64_t b = (items + threads - 1) / threads;
     const int64_t cap = (int64_t)num_sms() * 16;
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
-
-}  // namespace
 
 // ---- workspace ---------------------------------------------------------------------------
 int64_t sbm_max_segments(int64_t n, int K) {
@@ -453,6 +464,18 @@ cudaError_t sbm_emit(const raftgp_sbm* p, const SbmWs& w, int64_t G, int32_t* sr
     return cudaGetLastError();
 }
 
+// ---- CSR rows sorted in place --------------------------------------------------------------
+cudaError_t sort_csr_rows(const int64_t* row_ptr, int64_t n, int32_t* col, const uint8_t* only, int* long_rows,
+                          int* n_long, uint32_t* err, cudaStream_t s) {
+    cudaMemsetAsync(n_long, 0, sizeof(int), s);
+    k_csr_sort_short<<<grid_for(n * 32, 256), 256, 0, s>>>(row_ptr, n, col, only, long_rows, n_long, err);
+    const size_t smem = CSR_BLOCK_MAX * sizeof(int32_t);
+    cudaError_t e = cudaFuncSetAttribute(k_csr_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_csr_sort_long<<<num_sms() * 2, 1024, smem, s>>>(row_ptr, col, long_rows, n_long);
+    return cudaGetLastError();
+}
+
 // ---- CSR of the drawn graph ---------------------------------------------------------------
 CsrBuildWs carve_csr_build(Carver& c, int64_t n) {
     CsrBuildWs w{};
@@ -477,11 +500,8 @@ cudaError_t coo_to_csr(int64_t n, int64_t m, const int32_t* src, const int32_t* 
     k_csr_rowptr<<<grid_for(n + 1, 256), 256, 0, s>>>(w.incl, n, row_ptr, w.fill);
     if (m > 0) k_csr_scatter<<<grid_for(m, 256), 256, 0, s>>>(src, dst, m, n, w.fill, col);
     if (n > 0) {
-        k_csr_sort_short<<<grid_for(n * 32, 256), 256, 0, s>>>(row_ptr, n, col, w.long_rows, w.n_long, w.err);
-        const size_t smem = CSR_BLOCK_MAX * sizeof(int32_t);
-        cudaError_t e = cudaFuncSetAttribute(k_csr_sort_long, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = sort_csr_rows(row_ptr, n, col, nullptr, w.long_rows, w.n_long, w.err, s);
         if (e != cudaSuccess) return e;
-        k_csr_sort_long<<<num_sms() * 2, 1024, smem, s>>>(row_ptr, col, w.long_rows, w.n_long);
     }
     cudaMemcpyAsync(herr, w.err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     return cudaStreamSynchronize(s);
