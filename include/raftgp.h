@@ -160,7 +160,8 @@ raftgp_status raftgp_kmeanspp(const void* Z, int64_t n, int32_t d, int32_t z_dty
  * `iters` assignment passes, ties to the lowest centroid, stop when no label changes, an
  * empty cluster keeps its centroid.  labels: device int32[N]; mu_out: device FP32 K x d
  * (may be NULL); *passes (host): assignment passes used.  `assign` picks the distance
- * engine.  Synchronises the stream. */
+ * engine.  ws: raftgp_lloyd_workspace_size(n, d, K) bytes.  Synchronises the stream. */
+size_t raftgp_lloyd_workspace_size(int64_t n, int32_t d, int32_t K);
 raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype, const float* mu0, int32_t K,
                            int32_t iters, int32_t assign, int32_t* labels, float* mu_out, int32_t* passes,
                            void* ws, size_t ws_bytes, raftgp_stream_t stream);

@@ -22,7 +22,7 @@ MAX_BATCH_CAND = 64
 
 # Every entry point declared in include/raftgp.h.
 EXPORTS = ("raftgp_workspace_size", "raftgp_embed", "raftgp_select", "raftgp_partition", "raftgp_score",
-           "raftgp_kmeanspp", "raftgp_kmeanspp_noalloc", "raftgp_lloyd", "raftgp_profile_enable", "raftgp_profile_enable_family", "raftgp_profile_read", "raftgp_last_error",
+           "raftgp_kmeanspp", "raftgp_kmeanspp_noalloc", "raftgp_lloyd", "raftgp_lloyd_workspace_size", "raftgp_profile_enable", "raftgp_profile_enable_family", "raftgp_profile_read", "raftgp_last_error",
            "raftgp_version", "raftgp_diff_workspace_size", "raftgp_gcn_layer_forward", "raftgp_gcn_layer_backward",
            "raftgp_softmod_loss", "raftgp_centroids", "raftgp_gcn_weights", "raftgp_adam_step",
            "raftgp_batch_workspace_size", "raftgp_batch_plan_create", "raftgp_batch_plan_run",
@@ -150,6 +150,8 @@ def lib():
         L.raftgp_select_bisect.restype = C.c_int
         L.raftgp_select_bisect.argtypes = [C.POINTER(Csr), P, C.c_int32, C.c_int32, C.POINTER(BisectOpts), P,
                                            C.POINTER(C.c_int32), P, C.c_size_t, P]
+        L.raftgp_lloyd_workspace_size.restype = C.c_size_t
+        L.raftgp_lloyd_workspace_size.argtypes = [C.c_int64, C.c_int32, C.c_int32]
         L.raftgp_sbm_workspace_size.restype = C.c_size_t
         L.raftgp_sbm_workspace_size.argtypes = [C.c_int64, C.c_int32]
         L.raftgp_sbm_count.restype = C.c_int

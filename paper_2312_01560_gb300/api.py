@@ -212,10 +212,7 @@ def lloyd(Z: torch.Tensor, mu0: torch.Tensor, iters=50, assign="ffma", stream=No
     labels = torch.empty(n, dtype=torch.int32, device=Z.device)
     mu = torch.empty((K, d), dtype=torch.float32, device=Z.device)
     m0 = mu0.to(Z.device, torch.float32).contiguous()
-    kp = (K + 255) // 256 * 256
-    # mu (4 B), sums (8 B), hi and lo (2 + 2 B) per centroid coordinate, norms and the norm
-    # slice per centroid, labels and re-check list per point, alignment slack
-    ws = _workspace(kp * d * 16 + kp * 128 + 64 * n + 256 * 1024, Z.device)
+    ws = _workspace(int(lib().raftgp_lloyd_workspace_size(n, d, int(K))), Z.device)
     passes = C.c_int32(0)
     Zc = Z.contiguous()
     check(lib().raftgp_lloyd(C.c_void_p(Zc.data_ptr()), n, d, code, C.c_void_p(m0.data_ptr()), int(K),

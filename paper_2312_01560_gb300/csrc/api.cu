@@ -653,6 +653,17 @@ __global__ void k_labels_out(const int16_t* l16, int cs, int64_t n, int32_t* out
         out[i] = l16[i * cs];
 }
 
+size_t raftgp_lloyd_workspace_size(int64_t n, int32_t d, int32_t K) {
+    if (n < 1 || K < 1) return 0;
+    Carver c(nullptr);
+    KmState km{};
+    carve_km(c, km, pad64h(K), d, n, 8);
+    c.take<uint32_t>(64);
+    c.take<int2>((size_t)n);
+    c.take<int>(64);
+    return c.off + 256;
+}
+
 raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype, const float* mu0, int32_t K,
                            int32_t iters, int32_t assign, int32_t* labels, float* mu_out, int32_t* passes, void* ws,
                            size_t ws_bytes, raftgp_stream_t stream) {
