@@ -1,6 +1,6 @@
 // assign_tc.cu -- k-means assignment on the 5th-generation tensor cores (sm_103a).
 //
-// For a tile of 128 points and a chunk of NCH centroids the distance GEMM
+// For a tile of 128 points and a chunk of NCH = 256 centroids the distance GEMM
 //     D[p][c] = z_p . mu_c
 // runs as tcgen05.mma (kind::f16, BF16 operands, FP32 accumulator in tensor memory).  The
 // centroids are split into two BF16 halves, mu = hi + lo (lo = the rounded residual), and
@@ -14,11 +14,13 @@
 // integer multiply-add turns it into the key 64 m + column, whose minimum gives score and
 // column at once.
 //
-// Warp roles in a persistent CTA (one per SM): warp 0 issues TMA loads (four point tiles per
-// step, centroid chunks of NCH = 128 columns through a ring of up to 8 stages), warp 1
-// allocates tensor memory and issues the MMAs, warps 2-17 are four epilogue groups of 4
-// warps, each owning one point tile of the step and one 128-column accumulator (4 x 128
-// columns fill tensor memory; 64-column chunks with two buffers per group measured slower).
+// Warp roles in a persistent CTA (one per SM): warp 0 issues TMA loads (two point tiles per
+// step, centroid chunks of NCH = 256 columns through a ring of stages), warp 1 allocates
+// tensor memory and issues the MMAs (M = 128, N = 256, K = 16), warps 2-9 are two epilogue
+// groups of 4 warps, each owning one point tile of the step and one 256-column accumulator
+// (2 x 256 columns fill tensor memory).  N = 256 halves the shared-memory operand bytes per
+// FLOP against N = 128 with four groups (6% faster at 1M points, 10 candidates); 64-column
+// chunks with two buffers per group measured slower still.
 // Every mbarrier wait is bounded: on timeout the CTA raises an abort flag, records
 // DERR_TIMEOUT, drains its in-flight copies and MMAs (again bounded), frees its tensor memory
 // and returns.
@@ -37,7 +39,8 @@
 
 namespace raftgp {
 
-constexpr int TC_GROUPS = 4;                          // epilogue warpgroups = point tiles per step
+constexpr int TC_NCH = 256;                            // centroids per chunk = MMA N
+constexpr int TC_GROUPS = 512 / TC_NCH;               // epilogue warpgroups = point tiles per step
 
 // LO: the centroid chunks carry the lo half too (FINAL always; FAST optionally).  Without it a
 // ring stage is smaller, so the ring gets deeper.
@@ -46,7 +49,7 @@ struct TcCfg {
     static constexpr int ATOM = D < 64 ? D : 64;          // K elements per swizzle-atom row
     static constexpr int ATOM_BYTES = ATOM * 2;           // 64 or 128
     static constexpr int NATOM = D / ATOM;
-    static constexpr int NCH = 128;                       // centroids per chunk = MMA N = two slices
+    static constexpr int NCH = TC_NCH;                    // centroids per chunk = MMA N
     static constexpr int SLICES = NCH / 64;               // 64-column slices per chunk
     static constexpr int GROUPS = TC_GROUPS;              // point tiles per CTA step, one per epilogue group
     static constexpr int ACC_BUFS = 512 / (GROUPS * NCH); // accumulator buffers per group
@@ -86,7 +89,7 @@ struct TcCtl {
     int chunk_col[TC_MAX_CHUNKS];
     // per 64-column slice (two per chunk): candidate + 128 if the candidate's padded range ends
     // with the slice, or -1 (inactive candidate / beyond the batch)
-    int16_t slice_info[2 * TC_MAX_CHUNKS];   // SLICES per chunk (at most 2)
+    int16_t slice_info[(TC_NCH / 64) * TC_MAX_CHUNKS];   // SLICES per chunk
 };
 
 // ---------------------------------------------------------------------------------------
@@ -147,7 +150,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int total_chunks = (b.total_k + C::NCH - 1) / C::NCH;
         for (int q = 0; q < total_chunks && nch < TC_MAX_CHUNKS; ++q) {
             const int lo = q * C::NCH;
-            int info[2] = {-1, -1};
+            int info[C::SLICES];
+            for (int h = 0; h < C::SLICES; ++h) info[h] = -1;
             bool need = false;
             for (int h = 0; h < C::SLICES; ++h) {
                 const int col0 = lo + 64 * h;
