@@ -127,7 +127,7 @@ def algorithmic_work(fam, g, wl, elem, cands):
 # of the kernel at this workload: the Lloyd pass of the coarse candidate batch (k_assign_tc,
 # hi-only) and the whole seeding launch (k_seed_persistent).  An entry goes back to None
 # when its kernel changes, until it is captured again.
-TRAFFIC_PER_LAUNCH = {"assign_tc": 1.658e8, "seed_update": 8.116e9}
+TRAFFIC_PER_LAUNCH = {"assign_tc": 1.658e8, "seed_update": None}
 
 
 def roofline(full, timed, dom, g, wl, elem, cands, steps):

@@ -18,7 +18,9 @@
  *     undirected, unweighted).  row_ptr has n+1 entries (int32 or int64), col has nnz int32
  *     entries, nnz = 2|E|.  All graph, feature and label arrays are DEVICE pointers owned by
  *     the caller; the library never allocates or frees device memory.  Scratch memory is a
- *     caller-owned device workspace whose size raftgp_workspace_size() returns.
+ *     caller-owned device workspace whose size raftgp_workspace_size() returns.  A feature
+ *     matrix Z (N x d, row-major, rows packed) must start on a 16-byte boundary; a Z that
+ *     does not is rejected with RAFTGP_EINVAL (rows of 32 x elem bytes keep every row aligned).
  *   - Every call is ordered on the given CUDA stream.  Calls with host outputs synchronise
  *     that stream before returning; the others return as soon as the work is queued.
  *   - Every call returns a raftgp_status and never aborts.  Invalid arguments (null

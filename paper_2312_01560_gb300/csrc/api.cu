@@ -537,6 +537,7 @@ raftgp_status raftgp_embed(const raftgp_csr* g, const raftgp_embed_opts* eopts, 
                            raftgp_stream_t stream) {
     raftgp_status st = check_csr(g);
     if (st) return st;
+    if ((uintptr_t)Z & 15) return fail(RAFTGP_EINVAL, "Z must be 16-byte aligned");
     if ((st = check_embed(eopts))) return st;
     if (!Z || !ws) return fail(RAFTGP_EINVAL, "Z or workspace is NULL");
     if (ws_bytes < raftgp_workspace_size(g, eopts, nullptr, 0)) return fail(RAFTGP_ENOMEM, "workspace too small");
@@ -556,6 +557,7 @@ raftgp_status raftgp_select(const raftgp_csr* g, const void* Z, int32_t d, int32
                             size_t ws_bytes, raftgp_stream_t stream) {
     raftgp_status st = check_csr(g);
     if (st) return st;
+    if ((uintptr_t)Z & 15) return fail(RAFTGP_EINVAL, "Z must be 16-byte aligned");
     if ((st = check_select(sopts, g->n))) return st;
     if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d = %d: must be 32, 64 or 128", d);
     if (z_dtype != RAFTGP_F32 && z_dtype != RAFTGP_BF16) return fail(RAFTGP_EINVAL, "unknown z_dtype");
@@ -634,6 +636,7 @@ raftgp_status raftgp_score(const raftgp_csr* g, const int32_t* labels, int32_t K
 raftgp_status raftgp_kmeanspp(const void* Z, int64_t n, int32_t d, int32_t z_dtype, int32_t K, uint64_t seed,
                               int32_t* seeds, void* ws, size_t ws_bytes, raftgp_stream_t stream) {
     if (!Z || !seeds || !ws || n < 1) return fail(RAFTGP_EINVAL, "NULL argument or n < 1");
+    if ((uintptr_t)Z & 15) return fail(RAFTGP_EINVAL, "Z must be 16-byte aligned");
     if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d must be 32, 64 or 128");
     if (K < 1 || K > n) return fail(RAFTGP_EINVAL, "need 1 <= K <= n");
     if (K > 32767) return fail(RAFTGP_EUNSUPPORTED, "K above 32767 is not supported");
@@ -668,6 +671,7 @@ raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype,
                            int32_t iters, int32_t assign, int32_t* labels, float* mu_out, int32_t* passes, void* ws,
                            size_t ws_bytes, raftgp_stream_t stream) {
     if (!Z || !mu0 || !labels || !ws || n < 1) return fail(RAFTGP_EINVAL, "NULL argument or n < 1");
+    if ((uintptr_t)Z & 15) return fail(RAFTGP_EINVAL, "Z must be 16-byte aligned");
     if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d must be 32, 64 or 128");
     if (K < 1 || K > 32767) return fail(RAFTGP_EINVAL, "need 1 <= K <= 32767");
     if (iters < 1) return fail(RAFTGP_EINVAL, "iters must be >= 1");
@@ -809,6 +813,7 @@ raftgp_status raftgp_softmod_loss(const raftgp_csr* g, const float* Z, int32_t d
                                   raftgp_stream_t stream) {
     raftgp_status st = check_csr(g);
     if (st) return st;
+    if ((uintptr_t)Z & 15) return fail(RAFTGP_EINVAL, "Z must be 16-byte aligned");
     if (!Z || !mu || !loss || !ws) return fail(RAFTGP_EINVAL, "NULL argument");
     if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d must be 32, 64 or 128");
     if (K < 1 || K > 128) return fail(RAFTGP_EUNSUPPORTED, "K must be in [1, 128]");
@@ -838,6 +843,7 @@ raftgp_status raftgp_softmod_loss(const raftgp_csr* g, const float* Z, int32_t d
 raftgp_status raftgp_centroids(const float* Z, int64_t n, int32_t d, const int32_t* labels, int32_t K, float* mu,
                                void* ws, size_t ws_bytes, raftgp_stream_t stream) {
     if (!Z || !labels || !mu || !ws || n < 1) return fail(RAFTGP_EINVAL, "NULL argument or n < 1");
+    if ((uintptr_t)Z & 15) return fail(RAFTGP_EINVAL, "Z must be 16-byte aligned");
     if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d must be 32, 64 or 128");
     if (K < 1) return fail(RAFTGP_EINVAL, "K < 1");
     if (ws_bytes < raftgp_diff_workspace_size(n, d, K)) return fail(RAFTGP_ENOMEM, "workspace too small");
@@ -1208,6 +1214,7 @@ raftgp_status raftgp_select_bisect(const raftgp_csr* g, const void* Z, int32_t d
                                    size_t ws_bytes, raftgp_stream_t stream) {
     raftgp_status st = check_csr(g);
     if (st) return st;
+    if ((uintptr_t)Z & 15) return fail(RAFTGP_EINVAL, "Z must be 16-byte aligned");
     if (!Z || !o || !labels || !k_out || !ws) return fail(RAFTGP_EINVAL, "NULL argument");
     if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d must be 32, 64 or 128");
     if (z_dtype != RAFTGP_F32 && z_dtype != RAFTGP_BF16) return fail(RAFTGP_EINVAL, "unknown z_dtype");

@@ -309,6 +309,12 @@ __device__ __forceinline__ uint4 ld_keep16(const void* p, uint64_t pol) {
                  : "l"(p), "l"(pol));
     return v;
 }
+// One 32-byte sector per lane in a single request (a 256-bit load, sm_100 and later).
+__device__ __forceinline__ void ld_keep32(const void* p, uint64_t pol, uint4& lo, uint4& hi) {
+    asm volatile("ld.global.nc.L2::cache_hint.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
+                 : "=r"(lo.x), "=r"(lo.y), "=r"(lo.z), "=r"(lo.w), "=r"(hi.x), "=r"(hi.y), "=r"(hi.z), "=r"(hi.w)
+                 : "l"(p), "l"(pol));
+}
 __device__ __forceinline__ void load_keep(const float* p, float* out, uint64_t pol) {
     const uint4 v = ld_keep16(p, pol);
     out[0] = __uint_as_float(v.x); out[1] = __uint_as_float(v.y);
@@ -347,6 +353,8 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
     const int cnt = (int)(n - lo < per_block ? (n - lo > 0 ? n - lo : 0) : per_block);
     const int G = gridDim.x;
     const uint64_t pol = l2_keep_policy();
+    // rows are a multiple of 32 bytes, so the sectors are 32-byte aligned when Z is
+    const bool a32 = ((uintptr_t)Z & 31) == 0;
 
     long long p = (long long)mulhi64(kmpp_draw(seed, 0), (uint64_t)n);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -394,10 +402,17 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
         bool active = next_row();
         while (active) {
             const T* zs = Z + (lo + r) * D + sec * SEC;
+            uint4 rw[2];
+            if (a32) {
+                ld_keep32(zs, pol, rw[0], rw[1]);
+            } else {
+                rw[0] = ld_keep16(zs, pol);
+                rw[1] = ld_keep16(zs + E, pol);
+            }
 #pragma unroll
             for (int v = 0; v < SEC / E; ++v) {
                 float x[E];
-                load_keep(zs + v * E, x, pol);
+                Vec<T>::unpack(rw[v], x);
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const float dl = __fsub_rn(x[e], c[sec * SEC + v * E + e]);

@@ -52,6 +52,7 @@ using namespace raftgp;
 extern "C" raftgp_status raftgp_kmeanspp_noalloc(const void* Z, int64_t n, int32_t d, int32_t z_dtype, int32_t K,
                                                  uint64_t seed, int32_t* seeds, raftgp_stream_t stream) {
     if (!Z || !seeds || n < 1) return set_error(RAFTGP_EINVAL, "NULL argument or n < 1");
+    if ((uintptr_t)Z & 15) return set_error(RAFTGP_EINVAL, "Z must be 16-byte aligned");
     if (d != 32 && d != 64 && d != 128) return set_error(RAFTGP_EUNSUPPORTED, "d must be 32, 64 or 128");
     if (K < 1 || K > n) return set_error(RAFTGP_EINVAL, "need 1 <= K <= n");
     if (K > 32767) return set_error(RAFTGP_EUNSUPPORTED, "K above 32767 is not supported");

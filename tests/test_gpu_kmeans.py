@@ -133,3 +133,30 @@ def test_lloyd_k_equals_n(cuda):
     Z = _unit_rows(rng, 100, 32).astype(np.float32)
     lab, _, passes = api.lloyd(torch.tensor(Z, device=cuda), torch.tensor(Z, device=cuda), iters=5)
     assert lab.cpu().tolist() == list(range(100)) and passes == 2
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float32])
+def test_kmeanspp_16_byte_aligned_rows(cuda, dtype):
+    # Z starting 16 bytes past a 32-byte boundary takes the 16-byte loads of the seeding
+    # update instead of the 32-byte ones: the same seeds
+    rng = np.random.default_rng(13)
+    host = torch.tensor(_clustered_rows(rng, 20_003, 64, 40, 0.6), dtype=dtype)
+    esz = host.element_size()
+    raw = torch.zeros(host.numel() * esz + 64, dtype=torch.uint8, device=cuda)
+    Z = raw[16:16 + host.numel() * esz].view(dtype).view(host.shape)
+    Z.copy_(host.to(cuda))
+    assert Z.data_ptr() % 32 == 16
+    seeds = api.kmeanspp(Z, 120, seed=4).cpu().numpy()
+    ref = oracle.kmeanspp(host.float().numpy().astype(np.float64), 120, 4, fp32_decision=True)
+    assert np.array_equal(seeds, ref)
+
+
+def test_misaligned_z_is_rejected(cuda):
+    raw = torch.zeros(64 * 32 * 4 + 64, dtype=torch.uint8, device=cuda)
+    Z = raw[8:8 + 64 * 32 * 4].view(torch.float32).view(64, 32)
+    assert Z.data_ptr() % 16 == 8
+    with pytest.raises(RuntimeError, match="16-byte aligned"):
+        api.kmeanspp(Z, 4, seed=1)
+    mu0 = torch.zeros(4, 32)
+    with pytest.raises(RuntimeError, match="16-byte aligned"):
+        api.lloyd(Z, mu0, iters=2)
