@@ -196,6 +196,7 @@ static SelectWs carve_select(Carver& c, int64_t n, int d, const raftgp_select_op
     w.seeds = c.take<int32_t>(kmax);
     w.seed = carve_seed(c.take<char>(seed_scratch_bytes(n, kmax)), n, kmax, w.seeds);
     w.seed.err = w.err;   // a seeding timeout is reported with the other device errors
+    w.seed.zs = c.take<float>((size_t)n * d);   // the sector-major copy of Z for the seeding
     w.cmax = batch_cap(o, kmax);
     w.kcap = (int)std::min<int64_t>((int64_t)w.cmax * pad64h(kmax), kMaxBatchCols > pad64h(kmax) ? kMaxBatchCols : pad64h(kmax));
     const int cs = (w.cmax + 7) / 8 * 8;

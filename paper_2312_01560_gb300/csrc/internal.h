@@ -154,6 +154,7 @@ struct SeedState {
     unsigned* bar;                 // 4 words: grid barrier count, generation, abort; spare error word
     uint32_t* err;                 // device error word (DERR_TIMEOUT); bar + 3 unless the caller has one
     int32_t* seeds;                // K (caller's output)
+    void* zs;                      // optional sector-major copy of Z (n x d elements), or null
 };
 int seed_nblocks(int64_t n);
 size_t seed_scratch_bytes(int64_t n, int K);

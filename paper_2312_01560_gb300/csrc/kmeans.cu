@@ -250,12 +250,14 @@ int seed_nblocks(int64_t n) { return (int)((n + SEED_PPB - 1) / SEED_PPB); }
 //      monotone), so once a partial sum reaches the current D^2 the row cannot lower it and
 //      the rest of the row is not read.  The rows that do lower D^2 are summed in full, so
 //      every D^2 is the same as the plain evaluation.  Thread j walks rows j, j + 1024, ...;
-//      a thread that finishes a row starts its next one at once.
+//      a thread that finishes a row starts its next one at once.  When the caller provides
+//      a sector-major copy of Z (plane s = sector s of every row), lanes on consecutive rows
+//      read consecutive sectors.
 //   2. block partial sums of the quantised D^2 are published; grid barrier.
 //   3. every block finds the owner of the threshold from the partial sums (the same integer
-//      arithmetic in every block); the owner scans its points in index order, writes the
-//      seed; grid barrier.
-// The barriers spin with a 2 s limit; on a timeout the kernel records DERR_TIMEOUT, raises
+//      arithmetic in every block); the owner scans its points in index order and publishes
+//      the seed; the other blocks wait for that one word.
+// The waits spin with a 2 s limit; on a timeout the kernel records DERR_TIMEOUT, raises
 // an abort word that releases the other blocks, marks the unfinished seeds -1 and returns.
 // ------------------------------------------------------------------------------------
 constexpr int SP_THREADS = 1024;
@@ -286,6 +288,29 @@ __device__ bool grid_barrier(unsigned* bar, uint32_t* err, int* s_ok) {
                     ok = 0;
                     break;
                 }
+            }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// Waits until the owner block of round t has published seeds[t] (the seeds start at -1).
+// Same 2 s limit and abort word as grid_barrier.
+__device__ bool wait_seed(const int32_t* seeds, int t, unsigned* bar, uint32_t* err, int* s_ok) {
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const uint64_t t0 = global_ns();
+        unsigned it = 0;
+        while ((int)ld_volatile(reinterpret_cast<const unsigned*>(seeds + t)) < 0) {
+            if (ld_volatile(bar + 2)) { ok = 0; break; }
+            if ((++it & 63) == 0 && global_ns() - t0 > TC_WAIT_NS) {
+                atomicOr(err, (uint32_t)DERR_TIMEOUT);
+                atomicExch(bar + 2, 1u);
+                ok = 0;
+                break;
             }
         }
         __threadfence();
@@ -332,8 +357,8 @@ __device__ __forceinline__ void load_keep(const __nv_bfloat16* p, float* out, ui
 
 template <typename T, int D>
 __global__ void __launch_bounds__(SP_THREADS, 1)
-    k_seed_persistent(const T* __restrict__ Z, int64_t n, int K, uint64_t seed, SeedState ss, int per_block,
-                      int off_near, int off_rows, int off_cc2) {
+    k_seed_persistent(const T* __restrict__ Z, const T* __restrict__ ZS, int64_t n, int K, uint64_t seed,
+                      SeedState ss, int per_block, int off_near, int off_rows, int off_cc2) {
     extern __shared__ __align__(16) uint8_t sp_smem[];
     float* sD2 = reinterpret_cast<float*>(sp_smem);
     int16_t* sNear = reinterpret_cast<int16_t*>(sp_smem + off_near);
@@ -353,8 +378,9 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
     const int cnt = (int)(n - lo < per_block ? (n - lo > 0 ? n - lo : 0) : per_block);
     const int G = gridDim.x;
     const uint64_t pol = l2_keep_policy();
-    // rows are a multiple of 32 bytes, so the sectors are 32-byte aligned when Z is
-    const bool a32 = ((uintptr_t)Z & 31) == 0;
+    // rows are a multiple of 32 bytes, so the sectors are 32-byte aligned when Z is; the
+    // sector-major copy ZS (plane s holds sector s of every row) is 256-byte aligned
+    const bool a32 = ZS || ((uintptr_t)Z & 31) == 0;
 
     long long p = (long long)mulhi64(kmpp_draw(seed, 0), (uint64_t)n);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -401,7 +427,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
         };
         bool active = next_row();
         while (active) {
-            const T* zs = Z + (lo + r) * D + sec * SEC;
+            const T* zs = ZS ? ZS + ((int64_t)sec * n + lo + r) * SEC : Z + (lo + r) * D + sec * SEC;
             uint4 rw[2];
             if (a32) {
                 ld_keep32(zs, pol, rw[0], rw[1]);
@@ -446,7 +472,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
             part[blockIdx.x] = sum;
         }
         if (!grid_barrier(ss.bar, ss.err, &s_ok)) break;
-        // ---- 3. the owner of the threshold picks the seed; barrier ----
+        // ---- 3. the owner of the threshold picks and publishes the seed ----
         for (int b = threadIdx.x; b < G; b += SP_THREADS) s_part[b] = __ldcg(part + b);
         __syncthreads();
         if (warp == 0) {
@@ -521,11 +547,14 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
         if ((s_owner == -2 && blockIdx.x == 0) || s_owner == (int)blockIdx.x) {
             if (threadIdx.x == 0) {
                 const long long pk = s_pick < 0 ? 0 : s_pick;   // unreachable fallback keeps indices in range
-                ss.seeds[t] = (int32_t)pk;
                 ss.chosen[pk] = 1;
+                __threadfence();   // chosen before the seed: a block that sees the seed sees the mark
+                atomicExch(reinterpret_cast<unsigned*>(ss.seeds + t), (unsigned)pk);
             }
         }
-        if (!grid_barrier(ss.bar, ss.err, &s_ok)) break;
+        // the other blocks only need the new seed: wait for it instead of a second barrier (the
+        // block sums are double-buffered, and the next round's barrier orders everything else)
+        if (!wait_seed(ss.seeds, t, ss.bar, ss.err, &s_ok)) break;
         p = (long long)__ldcg(ss.seeds + t);
     }
     if (t < K && threadIdx.x == 0) {
@@ -547,6 +576,20 @@ static bool persistent_layout(int per_block, int K, int* off_near, int* off_rows
     *off_cc2 = (int)cc2;
     *bytes = (int)total;
     return true;
+}
+
+// The sector-major copy of Z: plane s (n x 32 bytes) holds the s-th 32-byte sector of every
+// row, so lanes on consecutive rows read consecutive sectors.
+template <typename T, int D>
+__global__ void k_sector_planes(const T* __restrict__ Z, int64_t n, T* __restrict__ ZS) {
+    constexpr int SEC = 32 / (int)sizeof(T), NSEC = D / SEC;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < 2 * n * NSEC;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q / (2 * NSEC);
+        const int sec = (int)(q / 2 % NSEC), h = (int)(q & 1);
+        reinterpret_cast<uint4*>(ZS + ((int64_t)sec * n + i) * SEC)[h] =
+            reinterpret_cast<const uint4*>(Z + i * D + sec * SEC)[h];
+    }
 }
 
 // Launches the persistent kernel; returns false (nothing launched) if the state does not fit
@@ -571,9 +614,16 @@ static bool seed_persistent_t(const T* Z, int64_t n, int K, uint64_t seed, SeedS
     }
     cudaMemsetAsync(ss.chosen, 0, (size_t)n, s);
     cudaMemsetAsync(ss.bar, 0, 3 * sizeof(unsigned), s);
-    void* args[] = {(void*)&Z, (void*)&n, (void*)&K, (void*)&seed, (void*)&ss, (void*)&per_block,
+    cudaMemsetAsync(ss.seeds, 0xff, (size_t)K * sizeof(int32_t), s);   // -1: not published yet
+    const T* ZS = reinterpret_cast<const T*>(ss.zs);
+    void* args[] = {(void*)&Z, (void*)&ZS, (void*)&n, (void*)&K, (void*)&seed, (void*)&ss, (void*)&per_block,
                     (void*)&off_near, (void*)&off_rows, (void*)&off_cc2};
-    ProfScope ps(s, PF_SEED_UPDATE, 1);
+    ProfScope ps(s, PF_SEED_UPDATE, ZS ? 2 : 1);
+    if (ZS) {
+        int64_t blocks = (2 * n * (D * (int64_t)sizeof(T) / 32) + 255) / 256;
+        if (blocks > (int64_t)num_sms() * 16) blocks = (int64_t)num_sms() * 16;
+        k_sector_planes<T, D><<<(unsigned)blocks, 256, 0, s>>>(Z, n, reinterpret_cast<T*>(ss.zs));
+    }
     if (cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(SP_THREADS), args, (size_t)bytes, s) !=
         cudaSuccess) {
         cudaGetLastError();
@@ -612,6 +662,7 @@ SeedState carve_seed(void* base, int64_t n, int K, int32_t* seeds) {
     ss.bar = (unsigned*)p;
     ss.err = ss.bar + 3;
     ss.seeds = seeds;
+    ss.zs = nullptr;
     return ss;
 }
 
