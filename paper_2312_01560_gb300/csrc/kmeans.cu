@@ -299,12 +299,13 @@ __device__ bool grid_barrier(unsigned* bar, uint32_t* err, int* s_ok) {
 
 // Waits until the owner block of round t has published seeds[t] (the seeds start at -1).
 // Same 2 s limit and abort word as grid_barrier.
-__device__ bool wait_seed(const int32_t* seeds, int t, unsigned* bar, uint32_t* err, int* s_ok) {
+__device__ bool wait_seed(const int32_t* seeds, int t, unsigned* bar, uint32_t* err, int* s_ok, long long* s_seed) {
     if (threadIdx.x == 0) {
         int ok = 1;
         const uint64_t t0 = global_ns();
         unsigned it = 0;
-        while ((int)ld_volatile(reinterpret_cast<const unsigned*>(seeds + t)) < 0) {
+        int v;
+        while ((v = (int)ld_volatile(reinterpret_cast<const unsigned*>(seeds + t))) < 0) {
             if (ld_volatile(bar + 2)) { ok = 0; break; }
             if ((++it & 63) == 0 && global_ns() - t0 > TC_WAIT_NS) {
                 atomicOr(err, (uint32_t)DERR_TIMEOUT);
@@ -314,6 +315,7 @@ __device__ bool wait_seed(const int32_t* seeds, int t, unsigned* bar, uint32_t* 
             }
         }
         __threadfence();
+        *s_seed = v;
         *s_ok = ok;
     }
     __syncthreads();
@@ -358,16 +360,18 @@ __device__ __forceinline__ void load_keep(const __nv_bfloat16* p, float* out, ui
 template <typename T, int D>
 __global__ void __launch_bounds__(SP_THREADS, 1)
     k_seed_persistent(const T* __restrict__ Z, const T* __restrict__ ZS, int64_t n, int K, uint64_t seed,
-                      SeedState ss, int per_block, int off_near, int off_rows, int off_cc2) {
+                      SeedState ss, int per_block, int off_near, int off_rows, int off_cc2, int off_list,
+                      int list_per_warp) {
     extern __shared__ __align__(16) uint8_t sp_smem[];
     float* sD2 = reinterpret_cast<float*>(sp_smem);
     int16_t* sNear = reinterpret_cast<int16_t*>(sp_smem + off_near);
     T* srow = reinterpret_cast<T*>(sp_smem + off_rows);
     float* scc2 = reinterpret_cast<float*>(sp_smem + off_cc2);
+    uint16_t* sList = reinterpret_cast<uint16_t*>(sp_smem + off_list);   // rows to read, per warp
     __shared__ float c[D];
     __shared__ unsigned long long wsum[SP_THREADS / 32];
     __shared__ unsigned long long s_thr, s_base;
-    __shared__ long long s_pick;
+    __shared__ long long s_pick, s_seed;
     __shared__ int s_owner, s_ok;
     __shared__ unsigned long long s_part[1024];
     constexpr int E = Vec<T>::E;                    // elements per 16-byte load
@@ -407,23 +411,38 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
         }
         __syncthreads();
         unsigned long long q = 0;
-        int r = threadIdx.x;
+        // the skip bound over the warp's rows (warp * 32 + lane + 1024 k); the rows that need
+        // their distance are listed in the warp's slice of sList and dealt to the lanes in
+        // turn, so every lane gets the same number of rows to read (within one)
+        uint16_t* wl = sList + warp * list_per_warp;
+        int nl = 0;
+        for (int k0 = warp * 32; k0 < cnt; k0 += SP_THREADS) {
+            const int rr = k0 + lane;
+            bool need = false;
+            if (rr < cnt) {
+                if (t == 1) {
+                    need = true;
+                } else {
+                    const float c0 = sD2[rr];
+                    if (scc2[sNear[rr]] >= 4.0f * c0 * 1.0001f) q += quantise(c0);
+                    else need = true;
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, need);
+            if (need) wl[nl + __popc(m & ((1u << lane) - 1u))] = (uint16_t)rr;
+            nl += __popc(m);
+        }
+        __syncwarp();
+        int idx = lane, r = 0;
         float cur = 0.f, acc = 0.f;
         int sec = 0;
-        // next row that needs its distance (rows passing the skip test only add their q)
         auto next_row = [&]() -> bool {
-            for (; r < cnt; r += SP_THREADS) {
-                if (t == 1) {
-                    cur = INFINITY;
-                    break;
-                }
-                cur = sD2[r];
-                if (!(scc2[sNear[r]] >= 4.0f * cur * 1.0001f)) break;
-                q += quantise(cur);
-            }
+            if (idx >= nl) return false;
+            r = wl[idx];
+            cur = t > 1 ? sD2[r] : INFINITY;
             acc = 0.f;
             sec = 0;
-            return r < cnt;
+            return true;
         };
         bool active = next_row();
         while (active) {
@@ -456,10 +475,11 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
                     sNear[r] = (int16_t)(t - 1);
                 }
                 q += quantise(cur);
-                r += SP_THREADS;
+                idx += 32;
                 active = next_row();
             }
         }
+        __syncwarp();   // the list slice is rewritten next round
         // ---- 2. block partial sum; barrier ----
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
@@ -554,8 +574,8 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
         }
         // the other blocks only need the new seed: wait for it instead of a second barrier (the
         // block sums are double-buffered, and the next round's barrier orders everything else)
-        if (!wait_seed(ss.seeds, t, ss.bar, ss.err, &s_ok)) break;
-        p = (long long)__ldcg(ss.seeds + t);
+        if (!wait_seed(ss.seeds, t, ss.bar, ss.err, &s_ok, &s_seed)) break;
+        p = s_seed;
     }
     if (t < K && threadIdx.x == 0) {
         for (int j = t; j < K; ++j) ss.seeds[j] = -1;   // aborted: the unfinished seeds are invalid
@@ -564,16 +584,22 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
 
 // Shared-memory layout of the persistent kernel; false if it does not fit.
 template <typename T, int D>
-static bool persistent_layout(int per_block, int K, int* off_near, int* off_rows, int* off_cc2, int* bytes) {
+static bool persistent_layout(int per_block, int K, int* off_near, int* off_rows, int* off_cc2, int* off_list,
+                              int* list_per_warp, int* bytes) {
     auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    if (per_block > 65535) return false;   // row lists hold 16-bit indices
+    const int lpw = (per_block + SP_THREADS - 1) / SP_THREADS * 32;
     const size_t near = a16((size_t)per_block * 4);
     const size_t rows = near + a16((size_t)per_block * 2);
     const size_t cc2 = rows + a16((size_t)K * D * sizeof(T));
-    const size_t total = cc2 + a16((size_t)K * 4);
+    const size_t list = cc2 + a16((size_t)K * 4);
+    const size_t total = list + a16((size_t)(SP_THREADS / 32) * lpw * 2);
     if (total > (size_t)SP_MAX_SMEM) return false;
     *off_near = (int)near;
     *off_rows = (int)rows;
     *off_cc2 = (int)cc2;
+    *off_list = (int)list;
+    *list_per_warp = lpw;
     *bytes = (int)total;
     return true;
 }
@@ -600,8 +626,9 @@ static bool seed_persistent_t(const T* Z, int64_t n, int K, uint64_t seed, SeedS
     if (G > 1024) G = 1024;
     if ((int64_t)G > n) G = (int)n;
     const int per_block = (int)((n + G - 1) / G);
-    int off_near, off_rows, off_cc2, bytes;
-    if (!persistent_layout<T, D>(per_block, K, &off_near, &off_rows, &off_cc2, &bytes)) return false;
+    int off_near, off_rows, off_cc2, off_list, list_per_warp, bytes;
+    if (!persistent_layout<T, D>(per_block, K, &off_near, &off_rows, &off_cc2, &off_list, &list_per_warp, &bytes))
+        return false;
     auto kern = k_seed_persistent<T, D>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -617,7 +644,7 @@ static bool seed_persistent_t(const T* Z, int64_t n, int K, uint64_t seed, SeedS
     cudaMemsetAsync(ss.seeds, 0xff, (size_t)K * sizeof(int32_t), s);   // -1: not published yet
     const T* ZS = reinterpret_cast<const T*>(ss.zs);
     void* args[] = {(void*)&Z, (void*)&ZS, (void*)&n, (void*)&K, (void*)&seed, (void*)&ss, (void*)&per_block,
-                    (void*)&off_near, (void*)&off_rows, (void*)&off_cc2};
+                    (void*)&off_near, (void*)&off_rows, (void*)&off_cc2, (void*)&off_list, (void*)&list_per_warp};
     ProfScope ps(s, PF_SEED_UPDATE, ZS ? 2 : 1);
     if (ZS) {
         int64_t blocks = (2 * n * (D * (int64_t)sizeof(T) / 32) + 255) / 256;
