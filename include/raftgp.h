@@ -209,6 +209,14 @@ raftgp_status raftgp_profile_enable(int32_t on);
 raftgp_status raftgp_profile_enable_family(const char* family);
 int32_t raftgp_profile_read(raftgp_prof_entry* out, int32_t cap);
 
+/* ---- Test hook (failure detection without a GPU fault) ----
+ * From the next seeding on, block `block` of the persistent k-means++ kernel leaves at the
+ * start of round 2 without arriving at the grid barrier.  The other blocks' bounded wait
+ * (2 s) runs out: the kernel records a timeout, marks the unfinished seeds -1 and returns, and
+ * raftgp_select / raftgp_partition report RAFTGP_ETIMEOUT; the context stays usable.  -1 (the
+ * default) turns the hook off.  Not thread-safe; for tests only. */
+void raftgp_debug_seed_skip_block(int32_t block);
+
 /* Message for the last non-OK status returned on the calling thread. */
 const char* raftgp_last_error(void);
 

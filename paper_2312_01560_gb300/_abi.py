@@ -22,7 +22,7 @@ MAX_BATCH_CAND = 64
 
 # Every entry point declared in include/raftgp.h.
 EXPORTS = ("raftgp_workspace_size", "raftgp_embed", "raftgp_select", "raftgp_partition", "raftgp_score",
-           "raftgp_kmeanspp", "raftgp_kmeanspp_noalloc", "raftgp_lloyd", "raftgp_lloyd_workspace_size", "raftgp_profile_enable", "raftgp_profile_enable_family", "raftgp_profile_read", "raftgp_last_error",
+           "raftgp_kmeanspp", "raftgp_kmeanspp_noalloc", "raftgp_lloyd", "raftgp_lloyd_workspace_size", "raftgp_profile_enable", "raftgp_profile_enable_family", "raftgp_profile_read", "raftgp_last_error", "raftgp_debug_seed_skip_block",
            "raftgp_version", "raftgp_diff_workspace_size", "raftgp_gcn_layer_forward", "raftgp_gcn_layer_backward",
            "raftgp_softmod_loss", "raftgp_centroids", "raftgp_gcn_weights", "raftgp_adam_step",
            "raftgp_batch_workspace_size", "raftgp_batch_plan_create", "raftgp_batch_plan_run",
@@ -111,6 +111,8 @@ def lib():
             getattr(L, name).restype = C.c_int
         L.raftgp_profile_enable.restype = C.c_int
         L.raftgp_profile_enable.argtypes = [C.c_int32]
+        L.raftgp_debug_seed_skip_block.argtypes = [C.c_int32]
+        L.raftgp_debug_seed_skip_block.restype = None
         L.raftgp_profile_enable_family.restype = C.c_int
         L.raftgp_profile_enable_family.argtypes = [C.c_char_p]
         L.raftgp_profile_read.restype = C.c_int32

@@ -193,6 +193,12 @@ def score(g: DeviceGraph, labels: torch.Tensor, K: int, stream=None):
     return m, vol, mod.value, ncut.value
 
 
+def debug_seed_skip_block(block: int):
+    """Test hook: block `block` of the persistent seeding kernel leaves at round 2 without
+    arriving at the grid barrier (the bounded wait of the others runs out); -1 turns it off."""
+    lib().raftgp_debug_seed_skip_block(int(block))
+
+
 def kmeanspp(Z: torch.Tensor, K: int, seed: int, stream=None):
     n, d = Z.shape
     code = 1 if Z.dtype == torch.bfloat16 else 0

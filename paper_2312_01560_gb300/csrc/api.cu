@@ -634,6 +634,8 @@ raftgp_status raftgp_score(const raftgp_csr* g, const int32_t* labels, int32_t K
     return RAFTGP_OK;
 }
 
+void raftgp_debug_seed_skip_block(int32_t block) { set_seed_skip_block(block); }
+
 raftgp_status raftgp_kmeanspp(const void* Z, int64_t n, int32_t d, int32_t z_dtype, int32_t K, uint64_t seed,
                               int32_t* seeds, void* ws, size_t ws_bytes, raftgp_stream_t stream) {
     if (!Z || !seeds || !ws || n < 1) return fail(RAFTGP_EINVAL, "NULL argument or n < 1");

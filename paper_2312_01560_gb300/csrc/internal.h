@@ -161,6 +161,7 @@ size_t seed_scratch_bytes(int64_t n, int K);
 SeedState carve_seed(void* base, int64_t n, int K, int32_t* seeds);
 cudaError_t launch_seeding(const void* Z, int zdtype, int64_t n, int d, int K, uint64_t seed, SeedState ss,
                            cudaStream_t s);
+void set_seed_skip_block(int block);   // test hook of the persistent seeding
 
 void launch_batch_init(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, const int32_t* seeds,
                        const float* mu0, KmState st, cudaStream_t s);

@@ -361,7 +361,7 @@ template <typename T, int D>
 __global__ void __launch_bounds__(SP_THREADS, 1)
     k_seed_persistent(const T* __restrict__ Z, const T* __restrict__ ZS, int64_t n, int K, uint64_t seed,
                       SeedState ss, int per_block, int off_near, int off_rows, int off_cc2, int off_list,
-                      int list_per_warp) {
+                      int list_per_warp, int skip_block) {
     extern __shared__ __align__(16) uint8_t sp_smem[];
     float* sD2 = reinterpret_cast<float*>(sp_smem);
     int16_t* sNear = reinterpret_cast<int16_t*>(sp_smem + off_near);
@@ -393,6 +393,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
     }
     int t = 1;
     for (; t < K; ++t) {
+        if (t == 2 && (int)blockIdx.x == skip_block) break;   // test hook: leave without arriving
         // ---- 1. the newest seed, its distance to the earlier ones, the update ----
         for (int k = threadIdx.x; k < D; k += SP_THREADS) {
             const T v = Z[p * D + k];
@@ -618,6 +619,12 @@ __global__ void k_sector_planes(const T* __restrict__ Z, int64_t n, T* __restric
     }
 }
 
+// Test hook (raftgp_debug_seed_skip_block): this block of the persistent kernel leaves at the
+// start of round 2 without arriving at the grid barrier, so the other blocks' bounded wait
+// runs out; -1 (the default) turns it off.
+static int g_seed_skip_block = -1;
+void set_seed_skip_block(int block) { g_seed_skip_block = block; }
+
 // Launches the persistent kernel; returns false (nothing launched) if the state does not fit
 // shared memory or the device cannot hold one resident block per SM.
 template <typename T, int D>
@@ -644,7 +651,8 @@ static bool seed_persistent_t(const T* Z, int64_t n, int K, uint64_t seed, SeedS
     cudaMemsetAsync(ss.seeds, 0xff, (size_t)K * sizeof(int32_t), s);   // -1: not published yet
     const T* ZS = reinterpret_cast<const T*>(ss.zs);
     void* args[] = {(void*)&Z, (void*)&ZS, (void*)&n, (void*)&K, (void*)&seed, (void*)&ss, (void*)&per_block,
-                    (void*)&off_near, (void*)&off_rows, (void*)&off_cc2, (void*)&off_list, (void*)&list_per_warp};
+                    (void*)&off_near, (void*)&off_rows, (void*)&off_cc2, (void*)&off_list, (void*)&list_per_warp,
+                    (void*)&g_seed_skip_block};
     ProfScope ps(s, PF_SEED_UPDATE, ZS ? 2 : 1);
     if (ZS) {
         int64_t blocks = (2 * n * (D * (int64_t)sizeof(T) / 32) + 255) / 256;
@@ -809,15 +817,17 @@ __device__ void warp_row_operands(KmState st, int64_t row, int d) {
 }
 
 template <typename T>
-__global__ void k_batch_init_mu(CandBatch b, const T* Z, int d, const int32_t* seeds, const float* mu0, KmState st) {
+__global__ void k_batch_init_mu(CandBatch b, const T* Z, int64_t n, int d, const int32_t* seeds, const float* mu0,
+                                KmState st) {
     const int c = blockIdx.y;
     if (c >= b.n) return;
     const int K = b.k[c], off = b.off[c];
     for (int j = blockIdx.x; j < pad64(K); j += gridDim.x) {
-        const int64_t src = (seeds && j < K) ? (int64_t)seeds[j] : -1;
+        int64_t src = (seeds && j < K) ? (int64_t)seeds[j] : -1;
+        if (src >= n) src = -1;   // an aborted seeding leaves -1: such a centroid starts at 0
         for (int k = threadIdx.x; k < d; k += blockDim.x) {
             float v = 0.f;
-            if (j < K) v = mu0 ? mu0[(int64_t)j * d + k] : zval(Z, src * d + k);
+            if (j < K) v = mu0 ? mu0[(int64_t)j * d + k] : (src >= 0 ? zval(Z, src * d + k) : 0.f);
             st.mu[(int64_t)(off + j) * d + k] = v;
             st.sums[(int64_t)(off + j) * d + k] = 0;
         }
@@ -860,9 +870,9 @@ void launch_batch_init(const CandBatch& b, const void* Z, int zdtype, int64_t n,
     ProfScope ps(s, PF_BATCH_INIT, 3);
     dim3 grid(64, b.n);
     if (zdtype == RAFTGP_BF16)
-        k_batch_init_mu<__nv_bfloat16><<<grid, 128, 0, s>>>(b, (const __nv_bfloat16*)Z, d, seeds, mu0, st);
+        k_batch_init_mu<__nv_bfloat16><<<grid, 128, 0, s>>>(b, (const __nv_bfloat16*)Z, n, d, seeds, mu0, st);
     else
-        k_batch_init_mu<float><<<grid, 128, 0, s>>>(b, (const float*)Z, d, seeds, mu0, st);
+        k_batch_init_mu<float><<<grid, 128, 0, s>>>(b, (const float*)Z, n, d, seeds, mu0, st);
     k_operands<<<(b.total_k + 127) / 128, 128, 0, s>>>(b, d, st);
     const int64_t cnt = n * (int64_t)b.cs;
     int blocks = (int)((cnt + 255) / 256);
