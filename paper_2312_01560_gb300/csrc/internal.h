@@ -120,7 +120,7 @@ constexpr int MAXC = RAFTGP_MAX_BATCH_CAND;
 // One batch of candidates evaluated together; passed by value to every kernel.
 struct CandBatch {
     int n;              // candidates in the batch
-    int total_k;        // sum of k[]
+    int total_k;        // columns of the batch: the sum of the padded k[]
     int cs;             // label row stride (n rounded up to a multiple of 8)
     int k[MAXC];        // K of each candidate
     int off[MAXC];      // first centroid of each candidate (multiples of 64: candidates padded)

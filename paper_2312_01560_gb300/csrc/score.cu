@@ -16,24 +16,36 @@
 
 namespace raftgp {
 
-// Batched count over the labels of a candidate batch (labels: N x cs int16).
-__global__ void __launch_bounds__(256) k_score_count(CandBatch b, int64_t n, const int32_t* rp32, const int64_t* rp64,
+// Batched count over the labels of a candidate batch (labels: N x cs int16).  SMEM: the block
+// adds into 32-bit shared counters (every per-block sum is below 2^31 when nnz is) and flushes
+// the non-zero ones with one global atomic each, instead of contending on a few hot words.
+template <bool SMEM>
+__global__ void __launch_bounds__(512) k_score_count(CandBatch b, int64_t n, const int32_t* rp32, const int64_t* rp64,
                                                      const int32_t* col, const int32_t* deg,
                                                      const int16_t* __restrict__ labels, ScoreOut so) {
+    extern __shared__ uint32_t s_cnt[];   // SMEM: total_k m counters, then total_k vol counters
+    uint32_t* s_m = s_cnt;
+    uint32_t* s_vol = s_cnt + b.total_k;
+    if (SMEM) {
+        for (int t = threadIdx.x; t < 2 * b.total_k; t += blockDim.x) s_cnt[t] = 0;
+        __syncthreads();
+    }
+    auto add_vol = [&](int slot, int v) {
+        if (SMEM) atomicAdd(s_vol + slot, (uint32_t)v);
+        else atomicAdd(reinterpret_cast<unsigned long long*>(so.vol + slot), (unsigned long long)v);
+    };
+    auto add_m = [&](int slot, int v) {
+        if (SMEM) atomicAdd(s_m + slot, (uint32_t)v);
+        else atomicAdd(reinterpret_cast<unsigned long long*>(so.m + slot), (unsigned long long)v);
+    };
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nwarps) {
         const int64_t beg = rp64 ? rp64[i] : rp32[i];
         const int64_t end = rp64 ? rp64[i + 1] : rp32[i + 1];
         const int16_t* li = labels + i * b.cs;
-        if (lane < b.n) {
-            const int c = lane;
-            atomicAdd(reinterpret_cast<unsigned long long*>(so.vol + b.off[c] + li[c]), (unsigned long long)deg[i]);
-        }
-        if (lane + 32 < b.n) {
-            const int c = lane + 32;
-            atomicAdd(reinterpret_cast<unsigned long long*>(so.vol + b.off[c] + li[c]), (unsigned long long)deg[i]);
-        }
+        if (lane < b.n) add_vol(b.off[lane] + li[lane], deg[i]);
+        if (lane + 32 < b.n) add_vol(b.off[lane + 32] + li[lane + 32], deg[i]);
         for (int g0 = 0; g0 < b.n; g0 += 8) {
             const uint4 rv = *reinterpret_cast<const uint4*>(li + g0);
             const uint32_t rw[4] = {rv.x, rv.y, rv.z, rv.w};
@@ -58,8 +70,15 @@ __global__ void __launch_bounds__(256) k_score_count(CandBatch b, int64_t n, con
 #pragma unroll
                 for (int q = 0; q < 8; ++q) v = (lane == q) ? cnt[q] : v;
                 const int c = g0 + lane;
-                if (v) atomicAdd(reinterpret_cast<unsigned long long*>(so.m + b.off[c] + li[c]), (unsigned long long)v);
+                if (v) add_m(b.off[c] + li[c], v);
             }
+        }
+    }
+    if (SMEM) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < b.total_k; t += blockDim.x) {
+            if (s_m[t]) atomicAdd(reinterpret_cast<unsigned long long*>(so.m + t), (unsigned long long)s_m[t]);
+            if (s_vol[t]) atomicAdd(reinterpret_cast<unsigned long long*>(so.vol + t), (unsigned long long)s_vol[t]);
         }
     }
 }
@@ -123,13 +142,24 @@ void launch_score_batch(const CandBatch& b, const raftgp_csr* g, const int32_t* 
     ProfScope ps(s, PF_SCORE, 2);
     cudaMemsetAsync(so.m, 0, sizeof(long long) * (size_t)b.total_k, s);
     cudaMemsetAsync(so.vol, 0, sizeof(long long) * (size_t)b.total_k, s);
-    int64_t blocks = (g->n * 32 + 255) / 256;
-    const int64_t cap = (int64_t)num_sms() * 8;
-    if (blocks > cap) blocks = cap;
-    if (blocks < 1) blocks = 1;
-    k_score_count<<<(unsigned)blocks, 256, 0, s>>>(
-        b, g->n, g->row_ptr_bits == 32 ? (const int32_t*)g->row_ptr : nullptr,
-        g->row_ptr_bits == 64 ? (const int64_t*)g->row_ptr : nullptr, g->col, deg, labels, so);
+    const int32_t* rp32 = g->row_ptr_bits == 32 ? (const int32_t*)g->row_ptr : nullptr;
+    const int64_t* rp64 = g->row_ptr_bits == 64 ? (const int64_t*)g->row_ptr : nullptr;
+    const size_t smem = (size_t)b.total_k * 2 * sizeof(uint32_t);
+    if (g->nnz < ((int64_t)1 << 31) && smem <= 160 * 1024) {
+        int64_t blocks = (g->n * 32 + 511) / 512;
+        const int64_t cap = (int64_t)num_sms() * 2;
+        if (blocks > cap) blocks = cap;
+        if (blocks < 1) blocks = 1;
+        auto k = k_score_count<true>;
+        if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k<<<(unsigned)blocks, 512, smem, s>>>(b, g->n, rp32, rp64, g->col, deg, labels, so);
+    } else {
+        int64_t blocks = (g->n * 32 + 511) / 512;
+        const int64_t cap = (int64_t)num_sms() * 4;
+        if (blocks > cap) blocks = cap;
+        if (blocks < 1) blocks = 1;
+        k_score_count<false><<<(unsigned)blocks, 512, 0, s>>>(b, g->n, rp32, rp64, g->col, deg, labels, so);
+    }
     k_score_finalize<<<1, MAXC, 0, s>>>(b, g->nnz, so);
 }
 
