@@ -125,9 +125,8 @@ def algorithmic_work(fam, g, wl, elem, cands):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # of the kernel at this workload: the Lloyd pass of the coarse candidate batch (k_assign_tc,
-# hi-only) and the whole seeding launch (k_seed_persistent).  An entry goes back to None
-# when its kernel changes, until it is captured again.
-TRAFFIC_PER_LAUNCH = {"assign_tc": 1.658e8, "seed_update": None}
+# hi-only).  An entry goes back to None when its kernel changes, until it is captured again.
+TRAFFIC_PER_LAUNCH = {"assign_tc": 1.658e8}
 
 
 def roofline(full, timed, dom, g, wl, elem, cands, steps):
