@@ -350,9 +350,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         if (info >= 128) finish(info);
                     }
                 } else {
-                    // Lloyd pass: the chunk in 32-column pieces, the next piece's load in flight
-                    // while the current one is reduced; the buffer is released once the last
-                    // piece has landed.  Keys: accumulator bits x 64 + (0x48000000 + column)
+                    // Lloyd pass: the chunk in 32-column pieces, loaded four at a time with one
+                    // wait per four (a wait covers every load in flight); the buffer is released
+                    // once the last four have landed, before they are reduced.  Keys: accumulator bits x 64 + (0x48000000 + column)
                     // wraps to 0x08000000 + 64 m + column, a positive normal float, so a float
                     // minimum gives the (score, column) minimum (four independent chains).  An
                     // accumulator outside [128, 256) (a non-finite row) gives a meaningless
@@ -360,41 +360,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     constexpr int PIECES = C::NCH / 32;
                     const uint32_t mul = a.key_mul;
                     const uint32_t cbase = lane_base + (uint32_t)(buf * C::NCH);
-                    uint32_t r[2][32];
+                    constexpr int BATCH = 4;   // pieces loaded per wait (eight do not fit the registers)
+                    uint32_t r[BATCH][32];
                     float m0 = INFINITY, m1 = INFINITY, m2 = INFINITY, m3 = INFINITY;
-                    tmem_ld32_issue(cbase, r[0]);
-                    tmem_wait_ld(r[0]);
 #pragma unroll
-                    for (int pc = 0; pc < PIECES; ++pc) {
-                        if (pc + 1 < PIECES) {
-                            tmem_ld32_issue(cbase + 32u * (pc + 1), r[(pc + 1) & 1]);
-                        } else {
+                    for (int b0 = 0; b0 < PIECES; b0 += BATCH) {
+#pragma unroll
+                        for (int j = 0; j < BATCH; ++j) tmem_ld32_issue(cbase + 32u * (b0 + j), r[j]);
+#pragma unroll
+                        for (int j = 0; j < BATCH; ++j) tmem_wait_ld(r[j]);
+                        if (b0 + BATCH == PIECES) {
                             tc_fence_before();
                             mbar_arrive(&ctl.acc_empty[wg][buf]);   // every piece read: the buffer is free
                         }
-                        const uint32_t* x = r[pc & 1];
-                        const uint32_t c0 = 0x48000000u + 32u * (pc & 1);
 #pragma unroll
-                        for (int k = 0; k < 32; k += 8) {
-                            m0 = min3f(m0, __uint_as_float(x[k] * mul + (c0 + k)), __uint_as_float(x[k + 1] * mul + (c0 + k + 1)));
-                            m1 = min3f(m1, __uint_as_float(x[k + 2] * mul + (c0 + k + 2)), __uint_as_float(x[k + 3] * mul + (c0 + k + 3)));
-                            m2 = min3f(m2, __uint_as_float(x[k + 4] * mul + (c0 + k + 4)), __uint_as_float(x[k + 5] * mul + (c0 + k + 5)));
-                            m3 = min3f(m3, __uint_as_float(x[k + 6] * mul + (c0 + k + 6)), __uint_as_float(x[k + 7] * mul + (c0 + k + 7)));
-                        }
-                        if (pc & 1) {
-                            // end of 64-column slice h
-                            const int h = pc >> 1;
-                            const int info = ctl.slice_info[C::SLICES * q + h];
-                            if (info >= 0) {
-                                const float kmin = fminf(min3f(m0, m1, m2), m3);
-                                const uint32_t kb = __float_as_uint(kmin);
-                                const float v = __uint_as_float(kb & 0xFFFFFFC0u);
-                                if (v < bv) { bv = v; bi = col_q + 64 * h + (int)(kb & 63u); }
-                                if (info >= 128) finish(info);
+                        for (int j = 0; j < BATCH; ++j) {
+                            const int pc = b0 + j;
+                            const uint32_t* x = r[j];
+                            const uint32_t c0 = 0x48000000u + 32u * (pc & 1);
+#pragma unroll
+                            for (int k = 0; k < 32; k += 8) {
+                                m0 = min3f(m0, __uint_as_float(x[k] * mul + (c0 + k)), __uint_as_float(x[k + 1] * mul + (c0 + k + 1)));
+                                m1 = min3f(m1, __uint_as_float(x[k + 2] * mul + (c0 + k + 2)), __uint_as_float(x[k + 3] * mul + (c0 + k + 3)));
+                                m2 = min3f(m2, __uint_as_float(x[k + 4] * mul + (c0 + k + 4)), __uint_as_float(x[k + 5] * mul + (c0 + k + 5)));
+                                m3 = min3f(m3, __uint_as_float(x[k + 6] * mul + (c0 + k + 6)), __uint_as_float(x[k + 7] * mul + (c0 + k + 7)));
                             }
-                            m0 = m1 = m2 = m3 = INFINITY;
+                            if (pc & 1) {
+                                const int h = pc >> 1;
+                                const int info = ctl.slice_info[C::SLICES * q + h];
+                                if (info >= 0) {
+                                    const float kmin = fminf(min3f(m0, m1, m2), m3);
+                                    const uint32_t kb = __float_as_uint(kmin);
+                                    const float v = __uint_as_float(kb & 0xFFFFFFC0u);
+                                    if (v < bv) { bv = v; bi = col_q + 64 * h + (int)(kb & 63u); }
+                                    if (info >= 128) finish(info);
+                                }
+                                m0 = m1 = m2 = m3 = INFINITY;
+                            }
                         }
-                        if (pc + 1 < PIECES) tmem_wait_ld(r[(pc + 1) & 1]);
                     }
                 }
             }
