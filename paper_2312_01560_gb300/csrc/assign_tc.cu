@@ -350,33 +350,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         if (info >= 128) finish(info);
                     }
                 } else {
-                    // Lloyd pass: the chunk in 32-column pieces, loaded four at a time with one
-                    // wait per four (a wait covers every load in flight); the buffer is released
-                    // once the last four have landed, before they are reduced.  Keys: accumulator bits x 64 + (0x48000000 + column)
+                    // Lloyd pass: the chunk in two 128-column tensor-memory loads (one wait each),
+                    // reduced in 32-column pieces; the buffer is released as soon as the second
+                    // load has landed, before its columns are reduced.  Keys: accumulator bits x 64 + (0x48000000 + column)
                     // wraps to 0x08000000 + 64 m + column, a positive normal float, so a float
                     // minimum gives the (score, column) minimum (four independent chains).  An
                     // accumulator outside [128, 256) (a non-finite row) gives a meaningless
                     // key; the label stays in range in finish().
-                    constexpr int PIECES = C::NCH / 32;
                     const uint32_t mul = a.key_mul;
                     const uint32_t cbase = lane_base + (uint32_t)(buf * C::NCH);
-                    constexpr int BATCH = 4;   // pieces loaded per wait (eight do not fit the registers)
-                    uint32_t r[BATCH][32];
+                    uint32_t r[128];
                     float m0 = INFINITY, m1 = INFINITY, m2 = INFINITY, m3 = INFINITY;
 #pragma unroll
-                    for (int b0 = 0; b0 < PIECES; b0 += BATCH) {
-#pragma unroll
-                        for (int j = 0; j < BATCH; ++j) tmem_ld32_issue(cbase + 32u * (b0 + j), r[j]);
-#pragma unroll
-                        for (int j = 0; j < BATCH; ++j) tmem_wait_ld(r[j]);
-                        if (b0 + BATCH == PIECES) {
+                    for (int hh = 0; hh < C::NCH / 128; ++hh) {
+                        tmem_ld128_issue(cbase + 128u * hh, r);
+                        tmem_wait_ld128(r);
+                        if (hh + 1 == C::NCH / 128) {
                             tc_fence_before();
-                            mbar_arrive(&ctl.acc_empty[wg][buf]);   // every piece read: the buffer is free
+                            mbar_arrive(&ctl.acc_empty[wg][buf]);   // every column read: the buffer is free
                         }
 #pragma unroll
-                        for (int j = 0; j < BATCH; ++j) {
-                            const int pc = b0 + j;
-                            const uint32_t* x = r[j];
+                        for (int pp = 0; pp < 4; ++pp) {
+                            const int pc = 4 * hh + pp;           // 32-column piece of the chunk
+                            const uint32_t* x = r + 32 * pp;
                             const uint32_t c0 = 0x48000000u + 32u * (pc & 1);
 #pragma unroll
                             for (int k = 0; k < 32; k += 8) {
@@ -386,6 +382,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 m3 = min3f(m3, __uint_as_float(x[k + 6] * mul + (c0 + k + 6)), __uint_as_float(x[k + 7] * mul + (c0 + k + 7)));
                             }
                             if (pc & 1) {
+                                // end of 64-column slice h
                                 const int h = pc >> 1;
                                 const int info = ctl.slice_info[C::SLICES * q + h];
                                 if (info >= 0) {
