@@ -265,22 +265,19 @@ constexpr int SP_MAX_SMEM = 200 * 1024;
 
 __device__ __forceinline__ unsigned ld_volatile(const unsigned* p) { return *(volatile const unsigned*)p; }
 
-// bar[0] arrivals, bar[1] generation, bar[2] abort.  Returns false in every thread of the
-// block if the wait gave up or another block aborted.
-__device__ bool grid_barrier(unsigned* bar, uint32_t* err, int* s_ok) {
+// bar[0] counts arrivals and never resets: the barrier of round t completes when it reaches
+// t x gridDim.x, so the last block to arrive releases the others with its one atomic.
+// bar[2] is the abort word.  Returns false in every thread of the block if the wait gave up
+// (2 s limit: records DERR_TIMEOUT and raises the abort word) or another block aborted.
+__device__ bool grid_barrier(unsigned* bar, unsigned target, uint32_t* err, int* s_ok) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned gen = ld_volatile(bar + 1);
         __threadfence();
-        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
+        if (atomicAdd(bar, 1u) + 1u != target) {
             const uint64_t t0 = global_ns();
             unsigned it = 0;
-            while (ld_volatile(bar + 1) == gen) {
+            while (ld_volatile(bar) < target) {
                 if (ld_volatile(bar + 2)) { ok = 0; break; }
                 if ((++it & 63) == 0 && global_ns() - t0 > TC_WAIT_NS) {
                     atomicOr(err, (uint32_t)DERR_TIMEOUT);
@@ -487,16 +484,17 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
         if (lane == 0) wsum[warp] = q;
         __syncthreads();
         unsigned long long* part = ss.blocksum + (size_t)(t & 1) * G;
-        if (threadIdx.x == 0) {
-            unsigned long long sum = 0;
-            for (int w = 0; w < SP_THREADS / 32; ++w) sum += wsum[w];
-            part[blockIdx.x] = sum;
-        }
-        if (!grid_barrier(ss.bar, ss.err, &s_ok)) break;
-        // ---- 3. the owner of the threshold picks and publishes the seed ----
-        for (int b = threadIdx.x; b < G; b += SP_THREADS) s_part[b] = __ldcg(part + b);
-        __syncthreads();
         if (warp == 0) {
+            unsigned long long sum = wsum[lane];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (lane == 0) part[blockIdx.x] = sum;
+        }
+        if (!grid_barrier(ss.bar, (unsigned)t * (unsigned)G, ss.err, &s_ok)) break;
+        // ---- 3. the owner of the threshold picks and publishes the seed ----
+        if (warp == 0) {
+            for (int b = lane; b < G; b += 32) s_part[b] = __ldcg(part + b);
+            __syncwarp();
             unsigned long long tot = 0;
             for (int b = lane; b < G; b += 32) tot += s_part[b];
 #pragma unroll
