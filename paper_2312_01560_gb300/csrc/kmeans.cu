@@ -249,10 +249,12 @@ int seed_nblocks(int64_t n) { return (int)((n + SEED_PPB - 1) / SEED_PPB); }
 //      coordinates; the FP32 partial sums never decrease (every term is >= 0 and rounding is
 //      monotone), so once a partial sum reaches the current D^2 the row cannot lower it and
 //      the rest of the row is not read.  The rows that do lower D^2 are summed in full, so
-//      every D^2 is the same as the plain evaluation.  Thread j walks rows j, j + 1024, ...;
-//      a thread that finishes a row starts its next one at once.  When the caller provides
-//      a sector-major copy of Z (plane s = sector s of every row), lanes on consecutive rows
-//      read consecutive sectors.
+//      every D^2 is the same as the plain evaluation.  Each warp applies the skip bound to
+//      its rows, lists the rest, and reads them in sector passes: pass s reads sector s of
+//      every listed row (lanes on consecutive entries, two entries per lane in flight) and
+//      keeps, compacted, the rows whose partial sum is still below their D^2.  When the
+//      caller provides a sector-major copy of Z (plane s = sector s of every row), the lanes
+//      of a pass read consecutive sectors.
 //   2. block partial sums of the quantised D^2 are published; grid barrier.
 //   3. every block finds the owner of the threshold from the partial sums (the same integer
 //      arithmetic in every block); the owner scans its points in index order and publishes
@@ -358,13 +360,14 @@ template <typename T, int D>
 __global__ void __launch_bounds__(SP_THREADS, 1)
     k_seed_persistent(const T* __restrict__ Z, const T* __restrict__ ZS, int64_t n, int K, uint64_t seed,
                       SeedState ss, int per_block, int off_near, int off_rows, int off_cc2, int off_list,
-                      int list_per_warp, int skip_block) {
+                      int off_acc, int list_per_warp, int skip_block) {
     extern __shared__ __align__(16) uint8_t sp_smem[];
     float* sD2 = reinterpret_cast<float*>(sp_smem);
     int16_t* sNear = reinterpret_cast<int16_t*>(sp_smem + off_near);
     T* srow = reinterpret_cast<T*>(sp_smem + off_rows);
     float* scc2 = reinterpret_cast<float*>(sp_smem + off_cc2);
     uint16_t* sList = reinterpret_cast<uint16_t*>(sp_smem + off_list);   // rows to read, per warp
+    float* sAcc = reinterpret_cast<float*>(sp_smem + off_acc);           // their partial sums
     __shared__ float c[D];
     __shared__ unsigned long long wsum[SP_THREADS / 32];
     __shared__ unsigned long long s_thr, s_base;
@@ -410,8 +413,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
         __syncthreads();
         unsigned long long q = 0;
         // the skip bound over the warp's rows (warp * 32 + lane + 1024 k); the rows that need
-        // their distance are listed in the warp's slice of sList and dealt to the lanes in
-        // turn, so every lane gets the same number of rows to read (within one)
+        // their distance are listed in the warp's slice of sList
         uint16_t* wl = sList + warp * list_per_warp;
         int nl = 0;
         for (int k0 = warp * 32; k0 < cnt; k0 += SP_THREADS) {
@@ -431,51 +433,76 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
             nl += __popc(m);
         }
         __syncwarp();
-        int idx = lane, r = 0;
-        float cur = 0.f, acc = 0.f;
-        int sec = 0;
-        auto next_row = [&]() -> bool {
-            if (idx >= nl) return false;
-            r = wl[idx];
-            cur = t > 1 ? sD2[r] : INFINITY;
-            acc = 0.f;
-            sec = 0;
-            return true;
-        };
-        bool active = next_row();
-        while (active) {
-            const T* zs = ZS ? ZS + ((int64_t)sec * n + lo + r) * SEC : Z + (lo + r) * D + sec * SEC;
-            uint4 rw[2];
-            if (a32) {
-                ld_keep32(zs, pol, rw[0], rw[1]);
-            } else {
-                rw[0] = ld_keep16(zs, pol);
-                rw[1] = ld_keep16(zs + E, pol);
-            }
+        // Sector passes over the list: pass s reads sector s of every listed row (lanes on
+        // consecutive entries, 2 entries per lane in flight), and keeps in the list, compacted
+        // in place with its partial sum, each row whose sum is still below its D^2.
+        float* wacc = sAcc + warp * list_per_warp;
+        constexpr int U = 2;
+        int len = nl;
+        for (int sec = 0; sec < NSEC && len > 0; ++sec) {
+            int out = 0;
+            for (int j0 = 0; j0 < len; j0 += 32 * U) {
+                int rr[U];
+                float acc[U];
+                uint4 rw[U][2];
 #pragma unroll
-            for (int v = 0; v < SEC / E; ++v) {
-                float x[E];
-                Vec<T>::unpack(rw[v], x);
+                for (int u = 0; u < U; ++u) {
+                    const int j = j0 + 32 * u + lane;
+                    rr[u] = j < len ? (int)wl[j] : -1;
+                    acc[u] = (j < len && sec > 0) ? wacc[j] : 0.f;
+                    if (rr[u] >= 0) {
+                        const T* zs = ZS ? ZS + ((int64_t)sec * n + lo + rr[u]) * SEC : Z + (lo + rr[u]) * D + sec * SEC;
+                        if (a32) {
+                            ld_keep32(zs, pol, rw[u][0], rw[u][1]);
+                        } else {
+                            rw[u][0] = ld_keep16(zs, pol);
+                            rw[u][1] = ld_keep16(zs + E, pol);
+                        }
+                    }
+                }
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const float dl = __fsub_rn(x[e], c[sec * SEC + v * E + e]);
-                    acc = __fadd_rn(acc, __fmul_rn(dl, dl));
+                for (int u = 0; u < U; ++u) {
+                    bool keep = false;
+                    if (rr[u] >= 0) {
+                        float a = acc[u];
+#pragma unroll
+                        for (int v = 0; v < SEC / E; ++v) {
+                            float x[E];
+                            Vec<T>::unpack(rw[u][v], x);
+#pragma unroll
+                            for (int e = 0; e < E; ++e) {
+                                const float dl = __fsub_rn(x[e], c[sec * SEC + v * E + e]);
+                                a = __fadd_rn(a, __fmul_rn(dl, dl));
+                            }
+                        }
+                        acc[u] = a;
+                        float cur = t > 1 ? sD2[rr[u]] : INFINITY;
+                        if (sec + 1 == NSEC) {
+                            // round 1 reads every row in full and always stores it, so the shared
+                            // state is initialised whatever the data (a non-finite sum included)
+                            if (t == 1 || a < cur) {
+                                cur = a;
+                                sD2[rr[u]] = a;
+                                sNear[rr[u]] = (int16_t)(t - 1);
+                            }
+                            q += quantise(cur);
+                        } else if (t > 1 && a >= cur) {
+                            q += quantise(cur);
+                        } else {
+                            keep = true;
+                        }
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, keep);
+                    if (keep) {
+                        const int pos = out + __popc(m & ((1u << lane) - 1u));
+                        wl[pos] = (uint16_t)rr[u];
+                        wacc[pos] = acc[u];
+                    }
+                    out += __popc(m);
                 }
             }
-            ++sec;
-            const bool full = sec == NSEC;
-            // round 1 reads every row in full and always stores it, so the shared state is
-            // initialised whatever the data (a non-finite sum included)
-            if (full || (t > 1 && acc >= cur)) {
-                if (full && (t == 1 || acc < cur)) {
-                    cur = acc;
-                    sD2[r] = acc;
-                    sNear[r] = (int16_t)(t - 1);
-                }
-                q += quantise(cur);
-                idx += 32;
-                active = next_row();
-            }
+            __syncwarp();
+            len = out;
         }
         __syncwarp();   // the list slice is rewritten next round
         // ---- 2. block partial sum; barrier ----
@@ -584,7 +611,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
 // Shared-memory layout of the persistent kernel; false if it does not fit.
 template <typename T, int D>
 static bool persistent_layout(int per_block, int K, int* off_near, int* off_rows, int* off_cc2, int* off_list,
-                              int* list_per_warp, int* bytes) {
+                              int* off_acc, int* list_per_warp, int* bytes) {
     auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
     if (per_block > 65535) return false;   // row lists hold 16-bit indices
     const int lpw = (per_block + SP_THREADS - 1) / SP_THREADS * 32;
@@ -592,12 +619,14 @@ static bool persistent_layout(int per_block, int K, int* off_near, int* off_rows
     const size_t rows = near + a16((size_t)per_block * 2);
     const size_t cc2 = rows + a16((size_t)K * D * sizeof(T));
     const size_t list = cc2 + a16((size_t)K * 4);
-    const size_t total = list + a16((size_t)(SP_THREADS / 32) * lpw * 2);
+    const size_t acc = list + a16((size_t)(SP_THREADS / 32) * lpw * 2);
+    const size_t total = acc + a16((size_t)(SP_THREADS / 32) * lpw * 4);
     if (total > (size_t)SP_MAX_SMEM) return false;
     *off_near = (int)near;
     *off_rows = (int)rows;
     *off_cc2 = (int)cc2;
     *off_list = (int)list;
+    *off_acc = (int)acc;
     *list_per_warp = lpw;
     *bytes = (int)total;
     return true;
@@ -631,8 +660,9 @@ static bool seed_persistent_t(const T* Z, int64_t n, int K, uint64_t seed, SeedS
     if (G > 1024) G = 1024;
     if ((int64_t)G > n) G = (int)n;
     const int per_block = (int)((n + G - 1) / G);
-    int off_near, off_rows, off_cc2, off_list, list_per_warp, bytes;
-    if (!persistent_layout<T, D>(per_block, K, &off_near, &off_rows, &off_cc2, &off_list, &list_per_warp, &bytes))
+    int off_near, off_rows, off_cc2, off_list, off_acc, list_per_warp, bytes;
+    if (!persistent_layout<T, D>(per_block, K, &off_near, &off_rows, &off_cc2, &off_list, &off_acc, &list_per_warp,
+                                 &bytes))
         return false;
     auto kern = k_seed_persistent<T, D>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) {
@@ -649,7 +679,8 @@ static bool seed_persistent_t(const T* Z, int64_t n, int K, uint64_t seed, SeedS
     cudaMemsetAsync(ss.seeds, 0xff, (size_t)K * sizeof(int32_t), s);   // -1: not published yet
     const T* ZS = reinterpret_cast<const T*>(ss.zs);
     void* args[] = {(void*)&Z, (void*)&ZS, (void*)&n, (void*)&K, (void*)&seed, (void*)&ss, (void*)&per_block,
-                    (void*)&off_near, (void*)&off_rows, (void*)&off_cc2, (void*)&off_list, (void*)&list_per_warp,
+                    (void*)&off_near, (void*)&off_rows, (void*)&off_cc2, (void*)&off_list, (void*)&off_acc,
+                    (void*)&list_per_warp,
                     (void*)&g_seed_skip_block};
     ProfScope ps(s, PF_SEED_UPDATE, ZS ? 2 : 1);
     if (ZS) {
