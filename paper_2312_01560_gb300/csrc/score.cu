@@ -83,23 +83,55 @@ __global__ void __launch_bounds__(512) k_score_count(CandBatch b, int64_t n, con
     }
 }
 
-__global__ void k_score_finalize(CandBatch b, int64_t two_e, ScoreOut so) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+// Block per candidate: the NCut terms (one FP64 division each) in parallel, summed by one
+// thread in ascending block order; the integer sums are exact in any order.
+constexpr int FIN_THREADS = 256;
+constexpr int FIN_CHUNK = 1024;
+__global__ void __launch_bounds__(FIN_THREADS) k_score_finalize(CandBatch b, int64_t two_e, ScoreOut so) {
+    const int c = blockIdx.x;
     if (c >= b.n) return;
+    __shared__ double terms[FIN_CHUNK];
+    __shared__ long long s_m[FIN_THREADS / 32], s_v[FIN_THREADS / 32];
     const int K = b.k[c], off = b.off[c];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     long long msum = 0, vsq = 0;
-    double s = 0.0;
-    for (int r = 0; r < K; ++r) {
-        const long long m = so.m[off + r] / 2;
-        const long long v = so.vol[off + r];
-        msum += m;
-        vsq += v * v;
-        if (v > 0) s += (double)(v - 2 * m) / (double)v;
+    double s = 0.0;   // thread 0's running sum, in ascending block order
+    for (int r0 = 0; r0 < K; r0 += FIN_CHUNK) {
+        const int nr = K - r0 < FIN_CHUNK ? K - r0 : FIN_CHUNK;
+        for (int j = threadIdx.x; j < nr; j += FIN_THREADS) {
+            const long long m = so.m[off + r0 + j] / 2;
+            const long long v = so.vol[off + r0 + j];
+            msum += m;
+            vsq += v * v;
+            terms[j] = v > 0 ? (double)(v - 2 * m) / (double)v : 0.0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int j = 0; j < nr; ++j) s += terms[j];
+        __syncthreads();
     }
-    const long long num = 2 * two_e * msum - vsq;
-    const long long den = two_e * two_e;
-    so.mod[c] = den > 0 ? (double)num / (double)den : 0.0;
-    so.ncut[c] = 0.5 * s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        msum += __shfl_xor_sync(0xffffffffu, msum, o);
+        vsq += __shfl_xor_sync(0xffffffffu, vsq, o);
+    }
+    if (lane == 0) {
+        s_m[warp] = msum;
+        s_v[warp] = vsq;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        msum = 0;
+        vsq = 0;
+        for (int w = 0; w < FIN_THREADS / 32; ++w) {
+            msum += s_m[w];
+            vsq += s_v[w];
+        }
+        const long long num = 2 * two_e * msum - vsq;
+        const long long den = two_e * two_e;
+        so.mod[c] = den > 0 ? (double)num / (double)den : 0.0;
+        so.ncut[c] = 0.5 * s;
+    }
 }
 
 __device__ __forceinline__ bool better(int criterion, double mod_a, double ncut_a, int k_a, double mod_b, double ncut_b,
@@ -160,7 +192,7 @@ void launch_score_batch(const CandBatch& b, const raftgp_csr* g, const int32_t* 
         if (blocks < 1) blocks = 1;
         k_score_count<false><<<(unsigned)blocks, 512, 0, s>>>(b, g->n, rp32, rp64, g->col, deg, labels, so);
     }
-    k_score_finalize<<<1, MAXC, 0, s>>>(b, g->nnz, so);
+    k_score_finalize<<<b.n, FIN_THREADS, 0, s>>>(b, g->nnz, so);
 }
 
 void launch_select_best(const CandBatch& b, ScoreOut so, int criterion, BestState* best, const int16_t* labels,
