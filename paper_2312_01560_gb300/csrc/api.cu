@@ -431,16 +431,34 @@ static raftgp_status run_candidates(const raftgp_csr* g, const void* Z, int d, i
     return RAFTGP_OK;
 }
 
+// Thread per 16-byte chunk of Z (coalesced); the G = d * elem / 16 lanes of a row (4 to 32,
+// aligned groups of a warp) add their squares with shuffles.
 __global__ void k_check_norms(const void* Z, int zdtype, int64_t n, int d, uint32_t* err) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const bool bf = zdtype == RAFTGP_BF16;
+    const int G = d * (bf ? 2 : 4) / 16;
+    const int64_t chunks = n * G;
+    // unit rows stored in BF16 round to norms up to (1 + 2^-8)^2; FP32 to 1 + a few ulp
+    const float lim = bf ? 1.02f : 1.0001f;
+    for (int64_t q0 = (int64_t)blockIdx.x * blockDim.x; q0 < chunks; q0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = q0 + threadIdx.x;
         float s = 0.f;
-        for (int k = 0; k < d; ++k) {
-            const float v = zdtype == RAFTGP_BF16 ? __bfloat162float(((const __nv_bfloat16*)Z)[i * d + k])
-                                                  : ((const float*)Z)[i * d + k];
-            s = fmaf(v, v, s);
+        if (q < chunks) {
+            const uint4 v = reinterpret_cast<const uint4*>(Z)[q];
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (bf) {
+                    const float a = __uint_as_float(w[i] << 16), b = __uint_as_float(w[i] & 0xffff0000u);
+                    s = fmaf(a, a, s);
+                    s = fmaf(b, b, s);
+                } else {
+                    const float a = __uint_as_float(w[i]);
+                    s = fmaf(a, a, s);
+                }
+            }
         }
-        // unit rows stored in BF16 round to norms up to (1 + 2^-8)^2; FP32 to 1 + a few ulp
-        if (!(s <= (zdtype == RAFTGP_BF16 ? 1.02f : 1.0001f))) flag_error(err, DERR_NORM);
+        for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (q < chunks && q % G == 0 && !(s <= lim)) flag_error(err, DERR_NORM);
     }
 }
 
@@ -454,7 +472,8 @@ static raftgp_status run_select(const raftgp_csr* g, const void* Z, int d, int z
         launch_degrees(g, w.deg, w.rs, w.rsh, w.err, nullptr, nullptr, s);
     }
     {
-        int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8);
+        const int64_t chunks = n * (int64_t)(d * (zdtype == RAFTGP_BF16 ? 2 : 4) / 16);
+        int blocks = (int)std::min<int64_t>((chunks + 255) / 256, (int64_t)num_sms() * 8);
         ProfScope ps(s, PF_OTHER, 1);
         k_check_norms<<<std::max(blocks, 1), 256, 0, s>>>(Z, zdtype, n, d, w.err);
     }

@@ -92,3 +92,20 @@ def test_bf16_partition_drift(cuda):
     print(f"bf16 vs fp32: K* {r16['k']} vs {r32['k']}, NMI {a:.4f}, planted "
           f"{nmi(l16.cpu().numpy(), g.planted):.4f} vs {nmi(l32.cpu().numpy(), g.planted):.4f}")
     assert a >= 0.9
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_select_rejects_rows_above_unit_norm(cuda, dtype):
+    # the norm check reads Z in 16-byte chunks and adds each row's squares across lanes: a
+    # doubled first or last row is reported, unit rows pass
+    from paper_2312_01560_gb300 import _abi
+    g = workload("dcsbm-1k")
+    _, Z = oracle.embed(g, "ncut", (64, 64, 32), seed=1)
+    dg = api.DeviceGraph.from_host(g, cuda)
+    for bad in (0, g.n - 1):
+        Zb = Z.astype(np.float32).copy()
+        Zb[bad] *= 2.0
+        with pytest.raises(_abi.RaftgpError, match="norm above 1"):
+            api.select(dg, torch.tensor(Zb, device=cuda).to(dtype), kmin=2, kmax=8, iters=3)
+    lab, rep = api.select(dg, torch.tensor(Z.astype(np.float32), device=cuda).to(dtype), kmin=2, kmax=8, iters=3)
+    assert 2 <= rep["k"] <= 8
