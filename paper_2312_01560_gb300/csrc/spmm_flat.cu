@@ -100,12 +100,17 @@ __device__ __forceinline__ void store_vals(__nv_bfloat16* p, const float* y) {
     }
 }
 
+// Widen 8 BF16 values and add them into 8 FP32 accumulators, two per packed f32x2 add (the same
+// two round-to-nearest additions as scalar code).
 __device__ __forceinline__ void add_raw(const uint4& v, float* acc) {
     const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        acc[2 * i] += __uint_as_float(w[i] << 16);
-        acc[2 * i + 1] += __uint_as_float(w[i] & 0xffff0000u);
+        uint64_t p, q;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(p) : "f"(acc[2 * i]), "f"(acc[2 * i + 1]));
+        asm("mov.b64 %0, {%1, %2};" : "=l"(q) : "r"(w[i] << 16), "r"(w[i] & 0xffff0000u));
+        asm("add.rn.f32x2 %0, %0, %1;" : "+l"(p) : "l"(q));
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[2 * i]), "=f"(acc[2 * i + 1]) : "l"(p));
     }
 }
 
