@@ -7,7 +7,13 @@ modularity matrix (Eq. 5, rank-one form), a four-layer random GCN (Eq. 6), k-mea
 `value` = undirected edges / device time per step with the graph already in HBM; `e2e`
 adds the pinned-host -> device copy of the CSR and the device -> host copy of the labels.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--form bf16|f32]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--form bf16|f32|diff|batched|bisect|sbm|stream] [--assign tc|tc8|ffma]
+                  [--no-e2e] [--no-cpu-baseline] [--no-fp32-check]
+
+The default (`--form bf16`) is the line above; the other forms time the FP32 path, the
+weight tuning through the hand-written backward, 512 batched graphs, Algorithm 1, the exact
+SBM sampler (Algorithm 2) and the streaming update (Section III-D) on their own workloads.
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
 With N > 1 (torchrun) every rank partitions its own replica (the path does not shard).
@@ -538,7 +544,9 @@ def main():
                     help="bf16/f32: the partition benchmark; diff: Adam tuning steps of the GNN weights "
                          "(N=200,000, GNN 128-128-64, --steps Adam steps, default 200); batched: 512 uneven graphs "
                          "partitioned by one captured plan (--steps replays); bisect: the 1M-node partition "
-                         "with Algorithm 1 (recursive bisection by local modularity) as the model selection")
+                         "with Algorithm 1 (recursive bisection by local modularity) as the model selection; "
+                         "sbm: the exact DC-SBM sampler (Algorithm 2) and the device CSR build; stream: edge "
+                         "batches merged and the affected rows re-embedded (Section III-D)")
     ap.add_argument("--assign", default=None, choices=["tc", "tc8", "ffma"],
                     help="k-means engine (default: tc8 for bf16, ffma for f32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
