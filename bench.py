@@ -677,8 +677,8 @@ def main():
         for _ in range(e_steps):
             rp_d.copy_(rp_h, non_blocking=True)
             col_d.copy_(col_h, non_blocking=True)
-            api.partition(dg2, **kw)
-            lab_h.copy_(labels, non_blocking=True)
+            lab_e, _ = api.partition(dg2, **kw)
+            lab_h.copy_(lab_e, non_blocking=True)   # this step's labels
             torch.cuda.synchronize()
         e_ms = (time.perf_counter() - t0) * 1e3 / e_steps
         if world > 1:
