@@ -321,8 +321,8 @@ __device__ bool wait_seed(const int32_t* seeds, int t, unsigned* bar, uint32_t* 
     return *s_ok != 0;
 }
 
-// 16-byte row loads that ask L2 to keep the lines (evict_last): the rows are read again
-// every round, and Z is about the size of L2.
+// Row loads that ask L2 to keep the lines (evict_last): the rows are read again every round,
+// and Z is about the size of L2.
 __device__ __forceinline__ uint64_t l2_keep_policy() {
     uint64_t pol;
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
@@ -340,20 +340,6 @@ __device__ __forceinline__ void ld_keep32(const void* p, uint64_t pol, uint4& lo
     asm volatile("ld.global.nc.L2::cache_hint.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
                  : "=r"(lo.x), "=r"(lo.y), "=r"(lo.z), "=r"(lo.w), "=r"(hi.x), "=r"(hi.y), "=r"(hi.z), "=r"(hi.w)
                  : "l"(p), "l"(pol));
-}
-__device__ __forceinline__ void load_keep(const float* p, float* out, uint64_t pol) {
-    const uint4 v = ld_keep16(p, pol);
-    out[0] = __uint_as_float(v.x); out[1] = __uint_as_float(v.y);
-    out[2] = __uint_as_float(v.z); out[3] = __uint_as_float(v.w);
-}
-__device__ __forceinline__ void load_keep(const __nv_bfloat16* p, float* out, uint64_t pol) {
-    const uint4 v = ld_keep16(p, pol);
-    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        out[2 * i] = __uint_as_float(w[i] << 16);
-        out[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
-    }
 }
 
 template <typename T, int D>
