@@ -252,7 +252,8 @@ int seed_nblocks(int64_t n) { return (int)((n + SEED_PPB - 1) / SEED_PPB); }
 //      every D^2 is the same as the plain evaluation.  Each warp applies the skip bound to
 //      its rows, lists the rest, and reads them in sector passes: pass s reads sector s of
 //      every listed row (lanes on consecutive entries, two entries per lane in flight) and
-//      keeps, compacted, the rows whose partial sum is still below their D^2.  When the
+//      keeps, compacted, the rows whose partial sum is still below their D^2.  When a block
+//      owns more points than the lists can hold, a warp works through its rows in chunks.  When the
 //      caller provides a sector-major copy of Z (plane s = sector s of every row), the lanes
 //      of a pass read consecutive sectors.
 //   2. block partial sums of the quantised D^2 are published; grid barrier.
@@ -398,99 +399,103 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
         }
         __syncthreads();
         unsigned long long q = 0;
-        // the skip bound over the warp's rows (warp * 32 + lane + 1024 k); the rows that need
-        // their distance are listed in the warp's slice of sList
+        // the warp's rows (warp * 32 + lane + 1024 k) in chunks of list_per_warp / 32 groups of
+        // 32: the skip bound over a chunk; the rows that need their distance are listed in the
+        // warp's slice of sList
         uint16_t* wl = sList + warp * list_per_warp;
-        int nl = 0;
-        for (int k0 = warp * 32; k0 < cnt; k0 += SP_THREADS) {
-            const int rr = k0 + lane;
-            bool need = false;
-            if (rr < cnt) {
-                if (t == 1) {
-                    need = true;
-                } else {
-                    const float c0 = sD2[rr];
-                    if (scc2[sNear[rr]] >= 4.0f * c0 * 1.0001f) q += quantise(c0);
-                    else need = true;
-                }
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, need);
-            if (need) wl[nl + __popc(m & ((1u << lane) - 1u))] = (uint16_t)rr;
-            nl += __popc(m);
-        }
-        __syncwarp();
-        // Sector passes over the list: pass s reads sector s of every listed row (lanes on
-        // consecutive entries, 2 entries per lane in flight), and keeps in the list, compacted
-        // in place with its partial sum, each row whose sum is still below its D^2.
         float* wacc = sAcc + warp * list_per_warp;
-        constexpr int U = 2;
-        int len = nl;
-        for (int sec = 0; sec < NSEC && len > 0; ++sec) {
-            int out = 0;
-            for (int j0 = 0; j0 < len; j0 += 32 * U) {
-                int rr[U];
-                float acc[U];
-                uint4 rw[U][2];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int j = j0 + 32 * u + lane;
-                    rr[u] = j < len ? (int)wl[j] : -1;
-                    acc[u] = (j < len && sec > 0) ? wacc[j] : 0.f;
-                    if (rr[u] >= 0) {
-                        const T* zs = ZS ? ZS + ((int64_t)sec * n + lo + rr[u]) * SEC : Z + (lo + rr[u]) * D + sec * SEC;
-                        if (a32) {
-                            ld_keep32(zs, pol, rw[u][0], rw[u][1]);
-                        } else {
-                            rw[u][0] = ld_keep16(zs, pol);
-                            rw[u][1] = ld_keep16(zs + E, pol);
-                        }
+        const int chunk_rows = SP_THREADS * (list_per_warp / 32);
+        for (int kc = warp * 32; kc < cnt; kc += chunk_rows) {
+            int nl = 0;
+            for (int k0 = kc; k0 < cnt && k0 < kc + chunk_rows; k0 += SP_THREADS) {
+                const int rr = k0 + lane;
+                bool need = false;
+                if (rr < cnt) {
+                    if (t == 1) {
+                        need = true;
+                    } else {
+                        const float c0 = sD2[rr];
+                        if (scc2[sNear[rr]] >= 4.0f * c0 * 1.0001f) q += quantise(c0);
+                        else need = true;
                     }
                 }
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    bool keep = false;
-                    if (rr[u] >= 0) {
-                        float a = acc[u];
-#pragma unroll
-                        for (int v = 0; v < SEC / E; ++v) {
-                            float x[E];
-                            Vec<T>::unpack(rw[u][v], x);
-#pragma unroll
-                            for (int e = 0; e < E; ++e) {
-                                const float dl = __fsub_rn(x[e], c[sec * SEC + v * E + e]);
-                                a = __fadd_rn(a, __fmul_rn(dl, dl));
-                            }
-                        }
-                        acc[u] = a;
-                        float cur = t > 1 ? sD2[rr[u]] : INFINITY;
-                        if (sec + 1 == NSEC) {
-                            // round 1 reads every row in full and always stores it, so the shared
-                            // state is initialised whatever the data (a non-finite sum included)
-                            if (t == 1 || a < cur) {
-                                cur = a;
-                                sD2[rr[u]] = a;
-                                sNear[rr[u]] = (int16_t)(t - 1);
-                            }
-                            q += quantise(cur);
-                        } else if (t > 1 && a >= cur) {
-                            q += quantise(cur);
-                        } else {
-                            keep = true;
-                        }
-                    }
-                    const unsigned m = __ballot_sync(0xffffffffu, keep);
-                    if (keep) {
-                        const int pos = out + __popc(m & ((1u << lane) - 1u));
-                        wl[pos] = (uint16_t)rr[u];
-                        wacc[pos] = acc[u];
-                    }
-                    out += __popc(m);
-                }
+                const unsigned m = __ballot_sync(0xffffffffu, need);
+                if (need) wl[nl + __popc(m & ((1u << lane) - 1u))] = (uint16_t)rr;
+                nl += __popc(m);
             }
             __syncwarp();
-            len = out;
+            // Sector passes over the list: pass s reads sector s of every listed row (lanes on
+            // consecutive entries, 2 entries per lane in flight), and keeps in the list, compacted
+            // in place with its partial sum, each row whose sum is still below its D^2.
+            constexpr int U = 2;
+            int len = nl;
+            for (int sec = 0; sec < NSEC && len > 0; ++sec) {
+                int out = 0;
+                for (int j0 = 0; j0 < len; j0 += 32 * U) {
+                    int rr[U];
+                    float acc[U];
+                    uint4 rw[U][2];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int j = j0 + 32 * u + lane;
+                        rr[u] = j < len ? (int)wl[j] : -1;
+                        acc[u] = (j < len && sec > 0) ? wacc[j] : 0.f;
+                        if (rr[u] >= 0) {
+                            const T* zs = ZS ? ZS + ((int64_t)sec * n + lo + rr[u]) * SEC : Z + (lo + rr[u]) * D + sec * SEC;
+                            if (a32) {
+                                ld_keep32(zs, pol, rw[u][0], rw[u][1]);
+                            } else {
+                                rw[u][0] = ld_keep16(zs, pol);
+                                rw[u][1] = ld_keep16(zs + E, pol);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        bool keep = false;
+                        if (rr[u] >= 0) {
+                            float a = acc[u];
+#pragma unroll
+                            for (int v = 0; v < SEC / E; ++v) {
+                                float x[E];
+                                Vec<T>::unpack(rw[u][v], x);
+#pragma unroll
+                                for (int e = 0; e < E; ++e) {
+                                    const float dl = __fsub_rn(x[e], c[sec * SEC + v * E + e]);
+                                    a = __fadd_rn(a, __fmul_rn(dl, dl));
+                                }
+                            }
+                            acc[u] = a;
+                            float cur = t > 1 ? sD2[rr[u]] : INFINITY;
+                            if (sec + 1 == NSEC) {
+                                // round 1 reads every row in full and always stores it, so the shared
+                                // state is initialised whatever the data (a non-finite sum included)
+                                if (t == 1 || a < cur) {
+                                    cur = a;
+                                    sD2[rr[u]] = a;
+                                    sNear[rr[u]] = (int16_t)(t - 1);
+                                }
+                                q += quantise(cur);
+                            } else if (t > 1 && a >= cur) {
+                                q += quantise(cur);
+                            } else {
+                                keep = true;
+                            }
+                        }
+                        const unsigned m = __ballot_sync(0xffffffffu, keep);
+                        if (keep) {
+                            const int pos = out + __popc(m & ((1u << lane) - 1u));
+                            wl[pos] = (uint16_t)rr[u];
+                            wacc[pos] = acc[u];
+                        }
+                        out += __popc(m);
+                    }
+                }
+                __syncwarp();
+                len = out;
+            }
+            __syncwarp();   // the list slice is rewritten by the next chunk
         }
-        __syncwarp();   // the list slice is rewritten next round
         // ---- 2. block partial sum; barrier ----
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
@@ -600,14 +605,20 @@ static bool persistent_layout(int per_block, int K, int* off_near, int* off_rows
                               int* off_acc, int* list_per_warp, int* bytes) {
     auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
     if (per_block > 65535) return false;   // row lists hold 16-bit indices
-    const int lpw = (per_block + SP_THREADS - 1) / SP_THREADS * 32;
     const size_t near = a16((size_t)per_block * 4);
     const size_t rows = near + a16((size_t)per_block * 2);
     const size_t cc2 = rows + a16((size_t)K * D * sizeof(T));
     const size_t list = cc2 + a16((size_t)K * 4);
-    const size_t acc = list + a16((size_t)(SP_THREADS / 32) * lpw * 2);
-    const size_t total = acc + a16((size_t)(SP_THREADS / 32) * lpw * 4);
-    if (total > (size_t)SP_MAX_SMEM) return false;
+    // the row lists cover all of a warp's rows at once when they fit, else chunks of fewer
+    // 32-row groups (lpw entries per warp)
+    int lpw = (per_block + SP_THREADS - 1) / SP_THREADS * 32;
+    size_t acc = 0, total = 0;
+    for (; lpw >= 32; lpw -= 32) {
+        acc = list + a16((size_t)(SP_THREADS / 32) * lpw * 2);
+        total = acc + a16((size_t)(SP_THREADS / 32) * lpw * 4);
+        if (total <= (size_t)SP_MAX_SMEM) break;
+    }
+    if (lpw < 32) return false;
     *off_near = (int)near;
     *off_rows = (int)rows;
     *off_cc2 = (int)cc2;

@@ -58,6 +58,16 @@ def test_kmeanspp_bit_exact_many_blocks(cuda, dtype):
     assert np.array_equal(seeds, ref)
 
 
+def test_kmeanspp_bit_exact_chunked_row_lists(cuda):
+    # 700 seed rows of 128 BF16 coordinates leave the persistent kernel room for one 32-row
+    # group per warp list, so every warp reads its rows in two chunks per round
+    rng = np.random.default_rng(14)
+    Z = torch.tensor(_clustered_rows(rng, 300_007, 128, 60, 0.6), dtype=torch.bfloat16, device=cuda)
+    seeds = api.kmeanspp(Z, 700, seed=6).cpu().numpy()
+    ref = oracle.kmeanspp(Z.float().cpu().numpy().astype(np.float64), 700, 6, fp32_decision=True)
+    assert np.array_equal(seeds, ref)
+
+
 def test_kmeanspp_bit_exact_per_round_kernels(cuda):
     # 450 seed rows of 128 FP32 coordinates do not fit the persistent kernel's shared memory,
     # so the seeding runs as one update and one pick launch per round
