@@ -54,6 +54,19 @@ PEAK_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustaine
 N_SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
+def replica_throughput(ms_local, n_units, world, device=None):
+    """Whole-job throughput of `world` replicas that each processed `n_units` in `ms_local`
+    milliseconds: world * n_units / (the slowest rank's time), the maximum taken with an
+    all-reduce over the process group.  Returns (units per second, max ms)."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * n_units / (ms * 1e-3), ms
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -569,13 +582,13 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     wl = WORKLOAD
+    if args.impl == "reference" and rank != 0:
+        return   # the oracle arm runs on rank 0 only; the other ranks exit without work
 
     from inputs.dcsbm import workload
     g = workload(wl["graph"], seed=wl["graph_seed"])
 
     if args.impl == "reference":
-        if rank != 0:
-            return
         cands = reference_candidates(wl)
         for _ in range(args.warmup):
             oracle_sample(g, wl, cands, rows=16, seed_rounds=1, lloyd_points=200)
@@ -649,11 +662,7 @@ def main():
     ms = ev0.elapsed_time(ev1) / args.steps
     prof_dom = api.profile_read()
     api.profile_enable(False)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * g.n_edges / (ms * 1e-3)
+    value, ms = replica_throughput(ms, g.n_edges, world, dev)
     launches = int(sum(v["launches"] for v in full.values()))
     elem = 2 if dtype == "bf16" else 4
     roof = roofline(full, prof_dom, dom, g, wl, elem, rep["cands"], args.steps)
@@ -681,11 +690,8 @@ def main():
             lab_h.copy_(lab_e, non_blocking=True)   # this step's labels
             torch.cuda.synchronize()
         e_ms = (time.perf_counter() - t0) * 1e3 / e_steps
-        if world > 1:
-            t = torch.tensor([e_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": world * g.n_edges / (e_ms * 1e-3), "unit": "edges/s",
+        e_value, e_ms = replica_throughput(e_ms, g.n_edges, world, dev)
+        e2e = {"value": e_value, "unit": "edges/s",
                "h2d_bytes_per_step": int(rp_h.numel() * 8 + col_h.numel() * 4),
                "d2h_bytes_per_step": int(lab_h.numel() * 4)}
 
