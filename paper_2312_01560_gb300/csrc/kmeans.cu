@@ -388,14 +388,22 @@ __global__ void __launch_bounds__(SP_THREADS, 1)
             srow[(int64_t)(t - 1) * D + k] = v;
         }
         __syncthreads();
-        for (int j = warp; j < t - 1; j += SP_THREADS / 32) {
+        // the new seed's squared distance to every earlier seed: 8-lane groups, four seeds
+        // per warp at a time
+        for (int jb = warp * 4; jb < t - 1; jb += SP_THREADS / 8) {
+            const int j = jb + (lane >> 3), sub = lane & 7;
             float acc = 0.f;
-            for (int k = lane; k < D; k += 32) {
-                const float dl = Vec<T>::to_float(srow[(int64_t)j * D + k]) - c[k];
-                acc = fmaf(dl, dl, acc);
+            if (j < t - 1) {
+#pragma unroll
+                for (int k = sub; k < D; k += 8) {
+                    const float dl = Vec<T>::to_float(srow[(int64_t)j * D + k]) - c[k];
+                    acc = fmaf(dl, dl, acc);
+                }
             }
-            acc = warp_sum(acc);
-            if (lane == 0) scc2[j] = acc;
+            acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            if (j < t - 1 && sub == 0) scc2[j] = acc;
         }
         __syncthreads();
         unsigned long long q = 0;
@@ -1173,7 +1181,7 @@ __global__ void k_lloyd_update(CandBatch b, int d, KmState st, int pass, int las
 }
 
 void launch_lloyd_update(const CandBatch& b, int d, KmState st, int pass, int last_pass, cudaStream_t s) {
-    dim3 grid(16, b.n);
+    dim3 grid(64, b.n);
     ProfScope ps(s, PF_LLOYD_UPDATE, 1);
     k_lloyd_update<<<grid, 256, 0, s>>>(b, d, st, pass, last_pass);
 }
