@@ -20,11 +20,11 @@
 namespace raftgp {
 
 // ------------------------------------------------------------------------------------
-// Degrees, reciprocal square roots and graph checks (warp per row).
+// Degrees, reciprocal square roots and graph checks (8 lanes per row, 4 rows per warp).
 // ------------------------------------------------------------------------------------
 __global__ void k_degrees(int64_t n, int64_t nnz, const int32_t* rp32, const int64_t* rp64, const int32_t* col,
                           int32_t* deg, float* rs, float* rsh, uint32_t* err, int32_t* heavy, int* heavy_count) {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, sub = lane & 7, grp = lane >> 3;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     if (warp == 0 && lane == 0) {
@@ -32,27 +32,38 @@ __global__ void k_degrees(int64_t n, int64_t nnz, const int32_t* rp32, const int
         const int64_t last = rp64 ? rp64[n] : rp32[n];
         if (first != 0 || last != nnz) flag_error(err, DERR_ROW_PTR);
     }
-    for (int64_t i = warp; i < n; i += nwarps) {
-        const int64_t b = rp64 ? rp64[i] : rp32[i];
-        const int64_t e = rp64 ? rp64[i + 1] : rp32[i + 1];
-        if (e < b || b < 0 || e > nnz) {
-            if (lane == 0) flag_error(err, DERR_ROW_PTR);
-            continue;
+    const unsigned gmask = 0xffu << (8 * grp);   // this row's lanes
+    for (int64_t i0 = warp * 4; i0 < n; i0 += nwarps * 4) {
+        const int64_t i = i0 + grp;
+        const bool valid = i < n;
+        int64_t b = 0, e = 0;
+        bool bad_rp = false;
+        if (valid) {
+            b = rp64 ? rp64[i] : rp32[i];
+            e = rp64 ? rp64[i + 1] : rp32[i + 1];
+            bad_rp = e < b || b < 0 || e > nnz;
         }
         bool bad_range = false, bad_loop = false;
-        for (int64_t p = b + lane; p < e; p += 32) {
-            const int32_t j = __ldg(col + p);
-            bad_range |= (j < 0 || (int64_t)j >= n);
-            bad_loop |= ((int64_t)j == i);
+        if (valid && !bad_rp) {
+            for (int64_t p = b + sub; p < e; p += 8) {
+                const int32_t j = __ldg(col + p);
+                bad_range |= (j < 0 || (int64_t)j >= n);
+                bad_loop |= ((int64_t)j == i);
+            }
         }
-        if (__any_sync(0xffffffffu, bad_range) && lane == 0) flag_error(err, DERR_COL_RANGE);
-        if (__any_sync(0xffffffffu, bad_loop) && lane == 0) flag_error(err, DERR_SELF_LOOP);
-        if (lane == 0) {
-            const int64_t d = e - b;
-            deg[i] = (int32_t)d;
-            rs[i] = d > 0 ? rsqrtf((float)d) : 0.0f;
-            rsh[i] = rsqrtf((float)(d + 1));
-            if (heavy && d > 256) heavy[atomicAdd(heavy_count, 1)] = (int32_t)i;   // HEAVY_DEG
+        const unsigned mr = __ballot_sync(0xffffffffu, bad_range), ml = __ballot_sync(0xffffffffu, bad_loop);
+        if (valid && sub == 0) {
+            if (bad_rp) {
+                flag_error(err, DERR_ROW_PTR);
+            } else {
+                if (mr & gmask) flag_error(err, DERR_COL_RANGE);
+                if (ml & gmask) flag_error(err, DERR_SELF_LOOP);
+                const int64_t d = e - b;
+                deg[i] = (int32_t)d;
+                rs[i] = d > 0 ? rsqrtf((float)d) : 0.0f;
+                rsh[i] = rsqrtf((float)(d + 1));
+                if (heavy && d > 256) heavy[atomicAdd(heavy_count, 1)] = (int32_t)i;   // HEAVY_DEG
+            }
         }
     }
 }

@@ -322,19 +322,20 @@ __global__ void __launch_bounds__(FL_WARPS * 32) k_spmm_flat(FlatArgs a, const _
 // CSR of A + I: row i holds i first, then its neighbours in their stored order.
 __global__ void k_self_csr(int64_t n, const int32_t* rp32, const int64_t* rp64, const int32_t* col, int64_t* rp_self,
                            int32_t* col_self) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = warp; i < n; i += nwarps) {
+    // 8 lanes per row, 4 rows per warp in flight
+    const int sub = threadIdx.x & 7;
+    const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3;
+    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) >> 3;
+    for (int64_t i = grp; i < n; i += ngrp) {
         const int64_t b = rp64 ? rp64[i] : rp32[i];
         const int64_t e = rp64 ? rp64[i + 1] : rp32[i + 1];
         const int64_t o = b + i;
-        if (lane == 0) {
+        if (sub == 0) {
             rp_self[i] = o;
             col_self[o] = (int32_t)i;
             if (i == n - 1) rp_self[n] = e + n;
         }
-        for (int64_t p = b + lane; p < e; p += 32) col_self[o + 1 + (p - b)] = __ldg(col + p);
+        for (int64_t p = b + sub; p < e; p += 8) col_self[o + 1 + (p - b)] = __ldg(col + p);
     }
 }
 
