@@ -52,7 +52,7 @@ typedef enum {
     RAFTGP_ENOMEM = 2,      /* workspace too small */
     RAFTGP_ECUDA = 3,       /* a CUDA runtime call failed */
     RAFTGP_ETIMEOUT = 4,    /* a bounded device-side wait gave up */
-    RAFTGP_EUNSUPPORTED = 5 /* a size or mode this build does not support */
+    RAFTGP_EUNSUPPORTED = 5 /* a size or mode the library does not support */
 } raftgp_status;
 
 enum { RAFTGP_OP_NCUT = 0, RAFTGP_OP_MOD_FULL = 1, RAFTGP_OP_MOD_REDUCED = 2 };

@@ -2,7 +2,7 @@
 
 NMI with the arithmetic-mean normalisation I(U;V) / ((H(U)+H(V))/2), and the
 Hubert-Arabie adjusted Rand index, both from an exact int64 contingency table.
-These judge a partition; they are not part of the partitioning path.
+These evaluate a partition; they are not part of the partitioning path.
 """
 from __future__ import annotations
 
