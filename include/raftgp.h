@@ -174,15 +174,21 @@ raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype,
  * device memory it may use before it starts partitioning.  The paper has no counterpart;
  * this is a deployment variant of the seeding step.
  * Its scratch (the D^2 array, nearest-seed indices, chosen-point flags, block sums and grid
- * barrier words, about 7 bytes per point) is a file-scope device array of RAFTGP_NOALLOC_SCRATCH_BYTES that every GPU which
- * loads this library holds until the process exits.  n above RAFTGP_NOALLOC_MAX_N (or K above
- * 32767) is rejected with RAFTGP_EUNSUPPORTED before any work is queued.  The call allocates nothing:
- * no cudaMalloc, cudaFree or allocating library routine.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call uses the same array, which keeps the previous
- * call's contents (the call clears what must start at zero): calls whose work overlaps on the
- * GPU (other streams, other host threads) race on it and must not be issued.  Same arguments,
- * results and status codes as raftgp_kmeanspp otherwise; asynchronous. */
+ * barrier words, about 7 bytes per point) is a file-scope device array of
+ * RAFTGP_NOALLOC_SCRATCH_BYTES.  Each CUDA context that runs the call holds its own copy until
+ * the context ends.  With lazy module loading (CUDA_MODULE_LOADING=LAZY, the default) the
+ * array's memory is committed by the first call in a context, not when the library is loaded:
+ * a caller that reserves all the remaining device memory up front makes one call (any small
+ * n) before reserving.  n above RAFTGP_NOALLOC_MAX_N (or K above 32767) is rejected with
+ * RAFTGP_EUNSUPPORTED before any work is queued.  The call allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine.  The array's device address belongs to the context:
+ * the first call in each context (the one current on the calling thread, else the device's
+ * primary context) looks it up (cudaGetSymbolAddress) and caches it under the context's unique
+ * id, so make that first call before any stream capture.  Every call in a context uses the same
+ * array, which keeps the previous call's contents (the call clears what must start at zero):
+ * calls whose work overlaps on the GPU (other streams, other host threads) race on it and must
+ * not be issued.  Same arguments, results and status codes as raftgp_kmeanspp otherwise;
+ * asynchronous. */
 #define RAFTGP_NOALLOC_SCRATCH_BYTES (32u << 20) /* 32 MiB */
 #define RAFTGP_NOALLOC_MAX_N 4500000
 raftgp_status raftgp_kmeanspp_noalloc(const void* Z, int64_t n, int32_t d, int32_t z_dtype, int32_t K, uint64_t seed,

@@ -197,6 +197,16 @@ WORKLOADS = {
 }
 
 
+def fingerprint(g: Graph) -> str:
+    """SHA-256 of the CSR arrays (little-endian int64 row_ptr, then int32 col): identifies a
+    generated graph, so stored results can be matched to the graph they were computed on."""
+    import hashlib
+    h = hashlib.sha256()
+    h.update(np.ascontiguousarray(g.row_ptr, dtype="<i8").tobytes())
+    h.update(np.ascontiguousarray(g.col, dtype="<i4").tobytes())
+    return h.hexdigest()
+
+
 def workload(name: str, seed: int = 0) -> Graph:
     return dcsbm(seed=seed, **WORKLOADS[name])
 

@@ -56,6 +56,12 @@ def _check(rc, what):
         raise ValueError(f"oracle {what} failed with status {rc}")
 
 
+def set_threads(n=0):
+    """Threads for the oracle's parallel loops (0: the OpenMP default, all cores); returns the
+    count in effect.  Results are bit-identical for any count."""
+    return int(lib().orc_set_threads(C.c_int(int(n))))
+
+
 def philox4x32_10(ctr, key):
     c = np.asarray(ctr, dtype=np.uint32)
     k = np.asarray(key, dtype=np.uint32)

@@ -1,7 +1,7 @@
 /*
  * raftgp_oracle.c -- TEST INFRASTRUCTURE ONLY.
  *
- * A plain, slow, single-threaded FP64 CPU restatement of RaftGP's hot path
+ * A plain, slow FP64 CPU restatement of RaftGP's hot path
  * (Gao et al., "RaftGP: Random Fast Graph Partitioning", HPEC 2023):
  *   random feature extraction   (Section III-A, Eq. 5)
  *   random GCN embedding        (Section III-B, Eq. 6 and the row l2-normalisation)
@@ -10,6 +10,12 @@
  * benchmark's CPU-baseline leg may load it; the library never does.  It shares no code,
  * header or table with the CUDA sources.  Every loop follows the definition it cites, in
  * the order the definition states, without blocking, fusion or reordering.
+ *
+ * Threads: where the iterations of a loop over rows or points are independent (each writes
+ * only its own row, point or cluster), the loop may be shared among OpenMP threads; every
+ * sum keeps its sequential order (per-point values are summed afterwards in index order,
+ * integer counts are exact), so every result is bit-identical for any thread count.
+ * orc_set_threads(1) runs everything on one thread.
  *
  * Conventions shared with the library by DEFINITION (each side writes its own code):
  *   - CSR: row_ptr int64[n+1], col int32[nnz]; symmetric, no self loops, no duplicates.
@@ -36,6 +42,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_OK 0
 #define ORC_EINVAL 1
@@ -43,6 +52,18 @@
 
 enum { ORC_OP_NCUT = 0, ORC_OP_MOD_FULL = 1, ORC_OP_MOD_REDUCED = 2 };
 enum { ORC_CRIT_MOD = 0, ORC_CRIT_NCUT = 1 };
+
+/* Number of threads for the parallel loops (n <= 0: the OpenMP default); returns the count
+ * in effect, 1 when the oracle was built without OpenMP. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 /* Counter word 3 of each random stream. */
 #define ORC_STREAM_THETA 0x54686574u   /* "Thet" */
@@ -158,6 +179,7 @@ int orc_project(int64_t n, const int64_t* row_ptr, const int32_t* col, int op, c
     double two_e = (double)row_ptr[n];
     for (int64_t i = 0; i < n * L; ++i) Y[i] = 0.0;
     if (op == ORC_OP_NCUT) {
+#pragma omp parallel for schedule(dynamic, 1024)
         for (int64_t i = 0; i < n; ++i) {
             int64_t di = degree(row_ptr, i);
             if (di == 0) continue;
@@ -175,6 +197,7 @@ int orc_project(int64_t n, const int64_t* row_ptr, const int32_t* col, int op, c
         if (!g) return ORC_ENOMEM;
         for (int64_t j = 0; j < n; ++j)          /* g = d^T Theta */
             for (int r = 0; r < L; ++r) g[r] += (double)degree(row_ptr, j) * theta[j * L + r];
+#pragma omp parallel for schedule(dynamic, 1024)
         for (int64_t i = 0; i < n; ++i) {
             for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p)
                 for (int r = 0; r < L; ++r) Y[i * L + r] += theta[(int64_t)col[p] * L + r];
@@ -187,6 +210,7 @@ int orc_project(int64_t n, const int64_t* row_ptr, const int32_t* col, int op, c
         return ORC_OK;
     }
     if (op == ORC_OP_MOD_REDUCED) {
+#pragma omp parallel for schedule(dynamic, 1024)
         for (int64_t i = 0; i < n; ++i) {
             double di = (double)degree(row_ptr, i);
             for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
@@ -206,10 +230,18 @@ int orc_project(int64_t n, const int64_t* row_ptr, const int32_t* col, int op, c
 /* ------------------------------------------------------------------------------------ */
 int orc_gcn_layer(int64_t n, const int64_t* row_ptr, const int32_t* col, const double* Zin, int lin,
                   const double* W, int lout, double* Zout) {
+    int rc = ORC_OK;
+#pragma omp parallel
+    {
     double* agg = (double*)malloc(sizeof(double) * (size_t)lin);
     double* h = (double*)malloc(sizeof(double) * (size_t)lout);
-    if (!agg || !h) { free(agg); free(h); return ORC_ENOMEM; }
+    if (!agg || !h) {
+#pragma omp atomic write
+        rc = ORC_ENOMEM;
+    }
+#pragma omp for schedule(dynamic, 1024)
     for (int64_t i = 0; i < n; ++i) {
+        if (!agg || !h) continue;
         double rhi = 1.0 / sqrt((double)(degree(row_ptr, i) + 1));
         /* (A-hat_n Z_in)_i = sum over {i} U N(i) of rhi * rhj * Z_in[j] */
         for (int a = 0; a < lin; ++a) agg[a] = rhi * rhi * Zin[i * lin + a];
@@ -232,7 +264,8 @@ int orc_gcn_layer(int64_t n, const int64_t* row_ptr, const int32_t* col, const d
     }
     free(agg);
     free(h);
-    return ORC_OK;
+    }
+    return rc;
 }
 
 /* Rows `rows` of Y = X Theta (Eq. 5) for a large graph, drawing the Theta rows of each
@@ -399,10 +432,12 @@ int orc_kmeanspp(const double* Z, int64_t n, int d, int K, uint64_t seed, int fp
     int64_t first = (int64_t)mulhi64(kmpp_draw(seed, 0), (uint64_t)n);
     seeds[0] = first;
     chosen[first] = 1;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i)
         D2[i] = fp32_decision ? (double)sqdist32(Z + i * d, Z + first * d, d) : sqdist64(Z + i * d, Z + first * d, d);
     for (int t = 1; t < K; ++t) {
-        uint64_t total = 0;
+        uint64_t total = 0;   /* an exact integer sum: its value does not depend on the order */
+#pragma omp parallel for schedule(static) reduction(+ : total)
         for (int64_t i = 0; i < n; ++i) total += (uint64_t)(D2[i] * 1099511627776.0);
         int64_t pick = -1;
         if (total == 0) {
@@ -417,6 +452,7 @@ int orc_kmeanspp(const double* Z, int64_t n, int d, int K, uint64_t seed, int fp
         }
         seeds[t] = pick;
         chosen[pick] = 1;
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; ++i) {
             double nd = fp32_decision ? (double)sqdist32(Z + i * d, Z + pick * d, d) : sqdist64(Z + i * d, Z + pick * d, d);
             if (nd < D2[i]) D2[i] = nd;
@@ -437,13 +473,13 @@ int orc_kmeanspp(const double* Z, int64_t n, int d, int K, uint64_t seed, int fp
 int orc_lloyd(const double* Z, int64_t n, int d, int K, double* mu, int T, int32_t* labels, int* passes,
               double* objective) {
     int32_t* nl = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n ? n : 1));
-    double* sum = (double*)malloc(sizeof(double) * (size_t)d);
-    if (!nl || !sum) { free(nl); free(sum); return ORC_ENOMEM; }
+    double* bestd = (double*)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    if (!nl || !bestd) { free(nl); free(bestd); return ORC_ENOMEM; }
     for (int64_t i = 0; i < n; ++i) labels[i] = -1;
     int p = 0;
     for (p = 1; p <= T; ++p) {
         int64_t changed = 0;
-        double obj = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : changed)
         for (int64_t i = 0; i < n; ++i) {
             double best = 0.0;
             int bc = -1;
@@ -452,17 +488,31 @@ int orc_lloyd(const double* Z, int64_t n, int d, int K, double* mu, int T, int32
                 if (bc < 0 || dist < best) { best = dist; bc = c; }
             }
             nl[i] = bc;
-            obj += best;
+            bestd[i] = best;
             if (bc != labels[i]) ++changed;
         }
-        if (objective) objective[p - 1] = obj;
+        if (objective) {
+            double obj = 0.0;   /* summed in index order */
+            for (int64_t i = 0; i < n; ++i) obj += bestd[i];
+            objective[p - 1] = obj;
+        }
         if (changed == 0) break;
         for (int64_t i = 0; i < n; ++i) labels[i] = nl[i];
         if (p == T) break;   /* the returned centroids are those the final labels were assigned against */
+        int rc = ORC_OK;
+#pragma omp parallel
+        {
+        double* sum = (double*)malloc(sizeof(double) * (size_t)d);
+        if (!sum) {
+#pragma omp atomic write
+            rc = ORC_ENOMEM;
+        }
+#pragma omp for schedule(dynamic, 1)
         for (int c = 0; c < K; ++c) {
+            if (!sum) continue;
             int64_t cnt = 0;
             for (int k = 0; k < d; ++k) sum[k] = 0.0;
-            for (int64_t i = 0; i < n; ++i) {
+            for (int64_t i = 0; i < n; ++i) {   /* the members of c, in index order */
                 if (labels[i] != c) continue;
                 ++cnt;
                 for (int k = 0; k < d; ++k) sum[k] += Z[i * d + k];
@@ -470,10 +520,13 @@ int orc_lloyd(const double* Z, int64_t n, int d, int K, double* mu, int T, int32
             if (cnt > 0)
                 for (int k = 0; k < d; ++k) mu[(int64_t)c * d + k] = sum[k] / (double)cnt;
         }
+        free(sum);
+        }
+        if (rc != ORC_OK) { free(nl); free(bestd); return rc; }
     }
     *passes = p > T ? T : p;
     free(nl);
-    free(sum);
+    free(bestd);
     return ORC_OK;
 }
 

@@ -7,8 +7,13 @@
 // program's CUDA context, whose device memory is owned and budgeted by that program's own
 // allocator, or a host process that has reserved all the device memory it may use before it
 // starts partitioning.  raftgp_kmeanspp_noalloc serves them: its scratch is the file-scope
-// array below, which every GPU that loads this library holds until the process exits.
+// array below.  Each CUDA context that runs the call holds the array until the context ends
+// (with lazy module loading, the default, its memory is committed by the first call in that
+// context, not when the library is loaded).
+#include <cuda.h>
 #include <cuda_runtime.h>
+
+#include <mutex>
 
 #include "common.cuh"
 #include "internal.h"
@@ -25,23 +30,73 @@ static_assert((size_t)RAFTGP_NOALLOC_MAX_N * 7 + (RAFTGP_NOALLOC_MAX_N / 1024 + 
                   (size_t)RAFTGP_NOALLOC_SCRATCH_BYTES,
               "static scratch too small for RAFTGP_NOALLOC_MAX_N");
 
-// Device address of the scratch, looked up once per device (the host-side name of a
-// __device__ variable is not a device address).
-constexpr int kMaxDevices = 64;
-static void* g_scratch_ptr[kMaxDevices] = {};
+// Device address of the scratch.  The address of a __device__ variable belongs to the CUDA
+// context that loaded the module (its host-side name is not a device address at all), so it
+// is looked up once per context, with that context current, and cached under the context's
+// unique id (cuCtxGetId: never reused within a process, so a destroyed and re-created context,
+// or a second context on the same device, gets its own lookup).  With lazy module loading
+// (the default), the first lookup in a context is also what commits the array's device memory.
+// The cache is shared by every host thread, under a mutex.
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext*);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long*);
+
+constexpr int kCacheSlots = 64;
+struct ScratchSlot {
+    unsigned long long ctx_id;
+    void* ptr;
+};
+static std::mutex g_scratch_mu;
+static ScratchSlot g_scratch_cache[kCacheSlots] = {};
+static int g_scratch_next = 0;
+static PfnCtxGetCurrent g_ctx_get_current = nullptr;
+static PfnCtxGetId g_ctx_get_id = nullptr;
+
+static cudaError_t driver_fn(const char* name, void** fn) {
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion(name, fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !*fn) return cudaErrorNotSupported;
+    return cudaSuccess;
+}
+
+// The unique id of the context current on this thread (0 if none is current yet).
+static cudaError_t current_ctx_id(unsigned long long* id) {
+    *id = 0;
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+    if (!ctx) return cudaSuccess;
+    if (g_ctx_get_id(ctx, id) != CUDA_SUCCESS || *id == 0) return cudaErrorDeviceUninitialized;
+    return cudaSuccess;
+}
 
 static cudaError_t scratch_address(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_ptr[dev] = p;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    cudaError_t e;
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        if ((e = driver_fn("cuCtxGetCurrent", &f1)) != cudaSuccess) return e;
+        if ((e = driver_fn("cuCtxGetId", &f2)) != cudaSuccess) return e;
+        g_ctx_get_current = (PfnCtxGetCurrent)f1;
+        g_ctx_get_id = (PfnCtxGetId)f2;
     }
-    *out = g_scratch_ptr[dev];
+    unsigned long long id = 0;
+    if ((e = current_ctx_id(&id)) != cudaSuccess) return e;
+    if (id != 0)
+        for (int s = 0; s < kCacheSlots; ++s)
+            if (g_scratch_cache[s].ctx_id == id) {
+                *out = g_scratch_cache[s].ptr;
+                return cudaSuccess;
+            }
+    // a miss: look the address up in the current context (with no context current yet, the
+    // runtime first makes the device's primary context current, and that is the one used)
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    if (id == 0 && ((e = current_ctx_id(&id)) != cudaSuccess || id == 0))
+        return e != cudaSuccess ? e : cudaErrorDeviceUninitialized;
+    g_scratch_cache[g_scratch_next] = ScratchSlot{id, p};   // the oldest entry is replaced when full
+    g_scratch_next = (g_scratch_next + 1) % kCacheSlots;
+    *out = p;
     return cudaSuccess;
 }
 

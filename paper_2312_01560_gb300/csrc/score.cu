@@ -9,6 +9,10 @@
 //          denominator, one IEEE FP64 division
 //   NCut = 1/2 * sum_{r ascending, vol_r > 0} (vol_r - 2 m_r) / vol_r  -- FP64
 // so both are bit-identical to any other program that evaluates the same expressions.
+// Range: the host rejects nnz >= 2^31, so |numerator| and the denominator stay below
+// nnz^2 < 2^62 and the int64 terms are exact.  Their conversions to FP64 are exact while they
+// are below 2^53 (2e up to about 9.49e7); above that each conversion rounds the exact integer
+// once, to nearest, which any program converting the same integers reproduces bit for bit.
 #include <cuda_runtime.h>
 
 #include "common.cuh"

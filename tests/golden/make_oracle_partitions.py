@@ -1,0 +1,90 @@
+"""Write the FP64 oracle's partitions of the 50,000- and 1,000,000-node workloads.
+
+Calls only the oracle (``oracle/``) and the seeded input generator (``inputs/``); nothing
+here touches the CUDA library.  Each output file holds, for one workload:
+  - ``labels``: the oracle's chosen partition (Section III-C model selection on the FP64
+    embedding of Eq. 5 and Eq. 6);
+  - ``labels_z32``: the oracle's partition of the same embedding rounded once to FP32 (the
+    sensitivity of the k-means model selection to one single-precision rounding of Z);
+  - ``cands`` / ``cands_z32``: (K, Mod, NCut, Lloyd passes) per evaluated candidate;
+  - ``fingerprint``: SHA-256 of the graph's CSR (``inputs.dcsbm.fingerprint``), so a reader
+    checks that its graph is the one these labels belong to;
+  - the configuration (operator, layer widths, K range, grid, pass cap, seeds).
+
+  python tests/golden/make_oracle_partitions.py [dcsbm-50k] [dcsbm-1m] [--threads T]
+
+The 1,000,000-node run takes about an hour of CPU time on 8 cores (about 3e13 FP64
+operations in the k-means passes)."""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+from inputs.dcsbm import fingerprint, workload  # noqa: E402
+
+# Embedding seed 1, selection seed 2; the modularity operator applied as a sparse product plus
+# a rank-one term; ten coarse and ten refined candidates; at most 50 Lloyd passes.
+CONFIGS = {
+    "dcsbm-50k": dict(op="mod_full", dims=(128, 128, 64), kmin=2, kmax=100, grid=10, T=50,
+                      embed_seed=1, select_seed=2),
+    "dcsbm-1m": dict(op="mod_full", dims=(128, 128, 128, 128, 64), kmin=50, kmax=400, grid=10, T=50,
+                     embed_seed=1, select_seed=2),
+}
+
+
+def path_for(name: str) -> str:
+    return os.path.join(HERE, f"oracle_partition_{name}.npz")
+
+
+def load(name: str) -> dict:
+    """The stored partition of workload `name` as a dict (labels, labels_z32, k, k_z32, cands,
+    cands_z32, fingerprint, config)."""
+    with np.load(path_for(name)) as f:
+        out = {k: f[k] for k in f.files}
+    out["labels"] = out["labels"].astype(np.int32)
+    out["labels_z32"] = out["labels_z32"].astype(np.int32)
+    out["k"] = int(out["k"])
+    out["k_z32"] = int(out["k_z32"])
+    out["fingerprint"] = str(out["fingerprint"])
+    out["config"] = json.loads(str(out["config"]))
+    return out
+
+
+def make(name: str) -> None:
+    cfg = CONFIGS[name]
+    g = workload(name)
+    t0 = time.time()
+    _, Z = oracle.embed(g, cfg["op"], cfg["dims"], cfg["embed_seed"])
+    t1 = time.time()
+    print(f"{name}: embedding {t1 - t0:.1f} s", flush=True)
+    res = {}
+    for tag, Zin in (("", Z), ("_z32", Z.astype(np.float32).astype(np.float64))):
+        r = oracle.select(g, Zin, cfg["kmin"], cfg["kmax"], cfg["grid"], cfg["T"], cfg["select_seed"])
+        res["labels" + tag] = r["labels"].astype(np.uint16)
+        res["k" + tag] = np.int32(r["k"])
+        res["cands" + tag] = np.array(r["cands"], dtype=np.float64)
+        print(f"{name}{tag}: K* = {r['k']}, selection {time.time() - t1:.1f} s", flush=True)
+        t1 = time.time()
+    np.savez_compressed(path_for(name), fingerprint=np.str_(fingerprint(g)),
+                        config=np.str_(json.dumps(cfg)), **res)
+    print(f"wrote {path_for(name)}", flush=True)
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    ap.add_argument("names", nargs="*", default=list(CONFIGS))
+    ap.add_argument("--threads", type=int, default=0)
+    a = ap.parse_args()
+    print(f"oracle threads: {oracle.set_threads(a.threads)}", flush=True)
+    for nm in a.names:
+        make(nm)

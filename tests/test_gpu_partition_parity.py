@@ -1,0 +1,64 @@
+"""End-to-end partitions of the 50,000-node workload against the FP64 oracle's partition.
+
+The oracle's partition is stored in ``tests/golden/oracle_partition_dcsbm-50k.npz`` by
+``tests/golden/make_oracle_partitions.py`` (which calls only ``oracle/``): the modularity
+operator (Eq. 4, sparse product plus rank-one term) projected to 128 dimensions (Eq. 5), a
+128-128-64 random GCN (Eq. 6), and model selection (Section III-C) over ten coarse and ten
+refined K in [2, 100] with at most 50 Lloyd passes.  The FP32 GPU partition must reach
+NMI >= 0.99 against it and choose the same K; the BF16 form's agreement is stated."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from inputs.dcsbm import fingerprint, workload
+from paper_2312_01560_gb300 import api
+from paper_2312_01560_gb300.metrics import ari, nmi
+from tests.golden.make_oracle_partitions import load
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c2():
+    g = workload("dcsbm-50k")
+    ref = load("dcsbm-50k")
+    assert fingerprint(g) == ref["fingerprint"], "the generated graph differs from the one the oracle partitioned"
+    return g, ref
+
+
+def _partition(g, cfg, cuda, dtype, assign):
+    dg = api.DeviceGraph.from_host(g, cuda)
+    lab, rep = api.partition(dg, op=cfg["op"], dims=tuple(cfg["dims"]), dtype=dtype, embed_seed=cfg["embed_seed"],
+                             kmin=cfg["kmin"], kmax=cfg["kmax"], grid=cfg["grid"], iters=cfg["T"],
+                             assign=assign, select_seed=cfg["select_seed"])
+    torch.cuda.synchronize()
+    return lab.cpu().numpy(), rep
+
+
+def test_partition_50k_fp32_matches_oracle_partition(cuda, c2):
+    g, ref = c2
+    lab, rep = _partition(g, ref["config"], cuda, "f32", "ffma")
+    a = nmi(lab, ref["labels"])
+    ks = [c[0] for c in rep["cands"]]
+    assert ks == [int(k) for k in ref["cands"][:, 0]]     # same coarse grid, same refined grid
+    dmod = max(abs(c[1] - m) for c, m in zip(rep["cands"], ref["cands"][:, 1]))
+    print(f"dcsbm-50k FP32: K* gpu {rep['k']} oracle {ref['k']}; NMI(gpu, oracle) {a:.4f}, "
+          f"ARI {ari(lab, ref['labels']):.4f}; max |dMod| over candidates {dmod:.2e}; "
+          f"oracle vs its own FP32-rounded Z: NMI {nmi(ref['labels'], ref['labels_z32']):.4f}")
+    assert rep["k"] == ref["k"]
+    assert a >= 0.99
+    # the reported score of the chosen partition is bit-exact against the oracle scorer
+    _, _, mod, _ = oracle.score(g, lab, int(lab.max()) + 1)
+    assert [c[1] for c in rep["cands"] if c[0] == rep["k"]][0] == mod
+
+
+@pytest.mark.parametrize("assign", ["tc", "tc8"])
+def test_partition_50k_bf16_drift_against_oracle(cuda, c2, assign):
+    g, ref = c2
+    lab, rep = _partition(g, ref["config"], cuda, "bf16", assign)
+    a = nmi(lab, ref["labels"])
+    print(f"dcsbm-50k BF16/{assign}: K* gpu {rep['k']} oracle {ref['k']}; NMI(gpu, oracle) {a:.4f}, "
+          f"ARI {ari(lab, ref['labels']):.4f}; NMI vs planted gpu {nmi(lab, g.planted):.4f} "
+          f"oracle {nmi(ref['labels'], g.planted):.4f}")
+    assert a >= 0.9

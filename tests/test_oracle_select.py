@@ -193,3 +193,42 @@ def test_hierarchical_select_refines_around_best():
     best = max(r["cands"], key=lambda c: (c[1], -c[0]))
     assert r["k"] == best[0]
     assert nmi(r["labels"], g.planted) > 0.95
+
+
+def test_oracle_results_do_not_depend_on_thread_count():
+    # the parallel loops write only their own rows, points or clusters and every floating-point
+    # sum keeps its sequential order, so one thread and four give the same bits
+    from inputs.dcsbm import workload
+    g = workload("dcsbm-1k")
+    runs = []
+    for t in (1, 4):
+        oracle.set_threads(t)
+        Y, Z = oracle.embed(g, "mod_full", (64, 64, 32), seed=1)
+        r = oracle.select(g, Z, 2, 30, grid=0, T=50, seed=2)
+        _, _, _, obj = oracle.lloyd(Z, Z[:7], 20, with_objective=True)
+        runs.append((Y, Z, r, obj))
+    oracle.set_threads(0)
+    (Y1, Z1, r1, o1), (Y4, Z4, r4, o4) = runs
+    assert np.array_equal(Y1, Y4) and np.array_equal(Z1, Z4) and np.array_equal(o1, o4)
+    assert r1["k"] == r4["k"] and r1["cands"] == r4["cands"] and np.array_equal(r1["labels"], r4["labels"])
+
+
+@pytest.mark.parametrize("name", ["dcsbm-50k", "dcsbm-1m"])
+def test_stored_oracle_partition_is_consistent(name):
+    # the stored partition belongs to the graph the generator draws here, its candidate scores
+    # are the oracle scorer's, and K* is the best of them (exact ties to the smaller K)
+    import os
+    from inputs.dcsbm import fingerprint, workload
+    from tests.golden.make_oracle_partitions import load, path_for
+    if not os.path.exists(path_for(name)):
+        pytest.skip(f"no stored oracle partition for {name}")
+    ref = load(name)
+    g = workload(name)
+    assert fingerprint(g) == ref["fingerprint"]
+    for tag in ("", "_z32"):
+        lab, cands, k = ref["labels" + tag], ref["cands" + tag], ref["k" + tag]
+        best = max(range(len(cands)), key=lambda i: (cands[i, 1], -cands[i, 0]))
+        assert int(cands[best, 0]) == k
+        assert lab.min() >= 0 and lab.max() < k
+        _, _, mod, ncut = oracle.score(g, lab, k)
+        assert mod == cands[best, 1] and ncut == cands[best, 2]
