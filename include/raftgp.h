@@ -64,6 +64,19 @@ enum { RAFTGP_CRIT_MOD = 0, RAFTGP_CRIT_NCUT = 1 };
  * (8-bit centroid products; the final assignment is still hi + lo with the FP32 re-check)
  * (RAFTGP_ASSIGN_TC8). */
 enum { RAFTGP_ASSIGN_FFMA = 0, RAFTGP_ASSIGN_TC = 1, RAFTGP_ASSIGN_TC8 = 2 };
+/* Re-check of near ties in the assignment whose labels are reported (the final assignment of
+ * every candidate).  Its scores carry a bounded rounding error (the bound is derived in
+ * assign_tc.cu and assign_ffma.cu from the operand splits and FP32 accumulation); every
+ * (point, candidate) whose best two scores lie within twice that bound (plus a 25% margin) is
+ * recomputed in the direct form sum_k (z_k - mu_k)^2 over ascending coordinates, each operation
+ * rounded on its own:
+ *   RAFTGP_RECHECK_NONE: no re-check (tensor cores: labels straight from the BF16 hi + lo scores);
+ *   RAFTGP_RECHECK_FP32: in FP32 (tensor cores; the FP32 engine already reports the FP32 argmin);
+ *   RAFTGP_RECHECK_FP64: in FP64 (both engines): every reported label is then the argmin of the
+ *     FP64 direct-form distance from the stored z (BF16 or FP32) to the FP32 centroid, lowest
+ *     index on ties, i.e. the same label an FP64 program evaluating that expression returns.
+ * The FP32 engine needs one more assignment pass for RAFTGP_RECHECK_FP64. */
+enum { RAFTGP_RECHECK_NONE = 0, RAFTGP_RECHECK_FP32 = 1, RAFTGP_RECHECK_FP64 = 2 };
 
 #define RAFTGP_MAX_LAYERS 4
 #define RAFTGP_MAX_BATCH_CAND 64 /* candidates evaluated together in one batch */
@@ -100,6 +113,7 @@ typedef struct {
     int32_t assign;     /* RAFTGP_ASSIGN_FFMA, RAFTGP_ASSIGN_TC or RAFTGP_ASSIGN_TC8 */
     int32_t batch;      /* candidates evaluated together (1 = one at a time, the plain form;
                            0 = as many as fit, at most RAFTGP_MAX_BATCH_CAND) */
+    int32_t recheck;    /* RAFTGP_RECHECK_*: near-tie re-check of the reported labels */
     uint64_t seed;      /* Philox4x32-10 key for k-means++ */
 } raftgp_select_opts;
 
@@ -160,13 +174,16 @@ raftgp_status raftgp_kmeanspp(const void* Z, int64_t n, int32_t d, int32_t z_dty
 
 /* Lloyd's k-means alone from given FP32 initial centroids mu0 (device K x d): at most
  * `iters` assignment passes, ties to the lowest centroid, stop when no label changes, an
- * empty cluster keeps its centroid.  labels: device int32[N]; mu_out: device FP32 K x d
- * (may be NULL); *passes (host): assignment passes used.  `assign` picks the distance
- * engine.  ws: raftgp_lloyd_workspace_size(n, d, K) bytes.  Synchronises the stream. */
+ * empty cluster keeps its centroid.  labels: device int32[N], assigned against the returned
+ * centroids; mu_out: device FP32 K x d (may be NULL); *passes (host): assignment passes
+ * used.  `assign` picks the distance engine, `recheck` (RAFTGP_RECHECK_*) the near-tie
+ * re-check of the reported labels; with iters = 1 and RAFTGP_RECHECK_FP64 the labels are the
+ * FP64 direct-form argmin against mu0 itself.  ws: raftgp_lloyd_workspace_size(n, d, K)
+ * bytes.  Synchronises the stream. */
 size_t raftgp_lloyd_workspace_size(int64_t n, int32_t d, int32_t K);
 raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype, const float* mu0, int32_t K,
-                           int32_t iters, int32_t assign, int32_t* labels, float* mu_out, int32_t* passes,
-                           void* ws, size_t ws_bytes, raftgp_stream_t stream);
+                           int32_t iters, int32_t assign, int32_t recheck, int32_t* labels, float* mu_out,
+                           int32_t* passes, void* ws, size_t ws_bytes, raftgp_stream_t stream);
 
 /* k-means++ seeding exactly as raftgp_kmeanspp, for callers that cannot allocate device
  * memory: for example a plugin running inside another program's CUDA context, whose device

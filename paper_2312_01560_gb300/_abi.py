@@ -17,6 +17,7 @@ OP = {"ncut": 0, "mod_full": 1, "mod_reduced": 2}
 DTYPE = {"f32": 0, "bf16": 1}
 CRIT = {"mod": 0, "ncut": 1}
 ASSIGN = {"ffma": 0, "tc": 1, "tc8": 2}
+RECHECK = {"none": 0, "fp32": 1, "fp64": 2}
 MAX_LAYERS = 4
 MAX_BATCH_CAND = 64
 
@@ -61,7 +62,8 @@ class BatchOpts(C.Structure):
 
 class SelectOpts(C.Structure):
     _fields_ = [("kmin", C.c_int32), ("kmax", C.c_int32), ("grid", C.c_int32), ("iters", C.c_int32),
-                ("criterion", C.c_int32), ("assign", C.c_int32), ("batch", C.c_int32), ("seed", C.c_uint64)]
+                ("criterion", C.c_int32), ("assign", C.c_int32), ("batch", C.c_int32), ("recheck", C.c_int32),
+                ("seed", C.c_uint64)]
 
 
 class SelectResult(C.Structure):
@@ -104,8 +106,8 @@ def lib():
         L.raftgp_kmeanspp.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P, P, C.c_size_t, P]
         L.raftgp_kmeanspp_noalloc.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P, P]
         L.raftgp_kmeanspp_noalloc.restype = C.c_int
-        L.raftgp_lloyd.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, P, C.c_int32, C.c_int32, C.c_int32, P, P,
-                                   C.POINTER(C.c_int32), P, C.c_size_t, P]
+        L.raftgp_lloyd.argtypes = [P, C.c_int64, C.c_int32, C.c_int32, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                   P, P, C.POINTER(C.c_int32), P, C.c_size_t, P]
         for name in ("raftgp_embed", "raftgp_select", "raftgp_partition", "raftgp_score", "raftgp_kmeanspp",
                      "raftgp_lloyd"):
             getattr(L, name).restype = C.c_int

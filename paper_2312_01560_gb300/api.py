@@ -87,12 +87,17 @@ def embed_opts(op="ncut", dims=(64, 64, 32), dtype="f32", seed=1, theta=None, W=
     return o
 
 
-def select_opts(kmin=2, kmax=40, grid=0, iters=50, criterion="mod", assign="ffma", batch=0, seed=2):
+def _code(table, v):
+    return table[v] if isinstance(v, str) else int(v)
+
+
+def select_opts(kmin=2, kmax=40, grid=0, iters=50, criterion="mod", assign="ffma", batch=0, seed=2, recheck="fp32"):
     o = _abi.SelectOpts()
     o.kmin, o.kmax, o.grid, o.iters = int(kmin), int(kmax), int(grid), int(iters)
-    o.criterion = _abi.CRIT[criterion] if isinstance(criterion, str) else int(criterion)
-    o.assign = _abi.ASSIGN[assign] if isinstance(assign, str) else int(assign)
+    o.criterion = _code(_abi.CRIT, criterion)
+    o.assign = _code(_abi.ASSIGN, assign)
     o.batch = int(batch)
+    o.recheck = _code(_abi.RECHECK, recheck)
     o.seed = int(seed)
     return o
 
@@ -141,10 +146,10 @@ def _unpack(r, keep):
 
 
 def select(g: DeviceGraph, Z: torch.Tensor, kmin=2, kmax=40, grid=0, iters=50, criterion="mod", assign="ffma",
-           batch=0, seed=2, stream=None, labels=None):
+           batch=0, seed=2, stream=None, labels=None, recheck="fp32"):
     """Stage 3: returns (labels int32[N] on the device, report dict)."""
     code = 1 if Z.dtype == torch.bfloat16 else 0
-    o = select_opts(kmin, kmax, grid, iters, criterion, assign, batch, seed)
+    o = select_opts(kmin, kmax, grid, iters, criterion, assign, batch, seed, recheck)
     csr = g.csr()
     d = Z.shape[1]
     nbytes = lib().raftgp_workspace_size(C.byref(csr), None, C.byref(o), d)
@@ -160,12 +165,13 @@ def select(g: DeviceGraph, Z: torch.Tensor, kmin=2, kmax=40, grid=0, iters=50, c
 
 
 def partition(g: DeviceGraph, op="ncut", dims=(64, 64, 32), dtype="f32", embed_seed=1, kmin=2, kmax=40, grid=0,
-              iters=50, criterion="mod", assign="ffma", batch=0, select_seed=2, stream=None, labels=None, W=None):
+              iters=50, criterion="mod", assign="ffma", batch=0, select_seed=2, stream=None, labels=None, W=None,
+              recheck="fp32"):
     """Stages 1-3 end to end: returns (labels, report).  W: optional GNN weights (FP32)."""
     if W is not None:
         W = [w.to(g.col.device, torch.float32).contiguous() for w in W]
     eo = embed_opts(op, dims, dtype, embed_seed, None, W)
-    so = select_opts(kmin, kmax, grid, iters, criterion, assign, batch, select_seed)
+    so = select_opts(kmin, kmax, grid, iters, criterion, assign, batch, select_seed, recheck)
     csr = g.csr()
     nbytes = lib().raftgp_workspace_size(C.byref(csr), C.byref(eo), C.byref(so), 0)
     ws = _workspace(nbytes, g.col.device)
@@ -210,7 +216,7 @@ def kmeanspp(Z: torch.Tensor, K: int, seed: int, stream=None):
     return seeds
 
 
-def lloyd(Z: torch.Tensor, mu0: torch.Tensor, iters=50, assign="ffma", stream=None):
+def lloyd(Z: torch.Tensor, mu0: torch.Tensor, iters=50, assign="ffma", recheck="fp32", stream=None):
     """Lloyd's iterations from mu0: returns (labels int32[N], mu float32[K, d], passes)."""
     n, d = Z.shape
     K = mu0.shape[0]
@@ -222,7 +228,7 @@ def lloyd(Z: torch.Tensor, mu0: torch.Tensor, iters=50, assign="ffma", stream=No
     passes = C.c_int32(0)
     Zc = Z.contiguous()
     check(lib().raftgp_lloyd(C.c_void_p(Zc.data_ptr()), n, d, code, C.c_void_p(m0.data_ptr()), int(K),
-                             int(iters), _abi.ASSIGN[assign] if isinstance(assign, str) else int(assign),
+                             int(iters), _code(_abi.ASSIGN, assign), _code(_abi.RECHECK, recheck),
                              C.c_void_p(labels.data_ptr()), C.c_void_p(mu.data_ptr()), C.byref(passes),
                              C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
     return labels, mu, passes.value

@@ -77,6 +77,8 @@ static raftgp_status check_select(const raftgp_select_opts* o, int64_t n) {
     if (o->iters < 1) return fail(RAFTGP_EINVAL, "iters must be >= 1");
     if (o->criterion != RAFTGP_CRIT_MOD && o->criterion != RAFTGP_CRIT_NCUT) return fail(RAFTGP_EINVAL, "unknown criterion");
     if (o->assign < RAFTGP_ASSIGN_FFMA || o->assign > RAFTGP_ASSIGN_TC8) return fail(RAFTGP_EINVAL, "unknown assign engine");
+    if (o->recheck < RAFTGP_RECHECK_NONE || o->recheck > RAFTGP_RECHECK_FP64)
+        return fail(RAFTGP_EINVAL, "unknown recheck mode");
     if (o->batch < 0) return fail(RAFTGP_EINVAL, "batch < 0");
     return RAFTGP_OK;
 }
@@ -161,6 +163,7 @@ constexpr int kMaxBatchCols = 65536;
 static void carve_km(Carver& c, KmState& km, int64_t kcap, int d, int64_t n, int cs) {
     const int64_t kp = kpad_of(kcap);
     km.mu = c.take<float>((size_t)kp * d);
+    km.muT = c.take<float>((size_t)kp * d);
     km.norm2 = c.take<float>(kp + 64);
     km.norm2p = c.take<float>(kp + 64);
     km.sums = c.take<long long>((size_t)kp * d);
@@ -354,24 +357,29 @@ static bool host_better(int criterion, const CandRecord& a, const CandRecord& b)
     return a.k < b.k;
 }
 
-// Lloyd passes for one batch.  Tensor-core engine: FAST passes, then one FINAL assignment
-// with the FP32 re-check of near ties (the reported labels).
+// Lloyd passes for one batch.  Tensor-core engine: FAST passes, then one FINAL assignment (the
+// reported labels) whose near ties are re-checked in the direct form (FP32, or FP64 for
+// recheck = 2).  FP32 engine: its passes already report the FP32 argmin; recheck = 2 adds a
+// FINAL pass that lists its near ties for the FP64 re-check.
 static raftgp_status run_lloyd(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, int iters, int engine,
-                               KmState km, int2* recheck, int* recheck_count, uint32_t* err, cudaStream_t s) {
+                               int recheck, KmState km, int2* recheck_list, int* recheck_count, uint32_t* err,
+                               cudaStream_t s) {
+    const bool tc = engine != RAFTGP_ASSIGN_FFMA;
     for (int pass = 1; pass <= iters; ++pass) {
-        const bool tc = engine != RAFTGP_ASSIGN_FFMA;
         cudaError_t e = tc ? launch_assign_tc(b, Z, n, d, km, pass, 0, engine == RAFTGP_ASSIGN_TC ? 1 : 0, nullptr,
                                               nullptr, err, s)
-                           : launch_assign_ffma(b, Z, zdtype, n, d, km, pass, s);
+                           : launch_assign_ffma(b, Z, zdtype, n, d, km, pass, 0, nullptr, nullptr, s);
         if (e != cudaSuccess) return cuda_fail(e, "assign");
         if (tc) launch_apply_changes(b, Z, zdtype, n, d, km, pass, s);
         launch_lloyd_update(b, d, km, pass, iters, s);
     }
-    if (engine != RAFTGP_ASSIGN_FFMA) {
+    if (tc || recheck == RAFTGP_RECHECK_FP64) {
         cudaMemsetAsync(recheck_count, 0, sizeof(int), s);
-        cudaError_t e = launch_assign_tc(b, Z, n, d, km, iters + 1, 1, 1, recheck, recheck_count, err, s);
+        cudaError_t e = tc ? launch_assign_tc(b, Z, n, d, km, iters + 1, 1, 1, recheck_list, recheck_count, err, s)
+                           : launch_assign_ffma(b, Z, zdtype, n, d, km, iters + 1, 1, recheck_list, recheck_count, s);
         if (e != cudaSuccess) return cuda_fail(e, "final assign");
-        launch_recheck(b, Z, d, km, recheck, recheck_count, s);
+        if (recheck != RAFTGP_RECHECK_NONE)
+            launch_recheck(b, Z, zdtype, d, km, recheck_list, recheck_count, recheck == RAFTGP_RECHECK_FP64 ? 1 : 0, s);
     }
     return RAFTGP_OK;
 }
@@ -415,7 +423,8 @@ static raftgp_status run_candidates(const raftgp_csr* g, const void* Z, int d, i
         b.total_k = off;
         assign_owners(b);
         launch_batch_init(b, Z, zdtype, n, d, w.seeds, nullptr, w.km, s);
-        raftgp_status st = run_lloyd(b, Z, zdtype, n, d, o->iters, o->assign, w.km, w.recheck, w.recheck_count, w.err, s);
+        raftgp_status st = run_lloyd(b, Z, zdtype, n, d, o->iters, o->assign, o->recheck, w.km, w.recheck, w.recheck_count,
+                                     w.err, s);
         if (st != RAFTGP_OK) return st;
         launch_score_batch(b, g, w.deg, w.km.labels, w.so, w.err, s);
         launch_select_best(b, w.so, o->criterion, w.best, w.km.labels, n, labels, s);
@@ -690,8 +699,8 @@ size_t raftgp_lloyd_workspace_size(int64_t n, int32_t d, int32_t K) {
 }
 
 raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype, const float* mu0, int32_t K,
-                           int32_t iters, int32_t assign, int32_t* labels, float* mu_out, int32_t* passes, void* ws,
-                           size_t ws_bytes, raftgp_stream_t stream) {
+                           int32_t iters, int32_t assign, int32_t recheck, int32_t* labels, float* mu_out,
+                           int32_t* passes, void* ws, size_t ws_bytes, raftgp_stream_t stream) {
     if (!Z || !mu0 || !labels || !ws || n < 1) return fail(RAFTGP_EINVAL, "NULL argument or n < 1");
     if ((uintptr_t)Z & 15) return fail(RAFTGP_EINVAL, "Z must be 16-byte aligned");
     if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d must be 32, 64 or 128");
@@ -700,11 +709,12 @@ raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype,
     if (assign < RAFTGP_ASSIGN_FFMA || assign > RAFTGP_ASSIGN_TC8) return fail(RAFTGP_EINVAL, "unknown assign engine");
     if (assign != RAFTGP_ASSIGN_FFMA && z_dtype != RAFTGP_BF16)
         return fail(RAFTGP_EINVAL, "tensor-core assignment needs BF16 embeddings");
+    if (recheck < RAFTGP_RECHECK_NONE || recheck > RAFTGP_RECHECK_FP64) return fail(RAFTGP_EINVAL, "unknown recheck mode");
     Carver c(ws);
     KmState km{};
     carve_km(c, km, pad64h(K), d, n, 8);
     uint32_t* err = c.take<uint32_t>(64);
-    int2* recheck = c.take<int2>((size_t)n);
+    int2* recheck_list = c.take<int2>((size_t)n);
     int* recheck_count = c.take<int>(64);
     if (ws_bytes < c.off) return fail(RAFTGP_ENOMEM, "workspace too small");
     cudaStream_t s = (cudaStream_t)stream;
@@ -716,7 +726,7 @@ raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype,
     b.total_k = pad64h(K);
     cudaMemsetAsync(err, 0, sizeof(uint32_t), s);
     launch_batch_init(b, Z, z_dtype, n, d, nullptr, mu0, km, s);
-    raftgp_status st = run_lloyd(b, Z, z_dtype, n, d, iters, assign, km, recheck, recheck_count, err, s);
+    raftgp_status st = run_lloyd(b, Z, z_dtype, n, d, iters, assign, recheck, km, recheck_list, recheck_count, err, s);
     if (st != RAFTGP_OK) return st;
     int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8);
     ProfScope ps(s, PF_OTHER, 1);

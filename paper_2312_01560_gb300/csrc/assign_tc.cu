@@ -33,6 +33,8 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 #include "tc_util.cuh"
@@ -406,41 +408,74 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
 }
 
-// FP32 direct-form re-check of the listed (point, candidate) pairs: one warp per pair, lanes
-// split the candidate's centroids, ascending coordinates per distance, ties to the lowest index.
-template <int D>
-__global__ void __launch_bounds__(256) k_recheck(CandBatch b, const __nv_bfloat16* __restrict__ Z, KmState st,
-                                                 const int2* list, const int* count) {
+// Direct-form re-check of the listed (point, candidate) pairs: one warp per pair, lanes split
+// the candidate's centroids, ||z - mu_c||^2 summed over ascending coordinates with every
+// subtract, multiply and add rounded on its own (no contraction), ties to the lowest index.
+// F64: in FP64 from the stored values (BF16 or FP32 z, FP32 mu, widened exactly), the same
+// expression as the FP64 oracle's, so the re-checked labels are the FP64 argmin bit for bit;
+// otherwise in FP32.
+template <typename T, int D, bool F64>
+__global__ void __launch_bounds__(256) k_recheck(CandBatch b, const T* __restrict__ Z, KmState st, const int2* list,
+                                                 const int* count) {
+    using R = typename std::conditional<F64, double, float>::type;
     const int lane = threadIdx.x & 31;
     const int total = *count;
     for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < total; e += (gridDim.x * blockDim.x) >> 5) {
         const int2 pc = list[e];
         const int64_t i = pc.x;
         const int c = pc.y;
-        float z[D];
+        R z[D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) z[k] = __bfloat162float(Z[i * D + k]);
+        for (int k = 0; k < D; ++k) z[k] = (R)Vec<T>::to_float(Z[i * D + k]);
         const int K = b.k[c], off = b.off[c];
-        float bv = INFINITY;
+        R bv = (R)INFINITY;
         int bi = 0x7fffffff;
         for (int j = lane; j < K; j += 32) {
             const float* mu = st.mu + (int64_t)(off + j) * D;
-            float s = 0.f;
+            R s = 0;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
-                const float t = __fsub_rn(z[k], mu[k]);
-                s = __fadd_rn(s, __fmul_rn(t, t));
+                if (F64) {
+                    const double t = __dsub_rn((double)z[k], (double)mu[k]);
+                    s = (R)__dadd_rn((double)s, __dmul_rn(t, t));
+                } else {
+                    const float t = __fsub_rn((float)z[k], mu[k]);
+                    s = (R)__fadd_rn((float)s, __fmul_rn(t, t));
+                }
             }
             if (s < bv) { bv = s; bi = j; }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const R ov = __shfl_xor_sync(0xffffffffu, bv, o);
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (ov < bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
         }
         if (lane == 0 && bi >= 0 && bi < K) st.labels[i * b.cs + c] = (int16_t)bi;
     }
+}
+
+// Error band of the final tensor-core assignment's scores.  Each score is
+//   s_c = fmaf(2, a_c, n_c),  a_c = the tensor-core sum of z_k hi_k and z_k lo_k (k < d),
+//   n_c = fl(fl(||mu_c||^2) + 4),  hi + lo = the two-term BF16 split of -mu_c,
+// and approximates t_c = ||mu_c||^2 + 4 - 2 z.mu_c from the stored z (BF16) and mu_c (FP32).
+// With BF16 unit roundoff 2^-8, FP32 unit roundoff u = 2^-24, ||z|| <= 1, ||mu_c|| <= 1:
+//   split:  hi = RN(-mu), lo = RN(-mu - hi) (the subtraction is exact), so
+//           |hi_k + lo_k + mu_k| <= 2^-16 |mu_k| and |z.(hi + lo) + z.mu| <= 2^-16;
+//   sum:    every product z_k hi_k, z_k lo_k is exact in FP32 (8-bit significands); the 2d
+//           products enter the FP32 accumulator 16 per MMA.  Modelled as each MMA rounding or
+//           truncating its 16 aligned products and the accumulator with an error of at most
+//           2^-23 of the largest magnitude per term: at most 17 * 2^-23 * S per MMA, d/8 MMAs,
+//           S = sum |z_k| (|hi_k| + |lo_k|) <= (1 + 2^-8)^2 < 1.01;
+//   norm:   ||mu||^2 as d fused multiply-adds: <= d u 1.01; the +4: <= 5 u;
+//   score:  the final fmaf, |s_c| <= 8: <= 8 u;
+//   E = 2 (2^-16 + (d/8) 17 2^-23 1.01) + 1.01 d u + 13 u.
+// Two scores whose exact order differs from their computed order lie within 2E; the band is
+// 2E with a 25% margin (also covering the FP64 re-check's own rounding, below 1e-13).
+float tc_tie_band(int d) {
+    const double u = 1.0 / 16777216.0;
+    const double E = 2.0 * (1.0 / 65536.0 + (d / 8.0) * 17.0 * (2.0 * u) * 1.01) + 1.01 * d * u + 13.0 * u;
+    return (float)(2.5 * E);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -503,7 +538,7 @@ static cudaError_t launch_tc_t(const CandBatch& b, const __nv_bfloat16* Z, int64
     a.st = st;
     a.pass = pass;
     a.key_mul = 64u;
-    a.tie_band = 1.5e-4f * (float)D / 64.0f + 2.0e-5f;
+    a.tie_band = tc_tie_band(D);
     a.recheck = recheck;
     a.recheck_count = recheck_count;
     a.err = err;
@@ -539,16 +574,21 @@ cudaError_t launch_assign_tc(const CandBatch& b, const void* Z, int64_t n, int d
     return cudaErrorInvalidValue;
 }
 
-void launch_recheck(const CandBatch& b, const void* Z, int d, KmState st, const int2* list, const int* count,
-                    cudaStream_t s) {
+void launch_recheck(const CandBatch& b, const void* Z, int zdtype, int d, KmState st, const int2* list,
+                    const int* count, int fp64, cudaStream_t s) {
     const int blocks = num_sms() * 4;
     ProfScope ps(s, PF_RECHECK, 1);
-    const __nv_bfloat16* z = (const __nv_bfloat16*)Z;
-    switch (d) {
-        case 32: k_recheck<32><<<blocks, 256, 0, s>>>(b, z, st, list, count); break;
-        case 64: k_recheck<64><<<blocks, 256, 0, s>>>(b, z, st, list, count); break;
-        case 128: k_recheck<128><<<blocks, 256, 0, s>>>(b, z, st, list, count); break;
+#define RAFTGP_RC(TT, DD)                                                                                  \
+    case DD:                                                                                               \
+        if (fp64) k_recheck<TT, DD, true><<<blocks, 256, 0, s>>>(b, (const TT*)Z, st, list, count);       \
+        else k_recheck<TT, DD, false><<<blocks, 256, 0, s>>>(b, (const TT*)Z, st, list, count);           \
+        break;
+    if (zdtype == RAFTGP_BF16) {
+        switch (d) { RAFTGP_RC(__nv_bfloat16, 32) RAFTGP_RC(__nv_bfloat16, 64) RAFTGP_RC(__nv_bfloat16, 128) }
+    } else {
+        switch (d) { RAFTGP_RC(float, 32) RAFTGP_RC(float, 64) RAFTGP_RC(float, 128) }
     }
+#undef RAFTGP_RC
 }
 
 }  // namespace raftgp

@@ -33,7 +33,7 @@ raftgp_status set_error(raftgp_status st, const char* fmt, ...);
 enum ProfFamily {
     PF_DEGREES, PF_THETA, PF_SPMM_PROJ, PF_SPMM_GCN, PF_DENSE_TC, PF_SEED_UPDATE, PF_SEED_PICK, PF_BATCH_INIT, PF_ASSIGN_FFMA,
     PF_ASSIGN_TC, PF_ASSIGN_TC_FIRST, PF_ASSIGN_TC_FINAL, PF_RECHECK, PF_APPLY, PF_APPLY_FIRST, PF_LLOYD_UPDATE, PF_SCORE,
-    PF_SELECT_BEST, PF_DIFF_SPMM, PF_DIFF_DENSE, PF_DIFF_LOSS, PF_DIFF, PF_OTHER, PF_COUNT
+    PF_SELECT_BEST, PF_DIFF_SPMM, PF_DIFF_DENSE, PF_DIFF_LOSS, PF_DIFF, PF_OTHER, PF_ASSIGN_FFMA_FINAL, PF_COUNT
 };
 // Brackets the kernels launched in its lifetime with CUDA events when profiling is on.
 class ProfScope {
@@ -129,6 +129,7 @@ struct CandBatch {
 
 struct KmState {                 // device arrays of one batch (workspace)
     float* mu;                   // total_k x d FP32 centroids
+    float* muT;                  // d x kpad: the same, k-major (row k holds coordinate k of every centroid)
     float* norm2;                // total_k, ||mu||^2 in FP32
     float* norm2p;               // kpad, ||mu||^2 + 4 (tensor-core epilogue: positive scores)
     long long* sums;             // total_k x d, 2^-40 fixed point
@@ -166,14 +167,16 @@ void set_seed_skip_block(int block);   // test hook of the persistent seeding
 void launch_batch_init(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, const int32_t* seeds,
                        const float* mu0, KmState st, cudaStream_t s);
 cudaError_t launch_assign_ffma(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, KmState st, int pass,
-                               cudaStream_t s);
+                               int final_mode, int2* recheck, int* recheck_count, cudaStream_t s);
+float ffma_tie_band(int d);
 void launch_lloyd_update(const CandBatch& b, int d, KmState st, int pass, int last_pass, cudaStream_t s);
 void launch_apply_changes(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, KmState st, int pass,
                           cudaStream_t s);
 cudaError_t launch_assign_tc(const CandBatch& b, const void* Z, int64_t n, int d, KmState st, int pass, int final_mode,
                              int fast_lo, int2* recheck, int* recheck_count, uint32_t* err, cudaStream_t s);
-void launch_recheck(const CandBatch& b, const void* Z, int d, KmState st, const int2* list, const int* count,
-                    cudaStream_t s);
+void launch_recheck(const CandBatch& b, const void* Z, int zdtype, int d, KmState st, const int2* list,
+                    const int* count, int fp64, cudaStream_t s);
+float tc_tie_band(int d);
 
 // ---- scoring (score.cu) ---------------------------------------------------------------
 struct ScoreOut {                // per batch

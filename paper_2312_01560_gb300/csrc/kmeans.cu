@@ -801,6 +801,7 @@ __device__ void write_row_operands(KmState st, int64_t row, int d, bool padding)
     if (padding) {
         for (int k = 0; k < d; ++k) {
             mu[k] = 0.f;
+            st.muT[(int64_t)k * st.bhi_rows + row] = 0.f;
             st.bhi[row * d + k] = __float2bfloat16_rn(0.f);
             st.blo[row * d + k] = __float2bfloat16_rn(0.f);
         }
@@ -816,6 +817,7 @@ __device__ void write_row_operands(KmState st, int64_t row, int d, bool padding)
     for (int k = 0; k < d; ++k) {
         const float v = mu[k];
         s = fmaf(v, v, s);
+        st.muT[(int64_t)k * st.bhi_rows + row] = v;
         split_bf16(-v, st.bhi + row * d + k, st.blo + row * d + k);
     }
     st.norm2[row] = s;
@@ -833,6 +835,7 @@ __device__ void warp_row_operands(KmState st, int64_t row, int d) {
     for (int k = lane; k < d; k += 32) {
         const float v = st.mu[row * d + k];
         s = fmaf(v, v, s);
+        st.muT[(int64_t)k * st.bhi_rows + row] = v;
         split_bf16(-v, st.bhi + row * d + k, st.blo + row * d + k);
     }
     s = warp_sum(s);
@@ -913,159 +916,6 @@ void launch_batch_init(const CandBatch& b, const void* Z, int zdtype, int64_t n,
     if (blocks > num_sms() * 8) blocks = num_sms() * 8;
     if (blocks < 1) blocks = 1;
     k_fill_labels<<<blocks, 256, 0, s>>>(st.labels, cnt);
-}
-
-// ------------------------------------------------------------------------------------
-// Plain FP32 assignment: CTA = 128 points x one candidate; centroids in chunks of 64.
-// Thread (pg, cg) owns points 4pg..4pg+3 and chunk centroids 8cg..8cg+7 (register tile).
-// After the scan, the label change is applied to the fixed-point sums and counts.
-// ------------------------------------------------------------------------------------
-constexpr int AS_TP = 128;  // points per CTA
-constexpr int AS_TC = 64;   // centroids per chunk
-
-template <typename T, int D>
-__global__ void __launch_bounds__(256) k_assign_ffma(CandBatch b, const T* __restrict__ Z, int64_t n, KmState st,
-                                                     int pass) {
-    const int c = blockIdx.y;
-    if (c >= b.n || !st.active[c]) return;
-    const int K = b.k[c], off = b.off[c];
-    extern __shared__ float sm[];
-    float* zT = sm;                     // D x AS_TP
-    float* mT = sm + D * AS_TP;         // D x AS_TC
-    float* nrm = mT + D * AS_TC;        // AS_TC
-    __shared__ int s_new[AS_TP], s_old[AS_TP];
-    const int64_t p0 = (int64_t)blockIdx.x * AS_TP;
-    for (int t = threadIdx.x; t < D * AS_TP; t += blockDim.x) {
-        const int p = t / D, k = t % D;
-        zT[k * AS_TP + p] = (p0 + p < n) ? zval(Z, (p0 + p) * D + k) : 0.f;
-    }
-    const int pg = threadIdx.x >> 3, cg = threadIdx.x & 7;
-    float bv[4];
-    int bi[4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) { bv[r] = INFINITY; bi[r] = 0x7fffffff; }
-    for (int c0 = 0; c0 < K; c0 += AS_TC) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < D * AS_TC; t += blockDim.x) {
-            const int j = t / D, k = t % D;
-            mT[k * AS_TC + j] = (c0 + j < K) ? st.mu[(int64_t)(off + c0 + j) * D + k] : 0.f;
-        }
-        for (int j = threadIdx.x; j < AS_TC; j += blockDim.x) nrm[j] = (c0 + j < K) ? st.norm2[off + c0 + j] : INFINITY;
-        __syncthreads();
-        float acc[4][8];
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
-#pragma unroll 4
-        for (int k = 0; k < D; ++k) {
-            const float4 zv = *reinterpret_cast<const float4*>(zT + k * AS_TP + 4 * pg);
-            const float4 m0 = *reinterpret_cast<const float4*>(mT + k * AS_TC + 8 * cg);
-            const float4 m1 = *reinterpret_cast<const float4*>(mT + k * AS_TC + 8 * cg + 4);
-            const float za[4] = {zv.x, zv.y, zv.z, zv.w};
-            const float ma[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(za[r], ma[q], acc[r][q]);
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const float nq = nrm[8 * cg + q];
-            const int idx = c0 + 8 * cg + q;
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const float s = fmaf(-2.0f, acc[r][q], nq);
-                if (s < bv[r]) { bv[r] = s; bi[r] = idx; }
-            }
-        }
-    }
-    // combine the 8 centroid groups (lanes differing in the low 3 bits)
-#pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const float ov = __shfl_xor_sync(0xffffffffu, bv[r], o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi[r], o);
-            if (ov < bv[r] || (ov == bv[r] && oi < bi[r])) { bv[r] = ov; bi[r] = oi; }
-        }
-    }
-    if (cg < 4) {
-        const int p = 4 * pg + cg;
-        const int64_t i = p0 + p;
-        int nl = -1, ol = -1;
-        if (i < n) {
-            nl = bi[cg];
-            if (nl < 0 || nl >= K) nl = 0;   // every score NaN (non-finite input): keep indices in range
-            int16_t* lp = st.labels + i * b.cs + c;
-            ol = *lp;
-            *lp = (int16_t)nl;
-        }
-        s_new[p] = nl;
-        s_old[p] = ol;
-    }
-    __shared__ int s_nch;
-    if (threadIdx.x == 0) s_nch = 0;
-    __syncthreads();
-    // label changes -> counts, fixed-point sums, changed counter
-    int nchanged = 0;
-    for (int p = threadIdx.x; p < AS_TP; p += blockDim.x) {
-        const int nl = s_new[p], ol = s_old[p];
-        if (nl >= 0 && nl != ol) {
-            ++nchanged;
-            atomicAdd(st.counts + off + nl, 1);
-            if (ol >= 0) atomicSub(st.counts + off + ol, 1);
-        }
-    }
-    for (int t = threadIdx.x; t < AS_TP * D; t += blockDim.x) {
-        const int p = t / D, k = t % D;
-        const int nl = s_new[p], ol = s_old[p];
-        if (nl < 0 || nl == ol) continue;
-        const long long v = __float2ll_rn(zT[k * AS_TP + p] * FIXED_SCALE_F);
-        atomicAdd(reinterpret_cast<unsigned long long*>(st.sums + (int64_t)(off + nl) * D + k), (unsigned long long)v);
-        if (ol >= 0)
-            atomicAdd(reinterpret_cast<unsigned long long*>(st.sums + (int64_t)(off + ol) * D + k),
-                      (unsigned long long)(-v));
-    }
-    // one global atomic per CTA on the candidate's change counter
-    nchanged = __reduce_add_sync(0xffffffffu, nchanged);
-    if ((threadIdx.x & 31) == 0 && nchanged) atomicAdd(&s_nch, nchanged);
-    __syncthreads();
-    if (threadIdx.x == 0 && s_nch) atomicAdd(st.changed + (pass & 1) * MAXC + c, s_nch);
-}
-
-template <typename T, int D>
-static cudaError_t launch_assign_t(const CandBatch& b, const T* Z, int64_t n, KmState st, int pass, cudaStream_t s) {
-    const size_t smem = (size_t)(D * AS_TP + D * AS_TC + AS_TC) * sizeof(float);
-    auto kern = k_assign_ffma<T, D>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    dim3 grid((unsigned)((n + AS_TP - 1) / AS_TP), b.n);
-    ProfScope ps(s, PF_ASSIGN_FFMA, 1);
-    kern<<<grid, 256, smem, s>>>(b, Z, n, st, pass);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_assign_ffma(const CandBatch& b, const void* Z, int zdtype, int64_t n, int d, KmState st, int pass,
-                               cudaStream_t s) {
-    if (zdtype == RAFTGP_BF16) {
-        const __nv_bfloat16* z = (const __nv_bfloat16*)Z;
-        switch (d) {
-            case 32: return launch_assign_t<__nv_bfloat16, 32>(b, z, n, st, pass, s);
-            case 64: return launch_assign_t<__nv_bfloat16, 64>(b, z, n, st, pass, s);
-            case 128: return launch_assign_t<__nv_bfloat16, 128>(b, z, n, st, pass, s);
-        }
-    } else {
-        const float* z = (const float*)Z;
-        switch (d) {
-            case 32: return launch_assign_t<float, 32>(b, z, n, st, pass, s);
-            case 64: return launch_assign_t<float, 64>(b, z, n, st, pass, s);
-            case 128: return launch_assign_t<float, 128>(b, z, n, st, pass, s);
-        }
-    }
-    return cudaErrorInvalidValue;
 }
 
 // ------------------------------------------------------------------------------------

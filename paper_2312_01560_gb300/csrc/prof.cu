@@ -14,7 +14,7 @@ namespace raftgp {
 static const char* kFamilyNames[PF_COUNT] = {
     "degrees", "theta", "spmm_project", "spmm_gcn", "dense_tc", "seed_update", "seed_pick", "batch_init", "assign_ffma",
     "assign_tc", "assign_tc_first", "assign_tc_final", "assign_recheck", "apply_changes", "apply_first", "lloyd_update",
-    "score_count", "select_best", "diff_spmm", "diff_dense", "diff_loss", "diff_other", "other"};
+    "score_count", "select_best", "diff_spmm", "diff_dense", "diff_loss", "diff_other", "other", "assign_ffma_final"};
 
 struct Profiler {
     std::mutex mu;
