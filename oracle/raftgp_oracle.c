@@ -274,16 +274,35 @@ int orc_gcn_layer(int64_t n, const int64_t* row_ptr, const int32_t* col, const d
 int orc_project_rows(int64_t n, const int64_t* row_ptr, const int32_t* col, int op, int L, uint64_t seed,
                      const int64_t* rows, int64_t n_rows, double* Y) {
     double two_e = (double)row_ptr[n];
-    double* th = (double*)malloc(sizeof(double) * (size_t)L);
+    const int64_t blk = 4096;
+    double* thb = (double*)malloc(sizeof(double) * (size_t)(blk * L));
     double* g = (double*)calloc((size_t)L, sizeof(double));
-    if (!th || !g) { free(th); free(g); return ORC_ENOMEM; }
+    if (!thb || !g) { free(thb); free(g); return ORC_ENOMEM; }
     if (op == ORC_OP_MOD_FULL) {
-        for (int64_t j = 0; j < n; ++j) {
-            orc_theta_rows(&j, 1, L, seed, th);
-            for (int r = 0; r < L; ++r) g[r] += (double)degree(row_ptr, j) * th[r];
+        /* g = d^T Theta over j ascending; the Theta rows of a block are drawn in parallel first */
+        for (int64_t j0 = 0; j0 < n; j0 += blk) {
+            const int64_t nb = n - j0 < blk ? n - j0 : blk;
+#pragma omp parallel for schedule(static)
+            for (int64_t t = 0; t < nb; ++t) {
+                int64_t j = j0 + t;
+                orc_theta_rows(&j, 1, L, seed, thb + t * L);
+            }
+            for (int64_t t = 0; t < nb; ++t)
+                for (int r = 0; r < L; ++r) g[r] += (double)degree(row_ptr, j0 + t) * thb[t * L + r];
         }
     }
+    free(thb);
+    int rc = ORC_OK;
+#pragma omp parallel
+    {
+    double* th = (double*)malloc(sizeof(double) * (size_t)L);
+    if (!th) {
+#pragma omp atomic write
+        rc = ORC_ENOMEM;
+    }
+#pragma omp for schedule(dynamic, 1)
     for (int64_t t = 0; t < n_rows; ++t) {
+        if (!th) continue;
         int64_t i = rows[t];
         double di = (double)degree(row_ptr, i);
         double* y = Y + t * L;
@@ -302,7 +321,9 @@ int orc_project_rows(int64_t n, const int64_t* row_ptr, const int32_t* col, int 
             for (int r = 0; r < L; ++r) y[r] -= di * g[r] / two_e;
     }
     free(th);
+    }
     free(g);
+    if (rc != ORC_OK) return rc;
     return (op >= ORC_OP_NCUT && op <= ORC_OP_MOD_REDUCED) ? ORC_OK : ORC_EINVAL;
 }
 
@@ -311,10 +332,18 @@ int orc_project_rows(int64_t n, const int64_t* row_ptr, const int32_t* col, int 
 int orc_gcn_rows(int64_t n, const int64_t* row_ptr, const int32_t* col, const float* Zin, int lin, const double* W,
                  int lout, const int64_t* rows, int64_t n_rows, double* Zout) {
     (void)n;
+    int rc = ORC_OK;
+#pragma omp parallel
+    {
     double* agg = (double*)malloc(sizeof(double) * (size_t)lin);
     double* h = (double*)malloc(sizeof(double) * (size_t)lout);
-    if (!agg || !h) { free(agg); free(h); return ORC_ENOMEM; }
+    if (!agg || !h) {
+#pragma omp atomic write
+        rc = ORC_ENOMEM;
+    }
+#pragma omp for schedule(dynamic, 1)
     for (int64_t t = 0; t < n_rows; ++t) {
+        if (!agg || !h) continue;
         int64_t i = rows[t];
         double rhi = 1.0 / sqrt((double)(degree(row_ptr, i) + 1));
         for (int a = 0; a < lin; ++a) agg[a] = rhi * rhi * (double)Zin[i * lin + a];
@@ -335,11 +364,12 @@ int orc_gcn_rows(int64_t n, const int64_t* row_ptr, const int32_t* col, const fl
     }
     free(agg);
     free(h);
-    return ORC_OK;
+    }
+    return rc;
 }
 
 /* Whole embedding: Y = X Theta, then n_layers GCN layers with widths dims[1..n_layers]
- * (dims[0] = L).  theta_in / W_in may be NULL (then drawn from `seed`); W_in, when given,
+ * (dims[0] = L); with n_layers = 0, Z = rownorm(Y).  theta_in / W_in may be NULL (then drawn from `seed`); W_in, when given,
  * is the concatenation of the row-major W^(1..n_layers).  Y_out may be NULL. */
 int orc_embed(int64_t n, const int64_t* row_ptr, const int32_t* col, int op, int n_layers, const int* dims,
               uint64_t seed, const double* theta_in, const double* W_in, double* Y_out, double* Z_out) {
@@ -376,6 +406,17 @@ int orc_embed(int64_t n, const int64_t* row_ptr, const int32_t* col, int op, int
         rc = orc_gcn_layer(n, row_ptr, col, a, lin, Wk, lout, b);
         free(W);
         double* t = a; a = b; b = t;
+    }
+    if (rc == ORC_OK && n_layers == 0) {
+        /* the "w/o Emb" ablation (Table IV): no GCN layer, so the model selection receives the
+         * random features themselves, row-normalised as every GCN output is (a zero row stays
+         * zero): the ablation removes the layers, not the normalised input of Section III-C */
+        for (int64_t i = 0; i < n; ++i) {
+            double s2 = 0.0;
+            for (int r = 0; r < L; ++r) s2 += a[i * L + r] * a[i * L + r];
+            double inv = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
+            for (int r = 0; r < L; ++r) a[i * L + r] *= inv;
+        }
     }
     if (rc == ORC_OK) memcpy(Z_out, a, sizeof(double) * (size_t)(n * dims[n_layers]));
     free(a);

@@ -10,8 +10,11 @@ here touches the CUDA library.  Each output file holds, for one workload:
   - ``fingerprint``: SHA-256 of the graph's CSR (``inputs.dcsbm.fingerprint``), so a reader
     checks that its graph is the one these labels belong to;
   - the configuration (operator, layer widths, K range, grid, pass cap, seeds).
+A second file per workload, ``oracle_stages_<name>.npz``, holds the oracle's values of every
+embedding stage (Y of Eq. 5, then Z^(1..n) of Eq. 6 with the row normalisation) on 64 seeded
+sample rows (63 uniform and the highest-degree node), for per-stage error reports.
 
-  python tests/golden/make_oracle_partitions.py [dcsbm-50k] [dcsbm-1m] [--threads T]
+  python tests/golden/make_oracle_partitions.py [dcsbm-50k] [dcsbm-1m] [--threads T] [--stages-only]
 
 The 1,000,000-node run takes about an hour of CPU time on 8 cores (about 3e13 FP64
 operations in the k-means passes)."""
@@ -44,6 +47,43 @@ CONFIGS = {
 
 def path_for(name: str) -> str:
     return os.path.join(HERE, f"oracle_partition_{name}.npz")
+
+
+def stages_path_for(name: str) -> str:
+    return os.path.join(HERE, f"oracle_stages_{name}.npz")
+
+
+def load_stages(name: str) -> dict:
+    """rows (int64), stage0 .. stageL (FP64, one row per sample), fingerprint, config."""
+    with np.load(stages_path_for(name)) as f:
+        out = {k: f[k] for k in f.files}
+    out["fingerprint"] = str(out["fingerprint"])
+    out["config"] = json.loads(str(out["config"]))
+    return out
+
+
+def make_stages(name: str, n_rows: int = 64) -> None:
+    cfg = CONFIGS[name]
+    g = workload(name)
+    dims, seed = cfg["dims"], cfg["embed_seed"]
+    rng = np.random.default_rng(12345)
+    rows = np.sort(np.concatenate([rng.choice(g.n, n_rows - 1, replace=False), [int(np.argmax(g.degrees()))]]))
+    rows = np.unique(rows).astype(np.int64)
+    t0 = time.time()
+    theta = oracle.theta(g.n, dims[0], seed)
+    Y = oracle.project(g, cfg["op"], theta)
+    del theta
+    out = {"stage0": Y[rows]}
+    Zk = Y
+    for k in range(1, len(dims)):
+        Zk = oracle.gcn_layer(g, Zk, oracle.gcn_weight(k, dims[k - 1], dims[k], seed))
+        out[f"stage{k}"] = Zk[rows]
+    # the stage-by-stage chain is the oracle's whole embedding
+    _, Z = oracle.embed(g, cfg["op"], dims, seed)
+    assert np.array_equal(Z[rows], out[f"stage{len(dims) - 1}"])
+    np.savez_compressed(stages_path_for(name), rows=rows, fingerprint=np.str_(fingerprint(g)),
+                        config=np.str_(json.dumps(cfg)), **out)
+    print(f"{name}: stage rows in {time.time() - t0:.1f} s, wrote {stages_path_for(name)}", flush=True)
 
 
 def load(name: str) -> dict:
@@ -84,7 +124,10 @@ if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("names", nargs="*", default=list(CONFIGS))
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--stages-only", action="store_true")
     a = ap.parse_args()
     print(f"oracle threads: {oracle.set_threads(a.threads)}", flush=True)
     for nm in a.names:
-        make(nm)
+        make_stages(nm)
+        if not a.stages_only:
+            make(nm)

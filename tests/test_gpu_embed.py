@@ -193,3 +193,18 @@ def test_embed_bf16_gathers_match_oracle(cuda, graph, op, dims):
         row_err = np.linalg.norm(got - ref, axis=1)
         print(f"{graph} {op} layer {k}: max row error {row_err.max():.2e}, mean {row_err.mean():.2e}")
         assert row_err.max() <= 6e-3, (k, int(np.argmax(row_err)), row_err.max())
+
+
+@pytest.mark.parametrize("dtype,tol", [("f32", 1e-5), ("bf16", 6e-3)])
+@pytest.mark.parametrize("op", ["ncut", "mod_full", "mod_reduced"])
+def test_embed_without_gcn_layers_matches_oracle(cuda, op, dtype, tol):
+    # the "w/o Emb" ablation: no GCN layer, Z = rownorm(Y) on both sides
+    g = workload("dcsbm-1k")
+    dg = api.DeviceGraph.from_host(g, cuda)
+    Z = api.embed(dg, op, (64,), dtype, seed=3)
+    _, Z_o = oracle.embed(g, op, (64,), seed=3)
+    assert rel_fro(_np(Z), Z_o) <= tol
+    lab, rep = api.select(dg, Z, kmin=2, kmax=20)
+    lab = lab.cpu().numpy()
+    _, _, mod, _ = oracle.score(g, lab, int(lab.max()) + 1)
+    assert [c[1] for c in rep["cands"] if c[0] == rep["k"]][0] == mod

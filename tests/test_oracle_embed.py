@@ -183,3 +183,18 @@ def test_row_sampled_forms_agree_with_whole_graph_forms():
     W = rng.normal(size=(8, 4))
     np.testing.assert_allclose(oracle.gcn_rows(g, Zin, W, rows), oracle.gcn_layer(g, Zin.astype(np.float64), W)[rows],
                                atol=1e-14)
+
+
+@pytest.mark.parametrize("op", ["ncut", "mod_full", "mod_reduced"])
+def test_embed_without_gcn_layers_is_the_row_normalised_projection(op):
+    # the "w/o Emb" ablation (Table IV): Z = rownorm(Y), a zero row stays zero
+    from inputs.dcsbm import workload
+    g = workload("dcsbm-1k")
+    Y, Z = oracle.embed(g, op, (64,), seed=3)
+    Y2, _ = oracle.embed(g, op, (64, 32), seed=3)
+    assert np.array_equal(Y, Y2)                     # the same projection as with layers
+    nrm = np.linalg.norm(Y, axis=1, keepdims=True)
+    want = np.where(nrm > 0, Y / np.where(nrm > 0, nrm, 1.0), 0.0)
+    assert np.abs(Z - want).max() <= 4e-16
+    live = nrm[:, 0] > 0
+    assert np.abs(np.linalg.norm(Z[live], axis=1) - 1).max() <= 1e-15

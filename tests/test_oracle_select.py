@@ -206,10 +206,15 @@ def test_oracle_results_do_not_depend_on_thread_count():
         Y, Z = oracle.embed(g, "mod_full", (64, 64, 32), seed=1)
         r = oracle.select(g, Z, 2, 30, grid=0, T=50, seed=2)
         _, _, _, obj = oracle.lloyd(Z, Z[:7], 20, with_objective=True)
-        runs.append((Y, Z, r, obj))
+        rows = np.arange(0, g.n, 7)
+        yr = oracle.project_rows(g, "mod_full", 64, 1, rows)
+        zr = oracle.gcn_rows(g, Y.astype(np.float32), oracle.gcn_weight(1, 64, 64, 1), rows)
+        runs.append((Y, Z, r, obj, yr, zr))
     oracle.set_threads(0)
-    (Y1, Z1, r1, o1), (Y4, Z4, r4, o4) = runs
+    (Y1, Z1, r1, o1, y1, z1), (Y4, Z4, r4, o4, y4, z4) = runs
     assert np.array_equal(Y1, Y4) and np.array_equal(Z1, Z4) and np.array_equal(o1, o4)
+    assert np.array_equal(y1, y4) and np.array_equal(z1, z4)
+    assert np.array_equal(y1, Y1[rows])       # the sampled rows are the whole projection's rows
     assert r1["k"] == r4["k"] and r1["cands"] == r4["cands"] and np.array_equal(r1["labels"], r4["labels"])
 
 
