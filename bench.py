@@ -543,7 +543,8 @@ def bench_batched(args):
     dg, off = api.concat_graphs(graphs, dev)
     edges = sum(g.n_edges for g in graphs)
     t0 = time.perf_counter()
-    plan = api.BatchPlan(dg, off, dims=wl["dims"], dtype=wl["dtype"], kmin=wl["kmin"], kmax_factor=wl["kmax_factor"],
+    dtype = args.batch_dtype or wl["dtype"]
+    plan = api.BatchPlan(dg, off, dims=wl["dims"], dtype=dtype, kmin=wl["kmin"], kmax_factor=wl["kmax_factor"],
                          grid=wl["grid"], iters=wl["iters"], seed=2)
     torch.cuda.synchronize()
     plan_s = time.perf_counter() - t0
@@ -564,9 +565,15 @@ def bench_batched(args):
     ks = ks.cpu().numpy()
     nmis = [nmi(lab[off[i]:off[i + 1]], g.planted) for i, g in enumerate(graphs)]
     kdiff = [int(ks[i]) - g.k_planted for i, g in enumerate(graphs)]
+    worst = sorted(range(len(graphs)), key=lambda i: nmis[i])[:5]
+    per_graph = {"nmi_planted_quantiles": [float(q) for q in np.quantile(nmis, [0.0, 0.05, 0.25, 0.5, 0.75, 1.0])],
+                 "graphs_below_0.5": int(sum(v < 0.5 for v in nmis)),
+                 "worst": [{"graph": i, "n": graphs[i].n, "edges": graphs[i].n_edges, "k_planted": graphs[i].k_planted,
+                            "k_best": int(ks[i]), "nmi_planted": nmis[i],
+                            "mean_degree": jobs[i][1]["mean_degree"], "ratio": jobs[i][1]["ratio"]} for i in worst]}
     line = {"metric": "batched partition of 512 uneven DC-SBM graphs: edges/s", "value": edges / (ms * 1e-3),
             "unit": "edges/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "dtype": wl["dtype"], "data": "synthetic",
+            "higher_is_better": True, "dtype": dtype, "data": "synthetic",
             "config": {"workload": "512 DC-SBM graphs, N log-uniform in [1000, 50000], K = round(N^0.35), exponent "
                                    "2.5, mean degree U[10, 30], ratio U[2, 6]; NCut operator, GNN 128-128-64, "
                                    "K in [2, ceil(2 N^0.35)] (10 coarse + 10 refined), <=50 Lloyd passes; "
@@ -574,7 +581,7 @@ def bench_batched(args):
                        "graphs": len(graphs), "nodes": int(off[-1]), "edges": edges},
             "graphs_per_s": len(graphs) / (ms * 1e-3), "plan_create_s": plan_s, "tuning": plan.tuning(),
             "quality": {"nmi_planted_mean": float(np.mean(nmis)), "nmi_planted_min": float(np.min(nmis)),
-                        "k_minus_planted_mean": float(np.mean(kdiff))},
+                        "k_minus_planted_mean": float(np.mean(kdiff)), "per_graph": per_graph},
             "clocks": clocks}
     plan.close()
     print(json.dumps(line), flush=True)
@@ -648,6 +655,8 @@ def main():
                          "batches merged and the affected rows re-embedded (Section III-D)")
     ap.add_argument("--assign", default=None, choices=["tc", "tc8", "ffma"],
                     help="k-means engine (default: tc8 for bf16, ffma for f32)")
+    ap.add_argument("--batch-dtype", default=None, choices=["f32", "bf16"],
+                    help="storage of the batched form's embedding (default f32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32-check", action="store_true",

@@ -286,6 +286,8 @@ typedef struct {
     int32_t grid;          /* coarse and refined grid size, 1..10 */
     int32_t iters;         /* Lloyd pass cap T */
     int32_t criterion;     /* RAFTGP_CRIT_MOD or RAFTGP_CRIT_NCUT */
+    int32_t lloyd_variant; /* 0: autotune the Lloyd kernel; v in 1..7: use variant v - 1 of the
+                              list raftgp_batch_plan_tuning reports (no timing) */
     uint64_t seed;         /* k-means++ seed (the same for every graph) */
 } raftgp_batch_opts;
 
@@ -310,10 +312,15 @@ raftgp_status raftgp_batch_plan_run(raftgp_batch_plan* plan, raftgp_stream_t str
  * refined; unused slots have k = 0) after a run.  Synchronises. */
 raftgp_status raftgp_batch_plan_candidates(raftgp_batch_plan* plan, int32_t* k, double* mod, double* ncut,
                                            int32_t* passes);
-/* The autotuner's choice and its measured times (ms of the coarse Lloyd phase) for the six
- * variants {128, 256, 512 threads} x {1, 2 points per thread}, in that order. */
+/* The autotuner's choice and its measured times (ms of the coarse Lloyd phase) for the seven
+ * variants: the scalar Lloyd kernel at {128, 256, 512 threads} x {1, 2 points per thread}, in
+ * that order, then the register-tiled kernel (256 threads, reported as 0 points per thread).
+ * Every variant computes the same labels. */
 raftgp_status raftgp_batch_plan_tuning(const raftgp_batch_plan* plan, int32_t* threads, int32_t* points_per_thread,
                                        float* ms);
+/* The embedding of the last replay (n x d in the plan's dtype, row-major, the Z every graph's
+ * model selection ran on) copied to the device buffer Z_out.  Synchronises. */
+raftgp_status raftgp_batch_plan_embedding(const raftgp_batch_plan* plan, void* Z_out);
 void raftgp_batch_plan_destroy(raftgp_batch_plan* plan);
 
 /* One-shot: plan, run, synchronise, destroy. */

@@ -358,10 +358,11 @@ def concat_graphs(graphs, device, row_ptr_bits=64):
     return dg, np.asarray(offs, dtype=np.int64)
 
 
-def batch_opts(kmin=2, kmax_factor=2.0, grid=10, iters=50, criterion="mod", seed=2):
+def batch_opts(kmin=2, kmax_factor=2.0, grid=10, iters=50, criterion="mod", seed=2, lloyd_variant=0):
     o = _abi.BatchOpts()
     o.kmin, o.kmax_factor, o.grid, o.iters = int(kmin), float(kmax_factor), int(grid), int(iters)
     o.criterion = _abi.CRIT[criterion] if isinstance(criterion, str) else int(criterion)
+    o.lloyd_variant = int(lloyd_variant)
     o.seed = int(seed)
     return o
 
@@ -416,9 +417,16 @@ class BatchPlan:
 
     def tuning(self):
         th, pp = C.c_int32(), C.c_int32()
-        ms = (C.c_float * 6)()
+        ms = (C.c_float * 7)()
         check(lib().raftgp_batch_plan_tuning(self._h, C.byref(th), C.byref(pp), ms))
         return {"threads": th.value, "points_per_thread": pp.value, "ms": list(ms)}
+
+    def embedding(self):
+        """The embedding of the last replay (n x d, the plan's dtype)."""
+        d = self.eo.dims[self.eo.n_layers]
+        Z = torch.empty((self.g.n, d), dtype=_torch_dtype(self.eo.dtype), device=self.g.col.device)
+        check(lib().raftgp_batch_plan_embedding(self._h, C.c_void_p(Z.data_ptr())))
+        return Z
 
     def close(self):
         if getattr(self, "_h", None):

@@ -928,7 +928,7 @@ struct raftgp_batch_plan {
     int32_t* labels = nullptr;
     int32_t* k_out = nullptr;
     int threads = 256, ppt = 1;
-    float tune_ms[6] = {};
+    float tune_ms[7] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;   // the plan's own stream, on which the graph is captured
@@ -950,6 +950,7 @@ raftgp_status batch_layout(const raftgp_csr* g, const int64_t* off, int ng, cons
     if (bo->grid < 1 || bo->grid > BATCH_COARSE) return fail(RAFTGP_EINVAL, "grid must be in [1, %d]", BATCH_COARSE);
     if (bo->iters < 1) return fail(RAFTGP_EINVAL, "iters must be >= 1");
     if (!(bo->kmax_factor > 0.f)) return fail(RAFTGP_EINVAL, "kmax_factor must be positive");
+    if (bo->lloyd_variant < 0 || bo->lloyd_variant > 7) return fail(RAFTGP_EINVAL, "lloyd_variant must be in [0, 7]");
     if (off[0] != 0 || off[ng] != g->n) return fail(RAFTGP_EINVAL, "graph_off must run from 0 to n");
     p.g = *g;
     p.eo = *eo;
@@ -1073,8 +1074,10 @@ raftgp_status raftgp_batch_plan_create(const raftgp_csr* g, const int64_t* graph
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = INFINITY;
-    for (int v = 0; v < 6; ++v) {
-        const int th = kTuneThreads[v / 2], pp = 1 + v % 2;
+    for (int v = 0; v < 7; ++v) {
+        if (p->bo.lloyd_variant > 0 && v != p->bo.lloyd_variant - 1) continue;   // a forced variant
+        // six shapes of the scalar kernel, then the register-tiled kernel (ppt 0)
+        const int th = v < 6 ? kTuneThreads[v / 2] : 256, pp = v < 6 ? 1 + v % 2 : 0;
         cudaMemsetAsync(b.queue + 1, 0, sizeof(int), s);
         cudaEventRecord(e0, s);
         cudaError_t e = launch_batch_lloyd(b, p->Z, p->eo.dtype, p->d, 0, p->bo.iters, &p->g, th, pp, s);
@@ -1149,7 +1152,17 @@ raftgp_status raftgp_batch_plan_tuning(const raftgp_batch_plan* plan, int32_t* t
     if (threads) *threads = plan->threads;
     if (points_per_thread) *points_per_thread = plan->ppt;
     if (ms)
-        for (int v = 0; v < 6; ++v) ms[v] = plan->tune_ms[v];
+        for (int v = 0; v < 7; ++v) ms[v] = plan->tune_ms[v];
+    return RAFTGP_OK;
+}
+
+raftgp_status raftgp_batch_plan_embedding(const raftgp_batch_plan* plan, void* Z_out) {
+    if (!plan || !Z_out) return fail(RAFTGP_EINVAL, "plan or Z_out is NULL");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpy(Z_out, plan->Z, (size_t)plan->total_n * plan->d * elem_size(plan->eo.dtype),
+                       cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "embedding");
     return RAFTGP_OK;
 }
 

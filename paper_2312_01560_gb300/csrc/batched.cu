@@ -235,6 +235,47 @@ __global__ void __launch_bounds__(1024) k_batch_seed(BatchDev b, const T* __rest
 }
 
 // ------------------------------------------------------------------------------------
+// Score of one (graph, candidate) partition: intra-block edge ends and volumes (exact
+// integers, in the 2 BATCH_KMAX shared counters `m2`), then Mod (Eq. 3 via Eq. 7, one FP64
+// division of exact integers) and NCut (Eq. 1, ascending blocks).  Every thread of the CTA
+// calls it.
+// ------------------------------------------------------------------------------------
+__device__ void batch_score_item(const BatchDev& b, int g, int slot, int K, int64_t o, int64_t n, const int16_t* lab,
+                                 int passes, unsigned long long* m2, const int64_t* __restrict__ rp64,
+                                 const int32_t* __restrict__ rp32, const int32_t* __restrict__ col) {
+    unsigned long long* vol = m2 + BATCH_KMAX;
+    for (int t = threadIdx.x; t < 2 * BATCH_KMAX; t += blockDim.x) m2[t] = 0;
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const int li = lab[i];
+        const int64_t a = rp64 ? rp64[o + i] : (int64_t)rp32[o + i];
+        const int64_t e = rp64 ? rp64[o + i + 1] : (int64_t)rp32[o + i + 1];
+        unsigned long long same = 0;
+        for (int64_t q = a; q < e; ++q) same += lab[(int64_t)col[q] - o] == li ? 1ull : 0ull;
+        atomicAdd(vol + li, (unsigned long long)(e - a));
+        if (same) atomicAdd(m2 + li, same);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int64_t ea = rp64 ? rp64[o] : (int64_t)rp32[o];
+        const int64_t eb = rp64 ? rp64[o + n] : (int64_t)rp32[o + n];
+        const long long two_e = eb - ea;
+        long long sm = 0, sv = 0;
+        double ncut = 0.0;
+        for (int r = 0; r < K; ++r) {
+            const long long mr = (long long)(m2[r] / 2), vr = (long long)vol[r];
+            sm += mr;
+            sv += vr * vr;
+            if (vr > 0) ncut += (double)(vr - 2 * mr) / (double)vr;
+        }
+        const double mod = two_e > 0 ? (double)(2 * two_e * sm - sv) / ((double)two_e * (double)two_e) : 0.0;
+        b.cand_mod[g * BATCH_SLOTS + slot] = mod;
+        b.cand_ncut[g * BATCH_SLOTS + slot] = 0.5 * ncut;
+        b.cand_passes[g * BATCH_SLOTS + slot] = passes;
+    }
+}
+
+// ------------------------------------------------------------------------------------
 // Lloyd + score: persistent, one CTA per (graph, candidate).  PHASE 0: coarse slots, 1: refined.
 // PPT points per thread share each centroid load.
 // ------------------------------------------------------------------------------------
@@ -357,38 +398,216 @@ __global__ void k_batch_lloyd(BatchDev b, const T* __restrict__ Z, int phase, in
             }
             __syncthreads();
         }
-        // score: intra-block edge ends and volumes (exact), sums reused as counters
-        unsigned long long* m2 = reinterpret_cast<unsigned long long*>(sums);
-        unsigned long long* vol = m2 + BATCH_KMAX;
-        for (int t = threadIdx.x; t < 2 * BATCH_KMAX; t += blockDim.x) m2[t] = 0;
+        batch_score_item(b, g, slot, K, o, n, lab, passes, reinterpret_cast<unsigned long long*>(sums), rp64, rp32, col);
         __syncthreads();
-        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-            const int li = lab[i];
-            const int64_t a = rp64 ? rp64[o + i] : (int64_t)rp32[o + i];
-            const int64_t e = rp64 ? rp64[o + i + 1] : (int64_t)rp32[o + i + 1];
-            unsigned long long same = 0;
-            for (int64_t q = a; q < e; ++q) same += lab[(int64_t)col[q] - o] == li ? 1ull : 0ull;
-            atomicAdd(vol + li, (unsigned long long)(e - a));
-            if (same) atomicAdd(m2 + li, same);
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Lloyd + score, register-tiled: persistent, one CTA of 256 threads per (graph, candidate).
+// The centroids live in shared memory k-major (muT[k][c], BATCH_KMAX columns, unused columns
+// zero with an infinite norm).  Each pass walks the graph's points in tiles of 256, staged
+// transposed (zT[k][p]); warp w scores points 32w..32w+31 against the centroids in column
+// groups: lane (pr, cr) = (lane / 8, lane % 8) holds 8 points {4pr..4pr+3, 16+4pr..16+4pr+3}
+// and NC centroids of a group of 8 NC columns (NC = 8: {4cr..4cr+3, 32+4cr..32+4cr+3};
+// NC = 4: {4cr..4cr+3}; NC = 2: {2cr, 2cr+1}), the group width chosen by how many real
+// centroids remain.  Scores, tie rule, fixed-point sums, FP64 means and norm order are the
+// scalar kernel's (and the single-graph engine's), so the labels are the same.
+// ------------------------------------------------------------------------------------
+constexpr int BT_THREADS = 256;
+constexpr int BT_PTS = 256;
+
+size_t batch_lloyd_tiled_smem(int d) {
+    return (size_t)BATCH_KMAX * d * sizeof(long long) + (size_t)d * BATCH_KMAX * sizeof(float) +
+           BATCH_KMAX * (sizeof(float) + sizeof(int)) + (size_t)d * BT_PTS * sizeof(float);
+}
+
+template <int D, int NC>
+__device__ __forceinline__ void bt_group(const float* __restrict__ zw, const float* __restrict__ muT,
+                                         const float* __restrict__ nrm, int c0, int pr, int cr, float* bv, int* bi) {
+    float acc[8][NC];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int j = 0; j < NC; ++j) acc[r][j] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < D; ++k) {
+        const float4 za = *reinterpret_cast<const float4*>(zw + k * BT_PTS + 4 * pr);
+        const float4 zb = *reinterpret_cast<const float4*>(zw + k * BT_PTS + 16 + 4 * pr);
+        const float z[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+        float m[NC];
+        const float* mk = muT + k * BATCH_KMAX + c0;
+        if constexpr (NC == 8) {
+            const float4 ma = *reinterpret_cast<const float4*>(mk + 4 * cr);
+            const float4 mb = *reinterpret_cast<const float4*>(mk + 32 + 4 * cr);
+            m[0] = ma.x; m[1] = ma.y; m[2] = ma.z; m[3] = ma.w;
+            m[4] = mb.x; m[5] = mb.y; m[6] = mb.z; m[7] = mb.w;
+        } else if constexpr (NC == 4) {
+            const float4 ma = *reinterpret_cast<const float4*>(mk + 4 * cr);
+            m[0] = ma.x; m[1] = ma.y; m[2] = ma.z; m[3] = ma.w;
+        } else {
+            const float2 ma = *reinterpret_cast<const float2*>(mk + 2 * cr);
+            m[0] = ma.x; m[1] = ma.y;
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+#pragma unroll
+            for (int j = 0; j < NC; ++j) acc[r][j] = fmaf(z[r], m[j], acc[r][j]);
+    }
+    // this lane's columns in ascending order
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        const int col = c0 + (NC == 8 ? (j < 4 ? 4 * cr + j : 32 + 4 * cr + (j - 4)) : NC == 4 ? 4 * cr + j : 2 * cr + j);
+        const float nq = nrm[col];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const float s = fmaf(-2.0f, acc[r][j], nq);
+            if (s < bv[r]) { bv[r] = s; bi[r] = col; }
+        }
+    }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(BT_THREADS, 1)
+    k_batch_lloyd_tiled(BatchDev b, const T* __restrict__ Z, int phase, int iters, const int64_t* __restrict__ rp64,
+                        const int32_t* __restrict__ rp32, const int32_t* __restrict__ col) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    long long* sums = reinterpret_cast<long long*>(smraw);              // BATCH_KMAX x D
+    float* muT = reinterpret_cast<float*>(sums + BATCH_KMAX * D);       // D x BATCH_KMAX
+    float* nrm = muT + D * BATCH_KMAX;                                   // BATCH_KMAX
+    int* cnt = reinterpret_cast<int*>(nrm + BATCH_KMAX);                 // BATCH_KMAX
+    float* zT = reinterpret_cast<float*>(cnt + BATCH_KMAX);              // D x BT_PTS
+    __shared__ int s_item, s_changed;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = BT_THREADS >> 5;
+    const int pr = lane >> 3, cr = lane & 7;
+    const int per_graph = phase == 0 ? BATCH_COARSE : BATCH_SLOTS - BATCH_COARSE;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(b.queue + 1 + phase, 1);
+        __syncthreads();
+        const int u = s_item;
+        if (u >= b.ng * per_graph) return;
+        const int g = b.order[u / per_graph];
+        const int j = u % per_graph;
+        const int slot = (phase == 0 ? 0 : BATCH_COARSE) + j;
+        if (j >= (phase == 0 ? b.n_coarse[g] : b.n_refine[g])) {
+            __syncthreads();
+            continue;
+        }
+        const int K = b.cand_k[g * BATCH_SLOTS + slot];
+        const int64_t o = b.node_off[g];
+        const int64_t n = b.node_off[g + 1] - o;
+        int16_t* lab = b.labels + (int64_t)slot * b.total_n + o;
+        const int32_t* seeds = b.seeds + b.seed_off[g];
+        // centroids from the first K seeds (unused columns zero); norms in ascending coordinates
+        for (int t = tid; t < BATCH_KMAX * D; t += BT_THREADS) {
+            const int c = t / D, k = t % D;
+            muT[k * BATCH_KMAX + c] = c < K ? load_elem(Z, (o + seeds[c]) * D + k) : 0.f;
+            sums[t] = 0;
+        }
+        for (int t = tid; t < BATCH_KMAX; t += BT_THREADS) cnt[t] = 0;
+        for (int64_t i = tid; i < n; i += BT_THREADS) lab[i] = -1;
+        __syncthreads();
+        for (int c = tid; c < BATCH_KMAX; c += BT_THREADS) {
+            float s = 0.f;
+            for (int k = 0; k < D; ++k) s = fmaf(muT[k * BATCH_KMAX + c], muT[k * BATCH_KMAX + c], s);
+            nrm[c] = c < K ? s : INFINITY;
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            const int64_t ea = rp64 ? rp64[o] : (int64_t)rp32[o];
-            const int64_t eb = rp64 ? rp64[o + n] : (int64_t)rp32[o + n];
-            const long long two_e = eb - ea;
-            long long sm = 0, sv = 0;
-            double ncut = 0.0;
-            for (int r = 0; r < K; ++r) {
-                const long long mr = (long long)(m2[r] / 2), vr = (long long)vol[r];
-                sm += mr;
-                sv += vr * vr;
-                if (vr > 0) ncut += (double)(vr - 2 * mr) / (double)vr;
+        int passes = iters;
+        for (int pass = 1; pass <= iters; ++pass) {
+            if (tid == 0) s_changed = 0;
+            int nch = 0;
+            for (int64_t p0 = 0; p0 < n; p0 += BT_PTS) {
+                __syncthreads();   // the previous tile's reads (and s_changed's reset) are done
+                {
+                    constexpr int E = Vec<T>::E;
+                    for (int t = tid; t < BT_PTS * (D / E); t += BT_THREADS) {
+                        const int p = t % BT_PTS, k0 = (t / BT_PTS) * E;
+                        float v[E];
+                        if (p0 + p < n) {
+                            Vec<T>::load(Z + (o + p0 + p) * D + k0, v);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < E; ++e) v[e] = 0.f;
+                        }
+#pragma unroll
+                        for (int e = 0; e < E; ++e) zT[(k0 + e) * BT_PTS + p] = v[e];
+                    }
+                }
+                __syncthreads();
+                float bv[8];
+                int bi[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) { bv[r] = INFINITY; bi[r] = 0x7fffffff; }
+                const float* zw = zT + 32 * warp;
+                for (int c0 = 0; c0 < K; c0 += 64) {
+                    const int left = K - c0;
+                    if (left > 32) bt_group<D, 8>(zw, muT, nrm, c0, pr, cr, bv, bi);
+                    else if (left > 16) bt_group<D, 4>(zw, muT, nrm, c0, pr, cr, bv, bi);
+                    else bt_group<D, 2>(zw, muT, nrm, c0, pr, cr, bv, bi);
+                }
+                // combine the 8 lanes of a point group (ties to the lowest column); lane cr
+                // reports point cr of its group
+#pragma unroll
+                for (int ofs = 1; ofs < 8; ofs <<= 1) {
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) {
+                        const float ov = __shfl_xor_sync(0xffffffffu, bv[r], ofs);
+                        const int oi = __shfl_xor_sync(0xffffffffu, bi[r], ofs);
+                        if (ov < bv[r] || (ov == bv[r] && oi < bi[r])) { bv[r] = ov; bi[r] = oi; }
+                    }
+                }
+                int mi = 0x7fffffff;
+#pragma unroll
+                for (int r = 0; r < 8; ++r)
+                    if (r == cr) mi = bi[r];
+                const int p = 32 * warp + (cr < 4 ? 4 * pr + cr : 16 + 4 * pr + (cr - 4));
+                const int64_t i = p0 + p;
+                if (i < n) {
+                    int nl = mi;
+                    if (nl < 0 || nl >= K) nl = 0;   // every score NaN (non-finite input): keep indices in range
+                    const int ol = lab[i];
+                    if (nl != ol) {
+                        lab[i] = (int16_t)nl;
+                        ++nch;
+                        atomicAdd(cnt + nl, 1);
+                        if (ol >= 0) atomicSub(cnt + ol, 1);
+#pragma unroll 4
+                        for (int k = 0; k < D; ++k) {
+                            const long long v = __float2ll_rn(zT[k * BT_PTS + p] * FIXED_SCALE_F);
+                            atomicAdd(reinterpret_cast<unsigned long long*>(sums + nl * D + k), (unsigned long long)v);
+                            if (ol >= 0)
+                                atomicAdd(reinterpret_cast<unsigned long long*>(sums + ol * D + k),
+                                          (unsigned long long)(-v));
+                        }
+                    }
+                }
             }
-            const double mod = two_e > 0 ? (double)(2 * two_e * sm - sv) / ((double)two_e * (double)two_e) : 0.0;
-            b.cand_mod[g * BATCH_SLOTS + slot] = mod;
-            b.cand_ncut[g * BATCH_SLOTS + slot] = 0.5 * ncut;
-            b.cand_passes[g * BATCH_SLOTS + slot] = passes;
+            nch = __reduce_add_sync(0xffffffffu, nch);
+            if (lane == 0 && nch) atomicAdd(&s_changed, nch);
+            __syncthreads();
+            if (s_changed == 0) {
+                passes = pass;
+                break;
+            }
+            if (pass == iters) break;       // no update after the last pass
+            // FP64 means of the fixed-point sums, norms in lane order then a warp sum
+            for (int cc = warp; cc < K; cc += nwarps) {
+                const int ct = cnt[cc];
+                if (ct <= 0) continue;
+                const double inv = 1.0 / ((double)ct * FIXED_SCALE);
+                float s = 0.f;
+                for (int k = lane; k < D; k += 32) {
+                    const float v = (float)((double)sums[cc * D + k] * inv);
+                    muT[k * BATCH_KMAX + cc] = v;
+                    s = fmaf(v, v, s);
+                }
+                s = warp_sum(s);
+                if (lane == 0) nrm[cc] = s;
+            }
+            __syncthreads();
         }
+        batch_score_item(b, g, slot, K, o, n, lab, passes, reinterpret_cast<unsigned long long*>(sums), rp64, rp32, col);
         __syncthreads();
     }
 }
@@ -471,9 +690,38 @@ static cudaError_t batch_lloyd_t(BatchDev b, const T* Z, int phase, int iters, c
     return cudaGetLastError();
 }
 
+template <typename T, int D>
+static cudaError_t batch_lloyd_tiled_t(BatchDev b, const T* Z, int phase, int iters, const raftgp_csr* g,
+                                       cudaStream_t s) {
+    const size_t smem = batch_lloyd_tiled_smem(D);
+    auto kern = k_batch_lloyd_tiled<T, D>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BT_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    kern<<<num_sms() * per_sm, BT_THREADS, smem, s>>>(b, Z, phase, iters,
+                                                      g->row_ptr_bits == 64 ? (const int64_t*)g->row_ptr : nullptr,
+                                                      g->row_ptr_bits == 32 ? (const int32_t*)g->row_ptr : nullptr,
+                                                      g->col);
+    return cudaGetLastError();
+}
+
+// threads / ppt pick the scalar kernel's shape; ppt == 0 picks the register-tiled kernel
 cudaError_t launch_batch_lloyd(BatchDev b, const void* Z, int zdtype, int d, int phase, int iters, const raftgp_csr* g,
                                int threads, int ppt, cudaStream_t s) {
     ProfScope ps(s, PF_ASSIGN_FFMA, 1);
+    if (ppt == 0) {
+        if (zdtype == RAFTGP_BF16) {
+            if (d == 32) return batch_lloyd_tiled_t<__nv_bfloat16, 32>(b, (const __nv_bfloat16*)Z, phase, iters, g, s);
+            if (d == 64) return batch_lloyd_tiled_t<__nv_bfloat16, 64>(b, (const __nv_bfloat16*)Z, phase, iters, g, s);
+        } else {
+            if (d == 32) return batch_lloyd_tiled_t<float, 32>(b, (const float*)Z, phase, iters, g, s);
+            if (d == 64) return batch_lloyd_tiled_t<float, 64>(b, (const float*)Z, phase, iters, g, s);
+        }
+        return cudaErrorInvalidValue;
+    }
 #define RAFTGP_BL(T, DD, P) return batch_lloyd_t<T, DD, P>(b, (const T*)Z, phase, iters, g, threads, s)
     if (zdtype == RAFTGP_BF16) {
         if (d == 32) { if (ppt == 2) RAFTGP_BL(__nv_bfloat16, 32, 2); RAFTGP_BL(__nv_bfloat16, 32, 1); }

@@ -6,7 +6,10 @@ here touches the CUDA library.  Each output file holds, for one workload:
     embedding of Eq. 5 and Eq. 6);
   - ``labels_z32``: the oracle's partition of the same embedding rounded once to FP32 (the
     sensitivity of the k-means model selection to one single-precision rounding of Z);
-  - ``cands`` / ``cands_z32``: (K, Mod, NCut, Lloyd passes) per evaluated candidate;
+  - ``labels_zbf16`` (1M-node workload): the same with Z rounded once to BF16 (round to nearest
+    even), the perturbation BF16 storage of the final embedding alone brings;
+  - ``cands`` / ``cands_z32`` / ``cands_zbf16``: (K, Mod, NCut, Lloyd passes) per evaluated
+    candidate, and ``k`` / ``k_z32`` / ``k_zbf16`` the chosen K;
   - ``fingerprint``: SHA-256 of the graph's CSR (``inputs.dcsbm.fingerprint``), so a reader
     checks that its graph is the one these labels belong to;
   - the configuration (operator, layer widths, K range, grid, pass cap, seeds).
@@ -91,32 +94,48 @@ def load(name: str) -> dict:
     cands_z32, fingerprint, config)."""
     with np.load(path_for(name)) as f:
         out = {k: f[k] for k in f.files}
-    out["labels"] = out["labels"].astype(np.int32)
-    out["labels_z32"] = out["labels_z32"].astype(np.int32)
-    out["k"] = int(out["k"])
-    out["k_z32"] = int(out["k_z32"])
+    for tag in VARIANTS:
+        if "labels" + tag in out:
+            out["labels" + tag] = out["labels" + tag].astype(np.int32)
+            out["k" + tag] = int(out["k" + tag])
     out["fingerprint"] = str(out["fingerprint"])
     out["config"] = json.loads(str(out["config"]))
     return out
 
 
-def make(name: str) -> None:
+def round_bf16(x: np.ndarray) -> np.ndarray:
+    """x rounded to the nearest BF16 value (ties to even), returned in FP64: the FP32 bits with
+    the low 16 bits rounded away (inputs are finite)."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+VARIANTS = {"": lambda Z: Z, "_z32": lambda Z: Z.astype(np.float32).astype(np.float64), "_zbf16": round_bf16}
+
+
+def make(name: str, variants=("", "_z32")) -> None:
+    """Computes the listed variants (keeping the ones already stored for the same graph)."""
     cfg = CONFIGS[name]
     g = workload(name)
+    fp = fingerprint(g)
+    res = {}
+    if os.path.exists(path_for(name)):
+        with np.load(path_for(name)) as f:
+            if str(f["fingerprint"]) == fp and json.loads(str(f["config"])) == json.loads(json.dumps(cfg)):
+                res = {k: f[k] for k in f.files if k not in ("fingerprint", "config")}
     t0 = time.time()
     _, Z = oracle.embed(g, cfg["op"], cfg["dims"], cfg["embed_seed"])
     t1 = time.time()
     print(f"{name}: embedding {t1 - t0:.1f} s", flush=True)
-    res = {}
-    for tag, Zin in (("", Z), ("_z32", Z.astype(np.float32).astype(np.float64))):
-        r = oracle.select(g, Zin, cfg["kmin"], cfg["kmax"], cfg["grid"], cfg["T"], cfg["select_seed"])
+    for tag in variants:
+        r = oracle.select(g, VARIANTS[tag](Z), cfg["kmin"], cfg["kmax"], cfg["grid"], cfg["T"], cfg["select_seed"])
         res["labels" + tag] = r["labels"].astype(np.uint16)
         res["k" + tag] = np.int32(r["k"])
         res["cands" + tag] = np.array(r["cands"], dtype=np.float64)
         print(f"{name}{tag}: K* = {r['k']}, selection {time.time() - t1:.1f} s", flush=True)
         t1 = time.time()
-    np.savez_compressed(path_for(name), fingerprint=np.str_(fingerprint(g)),
-                        config=np.str_(json.dumps(cfg)), **res)
+        np.savez_compressed(path_for(name), fingerprint=np.str_(fp), config=np.str_(json.dumps(cfg)), **res)
     print(f"wrote {path_for(name)}", flush=True)
 
 
@@ -125,9 +144,15 @@ if __name__ == "__main__":
     ap.add_argument("names", nargs="*", default=list(CONFIGS))
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--stages-only", action="store_true")
+    ap.add_argument("--variants", default=None,
+                    help="comma-separated subset of '', '_z32', '_zbf16' (default: all three for dcsbm-1m, "
+                         "the first two otherwise)")
     a = ap.parse_args()
     print(f"oracle threads: {oracle.set_threads(a.threads)}", flush=True)
     for nm in a.names:
-        make_stages(nm)
+        if not a.variants:
+            make_stages(nm)
         if not a.stages_only:
-            make(nm)
+            vs = a.variants.split(",") if a.variants is not None else (
+                ["", "_z32", "_zbf16"] if nm == "dcsbm-1m" else ["", "_z32"])
+            make(nm, [("" if v in ("''", '""', "base") else v) for v in vs])

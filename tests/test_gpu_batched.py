@@ -76,8 +76,9 @@ def test_replay_is_deterministic_and_tuned(cuda, batch):
     torch.cuda.synchronize()
     assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
     t = plan.tuning()
-    assert t["threads"] in (128, 256, 512) and t["points_per_thread"] in (1, 2)
-    assert all(m > 0 for m in t["ms"])
+    assert t["threads"] in (128, 256, 512) and t["points_per_thread"] in (0, 1, 2)
+    assert len(t["ms"]) == 7 and all(m > 0 for m in t["ms"])
+    print(f"batch tuning: {t}")
     plan.close()
 
 
@@ -107,3 +108,65 @@ def test_bad_offsets_are_rejected(cuda, batch):
     dg, off = api.concat_graphs(batch[:2], cuda)
     with pytest.raises(api._abi.RaftgpError):
         api.BatchPlan(dg, off[:-1], dims=DIMS, dtype="f32")
+
+
+def test_every_lloyd_variant_gives_the_same_result(cuda, batch):
+    # the autotuner's seven Lloyd kernels (six scalar shapes, the register-tiled kernel) differ
+    # only in speed: labels, K* and every candidate's score agree bit for bit
+    dg, off = api.concat_graphs(batch[:5], cuda)
+    ref = None
+    for v in range(1, 8):
+        plan = api.BatchPlan(dg, off, dims=DIMS, dtype="f32", kmin=2, grid=10, iters=50, seed=2, lloyd_variant=v)
+        labels, ks = plan.run()
+        torch.cuda.synchronize()
+        ck, cm, cn, cp = plan.candidates()
+        used = ck > 0                                 # unused slots (k = 0) hold no result
+        got = (labels.cpu().numpy(), ks.cpu().numpy(), ck, cm[used], cn[used], cp[used])
+        t = plan.tuning()
+        assert (t["threads"], t["points_per_thread"]) == (([128, 256, 512][(v - 1) // 2], 1 + (v - 1) % 2) if v < 7
+                                                          else (256, 0))
+        plan.close()
+        if ref is None:
+            ref = got
+        else:
+            for a, b in zip(ref, got):
+                assert np.array_equal(a, b), v
+
+
+def test_bf16_batch_equals_single_graph_selection_on_its_embedding(cuda, batch):
+    # BF16 storage: every graph's model selection on the plan's own BF16 embedding equals a
+    # single-graph selection (FP32 engine) on the same rows, and each chosen partition that
+    # converged assigns every point to its nearest centroid (FP32 band); drift against the
+    # FP32 batch is stated
+    sub = batch[:6]
+    dg, off = api.concat_graphs(sub, cuda)
+    plan = api.BatchPlan(dg, off, dims=DIMS, dtype="bf16", kmin=2, grid=10, iters=50, seed=2)
+    labels, ks = plan.run()
+    torch.cuda.synchronize()
+    Z = plan.embedding()
+    labels, ks = labels.cpu().numpy(), ks.cpu().numpy()
+    ck, cmod, cncut, cpass = plan.candidates()
+    plan32 = api.BatchPlan(dg, off, dims=DIMS, dtype="f32", kmin=2, grid=10, iters=50, seed=2)
+    l32, k32 = plan32.run()
+    torch.cuda.synchronize()
+    l32, k32 = l32.cpu().numpy(), k32.cpu().numpy()
+    for gi, g in enumerate(sub):
+        one = api.DeviceGraph.from_host(g, cuda)
+        Zg = Z[off[gi]:off[gi + 1]].contiguous()
+        lab1, rep1 = api.select(one, Zg, kmin=2, kmax=_kmax(g.n), grid=10, iters=50, assign="ffma", seed=2)
+        lab = labels[off[gi]:off[gi + 1]]
+        assert ks[gi] == rep1["k"] and np.array_equal(lab, lab1.cpu().numpy()), gi
+        slot = [j for j in range(20) if ck[gi, j] == ks[gi]][0]
+        if cpass[gi, slot] < 50:                     # converged: centroids are the label means
+            z = Zg.float().cpu().numpy().astype(np.float64)
+            K = int(ks[gi])
+            mu = np.stack([z[lab == c].mean(0) if (lab == c).any() else np.full(z.shape[1], np.inf)
+                           for c in range(K)])
+            d2 = ((z[:, None, :] - mu[None]) ** 2).sum(-1)
+            own = d2[np.arange(len(lab)), lab]
+            assert (own <= d2.min(1) + 1e-5).all(), gi
+        print(f"graph {gi} (N={g.n}): K* bf16 {ks[gi]} fp32 {k32[gi]}, NMI(bf16, fp32) "
+              f"{nmi(lab, l32[off[gi]:off[gi + 1]]):.4f}, NMI vs planted bf16 {nmi(lab, g.planted):.4f} "
+              f"fp32 {nmi(l32[off[gi]:off[gi + 1]], g.planted):.4f}")
+    plan.close()
+    plan32.close()
