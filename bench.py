@@ -295,6 +295,7 @@ def oracle_baseline(g, wl, cand_ks, **kw):
     v1, spent1, _, _ = res["one"]
     return {"value": v, "unit": "edges/s", "cores": used, "kind": "oracle", "sample": desc,
             "cpu_seconds": round(spent, 2), "cpu_model": cpu_model(), "nproc": os.cpu_count(),
+            "openmp": oracle.has_openmp(),
             "one_thread": {"value": v1, "cores": 1, "cpu_seconds": round(spent1, 2)}}
 
 
@@ -314,15 +315,18 @@ def stage_drift(api, dg, wl, dtype, st, dev):
 
 
 def equal_nmi_rule(quality, fp32):
-    """'At equal NMI': the BF16 form's NMI against the planted partition is within 0.005 of the
-    FP32 form's (or above it), and the two forms agree with each other at least as well as the
-    FP64 oracle agrees with itself when its embedding is rounded once to FP32 (the sensitivity
-    floor of the k-means model selection on this graph), less 0.01."""
+    """'At equal NMI', two clauses:
+    - the BF16 form's NMI against the planted partition is within 0.005 of the FP32 form's (or
+      above it);
+    - the BF16 form agrees with the FP32 form at least as well as the FP64 oracle agrees with
+      itself when its own embedding is rounded once to BF16 (the stored oracle run: how far BF16
+      storage alone moves the exact method's k-means model selection on this graph), less 0.01.
+    Without that stored run the agreement clause is not evaluated."""
     planted_ok = bool(quality["nmi_planted"] >= fp32["nmi_planted"] - 0.005)
     out = {"equal_nmi_planted": planted_ok}
-    floor = quality.get("oracle", {}).get("fp32_rounded_z", {}).get("nmi_vs_oracle")
+    floor = quality.get("oracle", {}).get("bf16_rounded_z", {}).get("nmi_vs_oracle")
     if floor is not None:
-        out["nmi_floor_fp64_vs_fp32_rounded"] = floor
+        out["nmi_floor_fp64_vs_bf16_rounded"] = floor
         out["equal_nmi_agreement"] = bool(fp32["nmi_bf16_vs_fp32"] >= floor - 0.01)
         out["equal_nmi"] = planted_ok and out["equal_nmi_agreement"]
     else:
@@ -782,6 +786,11 @@ def main():
                              "fp32_rounded_z": {"k_best": int(ref["k_z32"]),
                                                 "nmi_vs_oracle": nmi(ref["labels_z32"], ref_lab),
                                                 "ari_vs_oracle": ari(ref["labels_z32"], ref_lab)}}
+        if "labels_zbf16" in ref:
+            quality["oracle"]["bf16_rounded_z"] = {"k_best": int(ref["k_zbf16"]),
+                                                   "nmi_vs_oracle": nmi(ref["labels_zbf16"], ref_lab),
+                                                   "ari_vs_oracle": ari(ref["labels_zbf16"], ref_lab),
+                                                   "nmi_planted": nmi(ref["labels_zbf16"], g.planted)}
     stages_ref = stored_oracle(wl["graph"], g, kind="stages")
 
     e2e = None

@@ -57,9 +57,13 @@ def _check(rc, what):
 
 
 def set_threads(n=0):
-    """Threads for the oracle's parallel loops (0: the OpenMP default, all cores); returns the
-    count in effect.  Results are bit-identical for any count."""
+    """Threads for the oracle's parallel loops (0: one per processor); returns the count in
+    effect.  Results are bit-identical for any count."""
     return int(lib().orc_set_threads(C.c_int(int(n))))
+
+
+def has_openmp():
+    return bool(lib().orc_openmp())
 
 
 def philox4x32_10(ctr, key):

@@ -31,6 +31,8 @@ def build(verbose: bool = False) -> str:
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode == 0:
             break
+        if verbose:
+            print(f"(failed: {r.stderr.strip()[:300]})")
     else:
         raise RuntimeError(f"gcc failed on {SOURCE}:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, out)

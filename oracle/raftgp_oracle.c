@@ -53,15 +53,24 @@
 enum { ORC_OP_NCUT = 0, ORC_OP_MOD_FULL = 1, ORC_OP_MOD_REDUCED = 2 };
 enum { ORC_CRIT_MOD = 0, ORC_CRIT_NCUT = 1 };
 
-/* Number of threads for the parallel loops (n <= 0: the OpenMP default); returns the count
- * in effect, 1 when the oracle was built without OpenMP. */
+/* Number of threads for the parallel loops (n <= 0: one per processor); returns the count in
+ * effect, 1 when the oracle was built without OpenMP. */
 int orc_set_threads(int n) {
 #ifdef _OPENMP
-    if (n > 0) omp_set_num_threads(n);
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
     return omp_get_max_threads();
 #else
     (void)n;
     return 1;
+#endif
+}
+
+/* 1 when the parallel loops were compiled with OpenMP. */
+int orc_openmp(void) {
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
 #endif
 }
 

@@ -39,6 +39,20 @@ struct FfCfg {
     static_assert(SMEM <= 227 * 1024, "shared memory budget");
 };
 
+// Packed FP32 pairs (Blackwell f32x2): two independent IEEE fused multiply-adds per
+// instruction, each rounded exactly as fmaf, on 64-bit register pairs (low half first).
+__device__ __forceinline__ uint64_t ff_pack(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void ff_unpack(uint64_t v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ void ff_fma2(uint64_t& acc, uint64_t a, uint64_t b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+
 __device__ __forceinline__ void ff_cp16(void* dst, const void* src) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                  : "memory");
@@ -74,6 +88,71 @@ __device__ __forceinline__ void ff_load_chunk(float* buf, const KmState& st, int
         }
     }
     ff_commit();
+}
+
+// One chunk against the warp's 32 points: lane (pr, cr) accumulates its 8 points against NJ
+// centroids (NJ = 8: columns {4cr..4cr+3, 32+4cr..32+4cr+3}; NJ = 4: {4cr..4cr+3}, for a
+// chunk whose real centroids all lie in its first 32 columns), then folds the scores into its
+// running minimum (and second minimum, FINAL) per point, columns ascending.
+template <int D, bool FINAL, int NJ>
+__device__ __forceinline__ void ff_chunk(const float* __restrict__ zw, const float* __restrict__ mT, int pr, int cr,
+                                         int q, float* bv, float* b2, int* bi) {
+    constexpr int NB = NJ / 2;   // centroid pairs
+    // the accumulators as packed pairs: dg[a][b] = (z_2a m_2b, z_2a+1 m_2b+1) and
+    // an[a][b] = (z_2a m_2b+1, z_2a+1 m_2b), each summed over ascending coordinates
+    uint64_t dg[4][NB], an[4][NB];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b2i = 0; b2i < NB; ++b2i) { dg[a][b2i] = 0ull; an[a][b2i] = 0ull; }
+#pragma unroll 4
+    for (int k = 0; k < D; ++k) {
+        const float4 za = *reinterpret_cast<const float4*>(zw + k * FF_PTS + 4 * pr);
+        const float4 zb = *reinterpret_cast<const float4*>(zw + k * FF_PTS + 16 + 4 * pr);
+        const float4 ma = *reinterpret_cast<const float4*>(mT + k * FF_CH + 4 * cr);
+        const uint64_t zp[4] = {ff_pack(za.x, za.y), ff_pack(za.z, za.w), ff_pack(zb.x, zb.y), ff_pack(zb.z, zb.w)};
+        uint64_t mp[NB], ms[NB];
+        mp[0] = ff_pack(ma.x, ma.y); mp[1] = ff_pack(ma.z, ma.w);
+        ms[0] = ff_pack(ma.y, ma.x); ms[1] = ff_pack(ma.w, ma.z);
+        if constexpr (NJ == 8) {
+            const float4 mb = *reinterpret_cast<const float4*>(mT + k * FF_CH + 32 + 4 * cr);
+            mp[2] = ff_pack(mb.x, mb.y); mp[3] = ff_pack(mb.z, mb.w);
+            ms[2] = ff_pack(mb.y, mb.x); ms[3] = ff_pack(mb.w, mb.z);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b2i = 0; b2i < NB; ++b2i) {
+                ff_fma2(dg[a][b2i], zp[a], mp[b2i]);
+                ff_fma2(an[a][b2i], zp[a], ms[b2i]);
+            }
+    }
+    float acc[8][NJ];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b2i = 0; b2i < NB; ++b2i) {
+            ff_unpack(dg[a][b2i], acc[2 * a][2 * b2i], acc[2 * a + 1][2 * b2i + 1]);
+            ff_unpack(an[a][b2i], acc[2 * a][2 * b2i + 1], acc[2 * a + 1][2 * b2i]);
+        }
+    // this lane's columns, ascending: 4cr..4cr+3, then 32+4cr..32+4cr+3
+    const float* nrm = mT + D * FF_CH;
+#pragma unroll
+    for (int j = 0; j < NJ; ++j) {
+        const int jc = j < 4 ? 4 * cr + j : 32 + 4 * cr + (j - 4);
+        const float nq = nrm[jc];
+        const int col = q * FF_CH + jc;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const float sc = fmaf(-2.0f, acc[r][j], nq);
+            if (FINAL) {
+                if (sc < bv[r]) { b2[r] = bv[r]; bv[r] = sc; bi[r] = col; } else { b2[r] = fminf(b2[r], sc); }
+            } else if (sc < bv[r]) {
+                bv[r] = sc;
+                bi[r] = col;
+            }
+        }
+    }
 }
 
 template <typename T, int D, bool FINAL>
@@ -127,42 +206,9 @@ __global__ void __launch_bounds__(FF_THREADS, FfCfg<D>::MIN_BLOCKS)
         }
         __syncthreads();
         const float* mT = chunk0 + buf * C::CHUNK;
-        float acc[8][8];
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) acc[r][j] = 0.f;
-#pragma unroll 4
-        for (int k = 0; k < D; ++k) {
-            const float4 za = *reinterpret_cast<const float4*>(zw + k * FF_PTS + 4 * pr);
-            const float4 zb = *reinterpret_cast<const float4*>(zw + k * FF_PTS + 16 + 4 * pr);
-            const float4 ma = *reinterpret_cast<const float4*>(mT + k * FF_CH + 4 * cr);
-            const float4 mb = *reinterpret_cast<const float4*>(mT + k * FF_CH + 32 + 4 * cr);
-            const float z[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
-            const float m[8] = {ma.x, ma.y, ma.z, ma.w, mb.x, mb.y, mb.z, mb.w};
-#pragma unroll
-            for (int r = 0; r < 8; ++r)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[r][j] = fmaf(z[r], m[j], acc[r][j]);
-        }
-        // this lane's columns, ascending: 4cr..4cr+3, then 32+4cr..32+4cr+3
-        const float* nrm = mT + D * FF_CH;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int jc = j < 4 ? 4 * cr + j : 32 + 4 * cr + (j - 4);
-            const float nq = nrm[jc];
-            const int col = q * FF_CH + jc;
-#pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                const float s = fmaf(-2.0f, acc[r][j], nq);
-                if (FINAL) {
-                    if (s < bv[r]) { b2[r] = bv[r]; bv[r] = s; bi[r] = col; } else { b2[r] = fminf(b2[r], s); }
-                } else if (s < bv[r]) {
-                    bv[r] = s;
-                    bi[r] = col;
-                }
-            }
-        }
+        // a candidate's last chunk with at most 32 real centroids: only the first half
+        if (b.k[c] - q * FF_CH > 32) ff_chunk<D, FINAL, 8>(zw, mT, pr, cr, q, bv, b2, bi);
+        else ff_chunk<D, FINAL, 4>(zw, mT, pr, cr, q, bv, b2, bi);
         if (!hn || cn != c) {
             // candidate c is complete: combine the 8 lanes of each point group (ties to the
             // lowest column), then lane cr reports point cr of the group

@@ -30,7 +30,7 @@ def test_assign_work_counts_real_centroids_and_passes():
 
 
 def test_equal_nmi_rule_needs_both_clauses():
-    q = {"nmi_planted": 0.745, "oracle": {"fp32_rounded_z": {"nmi_vs_oracle": 0.86}}}
+    q = {"nmi_planted": 0.745, "oracle": {"bf16_rounded_z": {"nmi_vs_oracle": 0.86}}}
     ok = bench.equal_nmi_rule(q, {"nmi_planted": 0.7447, "nmi_bf16_vs_fp32": 0.861})
     assert ok["equal_nmi"] and ok["equal_nmi_planted"] and ok["equal_nmi_agreement"]
     worse = bench.equal_nmi_rule(q, {"nmi_planted": 0.76, "nmi_bf16_vs_fp32": 0.861})
