@@ -248,7 +248,7 @@ static raftgp_status run_embed(const raftgp_csr* g, const raftgp_embed_opts* o, 
     if (o->n_layers == 0) {
         if (flat0)
             e = launch_spmm_flat(agg0, n, g->row_ptr_bits, g->row_ptr, g->col, g->nnz, w.deg, w.rs, w.gvec, 2, L,
-                                 w.bufB, Z, o->stage_out[0], w.work, s);
+                                 w.bufB, Z, o->stage_out[0], w.work, w.err, s);
         else
             e = launch_layer(agg0, o->dtype, g, w.deg, w.rs, w.gvec, 2, nullptr, L, L, nullptr, w.bufB, Z,
                              o->stage_out[0], w.heavy, w.heavy_count, s);
@@ -264,7 +264,7 @@ static raftgp_status run_embed(const raftgp_csr* g, const raftgp_embed_opts* o, 
         launch_self_csr(g, w.rp_self, w.col_self, s);
         if (flat0)
             e = launch_spmm_flat(agg0, n, g->row_ptr_bits, g->row_ptr, g->col, g->nnz, w.deg, w.rs, w.gvec, 0, L,
-                                 w.bufB, w.bufA, o->stage_out[0], w.work, s);
+                                 w.bufB, w.bufA, o->stage_out[0], w.work, w.err, s);
         else
             e = launch_layer(agg0, o->dtype, g, w.deg, w.rs, w.gvec, 0, nullptr, L, L, nullptr, w.bufB, w.bufA,
                              o->stage_out[0], w.heavy, w.heavy_count, s);
@@ -275,7 +275,7 @@ static raftgp_status run_embed(const raftgp_csr* g, const raftgp_embed_opts* o, 
             const bool last = k == o->n_layers;
             if (spmm_flat_supported(AGG_GCN_, o->dtype, o->dims[k]))
                 e = launch_spmm_flat(AGG_GCN_, n, 64, w.rp_self, w.col_self, g->nnz, w.deg, w.rsh, nullptr, 1,
-                                     o->dims[k], w.bufB, last ? Z : w.bufA, o->stage_out[k], w.work + k, s);
+                                     o->dims[k], w.bufB, last ? Z : w.bufA, o->stage_out[k], w.work + k, w.err, s);
             else
                 e = launch_layer(AGG_GCN_, o->dtype, g, w.deg, w.rsh, nullptr, 1, nullptr, o->dims[k], o->dims[k],
                                  nullptr, w.bufB, last ? Z : w.bufA, o->stage_out[k], w.heavy, w.heavy_count, s);

@@ -19,6 +19,14 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tc_util.cuh"
+
+// Row staging: 0 = every lane copies 16 bytes of a gathered row with cp.async; 1 = TMA
+// tile::gather4 (four indexed rows of the feature matrix per instruction, completion on a
+// per-buffer mbarrier).  Both give the same bits.
+#ifndef RAFTGP_FLAT_G4
+#define RAFTGP_FLAT_G4 0
+#endif
 
 namespace raftgp {
 
@@ -39,7 +47,32 @@ struct FlatArgs {
     __nv_bfloat16* out;
     __nv_bfloat16* stage;    // optional copy of the finished rows
     int* work;               // chunk counter (zeroed before the launch)
+    uint32_t* err;           // device error word (a bounded wait that gave up: DERR_TIMEOUT)
 };
+
+// Four rows (y0..y3) of the 2D tensor map, the whole row width from x = 0, into dst (4 boxes
+// one after another); completion counted on bar.
+__device__ __forceinline__ void tma_gather4(void* dst, const CUtensorMap* map, uint64_t* bar, int y0, int y1, int y2,
+                                            int y3) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(smem_addr(bar)), "r"(0), "r"(y0), "r"(y1), "r"(y2), "r"(y3)
+        : "memory");
+}
+
+// Bounded wait on a staging buffer's mbarrier (2 s); false (and DERR_TIMEOUT) if it gave up.
+__device__ __forceinline__ bool fl_wait(uint64_t* bar, uint32_t parity, uint32_t* err) {
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if ((it & 255) == 255 && global_ns() - t0 > TC_WAIT_NS) {
+            if (err) atomicOr(err, DERR_TIMEOUT);
+            return false;
+        }
+    }
+}
 
 __device__ __forceinline__ int64_t rp_at(const FlatArgs& a, int64_t r) {
     r = r < a.n ? r : a.n;
@@ -144,16 +177,26 @@ struct FlCfg {
     static_assert(B <= 32 && B % GPW == 0 && E % GPW == 0, "lane layout");
 };
 
-template <int AGG, int LIN, int NBUF>
-__global__ void __launch_bounds__(FL_WARPS * 32) k_spmm_flat(FlatArgs a, const __nv_bfloat16* __restrict__ X) {
+template <int AGG, int LIN, int NBUF, bool G4>
+__global__ void __launch_bounds__(FL_WARPS * 32) k_spmm_flat(FlatArgs a, const __nv_bfloat16* __restrict__ X,
+                                                             const __grid_constant__ CUtensorMap tmX) {
     using C = FlCfg<LIN>;
     constexpr int E = C::E, LPR = C::LPR, GPW = C::GPW, B = C::B, U = C::U, ROWB = C::ROWB, EG = C::EG;
-    extern __shared__ __align__(16) unsigned char fl_smem[];
+    extern __shared__ __align__(1024) unsigned char fl_smem[];
+    __shared__ uint64_t fl_bar[FL_WARPS][NBUF];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int grp = lane / LPR, sub = lane % LPR;
     const int c0 = sub * E + grp * EG;   // first column this lane finishes
     unsigned char* wbuf = fl_smem + wid * (NBUF * B * ROWB);
     const __nv_bfloat16* Xl = X + sub * E;
+    if constexpr (G4) {
+        if (lane == 0)
+            for (int q = 0; q < NBUF; ++q) mbar_init(&fl_bar[wid][q], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+    }
+    bool ok = true;
 
     float gl[EG];
 #pragma unroll
@@ -195,13 +238,31 @@ __global__ void __launch_bounds__(FL_WARPS * 32) k_spmm_flat(FlatArgs a, const _
                 const int cnt = (items - iq) < B ? (int)(items - iq) : B;
                 unsigned char* buf = wbuf + (int)(bi % NBUF) * (B * ROWB);
                 __syncwarp();
+                if constexpr (G4) {
+                    // lane L < ceil(cnt / 4) gathers entries 4L .. 4L+3 (past cnt: entry 0 again)
+                    int32_t j[4];
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int t = u * GPW + grp;
-                    const int32_t j = __shfl_sync(0xffffffffu, my_col, t < cnt ? t : 0);
-                    if (t < cnt) cp_async16(buf + t * ROWB + sub * 16, Xl + (int64_t)j * LIN);
+                    for (int q = 0; q < 4; ++q) {
+                        const int t = 4 * lane + q;
+                        j[q] = __shfl_sync(0xffffffffu, my_col, t < cnt ? t : 0);
+                    }
+                    const int ninst = (cnt + 3) / 4;
+                    uint64_t* bar = &fl_bar[wid][(int)(bi % NBUF)];
+                    // the buffer's previous contents were read by every lane (generic proxy)
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_expect_tx(bar, (uint32_t)(ninst * 4 * ROWB));
+                    __syncwarp();
+                    if (lane < ninst) tma_gather4(buf + 4 * lane * ROWB, &tmX, bar, j[0], j[1], j[2], j[3]);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int t = u * GPW + grp;
+                        const int32_t j = __shfl_sync(0xffffffffu, my_col, t < cnt ? t : 0);
+                        if (t < cnt) cp_async16(buf + t * ROWB + sub * 16, Xl + (int64_t)j * LIN);
+                    }
+                    cp_async_commit();
                 }
-                cp_async_commit();
                 ++bi;
                 iq += cnt;
                 if (iq < items) {
@@ -224,7 +285,7 @@ __global__ void __launch_bounds__(FL_WARPS * 32) k_spmm_flat(FlatArgs a, const _
     };
 
     float acc[E];
-    while (nxt.id < nchunks) {
+    while (ok && nxt.id < nchunks) {
         cur = nxt;
         fetch_chunk<AGG>(a, lane, nchunks, nxt);
         if (ich == 1) {   // the issue side had moved into this chunk: iq and my_col are current
@@ -286,12 +347,19 @@ __global__ void __launch_bounds__(FL_WARPS * 32) k_spmm_flat(FlatArgs a, const _
             // keep NBUF - 1 batches in flight beyond the one about to be added
             while (bi - ba < NBUF && issue()) {
             }
-            const long long ahead = bi - ba - 1;   // batches issued after this one
             static_assert(NBUF >= 2 && NBUF <= 4, "pipeline depth");
-            if (ahead >= NBUF - 1) cp_async_wait<NBUF - 1>();
-            else if (ahead == 2) cp_async_wait<2>();
-            else if (ahead == 1) cp_async_wait<1>();
-            else cp_async_wait<0>();
+            if constexpr (G4) {
+                if (!fl_wait(&fl_bar[wid][(int)(ba % NBUF)], (uint32_t)((ba / NBUF) & 1), a.err)) {
+                    ok = false;
+                    break;
+                }
+            } else {
+                const long long ahead = bi - ba - 1;   // batches issued after this one
+                if (ahead >= NBUF - 1) cp_async_wait<NBUF - 1>();
+                else if (ahead == 2) cp_async_wait<2>();
+                else if (ahead == 1) cp_async_wait<1>();
+                else cp_async_wait<0>();
+            }
             __syncwarp();
             const unsigned char* buf = wbuf + (int)(ba % NBUF) * (B * ROWB) + sub * 16;
             const int cnt = (items - q0) < B ? (int)(items - q0) : B;
@@ -314,9 +382,15 @@ __global__ void __launch_bounds__(FL_WARPS * 32) k_spmm_flat(FlatArgs a, const _
             }
             ++ba;
         }
+        if (!ok) break;
         while (cr < nrows) finish();   // the last row and any empty rows at the end
     }
-    cp_async_wait<0>();
+    if constexpr (G4) {
+        // a wait gave up: let the copies still in flight land before the warp exits (bounded)
+        for (long long k = ba; k < bi; ++k) mbar_drain(&fl_bar[wid][(int)(k % NBUF)], (uint32_t)((k / NBUF) & 1));
+    } else {
+        cp_async_wait<0>();
+    }
 }
 
 // CSR of A + I: row i holds i first, then its neighbours in their stored order.
@@ -342,8 +416,16 @@ __global__ void k_self_csr(int64_t n, const int32_t* rp32, const int64_t* rp64, 
 template <int AGG, int LIN, int NBUF>
 cudaError_t launch_flat_t(const FlatArgs& a, const void* X, cudaStream_t s) {
     using C = FlCfg<LIN>;
-    auto kern = k_spmm_flat<AGG, LIN, NBUF>;
+    constexpr bool G4 = RAFTGP_FLAT_G4 != 0;
+    auto kern = k_spmm_flat<AGG, LIN, NBUF, G4>;
     const int smem = FL_WARPS * NBUF * C::B * C::ROWB;
+    CUtensorMap tmX;
+    memset(&tmX, 0, sizeof(tmX));
+    if (G4) {
+        // rows of X, one box = one whole row (the gather's boxes are one row high)
+        cudaError_t me = make_map_bf16(&tmX, X, LIN, a.n, LIN, 1, CU_TENSOR_MAP_SWIZZLE_NONE);
+        if (me != cudaSuccess) return me;
+    }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -355,7 +437,7 @@ cudaError_t launch_flat_t(const FlatArgs& a, const void* X, cudaStream_t s) {
     const int blocks = (int)(want < cap ? (want < 1 ? 1 : want) : cap);
     cudaMemsetAsync(a.work, 0, sizeof(int), s);
     ProfScope ps(s, AGG == AGG_GCN_ ? PF_SPMM_GCN : PF_SPMM_PROJ, 1);
-    kern<<<blocks, FL_WARPS * 32, smem, s>>>(a, reinterpret_cast<const __nv_bfloat16*>(X));
+    kern<<<blocks, FL_WARPS * 32, smem, s>>>(a, reinterpret_cast<const __nv_bfloat16*>(X), tmX);
     return cudaGetLastError();
 }
 
@@ -395,7 +477,7 @@ void launch_self_csr(const raftgp_csr* g, int64_t* rp_self, int32_t* col_self, c
 
 cudaError_t launch_spmm_flat(int agg, int64_t n, int rp_bits, const void* row_ptr, const int32_t* col, int64_t nnz_g,
                              const int32_t* deg, const float* rowscale, const float* gvec, int act, int lin,
-                             const void* X, void* out, void* stage, int* work, cudaStream_t s) {
+                             const void* X, void* out, void* stage, int* work, uint32_t* err, cudaStream_t s) {
     FlatArgs a;
     a.n = n;
     a.rp32 = rp_bits == 32 ? (const int32_t*)row_ptr : nullptr;
@@ -409,6 +491,7 @@ cudaError_t launch_spmm_flat(int agg, int64_t n, int rp_bits, const void* row_pt
     a.out = reinterpret_cast<__nv_bfloat16*>(out);
     a.stage = reinterpret_cast<__nv_bfloat16*>(stage);
     a.work = work;
+    a.err = err;
     if (n == 0) return cudaSuccess;
     switch (agg) {
         case AGG_NCUT_: return launch_flat_w<AGG_NCUT_>(a, lin, X, s);
