@@ -547,9 +547,10 @@ def bench_batched(args):
     dg, off = api.concat_graphs(graphs, dev)
     edges = sum(g.n_edges for g in graphs)
     t0 = time.perf_counter()
-    dtype = args.batch_dtype or wl["dtype"]
+    assign = args.batch_assign or "ffma"
+    dtype = args.batch_dtype or ("bf16" if assign != "ffma" else wl["dtype"])
     plan = api.BatchPlan(dg, off, dims=wl["dims"], dtype=dtype, kmin=wl["kmin"], kmax_factor=wl["kmax_factor"],
-                         grid=wl["grid"], iters=wl["iters"], seed=2)
+                         grid=wl["grid"], iters=wl["iters"], seed=2, assign=assign)
     torch.cuda.synchronize()
     plan_s = time.perf_counter() - t0
     for _ in range(max(args.warmup, 1)):
@@ -564,6 +565,7 @@ def bench_batched(args):
     e1.record()
     torch.cuda.synchronize()
     clocks = sampler.stop()
+    plan.check()
     ms = e0.elapsed_time(e1) / args.steps
     lab = labels.cpu().numpy()
     ks = ks.cpu().numpy()
@@ -584,6 +586,7 @@ def bench_batched(args):
                                    "one captured plan",
                        "graphs": len(graphs), "nodes": int(off[-1]), "edges": edges},
             "graphs_per_s": len(graphs) / (ms * 1e-3), "plan_create_s": plan_s, "tuning": plan.tuning(),
+            "assign": assign,
             "quality": {"nmi_planted_mean": float(np.mean(nmis)), "nmi_planted_min": float(np.min(nmis)),
                         "k_minus_planted_mean": float(np.mean(kdiff)), "per_graph": per_graph},
             "clocks": clocks}
@@ -660,7 +663,9 @@ def main():
     ap.add_argument("--assign", default=None, choices=["tc", "tc8", "ffma"],
                     help="k-means engine (default: tc8 for bf16, ffma for f32)")
     ap.add_argument("--batch-dtype", default=None, choices=["f32", "bf16"],
-                    help="storage of the batched form's embedding (default f32)")
+                    help="storage of the batched form's embedding (default f32; bf16 with --batch-assign tc/tc8)")
+    ap.add_argument("--batch-assign", default=None, choices=["ffma", "tc", "tc8"],
+                    help="the batched form's Lloyd engine (default ffma)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32-check", action="store_true",

@@ -288,6 +288,13 @@ typedef struct {
     int32_t criterion;     /* RAFTGP_CRIT_MOD or RAFTGP_CRIT_NCUT */
     int32_t lloyd_variant; /* 0: autotune the Lloyd kernel; v in 1..7: use variant v - 1 of the
                               list raftgp_batch_plan_tuning reports (no timing) */
+    int32_t assign;        /* RAFTGP_ASSIGN_FFMA (default): the FP32 Lloyd kernels above, each
+                              graph's result equal to a single-graph FP32 partition;
+                              RAFTGP_ASSIGN_TC8 / RAFTGP_ASSIGN_TC: tensor-core Lloyd (BF16
+                              embeddings only): Lloyd passes on the hi (TC8) or hi + lo (TC) BF16
+                              centroid operand, the final assignment on hi + lo with the FP32
+                              re-check of near ties, so every reported label is the FP32-nearest
+                              centroid (the autotuner is not run) */
     uint64_t seed;         /* k-means++ seed (the same for every graph) */
 } raftgp_batch_opts;
 
@@ -318,6 +325,10 @@ raftgp_status raftgp_batch_plan_candidates(raftgp_batch_plan* plan, int32_t* k, 
  * Every variant computes the same labels. */
 raftgp_status raftgp_batch_plan_tuning(const raftgp_batch_plan* plan, int32_t* threads, int32_t* points_per_thread,
                                        float* ms);
+/* Waits for the device to finish and reports the last replay's device-side status: RAFTGP_OK,
+ * or RAFTGP_ETIMEOUT if a bounded wait inside a kernel gave up (the labels are then
+ * incomplete).  Synchronises. */
+raftgp_status raftgp_batch_plan_check(const raftgp_batch_plan* plan);
 /* The embedding of the last replay (n x d in the plan's dtype, row-major, the Z every graph's
  * model selection ran on) copied to the device buffer Z_out.  Synchronises. */
 raftgp_status raftgp_batch_plan_embedding(const raftgp_batch_plan* plan, void* Z_out);

@@ -26,7 +26,7 @@ EXPORTS = ("raftgp_workspace_size", "raftgp_embed", "raftgp_select", "raftgp_par
            "raftgp_kmeanspp", "raftgp_kmeanspp_noalloc", "raftgp_lloyd", "raftgp_lloyd_workspace_size", "raftgp_profile_enable", "raftgp_profile_enable_family", "raftgp_profile_read", "raftgp_last_error", "raftgp_debug_seed_skip_block",
            "raftgp_version", "raftgp_diff_workspace_size", "raftgp_gcn_layer_forward", "raftgp_gcn_layer_backward",
            "raftgp_softmod_loss", "raftgp_centroids", "raftgp_gcn_weights", "raftgp_adam_step",
-           "raftgp_batch_workspace_size", "raftgp_batch_plan_create", "raftgp_batch_plan_run", "raftgp_batch_plan_embedding",
+           "raftgp_batch_workspace_size", "raftgp_batch_plan_create", "raftgp_batch_plan_run", "raftgp_batch_plan_embedding", "raftgp_batch_plan_check",
            "raftgp_batch_plan_candidates", "raftgp_batch_plan_tuning", "raftgp_batch_plan_destroy",
            "raftgp_partition_batched", "raftgp_bisect_workspace_size", "raftgp_select_bisect",
            "raftgp_sbm_workspace_size", "raftgp_sbm_count", "raftgp_sbm_emit", "raftgp_coo_to_csr_workspace_size",
@@ -57,7 +57,8 @@ class Sbm(C.Structure):
 
 class BatchOpts(C.Structure):
     _fields_ = [("kmin", C.c_int32), ("kmax_factor", C.c_float), ("grid", C.c_int32), ("iters", C.c_int32),
-                ("criterion", C.c_int32), ("lloyd_variant", C.c_int32), ("seed", C.c_uint64)]
+                ("criterion", C.c_int32), ("lloyd_variant", C.c_int32), ("assign", C.c_int32),
+                ("seed", C.c_uint64)]
 
 
 class SelectOpts(C.Structure):
@@ -140,6 +141,7 @@ def lib():
                                                C.POINTER(BatchOpts), P, P, P, C.c_size_t, P, C.POINTER(C.c_void_p)]
         L.raftgp_batch_plan_run.argtypes = [C.c_void_p, P]
         L.raftgp_batch_plan_embedding.argtypes = [C.c_void_p, P]
+        L.raftgp_batch_plan_check.argtypes = [C.c_void_p]
         L.raftgp_batch_plan_candidates.argtypes = [C.c_void_p, P, P, P, P]
         L.raftgp_batch_plan_tuning.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                                C.POINTER(C.c_float)]
@@ -148,7 +150,8 @@ def lib():
         L.raftgp_partition_batched.argtypes = [C.POINTER(Csr), I64P, C.c_int32, C.POINTER(EmbedOpts),
                                                C.POINTER(BatchOpts), P, P, P, C.c_size_t, P]
         for name in ("raftgp_batch_plan_create", "raftgp_batch_plan_run", "raftgp_batch_plan_candidates",
-                     "raftgp_batch_plan_tuning", "raftgp_batch_plan_embedding", "raftgp_partition_batched"):
+                     "raftgp_batch_plan_tuning", "raftgp_batch_plan_embedding", "raftgp_batch_plan_check",
+                     "raftgp_partition_batched"):
             getattr(L, name).restype = C.c_int
         L.raftgp_bisect_workspace_size.restype = C.c_size_t
         L.raftgp_bisect_workspace_size.argtypes = [C.c_int64, C.c_int32, C.c_int32]

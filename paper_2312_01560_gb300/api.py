@@ -358,11 +358,12 @@ def concat_graphs(graphs, device, row_ptr_bits=64):
     return dg, np.asarray(offs, dtype=np.int64)
 
 
-def batch_opts(kmin=2, kmax_factor=2.0, grid=10, iters=50, criterion="mod", seed=2, lloyd_variant=0):
+def batch_opts(kmin=2, kmax_factor=2.0, grid=10, iters=50, criterion="mod", seed=2, lloyd_variant=0, assign="ffma"):
     o = _abi.BatchOpts()
     o.kmin, o.kmax_factor, o.grid, o.iters = int(kmin), float(kmax_factor), int(grid), int(iters)
     o.criterion = _abi.CRIT[criterion] if isinstance(criterion, str) else int(criterion)
     o.lloyd_variant = int(lloyd_variant)
+    o.assign = _code(_abi.ASSIGN, assign)
     o.seed = int(seed)
     return o
 
@@ -388,7 +389,7 @@ class BatchPlan:
         offp = self.off.ctypes.data_as(C.POINTER(C.c_int64))
         nbytes = lib().raftgp_batch_workspace_size(C.byref(self.csr), offp, self.ng, C.byref(self.eo), C.byref(self.bo))
         if nbytes == 0:
-            raise _abi.RaftgpError(_abi.EINVAL, "invalid batch")
+            raise _abi.RaftgpError(_abi.EINVAL, "invalid batch: " + lib().raftgp_last_error().decode())
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
         self.labels = torch.empty(g.n, dtype=torch.int32, device=dev)
         self.k = torch.empty(self.ng, dtype=torch.int32, device=dev)
@@ -420,6 +421,10 @@ class BatchPlan:
         ms = (C.c_float * 7)()
         check(lib().raftgp_batch_plan_tuning(self._h, C.byref(th), C.byref(pp), ms))
         return {"threads": th.value, "points_per_thread": pp.value, "ms": list(ms)}
+
+    def check(self):
+        """Synchronises and raises if a bounded device wait of the last replay gave up."""
+        check(lib().raftgp_batch_plan_check(self._h))
 
     def embedding(self):
         """The embedding of the last replay (n x d, the plan's dtype)."""

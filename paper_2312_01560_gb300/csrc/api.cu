@@ -929,6 +929,7 @@ struct raftgp_batch_plan {
     int32_t* k_out = nullptr;
     int threads = 256, ppt = 1;
     float tune_ms[7] = {};
+    void* stg = nullptr;   // tensor-core Lloyd: staging of the centroid operands
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;   // the plan's own stream, on which the graph is captured
@@ -951,6 +952,9 @@ raftgp_status batch_layout(const raftgp_csr* g, const int64_t* off, int ng, cons
     if (bo->iters < 1) return fail(RAFTGP_EINVAL, "iters must be >= 1");
     if (!(bo->kmax_factor > 0.f)) return fail(RAFTGP_EINVAL, "kmax_factor must be positive");
     if (bo->lloyd_variant < 0 || bo->lloyd_variant > 7) return fail(RAFTGP_EINVAL, "lloyd_variant must be in [0, 7]");
+    if (bo->assign < RAFTGP_ASSIGN_FFMA || bo->assign > RAFTGP_ASSIGN_TC8) return fail(RAFTGP_EINVAL, "unknown assign engine");
+    if (bo->assign != RAFTGP_ASSIGN_FFMA && eo->dtype != RAFTGP_BF16)
+        return fail(RAFTGP_EINVAL, "tensor-core assignment needs BF16 embeddings");
     if (off[0] != 0 || off[ng] != g->n) return fail(RAFTGP_EINVAL, "graph_off must run from 0 to n");
     p.g = *g;
     p.eo = *eo;
@@ -1003,21 +1007,29 @@ void carve_batch(Carver& c, raftgp_batch_plan& p) {
     b.chosen = c.take<uint8_t>(n);
     b.queue = c.take<int>(64);
     p.ew.local_row = b.local_row;
+    p.stg = p.bo.assign != RAFTGP_ASSIGN_FFMA ? c.take<char>(batch_tc_staging_bytes(p.d)) : nullptr;
 }
 
 // everything after validation: embedding, grids, seeding, both Lloyd phases, selection
 raftgp_status batch_enqueue(raftgp_batch_plan& p, cudaStream_t s) {
     const int zdtype = p.eo.dtype;
+    cudaMemsetAsync(p.err, 0, sizeof(uint32_t), s);   // device error word of this replay
     cudaMemsetAsync(p.bd.cand_k, 0, sizeof(int32_t) * (size_t)p.ng * BATCH_SLOTS, s);
     launch_batch_prologue(p.bd, p.bo.kmin, p.bo.grid, s);   // work counters, local rows, coarse grids
     raftgp_status st = run_embed(&p.g, &p.eo, p.Z, p.ew, true, s);
     if (st) return st;
     cudaError_t e = launch_batch_seed(p.bd, p.Z, zdtype, p.d, p.bo.seed, s);
-    if (e == cudaSuccess) e = launch_batch_lloyd(p.bd, p.Z, zdtype, p.d, 0, p.bo.iters, &p.g, p.threads, p.ppt, s);
+    auto lloyd = [&](int phase) {
+        return p.bo.assign != RAFTGP_ASSIGN_FFMA
+                   ? launch_batch_lloyd_tc(p.bd, p.Z, p.d, phase, p.bo.iters, p.bo.assign == RAFTGP_ASSIGN_TC ? 1 : 0,
+                                           &p.g, p.stg, p.err, s)
+                   : launch_batch_lloyd(p.bd, p.Z, zdtype, p.d, phase, p.bo.iters, &p.g, p.threads, p.ppt, s);
+    };
+    if (e == cudaSuccess) e = lloyd(0);
     if (e != cudaSuccess) return cuda_fail(e, "batched selection");
     if (p.bo.grid > 1) {
         launch_batch_refine(p.bd, p.bo.grid, p.bo.criterion, s);
-        e = launch_batch_lloyd(p.bd, p.Z, zdtype, p.d, 1, p.bo.iters, &p.g, p.threads, p.ppt, s);
+        e = lloyd(1);
         if (e != cudaSuccess) return cuda_fail(e, "batched selection");
     }
     launch_batch_select(p.bd, p.bo.criterion, p.labels, p.k_out, s);
@@ -1075,6 +1087,12 @@ raftgp_status raftgp_batch_plan_create(const raftgp_csr* g, const int64_t* graph
     cudaEventCreate(&e1);
     float best = INFINITY;
     for (int v = 0; v < 7; ++v) {
+        if (p->bo.assign != RAFTGP_ASSIGN_FFMA) {   // the tensor-core Lloyd kernel has one shape
+            best = 0.f;
+            p->threads = 192;
+            p->ppt = -1;
+            break;
+        }
         if (p->bo.lloyd_variant > 0 && v != p->bo.lloyd_variant - 1) continue;   // a forced variant
         // six shapes of the scalar kernel, then the register-tiled kernel (ppt 0)
         const int th = v < 6 ? kTuneThreads[v / 2] : 256, pp = v < 6 ? 1 + v % 2 : 0;
@@ -1156,6 +1174,13 @@ raftgp_status raftgp_batch_plan_tuning(const raftgp_batch_plan* plan, int32_t* t
     return RAFTGP_OK;
 }
 
+raftgp_status raftgp_batch_plan_check(const raftgp_batch_plan* plan) {
+    if (!plan) return fail(RAFTGP_EINVAL, "plan is NULL");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "batched partition");
+    return read_error_word(plan->err, nullptr);
+}
+
 raftgp_status raftgp_batch_plan_embedding(const raftgp_batch_plan* plan, void* Z_out) {
     if (!plan || !Z_out) return fail(RAFTGP_EINVAL, "plan or Z_out is NULL");
     cudaError_t e = cudaDeviceSynchronize();
@@ -1183,6 +1208,7 @@ raftgp_status raftgp_partition_batched(const raftgp_csr* g, const int64_t* graph
     if (st) return st;
     st = raftgp_batch_plan_run(plan, stream);
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (!st && e == cudaSuccess) st = raftgp_batch_plan_check(plan);
     raftgp_batch_plan_destroy(plan);
     if (st) return st;
     if (e != cudaSuccess) return cuda_fail(e, "batched partition");

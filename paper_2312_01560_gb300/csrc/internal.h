@@ -250,6 +250,11 @@ void launch_batch_prologue(BatchDev b, int kmin, int G, cudaStream_t s);
 cudaError_t launch_batch_seed(BatchDev b, const void* Z, int zdtype, int d, uint64_t seed, cudaStream_t s);
 cudaError_t launch_batch_lloyd(BatchDev b, const void* Z, int zdtype, int d, int phase, int iters, const raftgp_csr* g,
                                int threads, int ppt, cudaStream_t s);
+// tensor-core Lloyd of the batched form (BF16 embeddings, d = 32 or 64); stg: a device staging
+// area of batch_tc_staging_bytes(d) for the centroid operands
+size_t batch_tc_staging_bytes(int d);
+cudaError_t launch_batch_lloyd_tc(BatchDev b, const void* Z, int d, int phase, int iters, int lo_fast,
+                                  const raftgp_csr* g, void* stg, uint32_t* err, cudaStream_t s);
 void launch_batch_refine(BatchDev b, int G, int criterion, cudaStream_t s);
 void launch_batch_select(BatchDev b, int criterion, int32_t* labels_out, int32_t* k_out, cudaStream_t s);
 void launch_batch_check(const raftgp_csr* g, int ng, const int64_t* node_off, uint32_t* err, cudaStream_t s);

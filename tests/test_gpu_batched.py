@@ -170,3 +170,46 @@ def test_bf16_batch_equals_single_graph_selection_on_its_embedding(cuda, batch):
               f"fp32 {nmi(l32[off[gi]:off[gi + 1]], g.planted):.4f}")
     plan.close()
     plan32.close()
+
+
+@pytest.mark.parametrize("engine", ["tc8", "tc"])
+def test_tensor_core_batch_matches_single_graph_tensor_core_selection(cuda, batch, engine):
+    # tensor-core Lloyd in the batched plan: every graph's candidates, K* and labels equal a
+    # single-graph selection with the same engine on the plan's own BF16 embedding (whose final
+    # labels are the FP32-nearest centroids of the last Lloyd pass, tested with the single-graph
+    # engine); drift against the FP32-engine batch is stated
+    sub = batch[:6]
+    dg, off = api.concat_graphs(sub, cuda)
+    plan = api.BatchPlan(dg, off, dims=DIMS, dtype="bf16", kmin=2, grid=10, iters=50, seed=2, assign=engine)
+    labels, ks = plan.run()
+    plan.check()
+    Z = plan.embedding()
+    labels, ks = labels.cpu().numpy(), ks.cpu().numpy()
+    ck, cmod, cncut, cpass = plan.candidates()
+    t = plan.tuning()
+    assert t["points_per_thread"] == -1
+    plan32 = api.BatchPlan(dg, off, dims=DIMS, dtype="bf16", kmin=2, grid=10, iters=50, seed=2)
+    l32, k32 = plan32.run()
+    plan32.check()
+    l32, k32 = l32.cpu().numpy(), k32.cpu().numpy()
+    for gi, g in enumerate(sub):
+        one = api.DeviceGraph.from_host(g, cuda)
+        Zg = Z[off[gi]:off[gi + 1]].contiguous()
+        lab1, rep1 = api.select(one, Zg, kmin=2, kmax=_kmax(g.n), grid=10, iters=50, assign=engine, seed=2)
+        lab = labels[off[gi]:off[gi + 1]]
+        mine = sorted((int(k), m, int(p)) for k, m, p in zip(ck[gi], cmod[gi], cpass[gi]) if k > 0)
+        theirs = sorted((int(c[0]), c[1], int(c[3])) for c in rep1["cands"])
+        same = sum(a == b for a, b in zip(mine, theirs))
+        print(f"graph {gi} (N={g.n}) {engine}: K* batch {ks[gi]} single {rep1['k']}; candidates equal {same}/"
+              f"{len(theirs)}; NMI(batch, single) {nmi(lab, lab1.cpu().numpy()):.4f}; NMI vs FP32-engine batch "
+              f"{nmi(lab, l32[off[gi]:off[gi + 1]]):.4f}")
+        assert ks[gi] == rep1["k"] and np.array_equal(lab, lab1.cpu().numpy()), gi
+        assert mine == theirs, gi
+    plan.close()
+    plan32.close()
+
+
+def test_tensor_core_batch_needs_bf16(cuda, batch):
+    dg, off = api.concat_graphs(batch[:2], cuda)
+    with pytest.raises(api._abi.RaftgpError, match="BF16"):
+        api.BatchPlan(dg, off, dims=DIMS, dtype="f32", assign="tc8")
