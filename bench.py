@@ -523,8 +523,8 @@ def bench_batched(args):
     """Times replays of one captured plan that partitions 512 DC-SBM graphs of uneven size
     (N log-uniform in [1,000, 50,000], K = round(N^0.35), exponent 2.5, mean degree uniform in
     [10, 30], ratio uniform in [2, 6]); each graph runs its own coarse + refined model
-    selection over [2, ceil(2 N^0.35)].  Plan creation (validation, autotuning, capture) is
-    not timed."""
+    selection over [2, ceil(2 N^0.35)], by default with BF16 storage and tensor-core Lloyd
+    (TC8).  Plan creation (validation, autotuning, capture) is not timed."""
     import multiprocessing as mp
     wl = BATCH_WORKLOAD
     # the generator's recipe, drawn in worker processes started before any GPU call
@@ -547,7 +547,7 @@ def bench_batched(args):
     dg, off = api.concat_graphs(graphs, dev)
     edges = sum(g.n_edges for g in graphs)
     t0 = time.perf_counter()
-    assign = args.batch_assign or "ffma"
+    assign = args.batch_assign or "tc8"
     dtype = args.batch_dtype or ("bf16" if assign != "ffma" else wl["dtype"])
     plan = api.BatchPlan(dg, off, dims=wl["dims"], dtype=dtype, kmin=wl["kmin"], kmax_factor=wl["kmax_factor"],
                          grid=wl["grid"], iters=wl["iters"], seed=2, assign=assign)
@@ -665,7 +665,8 @@ def main():
     ap.add_argument("--batch-dtype", default=None, choices=["f32", "bf16"],
                     help="storage of the batched form's embedding (default f32; bf16 with --batch-assign tc/tc8)")
     ap.add_argument("--batch-assign", default=None, choices=["ffma", "tc", "tc8"],
-                    help="the batched form's Lloyd engine (default ffma)")
+                    help="the batched form's Lloyd engine (default tc8: tensor cores, BF16 storage; ffma: the "
+                         "FP32 kernels)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32-check", action="store_true",
