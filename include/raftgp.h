@@ -264,9 +264,29 @@ typedef struct {
     uint64_t seed;
 } raftgp_bisect_opts;
 size_t raftgp_bisect_workspace_size(int64_t n, int32_t d, int32_t eps);
+/* leaf (device uint64[n], may be NULL): each node's block as its node id in the recursion tree
+ * (the input of a later raftgp_select_bisect_update). */
 raftgp_status raftgp_select_bisect(const raftgp_csr* g, const void* Z, int32_t d, int32_t z_dtype,
-                                   const raftgp_bisect_opts* o, int32_t* labels, int32_t* k_out, void* ws,
-                                   size_t ws_bytes, raftgp_stream_t stream);
+                                   const raftgp_bisect_opts* o, int32_t* labels, uint64_t* leaf, int32_t* k_out,
+                                   void* ws, size_t ws_bytes, raftgp_stream_t stream);
+
+/* Streaming update of Algorithm 1 (Section III-D: the partition tree lets one update only the
+ * tree paths of the nodes whose embedding changed).  g and Z are the new graph and embedding;
+ * old_labels / old_k / old_leaf (device) are a previous run's labels, block count and leaf ids
+ * (raftgp_select_bisect or this call) with the same options; changed (device uint8[n]) marks
+ * every node whose embedding row or degree changed since (for an edge batch: at least both
+ * endpoints of every new edge and every row the embedding recomputed).  A set of the recursion
+ * that is the previous tree's node (every ancestor split as before) and holds no changed node
+ * keeps its previous subtree without k-means; the others are partitioned again, and a changed
+ * split rebuilds the subtree below it.  With reading 0 (2e = the G-degree sum of U) the
+ * result equals raftgp_select_bisect on the new graph and embedding; with reading 1 every
+ * decision also depends on |E|, and kept subtrees are not re-decided (the path update).
+ * Outputs as raftgp_select_bisect; the same workspace size.  Synchronises the stream. */
+raftgp_status raftgp_select_bisect_update(const raftgp_csr* g, const void* Z, int32_t d, int32_t z_dtype,
+                                          const raftgp_bisect_opts* o, const int32_t* old_labels, int32_t old_k,
+                                          const uint64_t* old_leaf, const uint8_t* changed, int32_t* labels,
+                                          uint64_t* leaf, int32_t* k_out, void* ws, size_t ws_bytes,
+                                          raftgp_stream_t stream);
 
 /* ---- Many graphs at once ----
  * The graphs arrive as one block-diagonal CSR: graph g owns the nodes graph_off[g] ..

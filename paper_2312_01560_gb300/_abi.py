@@ -29,6 +29,7 @@ EXPORTS = ("raftgp_workspace_size", "raftgp_embed", "raftgp_select", "raftgp_par
            "raftgp_batch_workspace_size", "raftgp_batch_plan_create", "raftgp_batch_plan_run", "raftgp_batch_plan_embedding", "raftgp_batch_plan_check",
            "raftgp_batch_plan_candidates", "raftgp_batch_plan_tuning", "raftgp_batch_plan_destroy",
            "raftgp_partition_batched", "raftgp_bisect_workspace_size", "raftgp_select_bisect",
+           "raftgp_select_bisect_update",
            "raftgp_sbm_workspace_size", "raftgp_sbm_count", "raftgp_sbm_emit", "raftgp_coo_to_csr_workspace_size",
            "raftgp_coo_to_csr", "raftgp_stream_workspace_size", "raftgp_stream_create", "raftgp_stream_add_edges",
            "raftgp_stream_info", "raftgp_stream_copy", "raftgp_stream_destroy")
@@ -156,8 +157,11 @@ def lib():
         L.raftgp_bisect_workspace_size.restype = C.c_size_t
         L.raftgp_bisect_workspace_size.argtypes = [C.c_int64, C.c_int32, C.c_int32]
         L.raftgp_select_bisect.restype = C.c_int
-        L.raftgp_select_bisect.argtypes = [C.POINTER(Csr), P, C.c_int32, C.c_int32, C.POINTER(BisectOpts), P,
+        L.raftgp_select_bisect.argtypes = [C.POINTER(Csr), P, C.c_int32, C.c_int32, C.POINTER(BisectOpts), P, P,
                                            C.POINTER(C.c_int32), P, C.c_size_t, P]
+        L.raftgp_select_bisect_update.restype = C.c_int
+        L.raftgp_select_bisect_update.argtypes = [C.POINTER(Csr), P, C.c_int32, C.c_int32, C.POINTER(BisectOpts), P,
+                                                  C.c_int32, P, P, P, P, C.POINTER(C.c_int32), P, C.c_size_t, P]
         L.raftgp_lloyd_workspace_size.restype = C.c_size_t
         L.raftgp_lloyd_workspace_size.argtypes = [C.c_int64, C.c_int32, C.c_int32]
         L.raftgp_sbm_workspace_size.restype = C.c_size_t

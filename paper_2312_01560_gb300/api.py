@@ -449,22 +449,55 @@ class BatchPlan:
 READING = {"literal": 0, "global": 1}
 
 
-def select_bisect(g: DeviceGraph, Z: torch.Tensor, eps=5, iters=50, reading="literal", seed=2, stream=None):
-    """Algorithm 1 (recursive bisection by local modularity): returns (labels int32[N], K)."""
-    n, d = Z.shape
-    code = 1 if Z.dtype == torch.bfloat16 else 0
+def _bisect_opts(eps, iters, reading, seed):
     o = _abi.BisectOpts()
     o.eps, o.iters, o.seed = int(eps), int(iters), int(seed)
     o.reading = READING[reading] if isinstance(reading, str) else int(reading)
+    return o
+
+
+def select_bisect(g: DeviceGraph, Z: torch.Tensor, eps=5, iters=50, reading="literal", seed=2, stream=None,
+                  return_leaf=False):
+    """Algorithm 1 (recursive bisection by local modularity): returns (labels int32[N], K), and
+    the leaf ids (uint64 tree node of each node's block, as int64) with return_leaf."""
+    n, d = Z.shape
+    code = 1 if Z.dtype == torch.bfloat16 else 0
+    o = _bisect_opts(eps, iters, reading, seed)
     Zc = Z.contiguous()
     labels = torch.empty(n, dtype=torch.int32, device=Z.device)
+    leaf = torch.empty(n, dtype=torch.int64, device=Z.device)
     ws = _workspace(int(lib().raftgp_bisect_workspace_size(n, d, int(eps))), Z.device)
     k = C.c_int32(0)
     csr = g.csr()
     check(lib().raftgp_select_bisect(C.byref(csr), C.c_void_p(Zc.data_ptr()), d, code, C.byref(o),
-                                     C.c_void_p(labels.data_ptr()), C.byref(k), C.c_void_p(ws.data_ptr()),
-                                     ws.numel(), _stream(stream)))
-    return labels, k.value
+                                     C.c_void_p(labels.data_ptr()), C.c_void_p(leaf.data_ptr()), C.byref(k),
+                                     C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return (labels, k.value, leaf) if return_leaf else (labels, k.value)
+
+
+def select_bisect_update(g: DeviceGraph, Z: torch.Tensor, old_labels: torch.Tensor, old_k: int, old_leaf: torch.Tensor,
+                         changed: torch.Tensor, eps=5, iters=50, reading="literal", seed=2, stream=None):
+    """Streaming update of Algorithm 1 (Section III-D) on the new graph and embedding, reusing
+    the previous tree where no node changed: returns (labels, K, leaf ids)."""
+    n, d = Z.shape
+    code = 1 if Z.dtype == torch.bfloat16 else 0
+    o = _bisect_opts(eps, iters, reading, seed)
+    Zc = Z.contiguous()
+    dev = Z.device
+    old_labels = old_labels.to(dev, torch.int32).contiguous()
+    old_leaf = old_leaf.to(dev, torch.int64).contiguous()
+    changed = changed.to(dev, torch.uint8).contiguous()
+    labels = torch.empty(n, dtype=torch.int32, device=dev)
+    leaf = torch.empty(n, dtype=torch.int64, device=dev)
+    ws = _workspace(int(lib().raftgp_bisect_workspace_size(n, d, int(eps))), dev)
+    k = C.c_int32(0)
+    csr = g.csr()
+    check(lib().raftgp_select_bisect_update(C.byref(csr), C.c_void_p(Zc.data_ptr()), d, code, C.byref(o),
+                                            C.c_void_p(old_labels.data_ptr()), int(old_k),
+                                            C.c_void_p(old_leaf.data_ptr()), C.c_void_p(changed.data_ptr()),
+                                            C.c_void_p(labels.data_ptr()), C.c_void_p(leaf.data_ptr()), C.byref(k),
+                                            C.c_void_p(ws.data_ptr()), ws.numel(), _stream(stream)))
+    return labels, k.value, leaf
 
 
 # ---- Algorithm 2: graphs from the SBM of Definition 1 (argument marshalling only) ----

@@ -1256,9 +1256,13 @@ BisectDev carve_bisect(Carver& c, int64_t n, int d, int eps) {
     b.acc = c.take<unsigned long long>(5 * cap);
     b.scan_in = c.take<unsigned long long>(3 * cap);
     b.scan_out = c.take<unsigned long long>(3 * cap);
-    b.bmin = c.take<int32_t>(n);
+    b.bmin = c.take<int32_t>(n + cap);   // block indices: the previous run's (up to n) + this run's
     b.counters = c.take<int>(64);
     b.counters_ll = c.take<long long>(8);
+    b.set_keep = c.take<int32_t>(cap);
+    b.nset_keep = c.take<int32_t>(cap);
+    b.frozen = c.take<int32_t>(cap);
+    b.flag = c.take<int32_t>(cap);
     return b;
 }
 
@@ -1280,9 +1284,10 @@ size_t raftgp_bisect_workspace_size(int64_t n, int32_t d, int32_t eps) {
     return c.off + 256;
 }
 
-raftgp_status raftgp_select_bisect(const raftgp_csr* g, const void* Z, int32_t d, int32_t z_dtype,
-                                   const raftgp_bisect_opts* o, int32_t* labels, int32_t* k_out, void* ws,
-                                   size_t ws_bytes, raftgp_stream_t stream) {
+static raftgp_status bisect_common(const raftgp_csr* g, const void* Z, int32_t d, int32_t z_dtype,
+                                   const raftgp_bisect_opts* o, const int32_t* old_labels, int32_t old_k,
+                                   const uint64_t* old_leaf, const uint8_t* dirty, int32_t* labels, uint64_t* leaf,
+                                   int32_t* k_out, void* ws, size_t ws_bytes, cudaStream_t s) {
     raftgp_status st = check_csr(g);
     if (st) return st;
     if ((uintptr_t)Z & 15) return fail(RAFTGP_EINVAL, "Z must be 16-byte aligned");
@@ -1292,14 +1297,20 @@ raftgp_status raftgp_select_bisect(const raftgp_csr* g, const void* Z, int32_t d
     if (o->eps < 1) return fail(RAFTGP_EINVAL, "eps must be >= 1");
     if (o->iters < 1) return fail(RAFTGP_EINVAL, "iters must be >= 1");
     if (o->reading != 0 && o->reading != 1) return fail(RAFTGP_EINVAL, "reading must be 0 or 1");
+    if (dirty && (!old_labels || !old_leaf || old_k < 1 || old_k > g->n))
+        return fail(RAFTGP_EINVAL, "the update needs the previous labels (1 <= old_k <= n) and leaf ids");
     if (ws_bytes < raftgp_bisect_workspace_size(g->n, d, o->eps)) return fail(RAFTGP_ENOMEM, "workspace too small");
-    cudaStream_t s = (cudaStream_t)stream;
     Carver c(ws);
     uint32_t* err = c.take<uint32_t>(64);
     int32_t* deg = c.take<int32_t>(g->n);
     float* rs = c.take<float>(g->n);
     float* rsh = c.take<float>(g->n);
     BisectDev b = carve_bisect(c, g->n, d, o->eps);
+    b.leaf_of = leaf;
+    b.old_label = old_labels;
+    b.old_leaf = old_leaf;
+    b.dirty = dirty;
+    b.k_old = dirty ? old_k : 0;
     cudaMemsetAsync(err, 0, sizeof(uint32_t), s);
     launch_degrees(g, deg, rs, rsh, err, nullptr, nullptr, s);
     if ((st = read_error_word(err, s))) return st;
@@ -1307,6 +1318,23 @@ raftgp_status raftgp_select_bisect(const raftgp_csr* g, const void* Z, int32_t d
     cudaError_t e = launch_bisect(g, Z, z_dtype, d, b, o->iters, o->seed, o->reading, labels, k_out, s);
     if (e != cudaSuccess) return cuda_fail(e, "bisect");
     return RAFTGP_OK;
+}
+
+raftgp_status raftgp_select_bisect(const raftgp_csr* g, const void* Z, int32_t d, int32_t z_dtype,
+                                   const raftgp_bisect_opts* o, int32_t* labels, uint64_t* leaf, int32_t* k_out,
+                                   void* ws, size_t ws_bytes, raftgp_stream_t stream) {
+    return bisect_common(g, Z, d, z_dtype, o, nullptr, 0, nullptr, nullptr, labels, leaf, k_out, ws, ws_bytes,
+                         (cudaStream_t)stream);
+}
+
+raftgp_status raftgp_select_bisect_update(const raftgp_csr* g, const void* Z, int32_t d, int32_t z_dtype,
+                                          const raftgp_bisect_opts* o, const int32_t* old_labels, int32_t old_k,
+                                          const uint64_t* old_leaf, const uint8_t* changed, int32_t* labels,
+                                          uint64_t* leaf, int32_t* k_out, void* ws, size_t ws_bytes,
+                                          raftgp_stream_t stream) {
+    if (!changed) return fail(RAFTGP_EINVAL, "changed is NULL");
+    return bisect_common(g, Z, d, z_dtype, o, old_labels, old_k, old_leaf, changed, labels, leaf, k_out, ws,
+                         ws_bytes, (cudaStream_t)stream);
 }
 
 // ---- Algorithm 2 sampler and the CSR build ----

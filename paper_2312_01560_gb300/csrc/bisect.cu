@@ -18,6 +18,18 @@
 // Sets of at most 2 eps + 1 nodes are blocks without k-means (one half would have at most eps
 // nodes), and so is a set at depth 62.  At the end the blocks are numbered by their smallest
 // node index.
+//
+// Streaming update (Section III-D: "update only a tree path" once embeddings change).  Given
+// the previous run's labels and per-node leaf ids (the tree id of each node's block) and the
+// nodes whose embedding or degree changed, a set is kept as the previous tree node when it is
+// that node (every ancestor split exactly as before) and holds no changed node: its old
+// subtree's blocks are reused without any k-means.  A set holding a changed node is
+// partitioned again; if its new decision and every node's side equal the old ones, its
+// children may be kept in turn, otherwise its subtree is rebuilt.  With 2e the G-degree sum of
+// U (the literal reading) a kept subtree's inputs (its nodes' embeddings, degrees and inner
+// edges, and its tree ids) are those of the previous run, so the result equals a full run on
+// the new graph; with the global reading every decision also depends on |E|, which a new edge
+// changes, and the kept subtrees are the paper's path-update approximation.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -140,7 +152,35 @@ __global__ void k_bs_seed0(BisectDev b, int S, uint64_t seed) {
         b.s0[s] = b.set_off[s] + (int64_t)mulhi64(bs_draw(seed, 0, b.set_id[s]), (uint64_t)b.set_n[s]);
         b.changed[s] = 0;
         b.changed[b.cap_sets + s] = 0;
-        b.active[s] = bs_small(b, s) ? 0 : 1;
+        // streaming update: the previous tree node without a changed node keeps its subtree
+        const int fz = b.dirty ? (b.set_keep[s] && b.flag[s] == 0) : 0;
+        b.frozen[s] = fz;
+        if (b.dirty) b.flag[s] = 0;   // reused below for "the split changed"
+        b.active[s] = (bs_small(b, s) || fz) ? 0 : 1;
+    }
+}
+
+// Streaming update: flag the kept sets that hold a changed node.
+__global__ void k_bs_dirty(BisectDev b, int64_t M) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < M; p += (int64_t)gridDim.x * blockDim.x) {
+        const int s = b.pos_set[p];
+        if (b.set_keep[s] && b.dirty[b.perm[p]]) b.flag[s] = 1;
+    }
+}
+
+// Streaming update: does a kept, re-partitioned set split as before?  The old side of node i
+// under the set's tree id u is the bit below u on the path to i's old leaf; a set that was a
+// leaf before (old leaf == u) and splits now has changed too.
+__device__ __forceinline__ int bs_bitlen(uint64_t x) { return 64 - __clzll((long long)x); }
+__global__ void k_bs_sides(BisectDev b, int64_t M) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < M; p += (int64_t)gridDim.x * blockDim.x) {
+        const int s = b.pos_set[p];
+        if (!b.set_keep[s] || b.frozen[s] || !b.split[s]) continue;
+        const uint64_t u = b.set_id[s], leaf = b.old_leaf[b.perm[p]];
+        const int lu = bs_bitlen(u), ll = bs_bitlen(leaf);
+        bool same = false;
+        if (ll > lu && (leaf >> (ll - lu)) == u) same = (int)((leaf >> (ll - lu - 1)) & 1ull) == (int)b.lab[p];
+        if (!same) b.flag[s] = 1;
     }
 }
 
@@ -364,7 +404,7 @@ __global__ void __launch_bounds__(256) k_bs_lmod(BisectDev b, Csr<OffT> g, int64
 __global__ void k_bs_decide(BisectDev b, int S, int64_t two_e_global) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < S; s += gridDim.x * blockDim.x) {
         int split = 0;
-        if (!bs_small(b, s)) {
+        if (!bs_small(b, s) && !b.frozen[s]) {
             const long long n0 = b.counts[s * 2], n1 = b.counts[s * 2 + 1];
             const unsigned long long* a = b.acc + (int64_t)s * 5;
             const long long mU = (long long)(a[0] / 2), m0 = (long long)(a[1] / 2), m1c = (long long)(a[2] / 2);
@@ -397,6 +437,11 @@ __global__ void k_bs_emit(BisectDev b, int S, int block_base) {
             b.nset_n[c1] = b.set_n[s] - n0;
             b.nset_id[c1] = b.set_id[s] * 2 + 1;
             b.child_pos[s] = (int64_t)pos;
+            if (b.dirty) {
+                const int keep = b.set_keep[s] && !b.flag[s];   // split exactly as before
+                b.nset_keep[c0] = keep;
+                b.nset_keep[c1] = keep;
+            }
         } else {
             b.block_id[s] = block_base + (int)(b.scan_out[2 * (int64_t)b.cap_sets + s] - 1);
         }
@@ -424,8 +469,14 @@ __global__ void k_bs_scatter(BisectDev b, int64_t M, int64_t n) {
             else np = b.child_pos[s] + n0 + ((p - off + 1) - zeros_upto) - 1;
             if (np >= 0 && np < n) b.perm_next[np] = node;
             else atomicAdd(b.counters + 2, 1);       // inconsistent counts: reported, never written
+        } else if (b.frozen[s]) {
+            // a kept subtree: the node stays in its previous block
+            b.block_of[node] = b.old_label[node];
+            if (b.leaf_of) b.leaf_of[node] = b.old_leaf[node];
+            b.node_set[node] = -1;
         } else {
-            b.block_of[node] = b.block_id[s];
+            b.block_of[node] = b.k_old + b.block_id[s];
+            if (b.leaf_of) b.leaf_of[node] = b.set_id[s];
             b.node_set[node] = -1;
         }
     }
@@ -480,12 +531,21 @@ static cudaError_t bisect_t(const raftgp_csr* g, const T* Z, BisectDev b, int it
         cudaMemcpyAsync(b.set_id, &id1, sizeof(uint64_t), cudaMemcpyHostToDevice, s);
         cudaStreamSynchronize(s);
     }
+    if (b.dirty) {
+        const int32_t one = 1;
+        cudaMemcpyAsync(b.set_keep, &one, sizeof(int32_t), cudaMemcpyHostToDevice, s);   // the root is the old root
+        cudaStreamSynchronize(s);
+    }
     const int64_t two_e_global = reading == 1 ? g->nnz : 0;
     Csr<int64_t> c64{g->n, g->nnz, (const int64_t*)g->row_ptr, g->col};
     Csr<int32_t> c32{g->n, g->nnz, (const int32_t*)g->row_ptr, g->col};
     for (int depth = 0; S > 0; ++depth) {
         b.depth = depth;
         k_bs_setup<<<S < 65535 ? S : 65535, 256, 0, s>>>(b, S);
+        if (b.dirty) {
+            cudaMemsetAsync(b.flag, 0, sizeof(int32_t) * (size_t)S, s);
+            k_bs_dirty<<<grid1(M), 256, 0, s>>>(b, M);
+        }
         k_bs_seed0<<<grid1(S), 256, 0, s>>>(b, S, seed);
         k_bs_d2<T, D><<<grid1(M), 256, 0, s>>>(b, Z, M);
         scan_incl(b.q, M, b.P, b.tiles, s);
@@ -499,6 +559,7 @@ static cudaError_t bisect_t(const raftgp_csr* g, const T* Z, BisectDev b, int it
         if (g->row_ptr_bits == 64) k_bs_lmod<int64_t><<<grid1(M), 256, 0, s>>>(b, c64, M);
         else k_bs_lmod<int32_t><<<grid1(M), 256, 0, s>>>(b, c32, M);
         k_bs_decide<<<grid1(S), 256, 0, s>>>(b, S, two_e_global);
+        if (b.dirty) k_bs_sides<<<grid1(M), 256, 0, s>>>(b, M);
         for (int part = 0; part < 3; ++part)
             scan_incl(b.scan_in + (int64_t)part * b.cap_sets, S, b.scan_out + (int64_t)part * b.cap_sets, b.tiles, s);
         k_bs_emit<<<grid1(S), 256, 0, s>>>(b, S, block_base);
@@ -519,16 +580,22 @@ static cudaError_t bisect_t(const raftgp_csr* g, const T* Z, BisectDev b, int it
         std::swap(b.set_off, b.nset_off);
         std::swap(b.set_n, b.nset_n);
         std::swap(b.set_id, b.nset_id);
+        std::swap(b.set_keep, b.nset_keep);
     }
-    // numbering by smallest node
-    const int nb = block_base;
+    // numbering by smallest node (block indices: the previous run's for kept subtrees, then
+    // this run's new blocks)
+    const int nb = b.k_old + block_base;
     cudaMemsetAsync(b.bmin, 0x7f, sizeof(int) * (size_t)nb, s);
     k_bs_min<<<grid1(n), 256, 0, s>>>(b, n);
     k_bs_mark<<<grid1(n), 256, 0, s>>>(b, nb, n);
     k_bs_mark2<<<grid1(nb), 256, 0, s>>>(b, nb, n);
     scan_incl(b.q, n, b.P, b.tiles, s);
     k_bs_label<<<grid1(n), 256, 0, s>>>(b, n, labels);
-    *k_out = nb;
+    unsigned long long blocks = 0;   // the blocks that hold nodes (kept subtrees may leave gaps)
+    cudaMemcpyAsync(&blocks, b.P + (n - 1), sizeof(blocks), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    *k_out = (int32_t)blocks;
     return cudaGetLastError();
 }
 

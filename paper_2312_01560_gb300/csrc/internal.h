@@ -279,6 +279,18 @@ struct BisectDev {
     int32_t* bmin;
     int* counters;
     long long* counters_ll;
+    // tree ids of the final blocks (per node; may be null) and the streaming update's inputs:
+    // the previous run's labels (k_old blocks) and leaf ids, and the nodes whose embedding or
+    // degree changed (null in a full run)
+    uint64_t* leaf_of;
+    const int32_t* old_label;
+    const uint64_t* old_leaf;
+    const uint8_t* dirty;
+    int k_old;
+    // per set (current / next level): the set is the previous tree's node of the same id and
+    // every ancestor split as before (1), or it is new (0); frozen: kept with its old subtree;
+    // flag: a changed node inside (before the decision) or a changed split (after it)
+    int32_t *set_keep, *nset_keep, *frozen, *flag;
 };
 cudaError_t launch_bisect(const raftgp_csr* g, const void* Z, int zdtype, int d, BisectDev b, int iters, uint64_t seed,
                           int reading, int32_t* labels, int32_t* k_out, cudaStream_t s);
