@@ -308,6 +308,8 @@ typedef struct {
     int32_t criterion;     /* RAFTGP_CRIT_MOD or RAFTGP_CRIT_NCUT */
     int32_t lloyd_variant; /* 0: autotune the Lloyd kernel; v in 1..7: use variant v - 1 of the
                               list raftgp_batch_plan_tuning reports (no timing) */
+    int32_t embed_variant; /* BF16 embeddings: 0 autotunes the gathers' shape; v in 1..4 uses
+                              shape v - 1 of raftgp_batch_plan_tuning_embed's list (no timing) */
     int32_t assign;        /* RAFTGP_ASSIGN_FFMA (default): the FP32 Lloyd kernels above, each
                               graph's result equal to a single-graph FP32 partition;
                               RAFTGP_ASSIGN_TC8 / RAFTGP_ASSIGN_TC: tensor-core Lloyd (BF16
@@ -345,6 +347,11 @@ raftgp_status raftgp_batch_plan_candidates(raftgp_batch_plan* plan, int32_t* k, 
  * Every variant computes the same labels. */
 raftgp_status raftgp_batch_plan_tuning(const raftgp_batch_plan* plan, int32_t* threads, int32_t* points_per_thread,
                                        float* ms);
+/* The autotuner's choice for the BF16 embedding's gathers and its measured times (ms of one
+ * embedding of the batch) for the four flat-stream shapes: {16, 32} entries per batch (at
+ * width 128) x {2, 3} staging buffers, variant = 2 (batch 32) + (3 buffers); every shape gives
+ * the same bits.  FP32 embeddings: variant 0 and times 0 (not tuned). */
+raftgp_status raftgp_batch_plan_tuning_embed(const raftgp_batch_plan* plan, int32_t* variant, float* ms);
 /* Waits for the device to finish and reports the last replay's device-side status: RAFTGP_OK,
  * or RAFTGP_ETIMEOUT if a bounded wait inside a kernel gave up (the labels are then
  * incomplete).  Synchronises. */

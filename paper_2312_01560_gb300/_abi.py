@@ -27,6 +27,7 @@ EXPORTS = ("raftgp_workspace_size", "raftgp_embed", "raftgp_select", "raftgp_par
            "raftgp_version", "raftgp_diff_workspace_size", "raftgp_gcn_layer_forward", "raftgp_gcn_layer_backward",
            "raftgp_softmod_loss", "raftgp_centroids", "raftgp_gcn_weights", "raftgp_adam_step",
            "raftgp_batch_workspace_size", "raftgp_batch_plan_create", "raftgp_batch_plan_run", "raftgp_batch_plan_embedding", "raftgp_batch_plan_check",
+           "raftgp_batch_plan_tuning_embed",
            "raftgp_batch_plan_candidates", "raftgp_batch_plan_tuning", "raftgp_batch_plan_destroy",
            "raftgp_partition_batched", "raftgp_bisect_workspace_size", "raftgp_select_bisect",
            "raftgp_select_bisect_update",
@@ -58,7 +59,8 @@ class Sbm(C.Structure):
 
 class BatchOpts(C.Structure):
     _fields_ = [("kmin", C.c_int32), ("kmax_factor", C.c_float), ("grid", C.c_int32), ("iters", C.c_int32),
-                ("criterion", C.c_int32), ("lloyd_variant", C.c_int32), ("assign", C.c_int32),
+                ("criterion", C.c_int32), ("lloyd_variant", C.c_int32), ("embed_variant", C.c_int32),
+                ("assign", C.c_int32),
                 ("seed", C.c_uint64)]
 
 
@@ -143,6 +145,8 @@ def lib():
         L.raftgp_batch_plan_run.argtypes = [C.c_void_p, P]
         L.raftgp_batch_plan_embedding.argtypes = [C.c_void_p, P]
         L.raftgp_batch_plan_check.argtypes = [C.c_void_p]
+        L.raftgp_batch_plan_tuning_embed.argtypes = [C.c_void_p, C.POINTER(C.c_int32), P]
+        L.raftgp_batch_plan_tuning_embed.restype = C.c_int
         L.raftgp_batch_plan_candidates.argtypes = [C.c_void_p, P, P, P, P]
         L.raftgp_batch_plan_tuning.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                                C.POINTER(C.c_float)]

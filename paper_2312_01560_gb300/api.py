@@ -358,11 +358,13 @@ def concat_graphs(graphs, device, row_ptr_bits=64):
     return dg, np.asarray(offs, dtype=np.int64)
 
 
-def batch_opts(kmin=2, kmax_factor=2.0, grid=10, iters=50, criterion="mod", seed=2, lloyd_variant=0, assign="ffma"):
+def batch_opts(kmin=2, kmax_factor=2.0, grid=10, iters=50, criterion="mod", seed=2, lloyd_variant=0, assign="ffma",
+               embed_variant=0):
     o = _abi.BatchOpts()
     o.kmin, o.kmax_factor, o.grid, o.iters = int(kmin), float(kmax_factor), int(grid), int(iters)
     o.criterion = _abi.CRIT[criterion] if isinstance(criterion, str) else int(criterion)
     o.lloyd_variant = int(lloyd_variant)
+    o.embed_variant = int(embed_variant)
     o.assign = _code(_abi.ASSIGN, assign)
     o.seed = int(seed)
     return o
@@ -420,7 +422,11 @@ class BatchPlan:
         th, pp = C.c_int32(), C.c_int32()
         ms = (C.c_float * 7)()
         check(lib().raftgp_batch_plan_tuning(self._h, C.byref(th), C.byref(pp), ms))
-        return {"threads": th.value, "points_per_thread": pp.value, "ms": list(ms)}
+        fv = C.c_int32()
+        fms = (C.c_float * 4)()
+        check(lib().raftgp_batch_plan_tuning_embed(self._h, C.byref(fv), fms))
+        return {"threads": th.value, "points_per_thread": pp.value, "ms": list(ms),
+                "embed_gather_variant": fv.value, "embed_gather_ms": list(fms)}
 
     def check(self):
         """Synchronises and raises if a bounded device wait of the last replay gave up."""

@@ -104,6 +104,7 @@ struct EmbedWs {
     void* bufA;
     void* bufB;
     const int32_t* local_row;   // many graphs in one CSR: each node's index inside its graph
+    int flat_variant;           // shape of the BF16 flat-stream gathers (0: the default)
 };
 
 static int embed_maxw(const raftgp_embed_opts* o) {
@@ -248,7 +249,7 @@ static raftgp_status run_embed(const raftgp_csr* g, const raftgp_embed_opts* o, 
     if (o->n_layers == 0) {
         if (flat0)
             e = launch_spmm_flat(agg0, n, g->row_ptr_bits, g->row_ptr, g->col, g->nnz, w.deg, w.rs, w.gvec, 2, L,
-                                 w.bufB, Z, o->stage_out[0], w.work, w.err, s);
+                                 w.bufB, Z, o->stage_out[0], w.work, w.err, w.flat_variant, s);
         else
             e = launch_layer(agg0, o->dtype, g, w.deg, w.rs, w.gvec, 2, nullptr, L, L, nullptr, w.bufB, Z,
                              o->stage_out[0], w.heavy, w.heavy_count, s);
@@ -264,7 +265,7 @@ static raftgp_status run_embed(const raftgp_csr* g, const raftgp_embed_opts* o, 
         launch_self_csr(g, w.rp_self, w.col_self, s);
         if (flat0)
             e = launch_spmm_flat(agg0, n, g->row_ptr_bits, g->row_ptr, g->col, g->nnz, w.deg, w.rs, w.gvec, 0, L,
-                                 w.bufB, w.bufA, o->stage_out[0], w.work, w.err, s);
+                                 w.bufB, w.bufA, o->stage_out[0], w.work, w.err, w.flat_variant, s);
         else
             e = launch_layer(agg0, o->dtype, g, w.deg, w.rs, w.gvec, 0, nullptr, L, L, nullptr, w.bufB, w.bufA,
                              o->stage_out[0], w.heavy, w.heavy_count, s);
@@ -275,7 +276,7 @@ static raftgp_status run_embed(const raftgp_csr* g, const raftgp_embed_opts* o, 
             const bool last = k == o->n_layers;
             if (spmm_flat_supported(AGG_GCN_, o->dtype, o->dims[k]))
                 e = launch_spmm_flat(AGG_GCN_, n, 64, w.rp_self, w.col_self, g->nnz, w.deg, w.rsh, nullptr, 1,
-                                     o->dims[k], w.bufB, last ? Z : w.bufA, o->stage_out[k], w.work + k, w.err, s);
+                                     o->dims[k], w.bufB, last ? Z : w.bufA, o->stage_out[k], w.work + k, w.err, w.flat_variant, s);
             else
                 e = launch_layer(AGG_GCN_, o->dtype, g, w.deg, w.rsh, nullptr, 1, nullptr, o->dims[k], o->dims[k],
                                  nullptr, w.bufB, last ? Z : w.bufA, o->stage_out[k], w.heavy, w.heavy_count, s);
@@ -930,6 +931,7 @@ struct raftgp_batch_plan {
     int threads = 256, ppt = 1;
     float tune_ms[7] = {};
     void* stg = nullptr;   // tensor-core Lloyd: staging of the centroid operands
+    float flat_ms[4] = {};  // BF16 embedding: one embedding per flat-stream gather shape
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;   // the plan's own stream, on which the graph is captured
@@ -952,6 +954,7 @@ raftgp_status batch_layout(const raftgp_csr* g, const int64_t* off, int ng, cons
     if (bo->iters < 1) return fail(RAFTGP_EINVAL, "iters must be >= 1");
     if (!(bo->kmax_factor > 0.f)) return fail(RAFTGP_EINVAL, "kmax_factor must be positive");
     if (bo->lloyd_variant < 0 || bo->lloyd_variant > 7) return fail(RAFTGP_EINVAL, "lloyd_variant must be in [0, 7]");
+    if (bo->embed_variant < 0 || bo->embed_variant > 4) return fail(RAFTGP_EINVAL, "embed_variant must be in [0, 4]");
     if (bo->assign < RAFTGP_ASSIGN_FFMA || bo->assign > RAFTGP_ASSIGN_TC8) return fail(RAFTGP_EINVAL, "unknown assign engine");
     if (bo->assign != RAFTGP_ASSIGN_FFMA && eo->dtype != RAFTGP_BF16)
         return fail(RAFTGP_EINVAL, "tensor-core assignment needs BF16 embeddings");
@@ -1077,6 +1080,33 @@ raftgp_status raftgp_batch_plan_create(const raftgp_csr* g, const int64_t* graph
     launch_degrees(&p->g, p->ew.deg, p->ew.rs, p->ew.rsh, p->ew.err, p->ew.heavy, p->ew.heavy_count, s);
     launch_batch_check(&p->g, p->ng, b.node_off, p->ew.err, s);
     if ((st = read_error_word(p->ew.err, s))) return st;
+    // autotuning of the BF16 embedding's gathers: one embedding timed per flat-stream shape
+    // (batch size and staging depth; every shape gives the same bits)
+    if (p->eo.dtype == RAFTGP_BF16) {
+        cudaEvent_t f0, f1;
+        cudaEventCreate(&f0);
+        cudaEventCreate(&f1);
+        float fbest = INFINITY;
+        int fv = 0;
+        for (int v = 0; v < 4; ++v) {
+            if (p->bo.embed_variant > 0 && v != p->bo.embed_variant - 1) continue;   // a forced shape
+            p->ew.flat_variant = v;
+            cudaEventRecord(f0, s);
+            raftgp_status est = run_embed(&p->g, &p->eo, p->Z, p->ew, true, s);
+            cudaEventRecord(f1, s);
+            float ms = INFINITY;
+            if (est == RAFTGP_OK && cudaEventSynchronize(f1) == cudaSuccess) cudaEventElapsedTime(&ms, f0, f1);
+            p->flat_ms[v] = ms;
+            if (ms < fbest) {
+                fbest = ms;
+                fv = v;
+            }
+        }
+        cudaEventDestroy(f0);
+        cudaEventDestroy(f1);
+        p->ew.flat_variant = fv;
+        if (!(fbest < INFINITY)) return fail(RAFTGP_ECUDA, "no embedding gather shape could run");
+    }
     // autotuning: the coarse Lloyd phase timed for every variant on this batch (results are
     // the same for all of them)
     p->threads = 256;
@@ -1171,6 +1201,14 @@ raftgp_status raftgp_batch_plan_tuning(const raftgp_batch_plan* plan, int32_t* t
     if (points_per_thread) *points_per_thread = plan->ppt;
     if (ms)
         for (int v = 0; v < 7; ++v) ms[v] = plan->tune_ms[v];
+    return RAFTGP_OK;
+}
+
+raftgp_status raftgp_batch_plan_tuning_embed(const raftgp_batch_plan* plan, int32_t* variant, float* ms) {
+    if (!plan) return fail(RAFTGP_EINVAL, "plan is NULL");
+    if (variant) *variant = plan->ew.flat_variant;
+    if (ms)
+        for (int v = 0; v < 4; ++v) ms[v] = plan->flat_ms[v];
     return RAFTGP_OK;
 }
 

@@ -68,7 +68,8 @@ cudaError_t launch_layer(int agg, int dtype, const raftgp_csr* g, const int32_t*
 bool spmm_flat_supported(int agg, int dtype, int lin);
 cudaError_t launch_spmm_flat(int agg, int64_t n, int rp_bits, const void* row_ptr, const int32_t* col, int64_t nnz_g,
                              const int32_t* deg, const float* rowscale, const float* gvec, int act, int lin,
-                             const void* X, void* out, void* stage, int* work, uint32_t* err, cudaStream_t s);
+                             const void* X, void* out, void* stage, int* work, uint32_t* err, int variant,
+                             cudaStream_t s);
 // CSR of A + I (row i: i, then its neighbours): rp_self has n + 1 entries, col_self nnz + n.
 void launch_self_csr(const raftgp_csr* g, int64_t* rp_self, int32_t* col_self, cudaStream_t s);
 

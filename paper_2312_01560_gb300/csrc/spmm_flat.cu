@@ -165,22 +165,22 @@ __device__ __forceinline__ void cp_async_wait() {
 #endif
 constexpr int FL_WARPS = RAFTGP_FLAT_WARPS;   // warps per block
 
-template <int LIN>
+template <int LIN, int B128 = RAFTGP_FLAT_B128>
 struct FlCfg {
     static constexpr int E = 8;                 // BF16 elements per 16-byte lane chunk
     static constexpr int LPR = LIN / E;         // lanes per gathered row
     static constexpr int GPW = 32 / LPR;        // lane groups
-    static constexpr int B = LIN == 128 ? RAFTGP_FLAT_B128 : 32;   // entries per batch
+    static constexpr int B = LIN == 128 ? B128 : 32;   // entries per batch
     static constexpr int U = B / GPW;           // copies per lane per batch
     static constexpr int ROWB = LIN * 2;
     static constexpr int EG = E / GPW;          // columns each lane finishes
     static_assert(B <= 32 && B % GPW == 0 && E % GPW == 0, "lane layout");
 };
 
-template <int AGG, int LIN, int NBUF, bool G4>
+template <int AGG, int LIN, int NBUF, bool G4, int B128>
 __global__ void __launch_bounds__(FL_WARPS * 32) k_spmm_flat(FlatArgs a, const __nv_bfloat16* __restrict__ X,
                                                              const __grid_constant__ CUtensorMap tmX) {
-    using C = FlCfg<LIN>;
+    using C = FlCfg<LIN, B128>;
     constexpr int E = C::E, LPR = C::LPR, GPW = C::GPW, B = C::B, U = C::U, ROWB = C::ROWB, EG = C::EG;
     extern __shared__ __align__(1024) unsigned char fl_smem[];
     __shared__ uint64_t fl_bar[FL_WARPS][NBUF];
@@ -413,11 +413,11 @@ __global__ void k_self_csr(int64_t n, const int32_t* rp32, const int64_t* rp64, 
     }
 }
 
-template <int AGG, int LIN, int NBUF>
+template <int AGG, int LIN, int NBUF, int B128 = RAFTGP_FLAT_B128>
 cudaError_t launch_flat_t(const FlatArgs& a, const void* X, cudaStream_t s) {
-    using C = FlCfg<LIN>;
+    using C = FlCfg<LIN, B128>;
     constexpr bool G4 = RAFTGP_FLAT_G4 != 0;
-    auto kern = k_spmm_flat<AGG, LIN, NBUF, G4>;
+    auto kern = k_spmm_flat<AGG, LIN, NBUF, G4, B128>;
     const int smem = FL_WARPS * NBUF * C::B * C::ROWB;
     CUtensorMap tmX;
     memset(&tmX, 0, sizeof(tmX));
@@ -445,12 +445,23 @@ cudaError_t launch_flat_t(const FlatArgs& a, const void* X, cudaStream_t s) {
 #define RAFTGP_FLAT_NBUF 2
 #endif
 
+// Shape variants (the same sums in the same order, so the same bits): 0 = the default (16
+// entries per batch at width 128, two staging buffers), 1 = 16 entries and three buffers,
+// 2 = 32 entries and two buffers, 3 = 32 entries and three buffers.
 template <int AGG>
-cudaError_t launch_flat_w(const FlatArgs& a, int lin, const void* X, cudaStream_t s) {
+cudaError_t launch_flat_w(const FlatArgs& a, int lin, const void* X, int variant, cudaStream_t s) {
     switch (lin) {
-        case 32: return launch_flat_t<AGG, 32, RAFTGP_FLAT_NBUF>(a, X, s);
-        case 64: return launch_flat_t<AGG, 64, RAFTGP_FLAT_NBUF>(a, X, s);
-        case 128: return launch_flat_t<AGG, 128, RAFTGP_FLAT_NBUF>(a, X, s);
+        case 32:
+            return variant & 1 ? launch_flat_t<AGG, 32, 3>(a, X, s) : launch_flat_t<AGG, 32, RAFTGP_FLAT_NBUF>(a, X, s);
+        case 64:
+            return variant & 1 ? launch_flat_t<AGG, 64, 3>(a, X, s) : launch_flat_t<AGG, 64, RAFTGP_FLAT_NBUF>(a, X, s);
+        case 128:
+            switch (variant) {
+                case 1: return launch_flat_t<AGG, 128, 3, 16>(a, X, s);
+                case 2: return launch_flat_t<AGG, 128, 2, 32>(a, X, s);
+                case 3: return launch_flat_t<AGG, 128, 3, 32>(a, X, s);
+                default: return launch_flat_t<AGG, 128, RAFTGP_FLAT_NBUF>(a, X, s);
+            }
         default: return cudaErrorNotSupported;
     }
 }
@@ -477,7 +488,8 @@ void launch_self_csr(const raftgp_csr* g, int64_t* rp_self, int32_t* col_self, c
 
 cudaError_t launch_spmm_flat(int agg, int64_t n, int rp_bits, const void* row_ptr, const int32_t* col, int64_t nnz_g,
                              const int32_t* deg, const float* rowscale, const float* gvec, int act, int lin,
-                             const void* X, void* out, void* stage, int* work, uint32_t* err, cudaStream_t s) {
+                             const void* X, void* out, void* stage, int* work, uint32_t* err, int variant,
+                             cudaStream_t s) {
     FlatArgs a;
     a.n = n;
     a.rp32 = rp_bits == 32 ? (const int32_t*)row_ptr : nullptr;
@@ -494,9 +506,9 @@ cudaError_t launch_spmm_flat(int agg, int64_t n, int rp_bits, const void* row_pt
     a.err = err;
     if (n == 0) return cudaSuccess;
     switch (agg) {
-        case AGG_NCUT_: return launch_flat_w<AGG_NCUT_>(a, lin, X, s);
-        case AGG_MOD_FULL_: return launch_flat_w<AGG_MOD_FULL_>(a, lin, X, s);
-        case AGG_GCN_: return launch_flat_w<AGG_GCN_>(a, lin, X, s);
+        case AGG_NCUT_: return launch_flat_w<AGG_NCUT_>(a, lin, X, variant, s);
+        case AGG_MOD_FULL_: return launch_flat_w<AGG_MOD_FULL_>(a, lin, X, variant, s);
+        case AGG_GCN_: return launch_flat_w<AGG_GCN_>(a, lin, X, variant, s);
         default: return cudaErrorNotSupported;
     }
 }

@@ -213,3 +213,32 @@ def test_tensor_core_batch_needs_bf16(cuda, batch):
     dg, off = api.concat_graphs(batch[:2], cuda)
     with pytest.raises(api._abi.RaftgpError, match="BF16"):
         api.BatchPlan(dg, off, dims=DIMS, dtype="f32", assign="tc8")
+
+
+def test_every_embedding_gather_shape_gives_the_same_embedding(cuda, batch):
+    # the autotuner's four flat-stream gather shapes (entries per batch, staging depth) change
+    # only speed: the batch's BF16 embedding is the same bits for each, and equals every
+    # graph's single-graph BF16 embedding
+    dg, off = api.concat_graphs(batch[:4], cuda)
+    dims = (128, 128, 64)
+    ref = None
+    for v in range(1, 5):
+        plan = api.BatchPlan(dg, off, dims=dims, dtype="bf16", kmin=2, grid=10, iters=3, seed=2, embed_variant=v)
+        plan.run()
+        plan.check()
+        Z = plan.embedding()
+        assert plan.tuning()["embed_gather_variant"] == v - 1
+        plan.close()
+        if ref is None:
+            ref = Z
+        else:
+            assert torch.equal(Z.view(torch.int16), ref.view(torch.int16)), v
+    for gi, g in enumerate(batch[:4]):
+        one = api.DeviceGraph.from_host(g, cuda)
+        Zg = api.embed(one, "ncut", dims, "bf16", seed=1)
+        assert torch.equal(Zg.view(torch.int16), ref[off[gi]:off[gi + 1]].view(torch.int16)), gi
+    plan = api.BatchPlan(dg, off, dims=dims, dtype="bf16", kmin=2, grid=10, iters=3, seed=2)
+    t = plan.tuning()
+    print(f"embedding gather tuning: {t['embed_gather_variant']} {t['embed_gather_ms']}")
+    assert 0 <= t["embed_gather_variant"] <= 3 and all(m > 0 for m in t["embed_gather_ms"])
+    plan.close()
