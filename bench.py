@@ -185,7 +185,7 @@ def roofline(full, timed, dom, g, wl, elem, cands, steps):
 # ----------------------------------------------------------------------------------------
 # the oracle on a bounded sample (CPU baseline and the reference arm)
 # ----------------------------------------------------------------------------------------
-def oracle_sample(g, wl, cand_ks, rng_seed=0, rows=64, seed_rounds=4, lloyd_points=1500):
+def oracle_sample(g, wl, cand_ks, rng_seed=0, rows=4096, seed_rounds=128, lloyd_points=48000):
     """Times every oracle stage on a bounded sample at full-graph context and scales each to
     the whole workload: embedding rows (projection + GCN layers) x N, the rank-one term's
     Theta draw x N, k-means++ rounds x
@@ -209,20 +209,22 @@ def oracle_sample(g, wl, cand_ks, rng_seed=0, rows=64, seed_rounds=4, lloyd_poin
         oracle.theta(big, L, 1)
         t_rank1 = (time.perf_counter() - t0) / big.shape[0] * n
     t_gcn = 0.0
+    Zall = rng.standard_normal((n, max(dims)), dtype=np.float32)   # stand-in layer inputs (values do not matter)
     for k in range(1, len(dims)):
-        Zin = rng.normal(size=(n, dims[k - 1])).astype(np.float32)
+        Zin = np.ascontiguousarray(Zall[:, :dims[k - 1]])
         W = oracle.gcn_weight(k, dims[k - 1], dims[k], 1)
         t0 = time.perf_counter()
         oracle.gcn_rows(g, Zin, W, sample)
         t_gcn += time.perf_counter() - t0
         del Zin
-    Zs = rng.normal(size=(n, d))
+    del Zall
+    Zs = rng.standard_normal((n, d))
     Zs /= np.linalg.norm(Zs, axis=1, keepdims=True)
     t0 = time.perf_counter()
     oracle.kmeanspp(Zs, seed_rounds + 1, 2)
     t_seed = (time.perf_counter() - t0) / seed_rounds
     kmax = max(cand_ks)
-    pts = Zs[rng.choice(n, lloyd_points, replace=False)]
+    pts = Zs[rng.choice(n, min(lloyd_points, n), replace=False)]
     t0 = time.perf_counter()
     oracle.lloyd(pts, pts[:kmax].copy(), 1)
     t_pair = (time.perf_counter() - t0) / (lloyd_points * kmax)
@@ -698,7 +700,7 @@ def main():
         cands, same = reference_candidates(wl, g)
         threads = oracle.set_threads(0)
         for _ in range(args.warmup):
-            oracle_sample(g, wl, cands, rows=16, seed_rounds=1, lloyd_points=200)
+            oracle_sample(g, wl, cands, rows=64, seed_rounds=2, lloyd_points=1000)
         vals, spent_all, desc = [], 0.0, ""
         t0 = time.perf_counter()
         for s in range(args.steps):
