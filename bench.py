@@ -551,8 +551,9 @@ def bench_batched(args):
     t0 = time.perf_counter()
     assign = args.batch_assign or "tc8"
     dtype = args.batch_dtype or ("bf16" if assign != "ffma" else wl["dtype"])
+    op = args.batch_op or "ncut"
     plan = api.BatchPlan(dg, off, dims=wl["dims"], dtype=dtype, kmin=wl["kmin"], kmax_factor=wl["kmax_factor"],
-                         grid=wl["grid"], iters=wl["iters"], seed=2, assign=assign)
+                         grid=wl["grid"], iters=wl["iters"], seed=2, assign=assign, op=op)
     torch.cuda.synchronize()
     plan_s = time.perf_counter() - t0
     for _ in range(max(args.warmup, 1)):
@@ -583,12 +584,14 @@ def bench_batched(args):
             "unit": "edges/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "dtype": dtype, "data": "synthetic",
             "config": {"workload": "512 DC-SBM graphs, N log-uniform in [1000, 50000], K = round(N^0.35), exponent "
-                                   "2.5, mean degree U[10, 30], ratio U[2, 6]; NCut operator, GNN 128-128-64, "
+                                   "2.5, mean degree U[10, 30], ratio U[2, 6]; "
+                                   + ("NCut operator" if op == "ncut" else "full modularity operator (a rank-one "
+                                      "term per graph)") + ", GNN 128-128-64, "
                                    "K in [2, ceil(2 N^0.35)] (10 coarse + 10 refined), <=50 Lloyd passes; "
                                    "one captured plan",
                        "graphs": len(graphs), "nodes": int(off[-1]), "edges": edges},
             "graphs_per_s": len(graphs) / (ms * 1e-3), "plan_create_s": plan_s, "tuning": plan.tuning(),
-            "assign": assign,
+            "assign": assign, "op": op,
             "quality": {"nmi_planted_mean": float(np.mean(nmis)), "nmi_planted_min": float(np.min(nmis)),
                         "k_minus_planted_mean": float(np.mean(kdiff)), "per_graph": per_graph},
             "clocks": clocks}
@@ -669,6 +672,8 @@ def main():
     ap.add_argument("--batch-assign", default=None, choices=["ffma", "tc", "tc8"],
                     help="the batched form's Lloyd engine (default tc8: tensor cores, BF16 storage; ffma: the "
                          "FP32 kernels)")
+    ap.add_argument("--batch-op", default=None, choices=["ncut", "mod_full"],
+                    help="the batched form's operator (default ncut; mod_full needs BF16 storage)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp32-check", action="store_true",

@@ -292,9 +292,12 @@ raftgp_status raftgp_select_bisect_update(const raftgp_csr* g, const void* Z, in
  * The graphs arrive as one block-diagonal CSR: graph g owns the nodes graph_off[g] ..
  * graph_off[g+1]-1 (host int64[n_graphs + 1], graph_off[0] = 0, graph_off[n_graphs] = n) and
  * every column of its rows lies in that range (checked on the device).  Each graph is
- * partitioned as raftgp_partition would partition it alone with the NCut operator and the
- * FP32 k-means engine: its own Eq. 5 projection (Philox rows by the node's index inside the
- * graph), the Eq. 6 layers, k-means++ and Lloyd for the candidates of its own coarse + refined
+ * partitioned as raftgp_partition would partition it alone with the k-means engine of
+ * bo->assign: its own Eq. 5 projection (Philox rows by the node's index inside the graph;
+ * eo->op the NCut operator, or with BF16 storage the full modularity operator, whose rank-one
+ * term d (d^T Theta) / 2e is formed per graph from that graph's degrees and rows, in a fixed
+ * order that differs from a single-graph run's, so its embedding may differ from it by FP32
+ * rounding), the Eq. 6 layers, k-means++ and Lloyd for the candidates of its own coarse + refined
  * grid over [kmin, K_max(g)], K_max(g) = min(ceil(kmax_factor * N_g^0.35), 128, N_g), scored
  * by Eq. 3 / Eq. 1.  The embedding is one pass over the concatenation; the model selection
  * runs in persistent kernels over per-graph and per-candidate work queues; the whole

@@ -374,7 +374,7 @@ class BatchPlan:
     """A captured partition of many graphs (one block-diagonal CSR): run() replays it."""
 
     def __init__(self, g: DeviceGraph, graph_off, dims=(64, 64, 32), dtype="f32", embed_seed=1, theta=None, W=None,
-                 stream=None, **kw):
+                 stream=None, op="ncut", **kw):
         import numpy as np
         self.g = g
         self.off = np.ascontiguousarray(graph_off, dtype=np.int64)
@@ -385,7 +385,7 @@ class BatchPlan:
         if W is not None:
             W = [w.to(dev, torch.float32).contiguous() for w in W]
         self._keep = (theta, W)
-        self.eo = embed_opts("ncut", dims, _dtype_code(dtype), embed_seed, theta, W)
+        self.eo = embed_opts(op, dims, _dtype_code(dtype), embed_seed, theta, W)
         self.bo = batch_opts(**kw)
         self.csr = g.csr()
         offp = self.off.ctypes.data_as(C.POINTER(C.c_int64))

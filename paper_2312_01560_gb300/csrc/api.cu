@@ -105,6 +105,12 @@ struct EmbedWs {
     void* bufB;
     const int32_t* local_row;   // many graphs in one CSR: each node's index inside its graph
     int flat_variant;           // shape of the BF16 flat-stream gathers (0: the default)
+    // many graphs in one CSR with the full modularity operator: per-graph rank-one terms
+    int ng;
+    const int64_t* graph_off;   // ng + 1
+    const int32_t* graph_of;    // n: each node's graph
+    float* g_graph;             // ng x L: d^T Theta per graph
+    double* inv_two_e_graph;    // ng
 };
 
 static int embed_maxw(const raftgp_embed_opts* o) {
@@ -239,9 +245,12 @@ static raftgp_status run_embed(const raftgp_csr* g, const raftgp_embed_opts* o, 
         }
     }
     const bool rank1 = o->op == RAFTGP_OP_MOD_FULL;
+    const bool per_graph = rank1 && w.graph_of;   // several graphs: a rank-one term per graph
     // Theta (prescaled by rs_j for the NCut operator) into bufB
     launch_theta(n, L, o->dtype, o->seed, o->theta, o->op == RAFTGP_OP_NCUT ? w.rs : nullptr, w.local_row, w.deg, w.bufB,
-                 rank1 ? w.partial : nullptr, w.gvec, s);
+                 rank1 && !per_graph ? w.partial : nullptr, w.gvec, s);
+    if (per_graph) launch_rank1_graphs(w.ng, w.graph_off, L, o->dtype, w.bufB, w.deg, w.g_graph, w.inv_two_e_graph, s);
+    const int32_t* pg_of = per_graph ? w.graph_of : nullptr;
     const int agg0 = o->op == RAFTGP_OP_NCUT ? AGG_NCUT_ : (rank1 ? AGG_MOD_FULL_ : AGG_MOD_REDUCED_);
     cudaError_t e;
     // BF16 gathers without a fused weight product run as flat entry streams (spmm_flat.cu)
@@ -249,7 +258,8 @@ static raftgp_status run_embed(const raftgp_csr* g, const raftgp_embed_opts* o, 
     if (o->n_layers == 0) {
         if (flat0)
             e = launch_spmm_flat(agg0, n, g->row_ptr_bits, g->row_ptr, g->col, g->nnz, w.deg, w.rs, w.gvec, 2, L,
-                                 w.bufB, Z, o->stage_out[0], w.work, w.err, w.flat_variant, s);
+                                 w.bufB, Z, o->stage_out[0], w.work, w.err, w.flat_variant, s, pg_of, w.g_graph,
+                                 w.inv_two_e_graph, w.ng);
         else
             e = launch_layer(agg0, o->dtype, g, w.deg, w.rs, w.gvec, 2, nullptr, L, L, nullptr, w.bufB, Z,
                              o->stage_out[0], w.heavy, w.heavy_count, s);
@@ -265,7 +275,8 @@ static raftgp_status run_embed(const raftgp_csr* g, const raftgp_embed_opts* o, 
         launch_self_csr(g, w.rp_self, w.col_self, s);
         if (flat0)
             e = launch_spmm_flat(agg0, n, g->row_ptr_bits, g->row_ptr, g->col, g->nnz, w.deg, w.rs, w.gvec, 0, L,
-                                 w.bufB, w.bufA, o->stage_out[0], w.work, w.err, w.flat_variant, s);
+                                 w.bufB, w.bufA, o->stage_out[0], w.work, w.err, w.flat_variant, s, pg_of, w.g_graph,
+                                 w.inv_two_e_graph, w.ng);
         else
             e = launch_layer(agg0, o->dtype, g, w.deg, w.rs, w.gvec, 0, nullptr, L, L, nullptr, w.bufB, w.bufA,
                              o->stage_out[0], w.heavy, w.heavy_count, s);
@@ -315,6 +326,7 @@ static raftgp_status read_error_word(const uint32_t* err, cudaStream_t s) {
     if (h & DERR_LABEL_RANGE) return fail(RAFTGP_EINVAL, "a label is outside [0, K)");
     if (h & DERR_NORM) return fail(RAFTGP_EINVAL, "an embedding row has norm above 1");
     if (h & DERR_TIMEOUT) return fail(RAFTGP_ETIMEOUT, "a bounded device wait timed out");
+    if (h & DERR_BOUNDS) return fail(RAFTGP_ECUDA, "an internal index check failed (flags 0x%x)", h);
     return RAFTGP_OK;
 }
 
@@ -946,7 +958,9 @@ raftgp_status batch_layout(const raftgp_csr* g, const int64_t* off, int ng, cons
     if (st) return st;
     if ((st = check_embed(eo))) return st;
     if (!off || ng < 1 || !bo) return fail(RAFTGP_EINVAL, "NULL argument or n_graphs < 1");
-    if (eo->op != RAFTGP_OP_NCUT) return fail(RAFTGP_EUNSUPPORTED, "the batched form supports the NCut operator");
+    if (eo->op != RAFTGP_OP_NCUT && !(eo->op == RAFTGP_OP_MOD_FULL && eo->dtype == RAFTGP_BF16))
+        return fail(RAFTGP_EUNSUPPORTED,
+                    "the batched form supports the NCut operator, and the full modularity operator with BF16 storage");
     const int d = eo->dims[eo->n_layers];
     if (d != 32 && d != 64) return fail(RAFTGP_EUNSUPPORTED, "the batched form needs a final width of 32 or 64");
     if (bo->kmin < 2) return fail(RAFTGP_EINVAL, "kmin must be >= 2");
@@ -998,6 +1012,7 @@ void carve_batch(Carver& c, raftgp_batch_plan& p) {
     b.seed_off = c.take<int32_t>(p.ng + 1);
     b.order = c.take<int32_t>(p.ng);
     b.local_row = c.take<int32_t>(n);
+    b.graph_of = c.take<int32_t>(n);
     b.seeds = c.take<int32_t>(p.h_seed_off.empty() ? 1 : p.h_seed_off.back());
     b.cand_k = c.take<int32_t>((size_t)p.ng * BATCH_SLOTS);
     b.n_coarse = c.take<int32_t>(p.ng);
@@ -1010,6 +1025,13 @@ void carve_batch(Carver& c, raftgp_batch_plan& p) {
     b.chosen = c.take<uint8_t>(n);
     b.queue = c.take<int>(64);
     p.ew.local_row = b.local_row;
+    if (p.eo.op == RAFTGP_OP_MOD_FULL) {
+        p.ew.ng = p.ng;
+        p.ew.graph_off = b.node_off;
+        p.ew.graph_of = b.graph_of;
+        p.ew.g_graph = c.take<float>((size_t)p.ng * p.eo.dims[0]);
+        p.ew.inv_two_e_graph = c.take<double>(p.ng);
+    }
     p.stg = p.bo.assign != RAFTGP_ASSIGN_FFMA ? c.take<char>(batch_tc_staging_bytes(p.d)) : nullptr;
 }
 
@@ -1080,6 +1102,9 @@ raftgp_status raftgp_batch_plan_create(const raftgp_csr* g, const int64_t* graph
     launch_degrees(&p->g, p->ew.deg, p->ew.rs, p->ew.rsh, p->ew.err, p->ew.heavy, p->ew.heavy_count, s);
     launch_batch_check(&p->g, p->ng, b.node_off, p->ew.err, s);
     if ((st = read_error_word(p->ew.err, s))) return st;
+    // local rows and each node's graph, which the embedding reads (Philox counters, the
+    // per-graph rank-one term), before its first run
+    launch_batch_prologue(b, p->bo.kmin, p->bo.grid, s);
     // autotuning of the BF16 embedding's gathers: one embedding timed per flat-stream shape
     // (batch size and staging depth; every shape gives the same bits)
     if (p->eo.dtype == RAFTGP_BF16) {
@@ -1216,7 +1241,8 @@ raftgp_status raftgp_batch_plan_check(const raftgp_batch_plan* plan) {
     if (!plan) return fail(RAFTGP_EINVAL, "plan is NULL");
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "batched partition");
-    return read_error_word(plan->err, nullptr);
+    raftgp_status st = read_error_word(plan->err, nullptr);
+    return st ? st : read_error_word(plan->ew.err, nullptr);
 }
 
 raftgp_status raftgp_batch_plan_embedding(const raftgp_batch_plan* plan, void* Z_out) {

@@ -64,10 +64,14 @@ __device__ __forceinline__ unsigned long long bk_quant(float d2) { return __floa
 // ------------------------------------------------------------------------------------
 // Per-node index inside its graph (Philox row counters) and per-node graph ids.
 // ------------------------------------------------------------------------------------
-__global__ void k_batch_local_rows(int ng, const int64_t* __restrict__ node_off, int32_t* __restrict__ local_row) {
+__global__ void k_batch_local_rows(int ng, const int64_t* __restrict__ node_off, int32_t* __restrict__ local_row,
+                                   int32_t* __restrict__ graph_of) {
     for (int g = blockIdx.x; g < ng; g += gridDim.x) {
         const int64_t a = node_off[g], b = node_off[g + 1];
-        for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) local_row[i] = (int32_t)(i - a);
+        for (int64_t i = a + threadIdx.x; i < b; i += blockDim.x) {
+            local_row[i] = (int32_t)(i - a);
+            graph_of[i] = g;
+        }
     }
 }
 
@@ -616,7 +620,7 @@ size_t batch_lloyd_smem(int d) {
 void launch_batch_prologue(BatchDev b, int kmin, int G, cudaStream_t s) {
     ProfScope ps(s, PF_BATCH_INIT, 2);
     cudaMemsetAsync(b.queue, 0, 4 * sizeof(int), s);
-    k_batch_local_rows<<<b.ng < 4096 ? b.ng : 4096, 256, 0, s>>>(b.ng, b.node_off, b.local_row);
+    k_batch_local_rows<<<b.ng < 4096 ? b.ng : 4096, 256, 0, s>>>(b.ng, b.node_off, b.local_row, b.graph_of);
     k_batch_coarse<<<(b.ng + 127) / 128, 128, 0, s>>>(b, kmin, G);
 }
 

@@ -358,11 +358,16 @@ __global__ void __launch_bounds__(BTC_THREADS, 1)
                                 }
                                 lab[i] = (int16_t)nl;
                             } else {
-                                const int ol = lab[i];
+                                int ol = lab[i];
+                                if (ol < -1 || ol >= K) {   // never expected: reported, taken as unassigned
+                                    flag_error(a.err, DERR_BOUNDS);
+                                    ol = -1;
+                                }
                                 if (nl != ol) {
                                     lab[i] = (int16_t)nl;
                                     const int slot_c = atomicAdd(&ctl.nchg[t & 1], 1);
-                                    ctl.chg[t & 1][slot_c] = make_int4((int)i, ol, nl, 0);
+                                    if (slot_c < 128) ctl.chg[t & 1][slot_c] = make_int4((int)i, ol, nl, 0);
+                                    else flag_error(a.err, DERR_BOUNDS);
                                 }
                             }
                         }
@@ -374,9 +379,13 @@ __global__ void __launch_bounds__(BTC_THREADS, 1)
                     if (!fin) {
                         // the tile's changes: a warp per change, lanes over coordinates, each moving
                         // the point's 2^-40 fixed-point row from its old cluster's sum to its new one
-                        const int nch = ctl.nchg[t & 1];
+                        const int nch = ctl.nchg[t & 1] < 128 ? ctl.nchg[t & 1] : 128;
                         for (int e = ew; e < nch; e += 4) {
                             const int4 r = ctl.chg[t & 1][e];
+                            if (r.x < 0 || r.x >= n || r.y < -1 || r.y >= K || r.z < 0 || r.z >= K) {
+                                if (lane == 0) flag_error(a.err, DERR_BOUNDS);
+                                continue;
+                            }
                             const __nv_bfloat16* zi = a.Z + (o + r.x) * D;
                             if (lane == 0) {
                                 atomicAdd(cnt + r.z, 1);

@@ -19,6 +19,7 @@ enum DeviceError : uint32_t {
     DERR_LABEL_RANGE = 8u,   // a label outside [0, K)
     DERR_TIMEOUT = 16u,      // a bounded wait gave up
     DERR_NORM = 32u,         // an embedding row with norm well above 1
+    DERR_BOUNDS = 64u,       // an internal index outside its array (checked, the access skipped)
 };
 
 __device__ __forceinline__ void flag_error(uint32_t* err, uint32_t bit) { atomicOr(err, bit); }

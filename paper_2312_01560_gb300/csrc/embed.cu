@@ -138,6 +138,58 @@ __global__ void k_rank1_finish(int nblocks, int L, const double* partial, float*
     g[c] = (float)t;
 }
 
+// Per-graph rank-one term of the full modularity matrix when several graphs share one CSR: a
+// block per graph; thread (slot, q) sums d_j Theta_j,4q..4q+3 over the graph's rows slot,
+// slot + slots, ... in FP64, the slots are added in ascending order, and 2e = sum_j d_j (exact).
+template <typename T>
+__global__ void k_rank1_graphs(int ng, const int64_t* __restrict__ off, int L, const T* __restrict__ theta,
+                               const int32_t* __restrict__ deg, float* g_graph, double* inv_two_e_graph) {
+    extern __shared__ double sr[];   // [slots][L]
+    const int tpr = L / 4, slots = blockDim.x / tpr;
+    const int q = threadIdx.x % tpr, slot = threadIdx.x / tpr;
+    __shared__ long long s_two_e;
+    for (int g = blockIdx.x; g < ng; g += gridDim.x) {
+        const int64_t a = off[g], b = off[g + 1];
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        long long te = 0;
+        if (slot < slots)
+            for (int64_t j = a + slot; j < b; j += slots) {
+                const double dj = (double)deg[j];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[c] += dj * (double)Vec<T>::to_float(theta[j * L + 4 * q + c]);
+                if (q == 0) te += deg[j];
+            }
+        if (threadIdx.x == 0) s_two_e = 0;
+        __syncthreads();
+        if (slot < slots) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sr[slot * L + 4 * q + c] = acc[c];
+            if (q == 0 && te) atomicAdd(reinterpret_cast<unsigned long long*>(&s_two_e), (unsigned long long)te);
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < L; c += blockDim.x) {
+            double t = 0.0;
+            for (int r = 0; r < slots; ++r) t += sr[r * L + c];
+            g_graph[(int64_t)g * L + c] = (float)t;
+        }
+        if (threadIdx.x == 0) inv_two_e_graph[g] = s_two_e > 0 ? 1.0 / (double)s_two_e : 0.0;
+        __syncthreads();
+    }
+}
+
+void launch_rank1_graphs(int ng, const int64_t* off, int L, int dtype, const void* theta, const int32_t* deg,
+                         float* g_graph, double* inv_two_e_graph, cudaStream_t s) {
+    const int threads = 256;
+    const size_t sm = (size_t)(threads / (L / 4)) * L * sizeof(double);
+    const int blocks = ng < num_sms() * 4 ? ng : num_sms() * 4;
+    ProfScope ps(s, PF_THETA, 1);
+    if (dtype == RAFTGP_BF16)
+        k_rank1_graphs<__nv_bfloat16><<<blocks, threads, sm, s>>>(ng, off, L, (const __nv_bfloat16*)theta, deg, g_graph,
+                                                                  inv_two_e_graph);
+    else
+        k_rank1_graphs<float><<<blocks, threads, sm, s>>>(ng, off, L, (const float*)theta, deg, g_graph, inv_two_e_graph);
+}
+
 // GCN weights W^(k), Xavier-normal, entry (a, 4q+s) from Philox block (q, a, k, "Wgnn").
 __global__ void k_weights(int layer, int lin, int lout, uint64_t seed, float* W) {
     const int qn = lout / 4;

@@ -54,6 +54,10 @@ void launch_degrees(const raftgp_csr* g, int32_t* deg, float* rs, float* rsh, ui
                     int* heavy_count, cudaStream_t s);
 int theta_blocks(int64_t n);
 // With `rows`, only the listed rows of Theta are written (nrows of them; no rank-one partials).
+// Many graphs in one CSR (graph g owns rows off[g] .. off[g+1]-1): per graph d^T Theta from the
+// stored Theta (g_graph, ng x L, FP64 sums in a fixed order, rounded to FP32) and 1 / 2e.
+void launch_rank1_graphs(int ng, const int64_t* off, int L, int dtype, const void* theta, const int32_t* deg,
+                         float* g_graph, double* inv_two_e_graph, cudaStream_t s);
 void launch_theta(int64_t n, int L, int dtype, uint64_t seed, const float* user_theta, const float* colscale, const int32_t* local_row,
                   const int32_t* deg, void* theta, double* partial, float* gvec, cudaStream_t s,
                   const int32_t* rows = nullptr, int64_t nrows = 0);
@@ -69,7 +73,8 @@ bool spmm_flat_supported(int agg, int dtype, int lin);
 cudaError_t launch_spmm_flat(int agg, int64_t n, int rp_bits, const void* row_ptr, const int32_t* col, int64_t nnz_g,
                              const int32_t* deg, const float* rowscale, const float* gvec, int act, int lin,
                              const void* X, void* out, void* stage, int* work, uint32_t* err, int variant,
-                             cudaStream_t s);
+                             cudaStream_t s, const int32_t* graph_of = nullptr, const float* g_graph = nullptr,
+                             const double* inv_two_e_graph = nullptr, int ng = 0);
 // CSR of A + I (row i: i, then its neighbours): rp_self has n + 1 entries, col_self nnz + n.
 void launch_self_csr(const raftgp_csr* g, int64_t* rp_self, int32_t* col_self, cudaStream_t s);
 
@@ -234,6 +239,7 @@ struct BatchDev {
     const int32_t* seed_off;       // ng + 1: each graph's seeds in `seeds`
     const int32_t* order;          // ng: graphs by decreasing size (work order)
     int32_t* local_row;            // total_n: index of the node inside its graph
+    int32_t* graph_of;             // total_n: the node's graph
     int32_t* seeds;                // sum of kmax
     int32_t* cand_k;               // ng x BATCH_SLOTS
     int32_t* n_coarse;             // ng

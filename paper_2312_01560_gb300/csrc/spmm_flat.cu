@@ -48,7 +48,24 @@ struct FlatArgs {
     __nv_bfloat16* stage;    // optional copy of the finished rows
     int* work;               // chunk counter (zeroed before the launch)
     uint32_t* err;           // device error word (a bounded wait that gave up: DERR_TIMEOUT)
+    // many graphs in one CSR (full modularity operator): each row's graph, and per graph its
+    // d^T Theta (ng x L) and 1 / 2e; null for one graph (then g and inv_two_e above)
+    const int32_t* graph_of;
+    const float* g_graph;
+    const double* inv_two_e_graph;
+    int ng;
 };
+
+// A row's graph, checked against the graph count (an inconsistent index is reported and
+// graph 0 used instead).
+__device__ __forceinline__ int fl_graph(const FlatArgs& a, int64_t i) {
+    const int g = a.graph_of[i];
+    if (g < 0 || g >= a.ng) {
+        flag_error(a.err, DERR_BOUNDS);
+        return 0;
+    }
+    return g;
+}
 
 // Four rows (y0..y3) of the 2D tensor map, the whole row width from x = 0, into dst (4 boxes
 // one after another); completion counted on bar.
@@ -99,8 +116,13 @@ __device__ __forceinline__ void fetch_chunk(const FlatArgs& a, int lane, int64_t
     c.rpC = rp_at(a, r0 + FL_CH);
     const int64_t ra = r0 + lane, rb = r0 + 32 + lane;
     if constexpr (AGG == AGG_MOD_FULL_) {
-        c.scA = ra < a.n ? (float)((double)a.deg[ra] * a.inv_two_e) : 0.f;
-        c.scB = rb < a.n ? (float)((double)a.deg[rb] * a.inv_two_e) : 0.f;
+        if (a.graph_of) {
+            c.scA = ra < a.n ? (float)((double)a.deg[ra] * a.inv_two_e_graph[fl_graph(a, ra)]) : 0.f;
+            c.scB = rb < a.n ? (float)((double)a.deg[rb] * a.inv_two_e_graph[fl_graph(a, rb)]) : 0.f;
+        } else {
+            c.scA = ra < a.n ? (float)((double)a.deg[ra] * a.inv_two_e) : 0.f;
+            c.scB = rb < a.n ? (float)((double)a.deg[rb] * a.inv_two_e) : 0.f;
+        }
     } else {
         c.scA = ra < a.n ? a.rowscale[ra] : 0.f;
         c.scB = rb < a.n ? a.rowscale[rb] : 0.f;
@@ -201,7 +223,7 @@ __global__ void __launch_bounds__(FL_WARPS * 32) k_spmm_flat(FlatArgs a, const _
     float gl[EG];
 #pragma unroll
     for (int e = 0; e < EG; ++e) {
-        if constexpr (AGG == AGG_MOD_FULL_) gl[e] = a.g[c0 + e];
+        if constexpr (AGG == AGG_MOD_FULL_) gl[e] = a.graph_of ? 0.f : a.g[c0 + e];
         else gl[e] = 0.f;
     }
 
@@ -318,8 +340,13 @@ __global__ void __launch_bounds__(FL_WARPS * 32) k_spmm_flat(FlatArgs a, const _
 #pragma unroll
                 for (int q = 1; q < GPW; ++q)
                     if (grp == q) v = acc[q * EG + e];
-                if constexpr (AGG == AGG_MOD_FULL_) y[e] = v - sc * gl[e];
-                else y[e] = sc * v;
+                if constexpr (AGG == AGG_MOD_FULL_) {
+                    // the row's own graph's d^T Theta when several graphs share the CSR
+                    const float ge = a.graph_of ? a.g_graph[(int64_t)fl_graph(a, row0 + cr) * LIN + c0 + e] : gl[e];
+                    y[e] = v - sc * ge;
+                } else {
+                    y[e] = sc * v;
+                }
             }
             if (a.act != 0) {
                 float ss = 0.f;
@@ -489,8 +516,13 @@ void launch_self_csr(const raftgp_csr* g, int64_t* rp_self, int32_t* col_self, c
 cudaError_t launch_spmm_flat(int agg, int64_t n, int rp_bits, const void* row_ptr, const int32_t* col, int64_t nnz_g,
                              const int32_t* deg, const float* rowscale, const float* gvec, int act, int lin,
                              const void* X, void* out, void* stage, int* work, uint32_t* err, int variant,
-                             cudaStream_t s) {
+                             cudaStream_t s, const int32_t* graph_of, const float* g_graph,
+                             const double* inv_two_e_graph, int ng) {
     FlatArgs a;
+    a.ng = ng;
+    a.graph_of = graph_of;
+    a.g_graph = g_graph;
+    a.inv_two_e_graph = inv_two_e_graph;
     a.n = n;
     a.rp32 = rp_bits == 32 ? (const int32_t*)row_ptr : nullptr;
     a.rp64 = rp_bits == 64 ? (const int64_t*)row_ptr : nullptr;

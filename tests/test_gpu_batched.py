@@ -242,3 +242,38 @@ def test_every_embedding_gather_shape_gives_the_same_embedding(cuda, batch):
     print(f"embedding gather tuning: {t['embed_gather_variant']} {t['embed_gather_ms']}")
     assert 0 <= t["embed_gather_variant"] <= 3 and all(m > 0 for m in t["embed_gather_ms"])
     plan.close()
+
+
+def test_mod_full_batch_embedding_matches_the_oracle(cuda, batch):
+    # the full modularity operator in the batched form: each graph's rank-one term from its own
+    # degrees and Theta rows; the batch's BF16 embedding of each graph is within BF16 storage
+    # error of the FP64 oracle's embedding of that graph alone, and close to the single-graph
+    # BF16 embedding (the rank-one sums run in another order)
+    from conftest import rel_fro
+    sub = batch[:4]
+    dg, off = api.concat_graphs(sub, cuda)
+    dims = (64, 64, 32)
+    plan = api.BatchPlan(dg, off, dims=dims, dtype="bf16", op="mod_full", kmin=2, grid=10, iters=50, seed=2,
+                         assign="tc8")
+    labels, ks = plan.run()
+    plan.check()
+    Z = plan.embedding().float().cpu().numpy()
+    labels, ks = labels.cpu().numpy(), ks.cpu().numpy()
+    for gi, g in enumerate(sub):
+        _, Zo = oracle.embed(g, "mod_full", dims, seed=1)
+        Zg = Z[off[gi]:off[gi + 1]]
+        one = api.DeviceGraph.from_host(g, cuda)
+        Z1 = api.embed(one, "mod_full", dims, "bf16", seed=1).float().cpu().numpy()
+        e_or, e_one = rel_fro(Zg, Zo), rel_fro(Zg, Z1)
+        lab = labels[off[gi]:off[gi + 1]]
+        print(f"graph {gi} (N={g.n}): rel. error vs oracle {e_or:.2e}, vs single-graph BF16 {e_one:.2e}; "
+              f"K* {ks[gi]}, NMI vs planted {nmi(lab, g.planted):.4f}")
+        assert e_or <= 6e-3 and e_one <= 2e-3
+        assert 2 <= ks[gi] <= _kmax(g.n) and lab.min() >= 0 and lab.max() < ks[gi]
+    plan.close()
+
+
+def test_mod_full_batch_needs_bf16(cuda, batch):
+    dg, off = api.concat_graphs(batch[:2], cuda)
+    with pytest.raises(api._abi.RaftgpError, match="BF16"):
+        api.BatchPlan(dg, off, dims=DIMS, dtype="f32", op="mod_full")
