@@ -40,16 +40,31 @@ __device__ __forceinline__ uint64_t global_ns() {
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
     return t;
 }
+// The same test, but a thread whose phase is not complete yet is suspended until the phase
+// completes or about `ns` nanoseconds have passed, so a waiting warp does not take issue
+// slots from the warps that share its scheduler.
+__device__ __forceinline__ bool mbar_test_sleep(uint64_t* bar, uint32_t parity, uint32_t ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(ns)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait: false when the CTA aborted (another wait timed out) or this one timed out.
+// Each retry sleeps at most TC_SUSPEND_NS, so the abort flag and the clock are read at least
+// that often.
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;  // 2 s
+constexpr uint32_t TC_SUSPEND_NS = 100000;       // 100 us
 template <typename Ctl>
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, Ctl* ctl, uint32_t* err) {
     if (mbar_test(bar, parity)) return true;
     const uint64_t t0 = global_ns();
-    for (uint32_t it = 0;; ++it) {
-        if (mbar_test(bar, parity)) return true;
+    for (;;) {
+        if (mbar_test_sleep(bar, parity, TC_SUSPEND_NS)) return true;
         if (*(volatile int*)&ctl->abort) return false;
-        if ((it & 255) == 255 && global_ns() - t0 > TC_WAIT_NS) {
+        if (global_ns() - t0 > TC_WAIT_NS) {
             *(volatile int*)&ctl->abort = 1;
             if (err) atomicOr(err, DERR_TIMEOUT);
             return false;
