@@ -34,7 +34,10 @@ template <int D>
 struct FfCfg {
     static constexpr int ZT = D * FF_PTS;            // floats of the point tile
     static constexpr int CHUNK = D * FF_CH + FF_CH;  // floats of one chunk buffer (+ its norms)
-    static constexpr int SMEM = (ZT + 2 * CHUNK) * (int)sizeof(float);
+    // chunk buffers: three where they fit (two CTAs per SM at d <= 64: 2 x 115,456 bytes plus
+    // the per-CTA reserve stay within the SM's 233,472), so one barrier per chunk suffices
+    static constexpr int BUFS = D <= 64 ? 3 : 2;
+    static constexpr int SMEM = (ZT + BUFS * CHUNK) * (int)sizeof(float);
     static constexpr int MIN_BLOCKS = D <= 64 ? 2 : 1;
     static_assert(SMEM <= 227 * 1024, "shared memory budget");
 };
@@ -198,13 +201,16 @@ __global__ void __launch_bounds__(FF_THREADS, FfCfg<D>::MIN_BLOCKS)
     while (has) {
         int cn = c, qn = q;
         const bool hn = ff_next(b, st.active, FINAL, cn, qn);
+        const int nbuf = buf + 1 == C::BUFS ? 0 : buf + 1;
         if (hn) {
-            ff_load_chunk<D>(chunk0 + (buf ^ 1) * C::CHUNK, st, b.off[cn] + qn * FF_CH, tid);
+            // three buffers: the one refilled here was last read two chunks ago, before the
+            // previous barrier; two buffers: the barrier at the end of the previous chunk
+            ff_load_chunk<D>(chunk0 + nbuf * C::CHUNK, st, b.off[cn] + qn * FF_CH, tid);
             ff_wait_but_one();
         } else {
             ff_wait_all();
         }
-        __syncthreads();
+        __syncthreads();   // this chunk's copies, issued by every thread, have landed
         const float* mT = chunk0 + buf * C::CHUNK;
         // a candidate's last chunk with at most 32 real centroids: only the first half
         if (b.k[c] - q * FF_CH > 32) ff_chunk<D, FINAL, 8>(zw, mT, pr, cr, q, bv, b2, bi);
@@ -269,11 +275,11 @@ __global__ void __launch_bounds__(FF_THREADS, FfCfg<D>::MIN_BLOCKS)
 #pragma unroll
             for (int r = 0; r < 8; ++r) { bv[r] = INFINITY; b2[r] = INFINITY; bi[r] = 0x7fffffff; }
         }
-        __syncthreads();   // every warp is done with this buffer before it is refilled
+        if (C::BUFS == 2) __syncthreads();   // every warp is done with this buffer before it is refilled
         c = cn;
         q = qn;
         has = hn;
-        buf ^= 1;
+        buf = nbuf;
     }
 }
 
@@ -283,6 +289,8 @@ static cudaError_t launch_ff_t(const CandBatch& b, const T* Z, int64_t n, KmStat
     using C = FfCfg<D>;
     auto kern = k_assign_ffma<T, D, FINAL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     const int64_t tiles = (n + FF_PTS - 1) / FF_PTS;
     ProfScope ps(s, FINAL ? PF_ASSIGN_FFMA_FINAL : PF_ASSIGN_FFMA, 1);
