@@ -151,7 +151,7 @@ def algorithmic_work(fam, g, wl, elem, cands):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture
 # of the kernel at this workload: the Lloyd pass of the coarse candidate batch (k_assign_tc,
 # hi-only).  An entry goes back to None when its kernel changes, until it is captured again.
-TRAFFIC_PER_LAUNCH = {"assign_tc": 1.6615e8}
+TRAFFIC_PER_LAUNCH = {"assign_tc": 1.6569e8}
 
 
 def roofline(full, timed, dom, g, wl, elem, cands, steps):
