@@ -397,25 +397,6 @@ static raftgp_status run_lloyd(const CandBatch& b, const void* Z, int zdtype, in
     return RAFTGP_OK;
 }
 
-// Splits the candidates of a batch between the tensor-core epilogue groups, largest K first
-// onto the lightest group.
-static void assign_owners(CandBatch& b) {
-    constexpr int G = 4;
-    long long load[G] = {0, 0, 0, 0};
-    bool done[MAXC] = {};
-    for (int r = 0; r < b.n; ++r) {
-        int pick = -1;
-        for (int c = 0; c < b.n; ++c)
-            if (!done[c] && (pick < 0 || b.k[c] > b.k[pick])) pick = c;
-        done[pick] = true;
-        int g = 0;
-        for (int h = 1; h < G; ++h)
-            if (load[h] < load[g]) g = h;
-        b.owner[pick] = g;
-        load[g] += b.k[pick];
-    }
-}
-
 // Evaluate a list of candidates in batches; appends their records.
 static raftgp_status run_candidates(const raftgp_csr* g, const void* Z, int d, int zdtype,
                                     const raftgp_select_opts* o, const std::vector<int>& ks, const SelectWs& w,
@@ -434,7 +415,6 @@ static raftgp_status run_candidates(const raftgp_csr* g, const void* Z, int d, i
         b0 += b.n;
         b.cs = (b.n + 7) / 8 * 8;
         b.total_k = off;
-        assign_owners(b);
         launch_batch_init(b, Z, zdtype, n, d, w.seeds, nullptr, w.km, s);
         raftgp_status st = run_lloyd(b, Z, zdtype, n, d, o->iters, o->assign, o->recheck, w.km, w.recheck, w.recheck_count,
                                      w.err, s);

@@ -130,7 +130,6 @@ struct CandBatch {
     int cs;             // label row stride (n rounded up to a multiple of 8)
     int k[MAXC];        // K of each candidate
     int off[MAXC];      // first centroid of each candidate (multiples of 64: candidates padded)
-    int owner[MAXC];    // tensor-core epilogue group that evaluates the candidate (0..3)
 };
 
 struct KmState {                 // device arrays of one batch (workspace)
