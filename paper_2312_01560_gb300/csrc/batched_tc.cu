@@ -35,6 +35,10 @@ namespace raftgp {
 
 constexpr int BTC_ROWS = 128;         // centroid rows of the operand (BATCH_KMAX)
 constexpr int BTC_THREADS = 192;      // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+// At most two CTAs per SM (2 x 256 tensor-memory columns): an item's passes are a chain of
+// dependent steps on few tiles, so a second item on the SM fills the gaps where its shared
+// memory fits (d = 32: 92 KB; d = 64 needs 170 KB, one CTA).
+constexpr int BTC_MAX_CTAS_PER_SM = 2;
 static_assert(BTC_ROWS == BATCH_KMAX, "one operand row per possible centroid");
 
 template <int D>
@@ -59,6 +63,8 @@ struct BtcCfg {
     static constexpr int BYTES = OFF_CNT + 128 * 4;
     static constexpr int SMEM = BYTES + 1024;              // + alignment slack
     static_assert(SMEM <= 227 * 1024, "shared memory budget");
+    // resident CTAs per SM: the SM's 228 KB less 1 KB reserved per CTA
+    static constexpr int CTAS = 2 * (SMEM + 1024) <= 228 * 1024 ? BTC_MAX_CTAS_PER_SM : 1;
 };
 
 struct BtcCtl {
@@ -142,7 +148,7 @@ __device__ void btc_build(const BtcArgs& a, const float* mu, float* nrm4, int K,
 }
 
 template <int D>
-__global__ void __launch_bounds__(BTC_THREADS, 1)
+__global__ void __launch_bounds__(BTC_THREADS, BtcCfg<D>::CTAS)
     k_batch_lloyd_tc(const __grid_constant__ BtcArgs a, const __grid_constant__ CUtensorMap tmZ,
                      const __grid_constant__ CUtensorMap tmHi, const __grid_constant__ CUtensorMap tmLo,
                      const __grid_constant__ CUtensorMap tmAug) {
@@ -457,13 +463,15 @@ __global__ void __launch_bounds__(BTC_THREADS, 1)
 // ------------------------------------------------------------------------------------
 // Host side
 // ------------------------------------------------------------------------------------
-size_t batch_tc_staging_bytes(int d) { return (size_t)num_sms() * 128 * (2 * (size_t)d + 16) * sizeof(__nv_bfloat16); }
+size_t batch_tc_staging_bytes(int d) {
+    return (size_t)num_sms() * BTC_MAX_CTAS_PER_SM * 128 * (2 * (size_t)d + 16) * sizeof(__nv_bfloat16);
+}
 
 template <int D>
 static cudaError_t launch_btc_t(BatchDev b, const __nv_bfloat16* Z, int phase, int iters, int lo_fast,
                                 const raftgp_csr* g, void* stg, uint32_t* err, cudaStream_t s) {
     using C = BtcCfg<D>;
-    const int grid = num_sms();
+    const int grid = num_sms() * C::CTAS;   // the staging area holds up to that many x 128 rows
     BtcArgs a;
     a.b = b;
     a.Z = Z;
