@@ -152,12 +152,27 @@ __global__ void k_rank1_graphs(int ng, const int64_t* __restrict__ off, int L, c
         const int64_t a = off[g], b = off[g + 1];
         double acc[4] = {0.0, 0.0, 0.0, 0.0};
         long long te = 0;
+        // U of this slot's rows loaded before any is added (a graph of 50k rows is otherwise 6k
+        // dependent round trips for its block); the additions keep the row order
+        constexpr int U = 8;
         if (slot < slots)
-            for (int64_t j = a + slot; j < b; j += slots) {
-                const double dj = (double)deg[j];
+            for (int64_t j0 = a + slot; j0 < b; j0 += (int64_t)slots * U) {
+                int dj[U];
+                float th[U][4];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) acc[c] += dj * (double)Vec<T>::to_float(theta[j * L + 4 * q + c]);
-                if (q == 0) te += deg[j];
+                for (int u = 0; u < U; ++u) {
+                    const int64_t j = j0 + (int64_t)u * slots;
+                    dj[u] = j < b ? deg[j] : 0;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) th[u][c] = j < b ? Vec<T>::to_float(theta[j * L + 4 * q + c]) : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (j0 + (int64_t)u * slots >= b) break;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[c] += (double)dj[u] * (double)th[u][c];
+                    if (q == 0) te += dj[u];
+                }
             }
         if (threadIdx.x == 0) s_two_e = 0;
         __syncthreads();
