@@ -1,7 +1,8 @@
 // batched_tc.cu -- the batched form's Lloyd k-means on the 5th-generation tensor cores.
 //
-// One persistent CTA per (graph, candidate K) work item, as the FP32 batched kernel, but each
-// assignment pass is a tcgen05 GEMM of the graph's points against its K <= 128 centroids:
+// Persistent CTAs (two per SM) taking (graph, candidate K) work items from a queue, as the FP32
+// batched kernel, but each assignment pass is a tcgen05 GEMM of the graph's points against its
+// K <= 128 centroids:
 //   - the centroid operand (BF16 split of -mu into hi and lo, and the K=16 norm slice
 //     [(||mu||^2 + 4)/2 hi, lo, 128, 0...] of the tensor-core k-means) is rebuilt from the FP32
 //     centroids in shared memory at the start of every pass, written to this CTA's rows of a
@@ -13,7 +14,8 @@
 //   - Lloyd passes multiply the hi half only plus the norm slice, so the accumulator is
 //     128 + (||z - mu||^2 - ||z||^2 + 4) / 2 and the integer-key argmin of the single-graph
 //     engine applies (ties to the lowest column); a changed label moves the point's 2^-40
-//     fixed-point row between the clusters' sums in shared memory;
+//     fixed-point row between the clusters' sums (this CTA's slice of a global area, 64-bit
+//     reductions in L2);
 //   - the final assignment multiplies hi + lo, keeps the exact best and second-best FP32
 //     scores and re-checks every point whose two best lie within the derived band in the FP32
 //     direct form over all K centroids, so every reported label is the FP32-nearest centroid;
@@ -35,9 +37,9 @@ namespace raftgp {
 
 constexpr int BTC_ROWS = 128;         // centroid rows of the operand (BATCH_KMAX)
 constexpr int BTC_THREADS = 192;      // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
-// At most two CTAs per SM (2 x 256 tensor-memory columns): an item's passes are a chain of
-// dependent steps on few tiles, so a second item on the SM fills the gaps where its shared
-// memory fits (d = 32: 92 KB; d = 64 needs 170 KB, one CTA).
+// Two CTAs per SM (2 x 256 tensor-memory columns; shared memory 62 KB at d = 32, 107 KB at
+// d = 64): an item's passes are a chain of dependent steps on few tiles, so a second item on
+// the SM fills the gaps.
 constexpr int BTC_MAX_CTAS_PER_SM = 2;
 static_assert(BTC_ROWS == BATCH_KMAX, "one operand row per possible centroid");
 
@@ -58,13 +60,11 @@ struct BtcCfg {
     static constexpr int OFF_BAUG = OFF_BLO + TILE;
     static constexpr int OFF_MU = OFF_BAUG + AUG;          // FP32 centroids, 128 x D
     static constexpr int OFF_NRM = OFF_MU + 128 * D * 4;   // ||mu||^2 + 4 (infinite on padding rows)
-    static constexpr int OFF_SUMS = OFF_NRM + 128 * 4;     // int64 fixed-point sums, 128 x D
-    static constexpr int OFF_CNT = OFF_SUMS + 128 * D * 8;
+    static constexpr int OFF_SCORE = OFF_NRM + 128 * 4;    // the scorer's 2 x 128 counters (u64)
+    static constexpr int OFF_CNT = OFF_SCORE + 2 * 128 * 8;
     static constexpr int BYTES = OFF_CNT + 128 * 4;
     static constexpr int SMEM = BYTES + 1024;              // + alignment slack
     static_assert(SMEM <= 227 * 1024, "shared memory budget");
-    // resident CTAs per SM: the SM's 228 KB less 1 KB reserved per CTA
-    static constexpr int CTAS = 2 * (SMEM + 1024) <= 228 * 1024 ? BTC_MAX_CTAS_PER_SM : 1;
 };
 
 struct BtcCtl {
@@ -90,6 +90,7 @@ struct BtcArgs {
     __nv_bfloat16* stg_hi;    // gridDim.x x 128 x D
     __nv_bfloat16* stg_lo;
     __nv_bfloat16* stg_aug;   // gridDim.x x 128 x 16
+    long long* gsums;         // gridDim.x x 128 x D: each CTA's 2^-40 fixed-point centroid sums
     float band;               // near-tie band of the final assignment (tc_tie_band(D))
     uint32_t* err;
 };
@@ -148,7 +149,7 @@ __device__ void btc_build(const BtcArgs& a, const float* mu, float* nrm4, int K,
 }
 
 template <int D>
-__global__ void __launch_bounds__(BTC_THREADS, BtcCfg<D>::CTAS)
+__global__ void __launch_bounds__(BTC_THREADS, BTC_MAX_CTAS_PER_SM)
     k_batch_lloyd_tc(const __grid_constant__ BtcArgs a, const __grid_constant__ CUtensorMap tmZ,
                      const __grid_constant__ CUtensorMap tmHi, const __grid_constant__ CUtensorMap tmLo,
                      const __grid_constant__ CUtensorMap tmAug) {
@@ -164,7 +165,11 @@ __global__ void __launch_bounds__(BTC_THREADS, BtcCfg<D>::CTAS)
     uint8_t* sBaug = base + C::OFF_BAUG;
     float* mu = reinterpret_cast<float*>(base + C::OFF_MU);
     float* nrm4 = reinterpret_cast<float*>(base + C::OFF_NRM);
-    long long* sums = reinterpret_cast<long long*>(base + C::OFF_SUMS);
+    // the centroid sums live in global memory (L2), this CTA's slice: in shared memory they
+    // would take 64 KB at d = 64 and leave room for one CTA per SM; updated with 64-bit
+    // reductions, read back through L2 (ld.global.cg)
+    long long* sums = a.gsums + (size_t)blockIdx.x * 128 * D;
+    unsigned long long* score_scratch = reinterpret_cast<unsigned long long*>(base + C::OFF_SCORE);
     int* cnt = reinterpret_cast<int*>(base + C::OFF_CNT);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const BatchDev& b = a.b;
@@ -434,14 +439,13 @@ __global__ void __launch_bounds__(BTC_THREADS, BtcCfg<D>::CTAS)
                 const int ct = cnt[cc];
                 if (ct <= 0) continue;
                 const double inv = 1.0 / ((double)ct * FIXED_SCALE);
-                for (int k = lane; k < D; k += 32) mu[cc * D + k] = (float)((double)sums[cc * D + k] * inv);
+                for (int k = lane; k < D; k += 32) mu[cc * D + k] = (float)((double)__ldcg(sums + cc * D + k) * inv);
             }
             updated = true;
             __syncthreads();
         }
         if (*(volatile int*)&ctl.abort) break;
-        batch_score_item(b, g, slot, K, o, n, lab, passes, reinterpret_cast<unsigned long long*>(sums), a.rp64, a.rp32,
-                         a.col);
+        batch_score_item(b, g, slot, K, o, n, lab, passes, score_scratch, a.rp64, a.rp32, a.col);
         __syncthreads();
     }
     // exit: the producer lets its last copies land, the MMA issuer waits for its last MMAs
@@ -463,15 +467,29 @@ __global__ void __launch_bounds__(BTC_THREADS, BtcCfg<D>::CTAS)
 // ------------------------------------------------------------------------------------
 // Host side
 // ------------------------------------------------------------------------------------
+// operand rows (hi, lo, norm slice) and centroid sums of up to BTC_MAX_CTAS_PER_SM CTAs per SM
 size_t batch_tc_staging_bytes(int d) {
-    return (size_t)num_sms() * BTC_MAX_CTAS_PER_SM * 128 * (2 * (size_t)d + 16) * sizeof(__nv_bfloat16);
+    const size_t rows = (size_t)num_sms() * BTC_MAX_CTAS_PER_SM * 128;
+    const size_t ops = (rows * (2 * (size_t)d + 16) * sizeof(__nv_bfloat16) + 255) / 256 * 256;
+    return ops + rows * (size_t)d * sizeof(long long);
 }
 
 template <int D>
 static cudaError_t launch_btc_t(BatchDev b, const __nv_bfloat16* Z, int phase, int iters, int lo_fast,
                                 const raftgp_csr* g, void* stg, uint32_t* err, cudaStream_t s) {
     using C = BtcCfg<D>;
-    const int grid = num_sms() * C::CTAS;   // the staging area holds up to that many x 128 rows
+    auto kern = k_batch_lloyd_tc<D>;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)) != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    // the CTAs that can be resident at once (at most BTC_MAX_CTAS_PER_SM per SM, which the
+    // staging area is sized for)
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BTC_THREADS, C::SMEM)) != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > BTC_MAX_CTAS_PER_SM) per_sm = BTC_MAX_CTAS_PER_SM;
+    const int grid = num_sms() * per_sm;
     BtcArgs a;
     a.b = b;
     a.Z = Z;
@@ -484,18 +502,20 @@ static cudaError_t launch_btc_t(BatchDev b, const __nv_bfloat16* Z, int phase, i
     a.stg_hi = reinterpret_cast<__nv_bfloat16*>(stg);
     a.stg_lo = a.stg_hi + (size_t)grid * 128 * D;
     a.stg_aug = a.stg_lo + (size_t)grid * 128 * D;
+    {
+        const size_t rows = (size_t)num_sms() * BTC_MAX_CTAS_PER_SM * 128;   // as batch_tc_staging_bytes
+        const size_t ops = (rows * (2 * (size_t)D + 16) * sizeof(__nv_bfloat16) + 255) / 256 * 256;
+        a.gsums = reinterpret_cast<long long*>(reinterpret_cast<char*>(stg) + ops);
+    }
     a.band = tc_tie_band(D);
     a.err = err;
     const CUtensorMapSwizzle swz = C::ATOM_BYTES == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
     CUtensorMap tz, th, tl, tg;
-    cudaError_t e;
     if ((e = make_map_bf16(&tz, Z, D, b.total_n, C::ATOM, 128, swz)) != cudaSuccess) return e;
     if ((e = make_map_bf16(&th, a.stg_hi, D, (int64_t)grid * 128, C::ATOM, 128, swz)) != cudaSuccess) return e;
     if ((e = make_map_bf16(&tl, a.stg_lo, D, (int64_t)grid * 128, C::ATOM, 128, swz)) != cudaSuccess) return e;
     if ((e = make_map_bf16(&tg, a.stg_aug, 16, (int64_t)grid * 128, 16, 128, CU_TENSOR_MAP_SWIZZLE_32B)) != cudaSuccess)
         return e;
-    auto kern = k_batch_lloyd_tc<D>;
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM)) != cudaSuccess) return e;
     kern<<<grid, BTC_THREADS, C::SMEM, s>>>(a, tz, th, tl, tg);
     return cudaGetLastError();
 }

@@ -257,7 +257,7 @@ cudaError_t launch_batch_seed(BatchDev b, const void* Z, int zdtype, int d, uint
 cudaError_t launch_batch_lloyd(BatchDev b, const void* Z, int zdtype, int d, int phase, int iters, const raftgp_csr* g,
                                int threads, int ppt, cudaStream_t s);
 // tensor-core Lloyd of the batched form (BF16 embeddings, d = 32 or 64); stg: a device staging
-// area of batch_tc_staging_bytes(d) for the centroid operands
+// area of batch_tc_staging_bytes(d) for the centroid operands and the per-CTA centroid sums
 size_t batch_tc_staging_bytes(int d);
 cudaError_t launch_batch_lloyd_tc(BatchDev b, const void* Z, int d, int phase, int iters, int lo_fast,
                                   const raftgp_csr* g, void* stg, uint32_t* err, cudaStream_t s);
