@@ -307,32 +307,37 @@ __global__ void __launch_bounds__(BTC_THREADS, BTC_MAX_CTAS_PER_SM)
                 for (int t = 0; t < T; ++t) {
                     const uint32_t q = n_a + t;
                     const int buf = q & 1;
-                    const bool ok = __all_sync(0xffffffffu, mbar_wait(&ctl.acc_full[buf], (q >> 1) & 1, &ctl, a.err));
                     const int64_t i = 128 * (int64_t)t + row;
+                    // the point's previous label, loaded before the wait (only this thread
+                    // writes it, one pass earlier)
+                    const int ol_pre = (!fin && i < n) ? (int)lab[i] : -1;
+                    const bool ok = __all_sync(0xffffffffu, mbar_wait(&ctl.acc_full[buf], (q >> 1) & 1, &ctl, a.err));
                     float bv = INFINITY, b2 = INFINITY;
                     int bi = -1;
                     if (ok) {
                         tc_fence_after();
                         if (!fin) {
                             // keys: accumulator bits x 64 + (0x48000000 + column in its 64-column slice)
-                            float m0 = INFINITY, m1 = INFINITY;
-                            for (int pc = 0; pc < Np / 32; ++pc) {
-                                uint32_t r[32];
-                                tmem_ld32(lane_base + (uint32_t)(buf * 128 + 32 * pc), r);
-                                const uint32_t c0 = 0x48000000u + 32u * (pc & 1);
+                            // a 64-column slice per tensor-memory load (one wait), a last slice of 32
+                            // columns alone
+                            for (int h = 0; 64 * h < Np; ++h) {
+                                float m0 = INFINITY, m1 = INFINITY;
+                                uint32_t r[64];
+                                const int w = Np - 64 * h >= 64 ? 64 : 32;
+                                if (w == 64) tmem_ld64(lane_base + (uint32_t)(buf * 128 + 64 * h), r);
+                                else tmem_ld32(lane_base + (uint32_t)(buf * 128 + 64 * h), *reinterpret_cast<uint32_t(*)[32]>(r));
 #pragma unroll
-                                for (int k = 0; k < 32; k += 4) {
-                                    m0 = min3f(m0, __uint_as_float(r[k] * 64u + (c0 + k)),
-                                               __uint_as_float(r[k + 1] * 64u + (c0 + k + 1)));
-                                    m1 = min3f(m1, __uint_as_float(r[k + 2] * 64u + (c0 + k + 2)),
-                                               __uint_as_float(r[k + 3] * 64u + (c0 + k + 3)));
+                                for (int k = 0; k < 64; k += 4) {
+                                    if (k < w) {
+                                        m0 = min3f(m0, __uint_as_float(r[k] * 64u + (0x48000000u + k)),
+                                                   __uint_as_float(r[k + 1] * 64u + (0x48000000u + k + 1)));
+                                        m1 = min3f(m1, __uint_as_float(r[k + 2] * 64u + (0x48000000u + k + 2)),
+                                                   __uint_as_float(r[k + 3] * 64u + (0x48000000u + k + 3)));
+                                    }
                                 }
-                                if ((pc & 1) || pc == Np / 32 - 1) {   // end of 64-column slice pc / 2
-                                    const uint32_t kb = __float_as_uint(fminf(m0, m1));
-                                    const float v = __uint_as_float(kb & 0xFFFFFFC0u);
-                                    if (v < bv) { bv = v; bi = 64 * (pc >> 1) + (int)(kb & 63u); }
-                                    m0 = m1 = INFINITY;
-                                }
+                                const uint32_t kb = __float_as_uint(fminf(m0, m1));
+                                const float v = __uint_as_float(kb & 0xFFFFFFC0u);
+                                if (v < bv) { bv = v; bi = 64 * h + (int)(kb & 63u); }
                             }
                         } else {
                             // exact best and second best of ||mu||^2 + 4 - 2 z.mu
@@ -369,7 +374,7 @@ __global__ void __launch_bounds__(BTC_THREADS, BTC_MAX_CTAS_PER_SM)
                                 }
                                 lab[i] = (int16_t)nl;
                             } else {
-                                int ol = lab[i];
+                                int ol = ol_pre;
                                 if (ol < -1 || ol >= K) {   // never expected: reported, taken as unassigned
                                     flag_error(a.err, DERR_BOUNDS);
                                     ol = -1;
@@ -390,24 +395,43 @@ __global__ void __launch_bounds__(BTC_THREADS, BTC_MAX_CTAS_PER_SM)
                     if (!fin) {
                         // the tile's changes: a warp per change, lanes over coordinates, each moving
                         // the point's 2^-40 fixed-point row from its old cluster's sum to its new one
+                        // Eight of the warp's changes at a time: their rows are loaded before any
+                        // of their reductions is issued (the reductions would otherwise keep each
+                        // row load waiting on the one before), then applied in order.
                         const int nch = ctl.nchg[t & 1] < 128 ? ctl.nchg[t & 1] : 128;
-                        for (int e = ew; e < nch; e += 4) {
-                            const int4 r = ctl.chg[t & 1][e];
-                            if (r.x < 0 || r.x >= n || r.y < -1 || r.y >= K || r.z < 0 || r.z >= K) {
-                                if (lane == 0) flag_error(a.err, DERR_BOUNDS);
-                                continue;
+                        constexpr int GCH = 8, KPL = D / 32;   // changes per group, coordinates per lane
+                        for (int e0 = ew; e0 < nch; e0 += 4 * GCH) {
+                            int4 r[GCH];
+                            float zv[GCH][KPL];
+#pragma unroll
+                            for (int gq = 0; gq < GCH; ++gq) {
+                                const int e = e0 + 4 * gq;
+                                r[gq] = e < nch ? ctl.chg[t & 1][e] : make_int4(-1, -1, -1, 0);
+                                const bool okr = e < nch && r[gq].x >= 0 && r[gq].x < n && r[gq].y >= -1 && r[gq].y < K &&
+                                                 r[gq].z >= 0 && r[gq].z < K;
+                                if (e < nch && !okr && lane == 0) flag_error(a.err, DERR_BOUNDS);
+                                if (!okr) r[gq].x = -1;
+#pragma unroll
+                                for (int kk = 0; kk < KPL; ++kk)
+                                    zv[gq][kk] = okr ? __bfloat162float(a.Z[(o + r[gq].x) * D + lane + 32 * kk]) : 0.f;
                             }
-                            const __nv_bfloat16* zi = a.Z + (o + r.x) * D;
-                            if (lane == 0) {
-                                atomicAdd(cnt + r.z, 1);
-                                if (r.y >= 0) atomicSub(cnt + r.y, 1);
-                            }
-                            for (int k = lane; k < D; k += 32) {
-                                const long long v = __float2ll_rn(__bfloat162float(zi[k]) * FIXED_SCALE_F);
-                                atomicAdd(reinterpret_cast<unsigned long long*>(sums + r.z * D + k), (unsigned long long)v);
-                                if (r.y >= 0)
-                                    atomicAdd(reinterpret_cast<unsigned long long*>(sums + r.y * D + k),
-                                              (unsigned long long)(-v));
+#pragma unroll
+                            for (int gq = 0; gq < GCH; ++gq) {
+                                if (r[gq].x < 0) continue;
+                                if (lane == 0) {
+                                    atomicAdd(cnt + r[gq].z, 1);
+                                    if (r[gq].y >= 0) atomicSub(cnt + r[gq].y, 1);
+                                }
+#pragma unroll
+                                for (int kk = 0; kk < KPL; ++kk) {
+                                    const int k = lane + 32 * kk;
+                                    const long long v = __float2ll_rn(zv[gq][kk] * FIXED_SCALE_F);
+                                    atomicAdd(reinterpret_cast<unsigned long long*>(sums + r[gq].z * D + k),
+                                              (unsigned long long)v);
+                                    if (r[gq].y >= 0)
+                                        atomicAdd(reinterpret_cast<unsigned long long*>(sums + r[gq].y * D + k),
+                                                  (unsigned long long)(-v));
+                                }
                             }
                         }
                     }
@@ -435,11 +459,29 @@ __global__ void __launch_bounds__(BTC_THREADS, BTC_MAX_CTAS_PER_SM)
                 continue;
             }
             // FP64 means of the fixed-point sums; empty clusters keep their centroid
-            for (int cc = warp; cc < K; cc += BTC_THREADS / 32) {
-                const int ct = cnt[cc];
-                if (ct <= 0) continue;
-                const double inv = 1.0 / ((double)ct * FIXED_SCALE);
-                for (int k = lane; k < D; k += 32) mu[cc * D + k] = (float)((double)__ldcg(sums + cc * D + k) * inv);
+            {
+                // four of the warp's clusters at a time: their sums are read (through L2) before
+                // any mean is formed
+                constexpr int NW = BTC_THREADS / 32, UC = 4, KPL = D / 32;
+                for (int cc0 = warp; cc0 < K; cc0 += NW * UC) {
+                    int ct[UC];
+                    long long sv[UC][KPL];
+#pragma unroll
+                    for (int u = 0; u < UC; ++u) {
+                        const int cc = cc0 + NW * u;
+                        ct[u] = cc < K ? cnt[cc] : 0;
+#pragma unroll
+                        for (int kk = 0; kk < KPL; ++kk) sv[u][kk] = ct[u] > 0 ? __ldcg(sums + cc * D + lane + 32 * kk) : 0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < UC; ++u) {
+                        if (ct[u] <= 0) continue;
+                        const int cc = cc0 + NW * u;
+                        const double inv = 1.0 / ((double)ct[u] * FIXED_SCALE);
+#pragma unroll
+                        for (int kk = 0; kk < KPL; ++kk) mu[cc * D + lane + 32 * kk] = (float)((double)sv[u][kk] * inv);
+                    }
+                }
             }
             updated = true;
             __syncthreads();
