@@ -77,6 +77,17 @@ struct BtcCtl {
     int4 chg[2][128];        // (point, old label, new label)
 };
 
+// Coordinate k of row r of a point tile as TMA wrote it into shared memory: 16-byte chunk c of
+// the row sits at chunk c ^ (r & 7) (128-byte rows, 128B swizzle, D = 64) or c ^ ((r >> 1) & 3)
+// (64-byte rows, 64B swizzle, D = 32).
+template <int D>
+__device__ __forceinline__ float tile_coord(const uint8_t* tile, int r, int k) {
+    constexpr int RB = D * 2;
+    const int c = k >> 3;
+    const int pc = RB == 128 ? (c ^ (r & 7)) : (c ^ ((r >> 1) & 3));
+    return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(tile + r * RB + pc * 16 + (k & 7) * 2));
+}
+
 // Barrier of the 128 epilogue threads (warps 2-5) only.
 __device__ __forceinline__ void btc_epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
@@ -177,7 +188,7 @@ __global__ void __launch_bounds__(BTC_THREADS, BTC_MAX_CTAS_PER_SM)
     if (threadIdx.x == 0) {
         for (int q = 0; q < 2; ++q) {
             mbar_init(&ctl.a_full[q], 1);
-            mbar_init(&ctl.a_empty[q], 1);
+            mbar_init(&ctl.a_empty[q], 2);   // the tile's MMAs, and the epilogue's change application
             mbar_init(&ctl.acc_full[q], 1);
             mbar_init(&ctl.acc_empty[q], 128);
         }
@@ -395,9 +406,9 @@ __global__ void __launch_bounds__(BTC_THREADS, BTC_MAX_CTAS_PER_SM)
                     if (!fin) {
                         // the tile's changes: a warp per change, lanes over coordinates, each moving
                         // the point's 2^-40 fixed-point row from its old cluster's sum to its new one
-                        // Eight of the warp's changes at a time: their rows are loaded before any
-                        // of their reductions is issued (the reductions would otherwise keep each
-                        // row load waiting on the one before), then applied in order.
+                        // Eight of the warp's changes at a time, their rows read from the point tile
+                        // in shared memory (kept until this application is done) before any of
+                        // their reductions is issued.
                         const int nch = ctl.nchg[t & 1] < 128 ? ctl.nchg[t & 1] : 128;
                         constexpr int GCH = 8, KPL = D / 32;   // changes per group, coordinates per lane
                         for (int e0 = ew; e0 < nch; e0 += 4 * GCH) {
@@ -413,7 +424,9 @@ __global__ void __launch_bounds__(BTC_THREADS, BTC_MAX_CTAS_PER_SM)
                                 if (!okr) r[gq].x = -1;
 #pragma unroll
                                 for (int kk = 0; kk < KPL; ++kk)
-                                    zv[gq][kk] = okr ? __bfloat162float(a.Z[(o + r[gq].x) * D + lane + 32 * kk]) : 0.f;
+                                    zv[gq][kk] = okr ? tile_coord<D>(sA + buf * C::TILE, (int)(r[gq].x - 128 * (int64_t)t),
+                                                                  lane + 32 * kk)
+                                                     : 0.f;
                             }
 #pragma unroll
                             for (int gq = 0; gq < GCH; ++gq) {
@@ -436,6 +449,7 @@ __global__ void __launch_bounds__(BTC_THREADS, BTC_MAX_CTAS_PER_SM)
                         }
                     }
                     btc_epi_sync();
+                    if (threadIdx.x == 64) mbar_arrive(&ctl.a_empty[buf]);   // the point tile may be refilled
                     if (!fin && threadIdx.x == 64) {
                         ctl.changed += ctl.nchg[t & 1];
                         ctl.nchg[t & 1] = 0;

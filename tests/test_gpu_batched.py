@@ -172,15 +172,16 @@ def test_bf16_batch_equals_single_graph_selection_on_its_embedding(cuda, batch):
     plan32.close()
 
 
+@pytest.mark.parametrize("dims", [DIMS, (64, 64, 64)])
 @pytest.mark.parametrize("engine", ["tc8", "tc"])
-def test_tensor_core_batch_matches_single_graph_tensor_core_selection(cuda, batch, engine):
+def test_tensor_core_batch_matches_single_graph_tensor_core_selection(cuda, batch, engine, dims):
     # tensor-core Lloyd in the batched plan: every graph's candidates, K* and labels equal a
     # single-graph selection with the same engine on the plan's own BF16 embedding (whose final
     # labels are the FP32-nearest centroids of the last Lloyd pass, tested with the single-graph
     # engine); drift against the FP32-engine batch is stated
     sub = batch[:6]
     dg, off = api.concat_graphs(sub, cuda)
-    plan = api.BatchPlan(dg, off, dims=DIMS, dtype="bf16", kmin=2, grid=10, iters=50, seed=2, assign=engine)
+    plan = api.BatchPlan(dg, off, dims=dims, dtype="bf16", kmin=2, grid=10, iters=50, seed=2, assign=engine)
     labels, ks = plan.run()
     plan.check()
     Z = plan.embedding()
@@ -188,7 +189,7 @@ def test_tensor_core_batch_matches_single_graph_tensor_core_selection(cuda, batc
     ck, cmod, cncut, cpass = plan.candidates()
     t = plan.tuning()
     assert t["points_per_thread"] == -1
-    plan32 = api.BatchPlan(dg, off, dims=DIMS, dtype="bf16", kmin=2, grid=10, iters=50, seed=2)
+    plan32 = api.BatchPlan(dg, off, dims=dims, dtype="bf16", kmin=2, grid=10, iters=50, seed=2)
     l32, k32 = plan32.run()
     plan32.check()
     l32, k32 = l32.cpu().numpy(), k32.cpu().numpy()
