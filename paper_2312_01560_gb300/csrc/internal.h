@@ -92,6 +92,9 @@ struct SbmWs {
     double *th, *pre, *tri;             // theta in that order; per-block prefix sums
     unsigned long long *pseg, *pincl;   // segments per block pair, inclusive scan
     unsigned long long *seg_cnt, *seg_incl;   // edges per segment, inclusive scan
+    uint32_t* seg_order;                      // the segments grouped by their expected draws
+    uint8_t* seg_key;                         // each segment's group
+    unsigned long long* bucket;               // group sizes, then their fill cursors
     unsigned long long* tiles;
 };
 int64_t sbm_max_segments(int64_t n, int K);

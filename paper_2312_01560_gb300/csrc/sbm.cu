@@ -210,42 +210,111 @@ __global__ void k_sbm_pair_segs(SbmDev d, unsigned long long* pseg, uint32_t* er
     }
 }
 
-// One thread per global segment: Algorithm 2's loop on the segment.  COUNT mode stores the
-// number of edges; EMIT mode writes them at the segment's offset.
-template <bool EMIT>
-__global__ void __launch_bounds__(128) k_sbm_segments(SbmDev d, int64_t G, unsigned long long* seg_cnt,
-                                                      const unsigned long long* seg_incl, int32_t* src, int32_t* dst,
-                                                      int32_t* weight) {
+// Segment g: its block pair's table and its entry range [t0, t1).
+__device__ __forceinline__ void seg_setup(const SbmDev& d, int64_t g, SbmPairDev& P, int64_t& t0, int64_t& t1) {
+    // pair of segment g: the first p with pincl[p] > g
+    int64_t lo = 0, hi = d.npairs - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (d.pincl[mid] > (unsigned long long)g) hi = mid;
+        else lo = mid + 1;
+    }
+    const int64_t p = lo;
+    const int64_t sg = g - (p == 0 ? 0 : (int64_t)d.pincl[p - 1]);
+    int r, s;
+    pair_rs(d.K, p, r, s);
+    P.tri = r == s;
+    const int64_t orr = boff(d, r), os = boff(d, s);
+    P.nr = (int64_t)d.bincl[r] - orr;
+    P.ns = (int64_t)d.bincl[s] - os;
+    P.nodes_r = d.nodes + orr;
+    P.nodes_s = d.nodes + os;
+    P.th_r = d.th + orr;
+    P.th_s = d.th + os;
+    P.pre_r = d.pre + orr + r;
+    P.pre_s = d.pre + os + s;
+    P.tri_r = d.tri + orr + r;
+    P.tot_s = P.pre_s[P.ns];
+    P.inv_ns = P.ns > 0 ? __ddiv_rn(1.0, (double)P.ns) : 0.0;
+    P.om = d.omega[(int64_t)r * d.K + s];
+    const int64_t size = table_size(P.tri, P.nr, P.ns);
+    t0 = sg * SBM_SEG;
+    t1 = t0 + SBM_SEG < size ? t0 + SBM_SEG : size;
+}
+
+// Work order of the segments: grouped by their expected number of draws (the lambda mass of
+// their entries, on a log scale in SBM_BUCKETS buckets), so that the 32 segments of a warp run
+// loops of similar length.  Which thread runs a segment changes nothing in its draws or in
+// where its edges go.
+constexpr int SBM_BUCKETS = 32;
+__device__ __forceinline__ int seg_bucket(double w) {
+    if (!(w > 0.0)) return 0;                       // zero (and NaN: never sampled, flagged before)
+    if (!(w < 1.0e9)) return SBM_BUCKETS - 1;       // huge or infinite
+    const int b = (int)floor(2.0 * log2(1.0 + w));
+    return b < SBM_BUCKETS - 1 ? b : SBM_BUCKETS - 1;
+}
+
+// Pass 1: each segment's bucket, and the buckets' sizes (block histograms added once per block).
+__global__ void __launch_bounds__(256) k_sbm_seg_bucket(SbmDev d, int64_t G, uint8_t* key, unsigned long long* bcount) {
+    __shared__ unsigned int h[SBM_BUCKETS];
+    for (int b = threadIdx.x; b < SBM_BUCKETS; b += blockDim.x) h[b] = 0;
+    __syncthreads();
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G; g += (int64_t)gridDim.x * blockDim.x) {
-        // pair of segment g: the first p with pincl[p] > g
-        int64_t lo = 0, hi = d.npairs - 1;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (d.pincl[mid] > (unsigned long long)g) hi = mid;
-            else lo = mid + 1;
-        }
-        const int64_t p = lo;
-        const int64_t sg = g - (p == 0 ? 0 : (int64_t)d.pincl[p - 1]);
-        int r, s;
-        pair_rs(d.K, p, r, s);
         SbmPairDev P;
-        P.tri = r == s;
-        const int64_t orr = boff(d, r), os = boff(d, s);
-        P.nr = (int64_t)d.bincl[r] - orr;
-        P.ns = (int64_t)d.bincl[s] - os;
-        P.nodes_r = d.nodes + orr;
-        P.nodes_s = d.nodes + os;
-        P.th_r = d.th + orr;
-        P.th_s = d.th + os;
-        P.pre_r = d.pre + orr + r;
-        P.pre_s = d.pre + os + s;
-        P.tri_r = d.tri + orr + r;
-        P.tot_s = P.pre_s[P.ns];
-        P.inv_ns = P.ns > 0 ? __ddiv_rn(1.0, (double)P.ns) : 0.0;
-        P.om = d.omega[(int64_t)r * d.K + s];
-        const int64_t size = table_size(P.tri, P.nr, P.ns);
-        const int64_t t0 = sg * SBM_SEG;
-        const int64_t t1 = t0 + SBM_SEG < size ? t0 + SBM_SEG : size;
+        int64_t t0, t1;
+        seg_setup(d, g, P, t0, t1);
+        const int b = seg_bucket(__dsub_rn(prefix_mass(P, t1), prefix_mass(P, t0)));
+        key[g] = (uint8_t)b;
+        atomicAdd(&h[b], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < SBM_BUCKETS; b += blockDim.x)
+        if (h[b]) atomicAdd(bcount + b, (unsigned long long)h[b]);
+}
+
+// The buckets' starts (exclusive scan, one thread) and their fill cursors.
+__global__ void k_sbm_seg_starts(const unsigned long long* bcount, unsigned long long* cursor) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long run = 0;
+    for (int b = 0; b < SBM_BUCKETS; ++b) {
+        cursor[b] = run;
+        run += bcount[b];
+    }
+}
+
+// Pass 2: each block reserves its segments' places bucket by bucket (one global atomic per
+// bucket and block) and writes them there.
+__global__ void __launch_bounds__(256) k_sbm_seg_scatter(int64_t G, const uint8_t* key, unsigned long long* cursor,
+                                                         uint32_t* order) {
+    __shared__ unsigned int h[SBM_BUCKETS];
+    __shared__ unsigned long long base[SBM_BUCKETS];
+    for (int64_t g0 = (int64_t)blockIdx.x * blockDim.x; g0 < G; g0 += (int64_t)gridDim.x * blockDim.x) {
+        for (int b = threadIdx.x; b < SBM_BUCKETS; b += blockDim.x) h[b] = 0;
+        __syncthreads();
+        const int64_t g = g0 + threadIdx.x;
+        const int b = g < G ? (int)key[g] : -1;
+        unsigned int rank = 0;
+        if (b >= 0) rank = atomicAdd(&h[b], 1u);
+        __syncthreads();
+        for (int q = threadIdx.x; q < SBM_BUCKETS; q += blockDim.x)
+            base[q] = h[q] ? atomicAdd(cursor + q, (unsigned long long)h[q]) : 0ull;
+        __syncthreads();
+        if (b >= 0) order[base[b] + rank] = (uint32_t)g;
+        __syncthreads();
+    }
+}
+
+// One thread per global segment (taken in `order`): Algorithm 2's loop on the segment.  COUNT
+// mode stores the number of edges; EMIT mode writes them at the segment's offset.
+template <bool EMIT>
+__global__ void __launch_bounds__(128) k_sbm_segments(SbmDev d, int64_t G, const uint32_t* order,
+                                                      unsigned long long* seg_cnt, const unsigned long long* seg_incl,
+                                                      int32_t* src, int32_t* dst, int32_t* weight) {
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < G; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = order ? (int64_t)order[idx] : idx;
+        SbmPairDev P;
+        int64_t t0, t1;
+        seg_setup(d, g, P, t0, t1);
         const double Fend = prefix_mass(P, t1);
         int64_t out = EMIT ? (int64_t)seg_incl[g] - (int64_t)seg_cnt[g] : 0;
         const int64_t cap = EMIT ? (int64_t)seg_cnt[g] : 0;   // the count pass's edges of this segment
@@ -411,6 +480,9 @@ SbmWs carve_sbm(Carver& c, int64_t n, int K) {
     w.pincl = c.take<unsigned long long>(npairs);
     w.seg_cnt = c.take<unsigned long long>(G);
     w.seg_incl = c.take<unsigned long long>(G);
+    w.seg_order = c.take<uint32_t>(G);
+    w.seg_key = c.take<uint8_t>(G);
+    w.bucket = c.take<unsigned long long>(2 * SBM_BUCKETS);
     w.tiles = c.take<unsigned long long>((most + SCAN_TILE - 1) / SCAN_TILE + 1);
     return w;
 }
@@ -440,8 +512,18 @@ cudaError_t sbm_count(const raftgp_sbm* p, const SbmWs& w, int64_t* G_out, int64
     if (herr) return cudaErrorInvalidValue;
     if ((int64_t)G > sbm_max_segments(n, K)) return cudaErrorInvalidValue;
     if (G > 0) {
-        k_sbm_segments<false><<<grid_for((int64_t)G, 128), 128, 0, s>>>(d, (int64_t)G, w.seg_cnt, nullptr, nullptr,
-                                                                         nullptr, nullptr);
+        // segment indices in the work order fit 32 bits up to 2^32 segments; beyond, the
+        // segments run in index order
+        const uint32_t* order = G < (1ull << 32) ? w.seg_order : nullptr;
+        if (order) {
+            cudaMemsetAsync(w.bucket, 0, sizeof(unsigned long long) * SBM_BUCKETS, s);
+            k_sbm_seg_bucket<<<grid_for((int64_t)G, 256), 256, 0, s>>>(d, (int64_t)G, w.seg_key, w.bucket);
+            k_sbm_seg_starts<<<1, 32, 0, s>>>(w.bucket, w.bucket + SBM_BUCKETS);
+            k_sbm_seg_scatter<<<grid_for((int64_t)G, 256), 256, 0, s>>>((int64_t)G, w.seg_key, w.bucket + SBM_BUCKETS,
+                                                                         w.seg_order);
+        }
+        k_sbm_segments<false><<<grid_for((int64_t)G, 128), 128, 0, s>>>(d, (int64_t)G, order, w.seg_cnt, nullptr,
+                                                                         nullptr, nullptr, nullptr);
         scan_incl(w.seg_cnt, (int64_t)G, w.seg_incl, w.tiles, s);
     }
     unsigned long long m = 0;
@@ -460,7 +542,8 @@ cudaError_t sbm_emit(const raftgp_sbm* p, const SbmWs& w, int64_t G, int32_t* sr
     if (G <= 0) return cudaSuccess;
     SbmDev d{p->n, K, p->seed, p->omega, w.bincl, w.nodes, w.th, w.pre, w.tri, w.pincl, npairs};
     ProfScope ps(s, PF_OTHER, 1);
-    k_sbm_segments<true><<<grid_for(G, 128), 128, 0, s>>>(d, G, w.seg_cnt, w.seg_incl, src, dst, weight);
+    const uint32_t* order = (unsigned long long)G < (1ull << 32) ? w.seg_order : nullptr;
+    k_sbm_segments<true><<<grid_for(G, 128), 128, 0, s>>>(d, G, order, w.seg_cnt, w.seg_incl, src, dst, weight);
     return cudaGetLastError();
 }
 
