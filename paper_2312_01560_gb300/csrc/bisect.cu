@@ -243,12 +243,17 @@ __global__ void k_bs_seed1(BisectDev b, const T* __restrict__ Z, int S, uint64_t
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_bs_assign(BisectDev b, const T* __restrict__ Z, int64_t M, int pass) {
     __shared__ long long ssum[BS_WIN][2][D];
+    __shared__ float smu[BS_WIN][2 * D];   // the window's centroids
     __shared__ int scnt[BS_WIN][2], sch[BS_WIN];
     __shared__ int s_first;
+    constexpr int E = Vec<T>::E;           // elements per 16-byte load
     for (int64_t p0 = (int64_t)blockIdx.x * blockDim.x; p0 < M; p0 += (int64_t)gridDim.x * blockDim.x) {
         __syncthreads();
-        if (threadIdx.x == 0) s_first = b.pos_set[p0];
+        const int sf = b.pos_set[p0];
+        if (threadIdx.x == 0) s_first = sf;
         for (int t = threadIdx.x; t < BS_WIN * 2 * D; t += blockDim.x) (&ssum[0][0][0])[t] = 0;
+        for (int t = threadIdx.x; t < BS_WIN * 2 * D; t += blockDim.x)
+            (&smu[0][0])[t] = sf + t / (2 * D) < b.cap_sets ? b.mu[(int64_t)sf * 2 * D + t] : 0.f;
         for (int t = threadIdx.x; t < BS_WIN * 2; t += blockDim.x) (&scnt[0][0])[t] = 0;
         for (int t = threadIdx.x; t < BS_WIN; t += blockDim.x) sch[t] = 0;
         __syncthreads();
@@ -256,13 +261,24 @@ __global__ void __launch_bounds__(256) k_bs_assign(BisectDev b, const T* __restr
         if (p < M) {
             const int s = b.pos_set[p];
             if (b.active[s]) {
+                // the point's row in 16-byte loads, the centroids of the window's sets from
+                // shared memory; products added over ascending coordinates
                 const T* zi = Z + (int64_t)b.perm[p] * D;
-                const float* m0 = b.mu + (int64_t)s * 2 * D;
+                float z[D];
+#pragma unroll
+                for (int k0 = 0; k0 < D; k0 += E) {
+                    float v[E];
+                    Vec<T>::load(zi + k0, v);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) z[k0 + e] = v[e];
+                }
+                const int ws = s - sf;
+                const float* m0 = ws >= 0 && ws < BS_WIN ? smu[ws] : b.mu + (int64_t)s * 2 * D;
                 float d0 = 0.f, d1 = 0.f;
+#pragma unroll
                 for (int k = 0; k < D; ++k) {
-                    const float x = load_elem(zi, k);
-                    d0 = fmaf(x, m0[k], d0);
-                    d1 = fmaf(x, m0[D + k], d1);
+                    d0 = fmaf(z[k], m0[k], d0);
+                    d1 = fmaf(z[k], m0[D + k], d1);
                 }
                 // the FP32 engine's selection: ascending centroids, strict improvement
                 float bv = INFINITY;
@@ -279,8 +295,9 @@ __global__ void __launch_bounds__(256) k_bs_assign(BisectDev b, const T* __restr
                         atomicAdd(&sch[w], 1);
                         atomicAdd(&scnt[w][nl], 1);
                         if (ol >= 0) atomicSub(&scnt[w][ol], 1);
+#pragma unroll
                         for (int k = 0; k < D; ++k) {
-                            const long long v = __float2ll_rn(load_elem(zi, k) * FIXED_SCALE_F);
+                            const long long v = __float2ll_rn(z[k] * FIXED_SCALE_F);
                             atomicAdd(reinterpret_cast<unsigned long long*>(&ssum[w][nl][k]), (unsigned long long)v);
                             if (ol >= 0) atomicAdd(reinterpret_cast<unsigned long long*>(&ssum[w][ol][k]), (unsigned long long)(-v));
                         }
@@ -288,8 +305,9 @@ __global__ void __launch_bounds__(256) k_bs_assign(BisectDev b, const T* __restr
                         atomicAdd(b.changed + (pass & 1) * b.cap_sets + s, 1);
                         atomicAdd(b.counts + s * 2 + nl, 1);
                         if (ol >= 0) atomicSub(b.counts + s * 2 + ol, 1);
+#pragma unroll
                         for (int k = 0; k < D; ++k) {
-                            const long long v = __float2ll_rn(load_elem(zi, k) * FIXED_SCALE_F);
+                            const long long v = __float2ll_rn(z[k] * FIXED_SCALE_F);
                             atomicAdd(reinterpret_cast<unsigned long long*>(b.sums + ((int64_t)s * 2 + nl) * D + k),
                                       (unsigned long long)v);
                             if (ol >= 0)
