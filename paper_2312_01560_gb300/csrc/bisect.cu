@@ -135,15 +135,22 @@ void scan_incl(const unsigned long long* in, int64_t n, unsigned long long* out,
 __device__ __forceinline__ bool bs_small(const BisectDev& b, int s) { return b.set_n[s] <= 2 * b.eps + 1 || b.depth >= 62; }
 
 // positions -> set, nodes -> set, labels cleared
-__global__ void k_bs_setup(BisectDev b, int S) {
-    for (int s = blockIdx.x; s < S; s += gridDim.x) {
-        const int64_t off = b.set_off[s], n = b.set_n[s];
-        for (int64_t p = off + threadIdx.x; p < off + n; p += blockDim.x) {
-            b.pos_set[p] = s;
-            b.node_set[b.perm[p]] = s;
-            b.node_lab[b.perm[p]] = -1;
-            b.lab[p] = -1;
+// Thread per position (the sets of a level are ascending ranges of positions; one set can hold
+// every node, so the work is spread over positions, not sets): the position's set by binary
+// search over the set offsets.
+__global__ void k_bs_setup(BisectDev b, int S, int64_t M) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < M; p += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = S - 1;
+        while (lo < hi) {   // the last set starting at or before p
+            const int mid = (lo + hi + 1) >> 1;
+            if (b.set_off[mid] <= p) lo = mid;
+            else hi = mid - 1;
         }
+        if (S < 1 || p < b.set_off[lo] || p >= b.set_off[lo] + b.set_n[lo]) continue;
+        b.pos_set[p] = lo;
+        b.node_set[b.perm[p]] = lo;
+        b.node_lab[b.perm[p]] = -1;
+        b.lab[p] = -1;
     }
 }
 
@@ -382,21 +389,31 @@ __global__ void __launch_bounds__(256) k_bs_lmod(BisectDev b, Csr<OffT> g, int64
         if (threadIdx.x == 0) s_first = b.pos_set[p0];
         for (int t = threadIdx.x; t < BS_WIN * 5; t += blockDim.x) (&sv[0][0])[t] = 0;
         __syncthreads();
-        const int64_t p = p0 + threadIdx.x;
-        if (p < M) {
+        // a warp per position of the chunk, its lanes over the node's neighbours (a power-law
+        // graph's hubs have thousands)
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        for (int r = wid; r < (int)blockDim.x; r += (int)(blockDim.x >> 5)) {
+            const int64_t p = p0 + r;
+            if (p >= M) break;
             const int s = b.pos_set[p];
             const int c = b.lab[p];
-            if (c >= 0) {
-                const int i = b.perm[p];
-                const int64_t e0 = g.begin(i), e1 = g.end(i);
-                unsigned long long mu2 = 0, mc2 = 0;
-                for (int64_t q = e0; q < e1; ++q) {
-                    const int j = g.col[q];
-                    if (b.node_set[j] == s) {
-                        ++mu2;
-                        if (b.node_lab[j] == c) ++mc2;
-                    }
+            if (c < 0) continue;
+            const int i = b.perm[p];
+            const int64_t e0 = g.begin(i), e1 = g.end(i);
+            unsigned long long mu2 = 0, mc2 = 0;
+            for (int64_t q = e0 + lane; q < e1; q += 32) {
+                const int j = g.col[q];
+                if (b.node_set[j] == s) {
+                    ++mu2;
+                    if (b.node_lab[j] == c) ++mc2;
                 }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                mu2 += __shfl_xor_sync(0xffffffffu, mu2, o);
+                mc2 += __shfl_xor_sync(0xffffffffu, mc2, o);
+            }
+            if (lane == 0) {
                 const unsigned long long deg = (unsigned long long)(e1 - e0);
                 const int w = s - s_first;
                 if (w < BS_WIN) {
@@ -559,7 +576,7 @@ static cudaError_t bisect_t(const raftgp_csr* g, const T* Z, BisectDev b, int it
     Csr<int32_t> c32{g->n, g->nnz, (const int32_t*)g->row_ptr, g->col};
     for (int depth = 0; S > 0; ++depth) {
         b.depth = depth;
-        k_bs_setup<<<S < 65535 ? S : 65535, 256, 0, s>>>(b, S);
+        k_bs_setup<<<grid1(M), 256, 0, s>>>(b, S, M);
         if (b.dirty) {
             cudaMemsetAsync(b.flag, 0, sizeof(int32_t) * (size_t)S, s);
             k_bs_dirty<<<grid1(M), 256, 0, s>>>(b, M);
