@@ -248,7 +248,7 @@ __global__ void k_bs_seed1(BisectDev b, const T* __restrict__ Z, int S, uint64_t
 // changes of the first BS_WIN sets its positions cover in shared memory; positions of later
 // sets use global atomics directly.
 template <typename T, int D>
-__global__ void __launch_bounds__(256) k_bs_assign(BisectDev b, const T* __restrict__ Z, int64_t M, int pass) {
+__global__ void __launch_bounds__(256, 4) k_bs_assign(BisectDev b, const T* __restrict__ Z, int64_t M, int pass) {
     __shared__ long long ssum[BS_WIN][2][D];
     __shared__ float smu[BS_WIN][2 * D];   // the window's centroids
     __shared__ int scnt[BS_WIN][2], sch[BS_WIN];
@@ -271,21 +271,18 @@ __global__ void __launch_bounds__(256) k_bs_assign(BisectDev b, const T* __restr
                 // the point's row in 16-byte loads, the centroids of the window's sets from
                 // shared memory; products added over ascending coordinates
                 const T* zi = Z + (int64_t)b.perm[p] * D;
-                float z[D];
-#pragma unroll
+                const int ws = s - sf;
+                const float* m0 = ws >= 0 && ws < BS_WIN ? smu[ws] : b.mu + (int64_t)s * 2 * D;
+                float d0 = 0.f, d1 = 0.f;
+#pragma unroll 2
                 for (int k0 = 0; k0 < D; k0 += E) {
                     float v[E];
                     Vec<T>::load(zi + k0, v);
 #pragma unroll
-                    for (int e = 0; e < E; ++e) z[k0 + e] = v[e];
-                }
-                const int ws = s - sf;
-                const float* m0 = ws >= 0 && ws < BS_WIN ? smu[ws] : b.mu + (int64_t)s * 2 * D;
-                float d0 = 0.f, d1 = 0.f;
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    d0 = fmaf(z[k], m0[k], d0);
-                    d1 = fmaf(z[k], m0[D + k], d1);
+                    for (int e = 0; e < E; ++e) {
+                        d0 = fmaf(v[e], m0[k0 + e], d0);
+                        d1 = fmaf(v[e], m0[D + k0 + e], d1);
+                    }
                 }
                 // the FP32 engine's selection: ascending centroids, strict improvement
                 float bv = INFINITY;
@@ -302,19 +299,24 @@ __global__ void __launch_bounds__(256) k_bs_assign(BisectDev b, const T* __restr
                         atomicAdd(&sch[w], 1);
                         atomicAdd(&scnt[w][nl], 1);
                         if (ol >= 0) atomicSub(&scnt[w][ol], 1);
+                        for (int k0 = 0; k0 < D; k0 += E) {
+                            float zv[E];
+                            Vec<T>::load(zi + k0, zv);
 #pragma unroll
-                        for (int k = 0; k < D; ++k) {
-                            const long long v = __float2ll_rn(z[k] * FIXED_SCALE_F);
-                            atomicAdd(reinterpret_cast<unsigned long long*>(&ssum[w][nl][k]), (unsigned long long)v);
-                            if (ol >= 0) atomicAdd(reinterpret_cast<unsigned long long*>(&ssum[w][ol][k]), (unsigned long long)(-v));
+                            for (int e = 0; e < E; ++e) {
+                                const int k = k0 + e;
+                                const long long v = __float2ll_rn(zv[e] * FIXED_SCALE_F);
+                                atomicAdd(reinterpret_cast<unsigned long long*>(&ssum[w][nl][k]), (unsigned long long)v);
+                                if (ol >= 0)
+                                    atomicAdd(reinterpret_cast<unsigned long long*>(&ssum[w][ol][k]), (unsigned long long)(-v));
+                            }
                         }
                     } else {
                         atomicAdd(b.changed + (pass & 1) * b.cap_sets + s, 1);
                         atomicAdd(b.counts + s * 2 + nl, 1);
                         if (ol >= 0) atomicSub(b.counts + s * 2 + ol, 1);
-#pragma unroll
                         for (int k = 0; k < D; ++k) {
-                            const long long v = __float2ll_rn(z[k] * FIXED_SCALE_F);
+                            const long long v = __float2ll_rn(load_elem(zi, k) * FIXED_SCALE_F);
                             atomicAdd(reinterpret_cast<unsigned long long*>(b.sums + ((int64_t)s * 2 + nl) * D + k),
                                       (unsigned long long)v);
                             if (ol >= 0)
