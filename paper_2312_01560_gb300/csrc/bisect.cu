@@ -248,7 +248,7 @@ __global__ void k_bs_seed1(BisectDev b, const T* __restrict__ Z, int S, uint64_t
 // changes of the first BS_WIN sets its positions cover in shared memory; positions of later
 // sets use global atomics directly.
 template <typename T, int D>
-__global__ void __launch_bounds__(256, 4) k_bs_assign(BisectDev b, const T* __restrict__ Z, int64_t M, int pass) {
+__global__ void __launch_bounds__(256, 6) k_bs_assign(BisectDev b, const T* __restrict__ Z, int64_t M, int pass) {
     __shared__ long long ssum[BS_WIN][2][D];
     __shared__ float smu[BS_WIN][2 * D];   // the window's centroids
     __shared__ int scnt[BS_WIN][2], sch[BS_WIN];
