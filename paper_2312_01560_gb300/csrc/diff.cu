@@ -222,15 +222,21 @@ constexpr int SK = 128;   // padded soft-assignment width
 template <int D>
 __global__ void __launch_bounds__(256) k_soft_assign(int64_t n, const float* __restrict__ Z, const float* __restrict__ mu,
                                                      int K, float tau, float* __restrict__ S) {
-    extern __shared__ float smu[];   // K x D
-    for (int t = threadIdx.x; t < K * D; t += blockDim.x) smu[t] = mu[t];
+    // K rows of D + 1 floats: lane c reads row c, so the padded stride puts the 32 lanes'
+    // words in 32 different banks
+    constexpr int DP = D + 1;
+    extern __shared__ float smu[];   // K x DP
+    for (int t = threadIdx.x; t < K * D; t += blockDim.x) smu[(t / D) * DP + t % D] = mu[t];
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
         float z[D];
 #pragma unroll
-        for (int k = 0; k < D; ++k) z[k] = __ldg(Z + i * D + k);
+        for (int k = 0; k < D; k += 4) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(Z + i * D + k));
+            z[k] = v.x; z[k + 1] = v.y; z[k + 2] = v.z; z[k + 3] = v.w;
+        }
         float lg[4], mx = -INFINITY;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -240,7 +246,7 @@ __global__ void __launch_bounds__(256) k_soft_assign(int64_t n, const float* __r
                 float s = 0.f;
 #pragma unroll 8
                 for (int k = 0; k < D; ++k) {
-                    const float t = z[k] - smu[c * D + k];
+                    const float t = z[k] - smu[c * DP + k];
                     s = fmaf(t, t, s);
                 }
                 lg[u] = -s / tau;
@@ -510,7 +516,7 @@ int softmod_blocks(int64_t n) {
 cudaError_t launch_soft_assign(int64_t n, int d, const float* Z, const float* mu, int K, float tau, float* S,
                                cudaStream_t s) {
     ProfScope ps(s, PF_DIFF_LOSS, 1);
-    const size_t smem = (size_t)K * d * sizeof(float);
+    const size_t smem = (size_t)K * (d + 1) * sizeof(float);   // rows padded to d + 1 floats
     const int blocks = grid_for(n);
     switch (d) {
         case 32: k_soft_assign<32><<<blocks, 256, smem, s>>>(n, Z, mu, K, tau, S); break;
