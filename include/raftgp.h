@@ -398,6 +398,35 @@ raftgp_status raftgp_softmod_loss(const raftgp_csr* g, const float* Z, int32_t d
                                   float tau, double* loss, float* dZ, void* ws, size_t ws_bytes,
                                   raftgp_stream_t stream);
 
+/* The same calls against a graph checked once.  A tuning loop makes these calls many times
+ * per second: the one-shot calls above check the graph on the device and synchronise on
+ * every call, the plan does so once, at creation.
+ *
+ * raftgp_diff_plan_create validates g (RAFTGP_EINVAL for a malformed graph, no plan made),
+ * computes its degrees and the Eq. 6 normalisation into ws and synchronises the stream once.
+ * width (32, 64 or 128) bounds every layer width and d of later calls, K (0..128) every
+ * centroid count (0: no loss calls); ws holds at least raftgp_diff_workspace_size(n, width, K)
+ * bytes.  The plan keeps copies of g's pointers and of ws: the graph's arrays and ws must
+ * stay allocated and unchanged until raftgp_diff_plan_destroy.  The calls on a plan share
+ * the scratch in ws, so they must be ordered on one stream (or the caller synchronises
+ * between streams).  Each is asynchronous; argument errors are reported before any launch.
+ *
+ * raftgp_diff_plan_layer_forward / _layer_backward: as raftgp_gcn_layer_forward / _backward.
+ * raftgp_diff_plan_softmod_loss: as raftgp_softmod_loss, except that `loss` is a DEVICE
+ * pointer to one double, written on the stream (nothing is read back). */
+typedef struct raftgp_diff_plan raftgp_diff_plan;   /* opaque */
+raftgp_status raftgp_diff_plan_create(const raftgp_csr* g, int32_t width, int32_t K, void* ws, size_t ws_bytes,
+                                      raftgp_stream_t stream, raftgp_diff_plan** plan);
+raftgp_status raftgp_diff_plan_layer_forward(const raftgp_diff_plan* plan, const float* H_in, int32_t lin,
+                                             const float* W, int32_t lout, float* H_out, raftgp_stream_t stream);
+raftgp_status raftgp_diff_plan_layer_backward(const raftgp_diff_plan* plan, const float* H_in, int32_t lin,
+                                              const float* W, int32_t lout, const float* dH_out, float* dH_in,
+                                              float* dW, raftgp_stream_t stream);
+raftgp_status raftgp_diff_plan_softmod_loss(const raftgp_diff_plan* plan, const float* Z, int32_t d,
+                                            const float* mu, int32_t K, float tau, double* loss, float* dZ,
+                                            raftgp_stream_t stream);
+void raftgp_diff_plan_destroy(raftgp_diff_plan* plan);
+
 /* Centroids of a labelling: mu (K x d) = the mean of the rows of each label (exact 2^-40
  * fixed-point sums, FP64 mean); an empty label gets a zero row.  labels: int32 in [0, K)
  * (RAFTGP_EINVAL otherwise).  Synchronises. */

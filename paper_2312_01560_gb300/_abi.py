@@ -26,6 +26,8 @@ EXPORTS = ("raftgp_workspace_size", "raftgp_embed", "raftgp_select", "raftgp_par
            "raftgp_kmeanspp", "raftgp_kmeanspp_noalloc", "raftgp_lloyd", "raftgp_lloyd_workspace_size", "raftgp_profile_enable", "raftgp_profile_enable_family", "raftgp_profile_read", "raftgp_last_error", "raftgp_debug_seed_skip_block",
            "raftgp_version", "raftgp_diff_workspace_size", "raftgp_gcn_layer_forward", "raftgp_gcn_layer_backward",
            "raftgp_softmod_loss", "raftgp_centroids", "raftgp_gcn_weights", "raftgp_adam_step",
+           "raftgp_diff_plan_create", "raftgp_diff_plan_layer_forward", "raftgp_diff_plan_layer_backward",
+           "raftgp_diff_plan_softmod_loss", "raftgp_diff_plan_destroy",
            "raftgp_batch_workspace_size", "raftgp_batch_plan_create", "raftgp_batch_plan_run", "raftgp_batch_plan_embedding", "raftgp_batch_plan_check",
            "raftgp_batch_plan_tuning_embed",
            "raftgp_batch_plan_candidates", "raftgp_batch_plan_tuning", "raftgp_batch_plan_destroy",
@@ -133,8 +135,17 @@ def lib():
         L.raftgp_adam_step.argtypes = [P, P, P, P, C.c_int64, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int32,
                                        P]
         L.raftgp_gcn_weights.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P, P]
+        L.raftgp_diff_plan_create.argtypes = [C.POINTER(Csr), C.c_int32, C.c_int32, P, C.c_size_t, P,
+                                              C.POINTER(C.c_void_p)]
+        L.raftgp_diff_plan_layer_forward.argtypes = [C.c_void_p, P, C.c_int32, P, C.c_int32, P, P]
+        L.raftgp_diff_plan_layer_backward.argtypes = [C.c_void_p, P, C.c_int32, P, C.c_int32, P, P, P, P]
+        L.raftgp_diff_plan_softmod_loss.argtypes = [C.c_void_p, P, C.c_int32, P, C.c_int32, C.c_float, P, P, P]
+        L.raftgp_diff_plan_destroy.argtypes = [C.c_void_p]
+        L.raftgp_diff_plan_destroy.restype = None
         for name in ("raftgp_gcn_layer_forward", "raftgp_gcn_layer_backward", "raftgp_softmod_loss",
-                     "raftgp_centroids", "raftgp_gcn_weights", "raftgp_adam_step"):
+                     "raftgp_centroids", "raftgp_gcn_weights", "raftgp_adam_step", "raftgp_diff_plan_create",
+                     "raftgp_diff_plan_layer_forward", "raftgp_diff_plan_layer_backward",
+                     "raftgp_diff_plan_softmod_loss"):
             getattr(L, name).restype = C.c_int
         I64P = C.POINTER(C.c_int64)
         L.raftgp_batch_workspace_size.restype = C.c_size_t

@@ -330,6 +330,67 @@ def adam_step(param: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch
                                  float(eps), int(step), _stream(stream)))
 
 
+class DiffPlan:
+    """The differentiation form's calls against a graph checked once: creation validates the
+    graph and computes its normalisation (one synchronisation); every later call is
+    asynchronous, and the loss stays on the device.  The calls share the plan's workspace, so
+    they run in order on one stream.  `width` bounds the layer widths and d, `K` the centroid
+    count."""
+
+    def __init__(self, g: DeviceGraph, width: int, K: int = 0, stream=None):
+        self.g = g
+        self.width, self.K = int(width), int(K)
+        dev = g.col.device
+        self.ws = torch.empty(int(lib().raftgp_diff_workspace_size(g.n, self.width, self.K)), dtype=torch.uint8,
+                              device=dev)
+        h = C.c_void_p()
+        csr = g.csr()
+        check(lib().raftgp_diff_plan_create(C.byref(csr), self.width, self.K, C.c_void_p(self.ws.data_ptr()),
+                                            self.ws.numel(), _stream(stream), C.byref(h)))
+        self._h = h
+
+    def layer_forward(self, H: torch.Tensor, W: torch.Tensor, stream=None) -> torch.Tensor:
+        H, W = _f32(H), _f32(W)
+        lin, lout = W.shape
+        out = torch.empty((self.g.n, lout), dtype=torch.float32, device=H.device)
+        check(lib().raftgp_diff_plan_layer_forward(self._h, C.c_void_p(H.data_ptr()), lin, C.c_void_p(W.data_ptr()),
+                                                   lout, C.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def layer_backward(self, H: torch.Tensor, W: torch.Tensor, dH_out: torch.Tensor, need_dH=True, stream=None):
+        H, W, dH_out = _f32(H), _f32(W), _f32(dH_out)
+        lin, lout = W.shape
+        dW = torch.empty((lin, lout), dtype=torch.float32, device=H.device)
+        dH = torch.empty((self.g.n, lin), dtype=torch.float32, device=H.device) if need_dH else None
+        check(lib().raftgp_diff_plan_layer_backward(self._h, C.c_void_p(H.data_ptr()), lin, C.c_void_p(W.data_ptr()),
+                                                    lout, C.c_void_p(dH_out.data_ptr()),
+                                                    C.c_void_p(dH.data_ptr() if need_dH else None),
+                                                    C.c_void_p(dW.data_ptr()), _stream(stream)))
+        return dH, dW
+
+    def softmod_loss(self, Z: torch.Tensor, mu: torch.Tensor, tau: float, need_grad=True, stream=None):
+        """(loss as a 0-dim float64 device tensor, dL/dZ or None)."""
+        Z, mu = _f32(Z), _f32(mu)
+        loss = torch.empty((), dtype=torch.float64, device=Z.device)
+        dZ = torch.empty_like(Z) if need_grad else None
+        check(lib().raftgp_diff_plan_softmod_loss(self._h, C.c_void_p(Z.data_ptr()), Z.shape[1],
+                                                  C.c_void_p(mu.data_ptr()), mu.shape[0], float(tau),
+                                                  C.c_void_p(loss.data_ptr()),
+                                                  C.c_void_p(dZ.data_ptr() if need_grad else None), _stream(stream)))
+        return loss, dZ
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().raftgp_diff_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def gcn_weights(layer: int, lin: int, lout: int, seed: int, device, stream=None) -> torch.Tensor:
     """The Eq. 6 weights the embedding draws for `layer` (1-based) from `seed`."""
     W = torch.empty((lin, lout), dtype=torch.float32, device=device)

@@ -782,7 +782,63 @@ raftgp_status diff_prepare(const raftgp_csr* g, const DiffWs& w, cudaStream_t s)
     launch_degrees(g, w.deg, w.rs, w.rsh, w.err, nullptr, nullptr, s);
     return read_error_word(w.err, s);
 }
+
+// The steps of each call after the graph check; every launch is asynchronous.
+raftgp_status layer_forward(const raftgp_csr* g, const DiffWs& w, const float* H_in, int lin, const float* W, int lout,
+                            float* H_out, cudaStream_t s) {
+    cudaError_t e = launch_rowmm(g->n, H_in, lin, W, lout, false, w.P, s);
+    if (e == cudaSuccess) e = launch_spmm32(g, lout, w.rsh, w.P, nullptr, H_out, 0, s);
+    if (e != cudaSuccess) return cuda_fail(e, "gcn layer forward");
+    return RAFTGP_OK;
+}
+
+raftgp_status layer_backward(const raftgp_csr* g, const DiffWs& w, const float* H_in, int lin, const float* W,
+                             int lout, const float* dH_out, float* dH_in, float* dW, cudaStream_t s) {
+    // recompute P = H_in W; dA from the recomputed pre-activation and dH_out; dP = Ahat dA
+    cudaError_t e = launch_rowmm(g->n, H_in, lin, W, lout, false, w.P, s);
+    if (e == cudaSuccess) e = launch_spmm32(g, lout, w.rsh, w.P, dH_out, w.dA, 1, s);
+    if (e == cudaSuccess) e = launch_spmm32(g, lout, w.rsh, w.dA, nullptr, w.dP, 2, s);
+    if (e == cudaSuccess) e = launch_wgrad(g->n, H_in, lin, w.dP, lout, w.wpart, dW, s);
+    if (e == cudaSuccess && dH_in) e = launch_rowmm(g->n, w.dP, lout, W, lin, true, dH_in, s);
+    if (e != cudaSuccess) return cuda_fail(e, "gcn layer backward");
+    return RAFTGP_OK;
+}
+
+// Leaves d^T S in red[0..128), sum S . AS in red[128] and the loss in red[129].
+raftgp_status softmod(const raftgp_csr* g, const DiffWs& w, const float* Z, int d, const float* mu, int K, float tau,
+                      float* dZ, cudaStream_t s) {
+    const double two_e = (double)g->nnz;
+    cudaError_t e = launch_soft_assign(g->n, d, Z, mu, K, tau, w.S, s);
+    if (e == cudaSuccess) e = launch_spmm32(g, 128, w.rsh, w.S, nullptr, w.AS, 3, s);
+    if (e == cudaSuccess) e = launch_softmod_reduce(g->n, w.deg, w.S, w.AS, K, two_e, w.spart, w.red, s);
+    if (e == cudaSuccess && dZ) e = launch_softmod_grad(g->n, d, Z, mu, K, tau, w.deg, w.S, w.AS, w.red, two_e, dZ, s);
+    if (e != cudaSuccess) return cuda_fail(e, "softmod loss");
+    return RAFTGP_OK;
+}
+
+raftgp_status layer_args(const float* H_in, int lin, const float* W, int lout, const void* H_out) {
+    if (!H_in || !W || !H_out) return fail(RAFTGP_EINVAL, "NULL argument");
+    if (!width_ok(lin) || !width_ok(lout)) return fail(RAFTGP_EUNSUPPORTED, "widths must be 32, 64 or 128");
+    return RAFTGP_OK;
+}
+
+raftgp_status softmod_args(const raftgp_csr* g, const float* Z, int d, const float* mu, int K, float tau,
+                           const void* loss) {
+    if (!Z || !mu || !loss) return fail(RAFTGP_EINVAL, "NULL argument");
+    if ((uintptr_t)Z & 15) return fail(RAFTGP_EINVAL, "Z must be 16-byte aligned");
+    if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d must be 32, 64 or 128");
+    if (K < 1 || K > 128) return fail(RAFTGP_EUNSUPPORTED, "K must be in [1, 128]");
+    if (!(tau > 0.f)) return fail(RAFTGP_EINVAL, "tau must be positive");
+    if (g->nnz == 0) return fail(RAFTGP_EINVAL, "the loss needs at least one edge");
+    return RAFTGP_OK;
+}
 }  // namespace
+
+struct raftgp_diff_plan {
+    raftgp_csr g;
+    int width = 0, K = 0;
+    DiffWs w{};
+};
 
 extern "C" {
 
@@ -796,18 +852,15 @@ raftgp_status raftgp_gcn_layer_forward(const raftgp_csr* g, const float* H_in, i
                                        int32_t lout, float* H_out, void* ws, size_t ws_bytes, raftgp_stream_t stream) {
     raftgp_status st = check_csr(g);
     if (st) return st;
-    if (!H_in || !W || !H_out || !ws) return fail(RAFTGP_EINVAL, "NULL argument");
-    if (!width_ok(lin) || !width_ok(lout)) return fail(RAFTGP_EUNSUPPORTED, "widths must be 32, 64 or 128");
+    if ((st = layer_args(H_in, lin, W, lout, H_out))) return st;
+    if (!ws) return fail(RAFTGP_EINVAL, "NULL argument");
     const int width = std::max(lin, lout);
     if (ws_bytes < raftgp_diff_workspace_size(g->n, width, 0)) return fail(RAFTGP_ENOMEM, "workspace too small");
     cudaStream_t s = (cudaStream_t)stream;
     Carver c(ws);
     DiffWs w = carve_diff(c, g->n, width, 0);
     if ((st = diff_prepare(g, w, s))) return st;
-    cudaError_t e = launch_rowmm(g->n, H_in, lin, W, lout, false, w.P, s);
-    if (e == cudaSuccess) e = launch_spmm32(g, lout, w.rsh, w.P, nullptr, H_out, 0, s);
-    if (e != cudaSuccess) return cuda_fail(e, "gcn layer forward");
-    return RAFTGP_OK;
+    return layer_forward(g, w, H_in, lin, W, lout, H_out, s);
 }
 
 raftgp_status raftgp_gcn_layer_backward(const raftgp_csr* g, const float* H_in, int32_t lin, const float* W,
@@ -815,22 +868,15 @@ raftgp_status raftgp_gcn_layer_backward(const raftgp_csr* g, const float* H_in, 
                                         size_t ws_bytes, raftgp_stream_t stream) {
     raftgp_status st = check_csr(g);
     if (st) return st;
-    if (!H_in || !W || !dH_out || !dW || !ws) return fail(RAFTGP_EINVAL, "NULL argument");
-    if (!width_ok(lin) || !width_ok(lout)) return fail(RAFTGP_EUNSUPPORTED, "widths must be 32, 64 or 128");
+    if ((st = layer_args(H_in, lin, W, lout, dH_out))) return st;
+    if (!dW || !ws) return fail(RAFTGP_EINVAL, "NULL argument");
     const int width = std::max(lin, lout);
     if (ws_bytes < raftgp_diff_workspace_size(g->n, width, 0)) return fail(RAFTGP_ENOMEM, "workspace too small");
     cudaStream_t s = (cudaStream_t)stream;
     Carver c(ws);
     DiffWs w = carve_diff(c, g->n, width, 0);
     if ((st = diff_prepare(g, w, s))) return st;
-    // recompute P = H_in W; dA from the recomputed pre-activation and dH_out; dP = Ahat dA
-    cudaError_t e = launch_rowmm(g->n, H_in, lin, W, lout, false, w.P, s);
-    if (e == cudaSuccess) e = launch_spmm32(g, lout, w.rsh, w.P, dH_out, w.dA, 1, s);
-    if (e == cudaSuccess) e = launch_spmm32(g, lout, w.rsh, w.dA, nullptr, w.dP, 2, s);
-    if (e == cudaSuccess) e = launch_wgrad(g->n, H_in, lin, w.dP, lout, w.wpart, dW, s);
-    if (e == cudaSuccess && dH_in) e = launch_rowmm(g->n, w.dP, lout, W, lin, true, dH_in, s);
-    if (e != cudaSuccess) return cuda_fail(e, "gcn layer backward");
-    return RAFTGP_OK;
+    return layer_backward(g, w, H_in, lin, W, lout, dH_out, dH_in, dW, s);
 }
 
 raftgp_status raftgp_softmod_loss(const raftgp_csr* g, const float* Z, int32_t d, const float* mu, int32_t K,
@@ -838,32 +884,79 @@ raftgp_status raftgp_softmod_loss(const raftgp_csr* g, const float* Z, int32_t d
                                   raftgp_stream_t stream) {
     raftgp_status st = check_csr(g);
     if (st) return st;
-    if ((uintptr_t)Z & 15) return fail(RAFTGP_EINVAL, "Z must be 16-byte aligned");
-    if (!Z || !mu || !loss || !ws) return fail(RAFTGP_EINVAL, "NULL argument");
-    if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d must be 32, 64 or 128");
-    if (K < 1 || K > 128) return fail(RAFTGP_EUNSUPPORTED, "K must be in [1, 128]");
-    if (!(tau > 0.f)) return fail(RAFTGP_EINVAL, "tau must be positive");
+    if ((st = softmod_args(g, Z, d, mu, K, tau, loss))) return st;
+    if (!ws) return fail(RAFTGP_EINVAL, "NULL argument");
     if (ws_bytes < raftgp_diff_workspace_size(g->n, d, K)) return fail(RAFTGP_ENOMEM, "workspace too small");
-    if (g->nnz == 0) return fail(RAFTGP_EINVAL, "the loss needs at least one edge");
     cudaStream_t s = (cudaStream_t)stream;
     Carver c(ws);
     DiffWs w = carve_diff(c, g->n, d, K);
     if ((st = diff_prepare(g, w, s))) return st;
-    const double two_e = (double)g->nnz;
-    cudaError_t e = launch_soft_assign(g->n, d, Z, mu, K, tau, w.S, s);
-    if (e == cudaSuccess) e = launch_spmm32(g, 128, w.rsh, w.S, nullptr, w.AS, 3, s);
-    if (e == cudaSuccess) e = launch_softmod_reduce(g->n, w.deg, w.S, w.AS, w.spart, w.red, s);
-    if (e == cudaSuccess && dZ) e = launch_softmod_grad(g->n, d, Z, mu, K, tau, w.deg, w.S, w.AS, w.red, two_e, dZ, s);
-    if (e != cudaSuccess) return cuda_fail(e, "softmod loss");
-    double h[129];
-    e = cudaMemcpyAsync(h, w.red, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if ((st = softmod(g, w, Z, d, mu, K, tau, dZ, s))) return st;
+    cudaError_t e = cudaMemcpyAsync(loss, w.red + 129, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "softmod loss readback");
-    double dd = 0.0;
-    for (int k = 0; k < K; ++k) dd += h[k] * h[k];
-    *loss = -(h[128] - dd / two_e) / two_e;
     return RAFTGP_OK;
 }
+
+raftgp_status raftgp_diff_plan_create(const raftgp_csr* g, int32_t width, int32_t K, void* ws, size_t ws_bytes,
+                                      raftgp_stream_t stream, raftgp_diff_plan** plan) {
+    if (!plan) return fail(RAFTGP_EINVAL, "NULL plan");
+    *plan = nullptr;
+    raftgp_status st = check_csr(g);
+    if (st) return st;
+    if (!ws) return fail(RAFTGP_EINVAL, "NULL argument");
+    if (!width_ok(width)) return fail(RAFTGP_EUNSUPPORTED, "width must be 32, 64 or 128");
+    if (K < 0 || K > 128) return fail(RAFTGP_EUNSUPPORTED, "K must be in [0, 128]");
+    if (ws_bytes < raftgp_diff_workspace_size(g->n, width, K)) return fail(RAFTGP_ENOMEM, "workspace too small");
+    cudaStream_t s = (cudaStream_t)stream;
+    raftgp_diff_plan* p = new raftgp_diff_plan();
+    p->g = *g;
+    p->width = width;
+    p->K = K;
+    Carver c(ws);
+    p->w = carve_diff(c, g->n, width, K);
+    if ((st = diff_prepare(&p->g, p->w, s))) {
+        delete p;
+        return st;
+    }
+    *plan = p;
+    return RAFTGP_OK;
+}
+
+raftgp_status raftgp_diff_plan_layer_forward(const raftgp_diff_plan* p, const float* H_in, int32_t lin,
+                                             const float* W, int32_t lout, float* H_out, raftgp_stream_t stream) {
+    if (!p) return fail(RAFTGP_EINVAL, "NULL plan");
+    raftgp_status st = layer_args(H_in, lin, W, lout, H_out);
+    if (st) return st;
+    if (std::max(lin, lout) > p->width) return fail(RAFTGP_EINVAL, "layer wider than the plan");
+    return layer_forward(&p->g, p->w, H_in, lin, W, lout, H_out, (cudaStream_t)stream);
+}
+
+raftgp_status raftgp_diff_plan_layer_backward(const raftgp_diff_plan* p, const float* H_in, int32_t lin,
+                                              const float* W, int32_t lout, const float* dH_out, float* dH_in,
+                                              float* dW, raftgp_stream_t stream) {
+    if (!p) return fail(RAFTGP_EINVAL, "NULL plan");
+    raftgp_status st = layer_args(H_in, lin, W, lout, dH_out);
+    if (st) return st;
+    if (!dW) return fail(RAFTGP_EINVAL, "NULL argument");
+    if (std::max(lin, lout) > p->width) return fail(RAFTGP_EINVAL, "layer wider than the plan");
+    return layer_backward(&p->g, p->w, H_in, lin, W, lout, dH_out, dH_in, dW, (cudaStream_t)stream);
+}
+
+raftgp_status raftgp_diff_plan_softmod_loss(const raftgp_diff_plan* p, const float* Z, int32_t d, const float* mu,
+                                            int32_t K, float tau, double* loss, float* dZ, raftgp_stream_t stream) {
+    if (!p) return fail(RAFTGP_EINVAL, "NULL plan");
+    raftgp_status st = softmod_args(&p->g, Z, d, mu, K, tau, loss);
+    if (st) return st;
+    if (d > p->width || K > p->K) return fail(RAFTGP_EINVAL, "d or K larger than the plan's");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = softmod(&p->g, p->w, Z, d, mu, K, tau, dZ, s))) return st;
+    cudaError_t e = cudaMemcpyAsync(loss, p->w.red + 129, sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "softmod loss copy");
+    return RAFTGP_OK;
+}
+
+void raftgp_diff_plan_destroy(raftgp_diff_plan* plan) { delete plan; }
 
 raftgp_status raftgp_centroids(const float* Z, int64_t n, int32_t d, const int32_t* labels, int32_t K, float* mu,
                                void* ws, size_t ws_bytes, raftgp_stream_t stream) {

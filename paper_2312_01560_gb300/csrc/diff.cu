@@ -308,12 +308,21 @@ __global__ void __launch_bounds__(256) k_softmod_partials(int64_t n, const int32
     }
 }
 
-// Adds the block partials in block order: red[0..SK) = d^T S, red[SK] = sum S . AS.
-__global__ void k_softmod_finish(const double* __restrict__ partial, int blocks, double* __restrict__ red) {
+// Adds the block partials in block order: red[0..SK) = d^T S, red[SK] = sum S . AS; then
+// red[SK + 1] = the loss -(sum S . AS - ||d^T S||^2 / 2e) / 2e, the squares added over
+// ascending blocks c < K with every product and sum rounded on its own.
+__global__ void k_softmod_finish(const double* __restrict__ partial, int blocks, int K, double two_e,
+                                 double* __restrict__ red) {
     for (int c = threadIdx.x; c <= SK; c += blockDim.x) {
         double s = 0.0;
         for (int b = 0; b < blocks; ++b) s += partial[(int64_t)b * (SK + 1) + c];
         red[c] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double dd = 0.0;
+        for (int c = 0; c < K; ++c) dd = __dadd_rn(dd, __dmul_rn(red[c], red[c]));
+        red[SK + 1] = -__ddiv_rn(__dsub_rn(red[SK], __ddiv_rn(dd, two_e)), two_e);
     }
 }
 
@@ -530,13 +539,13 @@ cudaError_t launch_soft_assign(int64_t n, int d, const float* Z, const float* mu
     return cudaGetLastError();
 }
 
-cudaError_t launch_softmod_reduce(int64_t n, const int32_t* deg, const float* S, const float* AS, double* partial,
-                                  double* red, cudaStream_t s) {
+cudaError_t launch_softmod_reduce(int64_t n, const int32_t* deg, const float* S, const float* AS, int K,
+                                  double two_e, double* partial, double* red, cudaStream_t s) {
     ProfScope ps(s, PF_DIFF_LOSS, 2);
     const int blocks = softmod_blocks(n);
     const int64_t rpb = (n + blocks - 1) / blocks;
     k_softmod_partials<<<blocks, 256, 0, s>>>(n, deg, S, AS, rpb, partial);
-    k_softmod_finish<<<1, 256, 0, s>>>(partial, blocks, red);
+    k_softmod_finish<<<1, 256, 0, s>>>(partial, blocks, K, two_e, red);
     return cudaGetLastError();
 }
 

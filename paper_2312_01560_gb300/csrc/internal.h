@@ -219,8 +219,8 @@ cudaError_t launch_wgrad(int64_t n, const float* H, int lin, const float* dP, in
 int softmod_blocks(int64_t n);
 cudaError_t launch_soft_assign(int64_t n, int d, const float* Z, const float* mu, int K, float tau, float* S,
                                cudaStream_t s);
-cudaError_t launch_softmod_reduce(int64_t n, const int32_t* deg, const float* S, const float* AS, double* partial,
-                                  double* red, cudaStream_t s);
+cudaError_t launch_softmod_reduce(int64_t n, const int32_t* deg, const float* S, const float* AS, int K,
+                                  double two_e, double* partial, double* red, cudaStream_t s);
 cudaError_t launch_softmod_grad(int64_t n, int d, const float* Z, const float* mu, int K, float tau, const int32_t* deg,
                                 const float* S, const float* AS, const double* red, double two_e, float* dZ,
                                 cudaStream_t s);

@@ -111,6 +111,71 @@ def test_centroids_are_fp64_means(cuda):
         api.centroids(torch.tensor(Z, device=cuda), torch.tensor(lab, device=cuda), 20)
 
 
+def test_plan_calls_equal_one_shot_calls(cuda):
+    # the same kernels on the same inputs: every output bit-identical; the loss is left on the
+    # device by the plan and read back by the one-shot call, the same double either way
+    g = workload("dcsbm-2k")
+    dg = api.DeviceGraph.from_host(g, cuda)
+    plan = api.DiffPlan(dg, 128, 80)
+    rng = np.random.default_rng(5)
+    for lin, lout in [(64, 32), (128, 128), (32, 64)]:
+        H = torch.tensor(rng.normal(size=(g.n, lin)), dtype=torch.float32, device=cuda)
+        W = torch.tensor(rng.normal(size=(lin, lout)) * 0.1, dtype=torch.float32, device=cuda)
+        dHo = torch.tensor(rng.normal(size=(g.n, lout)), dtype=torch.float32, device=cuda)
+        assert torch.equal(plan.layer_forward(H, W), api.gcn_layer_forward(dg, H, W))
+        a, b = plan.layer_backward(H, W, dHo), api.gcn_layer_backward(dg, H, W, dHo)
+        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+        assert plan.layer_backward(H, W, dHo, need_dH=False)[0] is None
+    for K, d in [(80, 64), (7, 128)]:
+        Z = torch.nn.functional.normalize(torch.tensor(rng.normal(size=(g.n, d)), dtype=torch.float32, device=cuda))
+        mu = Z[torch.tensor(rng.choice(g.n, K, replace=False), device=cuda)].contiguous()
+        lp, dZp = plan.softmod_loss(Z, mu, 0.1)
+        lo, dZo = api.softmod_loss(dg, Z, mu, 0.1)
+        assert lp.device.type == "cuda" and lp.dtype == torch.float64
+        assert float(lp) == lo
+        assert torch.equal(dZp, dZo)
+
+
+def test_plan_rejects_bad_arguments_and_graphs(cuda):
+    g = workload("dcsbm-1k")
+    dg = api.DeviceGraph.from_host(g, cuda)
+    plan = api.DiffPlan(dg, 64, 16)
+    H = torch.zeros((g.n, 128), device=cuda)
+    with pytest.raises(api._abi.RaftgpError, match="wider"):
+        plan.layer_forward(H, torch.zeros((128, 64), device=cuda))
+    Z = torch.zeros((g.n, 64), device=cuda)
+    with pytest.raises(api._abi.RaftgpError, match="larger"):
+        plan.softmod_loss(Z, torch.zeros((17, 64), device=cuda), 0.1)
+    with pytest.raises(api._abi.RaftgpError, match="EUNSUPPORTED"):
+        api.DiffPlan(dg, 96, 16)
+    bad = dg.col.clone()
+    bad[17] = g.n                      # column index out of range: no plan is made
+    with pytest.raises(api._abi.RaftgpError, match="EINVAL"):
+        api.DiffPlan(api.DeviceGraph(g.n, dg.row_ptr, bad), 64, 16)
+
+
+def test_tuning_on_a_plan_equals_one_shot_calls(cuda):
+    # the loop on a plan (dL/dZ handed to the layers' backward) against autograd through the
+    # one-shot calls: the same weights bit for bit, the same losses
+    dg, Y, Ws, mu = _tune_setup(cuda)
+    W1, l1 = diff.tune(dg, Y, Ws, mu, tau=0.1, steps=5, lr=1e-2)
+    params = [W.detach().clone().requires_grad_(True) for W in Ws]
+    m = [torch.zeros_like(p) for p in params]
+    v = [torch.zeros_like(p) for p in params]
+    l2 = []
+    for t in range(1, 6):
+        loss = diff.SoftModLossFn.apply(diff.chain(dg, Y, params), mu, dg, 0.1)
+        for p in params:
+            p.grad = None
+        loss.backward()
+        with torch.no_grad():
+            for k, p in enumerate(params):
+                api.adam_step(p.data, p.grad.contiguous(), m[k], v[k], t, 1e-2)
+        l2.append(float(loss.detach()))
+    assert l1 == l2
+    assert all(torch.equal(a, b.detach()) for a, b in zip(W1, params))
+
+
 def _tune_setup(cuda):
     g = workload("dcsbm-2k")
     dg = api.DeviceGraph.from_host(g, cuda)
