@@ -18,7 +18,8 @@
  *     undirected, unweighted).  row_ptr has n+1 entries (int32 or int64), col has nnz int32
  *     entries, nnz = 2|E|.  All graph, feature and label arrays are DEVICE pointers owned by
  *     the caller; the library never allocates or frees device memory.  Scratch memory is a
- *     caller-owned device workspace whose size raftgp_workspace_size() returns.  A feature
+ *     caller-owned device workspace whose size raftgp_workspace_size() returns (it may start
+ *     at any address: the library aligns its pieces inside it).  A feature
  *     matrix Z (N x d, row-major, rows packed) must start on a 16-byte boundary; a Z that
  *     does not is rejected with RAFTGP_EINVAL (rows of 32 x elem bytes keep every row aligned).
  *   - Every call is ordered on the given CUDA stream.  Calls with host outputs synchronise
@@ -372,6 +373,7 @@ raftgp_status raftgp_partition_batched(const raftgp_csr* g, const int64_t* graph
 /* ---- Differentiation form (the paper trains nothing: its GNN stays random, Section III-B;
  * these calls let the Eq. 6 weights be tuned against a relaxed modularity) ----
  * All arrays are device FP32, row-major; widths (lin, lout, d) are 32, 64 or 128; K <= 128.
+ * H_in, H_out, dH_out, dH_in and Z start on 16-byte boundaries (RAFTGP_EINVAL otherwise).
  * Each call validates the graph on the device first (malformed graph: RAFTGP_EINVAL, nothing
  * else runs) and synchronises the stream once for that check.  `ws` is a device workspace
  * of at least raftgp_diff_workspace_size(n, width, K) bytes, width = the largest layer

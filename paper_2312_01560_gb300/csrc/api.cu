@@ -636,7 +636,7 @@ raftgp_status raftgp_score(const raftgp_csr* g, const int32_t* labels, int32_t K
     float* rs = c.take<float>(g->n);
     float* rsh = c.take<float>(g->n);
     double* out2 = c.take<double>(2);
-    if (ws_bytes < c.off) return fail(RAFTGP_ENOMEM, "workspace too small");
+    if (ws_bytes < c.bytes()) return fail(RAFTGP_ENOMEM, "workspace too small");
     cudaStream_t s = (cudaStream_t)stream;
     cudaMemsetAsync(err, 0, sizeof(uint32_t), s);
     launch_degrees(g, deg, rs, rsh, err, nullptr, nullptr, s);
@@ -667,7 +667,7 @@ raftgp_status raftgp_kmeanspp(const void* Z, int64_t n, int32_t d, int32_t z_dty
     if (z_dtype != RAFTGP_F32 && z_dtype != RAFTGP_BF16) return fail(RAFTGP_EINVAL, "unknown z_dtype");
     Carver c(ws);
     char* region = c.take<char>(seed_scratch_bytes(n, K));
-    if (ws_bytes < c.off) return fail(RAFTGP_ENOMEM, "workspace too small");
+    if (ws_bytes < c.bytes()) return fail(RAFTGP_ENOMEM, "workspace too small");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = launch_seeding(Z, z_dtype, n, d, K, seed, carve_seed(region, n, K, seeds), s);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -709,7 +709,7 @@ raftgp_status raftgp_lloyd(const void* Z, int64_t n, int32_t d, int32_t z_dtype,
     uint32_t* err = c.take<uint32_t>(64);
     int2* recheck_list = c.take<int2>((size_t)n);
     int* recheck_count = c.take<int>(64);
-    if (ws_bytes < c.off) return fail(RAFTGP_ENOMEM, "workspace too small");
+    if (ws_bytes < c.bytes()) return fail(RAFTGP_ENOMEM, "workspace too small");
     cudaStream_t s = (cudaStream_t)stream;
     CandBatch b{};
     b.n = 1;
@@ -816,8 +816,12 @@ raftgp_status softmod(const raftgp_csr* g, const DiffWs& w, const float* Z, int 
     return RAFTGP_OK;
 }
 
-raftgp_status layer_args(const float* H_in, int lin, const float* W, int lout, const void* H_out) {
+// H_in, the n x lout array (H_out or dH_out) and dH_in are read and written in 16-byte pieces.
+raftgp_status layer_args(const float* H_in, int lin, const float* W, int lout, const void* H_out,
+                         const void* dH_in = nullptr) {
     if (!H_in || !W || !H_out) return fail(RAFTGP_EINVAL, "NULL argument");
+    if (((uintptr_t)H_in | (uintptr_t)H_out | (uintptr_t)dH_in) & 15)
+        return fail(RAFTGP_EINVAL, "H_in, H_out, dH_out and dH_in must be 16-byte aligned");
     if (!width_ok(lin) || !width_ok(lout)) return fail(RAFTGP_EUNSUPPORTED, "widths must be 32, 64 or 128");
     return RAFTGP_OK;
 }
@@ -868,7 +872,7 @@ raftgp_status raftgp_gcn_layer_backward(const raftgp_csr* g, const float* H_in, 
                                         size_t ws_bytes, raftgp_stream_t stream) {
     raftgp_status st = check_csr(g);
     if (st) return st;
-    if ((st = layer_args(H_in, lin, W, lout, dH_out))) return st;
+    if ((st = layer_args(H_in, lin, W, lout, dH_out, dH_in))) return st;
     if (!dW || !ws) return fail(RAFTGP_EINVAL, "NULL argument");
     const int width = std::max(lin, lout);
     if (ws_bytes < raftgp_diff_workspace_size(g->n, width, 0)) return fail(RAFTGP_ENOMEM, "workspace too small");
@@ -936,7 +940,7 @@ raftgp_status raftgp_diff_plan_layer_backward(const raftgp_diff_plan* p, const f
                                               const float* W, int32_t lout, const float* dH_out, float* dH_in,
                                               float* dW, raftgp_stream_t stream) {
     if (!p) return fail(RAFTGP_EINVAL, "NULL plan");
-    raftgp_status st = layer_args(H_in, lin, W, lout, dH_out);
+    raftgp_status st = layer_args(H_in, lin, W, lout, dH_out, dH_in);
     if (st) return st;
     if (!dW) return fail(RAFTGP_EINVAL, "NULL argument");
     if (std::max(lin, lout) > p->width) return fail(RAFTGP_EINVAL, "layer wider than the plan");

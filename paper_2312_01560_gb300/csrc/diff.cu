@@ -19,52 +19,114 @@
 namespace raftgp {
 
 // ------------------------------------------------------------------------------------
-// Y = X W (TRANS: X W^T), X: n x LIN, W: LIN x LOUT (TRANS: LOUT x LIN, row-major).
-// Block of 256 threads, 64 rows per tile; thread (ty, tx) owns rows 4ty..4ty+3 and columns
-// tx*CW..tx*CW+CW-1 (CW = LOUT/16); the k loop runs in ascending order.
+// Y = X W (TRANS: X W^T), X: n x LIN (16-byte aligned), W: LIN x LOUT (TRANS: LOUT x LIN),
+// row-major.  W stays in shared memory, k-major; X comes in tiles of TR rows, KC columns at a
+// time, by cp.async into two buffers (rows padded to KC + 4 floats).  Thread (ty, tx) owns
+// rows ty + TYN i (i < 8) and columns 4 tx + 4 TXN g + q (g < 2, q < 4), reading X two
+// columns at a time: a warp's 8- and 16-byte shared reads fall in distinct banks.  Every
+// output is fmaf over ascending k from zero.
 // ------------------------------------------------------------------------------------
+template <int LIN, int LOUT>
+struct RmCfg {
+    static constexpr int TXN = LOUT / 8;   // column threads: 16, 8, 4
+    static constexpr int TYN = 256 / TXN;  // row threads: 16, 32, 64
+    static constexpr int TR = 8 * TYN;     // rows per tile: 128, 256, 512
+    static constexpr int KC = 4096 / TR;   // X columns per stage: 32, 16, 8
+    static constexpr int KCP = KC + 4;     // padded stage row, floats
+    static constexpr int NCH = LIN / KC;   // stages per tile
+    static constexpr int BUF = TR * KCP;   // floats per stage buffer
+    static constexpr int SMEM = (LIN * LOUT + 2 * BUF) * (int)sizeof(float);
+    static_assert(KC <= LIN && LIN % KC == 0, "stage width");
+    static_assert((TR * KC / 4) % 256 == 0, "stage pieces per thread");
+};
+
+__device__ __forceinline__ void rm_cp16(float* dst, const float* src, int bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(bytes)
+                 : "memory");
+}
+
+// Stage (rows r0.., columns k0..k0+KC) of X into buf; rows at or past n are zero-filled.
+template <int LIN, int LOUT>
+__device__ __forceinline__ void rm_stage(float* buf, const float* __restrict__ X, int64_t n, int64_t r0, int k0) {
+    using C = RmCfg<LIN, LOUT>;
+    constexpr int P = C::KC / 4;   // 16-byte pieces per stage row
+#pragma unroll
+    for (int u = 0; u < C::TR * P / 256; ++u) {
+        const int t = threadIdx.x + 256 * u;
+        const int r = t / P, j = t % P;
+        const bool ok = r0 + r < n;
+        rm_cp16(buf + r * C::KCP + 4 * j, ok ? X + (r0 + r) * LIN + k0 + 4 * j : X, ok ? 16 : 0);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 template <int LIN, int LOUT, bool TRANS>
-__global__ void __launch_bounds__(256) k_rowmm(int64_t n, const float* __restrict__ X, const float* __restrict__ W,
-                                               float* __restrict__ Y) {
-    constexpr int CW = LOUT / 16;
-    extern __shared__ float sm[];
-    float* sW = sm;                    // LIN x LOUT
-    float* sX = sm + LIN * LOUT;       // 64 x (LIN + 1)
+__global__ void __launch_bounds__(256, 2) k_rowmm(int64_t n, const float* __restrict__ X, const float* __restrict__ W,
+                                                  float* __restrict__ Y) {
+    using C = RmCfg<LIN, LOUT>;
+    extern __shared__ __align__(16) float sm[];
+    float* sW = sm;                    // LIN x LOUT, k-major
+    float* sX = sm + LIN * LOUT;       // two stage buffers
+    const int64_t tiles = (n + C::TR - 1) / C::TR;
+    if ((int64_t)blockIdx.x >= tiles) return;
+    const int64_t steps = (tiles - blockIdx.x + gridDim.x - 1) / gridDim.x * C::NCH;
+    rm_stage<LIN, LOUT>(sX, X, n, (int64_t)blockIdx.x * C::TR, 0);
     for (int t = threadIdx.x; t < LIN * LOUT; t += 256) {
         const int k = t / LOUT, c = t % LOUT;
         sW[t] = TRANS ? W[(int64_t)c * LIN + k] : W[t];
     }
-    const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
-    for (int64_t r0 = (int64_t)blockIdx.x * 64; r0 < n; r0 += (int64_t)gridDim.x * 64) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < 64 * LIN; t += 256) {
-            const int r = t / LIN, k = t % LIN;
-            sX[r * (LIN + 1) + k] = r0 + r < n ? X[(r0 + r) * LIN + k] : 0.f;
+    const int ty = threadIdx.x / C::TXN, tx = threadIdx.x % C::TXN;
+    float acc[8][8];
+    for (int64_t s = 0; s < steps; ++s) {
+        const int ch = (int)(s % C::NCH);
+        const int64_t r0 = ((int64_t)blockIdx.x + (s / C::NCH) * gridDim.x) * C::TR;
+        if (s + 1 < steps) {
+            const int64_t s1 = s + 1;
+            rm_stage<LIN, LOUT>(sX + (s1 & 1) * C::BUF, X, n,
+                                ((int64_t)blockIdx.x + (s1 / C::NCH) * gridDim.x) * C::TR, (int)(s1 % C::NCH) * C::KC);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();
-        float acc[4][CW];
+        if (ch == 0) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 8; ++i)
 #pragma unroll
-            for (int j = 0; j < CW; ++j) acc[i][j] = 0.f;
-        for (int k = 0; k < LIN; ++k) {
-            float a[4], b[CW];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = sX[(4 * ty + i) * (LIN + 1) + k];
-#pragma unroll
-            for (int j = 0; j < CW; ++j) b[j] = sW[k * LOUT + tx * CW + j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < CW; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
         }
+        const float* xb = sX + (s & 1) * C::BUF;
+        for (int kk = 0; kk < C::KC; kk += 2) {
+            float2 xa[8];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int64_t r = r0 + 4 * ty + i;
-            if (r < n)
+            for (int i = 0; i < 8; ++i) xa[i] = *reinterpret_cast<const float2*>(xb + (ty + C::TYN * i) * C::KCP + kk);
 #pragma unroll
-                for (int j = 0; j < CW; ++j) Y[r * LOUT + tx * CW + j] = acc[i][j];
+            for (int q = 0; q < 2; ++q) {
+                const float* wr = sW + (ch * C::KC + kk + q) * LOUT + 4 * tx;
+                const float4 w0 = *reinterpret_cast<const float4*>(wr);
+                const float4 w1 = *reinterpret_cast<const float4*>(wr + 4 * C::TXN);
+                const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float xv = q == 0 ? xa[i].x : xa[i].y;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(xv, wv[j], acc[i][j]);
+                }
+            }
         }
+        if (ch == C::NCH - 1) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int64_t r = r0 + ty + C::TYN * i;
+                if (r < n) {
+                    float* o = Y + r * LOUT + 4 * tx;
+                    *reinterpret_cast<float4*>(o) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+                    *reinterpret_cast<float4*>(o + 4 * C::TXN) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+                }
+            }
+        }
+        __syncthreads();   // this buffer is free before the stage two steps on is copied into it
     }
 }
 
@@ -79,6 +141,28 @@ __global__ void __launch_bounds__(256) k_rowmm(int64_t n, const float* __restric
 // ------------------------------------------------------------------------------------
 enum SpMode { SP_GCN_FWD = 0, SP_GCN_BWD = 1, SP_LINEAR = 2, SP_ADJ = 3 };
 
+// VW consecutive floats of one row as a single 4-, 8- or 16-byte access.
+template <int VW>
+struct RowPiece {
+    __device__ __forceinline__ static void load(const float* p, float* o) {
+        if constexpr (VW == 4) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+            o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+        } else if constexpr (VW == 2) {
+            const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+            o[0] = v.x; o[1] = v.y;
+        } else {
+            o[0] = __ldg(p);
+        }
+    }
+    __device__ __forceinline__ static void store(float* p, const float* v) {
+        if constexpr (VW == 4) *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+        else if constexpr (VW == 2) *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+        else p[0] = v[0];
+    }
+};
+
+
 template <typename OffT, int VW, int MODE>
 __global__ void __launch_bounds__(256) k_spmm32(Csr<OffT> g, const float* __restrict__ rsh, const float* __restrict__ X,
                                                 const float* __restrict__ G, float* __restrict__ out) {
@@ -88,8 +172,14 @@ __global__ void __launch_bounds__(256) k_spmm32(Csr<OffT> g, const float* __rest
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < g.n; i += warps) {
         float acc[VW];
         const float wi = MODE == SP_ADJ ? 0.f : __ldg(rsh + i);
+        if constexpr (MODE == SP_ADJ) {
 #pragma unroll
-        for (int v = 0; v < VW; ++v) acc[v] = MODE == SP_ADJ ? 0.f : wi * __ldg(X + i * L + lane * VW + v);
+            for (int v = 0; v < VW; ++v) acc[v] = 0.f;
+        } else {
+            RowPiece<VW>::load(X + i * L + lane * VW, acc);
+#pragma unroll
+            for (int v = 0; v < VW; ++v) acc[v] = wi * acc[v];
+        }
         const int64_t b = g.begin(i), e = g.end(i);
         int64_t p = b;
         for (; p + 4 <= e; p += 4) {
@@ -100,8 +190,7 @@ __global__ void __launch_bounds__(256) k_spmm32(Csr<OffT> g, const float* __rest
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 w[u] = MODE == SP_ADJ ? 1.f : __ldg(rsh + j[u]);
-#pragma unroll
-                for (int v = 0; v < VW; ++v) x[u][v] = __ldg(X + (int64_t)j[u] * L + lane * VW + v);
+                RowPiece<VW>::load(X + (int64_t)j[u] * L + lane * VW, x[u]);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -111,21 +200,21 @@ __global__ void __launch_bounds__(256) k_spmm32(Csr<OffT> g, const float* __rest
         for (; p < e; ++p) {
             const int j = __ldg(g.col + p);
             const float w = MODE == SP_ADJ ? 1.f : __ldg(rsh + j);
+            float x[VW];
+            RowPiece<VW>::load(X + (int64_t)j * L + lane * VW, x);
 #pragma unroll
-            for (int v = 0; v < VW; ++v) acc[v] = fmaf(w, __ldg(X + (int64_t)j * L + lane * VW + v), acc[v]);
+            for (int v = 0; v < VW; ++v) acc[v] = fmaf(w, x[v], acc[v]);
         }
         float* o = out + i * L + lane * VW;
         if constexpr (MODE == SP_ADJ) {
-#pragma unroll
-            for (int v = 0; v < VW; ++v) o[v] = acc[v];
+            RowPiece<VW>::store(o, acc);
             continue;
         } else {
 #pragma unroll
             for (int v = 0; v < VW; ++v) acc[v] *= wi;
         }
         if constexpr (MODE == SP_LINEAR) {
-#pragma unroll
-            for (int v = 0; v < VW; ++v) o[v] = acc[v];
+            RowPiece<VW>::store(o, acc);
             continue;
         }
         float T[VW], ss = 0.f;
@@ -138,20 +227,24 @@ __global__ void __launch_bounds__(256) k_spmm32(Csr<OffT> g, const float* __rest
         const float r = sqrtf(ss);
         if (MODE == SP_GCN_FWD) {
             const float inv = r > 0.f ? 1.0f / r : 0.f;
+            float h[VW];
 #pragma unroll
-            for (int v = 0; v < VW; ++v) o[v] = T[v] * inv;
+            for (int v = 0; v < VW; ++v) h[v] = T[v] * inv;
+            RowPiece<VW>::store(o, h);
         } else {
             float H[VW], gv[VW], dot = 0.f;
             const float inv = r > 0.f ? 1.0f / r : 0.f;
+            RowPiece<VW>::load(G + i * L + lane * VW, gv);
 #pragma unroll
             for (int v = 0; v < VW; ++v) {
                 H[v] = T[v] * inv;
-                gv[v] = __ldg(G + i * L + lane * VW + v);
                 dot = fmaf(H[v], gv[v], dot);
             }
             dot = warp_sum(dot);
+            float d[VW];
 #pragma unroll
-            for (int v = 0; v < VW; ++v) o[v] = (gv[v] - H[v] * dot) * inv * (1.0f - T[v] * T[v]);
+            for (int v = 0; v < VW; ++v) d[v] = (gv[v] - H[v] * dot) * inv * (1.0f - T[v] * T[v]);
+            RowPiece<VW>::store(o, d);
         }
     }
 }
@@ -161,12 +254,38 @@ __global__ void __launch_bounds__(256) k_spmm32(Csr<OffT> g, const float* __rest
 // partial (thread owns an 8 x 8 (or smaller) tile), then one kernel adds the partials in
 // block order in FP64.
 // ------------------------------------------------------------------------------------
+// Thread (ta, tb) owns rows {V ta + 16 V g + q} of dW (V = min(LIN / 16, 4) consecutive rows
+// per group, LIN / 16 / V groups) and the same pattern of columns over LOUT: every shared read
+// is a 16-byte (8-byte for width 32) piece, and a warp's pieces fall in distinct banks.
+template <int W>
+struct WgMap {
+    static constexpr int T = W / 16;             // values per thread: 8, 4, 2
+    static constexpr int V = T >= 4 ? 4 : T;     // consecutive values per group
+    static constexpr int G = T / V;              // groups
+    __device__ __forceinline__ static int idx(int t, int x) { return V * t + 16 * V * (x / V) + x % V; }
+    __device__ __forceinline__ static void load(const float* row, int t, float* out) {
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const float* p = row + V * t + 16 * V * g;
+            if constexpr (V == 4) {
+                const float4 v = *reinterpret_cast<const float4*>(p);
+                out[4 * g] = v.x; out[4 * g + 1] = v.y; out[4 * g + 2] = v.z; out[4 * g + 3] = v.w;
+            } else {
+                const float2 v = *reinterpret_cast<const float2*>(p);
+                out[2 * g] = v.x; out[2 * g + 1] = v.y;
+            }
+        }
+    }
+};
+
 template <int LIN, int LOUT>
 __global__ void __launch_bounds__(256) k_wgrad(int64_t n, int64_t rows_per_block, const float* __restrict__ H,
                                                const float* __restrict__ dP, float* __restrict__ partial) {
-    constexpr int TA = LIN / 16, TB = LOUT / 16;
-    __shared__ float sH[32][LIN + 1];
-    __shared__ float sP[32][LOUT + 1];
+    using MA = WgMap<LIN>;
+    using MB = WgMap<LOUT>;
+    constexpr int TA = MA::T, TB = MB::T;
+    __shared__ __align__(16) float sH[32][LIN];
+    __shared__ __align__(16) float sP[32][LOUT];
     const int ta = threadIdx.x / 16, tb = threadIdx.x % 16;
     float acc[TA][TB];
 #pragma unroll
@@ -177,21 +296,22 @@ __global__ void __launch_bounds__(256) k_wgrad(int64_t n, int64_t rows_per_block
     const int64_t hi = lo + rows_per_block < n ? lo + rows_per_block : n;
     for (int64_t r0 = lo; r0 < hi; r0 += 32) {
         __syncthreads();
-        for (int t = threadIdx.x; t < 32 * LIN; t += 256) {
-            const int r = t / LIN, k = t % LIN;
-            sH[r][k] = r0 + r < hi ? H[(r0 + r) * LIN + k] : 0.f;
+        for (int t = threadIdx.x; t < 32 * LIN / 4; t += 256) {
+            const int r = t / (LIN / 4), k = 4 * (t % (LIN / 4));
+            *reinterpret_cast<float4*>(&sH[r][k]) =
+                r0 + r < hi ? __ldg(reinterpret_cast<const float4*>(H + (r0 + r) * LIN + k)) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        for (int t = threadIdx.x; t < 32 * LOUT; t += 256) {
-            const int r = t / LOUT, k = t % LOUT;
-            sP[r][k] = r0 + r < hi ? dP[(r0 + r) * LOUT + k] : 0.f;
+        for (int t = threadIdx.x; t < 32 * LOUT / 4; t += 256) {
+            const int r = t / (LOUT / 4), k = 4 * (t % (LOUT / 4));
+            *reinterpret_cast<float4*>(&sP[r][k]) =
+                r0 + r < hi ? __ldg(reinterpret_cast<const float4*>(dP + (r0 + r) * LOUT + k)) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncthreads();
+#pragma unroll 2
         for (int r = 0; r < 32; ++r) {
             float a[TA], b[TB];
-#pragma unroll
-            for (int x = 0; x < TA; ++x) a[x] = sH[r][ta * TA + x];
-#pragma unroll
-            for (int y = 0; y < TB; ++y) b[y] = sP[r][tb * TB + y];
+            MA::load(sH[r], ta, a);
+            MB::load(sP[r], tb, b);
 #pragma unroll
             for (int x = 0; x < TA; ++x)
 #pragma unroll
@@ -202,7 +322,7 @@ __global__ void __launch_bounds__(256) k_wgrad(int64_t n, int64_t rows_per_block
 #pragma unroll
     for (int x = 0; x < TA; ++x)
 #pragma unroll
-        for (int y = 0; y < TB; ++y) out[(ta * TA + x) * LOUT + tb * TB + y] = acc[x][y];
+        for (int y = 0; y < TB; ++y) out[MA::idx(ta, x) * LOUT + MB::idx(tb, y)] = acc[x][y];
 }
 
 __global__ void k_sum_partials(const float* __restrict__ partial, int blocks, int count, float* __restrict__ out) {
@@ -433,11 +553,12 @@ static int grid_for(int64_t warps_needed) {
 template <int LIN, int LOUT, bool TRANS>
 static cudaError_t rowmm_t(int64_t n, const float* X, const float* W, float* Y, cudaStream_t s) {
     ProfScope ps(s, PF_DIFF_DENSE, 1);
-    const size_t smem = (size_t)(LIN * LOUT + 64 * (LIN + 1)) * sizeof(float);
+    using C = RmCfg<LIN, LOUT>;
+    const size_t smem = C::SMEM;
     auto kern = k_rowmm<LIN, LOUT, TRANS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int64_t blocks = (n + 63) / 64;
+    int64_t blocks = (n + C::TR - 1) / C::TR;
     const int64_t cap = (int64_t)num_sms() * 2;
     if (blocks > cap) blocks = cap;
     kern<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, smem, s>>>(n, X, W, Y);

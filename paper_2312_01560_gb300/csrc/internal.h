@@ -14,10 +14,21 @@ int num_sms();
 
 // Carves typed, 256-byte aligned arrays out of a caller-owned workspace; with a null base
 // it only adds up the size.
+// Carves a caller's workspace into 256-byte aligned pieces.  The base itself is rounded up
+// to 256 bytes (every *_workspace_size() adds 256 bytes for this), so a workspace that starts
+// anywhere still gives aligned pieces; bytes() is what the carve has used, counted from the
+// caller's pointer.
 struct Carver {
     char* base;
+    size_t shift = 0;
     size_t off = 0;
-    explicit Carver(void* b) : base((char*)b) {}
+    explicit Carver(void* b) : base((char*)b) {
+        if (b) {
+            shift = (size_t)((256 - ((uintptr_t)b & 255)) & 255);
+            base += shift;
+        }
+    }
+    size_t bytes() const { return shift + off; }
     template <typename T>
     T* take(size_t count) {
         off = (off + 255) & ~(size_t)255;
