@@ -339,6 +339,27 @@ __global__ void k_sum_partials(const float* __restrict__ partial, int blocks, in
 // ------------------------------------------------------------------------------------
 constexpr int SK = 128;   // padded soft-assignment width
 
+// Squared distances from z (registers) to the lane's centroids lane + 32 u, u < NU, each over
+// ascending coordinates; the coordinate loop is unrolled in full so z stays in registers
+// (lanes past K read row K - 1 and their sums are discarded).
+template <int D, int NU>
+__device__ __forceinline__ void sa_dist(const float* z, const float* smu, int lane, int K, float* s) {
+    constexpr int DP = D + 1;
+    int row[NU];
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+        row[u] = min(lane + 32 * u, K - 1) * DP;
+        s[u] = 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+            const float t = z[k] - smu[row[u] + k];
+            s[u] = fmaf(t, t, s[u]);
+        }
+}
+
 template <int D>
 __global__ void __launch_bounds__(256) k_soft_assign(int64_t n, const float* __restrict__ Z, const float* __restrict__ mu,
                                                      int K, float tau, float* __restrict__ S) {
@@ -349,6 +370,7 @@ __global__ void __launch_bounds__(256) k_soft_assign(int64_t n, const float* __r
     for (int t = threadIdx.x; t < K * D; t += blockDim.x) smu[(t / D) * DP + t % D] = mu[t];
     __syncthreads();
     const int lane = threadIdx.x & 31;
+    const int nu = (K + 31) / 32;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
         float z[D];
@@ -357,19 +379,19 @@ __global__ void __launch_bounds__(256) k_soft_assign(int64_t n, const float* __r
             const float4 v = __ldg(reinterpret_cast<const float4*>(Z + i * D + k));
             z[k] = v.x; z[k + 1] = v.y; z[k + 2] = v.z; z[k + 3] = v.w;
         }
+        float sq[4] = {0.f, 0.f, 0.f, 0.f};
+        switch (nu) {
+            case 1: sa_dist<D, 1>(z, smu, lane, K, sq); break;
+            case 2: sa_dist<D, 2>(z, smu, lane, K, sq); break;
+            case 3: sa_dist<D, 3>(z, smu, lane, K, sq); break;
+            default: sa_dist<D, 4>(z, smu, lane, K, sq); break;
+        }
         float lg[4], mx = -INFINITY;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int c = lane + 32 * u;
             lg[u] = -INFINITY;
-            if (c < K) {
-                float s = 0.f;
-#pragma unroll 8
-                for (int k = 0; k < D; ++k) {
-                    const float t = z[k] - smu[c * DP + k];
-                    s = fmaf(t, t, s);
-                }
-                lg[u] = -s / tau;
+            if (lane + 32 * u < K) {
+                lg[u] = -sq[u] / tau;
                 mx = fmaxf(mx, lg[u]);
             }
         }
@@ -415,28 +437,33 @@ __global__ void __launch_bounds__(256) k_softmod_partials(int64_t n, const int32
     for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
     if (lane == 0) sq[w] = q;
     __syncthreads();
-    double* out = partial + (int64_t)blockIdx.x * (SK + 1);
+    // column-major partials: column c of block b at partial[c * gridDim.x + b]
     for (int c = threadIdx.x; c < SK; c += blockDim.x) {
         double s = 0.0;
         for (int ww = 0; ww < 8; ++ww) s += sdts[ww][c];
-        out[c] = s;
+        partial[(int64_t)c * gridDim.x + blockIdx.x] = s;
     }
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int ww = 0; ww < 8; ++ww) s += sq[ww];
-        out[SK] = s;
+        partial[(int64_t)SK * gridDim.x + blockIdx.x] = s;
     }
 }
 
-// Adds the block partials in block order: red[0..SK) = d^T S, red[SK] = sum S . AS; then
-// red[SK + 1] = the loss -(sum S . AS - ||d^T S||^2 / 2e) / 2e, the squares added over
-// ascending blocks c < K with every product and sum rounded on its own.
-__global__ void k_softmod_finish(const double* __restrict__ partial, int blocks, int K, double two_e,
-                                 double* __restrict__ red) {
-    for (int c = threadIdx.x; c <= SK; c += blockDim.x) {
+// Adds the block partials, one warp per column: lane l takes blocks l, l + 32, ... in order,
+// then the lanes' sums meet in a butterfly (every lane ends with the same total), a fixed
+// order at any launch.  red[0..SK) = d^T S, red[SK] = sum S . AS; then red[SK + 1] = the loss
+// -(sum S . AS - ||d^T S||^2 / 2e) / 2e, the squares added over ascending blocks c < K with
+// every product and sum rounded on its own.
+__global__ void __launch_bounds__(1024) k_softmod_finish(const double* __restrict__ partial, int blocks, int K,
+                                                         double two_e, double* __restrict__ red) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int c = threadIdx.x >> 5; c <= SK; c += nw) {
         double s = 0.0;
-        for (int b = 0; b < blocks; ++b) s += partial[(int64_t)b * (SK + 1) + c];
-        red[c] = s;
+        for (int b = lane; b < blocks; b += 32) s += partial[(int64_t)c * blocks + b];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[c] = s;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -638,8 +665,8 @@ cudaError_t launch_wgrad(int64_t n, const float* H, int lin, const float* dP, in
 }
 
 int softmod_blocks(int64_t n) {
-    int64_t b = (n + 2047) / 2048;
-    const int64_t cap = (int64_t)num_sms() * 2;
+    int64_t b = (n + 255) / 256;
+    const int64_t cap = (int64_t)num_sms() * 4;
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
@@ -666,7 +693,7 @@ cudaError_t launch_softmod_reduce(int64_t n, const int32_t* deg, const float* S,
     const int blocks = softmod_blocks(n);
     const int64_t rpb = (n + blocks - 1) / blocks;
     k_softmod_partials<<<blocks, 256, 0, s>>>(n, deg, S, AS, rpb, partial);
-    k_softmod_finish<<<1, 256, 0, s>>>(partial, blocks, K, two_e, red);
+    k_softmod_finish<<<1, 1024, 0, s>>>(partial, blocks, K, two_e, red);
     return cudaGetLastError();
 }
 
