@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(256, 2) k_rowmm(int64_t n, const float* __rest
 
 // ------------------------------------------------------------------------------------
 // Warp-per-row SpMM over FP32 rows of width L (a multiple of 32; each lane VW = L/32
-// consecutive columns), four neighbour rows in flight per lane.  Modes:
+// consecutive columns), eight neighbour rows in flight per lane.  Modes:
 //   SP_GCN_FWD  out = rownorm(tanh(rsh_i (rsh_i x_i + sum_j rsh_j x_j)))
 //   SP_GCN_BWD  the same T, r, H' recomputed, then with g = dH'_i:
 //               out = (g - H' (H'.g)) / r * (1 - T^2)            (dA of the layer)
@@ -155,10 +155,30 @@ struct RowPiece {
             o[0] = __ldg(p);
         }
     }
+    // read once: evict first
+    __device__ __forceinline__ static void load_once(const float* p, float* o) {
+        if constexpr (VW == 4) {
+            const float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+            o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+        } else if constexpr (VW == 2) {
+            const float2 v = __ldcs(reinterpret_cast<const float2*>(p));
+            o[0] = v.x; o[1] = v.y;
+        } else {
+            o[0] = __ldcs(p);
+        }
+    }
+    // STREAM: evict-first store, for outputs that no later pass gathers from
+    template <bool STREAM>
     __device__ __forceinline__ static void store(float* p, const float* v) {
-        if constexpr (VW == 4) *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-        else if constexpr (VW == 2) *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
-        else p[0] = v[0];
+        if constexpr (VW == 4) {
+            const float4 x = make_float4(v[0], v[1], v[2], v[3]);
+            if constexpr (STREAM) __stcs(reinterpret_cast<float4*>(p), x); else *reinterpret_cast<float4*>(p) = x;
+        } else if constexpr (VW == 2) {
+            const float2 x = make_float2(v[0], v[1]);
+            if constexpr (STREAM) __stcs(reinterpret_cast<float2*>(p), x); else *reinterpret_cast<float2*>(p) = x;
+        } else {
+            if constexpr (STREAM) __stcs(p, v[0]); else p[0] = v[0];
+        }
     }
 };
 
@@ -182,18 +202,18 @@ __global__ void __launch_bounds__(256) k_spmm32(Csr<OffT> g, const float* __rest
         }
         const int64_t b = g.begin(i), e = g.end(i);
         int64_t p = b;
-        for (; p + 4 <= e; p += 4) {
-            int j[4];
-            float w[4], x[4][VW];
+        for (; p + 8 <= e; p += 8) {
+            int j[8];
+            float w[8], x[8][VW];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) j[u] = __ldg(g.col + p + u);
+            for (int u = 0; u < 8; ++u) j[u] = __ldg(g.col + p + u);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
                 w[u] = MODE == SP_ADJ ? 1.f : __ldg(rsh + j[u]);
                 RowPiece<VW>::load(X + (int64_t)j[u] * L + lane * VW, x[u]);
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 8; ++u)
 #pragma unroll
                 for (int v = 0; v < VW; ++v) acc[v] = fmaf(w[u], x[u][v], acc[v]);
         }
@@ -207,14 +227,14 @@ __global__ void __launch_bounds__(256) k_spmm32(Csr<OffT> g, const float* __rest
         }
         float* o = out + i * L + lane * VW;
         if constexpr (MODE == SP_ADJ) {
-            RowPiece<VW>::store(o, acc);
+            RowPiece<VW>::template store<true>(o, acc);
             continue;
         } else {
 #pragma unroll
             for (int v = 0; v < VW; ++v) acc[v] *= wi;
         }
         if constexpr (MODE == SP_LINEAR) {
-            RowPiece<VW>::store(o, acc);
+            RowPiece<VW>::template store<true>(o, acc);
             continue;
         }
         float T[VW], ss = 0.f;
@@ -230,11 +250,11 @@ __global__ void __launch_bounds__(256) k_spmm32(Csr<OffT> g, const float* __rest
             float h[VW];
 #pragma unroll
             for (int v = 0; v < VW; ++v) h[v] = T[v] * inv;
-            RowPiece<VW>::store(o, h);
+            RowPiece<VW>::template store<true>(o, h);
         } else {
             float H[VW], gv[VW], dot = 0.f;
             const float inv = r > 0.f ? 1.0f / r : 0.f;
-            RowPiece<VW>::load(G + i * L + lane * VW, gv);
+            RowPiece<VW>::load_once(G + i * L + lane * VW, gv);
 #pragma unroll
             for (int v = 0; v < VW; ++v) {
                 H[v] = T[v] * inv;
@@ -244,7 +264,7 @@ __global__ void __launch_bounds__(256) k_spmm32(Csr<OffT> g, const float* __rest
             float d[VW];
 #pragma unroll
             for (int v = 0; v < VW; ++v) d[v] = (gv[v] - H[v] * dot) * inv * (1.0f - T[v] * T[v]);
-            RowPiece<VW>::store(o, d);
+            RowPiece<VW>::template store<false>(o, d);   // dA: the next pass gathers it
         }
     }
 }
@@ -325,11 +345,20 @@ __global__ void __launch_bounds__(256) k_wgrad(int64_t n, int64_t rows_per_block
         for (int y = 0; y < TB; ++y) out[MA::idx(ta, x) * LOUT + MB::idx(tb, y)] = acc[x][y];
 }
 
+// Four FP64 chains over the blocks (block b into chain b mod 4, the tail into chain 0),
+// joined as (s0 + s1) + (s2 + s3): a fixed order for a given block count.
 __global__ void k_sum_partials(const float* __restrict__ partial, int blocks, int count, float* __restrict__ out) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < blocks; ++b) s += (double)partial[(int64_t)b * count + t];
-        out[t] = (float)s;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int b = 0;
+        for (; b + 4 <= blocks; b += 4) {
+            s0 += (double)partial[(int64_t)b * count + t];
+            s1 += (double)partial[(int64_t)(b + 1) * count + t];
+            s2 += (double)partial[(int64_t)(b + 2) * count + t];
+            s3 += (double)partial[(int64_t)(b + 3) * count + t];
+        }
+        for (; b < blocks; ++b) s0 += (double)partial[(int64_t)b * count + t];
+        out[t] = (float)((s0 + s1) + (s2 + s3));
     }
 }
 
@@ -473,55 +502,95 @@ __global__ void __launch_bounds__(1024) k_softmod_finish(const double* __restric
     }
 }
 
+// dL/dZ for tiles of SG_TP nodes.  Phase 1, a warp per node: G_i = -S_i (g_i - S_i . g_i) / tau
+// with g_i = -(AS_i - d_i d^T S / 2e) / e, into shared memory with the node's sum of G.
+// Phase 2: M = G mu for the tile from register tiles (thread: SG_TP / PG nodes x 8 coordinates
+// 4 cg + 4 CG h + q, so a warp's 16-byte reads of mu fall in distinct banks; the G rows have an
+// odd stride), each entry fmaf over ascending c from zero; then dZ = 2 (sum G z - M).
+constexpr int SG_TP = 64;
+
 template <int D>
 __global__ void __launch_bounds__(256) k_softmod_grad(int64_t n, const float* __restrict__ Z, const float* __restrict__ mu,
                                                       int K, float tau, const int32_t* __restrict__ deg,
                                                       const float* __restrict__ S, const float* __restrict__ AS,
                                                       const double* __restrict__ red, double two_e,
                                                       float* __restrict__ dZ) {
-    extern __shared__ float smu[];   // K x D, then SK values of d^T S / 2e
+    constexpr int CG = D / 8, PG = 256 / CG, PPT = SG_TP / PG;
+    const int KP = K + ((K & 1) ? 2 : 1);   // odd row stride of the G tile
+    extern __shared__ __align__(16) float smu[];   // K x D, SK values of d^T S / 2e, G tile, sums
     float* sdts = smu + K * D;
+    float* sG = sdts + SK;
+    float* sgs = sG + SG_TP * KP;
     for (int t = threadIdx.x; t < K * D; t += blockDim.x) smu[t] = mu[t];
     for (int c = threadIdx.x; c < SK; c += blockDim.x) sdts[c] = (float)(red[c] / two_e);
-    __syncthreads();
     const float inv_e = (float)(2.0 / two_e);
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
-        const float di = (float)__ldg(deg + i);
-        float s[4], gs[4], sdot = 0.f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cg = threadIdx.x % CG, pg = threadIdx.x / CG;
+    const int64_t tiles = (n + SG_TP - 1) / SG_TP;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t t0 = tile * SG_TP;
+        __syncthreads();   // the previous tile's G is consumed (and mu is in place)
+        for (int pp = warp; pp < SG_TP; pp += 8) {
+            const int64_t i = t0 + pp;
+            if (i >= n) break;
+            const float di = (float)__ldg(deg + i);
+            float s[4], gs[4], sdot = 0.f;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int c = lane + 32 * u;
-            s[u] = __ldg(S + i * SK + c);
-            gs[u] = c < K ? -(__ldg(AS + i * SK + c) - di * sdts[c]) * inv_e : 0.f;
-            sdot = fmaf(s[u], gs[u], sdot);
+            for (int u = 0; u < 4; ++u) {
+                const int c = lane + 32 * u;
+                s[u] = __ldg(S + i * SK + c);
+                gs[u] = c < K ? -(__ldg(AS + i * SK + c) - di * sdts[c]) * inv_e : 0.f;
+                sdot = fmaf(s[u], gs[u], sdot);
+            }
+            sdot = warp_sum(sdot);
+            float G[4], gsum = 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                G[u] = -s[u] * (gs[u] - sdot) / tau;
+                gsum += G[u];
+            }
+            gsum = warp_sum(gsum);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (lane + 32 * u < K) sG[pp * KP + lane + 32 * u] = G[u];
+            if (lane == 0) sgs[pp] = gsum;
         }
-        sdot = warp_sum(sdot);
-        float G[4], gsum = 0.f;
+        __syncthreads();
+        float m[PPT][8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            G[u] = -s[u] * (gs[u] - sdot) / tau;
-            gsum += G[u];
-        }
-        gsum = warp_sum(gsum);
-        // dZ_i[k] = 2 gsum z_ik - 2 sum_c G_c mu_ck, lanes over coordinates
-        float m[D / 32];
+        for (int a = 0; a < PPT; ++a)
 #pragma unroll
-        for (int q = 0; q < D / 32; ++q) m[q] = 0.f;
+            for (int j = 0; j < 8; ++j) m[a][j] = 0.f;
+        for (int c = 0; c < K; ++c) {
+            const float4 b0 = *reinterpret_cast<const float4*>(smu + c * D + 4 * cg);
+            const float4 b1 = *reinterpret_cast<const float4*>(smu + c * D + 4 * CG + 4 * cg);
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int cend = K - 32 * u < 32 ? K - 32 * u : 32;
-            for (int l = 0; l < cend; ++l) {
-                const float Gc = __shfl_sync(0xffffffffu, G[u], l);
-                const int c = 32 * u + l;
+            for (int a = 0; a < PPT; ++a) {
+                const float g = sG[(pg + PG * a) * KP + c];
 #pragma unroll
-                for (int q = 0; q < D / 32; ++q) m[q] = fmaf(Gc, smu[c * D + lane + 32 * q], m[q]);
+                for (int j = 0; j < 8; ++j) m[a][j] = fmaf(g, bv[j], m[a][j]);
             }
         }
 #pragma unroll
-        for (int q = 0; q < D / 32; ++q)
-            dZ[i * D + lane + 32 * q] = 2.0f * (gsum * __ldg(Z + i * D + lane + 32 * q) - m[q]);
+        for (int a = 0; a < PPT; ++a) {
+            const int pp = pg + PG * a;
+            const int64_t i = t0 + pp;
+            if (i < n) {
+                const float gsum = sgs[pp];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k0 = 4 * cg + 4 * CG * h;
+                    const float4 z = __ldg(reinterpret_cast<const float4*>(Z + i * D + k0));
+                    float4 o;
+                    o.x = 2.0f * (gsum * z.x - m[a][4 * h]);
+                    o.y = 2.0f * (gsum * z.y - m[a][4 * h + 1]);
+                    o.z = 2.0f * (gsum * z.z - m[a][4 * h + 2]);
+                    o.w = 2.0f * (gsum * z.w - m[a][4 * h + 3]);
+                    *reinterpret_cast<float4*>(dZ + i * D + k0) = o;
+                }
+            }
+        }
     }
 }
 
@@ -639,8 +708,9 @@ cudaError_t launch_spmm32(const raftgp_csr* g, int L, const float* rsh, const fl
     return spmm32_w(c, L, rsh, X, G, out, mode, s);
 }
 
+// Two CTAs on every SM (the widest form holds 101 registers a thread), rows split evenly.
 int wgrad_blocks(int64_t n) {
-    int64_t b = (n + 1023) / 1024;
+    int64_t b = (n + 255) / 256;
     const int64_t cap = (int64_t)num_sms() * 2;
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
@@ -701,18 +771,18 @@ cudaError_t launch_softmod_grad(int64_t n, int d, const float* Z, const float* m
                                 const float* S, const float* AS, const double* red, double two_e, float* dZ,
                                 cudaStream_t s) {
     ProfScope ps(s, PF_DIFF_LOSS, 1);
-    const size_t smem = (size_t)(K * d + SK) * sizeof(float);
-    const int blocks = grid_for(n);
-    switch (d) {
-        case 32: k_softmod_grad<32><<<blocks, 256, smem, s>>>(n, Z, mu, K, tau, deg, S, AS, red, two_e, dZ); break;
-        case 64: k_softmod_grad<64><<<blocks, 256, smem, s>>>(n, Z, mu, K, tau, deg, S, AS, red, two_e, dZ); break;
-        case 128:
-            cudaFuncSetAttribute(k_softmod_grad<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_softmod_grad<128><<<blocks, 256, smem, s>>>(n, Z, mu, K, tau, deg, S, AS, red, two_e, dZ);
-            break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
+    const int KP = K + ((K & 1) ? 2 : 1);
+    const size_t smem = (size_t)(K * d + SK + SG_TP * KP + SG_TP) * sizeof(float);
+    int64_t blocks = (n + SG_TP - 1) / SG_TP;
+    const int64_t cap = (int64_t)num_sms() * 4;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+#define RAFTGP_SG(DD)                                                                                   if (d == DD) {                                                                                          cudaError_t e = cudaFuncSetAttribute(k_softmod_grad<DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         if (e != cudaSuccess) return e;                                                                     k_softmod_grad<DD><<<(unsigned)blocks, 256, smem, s>>>(n, Z, mu, K, tau, deg, S, AS, red, two_e, dZ);         return cudaGetLastError();                                                                      }
+    RAFTGP_SG(32)
+    RAFTGP_SG(64)
+    RAFTGP_SG(128)
+#undef RAFTGP_SG
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_adam(float* p, const float* g, float* m, float* v, int64_t count, float lr, float b1, float b2,
