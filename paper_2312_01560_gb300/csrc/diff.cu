@@ -673,17 +673,27 @@ cudaError_t launch_rowmm(int64_t n, const float* X, int lin, const float* W, int
     return cudaErrorInvalidValue;
 }
 
+// CTAs of two warps, a warp per row: row lengths follow a power law, and small CTAs let the
+// block scheduler balance them (a CTA's warp slots stay held until its slowest row is done).
+template <typename OffT, int VW, int MODE>
+static cudaError_t spmm32_launch(const Csr<OffT>& g, const float* rsh, const float* X, const float* G, float* out,
+                                 cudaStream_t s) {
+    int64_t blocks = (g.n + 1) / 2;
+    if (blocks > (int64_t)INT32_MAX) blocks = INT32_MAX;
+    if (blocks < 1) blocks = 1;
+    k_spmm32<OffT, VW, MODE><<<(unsigned)blocks, 64, 0, s>>>(g, rsh, X, G, out);
+    return cudaGetLastError();
+}
+
 template <typename OffT, int VW>
 static cudaError_t spmm32_t(const Csr<OffT>& g, const float* rsh, const float* X, const float* G, float* out, int mode,
                             cudaStream_t s) {
-    const int blocks = grid_for(g.n);
     switch (mode) {
-        case SP_GCN_FWD: k_spmm32<OffT, VW, SP_GCN_FWD><<<blocks, 256, 0, s>>>(g, rsh, X, G, out); break;
-        case SP_GCN_BWD: k_spmm32<OffT, VW, SP_GCN_BWD><<<blocks, 256, 0, s>>>(g, rsh, X, G, out); break;
-        case SP_LINEAR: k_spmm32<OffT, VW, SP_LINEAR><<<blocks, 256, 0, s>>>(g, rsh, X, G, out); break;
-        default: k_spmm32<OffT, VW, SP_ADJ><<<blocks, 256, 0, s>>>(g, rsh, X, G, out); break;
+        case SP_GCN_FWD: return spmm32_launch<OffT, VW, SP_GCN_FWD>(g, rsh, X, G, out, s);
+        case SP_GCN_BWD: return spmm32_launch<OffT, VW, SP_GCN_BWD>(g, rsh, X, G, out, s);
+        case SP_LINEAR: return spmm32_launch<OffT, VW, SP_LINEAR>(g, rsh, X, G, out, s);
+        default: return spmm32_launch<OffT, VW, SP_ADJ>(g, rsh, X, G, out, s);
     }
-    return cudaGetLastError();
 }
 
 template <typename OffT>
