@@ -439,7 +439,10 @@ __global__ void __launch_bounds__(256) k_soft_assign(int64_t n, const float* __r
     }
 }
 
-// Per-block FP64 partials of d^T S (SK columns) and of sum_i S_i . (AS)_i (column SK).
+// Per-block FP64 partials of d^T S (SK columns) and of sum_i S_i . (AS)_i (column SK).  Each
+// lane adds its products in FP32 over eight of its warp's rows, then moves that short sum into
+// its FP64 totals: FP64 runs at a small fraction of the FP32 rate here, and one FP64 update per
+// product made this kernel arithmetic-bound.
 __global__ void __launch_bounds__(256) k_softmod_partials(int64_t n, const int32_t* __restrict__ deg,
                                                           const float* __restrict__ S, const float* __restrict__ AS,
                                                           int64_t rows_per_block, double* __restrict__ partial) {
@@ -447,19 +450,32 @@ __global__ void __launch_bounds__(256) k_softmod_partials(int64_t n, const int32
     __shared__ double sq[8];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     double dts[4] = {0, 0, 0, 0}, q = 0.0;
+    float fd[4] = {0.f, 0.f, 0.f, 0.f}, fq = 0.f;
+    int rows = 0;
     const int64_t lo = (int64_t)blockIdx.x * rows_per_block;
     const int64_t hi = lo + rows_per_block < n ? lo + rows_per_block : n;
     for (int64_t i = lo + w; i < hi; i += 8) {
-        const double di = (double)__ldg(deg + i);
-        double qi = 0.0;
+        const float di = (float)__ldg(deg + i);
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const float s = __ldg(S + i * SK + lane + 32 * u);
-            dts[u] += di * (double)s;
-            qi += (double)s * (double)__ldg(AS + i * SK + lane + 32 * u);
+            fd[u] = fmaf(di, s, fd[u]);
+            fq = fmaf(s, __ldg(AS + i * SK + lane + 32 * u), fq);
         }
-        q += qi;
+        if (++rows == 8) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                dts[u] += (double)fd[u];
+                fd[u] = 0.f;
+            }
+            q += (double)fq;
+            fq = 0.f;
+            rows = 0;
+        }
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) dts[u] += (double)fd[u];
+    q += (double)fq;
 #pragma unroll
     for (int u = 0; u < 4; ++u) sdts[w][lane + 32 * u] = dts[u];
 #pragma unroll
