@@ -345,20 +345,36 @@ __global__ void __launch_bounds__(256) k_wgrad(int64_t n, int64_t rows_per_block
         for (int y = 0; y < TB; ++y) out[MA::idx(ta, x) * LOUT + MB::idx(tb, y)] = acc[x][y];
 }
 
-// Four FP64 chains over the blocks (block b into chain b mod 4, the tail into chain 0),
-// joined as (s0 + s1) + (s2 + s3): a fixed order for a given block count.
-__global__ void k_sum_partials(const float* __restrict__ partial, int blocks, int count, float* __restrict__ out) {
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int b = 0;
-        for (; b + 4 <= blocks; b += 4) {
+// dW from the block partials: 32 entries per CTA, each entry's blocks cut into SP_SEG
+// contiguous ranges, a warp per range (lane = entry, so every read is 128 contiguous bytes);
+// a range is summed in four FP64 chains (block b of the range into chain b mod 4, joined as
+// (s0 + s1) + (s2 + s3)), then the ranges are added in order: a fixed order for a given block
+// count.
+constexpr int SP_SEG = 8;
+__global__ void __launch_bounds__(256) k_sum_partials(const float* __restrict__ partial, int blocks, int count,
+                                                      float* __restrict__ out) {
+    __shared__ double part[SP_SEG][32];
+    const int e = threadIdx.x & 31, seg = threadIdx.x >> 5;
+    const int t = blockIdx.x * 32 + e;
+    const int per = (blocks + SP_SEG - 1) / SP_SEG;
+    const int b0 = seg * per, b1 = min(blocks, b0 + per);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    if (t < count) {
+        int b = b0;
+        for (; b + 4 <= b1; b += 4) {
             s0 += (double)partial[(int64_t)b * count + t];
             s1 += (double)partial[(int64_t)(b + 1) * count + t];
             s2 += (double)partial[(int64_t)(b + 2) * count + t];
             s3 += (double)partial[(int64_t)(b + 3) * count + t];
         }
-        for (; b < blocks; ++b) s0 += (double)partial[(int64_t)b * count + t];
-        out[t] = (float)((s0 + s1) + (s2 + s3));
+        for (; b < b1; ++b) s0 += (double)partial[(int64_t)b * count + t];
+    }
+    part[seg][e] = (s0 + s1) + (s2 + s3);
+    __syncthreads();
+    if (seg == 0 && t < count) {
+        double s = 0.0;
+        for (int k = 0; k < SP_SEG; ++k) s += part[k][e];
+        out[t] = (float)s;
     }
 }
 
@@ -756,7 +772,7 @@ cudaError_t launch_wgrad(int64_t n, const float* H, int lin, const float* dP, in
 #undef RAFTGP_WG
     if (!done) return cudaErrorInvalidValue;
     const int count = lin * lout;
-    k_sum_partials<<<(count + 255) / 256, 256, 0, s>>>(partial, blocks, count, dW);
+    k_sum_partials<<<(count + 31) / 32, 256, 0, s>>>(partial, blocks, count, dW);
     return cudaGetLastError();
 }
 
