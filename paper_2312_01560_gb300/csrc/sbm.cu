@@ -178,19 +178,46 @@ __global__ void k_sbm_fill(const int32_t* block, const double* theta, int64_t n,
     }
 }
 
-// Per block (one thread each, left to right): Pre_r[k] = sum_{q<k} theta, and
-// Tri_r[a] = sum_{a'<a} theta_a' (Tot_r - Pre_r[a'+1]).
-__global__ void k_sbm_prefix(int K, const unsigned long long* bincl, const double* th, double* pre, double* tri) {
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < K; r += gridDim.x * blockDim.x) {
+// Per block, a warp each, left to right: Pre_r[k] = sum_{q<k} theta, and
+// Tri_r[a] = sum_{a'<a} theta_a' (Tot_r - Pre_r[a'+1]).  The lanes load 32 terms at a time;
+// the running sum then takes them one by one through shuffles, every lane doing the same
+// additions in the same order (so all hold the same value): the sums of a sequential loop,
+// without a round trip through memory between one term and the next.
+__global__ void k_sbm_prefix(int K, const unsigned long long* __restrict__ bincl, const double* __restrict__ th,
+                             double* __restrict__ pre, double* __restrict__ tri) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < K; r += warps) {
         const int64_t o = r == 0 ? 0 : (int64_t)bincl[r - 1];
         const int64_t nr = (int64_t)bincl[r] - o;
         double* P = pre + o + r;
         double* T = tri + o + r;
-        P[0] = 0.0;
-        for (int64_t k = 0; k < nr; ++k) P[k + 1] = __dadd_rn(P[k], th[o + k]);
-        const double tot = P[nr];
-        T[0] = 0.0;
-        for (int64_t a = 0; a < nr; ++a) T[a + 1] = __dadd_rn(T[a], __dmul_rn(th[o + a], __dsub_rn(tot, P[a + 1])));
+        double run = 0.0;
+        for (int64_t base = 0; base < nr; base += 32) {
+            const int cnt = nr - base < 32 ? (int)(nr - base) : 32;
+            const double v = lane < cnt ? th[o + base + lane] : 0.0;
+            double mine = 0.0;
+            for (int j = 0; j < cnt; ++j) {
+                run = __dadd_rn(run, __shfl_sync(0xffffffffu, v, j));
+                if (lane == j) mine = run;
+            }
+            if (lane < cnt) P[base + lane + 1] = mine;
+        }
+        if (lane == 0) P[0] = 0.0;
+        const double tot = run;
+        __syncwarp();
+        run = 0.0;
+        for (int64_t base = 0; base < nr; base += 32) {
+            const int cnt = nr - base < 32 ? (int)(nr - base) : 32;
+            const double x = lane < cnt ? __dmul_rn(th[o + base + lane], __dsub_rn(tot, P[base + lane + 1])) : 0.0;
+            double mine = 0.0;
+            for (int j = 0; j < cnt; ++j) {
+                run = __dadd_rn(run, __shfl_sync(0xffffffffu, x, j));
+                if (lane == j) mine = run;
+            }
+            if (lane < cnt) T[base + lane + 1] = mine;
+        }
+        if (lane == 0) T[0] = 0.0;
     }
 }
 
@@ -247,6 +274,8 @@ __device__ __forceinline__ void seg_setup(const SbmDev& d, int64_t g, SbmPairDev
 // loops of similar length.  Which thread runs a segment changes nothing in its draws or in
 // where its edges go.
 constexpr int SBM_BUCKETS = 32;
+// Buckets from here on (about 255 expected draws and more) run a warp per segment.
+constexpr int SBM_HEAVY = 16;
 __device__ __forceinline__ int seg_bucket(double w) {
     if (!(w > 0.0)) return 0;                       // zero (and NaN: never sampled, flagged before)
     if (!(w < 1.0e9)) return SBM_BUCKETS - 1;       // huge or infinite
@@ -304,13 +333,17 @@ __global__ void __launch_bounds__(256) k_sbm_seg_scatter(int64_t G, const uint8_
     }
 }
 
-// One thread per global segment (taken in `order`): Algorithm 2's loop on the segment.  COUNT
+// One thread per global segment: Algorithm 2's loop on the segment.  The segments are taken
+// from `order` positions [0, *split) (all G without an order), heaviest bucket first.  COUNT
 // mode stores the number of edges; EMIT mode writes them at the segment's offset.
 template <bool EMIT>
 __global__ void __launch_bounds__(128) k_sbm_segments(SbmDev d, int64_t G, const uint32_t* order,
-                                                      unsigned long long* seg_cnt, const unsigned long long* seg_incl,
-                                                      int32_t* src, int32_t* dst, int32_t* weight) {
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < G; idx += (int64_t)gridDim.x * blockDim.x) {
+                                                      const unsigned long long* split, unsigned long long* seg_cnt,
+                                                      const unsigned long long* seg_incl, int32_t* src, int32_t* dst,
+                                                      int32_t* weight) {
+    const int64_t end = split ? (int64_t)*split : G;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < end; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t idx = end - 1 - k;
         const int64_t g = order ? (int64_t)order[idx] : idx;
         SbmPairDev P;
         int64_t t0, t1;
@@ -347,6 +380,93 @@ __global__ void __launch_bounds__(128) k_sbm_segments(SbmDev d, int64_t G, const
             m = a0 + 1;
         }
         if (!EMIT) seg_cnt[g] = (unsigned long long)count;
+    }
+}
+
+// The binary search of Algorithm 2's skip (the first entry a in [a0, a1] with F(a + 1) > V),
+// five levels per round: lane L < 31 evaluates node L + 1 of the next five levels' decision
+// tree (heap order; node h's children are 2h, taken when the probe is true, and 2h + 1) at the
+// range the one-thread search would hold there, then the warp follows the actual outcomes.  It
+// reaches the same entry as the one-thread search through the same probes, so the result does
+// not depend on F being monotone in its rounding.
+__device__ __forceinline__ void warp_skip_search(const SbmPairDev& P, double V, int64_t& a0, int64_t& a1, int lane) {
+    while (a0 < a1) {
+        const int h = lane + 1;
+        const int depth = 31 - __clz(h);
+        int64_t lo = a0, hi = a1;
+        bool live = lane < 31;
+        for (int dd = depth - 1; dd >= 0 && live; --dd) {
+            if (lo >= hi) {
+                live = false;
+                break;
+            }
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (((h >> dd) & 1) == 0) hi = mid;
+            else lo = mid + 1;
+        }
+        bool pr = false;
+        if (live && lo < hi) pr = prefix_mass(P, lo + (hi - lo) / 2 + 1) > V;
+        const unsigned res = __ballot_sync(0xffffffffu, pr);
+        int node = 1;
+        for (int step = 0; step < 5 && a0 < a1; ++step) {
+            const int64_t mid = a0 + (a1 - a0) / 2;
+            if ((res >> (node - 1)) & 1u) {
+                a1 = mid;
+                node = 2 * node;
+            } else {
+                a0 = mid + 1;
+                node = 2 * node + 1;
+            }
+        }
+    }
+}
+
+// A warp per segment for order positions [*split, G), the heaviest buckets (a segment there
+// holds hundreds to thousands of edges, and one thread's chain of dependent probes through the
+// heaviest set the length of the whole pass), heaviest first.  Every lane draws the same
+// numbers; lane 0 writes.
+template <bool EMIT>
+__global__ void __launch_bounds__(256) k_sbm_segments_warp(SbmDev d, int64_t G, const uint32_t* __restrict__ order,
+                                                           const unsigned long long* __restrict__ split,
+                                                           unsigned long long* seg_cnt,
+                                                           const unsigned long long* seg_incl, int32_t* src,
+                                                           int32_t* dst, int32_t* weight) {
+    const int lane = threadIdx.x & 31;
+    const int64_t begin = (int64_t)*split;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; begin + k < G; k += nw) {
+        const int64_t g = (int64_t)order[G - 1 - k];
+        SbmPairDev P;
+        int64_t t0, t1;
+        seg_setup(d, g, P, t0, t1);
+        const double Fend = prefix_mass(P, t1);
+        int64_t out = EMIT ? (int64_t)seg_incl[g] - (int64_t)seg_cnt[g] : 0;
+        const int64_t cap = EMIT ? (int64_t)seg_cnt[g] : 0;
+        int64_t count = 0;
+        int64_t m = t0;
+        uint32_t j = 0;
+        while (m < t1) {
+            const U32x4 x = philox4x32_10((uint32_t)g, (uint32_t)((uint64_t)g >> 32), j, STREAM_SBM, d.seed);
+            ++j;
+            const uint64_t w01 = (uint64_t)x.x | ((uint64_t)x.y << 32);
+            const uint64_t w23 = (uint64_t)x.z | ((uint64_t)x.w << 32);
+            const double pu = __dmul_rn((double)((w01 >> 11) + 1), TWO_M53);
+            const double V = __dadd_rn(prefix_mass(P, m), -log(pu));
+            if (!(Fend > V)) break;
+            int64_t a0 = m, a1 = t1 - 1;
+            warp_skip_search(P, V, a0, a1, lane);
+            if (EMIT && count < cap && lane == 0) {
+                int64_t a, b;
+                table_entry(P, a0, a, b);
+                src[out] = P.nodes_r[a];
+                dst[out] = P.nodes_s[b];
+                if (weight) weight[out] = pois_ge1(__dmul_rn(P.om, __dmul_rn(P.th_r[a], P.th_s[b])), w23);
+            }
+            if (EMIT && count < cap) ++out;
+            ++count;
+            m = a0 + 1;
+        }
+        if (!EMIT && lane == 0) seg_cnt[g] = (unsigned long long)count;
     }
 }
 
@@ -458,6 +578,18 @@ int grid_for(int64_t items, int threads) {
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
+// One resident wave of the warp-per-segment kernel (its CTAs per SM from the occupancy API).
+template <bool EMIT>
+int sbm_warp_grid() {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sbm_segments_warp<EMIT>, 256, 0) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+    }
+    return num_sms() * per_sm;
+}
+
 // ---- workspace ---------------------------------------------------------------------------
 int64_t sbm_max_segments(int64_t n, int K) {
     const int64_t npairs = (int64_t)K * (K + 1) / 2;
@@ -499,7 +631,7 @@ cudaError_t sbm_count(const raftgp_sbm* p, const SbmWs& w, int64_t* G_out, int64
     k_sbm_count_blocks<<<grid_for(n, 256), 256, 0, s>>>(p->block, p->theta, n, K, w.bcnt, w.err);
     scan_incl(w.bcnt, K, w.bincl, w.tiles, s);
     k_sbm_fill<<<grid_for((int64_t)K * 32, 256), 256, 0, s>>>(p->block, p->theta, n, K, w.bincl, w.nodes, w.th);
-    k_sbm_prefix<<<grid_for(K, 128), 128, 0, s>>>(K, w.bincl, w.th, w.pre, w.tri);
+    k_sbm_prefix<<<grid_for((int64_t)K * 32, 128), 128, 0, s>>>(K, w.bincl, w.th, w.pre, w.tri);
     SbmDev d{n, K, p->seed, p->omega, w.bincl, w.nodes, w.th, w.pre, w.tri, w.pincl, npairs};
     k_sbm_pair_segs<<<grid_for(npairs, 256), 256, 0, s>>>(d, w.pseg, w.err);
     scan_incl(w.pseg, npairs, w.pincl, w.tiles, s);
@@ -522,8 +654,12 @@ cudaError_t sbm_count(const raftgp_sbm* p, const SbmWs& w, int64_t* G_out, int64
             k_sbm_seg_scatter<<<grid_for((int64_t)G, 256), 256, 0, s>>>((int64_t)G, w.seg_key, w.bucket + SBM_BUCKETS,
                                                                          w.seg_order);
         }
-        k_sbm_segments<false><<<grid_for((int64_t)G, 128), 128, 0, s>>>(d, (int64_t)G, order, w.seg_cnt, nullptr,
-                                                                         nullptr, nullptr, nullptr);
+        const unsigned long long* split = order ? w.bucket + SBM_BUCKETS + (SBM_HEAVY - 1) : nullptr;
+        k_sbm_segments<false><<<grid_for((int64_t)G, 128), 128, 0, s>>>(d, (int64_t)G, order, split, w.seg_cnt,
+                                                                         nullptr, nullptr, nullptr, nullptr);
+        if (order)
+            k_sbm_segments_warp<false><<<sbm_warp_grid<false>(), 256, 0, s>>>(d, (int64_t)G, order, split, w.seg_cnt,
+                                                                               nullptr, nullptr, nullptr, nullptr);
         scan_incl(w.seg_cnt, (int64_t)G, w.seg_incl, w.tiles, s);
     }
     unsigned long long m = 0;
@@ -543,7 +679,11 @@ cudaError_t sbm_emit(const raftgp_sbm* p, const SbmWs& w, int64_t G, int32_t* sr
     SbmDev d{p->n, K, p->seed, p->omega, w.bincl, w.nodes, w.th, w.pre, w.tri, w.pincl, npairs};
     ProfScope ps(s, PF_OTHER, 1);
     const uint32_t* order = (unsigned long long)G < (1ull << 32) ? w.seg_order : nullptr;
-    k_sbm_segments<true><<<grid_for(G, 128), 128, 0, s>>>(d, G, order, w.seg_cnt, w.seg_incl, src, dst, weight);
+    const unsigned long long* split = order ? w.bucket + SBM_BUCKETS + (SBM_HEAVY - 1) : nullptr;
+    k_sbm_segments<true><<<grid_for(G, 128), 128, 0, s>>>(d, G, order, split, w.seg_cnt, w.seg_incl, src, dst, weight);
+    if (order)
+        k_sbm_segments_warp<true><<<sbm_warp_grid<true>(), 256, 0, s>>>(d, G, order, split, w.seg_cnt, w.seg_incl, src,
+                                                                         dst, weight);
     return cudaGetLastError();
 }
 
