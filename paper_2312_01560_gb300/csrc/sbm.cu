@@ -49,7 +49,7 @@ __device__ __forceinline__ void pair_rs(int64_t K, int64_t p, int& r, int& s) {
 struct SbmPairDev {
     bool tri;
     int64_t nr, ns;
-    double inv_ns;        // 1 / ns: the row estimate of a rectangular table (corrected exactly)
+    float inv_ns;         // 1 / ns: the row estimate of a rectangular table (corrected exactly)
     const int32_t* nodes_r;
     const int32_t* nodes_s;
     const double* th_r;
@@ -62,10 +62,13 @@ struct SbmPairDev {
 
 __device__ __forceinline__ int64_t tri_row_start(int64_t n, int64_t a) { return a * n - a * (a + 1) / 2; }
 
+// Row a and column b of linear index t.  Both are exact integers: an FP32 estimate of the row
+// (FP64 runs at a small fraction of the FP32 rate here, and the prefix-mass probes that call
+// this made the sampler FP64-bound), then exact integer steps to the row that holds t.
 __device__ __forceinline__ void table_entry(const SbmPairDev& P, int64_t t, int64_t& a, int64_t& b) {
     if (!P.tri) {
-        // a = t / ns without a 64-bit division: an FP64 estimate, then exact integer steps
-        int64_t r = (int64_t)__dmul_rn((double)t, P.inv_ns);
+        int64_t r = (int64_t)__fmul_rn((float)t, P.inv_ns);
+        if (r < 0) r = 0;
         while (r > 0 && r * P.ns > t) --r;
         while ((r + 1) * P.ns <= t) ++r;
         a = r;
@@ -79,9 +82,10 @@ __device__ __forceinline__ void table_entry(const SbmPairDev& P, int64_t t, int6
         b = n;
         return;
     }
-    const double q = (double)(2 * n - 1);
-    const double disc = __dsub_rn(__dmul_rn(q, q), __dmul_rn(8.0, (double)t));
-    int64_t r = (int64_t)(__dmul_rn(__dsub_rn(q, __dsqrt_rn(disc)), 0.5));
+    // row a solves a^2 - (2n - 1) a + 2t = 0; the discriminant in exact unsigned arithmetic
+    const uint64_t q = (uint64_t)(2 * n - 1);
+    const uint64_t disc = q * q - 8ull * (uint64_t)t;
+    int64_t r = (int64_t)__fmul_rn(__fsub_rn((float)q, __fsqrt_rn((float)disc)), 0.5f);
     if (r < 0) r = 0;
     if (r > n - 2) r = n - 2;
     while (r > 0 && tri_row_start(n, r) > t) --r;
@@ -262,7 +266,7 @@ __device__ __forceinline__ void seg_setup(const SbmDev& d, int64_t g, SbmPairDev
     P.pre_s = d.pre + os + s;
     P.tri_r = d.tri + orr + r;
     P.tot_s = P.pre_s[P.ns];
-    P.inv_ns = P.ns > 0 ? __ddiv_rn(1.0, (double)P.ns) : 0.0;
+    P.inv_ns = P.ns > 0 ? __frcp_rn((float)P.ns) : 0.f;
     P.om = d.omega[(int64_t)r * d.K + s];
     const int64_t size = table_size(P.tri, P.nr, P.ns);
     t0 = sg * SBM_SEG;
@@ -446,12 +450,18 @@ __global__ void __launch_bounds__(256) k_sbm_segments_warp(SbmDev d, int64_t G, 
         int64_t m = t0;
         uint32_t j = 0;
         while (m < t1) {
-            const U32x4 x = philox4x32_10((uint32_t)g, (uint32_t)((uint64_t)g >> 32), j, STREAM_SBM, d.seed);
+            // the draw and its target mass by lane 0 alone, then shared with the warp
+            double V = 0.0;
+            uint64_t w23 = 0;
+            if (lane == 0) {
+                const U32x4 x = philox4x32_10((uint32_t)g, (uint32_t)((uint64_t)g >> 32), j, STREAM_SBM, d.seed);
+                const uint64_t w01 = (uint64_t)x.x | ((uint64_t)x.y << 32);
+                w23 = (uint64_t)x.z | ((uint64_t)x.w << 32);
+                const double pu = __dmul_rn((double)((w01 >> 11) + 1), TWO_M53);
+                V = __dadd_rn(prefix_mass(P, m), -log(pu));
+            }
             ++j;
-            const uint64_t w01 = (uint64_t)x.x | ((uint64_t)x.y << 32);
-            const uint64_t w23 = (uint64_t)x.z | ((uint64_t)x.w << 32);
-            const double pu = __dmul_rn((double)((w01 >> 11) + 1), TWO_M53);
-            const double V = __dadd_rn(prefix_mass(P, m), -log(pu));
+            V = __shfl_sync(0xffffffffu, V, 0);
             if (!(Fend > V)) break;
             int64_t a0 = m, a1 = t1 - 1;
             warp_skip_search(P, V, a0, a1, lane);
