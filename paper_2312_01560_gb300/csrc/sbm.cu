@@ -159,15 +159,15 @@ __global__ void k_sbm_fill(const int32_t* block, const double* theta, int64_t n,
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < K; r += warps) {
         int64_t pos = r == 0 ? 0 : (int64_t)bincl[r - 1];
-        for (int64_t base = 0; base < n; base += 256) {
-            int32_t c[8];   // eight independent loads in flight, then the ballots in order
+        for (int64_t base = 0; base < n; base += 1024) {
+            int32_t c[32];   // 32 independent loads in flight, then the ballots in order
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
+            for (int k = 0; k < 32; ++k) {
                 const int64_t i = base + 32 * k + lane;
-                c[k] = i < n ? block[i] : -1;
+                c[k] = i < n ? __ldg(block + i) : -1;
             }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
+            for (int k = 0; k < 32; ++k) {
                 const int64_t i = base + 32 * k + lane;
                 const bool mine = c[k] == r;
                 const unsigned m = __ballot_sync(0xffffffffu, mine);
@@ -183,13 +183,15 @@ __global__ void k_sbm_fill(const int32_t* block, const double* theta, int64_t n,
 }
 
 // Per block, a warp each, left to right: Pre_r[k] = sum_{q<k} theta, and
-// Tri_r[a] = sum_{a'<a} theta_a' (Tot_r - Pre_r[a'+1]).  The lanes load 32 terms at a time;
-// the running sum then takes them one by one through shuffles, every lane doing the same
-// additions in the same order (so all hold the same value): the sums of a sequential loop,
-// without a round trip through memory between one term and the next.
-__global__ void k_sbm_prefix(int K, const unsigned long long* __restrict__ bincl, const double* __restrict__ th,
-                             double* __restrict__ pre, double* __restrict__ tri) {
-    const int lane = threadIdx.x & 31;
+// Tri_r[a] = sum_{a'<a} theta_a' (Tot_r - Pre_r[a'+1]).  The lanes load (or form) 32 terms at
+// a time into shared memory; lane 0 alone adds them in order and stores the running sums, so
+// the chain of FP64 additions is one lane's (FP64 runs at a small fraction of the FP32 rate
+// here) and no term waits on a round trip through global memory.
+__global__ void __launch_bounds__(128) k_sbm_prefix(int K, const unsigned long long* __restrict__ bincl,
+                                                    const double* __restrict__ th, double* __restrict__ pre,
+                                                    double* __restrict__ tri) {
+    __shared__ double sv[4][32];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < K; r += warps) {
         const int64_t o = r == 0 ? 0 : (int64_t)bincl[r - 1];
@@ -199,27 +201,29 @@ __global__ void k_sbm_prefix(int K, const unsigned long long* __restrict__ bincl
         double run = 0.0;
         for (int64_t base = 0; base < nr; base += 32) {
             const int cnt = nr - base < 32 ? (int)(nr - base) : 32;
-            const double v = lane < cnt ? th[o + base + lane] : 0.0;
-            double mine = 0.0;
-            for (int j = 0; j < cnt; ++j) {
-                run = __dadd_rn(run, __shfl_sync(0xffffffffu, v, j));
-                if (lane == j) mine = run;
-            }
-            if (lane < cnt) P[base + lane + 1] = mine;
+            sv[wl][lane] = lane < cnt ? th[o + base + lane] : 0.0;
+            __syncwarp();
+            if (lane == 0)
+                for (int j = 0; j < cnt; ++j) {
+                    run = __dadd_rn(run, sv[wl][j]);
+                    P[base + j + 1] = run;
+                }
+            __syncwarp();
         }
         if (lane == 0) P[0] = 0.0;
-        const double tot = run;
+        const double tot = __shfl_sync(0xffffffffu, run, 0);
         __syncwarp();
         run = 0.0;
         for (int64_t base = 0; base < nr; base += 32) {
             const int cnt = nr - base < 32 ? (int)(nr - base) : 32;
-            const double x = lane < cnt ? __dmul_rn(th[o + base + lane], __dsub_rn(tot, P[base + lane + 1])) : 0.0;
-            double mine = 0.0;
-            for (int j = 0; j < cnt; ++j) {
-                run = __dadd_rn(run, __shfl_sync(0xffffffffu, x, j));
-                if (lane == j) mine = run;
-            }
-            if (lane < cnt) T[base + lane + 1] = mine;
+            sv[wl][lane] = lane < cnt ? __dmul_rn(th[o + base + lane], __dsub_rn(tot, P[base + lane + 1])) : 0.0;
+            __syncwarp();
+            if (lane == 0)
+                for (int j = 0; j < cnt; ++j) {
+                    run = __dadd_rn(run, sv[wl][j]);
+                    T[base + j + 1] = run;
+                }
+            __syncwarp();
         }
         if (lane == 0) T[0] = 0.0;
     }
