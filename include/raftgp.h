@@ -373,7 +373,7 @@ raftgp_status raftgp_partition_batched(const raftgp_csr* g, const int64_t* graph
 /* ---- Differentiation form (the paper trains nothing: its GNN stays random, Section III-B;
  * these calls let the Eq. 6 weights be tuned against a relaxed modularity) ----
  * All arrays are device FP32, row-major; widths (lin, lout, d) are 32, 64 or 128; K <= 128.
- * H_in, H_out, dH_out, dH_in and Z start on 16-byte boundaries (RAFTGP_EINVAL otherwise).
+ * H_in, H_out, dH_out, dH_in, Z and dZ start on 16-byte boundaries (RAFTGP_EINVAL otherwise).
  * Each call validates the graph on the device first (malformed graph: RAFTGP_EINVAL, nothing
  * else runs) and synchronises the stream once for that check.  `ws` is a device workspace
  * of at least raftgp_diff_workspace_size(n, width, K) bytes, width = the largest layer

@@ -826,10 +826,11 @@ raftgp_status layer_args(const float* H_in, int lin, const float* W, int lout, c
     return RAFTGP_OK;
 }
 
+// Z is read and dZ written in 16-byte pieces.
 raftgp_status softmod_args(const raftgp_csr* g, const float* Z, int d, const float* mu, int K, float tau,
-                           const void* loss) {
+                           const void* loss, const float* dZ) {
     if (!Z || !mu || !loss) return fail(RAFTGP_EINVAL, "NULL argument");
-    if ((uintptr_t)Z & 15) return fail(RAFTGP_EINVAL, "Z must be 16-byte aligned");
+    if (((uintptr_t)Z | (uintptr_t)dZ) & 15) return fail(RAFTGP_EINVAL, "Z and dZ must be 16-byte aligned");
     if (!width_ok(d)) return fail(RAFTGP_EUNSUPPORTED, "d must be 32, 64 or 128");
     if (K < 1 || K > 128) return fail(RAFTGP_EUNSUPPORTED, "K must be in [1, 128]");
     if (!(tau > 0.f)) return fail(RAFTGP_EINVAL, "tau must be positive");
@@ -888,7 +889,7 @@ raftgp_status raftgp_softmod_loss(const raftgp_csr* g, const float* Z, int32_t d
                                   raftgp_stream_t stream) {
     raftgp_status st = check_csr(g);
     if (st) return st;
-    if ((st = softmod_args(g, Z, d, mu, K, tau, loss))) return st;
+    if ((st = softmod_args(g, Z, d, mu, K, tau, loss, dZ))) return st;
     if (!ws) return fail(RAFTGP_EINVAL, "NULL argument");
     if (ws_bytes < raftgp_diff_workspace_size(g->n, d, K)) return fail(RAFTGP_ENOMEM, "workspace too small");
     cudaStream_t s = (cudaStream_t)stream;
@@ -950,7 +951,7 @@ raftgp_status raftgp_diff_plan_layer_backward(const raftgp_diff_plan* p, const f
 raftgp_status raftgp_diff_plan_softmod_loss(const raftgp_diff_plan* p, const float* Z, int32_t d, const float* mu,
                                             int32_t K, float tau, double* loss, float* dZ, raftgp_stream_t stream) {
     if (!p) return fail(RAFTGP_EINVAL, "NULL plan");
-    raftgp_status st = softmod_args(&p->g, Z, d, mu, K, tau, loss);
+    raftgp_status st = softmod_args(&p->g, Z, d, mu, K, tau, loss, dZ);
     if (st) return st;
     if (d > p->width || K > p->K) return fail(RAFTGP_EINVAL, "d or K larger than the plan's");
     cudaStream_t s = (cudaStream_t)stream;

@@ -5,7 +5,7 @@ workspace pointer up to a 256-byte boundary inside it, so a workspace handed ove
 a boundary must give the same results, bit for bit, as an aligned one (the TMA, cp.async and
 16-byte accesses into workspace pieces stay aligned).  The layer arrays of the
 differentiation calls are read and written in 16-byte pieces: a misaligned one is rejected
-with RAFTGP_EINVAL before any launch."""
+with RAFTGP_EINVAL before any launch, and so is a misaligned loss gradient dZ."""
 import numpy as np
 import pytest
 import torch
@@ -73,6 +73,14 @@ def test_misaligned_layer_arrays_are_rejected(cuda):
     assert H_odd.is_contiguous() and H_odd.data_ptr() % 16 == 4
     with pytest.raises(api._abi.RaftgpError, match="16-byte"):
         api.gcn_layer_forward(dg, H_odd, W)
-    plan = api.DiffPlan(dg, 64, 0)
+    plan = api.DiffPlan(dg, 64, 4)
     with pytest.raises(api._abi.RaftgpError, match="16-byte"):
         plan.layer_backward(torch.zeros((g.n, 64), device=cuda), W, H_odd)
+    # the loss gradient is written in 16-byte pieces too: an odd dZ is refused before any launch
+    import ctypes as C
+    Z = torch.nn.functional.normalize(torch.ones((g.n, 64), device=cuda))
+    mu = Z[:4].contiguous()
+    loss = torch.empty((), dtype=torch.float64, device=cuda)
+    st = api.lib().raftgp_diff_plan_softmod_loss(plan._h, C.c_void_p(Z.data_ptr()), 64, C.c_void_p(mu.data_ptr()), 4,
+                                                 0.1, C.c_void_p(loss.data_ptr()), C.c_void_p(H_odd.data_ptr()), None)
+    assert st == api._abi.EINVAL and "dZ" in api.lib().raftgp_last_error().decode()
