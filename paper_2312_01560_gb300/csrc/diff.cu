@@ -1,7 +1,8 @@
 // diff.cu -- the differentiation form: forward and backward of one Eq. 6 GCN layer, a relaxed
 // soft-assignment modularity loss with its gradient, an Adam step, and centroids from labels.
 //
-// Layer (FP32 storage, FP32 arithmetic, FP64 for the reductions over points):
+// Layer (FP32 storage, FP32 arithmetic; sums over many points end in FP64: the weight
+// gradient's block partials are added in FP64, the loss adds FP32 sums of eight rows in FP64):
 //     P = H W,  A = Ahat P,  T = tanh(A),  H' = T / ||T||_row          (a zero row stays 0)
 //     Ahat = Dhat^-1/2 (A + I) Dhat^-1/2, dhat = d + 1
 // Backward with recomputation (only the layer input is kept): P and A are computed again,
